@@ -1,0 +1,226 @@
+"""FP64 CPU oracle of the modified Artificial Retina - TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA path never calls it and it
+never calls the CUDA path; the two share no code.  The arithmetic lives in
+``retina_oracle.c`` (plain C, double precision, libm ``exp``) plus, for the
+learned-seed rows, ``seednet.py`` (numpy, double precision).  This module only
+compiles that C file with gcc, loads it with ctypes and marshals numpy arrays.
+
+Functions and the passages they follow (arXiv:1709.08610):
+
+* :func:`rgh`, :func:`response` - Eq. 1 and its gradient / Hessian
+  (Section 2, the remark on the small overhead of derivatives).
+* :func:`grid_response` - Eq. 2, step 2 of the grid algorithm (Section 2).
+* :func:`grid_maxima` - steps 3-4 of the grid algorithm: strict 8-neighbour
+  local maxima at or above R0.
+* :func:`local_search` - Algorithm 1 with the truncated Newton update and the
+  annealed sigma schedule of Section 3.
+* :func:`extract_tracks` - the last two lines of Algorithm 1: cluster the
+  converged points and keep the best of each cluster above R0.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "retina_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "libretina_oracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+TOY2D = 0
+VELO_SLOPES = 1
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 2), ("step", ctypes.c_double * 2), ("n", ctypes.c_int64 * 2)]
+
+
+class _LsOpts(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_double * 8), ("c1", ctypes.c_double),
+                ("max_halvings", ctypes.c_int32), ("step_cap_cells", ctypes.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, IEEE semantics, no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            D = ctypes.c_double
+            L.or_rgh.argtypes = [P, I64, ctypes.c_int, P, D, P]
+            L.or_response.argtypes = [P, I64, ctypes.c_int, P, D]
+            L.or_response.restype = D
+            L.or_response_points.argtypes = [P, I64, ctypes.c_int, P, I64, D, P]
+            L.or_grid_response.argtypes = [P, I64, ctypes.c_int, P, D, P]
+            L.or_grid_maxima.argtypes = [P, I64, I64, D, P, I64, P]
+            L.or_grid_maxima.restype = I64
+            L.or_local_search.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, P, P, P, P]
+            L.or_extract_tracks.argtypes = [P, P, P, I64, P, D, D, P, I64]
+            L.or_extract_tracks.restype = I64
+            _LIB = L
+    return _LIB
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _hits(h) -> np.ndarray:
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    if h.ndim != 2 or h.shape[1] != 4:
+        raise ValueError("hits must be float32 [H, 4]")
+    return h
+
+
+def make_grid(lo: Sequence[float], step: Sequence[float], n: Sequence[int]) -> _Grid:
+    g = _Grid()
+    for a in range(2):
+        g.lo[a] = float(lo[a])
+        g.step[a] = float(step[a])
+        g.n[a] = int(n[a])
+    return g
+
+
+def grid_of(wl) -> _Grid:
+    return make_grid(wl.grid_lo, wl.grid_step, wl.grid_n)
+
+
+def cell_centres(lo, step, n) -> Tuple[np.ndarray, np.ndarray]:
+    """Cell centres lo + (i + 1/2) step per axis (exact binary for step = 2^-k)."""
+    c0 = lo[0] + (np.arange(n[0], dtype=np.float64) + 0.5) * step[0]
+    c1 = lo[1] + (np.arange(n[1], dtype=np.float64) + 0.5) * step[1]
+    return c0, c1
+
+
+def rgh(hits, model: int, theta, sigma: float) -> dict:
+    """R, grad R, Hess R at one theta (Eq. 1 and its derivatives)."""
+    h = _hits(hits)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(2)
+    out = np.zeros(12)
+    lib().or_rgh(_ptr(h), h.shape[0], model, _ptr(th), float(sigma), _ptr(out))
+    return dict(R=out[0], grad=out[1:3].copy(), hess=np.array([[out[3], out[4]], [out[4], out[5]]]),
+                grad_abs=out[7:9].copy(), hess_abs=np.array([[out[9], out[10]], [out[10], out[11]]]))
+
+
+def response(hits, model: int, theta, sigma: float) -> np.ndarray:
+    """R(theta_p) for points theta [P, 2] (Eq. 1)."""
+    h = _hits(hits)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 2)
+    R = np.zeros(th.shape[0])
+    lib().or_response_points(_ptr(h), h.shape[0], model, _ptr(th), th.shape[0], float(sigma), _ptr(R))
+    return R
+
+
+def grid_response(hits, model: int, lo, step, n, sigma: float) -> np.ndarray:
+    """R[i1, i0] over the grid of units (Eq. 2)."""
+    h = _hits(hits)
+    g = make_grid(lo, step, n)
+    R = np.zeros((int(n[1]), int(n[0])))
+    lib().or_grid_response(_ptr(h), h.shape[0], model, ctypes.byref(g), float(sigma), _ptr(R))
+    return R
+
+
+def grid_maxima(R: np.ndarray, R0: float, cap: Optional[int] = None, with_margin: bool = False):
+    """Linear indices of strict 3x3 local maxima with R >= R0 (ties -> lower index)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    n1, n0 = R.shape
+    cap = R.size if cap is None else cap
+    idx = np.zeros(max(cap, 1), dtype=np.int64)
+    margin = np.zeros(R.shape) if with_margin else None
+    cnt = lib().or_grid_maxima(_ptr(R), n0, n1, float(R0), _ptr(idx), cap, _ptr(margin))
+    out = idx[:min(cnt, cap)].copy()
+    return (out, cnt, margin) if with_margin else out
+
+
+def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, step, n,
+                 c1: float = 1e-4, max_halvings: int = 8, step_cap_cells: float = 4.0):
+    """Algorithm 1's q truncated-Newton updates for every seed.
+
+    Returns (theta [n, 2] float64, R_final [n], status [n] uint8, margin [n]).
+    """
+    h = _hits(hits)
+    s = np.ascontiguousarray(seeds, dtype=np.float32).reshape(-1, 2)
+    o = _LsOpts()
+    o.q = len(sigma_schedule)
+    if not 1 <= o.q <= 8:
+        raise ValueError("1 <= q <= 8")
+    for j, v in enumerate(sigma_schedule):
+        o.sigma[j] = float(v)
+    o.c1 = float(c1)
+    o.max_halvings = int(max_halvings)
+    o.step_cap_cells = float(step_cap_cells)
+    g = make_grid(lo, step, n)
+    ns = s.shape[0]
+    th = np.zeros((ns, 2))
+    R = np.zeros(ns)
+    st = np.zeros(ns, dtype=np.uint8)
+    m = np.zeros(ns)
+    lib().or_local_search(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
+                          _ptr(th), _ptr(R), _ptr(st), _ptr(m))
+    return th, R, st, m
+
+
+def extract_tracks(theta, R, status, lo, step, n, R0: float, merge_cells: float = 2.0) -> np.ndarray:
+    """Indices of the kept points, in decreasing-R order (cluster + select)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 2)
+    Rv = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
+    st = None if status is None else np.ascontiguousarray(status, dtype=np.uint8).reshape(-1)
+    g = make_grid(lo, step, n)
+    npt = th.shape[0]
+    keep = np.zeros(max(npt, 1), dtype=np.int64)
+    cnt = lib().or_extract_tracks(_ptr(th), _ptr(Rv), _ptr(st), npt, ctypes.byref(g), float(R0),
+                                  float(merge_cells), _ptr(keep), npt)
+    return keep[:cnt].copy()
+
+
+# ---------------------------------------------------------------------------
+# Track-finding evaluation (Section 3: a track is reconstructed when an
+# estimate lies within epsilon of its true parameters).
+# ---------------------------------------------------------------------------
+
+def match_tracks(found: np.ndarray, truth: np.ndarray, tol: Sequence[float]) -> Tuple[int, int]:
+    """Greedy one-to-one matching by ascending inf-norm distance (scaled by tol).
+
+    Returns (matched, n_found).  truth: [T, 2] parameters of reconstructible
+    tracks; found: [F, 2].
+    """
+    found = np.asarray(found, dtype=np.float64).reshape(-1, 2)
+    truth = np.asarray(truth, dtype=np.float64).reshape(-1, 2)
+    if found.size == 0 or truth.size == 0:
+        return 0, found.shape[0]
+    tol = np.asarray(tol, dtype=np.float64)
+    d = np.max(np.abs(found[:, None, :] - truth[None, :, :]) / tol[None, None, :], axis=2)
+    pairs = np.argwhere(d <= 1.0)
+    order = np.argsort(d[pairs[:, 0], pairs[:, 1]], kind="stable")
+    used_f = np.zeros(found.shape[0], bool)
+    used_t = np.zeros(truth.shape[0], bool)
+    m = 0
+    for k in order:
+        f, t = pairs[k]
+        if not used_f[f] and not used_t[t]:
+            used_f[f] = used_t[t] = True
+            m += 1
+    return m, found.shape[0]

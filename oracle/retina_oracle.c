@@ -1,0 +1,386 @@
+/*
+ * FP64 CPU oracle of the modified Artificial Retina (arXiv:1709.08610).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the bench load this file's library.  It shares no source,
+ * header, table or helper with the CUDA path, and the CUDA path never calls
+ * it.  Everything is plain double arithmetic with libm exp(), written for a
+ * reader to check against the paper by eye; OpenMP only splits independent
+ * cells / seeds / events across threads and never changes an operation order
+ * inside one cell or seed.
+ *
+ * Notation (Section 2, Eq. 1): hits x_k, pattern theta = (theta0, theta1),
+ * residual r_k = h_k - J_k theta (the hit minus the track's prediction in the
+ * hit's detector plane), s^2 = |r_k|^2,
+ *     R(theta) = sum_k exp(-s_k^2 / sigma^2).
+ * Track models:
+ *   model 0, the 2D toy (Section 2, Figure 1): theta = (alpha, beta),
+ *     prediction alpha*x + beta in the plane x = const, so h = y,
+ *     J = [x, 1] (1 x 2).
+ *   model 1, the simplified VELO (Section 3): theta = (t_x, t_y), a straight
+ *     line through the origin crossing the layer z = const at (t_x z, t_y z),
+ *     so h = (x, y), J = z * I_2.
+ * Derivatives (Section 2, "gradient and Hessian ... small overhead"):
+ *     grad R = (2 / sigma^2) sum_k e_k J_k^T r_k
+ *     Hess R = sum_k e_k [ (4 / sigma^4) (J_k^T r_k)(J_k^T r_k)^T
+ *                          - (2 / sigma^2) J_k^T J_k ].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_TOY2D 0
+#define OR_VELO_SLOPES 1
+
+typedef struct {
+    double lo[2];
+    double step[2];
+    int64_t n[2];
+} or_grid;
+
+/* Residual r (m = 1 or 2 components) and Jacobian rows J (m x 2) of one hit. */
+static int hit_residual(const float *hit, int model, const double th[2], double r[2], double J[2][2]) {
+    const double x = (double)hit[0], y = (double)hit[1], z = (double)hit[2];
+    if (model == OR_TOY2D) {
+        J[0][0] = x;
+        J[0][1] = 1.0;
+        r[0] = y - (th[0] * x + th[1]);
+        return 1;
+    }
+    J[0][0] = z; J[0][1] = 0.0;
+    J[1][0] = 0.0; J[1][1] = z;
+    r[0] = x - th[0] * z;
+    r[1] = y - th[1] * z;
+    return 2;
+}
+
+/*
+ * Eq. 1 with its gradient and Hessian at one theta.
+ * out[0] = R, out[1..2] = grad, out[3..5] = (H00, H01, H11),
+ * out[6] = sum_k e_k (= R, kept for symmetry),
+ * out[7..8] = sum of |gradient terms| per component,
+ * out[9..11] = sum of |Hessian terms| per entry (scales for tolerances).
+ */
+void or_rgh(const float *hits, int64_t n_hits, int model, const double theta[2], double sigma, double *out) {
+    const double inv_s2 = 1.0 / (sigma * sigma);
+    double R = 0, g0 = 0, g1 = 0, h00 = 0, h01 = 0, h11 = 0;
+    double ag0 = 0, ag1 = 0, ah00 = 0, ah01 = 0, ah11 = 0;
+    for (int64_t k = 0; k < n_hits; ++k) {
+        double r[2], J[2][2];
+        const int m = hit_residual(hits + 4 * k, model, theta, r, J);
+        double s2 = 0.0;
+        for (int a = 0; a < m; ++a) s2 += r[a] * r[a];
+        const double e = exp(-s2 * inv_s2);
+        /* J^T r and J^T J */
+        double jr[2] = {0.0, 0.0}, jj[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int c = 0; c < 2; ++c)
+            for (int a = 0; a < m; ++a) jr[c] += J[a][c] * r[a];
+        for (int c = 0; c < 2; ++c)
+            for (int d = 0; d < 2; ++d)
+                for (int a = 0; a < m; ++a) jj[c][d] += J[a][c] * J[a][d];
+        const double tg0 = 2.0 * inv_s2 * e * jr[0];
+        const double tg1 = 2.0 * inv_s2 * e * jr[1];
+        const double t00 = e * (4.0 * inv_s2 * inv_s2 * jr[0] * jr[0] - 2.0 * inv_s2 * jj[0][0]);
+        const double t01 = e * (4.0 * inv_s2 * inv_s2 * jr[0] * jr[1] - 2.0 * inv_s2 * jj[0][1]);
+        const double t11 = e * (4.0 * inv_s2 * inv_s2 * jr[1] * jr[1] - 2.0 * inv_s2 * jj[1][1]);
+        R += e;
+        g0 += tg0; g1 += tg1;
+        h00 += t00; h01 += t01; h11 += t11;
+        ag0 += fabs(tg0); ag1 += fabs(tg1);
+        ah00 += fabs(t00); ah01 += fabs(t01); ah11 += fabs(t11);
+    }
+    out[0] = R; out[1] = g0; out[2] = g1;
+    out[3] = h00; out[4] = h01; out[5] = h11;
+    out[6] = R; out[7] = ag0; out[8] = ag1;
+    out[9] = ah00; out[10] = ah01; out[11] = ah11;
+}
+
+/* Eq. 1 alone (no derivatives). */
+double or_response(const float *hits, int64_t n_hits, int model, const double theta[2], double sigma) {
+    const double inv_s2 = 1.0 / (sigma * sigma);
+    double R = 0.0;
+    for (int64_t k = 0; k < n_hits; ++k) {
+        double r[2], J[2][2];
+        const int m = hit_residual(hits + 4 * k, model, theta, r, J);
+        double s2 = 0.0;
+        for (int a = 0; a < m; ++a) s2 += r[a] * r[a];
+        R += exp(-s2 * inv_s2);
+    }
+    return R;
+}
+
+/* Responses at a list of points: R[p] = R(theta_p). */
+void or_response_points(const float *hits, int64_t n_hits, int model, const double *theta, int64_t n_pts,
+                        double sigma, double *R) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < n_pts; ++p) R[p] = or_response(hits, n_hits, model, theta + 2 * p, sigma);
+}
+
+/* Grid of units (Eq. 2, step 2 of the grid algorithm): R[i1][i0] = R(theta_{i0 i1}),
+ * cell centres theta_a = lo_a + (i_a + 1/2) step_a. */
+void or_grid_response(const float *hits, int64_t n_hits, int model, const or_grid *g, double sigma, double *R) {
+    const int64_t n0 = g->n[0], n1 = g->n[1];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i1 = 0; i1 < n1; ++i1) {
+        for (int64_t i0 = 0; i0 < n0; ++i0) {
+            double th[2];
+            th[0] = g->lo[0] + ((double)i0 + 0.5) * g->step[0];
+            th[1] = g->lo[1] + ((double)i1 + 0.5) * g->step[1];
+            R[i1 * n0 + i0] = or_response(hits, n_hits, model, th, sigma);
+        }
+    }
+}
+
+/*
+ * Cluster selection on the grid (steps 3-4 of the grid algorithm): a unit is
+ * selected when its response is at least R0 and it beats every existing
+ * neighbour of its 3 x 3 neighbourhood in the order (R, -linear index), i.e.
+ * a strict local maximum with ties going to the lower linear index.  Writes
+ * the linear indices (i1 * n0 + i0) of the selected units in increasing
+ * order; returns how many there are (which may exceed cap; only cap are
+ * written).  margin_out (nullable, one per unit) receives, for every unit,
+ * min over its comparisons of |R - R_other| (including R - R0): the distance
+ * of that unit's decision from a tie.
+ */
+int64_t or_grid_maxima(const double *R, int64_t n0, int64_t n1, double R0, int64_t *idx_out, int64_t cap,
+                       double *margin_out) {
+    int64_t count = 0;
+    for (int64_t i1 = 0; i1 < n1; ++i1) {
+        for (int64_t i0 = 0; i0 < n0; ++i0) {
+            const int64_t lin = i1 * n0 + i0;
+            const double v = R[lin];
+            int is_max = v >= R0;
+            double margin = fabs(v - R0);
+            for (int d1 = -1; d1 <= 1; ++d1) {
+                for (int d0 = -1; d0 <= 1; ++d0) {
+                    if (d0 == 0 && d1 == 0) continue;
+                    const int64_t j0 = i0 + d0, j1 = i1 + d1;
+                    if (j0 < 0 || j0 >= n0 || j1 < 0 || j1 >= n1) continue;
+                    const int64_t nb = j1 * n0 + j0;
+                    const double w = R[nb];
+                    const int beats = (v > w) || (v == w && lin < nb);
+                    if (!beats) is_max = 0;
+                    if (fabs(v - w) < margin) margin = fabs(v - w);
+                }
+            }
+            if (margin_out) margin_out[lin] = margin;
+            if (is_max) {
+                if (count < cap) idx_out[count] = lin;
+                ++count;
+            }
+        }
+    }
+    return count;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local search: Algorithm 1 with the truncated Newton update (Section 3).    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t q;               /* number of updates per seed (Section 2: fixed count) */
+    double sigma[8];         /* bandwidth used at update j (Section 3: annealed)    */
+    double c1;               /* Armijo sufficient-increase constant                 */
+    int32_t max_halvings;    /* backtracking halvings after the unit step           */
+    double step_cap_cells;   /* cap on ||p / step||_inf, in grid cells              */
+} or_ls_opts;
+
+/*
+ * One truncated Newton direction (Newton-CG, Nocedal & Wright Alg. 7.1)
+ * for maximising R, i.e. minimising f = -R with gradient -g and Hessian
+ * B = -H.  CG on B p = g from p = 0, forcing tolerance
+ * eps = min(1/2, sqrt(|g|)) |g|, stopping at negative curvature (first
+ * iteration: fall back to the steepest-ascent direction g) and after at
+ * most 2 iterations (the dimension).  *margin gets the smallest distance of
+ * a branch test from its threshold, in units of the FP32 parity tolerance
+ * of the quantities compared (1e-4 of the sum of absolute terms).
+ */
+static void newton_cg_direction(const double g[2], const double H[3], const double gabs[2],
+                                const double Habs[3], double p[2], double *margin) {
+    const double B00 = -H[0], B01 = -H[1], B11 = -H[2];
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1]);
+    const double eps = fmin(0.5, sqrt(gn)) * gn;
+    double z[2] = {0.0, 0.0};
+    double r[2] = {-g[0], -g[1]};   /* residual of B z = g at z = 0, as B z - g */
+    double d[2] = {g[0], g[1]};
+    const double hscale = Habs[0] + 2.0 * Habs[1] + Habs[2];
+    for (int it = 0; it < 2; ++it) {
+        const double Bd0 = B00 * d[0] + B01 * d[1];
+        const double Bd1 = B01 * d[0] + B11 * d[1];
+        const double dBd = d[0] * Bd0 + d[1] * Bd1;
+        const double dd = d[0] * d[0] + d[1] * d[1];
+        {
+            const double tol = 1e-4 * hscale * dd;
+            const double m = tol > 0.0 ? fabs(dBd) / tol : 0.0;
+            if (m < *margin) *margin = m;
+        }
+        if (dBd <= 0.0) {
+            if (it == 0) { p[0] = g[0]; p[1] = g[1]; }
+            else { p[0] = z[0]; p[1] = z[1]; }
+            return;
+        }
+        const double rr = r[0] * r[0] + r[1] * r[1];
+        const double alpha = rr / dBd;
+        z[0] += alpha * d[0];
+        z[1] += alpha * d[1];
+        double rn[2] = {r[0] + alpha * Bd0, r[1] + alpha * Bd1};
+        const double rnn = sqrt(rn[0] * rn[0] + rn[1] * rn[1]);
+        if (it == 0) {
+            const double tol = 1e-4 * (gabs[0] + gabs[1]);
+            const double m = tol > 0.0 ? fabs(rnn - eps) / tol : 0.0;
+            if (m < *margin) *margin = m;
+        }
+        if (rnn < eps) { p[0] = z[0]; p[1] = z[1]; return; }
+        const double beta = (rn[0] * rn[0] + rn[1] * rn[1]) / rr;
+        d[0] = -rn[0] + beta * d[0];
+        d[1] = -rn[1] + beta * d[1];
+        r[0] = rn[0];
+        r[1] = rn[1];
+    }
+    p[0] = z[0];
+    p[1] = z[1];
+}
+
+/*
+ * One seed through Algorithm 1's q updates.  Returns the status:
+ * 0 ok, 1 some line search accepted no step, 2 final point outside the box,
+ * 3 non-finite.  *margin receives the smallest distance of any discrete
+ * decision (curvature sign, CG stop, Armijo test, box test) from its
+ * threshold, in units of the FP32 parity tolerance of the compared values
+ * (R: 1e-5 R + 1e-6; gradient / Hessian: 1e-4 of the absolute terms;
+ * theta: 1e-3 of a cell), so that callers can tell genuine disagreements
+ * from ties (margin < 1).
+ */
+static int search_one(const float *hits, int64_t n_hits, int model, const float seed[2], const or_ls_opts *o,
+                      const or_grid *box, double theta_out[2], double *R_out, double *margin) {
+    double th[2] = {(double)seed[0], (double)seed[1]};
+    int status = 0;
+    *margin = INFINITY;
+    for (int j = 0; j < o->q; ++j) {
+        const double sigma = o->sigma[j];
+        double rgh[12];
+        or_rgh(hits, n_hits, model, th, sigma, rgh);
+        const double R = rgh[0];
+        const double g[2] = {rgh[1], rgh[2]};
+        const double H[3] = {rgh[3], rgh[4], rgh[5]};
+        const double gabs[2] = {rgh[7], rgh[8]};
+        const double Habs[3] = {rgh[9], rgh[10], rgh[11]};
+        double p[2];
+        newton_cg_direction(g, H, gabs, Habs, p, margin);
+        /* cap the step length, measured in grid cells */
+        const double cells = fmax(fabs(p[0]) / box->step[0], fabs(p[1]) / box->step[1]);
+        if (cells > o->step_cap_cells) {
+            const double s = o->step_cap_cells / cells;
+            p[0] *= s;
+            p[1] *= s;
+        }
+        /* backtracking line search with the Armijo sufficient-increase test */
+        const double slope = g[0] * p[0] + g[1] * p[1];
+        double t = 1.0;
+        int accepted = 0;
+        for (int h = 0; h <= o->max_halvings; ++h) {
+            const double trial[2] = {th[0] + t * p[0], th[1] + t * p[1]};
+            const double Rt = or_response(hits, n_hits, model, trial, sigma);
+            const double need = R + o->c1 * t * slope;
+            const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
+            const double m = fabs(Rt - need) / tol;
+            if (m < *margin) *margin = m;
+            if (Rt >= need) {
+                th[0] = trial[0];
+                th[1] = trial[1];
+                accepted = 1;
+                break;
+            }
+            t *= 0.5;
+        }
+        if (!accepted) status = 1;
+    }
+    *R_out = or_response(hits, n_hits, model, th, o->sigma[o->q - 1]);
+    theta_out[0] = th[0];
+    theta_out[1] = th[1];
+    if (!(isfinite(th[0]) && isfinite(th[1]) && isfinite(*R_out))) return 3;
+    for (int a = 0; a < 2; ++a) {
+        const double lo = box->lo[a], hi = box->lo[a] + (double)box->n[a] * box->step[a];
+        const double m = fmin(fabs(th[a] - lo), fabs(th[a] - hi)) / (1e-3 * box->step[a]);
+        if (m < *margin) *margin = m;
+        if (!(th[a] >= lo && th[a] < hi)) return 2;
+    }
+    return status;
+}
+
+void or_local_search(const float *hits, int64_t n_hits, int model, const float *seeds, int64_t n_seeds,
+                     const or_ls_opts *o, const or_grid *box, double *theta_out, double *R_out, uint8_t *status,
+                     double *margin_out) {
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n_seeds; ++i) {
+        double m;
+        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, theta_out + 2 * i, R_out + i, &m);
+        if (margin_out) margin_out[i] = m;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cluster the converged points and keep the best of each (Algorithm 1).     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double R;
+    int64_t idx;
+} or_rank;
+
+static int rank_cmp(const void *a, const void *b) {
+    const or_rank *x = (const or_rank *)a, *y = (const or_rank *)b;
+    if (x->R > y->R) return -1;
+    if (x->R < y->R) return 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx) ? 1 : 0;
+}
+
+/*
+ * Points with status 0 or 1, inside the box [lo, lo + n step) and with
+ * R >= R0 are candidates.  They are visited by decreasing R (ties: lower
+ * index first); a candidate is kept when, for every point kept before it,
+ * max_a |theta_a - theta_kept_a| / step_a >= merge_cells.  Writes the kept
+ * point indices in that visiting order; returns how many (may exceed cap).
+ * status may be NULL (all 0).
+ */
+int64_t or_extract_tracks(const double *theta, const double *R, const uint8_t *status, int64_t n_points,
+                          const or_grid *box, double R0, double merge_cells, int64_t *keep_out, int64_t cap) {
+    or_rank *cand = (or_rank *)malloc(sizeof(or_rank) * (size_t)(n_points > 0 ? n_points : 1));
+    int64_t nc = 0;
+    for (int64_t i = 0; i < n_points; ++i) {
+        if (status && status[i] > 1) continue;
+        const double t0 = theta[2 * i], t1 = theta[2 * i + 1];
+        if (!(isfinite(t0) && isfinite(t1) && isfinite(R[i]))) continue;
+        int inside = 1;
+        for (int a = 0; a < 2; ++a) {
+            const double v = theta[2 * i + a];
+            const double lo = box->lo[a], hi = box->lo[a] + (double)box->n[a] * box->step[a];
+            if (!(v >= lo && v < hi)) inside = 0;
+        }
+        if (!inside || !(R[i] >= R0)) continue;
+        cand[nc].R = R[i];
+        cand[nc].idx = i;
+        ++nc;
+    }
+    qsort(cand, (size_t)nc, sizeof(or_rank), rank_cmp);
+    int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    int64_t nk = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t i = cand[c].idx;
+        int keep = 1;
+        for (int64_t k = 0; k < nk && keep; ++k) {
+            const int64_t j = kept[k];
+            const double d0 = fabs(theta[2 * i] - theta[2 * j]) / box->step[0];
+            const double d1 = fabs(theta[2 * i + 1] - theta[2 * j + 1]) / box->step[1];
+            if (fmax(d0, d1) < merge_cells) keep = 0;
+        }
+        if (keep) {
+            if (nk < cap) keep_out[nk] = i;
+            kept[nk++] = i;
+        }
+    }
+    free(kept);
+    free(cand);
+    return nk;
+}

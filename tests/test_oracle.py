@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these tests re-types the oracle's formulas: they use hand-worked
+examples (tests/golden), closed forms, finite differences, least squares
+(numpy.linalg.lstsq), library local-maximum filters (scipy.ndimage) and brute
+force, chosen so that a dropped term, a flipped sign, a wrong index or a
+transposed operand anywhere in the oracle breaks at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import WORKLOADS, make_event, make_toy2d_event, close_tracks_event, uniform_seeds
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")))
+E1, E4 = math.exp(-1.0), math.exp(-4.0)
+
+
+def _c(coeffs):
+    return coeffs[0] + coeffs[1] * E1 + coeffs[2] * E4
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 and its derivatives
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["response"], ids=lambda c: c["name"])
+def test_worked_example_response_grad_hess(case):
+    hits = np.array(case["hits"], dtype=np.float32)
+    out = oracle.rgh(hits, case["model"], case["theta"], case["sigma"])
+    assert out["R"] == pytest.approx(_c(case["R"]), rel=1e-14)
+    for a in range(2):
+        assert out["grad"][a] == pytest.approx(_c(case["grad"][a]), rel=1e-12, abs=1e-9)
+        for b in range(2):
+            assert out["hess"][a, b] == pytest.approx(_c(case["hess"][a][b]), rel=1e-12, abs=1e-6)
+    # R alone agrees with R from the derivative routine
+    assert oracle.response(hits, case["model"], [case["theta"]], case["sigma"])[0] == pytest.approx(out["R"], rel=1e-15)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_single_hit_closed_form(model):
+    # one hit displaced by exactly d in the measured coordinate: R = exp(-d^2 / sigma^2)
+    sigma = 0.125
+    for d in [0.0, 0.0625, 0.125, 0.25, 0.5]:
+        if model == 0:
+            hits = np.array([[3.0, 0.25 * 3.0 - 0.5 + d, 0, 0]], np.float32)
+            th = [0.25, -0.5]
+        else:
+            hits = np.array([[0.25 * 64.0 + d, -0.5 * 64.0, 64.0, 0]], np.float32)
+            th = [0.25, -0.5]
+        R = oracle.response(hits, model, [th], sigma)[0]
+        assert R == pytest.approx(math.exp(-(d / sigma) ** 2), rel=1e-14)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_all_hits_on_pattern_gives_R_equal_N_and_closed_form_hessian(model):
+    # hits exactly on the pattern: R = N, grad = 0, Hess = -(2 / sigma^2) sum J^T J
+    th = np.array([0.25, -0.125])
+    sigma = 0.3
+    if model == 0:
+        xs = np.arange(1, 11, dtype=np.float64)
+        hits = np.stack([xs, th[0] * xs + th[1], 0 * xs, 0 * xs], 1).astype(np.float32)
+        JtJ = np.array([[np.sum(xs * xs), np.sum(xs)], [np.sum(xs), len(xs)]])
+    else:
+        zs = np.array([-128.0, -32.0, 16.0, 64.0, 256.0, 512.0])
+        hits = np.stack([th[0] * zs, th[1] * zs, zs, 0 * zs], 1).astype(np.float32)
+        JtJ = np.eye(2) * np.sum(zs * zs)
+    out = oracle.rgh(hits, model, th, sigma)
+    assert out["R"] == len(hits)
+    np.testing.assert_array_equal(out["grad"], [0.0, 0.0])
+    np.testing.assert_allclose(out["hess"], -(2.0 / sigma ** 2) * JtJ, rtol=1e-14)
+
+
+@pytest.mark.parametrize("wl_name", ["toy2d", "velo"])
+def test_bounds_and_permutation_invariance(wl_name):
+    wl = WORKLOADS[wl_name]
+    ev = make_event(wl, 7, 3)
+    rng = np.random.default_rng(0)
+    th = np.asarray(wl.grid_lo) + rng.uniform(0, 1, (64, 2)) * np.asarray(wl.grid_n) * np.asarray(wl.grid_step)
+    R = oracle.response(ev.hits, wl.model, th, wl.sigma_grid)
+    assert np.all(R >= 0) and np.all(R <= ev.n_hits)
+    perm = rng.permutation(ev.n_hits)
+    R2 = oracle.response(ev.hits[perm], wl.model, th, wl.sigma_grid)
+    np.testing.assert_allclose(R2, R, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("wl_name", ["toy2d", "velo"])
+def test_gradient_and_hessian_match_central_differences(wl_name):
+    wl = WORKLOADS[wl_name]
+    ev = make_event(wl, 1, 0, **({"vertex_sigma": (0, 0, 0)} if wl.model == 1 else {}))
+    sigma = wl.sigma_schedule[0]
+    # points near true tracks, where R and its derivatives are far from underflow
+    rng = np.random.default_rng(5)
+    pts = ev.truth[:6, :2] + rng.normal(0, 0.5, (6, 2)) * np.asarray(wl.grid_step)
+    for th in pts:
+        out = oracle.rgh(ev.hits, wl.model, th, sigma)
+        h = 1e-4 * np.asarray(wl.grid_step)
+        g_fd = np.zeros(2)
+        H_fd = np.zeros((2, 2))
+        for a in range(2):
+            ea = np.zeros(2)
+            ea[a] = h[a]
+            Rp = oracle.response(ev.hits, wl.model, [th + ea], sigma)[0]
+            Rm = oracle.response(ev.hits, wl.model, [th - ea], sigma)[0]
+            g_fd[a] = (Rp - Rm) / (2 * h[a])
+            gp = oracle.rgh(ev.hits, wl.model, th + ea, sigma)["grad"]
+            gm = oracle.rgh(ev.hits, wl.model, th - ea, sigma)["grad"]
+            H_fd[:, a] = (gp - gm) / (2 * h[a])
+        scale_g = out["grad_abs"].sum()
+        scale_H = out["hess_abs"].sum()
+        assert np.max(np.abs(g_fd - out["grad"])) <= 1e-6 * scale_g
+        assert np.max(np.abs(H_fd - out["hess"])) <= 1e-6 * scale_H
+        assert out["hess"][0, 1] == out["hess"][1, 0]
+
+
+# --------------------------------------------------------------------------
+# Grid maxima and cluster selection
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["grid_maxima"], ids=lambda c: "R0=%g" % c["R0"])
+def test_worked_example_grid_maxima(case):
+    R = np.array(case["R"], dtype=np.float64)
+    idx = oracle.grid_maxima(R, case["R0"])
+    assert idx.tolist() == case["expected"]
+
+
+def test_grid_maxima_agree_with_library_maximum_filter():
+    ndi = pytest.importorskip("scipy.ndimage")
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 0, 4, vertex_sigma=(0, 0, 0))
+    # a 192 x 160 window of the slope grid (continuous data: no exact ties)
+    lo = (wl.grid_lo[0] + 400 * wl.grid_step[0], wl.grid_lo[1] + 420 * wl.grid_step[1])
+    R = oracle.grid_response(ev.hits, wl.model, lo, wl.grid_step, (192, 160), wl.sigma_grid)
+    assert len(np.unique(R)) == R.size
+    mx = ndi.maximum_filter(R, size=3, mode="constant", cval=-np.inf)
+    expect = np.flatnonzero((R == mx) & (R >= 3.0))
+    assert len(expect) >= 3
+    assert oracle.grid_maxima(R, 3.0).tolist() == expect.tolist()
+
+
+@pytest.mark.parametrize("case", GOLD["extract_tracks"], ids=lambda c: "m=%g" % c["merge_cells"])
+def test_worked_example_extract_tracks(case):
+    b = case["box"]
+    keep = oracle.extract_tracks(np.array(case["theta"]), np.array(case["R"], float), np.array(case["status"]),
+                                 b["lo"], b["step"], b["n"], case["R0"], case["merge_cells"])
+    assert keep.tolist() == case["expected"]
+
+
+def test_extract_tracks_invariants_on_random_points():
+    rng = np.random.default_rng(3)
+    lo, step, n = (-1.0, -1.0), (0.0625, 0.0625), (32, 32)
+    th = rng.uniform(-1.1, 1.1, (600, 2))
+    R = rng.integers(0, 50, 600).astype(float)  # many exact ties in R
+    st = rng.integers(0, 4, 600).astype(np.uint8)
+    m = 2.0
+    keep = oracle.extract_tracks(th, R, st, lo, step, n, 10.0, m)
+    hi = np.asarray(lo) + np.asarray(n) * np.asarray(step)
+    cand = np.flatnonzero((st <= 1) & (R >= 10.0) & np.all((th >= lo) & (th < hi), axis=1))
+    assert set(keep.tolist()) <= set(cand.tolist())
+    dist = lambda i, j: np.max(np.abs(th[i] - th[j]) / np.asarray(step))
+    # kept points are pairwise at least m apart and visited by (R desc, index asc)
+    for a in range(len(keep)):
+        for b in range(a + 1, len(keep)):
+            assert dist(keep[a], keep[b]) >= m
+            assert (R[keep[a]], -keep[a]) > (R[keep[b]], -keep[b])
+    # every rejected candidate lies within m of a kept point ranked before it
+    for c in set(cand.tolist()) - set(keep.tolist()):
+        assert any(dist(c, k) < m and (R[k], -k) > (R[c], -c) for k in keep)
+
+
+# --------------------------------------------------------------------------
+# Local search: truncated Newton (Section 3) inside Algorithm 1
+# --------------------------------------------------------------------------
+
+def test_large_sigma_newton_step_lands_on_least_squares_fit_toy():
+    # For residuals r << sigma, R ~ N - sum r^2 / sigma^2 is quadratic, so a
+    # full Newton step lands on the least-squares line fit up to O(delta (r/sigma)^2).
+    # The start is chosen so the CG forcing test needs the second iteration
+    # (gradient with equal components along both eigenvectors of J^T J).
+    ev = make_toy2d_event(11, 0, n_tracks=1, noise_frac=0.0)
+    x = ev.hits[:, 0].astype(np.float64)
+    y = ev.hits[:, 1].astype(np.float64)
+    A = np.stack([x, np.ones_like(x)], 1)
+    ls = np.linalg.lstsq(A, y, rcond=None)[0]
+    w, V = np.linalg.eigh(A.T @ A)
+    sigma = 1.0
+    for c in (0.04, -0.06, 0.08):
+        start = ls + c * V[:, 0] + c * (w[0] / w[1]) * V[:, 1]
+        s32 = np.array([start], np.float32)
+        th, R, st, m = oracle.local_search(ev.hits, 0, s32, [sigma], (-1, -1), (1e-3, 1e-3), (2000, 2000),
+                                           step_cap_cells=1e9)
+        assert st[0] == 0
+        delta = np.max(np.abs(s32[0] - ls))
+        rmax = np.max(np.abs(A @ s32[0].astype(float) - y))
+        assert np.max(np.abs(th[0] - ls)) < 2.0 * delta * (rmax / sigma) ** 2
+
+
+def test_large_sigma_newton_step_lands_on_least_squares_fit_velo():
+    # Same limit for the slope model: the least-squares slope per axis is
+    # sum(z x) / sum(z^2); J^T J = sum z^2 I is isotropic.
+    ev = make_event(WORKLOADS["velo"], 12, 0, n_tracks=1, noise_frac=0.0, vertex_sigma=(0, 0, 0))
+    h = ev.hits.astype(np.float64)
+    ls = np.array([np.sum(h[:, 2] * h[:, 0]), np.sum(h[:, 2] * h[:, 1])]) / np.sum(h[:, 2] ** 2)
+    sigma = 5.0
+    for off in ((1e-3, -5e-4), (-8e-4, 2e-4)):
+        s32 = np.array([ls + np.asarray(off)], np.float32)
+        th, R, st, m = oracle.local_search(ev.hits, 1, s32, [sigma], (-0.5, -0.5), (2 ** -10,) * 2, (1024, 1024),
+                                           step_cap_cells=1e9)
+        assert st[0] == 0
+        delta = np.max(np.abs(s32[0] - ls))
+        r = np.concatenate([h[:, 0] - s32[0, 0] * h[:, 2], h[:, 1] - s32[0, 1] * h[:, 2]])
+        assert np.max(np.abs(th[0] - ls)) < 2.0 * delta * (np.max(np.abs(r)) / sigma) ** 2
+
+
+def test_newton_converges_quadratically_on_noiseless_track():
+    # Noiseless single VELO track through the origin.  Inside the peak (start
+    # at ~0.1 of its width w = sigma / z_rms) each truncated Newton step
+    # satisfies err_next <= 2 err^2 / w (a Gaussian peak is even in fact
+    # cubic there); 1e-9 covers the float32 rounding of the hits.
+    zs = np.array([-300.0 + 42.0 * p for p in range(26)])
+    t = np.array([0.07, -0.045])
+    hits = np.stack([t[0] * zs, t[1] * zs, zs, 0 * zs], 1).astype(np.float32)
+    sigma = 0.3
+    w = sigma / math.sqrt(np.mean(zs ** 2))
+    seeds = np.array([t + np.array([0.08, -0.05]) * w], np.float32)
+    errs = [np.max(np.abs(seeds[0] - t))]
+    for q in range(1, 4):
+        th, R, st, m = oracle.local_search(hits, 1, seeds, [sigma] * q, (-0.5, -0.5), (2 ** -10,) * 2, (1024, 1024))
+        assert st[0] == 0
+        errs.append(np.max(np.abs(th[0] - t)))
+    for k in range(3):
+        assert errs[k + 1] <= 2.0 * errs[k] ** 2 / w + 1e-9
+    assert errs[1] < 0.05 * errs[0]
+    assert errs[3] < 1e-8
+
+
+def test_negative_curvature_takes_capped_steepest_ascent_and_armijo_by_brute_force():
+    # one hit; a start in the convex tail of its Gaussian has d^T H d > 0 along g,
+    # so the direction is g itself, capped to step_cap_cells; the accepted step is
+    # the first of 1, 1/2, 1/4 ... passing the sufficient-increase test.
+    sigma = 0.25
+    hits = np.array([[0.0, 0.0, 0.0, 0.0]], np.float32)  # toy: y = 0 at x = 0 -> constrains beta only
+    hits = np.array([[1.0, 0.0, 0.0, 0.0], [2.0, 0.0, 0.0, 0.0]], np.float32)
+    start = np.array([0.0, 0.3], np.float64)  # beta = 0.3 > sigma / sqrt(2): convex tail
+    step = (2 ** -8, 2 ** -8)
+    out = oracle.rgh(hits, 0, start, sigma)
+    g = out["grad"]
+    assert g @ out["hess"] @ g > 0
+    cap = 4.0
+    p = g * cap / np.max(np.abs(g) / np.asarray(step))
+    R0 = out["R"]
+    t_expect = None
+    for h in range(9):
+        t = 0.5 ** h
+        Rt = oracle.response(hits, 0, [start + t * p], sigma)[0]
+        if Rt >= R0 + 1e-4 * t * (g @ p):
+            t_expect = t
+            break
+    assert t_expect is not None
+    th, R, st, m = oracle.local_search(hits, 0, np.array([start], np.float32), [sigma], (-1, -1), step, (512, 512),
+                                       step_cap_cells=cap)
+    np.testing.assert_allclose(th[0], start.astype(np.float32).astype(float) + t_expect * p, rtol=0, atol=1e-12)
+
+
+def test_search_maxima_agree_with_brute_force_fine_grid():
+    # tiny event (3 tracks, ~30 hits): every converged point with R >= R0 is a
+    # local maximum of R to within a fine-grid step around it.
+    ev = make_toy2d_event(21, 0, n_tracks=3, noise_frac=0.1)
+    wl = WORKLOADS["toy2d"]
+    sigma = 0.02
+    seeds = uniform_seeds(wl, 512, 21, 0)
+    # the toy's ridge is ill-conditioned: run 12 rounds of 8 updates each
+    for _ in range(12):
+        th, R, st, m = oracle.local_search(ev.hits, 0, seeds, [sigma] * 8, wl.grid_lo, wl.grid_step, wl.grid_n)
+        seeds = th.astype(np.float32)
+    keep = oracle.extract_tracks(th, R, st, wl.grid_lo, wl.grid_step, wl.grid_n, 5.0, 2.0)
+    # stationary points among the kept ones (the rest are still crawling along a ridge)
+    stat = [k for k in keep if np.all(np.abs(oracle.rgh(ev.hits, 0, th[k], sigma)["grad"]) <= 1e-9 *
+                                       oracle.rgh(ev.hits, 0, th[k], sigma)["grad_abs"].sum())]
+    assert len(stat) >= 3
+    fine = 1e-5
+    for k in stat:
+        c = th[k]
+        lo = (c[0] - 50.5 * fine, c[1] - 50.5 * fine)
+        Rf = oracle.grid_response(ev.hits, 0, lo, (fine, fine), (101, 101), sigma)
+        i1, i0 = np.unravel_index(np.argmax(Rf), Rf.shape)
+        best = np.array([lo[0] + (i0 + 0.5) * fine, lo[1] + (i1 + 0.5) * fine])
+        assert np.max(np.abs(best - c)) <= 1.0 * fine
+        assert Rf.max() <= R[k] * (1 + 1e-9)
+
+
+def test_grid_maxima_near_search_maxima():
+    # Grid-scan maxima at or above R0 mostly lie within one cell of the
+    # continuous maximum the Newton search reaches from them (a discrete
+    # maximum on a ridge need not), and the search never lowers R (Armijo).
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 3, 0, vertex_sigma=(0, 0, 0))
+    tr = ev.truth[np.argsort(np.abs(ev.truth[:, 0]) + np.abs(ev.truth[:, 1]))[0], :2]
+    i0 = int(np.floor((tr[0] - wl.grid_lo[0]) / wl.grid_step[0])) - 48
+    i1 = int(np.floor((tr[1] - wl.grid_lo[1]) / wl.grid_step[1])) - 48
+    lo = (wl.grid_lo[0] + i0 * wl.grid_step[0], wl.grid_lo[1] + i1 * wl.grid_step[1])
+    n = (96, 96)
+    R = oracle.grid_response(ev.hits, 1, lo, wl.grid_step, n, wl.sigma_grid)
+    idx = oracle.grid_maxima(R, wl.R0)
+    assert len(idx) >= 1
+    c0, c1 = oracle.cell_centres(lo, wl.grid_step, n)
+    gth = np.stack([c0[idx % n[0]], c1[idx // n[0]]], 1)
+    th, Rs, st, m = oracle.local_search(ev.hits, 1, gth.astype(np.float32), [wl.sigma_grid] * 8, wl.grid_lo,
+                                        wl.grid_step, wl.grid_n)
+    d = np.max(np.abs(th - gth) / np.asarray(wl.grid_step), axis=1)
+    assert np.all(st <= 1)
+    assert np.mean(d <= 1.0) >= 0.9
+    assert np.all(Rs >= R.reshape(-1)[idx] * (1 - 1e-12))
+
+
+def test_figure2_close_tracks_split_and_merge():
+    # Figure 2: small sigma splits each smeared track into several clusters of
+    # activated units, sigma comparable to the smear resolves the two tracks,
+    # large sigma merges them into one cluster.
+    ndi = pytest.importorskip("scipy.ndimage")
+    lo, step, n = (0.0, -0.2), (2 ** -9, 2 ** -9), (256, 256)
+    for seed in range(3):
+        ev = close_tracks_event(seed)
+        counts = {}
+        for sigma in (1e-3, 1e-2, 1e-1):
+            R = oracle.grid_response(ev.hits, 0, lo, step, n, sigma)
+            counts[sigma] = ndi.label(R >= 0.5 * R.max(), structure=np.ones((3, 3)))[1]
+        assert counts[1e-3] > 4
+        assert counts[1e-2] == 2
+        assert counts[1e-1] == 1
