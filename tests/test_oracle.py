@@ -238,7 +238,8 @@ def test_newton_converges_quadratically_on_noiseless_track():
     assert errs[3] < 1e-8
 
 
-def test_negative_curvature_takes_capped_steepest_ascent_and_armijo_by_brute_force():
+@pytest.mark.parametrize("c1", [1e-4, 0.3, 0.6])
+def test_negative_curvature_takes_capped_steepest_ascent_and_armijo_by_brute_force(c1):
     # one hit; a start in the convex tail of its Gaussian has d^T H d > 0 along g,
     # so the direction is g itself, capped to step_cap_cells; the accepted step is
     # the first of 1, 1/2, 1/4 ... passing the sufficient-increase test.
@@ -257,13 +258,45 @@ def test_negative_curvature_takes_capped_steepest_ascent_and_armijo_by_brute_for
     for h in range(9):
         t = 0.5 ** h
         Rt = oracle.response(hits, 0, [start + t * p], sigma)[0]
-        if Rt >= R0 + 1e-4 * t * (g @ p):
+        if Rt >= R0 + c1 * t * (g @ p):
             t_expect = t
             break
     assert t_expect is not None
     th, R, st, m = oracle.local_search(hits, 0, np.array([start], np.float32), [sigma], (-1, -1), step, (512, 512),
-                                       step_cap_cells=cap)
+                                       step_cap_cells=cap, c1=c1)
     np.testing.assert_allclose(th[0], start.astype(np.float32).astype(float) + t_expect * p, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("c1", [1e-4, 0.3, 0.6, 0.9])
+def test_newton_overshoot_backtracks_by_armijo_brute_force(c1):
+    # One VELO hit, seed offset along t_x only: g = (g0, 0) and H is diagonal,
+    # so the first CG iteration is the exact 1D Newton step p = (-g0/H00, 0).
+    # From 0.3 peak widths the step overshoots (increase ratio ~0.41), so the
+    # accepted t depends on c1; the expected t is found by brute force.
+    hits = np.array([[12.5, -25.0, 100.0, 0.0]], np.float32)
+    sigma = 0.25
+    w = sigma / 100.0
+    start = np.array([0.125 + 0.3 * w, -0.25])
+    s32 = np.array([start], np.float32)
+    th0 = s32[0].astype(np.float64)
+    out = oracle.rgh(hits, 1, th0, sigma)
+    g, H = out["grad"], out["hess"]
+    assert g[1] == 0 and H[0, 1] == 0 and H[0, 0] < 0
+    p = np.array([-g[0] / H[0, 0], 0.0])
+    t_expect = None
+    for h in range(9):
+        t = 0.5 ** h
+        if oracle.response(hits, 1, [th0 + t * p], sigma)[0] >= out["R"] + c1 * t * (g @ p):
+            t_expect = t
+            break
+    th, R, st, m = oracle.local_search(hits, 1, s32, [sigma], (-0.5, -0.5), (2 ** -10,) * 2, (1024, 1024),
+                                       step_cap_cells=1e9, c1=c1)
+    if t_expect is None:
+        assert st[0] == 1 and np.all(th[0] == th0)
+    else:
+        assert st[0] == 0
+        np.testing.assert_allclose(th[0], th0 + t_expect * p, rtol=0, atol=1e-15)
+    assert {1e-4: 1.0, 0.3: 1.0, 0.6: 0.5, 0.9: 0.125}[c1] == t_expect
 
 
 def test_search_maxima_agree_with_brute_force_fine_grid():
