@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the Artificial Retina hot path on GB300 (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over one synthetic VELO-like event
+(150 straight tracks, 26 layers, ~3.9k hits): the 1024 x 1024 grid scan
+(Eq. 2 + maxima, grid algorithm of Section 2), the 8192-seed truncated-Newton
+multistart search (Algorithm 1 with the Section 3 update), and the
+cluster / select extraction of both candidate sets.  ``value`` is events per
+second of that step over all ranks (each rank runs its own event: replicas,
+weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+method has) on the host cores, on a bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS, make_event, uniform_seeds  # noqa: E402
+
+WORKLOAD = "velo"
+RUN_SEED = 0
+METRIC = "events/s (grid scan + truncated-Newton search + extraction, one VELO-like event per step)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(wl, n_hits):
+    return {
+        "workload": "velo: one VELO-like event per step (150 tracks from a smeared origin, 26 layers at "
+                    "z=-300..750 mm, 90%% layer efficiency, 10%% noise, %d hits); 1024x1024 slope grid scan "
+                    "(sigma %.4f mm) + 8192-seed truncated-Newton search (q=3, sigma 0.3/0.175/0.05 mm) + "
+                    "track extraction of both" % (n_hits, wl.sigma_grid),
+        "grid": list(wl.grid_n), "seeds": wl.n_seeds, "hits_per_event": n_hits, "q": len(wl.sigma_schedule),
+        "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+        "parallelism": "replicas (one event per rank, no collective on the data path)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step_sample(ev, wl, seeds, row_frac: int, seed_frac: int):
+    """Oracle time for 1/row_frac of the grid rows and 1/seed_frac of the
+    seeds, extrapolated to seconds for the whole step of one event."""
+    import oracle
+    n0, n1 = wl.grid_n
+    rows = max(1, n1 // row_frac)
+    ns = max(1, len(seeds) // seed_frac)
+    t0 = time.perf_counter()
+    R = oracle.grid_response(ev.hits, wl.model, wl.grid_lo, wl.grid_step, (n0, rows), wl.sigma_grid)
+    idx = oracle.grid_maxima(R, wl.R0)
+    c0, c1 = oracle.cell_centres(wl.grid_lo, wl.grid_step, (n0, rows))
+    gth = np.stack([c0[idx % n0], c1[idx // n0]], 1)
+    oracle.extract_tracks(gth, R.reshape(-1)[idx], None, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0, wl.merge_cells)
+    t1 = time.perf_counter()
+    th, Rs, st, m = oracle.local_search(ev.hits, wl.model, seeds[:ns], wl.sigma_schedule, wl.grid_lo, wl.grid_step,
+                                        wl.grid_n)
+    oracle.extract_tracks(th, Rs, st, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0, wl.merge_cells)
+    t2 = time.perf_counter()
+    return (t1 - t0) * (n1 / rows) + (t2 - t1) * (len(seeds) / ns), (t2 - t0)
+
+
+def oracle_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = WORKLOADS[WORKLOAD]
+    ev = make_event(wl, RUN_SEED, 0)
+    seeds = uniform_seeds(wl, wl.n_seeds, RUN_SEED, 0)
+    row_frac, seed_frac = 64, 16
+    for _ in range(max(args.warmup, 0)):
+        oracle_step_sample(ev, wl, seeds, row_frac, seed_frac)
+    est = []
+    cpu_s = 0.0
+    for _ in range(args.steps):
+        e, c = oracle_step_sample(ev, wl, seeds, row_frac, seed_frac)
+        est.append(e)
+        cpu_s += c
+    sec_per_event = float(np.mean(est))
+    value = 1.0 / sec_per_event
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_event, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl, ev.n_hits),
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle_threads(), "kind": "oracle",
+                         "sample": "per step: 1/%d of the grid rows (%d x %d cells) and 1/%d of the seeds (%d), "
+                                   "extrapolated to the whole event" % (row_frac, wl.grid_n[0],
+                                                                        wl.grid_n[1] // row_frac, seed_frac,
+                                                                        wl.n_seeds // seed_frac)},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1709_08610_gb300 import build as rbuild
+    rbuild.build()
+    from paper_1709_08610_gb300 import retina as rt
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    wl = WORKLOADS[WORKLOAD]
+    ev = make_event(wl, RUN_SEED, rank)
+    seeds_np = uniform_seeds(wl, wl.n_seeds, RUN_SEED, rank)
+    H = ev.n_hits
+    grid = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    K_MAX = 8192
+    K_TR = 4096
+    R0 = wl.R0
+
+    # device-resident inputs, preallocated outputs and workspaces
+    hits = torch.from_numpy(ev.hits).to(dev)
+    offs = torch.tensor([0, H], dtype=torch.int64, device=dev)
+    seeds = torch.from_numpy(seeds_np).to(dev).view(1, -1, 2)
+    n0, n1 = wl.grid_n
+    Rg = torch.empty((1, n1, n0), dtype=torch.float32, device=dev)
+    ws_grid = torch.empty(max(rt.grid_response_workspace_size(1, wl.model, grid), 1), dtype=torch.uint8, device=dev)
+    mx = dict(max_idx=torch.empty((1, K_MAX), dtype=torch.int32, device=dev),
+              max_theta=torch.empty((1, K_MAX, 2), dtype=torch.float32, device=dev),
+              max_R=torch.empty((1, K_MAX), dtype=torch.float32, device=dev),
+              n_max=torch.empty((1,), dtype=torch.int32, device=dev))
+    ws_max = torch.empty(1 << 16, dtype=torch.uint8, device=dev)
+    ls_out = (torch.empty((1, wl.n_seeds, 2), dtype=torch.float32, device=dev),
+              torch.empty((1, wl.n_seeds), dtype=torch.float32, device=dev),
+              torch.empty((1, wl.n_seeds), dtype=torch.uint8, device=dev))
+    n_evals = torch.empty((1, wl.n_seeds), dtype=torch.uint8, device=dev)
+
+    def tr_out():
+        return dict(tracks=torch.empty((1, K_TR, 2), dtype=torch.float32, device=dev),
+                    track_R=torch.empty((1, K_TR), dtype=torch.float32, device=dev),
+                    track_src=torch.empty((1, K_TR), dtype=torch.int32, device=dev),
+                    n_tracks=torch.empty((1,), dtype=torch.int32, device=dev))
+
+    tr_grid, tr_search = tr_out(), tr_out()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        rt.grid_response(hits, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid)
+        if evs:
+            evs[1].record(stream)
+        rt.grid_maxima(Rg, grid, R0, K_MAX, out=mx, ws=ws_max)
+        rt.extract_tracks(mx["max_theta"], mx["max_R"], None, grid, R0, wl.merge_cells, K_TR,
+                          n_valid=mx["n_max"], out=tr_grid)
+        if evs:
+            evs[2].record(stream)
+        rt.local_search(hits, offs, wl.model, seeds, opts, grid, out=ls_out, n_evals=n_evals)
+        if evs:
+            evs[3].record(stream)
+        rt.extract_tracks(ls_out[0], ls_out[1], ls_out[2], grid, R0, wl.merge_cells, K_TR, out=tr_search)
+        if evs:
+            evs[4].record(stream)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # ---- peaks of the FP32 and MUFU pipes, measured live (burst)
+    peaks = {}
+    if not args.no_probe:
+        sink = torch.empty(rt.alu_probe_sink_floats(), dtype=torch.float32, device=dev)
+        for kind, name, iters in ((0, "ffma", 4096), (2, "ffma2", 4096), (1, "ex2", 1024)):
+            rt.alu_probe(kind, 64, sink)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best = None
+            for _ in range(3):
+                a.record(stream)
+                ops = rt.alu_probe(kind, iters, sink)
+                b.record(stream)
+                b.synchronize()
+                r = ops / (a.elapsed_time(b) * 1e-3)
+                best = r if best is None else max(best, r)
+            peaks[name] = best
+    fma_rate = max(peaks.get("ffma", 0.0), peaks.get("ffma2", 0.0))
+
+    # ---- warm-up
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank) if not args.no_clocks else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    launches0 = rt.launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    t_wall1 = time.perf_counter()
+    launches = rt.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+
+    stage = np.zeros((args.steps, 4))
+    for k in range(args.steps):
+        for j in range(4):
+            stage[k, j] = evs[k][j].elapsed_time(evs[k][j + 1])
+    step_ms = stage.sum(axis=1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # ---- algorithmic work of the two response kernels
+    n_ev = n_evals.to(torch.int64).sum().item()
+    cells = n0 * n1
+    grid_pairs = cells * H
+    rgh_pairs = wl.n_seeds * len(wl.sigma_schedule) * H
+    r_pairs = n_ev * H
+    grid_ms = float(np.mean(stage[:, 0]))
+    search_ms = float(np.mean(stage[:, 2]))
+    # grid contraction: one FP32 FMA (2 flops) per (cell, hit) pair
+    grid_tflops = 2.0 * grid_pairs / (grid_ms * 1e-3) / 1e12
+    # local search: 16 FP32 ops + 1 ex2 per (seed, hit) in a gradient/Hessian
+    # pass, 6 FP32 ops + 1 ex2 in an R-only pass (counts from the kernel source)
+    search_fp32_ops = 16.0 * rgh_pairs + 6.0 * r_pairs
+    search_ex2 = rgh_pairs + r_pairs
+    search_fp32_rate = search_fp32_ops / (search_ms * 1e-3)
+    search_ex2_rate = search_ex2 / (search_ms * 1e-3)
+    fma_peak_tflops = 2.0 * fma_rate / 1e12 if fma_rate else None
+    ex2_peak = peaks.get("ex2")
+    roof_grid = {"kernel": "grid_sep_kernel (+ slice reduction)", "bound": "alu", "unit": "TFLOP/s",
+                 "achieved": grid_tflops, "peak": fma_peak_tflops,
+                 "frac": (grid_tflops / fma_peak_tflops) if fma_peak_tflops else None,
+                 "traffic": None, "pairs_per_s": grid_pairs / (grid_ms * 1e-3),
+                 "peak_source": "FP32 FMA rate measured live by retina_alu_probe (burst; the faster of FFMA and "
+                                "packed FFMA2)"}
+    # the search's bound: FP32 issue vs ex2 pipe, whichever is closer to its peak
+    fr_fp32 = (search_fp32_rate / (2 * fma_rate) if fma_rate else None)  # ops vs FMA-pipe ops (1 op per lane slot)
+    fr_ex2 = (search_ex2_rate / ex2_peak) if ex2_peak else None
+    roof_search = {"kernel": "local_search_kernel", "bound": "alu", "unit": "Gpair/s",
+                   "achieved": (rgh_pairs + r_pairs) / (search_ms * 1e-3) / 1e9,
+                   "fp32_ops_per_s": search_fp32_rate, "ex2_per_s": search_ex2_rate,
+                   "frac_fp32": fr_fp32, "frac_ex2": fr_ex2, "rgh_pairs": rgh_pairs, "r_pairs": r_pairs,
+                   "traffic": None}
+    dominant = "grid" if grid_ms >= search_ms else "search"
+    roofline = roof_grid if dominant == "grid" else dict(roof_search, frac=max(x for x in (fr_fp32, fr_ex2) if x),
+                                                          peak=None, unit="Gpair/s")
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or True:
+        hits_h = torch.from_numpy(ev.hits).pin_memory()
+        seeds_h = torch.from_numpy(seeds_np).view(1, -1, 2).pin_memory()
+        out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in tr_search.items()}
+        outg_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in tr_grid.items()}
+        n_e2e = max(10, min(args.steps, 200))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(n_e2e):
+            hits.copy_(hits_h, non_blocking=True)
+            seeds.copy_(seeds_h, non_blocking=True)
+            step()
+            for k2 in out_h:
+                out_h[k2].copy_(tr_search[k2], non_blocking=True)
+                outg_h[k2].copy_(tr_grid[k2], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms = a.elapsed_time(b) / n_e2e
+        d2h = sum(v.numel() * v.element_size() for v in out_h.values()) * 2
+        h2d = hits_h.numel() * 4 + seeds_h.numel() * 4
+        e2e = {"value": world * 1e3 / e2e_ms, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+               "note": "includes the flush-free step plus pinned host<->device copies, timed with CUDA events"}
+
+    # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        row_frac, seed_frac = 8, 2
+        est, wall = oracle_step_sample(ev, wl, seeds_np, row_frac, seed_frac)
+        cpu = {"value": 1.0 / est, "unit": "events/s", "cores": oracle_threads(), "kind": "oracle",
+               "sample": "1/%d of the grid rows (%d x %d cells) and 1/%d of the seeds (%d); %.1f s of CPU work "
+                         "extrapolated to the whole event" % (row_frac, n0, n1 // row_frac, seed_frac,
+                                                             wl.n_seeds // seed_frac, wall)}
+
+    if rank == 0:
+        tr_n = (int(tr_grid["n_tracks"].item()), int(tr_search["n_tracks"].item()))
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(wl, H),
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "roofline_other": roof_search if dominant == "grid" else roof_grid,
+            "stages_ms": {"grid_response": grid_ms, "grid_maxima_extract": float(np.mean(stage[:, 1])),
+                          "local_search": search_ms, "search_extract": float(np.mean(stage[:, 3]))},
+            "methods_events_per_s": {"grid_scan": 1e3 / (grid_ms + float(np.mean(stage[:, 1]))),
+                                     "local_search": 1e3 / (search_ms + float(np.mean(stage[:, 3])))},
+            "tracks_found": {"grid": tr_n[0], "search": tr_n[1]},
+            "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
+                               "ex2_per_s": peaks.get("ex2")},
+            "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * retina.h - C ABI of the GB300 (sm_103a) Artificial Retina library.
+ *
+ * The library evaluates the retina response of arXiv:1709.08610 (Borisyak,
+ * Ustyuzhanin, Derkach, Belous, "Numerical optimization for Artificial
+ * Retina Algorithm"), Section 2, Eq. 1:
+ *
+ *     R(theta) = sum_k exp(-s(x_k, theta)^2 / sigma^2)
+ *
+ * over all hits x_k of an event, on a grid of units (Eq. 2, the brute-force
+ * grid algorithm of Section 2) or along a multistart truncated-Newton local
+ * search (Algorithm 1 with the update and sigma schedule of Section 3), and
+ * turns grid maxima or converged points into tracks (the cluster / select
+ * lines of Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller (allocated
+ *   with cudaMalloc or any allocator of device memory); the library never
+ *   frees them, never retains them after the call returns, and allocates no
+ *   device memory itself.  Scratch memory comes from a caller-provided
+ *   workspace whose size the matching *_workspace_size function reports.
+ *   Struct arguments (retina_grid, retina_ls_opts) are HOST pointers, read
+ *   during the call only.
+ * - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *   NULL means the legacy default stream).  Outputs are valid once the
+ *   stream reaches the call.
+ * - Return value: RETINA_OK or an error code.  Arguments are validated on
+ *   the host before any launch; on RETINA_EINVAL nothing was launched.
+ *   RETINA_ECUDA reports a failed launch (cudaGetLastError).  Conditions
+ *   found on the device (a non-finite point, an output list that overflowed)
+ *   are written to status arrays and counts; kernels never trap.
+ * - hits: float32 [n_hits][4], 16-byte aligned, events concatenated:
+ *   event e owns rows event_offsets[e] .. event_offsets[e+1]-1
+ *   (event_offsets: int64 [n_events + 1], non-decreasing, device memory).
+ *   Kernels clamp every offset to [0, n_hits] and treat a decreasing pair as
+ *   an empty event, so malformed offsets cannot make them read outside hits.
+ *   Row layout per model:
+ *     RETINA_TOY2D       (x, y, -, -): 2D line y = theta0 * x + theta1 seen by
+ *                        detector planes x = const; s = y - theta0 x - theta1
+ *                        (Section 2, Figure 1 caption).
+ *     RETINA_VELO_SLOPES (x, y, z, -): straight 3D track through the origin
+ *                        with slopes theta = (t_x, t_y); s is the distance in
+ *                        the layer z = const between the hit and the track's
+ *                        crossing (t_x z, t_y z) (Section 3).
+ * - A grid / box: cell centres theta_a = lo[a] + (i_a + 1/2) step[a],
+ *   i_a = 0 .. n[a]-1; the box is [lo, lo + n * step).  Response grids are
+ *   float32 [n_events][n[1]][n[0]] (theta1 slow, theta0 fast), and a cell's
+ *   linear index is i1 * n[0] + i0.
+ */
+#ifndef RETINA_H
+#define RETINA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RETINA_OK 0
+#define RETINA_EINVAL 1   /* invalid argument; nothing launched               */
+#define RETINA_ECUDA 2    /* a CUDA launch or runtime call failed             */
+#define RETINA_ENOSPACE 3 /* workspace too small, or a size limit exceeded    */
+
+#define RETINA_TOY2D 0
+#define RETINA_VELO_SLOPES 1
+
+/* grid-scan method flags (retina_grid_scan `flags`) */
+#define RETINA_GRID_AUTO 0
+#define RETINA_GRID_DIRECT 1    /* force the per-pair exp kernel           */
+#define RETINA_GRID_SEPARABLE 2 /* force exp(-u^2-v^2)=exp(-u^2)exp(-v^2)   */
+                                /* contraction (RETINA_VELO_SLOPES only)     */
+
+/* maximum number of local-search updates q */
+#define RETINA_MAX_Q 8
+/* maximum number of candidate points per event in retina_extract_tracks */
+#define RETINA_MAX_EXTRACT_POINTS 8192
+
+/* tuning options (retina_set_option); values are validated, defaults in () */
+#define RETINA_OPT_LS_SEEDS_PER_WARP 1 /* 1, 2 or 4 seeds per warp (1)          */
+#define RETINA_OPT_LS_SMEM_HITS 2      /* hits staged in shared memory (4096)   */
+#define RETINA_OPT_GRID_SPLITS 3       /* hit slices per grid tile, 0=auto (0)  */
+
+typedef struct {
+    float lo[2];   /* lower edge of the box per axis                      */
+    float step[2]; /* cell size per axis (> 0)                            */
+    int32_t n[2];  /* cells per axis (> 0)                                */
+} retina_grid;
+
+/* Options of the local search (Algorithm 1; Section 3). */
+typedef struct {
+    int32_t q;            /* updates per seed, 1 .. RETINA_MAX_Q (paper: 3)     */
+    float sigma[8];       /* bandwidth at update j (paper: 0.3, 0.175, 0.05)    */
+    float c1;             /* Armijo sufficient-increase constant, in [0, 1)    */
+    int32_t max_halvings; /* backtracking halvings after t = 1, 0 .. 30        */
+    float step_cap_cells; /* cap on max_a |p_a| / step_a, > 0                  */
+} retina_ls_opts;
+
+/* Human-readable text for a status code (static storage). */
+const char *retina_strerror(int code);
+
+/* ABI version of this header (incremented on incompatible change). */
+int retina_abi_version(void);
+
+/* Set a process-wide tuning option (RETINA_OPT_*).  Affects launches made
+ * after the call; results do not depend on it beyond FP32 summation order.
+ * Returns RETINA_EINVAL for an unknown option or an out-of-range value. */
+int retina_set_option(int32_t option, int32_t value);
+int retina_get_option(int32_t option, int32_t *value);
+
+/* Number of kernels this library has launched in this process (all entry
+ * points, all threads); callers difference it around a region to count the
+ * library's launches in it.  Not part of the paper: instrumentation. */
+uint64_t retina_launch_count(void);
+
+/*
+ * retina_alu_probe - throughput probe of the arithmetic pipes the retina
+ * kernels use (not part of the paper; it supplies the FP32 / SFU peaks of
+ * the roofline, which no vendor table gives for this part).  Launches one
+ * saturating kernel on `stream`: every thread runs `iters` iterations of
+ * eight independent dependency chains of
+ *   kind 0: FP32 fused multiply-add (FFMA pipe),
+ *   kind 1: ex2.approx (MUFU / SFU pipe),
+ *   kind 2: packed FP32x2 fused multiply-add (two FMAs per instruction).
+ * *ops receives the number of FP32 operations (kind 0, 2: FMAs; kind 1:
+ * ex2) the launch performs; time the launch with events on `stream`.
+ * sink: float32 device buffer of retina_alu_probe_sink_floats() elements
+ * (keeps the chains live).  iters in [1, 1<<20].
+ */
+int64_t retina_alu_probe_sink_floats(void);
+int retina_alu_probe(int32_t kind, int32_t iters, float *sink, double *ops, void *stream);
+
+/*
+ * retina_grid_scan - response on a grid of units and its local maxima.
+ *
+ * Paper: Section 2, Eq. 2 (R_ij = R(theta_ij) for every unit) and steps 2-4
+ * of the grid algorithm (compute the grid response, select activated units,
+ * estimate parameters).  A unit is selected when R_ij >= R0 and it beats
+ * every existing neighbour of its 3 x 3 neighbourhood in the order
+ * (R, -linear index): a strict local maximum, ties going to the lower
+ * linear index.  Its estimate is the cell centre.
+ *
+ *   hits, event_offsets, n_events, model : see the conventions above.
+ *   g        : host pointer; the grid of units.
+ *   sigma    : bandwidth (> 0, finite).
+ *   R0       : selection threshold.
+ *   flags    : RETINA_GRID_AUTO / _DIRECT / _SEPARABLE.
+ *   R_out    : nullable; float32 [n_events][n1][n0] response grid.  When
+ *              NULL the grid lives in the workspace.
+ *   max_idx  : int32 [n_events][K]; linear cell index of each selected unit,
+ *              increasing, per event.
+ *   max_theta: float32 [n_events][K][2]; cell centre of each selected unit.
+ *   max_R    : float32 [n_events][K]; its response.
+ *   n_max    : int32 [n_events]; number of selected units (may exceed K:
+ *              only the first K, in index order, are written).
+ *   K        : capacity per event (>= 1).
+ *   ws, ws_bytes : workspace of at least retina_grid_scan_workspace_size().
+ * Returns RETINA_ENOSPACE (nothing launched) when ws_bytes is too small.
+ */
+int retina_grid_scan_workspace_size(int32_t n_events, int32_t model, const retina_grid *g, int32_t flags,
+                                    int32_t store_R, size_t *bytes);
+int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
+                     const retina_grid *g, float sigma, float R0, int32_t flags, float *R_out, int32_t *max_idx,
+                     float *max_theta, float *max_R, int32_t *n_max, int32_t K, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/*
+ * retina_grid_response - the grid response alone (Section 2, Eq. 2): writes
+ * R_out float32 [n_events][n1][n0] (required), no selection.  Same arguments
+ * as retina_grid_scan; workspace from retina_grid_response_workspace_size.
+ */
+int retina_grid_response_workspace_size(int32_t n_events, int32_t model, const retina_grid *g, int32_t flags,
+                                        size_t *bytes);
+int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                         int32_t model, const retina_grid *g, float sigma, int32_t flags, float *R_out, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/*
+ * retina_grid_maxima - the selection step alone, on a caller-supplied grid.
+ *
+ * Paper: Section 2, steps 3-4 of the grid algorithm.  Same rule and outputs
+ * as retina_grid_scan, reading R float32 [n_events][n1][n0].
+ */
+int retina_grid_maxima_workspace_size(int32_t n_events, const retina_grid *g, size_t *bytes);
+int retina_grid_maxima(const float *R, int32_t n_events, const retina_grid *g, float R0, int32_t *max_idx,
+                       float *max_theta, float *max_R, int32_t *n_max, int32_t K, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/*
+ * retina_response - R, grad R and Hess R at arbitrary points.
+ *
+ * Paper: Section 2, Eq. 1, and the remark that the gradient and the Hessian
+ * cost little more than R itself:
+ *     grad R = (2/sigma^2) sum_k e_k J_k^T r_k
+ *     Hess R = sum_k e_k [(4/sigma^4)(J_k^T r_k)(J_k^T r_k)^T - (2/sigma^2) J_k^T J_k]
+ * with r_k the residual of hit k and J_k its Jacobian in theta.
+ *
+ *   theta : float32 [n_events][n_points][2].
+ *   out   : float32 [n_events][n_points][6] = (R, g0, g1, H00, H01, H11);
+ *           when want_derivs == 0 only R (column 0) is written.
+ */
+int retina_response(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
+                    const float *theta, int32_t n_points, float sigma, int32_t want_derivs, float *out,
+                    void *stream);
+
+/*
+ * retina_local_search - Algorithm 1's q updates for every seed.
+ *
+ * Paper: Algorithm 1 (seeds drawn from a prior, q updates each using R,
+ * grad R and Hess R) with the truncated Newton update and the annealed
+ * bandwidths of Section 3.  Update j (j = 1..q) at bandwidth sigma_j:
+ *   1. (R, g, H) at theta.
+ *   2. Direction p: conjugate gradients on -H p = g from p = 0 (Newton-CG,
+ *      Nocedal & Wright, Algorithm 7.1), forcing tolerance
+ *      min(1/2, sqrt|g|) |g|, at most 2 iterations; on non-positive
+ *      curvature of -R along the CG direction: p = g at the first
+ *      iteration, else the current iterate.
+ *   3. If max_a |p_a| / step_a > step_cap_cells, p is scaled down to it.
+ *   4. Backtracking: the first t in 1, 1/2, ..., 2^-max_halvings with
+ *      R(theta + t p) >= R(theta) + c1 t g.p is taken; if none, theta
+ *      stays and the seed's status becomes 1.
+ * Then R_out = R(theta_q; sigma_q).
+ *
+ *   seeds     : float32 [n_events][n_seeds][2] starting points.
+ *   opts      : host pointer.
+ *   box       : host pointer; its step sizes set the step cap, and the box
+ *               decides status 2.
+ *   theta_out : float32 [n_events][n_seeds][2] final points.
+ *   R_out     : float32 [n_events][n_seeds] response at sigma_q.
+ *   status    : uint8 [n_events][n_seeds]: 0 ok, 1 some line search took no
+ *               step, 2 final point outside the box, 3 non-finite.
+ *   n_evals   : nullable uint8 [n_events][n_seeds]: number of R-only passes
+ *               over the hits the seed used (line-search trials plus the
+ *               final response); with the q passes of R, grad R and Hess R
+ *               this is the seed's exact work, in units of the paper's T0.
+ */
+int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
+                        const float *seeds, int32_t n_seeds, const retina_ls_opts *opts, const retina_grid *box,
+                        float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, void *stream);
+
+/*
+ * retina_extract_tracks - cluster the points and keep the best of each.
+ *
+ * Paper: Algorithm 1, "cluster solutions" and "for each cluster select the
+ * solution with the highest response above R0".  Candidates are points with
+ * status 0 or 1 (status may be NULL), finite, inside the box and with
+ * R >= R0; they are visited by decreasing R (equal R: lower point index
+ * first) and a candidate is kept when, for every point kept before it,
+ * max_a |theta_a - theta_kept_a| / step_a >= merge_cells.  The comparison is
+ * exact (no rounding decides it) when the steps are powers of two.
+ *
+ *   theta   : float32 [n_events][n_points][2];  R: float32 [n_events][n_points].
+ *   status  : nullable uint8 [n_events][n_points].
+ *   n_valid : nullable int32 [n_events]; only the first
+ *             min(n_valid[e], n_points) points of event e are considered.
+ *   tracks  : float32 [n_events][K][2];  track_R: float32 [n_events][K];
+ *   track_src: nullable int32 [n_events][K], index of the kept point.
+ *   n_tracks: int32 [n_events]; number kept (may exceed K; the first K in
+ *             visiting order are written).
+ *   n_points must be <= RETINA_MAX_EXTRACT_POINTS (else RETINA_ENOSPACE).
+ */
+int retina_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                          int32_t n_events, int32_t n_points, const retina_grid *box, float R0,
+                          float merge_cells, float *tracks, float *track_R, int32_t *track_src,
+                          int32_t *n_tracks, int32_t K, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RETINA_H */

@@ -1,0 +1,261 @@
+// Cluster the converged points and keep the best of each cluster above R0
+// (Algorithm 1, its last two lines), on the GPU, one CTA per event.
+//
+// Sequential definition: visit the candidates by decreasing R (equal R:
+// lower point index first) and keep one when every point kept before it is at
+// least merge_cells away in max_a |dtheta_a| / step_a.
+//
+// Parallel evaluation of exactly that definition:
+//   1. filter candidates into shared memory (status <= 1, finite, inside the
+//      box, R >= R0) with 64-bit keys (~order(R), index);
+//   2. bitonic sort -> rank order;
+//   3. bucket the candidates on a grid of cells slightly wider than the merge
+//      distance (so any two conflicting candidates lie in adjacent buckets)
+//      and sort (bucket row, bucket column, rank);
+//   4. resolve in rounds: an undecided candidate is rejected as soon as a
+//      lower-ranked conflicting candidate is kept, kept once every
+//      lower-ranked conflicting candidate is rejected; the lowest undecided
+//      rank always resolves, so rounds end;
+//   5. write the kept ones in rank order.
+// Conflict tests are exact: |a - b| < c is decided without rounding (c =
+// merge_cells * step is exact for power-of-two steps), see abs_diff_lt.
+#include "internal.cuh"
+
+namespace retina {
+
+constexpr int EX_THREADS = 1024;
+constexpr int BUCKET_BITS = 21;
+constexpr int RANK_BITS = 22;
+
+// Exact test |a - b| < c for finite floats and c > 0 representable.
+// fl() is monotone and c is representable, so |fl(a-b)| < c or > c decides
+// it; on |fl(a-b)| == c the TwoSum error term says on which side a-b lies.
+__device__ __forceinline__ bool abs_diff_lt(float a, float b, float c) {
+    const float s = __fsub_rn(a, b);
+    const float as = fabsf(s);
+    if (as < c) return true;
+    if (as > c) return false;
+    const float nb = -b;
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(nb, bb));
+    return s > 0.f ? (err < 0.f) : (err > 0.f);
+}
+
+__device__ void bitonic_sort(uint64_t *keys, int C) {
+    for (int k = 2; k <= C; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < C; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = keys[i], b = keys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int lower_bound_u64(const uint64_t *keys, int n, uint64_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+struct ExtractParams {
+    float lo0, lo1, hi0, hi1;
+    float c0, c1;    // merge distance per axis: merge_cells * step
+    float w0, w1;    // bucket width per axis (slightly above c)
+    float R0;
+    int n_points, K, cap;
+};
+
+__global__ void __launch_bounds__(EX_THREADS)
+extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__ R, const uint8_t *__restrict__ status,
+                      const int32_t *__restrict__ n_valid, ExtractParams prm, float *__restrict__ tracks,
+                      float *__restrict__ track_R, int32_t *__restrict__ track_src, int32_t *__restrict__ n_tracks) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cap = prm.cap;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(smem);
+    float *th0 = reinterpret_cast<float *>(keys + cap);
+    float *th1 = th0 + cap;
+    int32_t *src = reinterpret_cast<int32_t *>(th1 + cap);
+    volatile uint8_t *state = reinterpret_cast<uint8_t *>(src + cap);
+    __shared__ int nc_s;
+    __shared__ int warp_tot[EX_THREADS / 32];
+    __shared__ int run;
+
+    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int n = prm.n_points;
+    if (n_valid) {
+        const int v = n_valid[e];
+        n = v < n ? (v > 0 ? v : 0) : n;
+    }
+    const int64_t base = (int64_t)e * prm.n_points;
+    if (tid == 0) nc_s = 0;
+    __syncthreads();
+    // 1. filter
+    for (int i = tid; i < n; i += EX_THREADS) {
+        const int64_t o = base + i;
+        const float r = R[o], a0 = theta[2 * o], a1 = theta[2 * o + 1];
+        bool ok = isfinite(r) && isfinite(a0) && isfinite(a1) && (r >= prm.R0);
+        if (status) ok = ok && status[o] <= 1;
+        ok = ok && a0 >= prm.lo0 && a0 < prm.hi0 && a1 >= prm.lo1 && a1 < prm.hi1;
+        if (ok) {
+            const int pos = atomicAdd(&nc_s, 1);
+            keys[pos] = ((uint64_t)(~float_order_key(r)) << 32) | (uint32_t)i;
+        }
+    }
+    __syncthreads();
+    const int nc = nc_s;
+    int C = 1;
+    while (C < nc) C <<= 1;
+    for (int i = nc + tid; i < C; i += EX_THREADS) keys[i] = ~0ull;
+    __syncthreads();
+    // 2. rank order
+    bitonic_sort(keys, C);
+    for (int r = tid; r < nc; r += EX_THREADS) {
+        const int i = (int)(uint32_t)keys[r];
+        const int64_t o = base + i;
+        th0[r] = theta[2 * o];
+        th1[r] = theta[2 * o + 1];
+        src[r] = i;
+        state[r] = 0;
+    }
+    __syncthreads();
+    // 3. buckets
+    const uint64_t bmax = (1ull << BUCKET_BITS) - 1;
+    for (int r = tid; r < C; r += EX_THREADS) {
+        if (r < nc) {
+            uint64_t b0 = (uint64_t)fminf(fmaxf(floorf((th0[r] - prm.lo0) / prm.w0), 0.f), (float)bmax);
+            uint64_t b1 = (uint64_t)fminf(fmaxf(floorf((th1[r] - prm.lo1) / prm.w1), 0.f), (float)bmax);
+            keys[r] = (b1 << (BUCKET_BITS + RANK_BITS)) | (b0 << RANK_BITS) | (uint64_t)r;
+        } else {
+            keys[r] = ~0ull;
+        }
+    }
+    __syncthreads();
+    bitonic_sort(keys, C);
+    // 4. rounds
+    for (int round = 0; round <= nc + 1; ++round) {
+        bool undecided = false;
+        for (int r = tid; r < nc; r += EX_THREADS) {
+            if (state[r] != 0) continue;
+            const float a0 = th0[r], a1 = th1[r];
+            const int64_t b0 = (int64_t)fminf(fmaxf(floorf((a0 - prm.lo0) / prm.w0), 0.f), (float)bmax);
+            const int64_t b1 = (int64_t)fminf(fmaxf(floorf((a1 - prm.lo1) / prm.w1), 0.f), (float)bmax);
+            bool rejected = false, blocked = false;
+            for (int dy = -1; dy <= 1 && !rejected; ++dy) {
+                const int64_t row = b1 + dy;
+                if (row < 0 || row > (int64_t)bmax) continue;
+                const int64_t c_lo = b0 > 0 ? b0 - 1 : 0;
+                const int64_t c_hi = b0 + 2;  // exclusive
+                // keys of columns [c_lo, c_hi) in this row; a column past the last
+                // one carries into the next row, which is the end of this row
+                const uint64_t k_lo = ((uint64_t)row << (BUCKET_BITS + RANK_BITS)) + ((uint64_t)c_lo << RANK_BITS);
+                const uint64_t k_hi = ((uint64_t)row << (BUCKET_BITS + RANK_BITS)) +
+                                      ((uint64_t)(c_hi <= (int64_t)bmax ? c_hi : bmax + 1) << RANK_BITS);
+                const int q0 = lower_bound_u64(keys, nc, k_lo);
+                const int q1 = lower_bound_u64(keys, nc, k_hi);
+                for (int q = q0; q < q1; ++q) {
+                    const int rj = (int)(keys[q] & ((1ull << RANK_BITS) - 1));
+                    if (rj >= r) continue;
+                    if (!(abs_diff_lt(a0, th0[rj], prm.c0) && abs_diff_lt(a1, th1[rj], prm.c1))) continue;
+                    const uint8_t sj = state[rj];
+                    if (sj == 1) {
+                        rejected = true;
+                        break;
+                    }
+                    if (sj == 0) blocked = true;
+                }
+            }
+            if (rejected)
+                state[r] = 2;
+            else if (!blocked)
+                state[r] = 1;
+            else
+                undecided = true;
+        }
+        if (!__syncthreads_or(undecided)) break;
+    }
+    // 5. output in rank order
+    if (tid == 0) run = 0;
+    __syncthreads();
+    for (int r0 = 0; r0 < nc; r0 += EX_THREADS) {
+        const int r = r0 + tid;
+        const bool kept = r < nc && state[r] == 1;
+        const unsigned bal = __ballot_sync(0xffffffffu, kept);
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int w = 0; w < EX_THREADS / 32; ++w) {
+            const int v = warp_tot[w];
+            before += (w < warp) ? v : 0;
+            tot += v;
+        }
+        if (kept) {
+            const int pos = run + before + __popc(bal & ((1u << lane) - 1u));
+            if (pos < prm.K) {
+                const int64_t o = (int64_t)e * prm.K + pos;
+                tracks[2 * o] = th0[r];
+                tracks[2 * o + 1] = th1[r];
+                track_R[o] = R[base + src[r]];
+                if (track_src) track_src[o] = src[r];
+            }
+        }
+        __syncthreads();
+        if (tid == 0) run += tot;
+        __syncthreads();
+    }
+    if (tid == 0) n_tracks[e] = run;
+}
+
+size_t extract_smem_bytes(int n_points) {
+    int C = 1;
+    while (C < n_points) C <<= 1;
+    return (size_t)C * (sizeof(uint64_t) + 2 * sizeof(float) + sizeof(int32_t) + 1) + 16;
+}
+
+cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                                  int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
+                                  float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
+                                  cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(extract_tracks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)extract_smem_bytes(RETINA_MAX_EXTRACT_POINTS));
+        if (err != cudaSuccess) return err;
+        configured = true;
+    }
+    ExtractParams prm;
+    prm.lo0 = box->lo[0];
+    prm.lo1 = box->lo[1];
+    prm.hi0 = box->lo[0] + (float)box->n[0] * box->step[0];
+    prm.hi1 = box->lo[1] + (float)box->n[1] * box->step[1];
+    prm.c0 = merge_cells * box->step[0];
+    prm.c1 = merge_cells * box->step[1];
+    prm.w0 = prm.c0 * 1.015625f;
+    prm.w1 = prm.c1 * 1.015625f;
+    prm.R0 = R0;
+    prm.n_points = n_points;
+    prm.K = K;
+    int C = 1;
+    while (C < n_points) C <<= 1;
+    prm.cap = C;
+    extract_tracks_kernel<<<n_events, EX_THREADS, extract_smem_bytes(n_points), st>>>(
+        theta, R, status, n_valid, prm, tracks, track_R, track_src, n_tracks);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace retina

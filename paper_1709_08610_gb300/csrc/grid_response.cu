@@ -1,0 +1,279 @@
+// Grid of units: R_ij = R(theta_ij) for every cell (Section 2, Eq. 2).
+//
+// Two kernels compute the same sum over hits:
+//
+// * grid_sep_kernel (slope model only).  For theta = (t_x, t_y) and a hit
+//   (x, y, z) the squared distance splits into per-axis parts,
+//   s^2 = (x - t_x z)^2 + (y - t_y z)^2, so each term of Eq. 1 factorises:
+//   exp(-s^2/sigma^2) = exp(-(x - t_x z)^2/sigma^2) * exp(-(y - t_y z)^2/sigma^2).
+//   Over an axis-aligned grid, R_ij = sum_k A_ik B_jk with
+//   A_ik = exp(-(x_k - t_x,i z_k)^2/sigma^2), B_jk = exp(-(y_k - t_y,j z_k)^2/sigma^2):
+//   a dense contraction over hits.  A CTA owns a 128 x 128 block of cells,
+//   builds the A and B panels of a 32-hit chunk in shared memory (MUFU ex2,
+//   (n0 + n1) exps per hit instead of n0 * n1), then each thread accumulates
+//   an 8 x 8 outer product with FP32 FMAs (one FMA per pair).
+//
+// * grid_direct_kernel (both models).  Each pair (cell, hit) evaluates its
+//   own exp on the MUFU pipe; per-axis parts of the distance are shared by a
+//   thread's 4 x 4 cells so a pair costs one FMA, one ex2 and one add
+//   (slope model) or sub, mul, mul, ex2, add (2D toy).
+//
+// Both kernels split an event's hits into `splits` slices (one CTA per
+// (tile, slice, event)) so that a single event fills the GPU; slice partial
+// grids are then summed in fixed slice order by reduce_partials_kernel, so
+// results are deterministic.
+#include "internal.cuh"
+
+namespace retina {
+
+constexpr int SEP_BM = 128, SEP_BN = 128, SEP_BK = 32, SEP_THREADS = 256;
+constexpr int DIR_TILE = 64, DIR_THREADS = 256, DIR_CHUNK = 512;
+
+__device__ __forceinline__ void slice_range(const int64_t *off, int64_t n_hits, int e, int s, int splits, int align,
+                                            int64_t &k0, int64_t &k1) {
+    int64_t hb, he;
+    event_range(off, n_hits, e, hb, he);
+    const int64_t H = he - hb;
+    int64_t per = (H + splits - 1) / splits;
+    per = (per + align - 1) / align * align;
+    k0 = hb + (int64_t)s * per;
+    k1 = k0 + per < he ? k0 + per : he;
+}
+
+__global__ void __launch_bounds__(SEP_THREADS, 2)
+grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, GridDev g, float kk,
+                int splits,
+                int tiles0, float *__restrict__ out, int64_t split_stride, int64_t event_stride) {
+    __shared__ __align__(16) float sA[SEP_BK][SEP_BM];
+    __shared__ __align__(16) float sB[SEP_BK][SEP_BN];
+    const int e = blockIdx.z, s = blockIdx.y;
+    const int ti0 = (blockIdx.x % tiles0) * SEP_BM;
+    const int tj0 = (blockIdx.x / tiles0) * SEP_BN;
+    int64_t k0, k1;
+    slice_range(off, n_hits, e, s, splits, SEP_BK, k0, k1);
+
+    const int t = threadIdx.x;
+    // panel-building role: one cell per axis, every other hit of the chunk
+    const int ci = t & (SEP_BM - 1), hpar = t >> 7;
+    const float t0 = cell_centre(g.lo0, g.step0, ti0 + ci);
+    const float t1 = cell_centre(g.lo1, g.step1, tj0 + ci);
+    // contraction role: 8 x 8 cells per thread (two 4-wide groups per axis)
+    const int tm = t & 15, tn = t >> 4;
+
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+    for (int64_t kb = k0; kb < k1; kb += SEP_BK) {
+        __syncthreads();
+#pragma unroll 4
+        for (int m = 0; m < SEP_BK / 2; ++m) {
+            const int kc = hpar + 2 * m;
+            const int64_t k = kb + kc;
+            float va = 0.f, vb = 0.f;
+            if (k < k1) {
+                const float4 h = __ldg(hits + k);
+                const float u = __fmaf_rn(-t0, h.z, h.x);  // x - t_x z, one rounding
+                const float v = __fmaf_rn(-t1, h.z, h.y);  // y - t_y z
+                va = ex2_mufu(-(u * u) * kk);
+                vb = ex2_mufu(-(v * v) * kk);
+            }
+            sA[kc][ci] = va;
+            sB[kc][ci] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kc = 0; kc < SEP_BK; ++kc) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&sA[kc][tm * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&sA[kc][64 + tm * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&sB[kc][tn * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&sB[kc][64 + tn * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+        }
+    }
+
+    float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
+    const bool vec = (g.n0 % 4) == 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int row = tj0 + (b < 4 ? tn * 4 + b : 64 + tn * 4 + (b - 4));
+        if (row >= g.n1) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int col = ti0 + half * 64 + tm * 4;
+            float *p = dst + (int64_t)row * g.n0 + col;
+            const float v0 = acc[half * 4 + 0][b], v1 = acc[half * 4 + 1][b];
+            const float v2 = acc[half * 4 + 2][b], v3 = acc[half * 4 + 3][b];
+            if (vec && col + 3 < g.n0) {
+                *reinterpret_cast<float4 *>(p) = make_float4(v0, v1, v2, v3);
+            } else {
+                if (col + 0 < g.n0) p[0] = v0;
+                if (col + 1 < g.n0) p[1] = v1;
+                if (col + 2 < g.n0) p[2] = v2;
+                if (col + 3 < g.n0) p[3] = v3;
+            }
+        }
+    }
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(DIR_THREADS)
+grid_direct_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, GridDev g,
+                   float kk, float sk,
+                   int splits, int tiles0, float *__restrict__ out, int64_t split_stride, int64_t event_stride) {
+    __shared__ float4 sh[DIR_CHUNK];
+    const int e = blockIdx.z, s = blockIdx.y;
+    const int ti0 = (blockIdx.x % tiles0) * DIR_TILE;
+    const int tj0 = (blockIdx.x / tiles0) * DIR_TILE;
+    int64_t k0, k1;
+    slice_range(off, n_hits, e, s, splits, 1, k0, k1);
+    const int t = threadIdx.x;
+    const int tx = t & 15, ty = t >> 4;
+    float c0[4], c1[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        c0[a] = cell_centre(g.lo0, g.step0, ti0 + tx + 16 * a);
+        c1[a] = cell_centre(g.lo1, g.step1, tj0 + ty + 16 * a);
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+
+    for (int64_t kb = k0; kb < k1; kb += DIR_CHUNK) {
+        const int n = (int)((k1 - kb) < DIR_CHUNK ? (k1 - kb) : DIR_CHUNK);
+        __syncthreads();
+        for (int i = t; i < n; i += DIR_THREADS) sh[i] = __ldg(hits + kb + i);
+        __syncthreads();
+        for (int i = 0; i < n; ++i) {
+            const float4 h = sh[i];
+            if (MODEL == RETINA_VELO_SLOPES) {
+                float u[4], vv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) u[a] = __fmaf_rn(-c0[a], h.z, h.x) * sk;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float v = __fmaf_rn(-c1[b], h.z, h.y) * sk;
+                    vv[b] = v * v;
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += ex2_mufu(-__fmaf_rn(u[a], u[a], vv[b]));
+            } else {
+                float w[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) w[a] = __fmaf_rn(-c0[a], h.x, h.y);  // y - alpha x
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const float r = w[a] - c1[b];                          // minus beta
+                        acc[a][b] += ex2_mufu(-(r * r) * kk);
+                    }
+            }
+        }
+    }
+    float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int row = tj0 + ty + 16 * b;
+        if (row >= g.n1) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int col = ti0 + tx + 16 * a;
+            if (col < g.n0) dst[(int64_t)row * g.n0 + col] = acc[a][b];
+        }
+    }
+}
+
+__global__ void reduce_partials_kernel(const float *__restrict__ part, int splits, int64_t split_stride, int64_t n,
+                                       float *__restrict__ R) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int s = 0; s < splits; ++s) v += part[(int64_t)s * split_stride + i];
+        R[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int forced_splits) {
+    GridPlan p;
+    p.separable = (model == RETINA_VELO_SLOPES) && (flags != RETINA_GRID_DIRECT);
+    const int tile = p.separable ? SEP_BM : DIR_TILE;
+    p.tiles0 = (g->n[0] + tile - 1) / tile;
+    p.tiles1 = (g->n[1] + tile - 1) / tile;
+    const int64_t ctas = (int64_t)p.tiles0 * p.tiles1 * (n_events > 0 ? n_events : 1);
+    const int per_sm = p.separable ? 2 : 4;
+    const int64_t target = 4LL * sm_count() * per_sm;
+    int64_t s = (target + ctas - 1) / ctas;
+    if (s < 1) s = 1;
+    if (s > 32) s = 32;
+    p.splits = forced_splits > 0 ? forced_splits : (int)s;
+    return p;
+}
+
+size_t grid_partials_bytes(const GridPlan &p, int n_events, const retina_grid *g) {
+    if (p.splits <= 1) return 0;
+    return (size_t)p.splits * (size_t)n_events * (size_t)g->n[0] * (size_t)g->n[1] * sizeof(float);
+}
+
+cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t n_hits, const int64_t *off,
+                                 int n_events, int model,
+                                 const retina_grid *g, float sigma, float *R, float *partials, cudaStream_t st) {
+    GridDev gd{g->lo[0], g->lo[1], g->step[0], g->step[1], g->n[0], g->n[1]};
+    const double kkd = kLog2e / ((double)sigma * (double)sigma);
+    const float kk = (float)kkd;
+    const float sk = (float)sqrt(kkd);
+    const int64_t cells = (int64_t)g->n[0] * g->n[1];
+    float *dst = p.splits > 1 ? partials : R;
+    const int64_t split_stride = cells * n_events;
+    dim3 grid(p.tiles0 * p.tiles1, p.splits, n_events);
+    if (p.separable) {
+        grid_sep_kernel<<<grid, SEP_THREADS, 0, st>>>(hits, n_hits, off, gd, kk, p.splits, p.tiles0, dst, split_stride, cells);
+    } else if (model == RETINA_VELO_SLOPES) {
+        grid_direct_kernel<RETINA_VELO_SLOPES>
+            <<<grid, DIR_THREADS, 0, st>>>(hits, n_hits, off, gd, kk, sk, p.splits, p.tiles0, dst, split_stride, cells);
+    } else {
+        grid_direct_kernel<RETINA_TOY2D>
+            <<<grid, DIR_THREADS, 0, st>>>(hits, n_hits, off, gd, kk, sk, p.splits, p.tiles0, dst, split_stride, cells);
+    }
+    count_launches(1);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    if (p.splits > 1) {
+        count_launches(1);
+        const int64_t n = split_stride;
+        int blocks = (int)((n + 255) / 256);
+        const int cap = sm_count() * 8;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        reduce_partials_kernel<<<blocks, 256, 0, st>>>(partials, p.splits, split_stride, n, R);
+        err = cudaGetLastError();
+    }
+    return err;
+}
+
+}  // namespace retina

@@ -1,0 +1,40 @@
+// Launchers shared between the translation units of the library (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace retina {
+
+struct GridPlan {
+    int separable;
+    int splits;
+    int tiles0, tiles1;
+};
+GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int forced_splits);
+size_t grid_partials_bytes(const GridPlan &p, int n_events, const retina_grid *g);
+cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t n_hits, const int64_t *off,
+                                 int n_events, int model, const retina_grid *g, float sigma, float *R, float *partials,
+                                 cudaStream_t st);
+size_t maxima_ws_bytes(int n_events, const retina_grid *g);
+cudaError_t launch_grid_maxima(const float *R, int n_events, const retina_grid *g, float R0, int32_t *max_idx,
+                               float *max_theta, float *max_R, int32_t *n_max, int K, int32_t *ws_counts,
+                               cudaStream_t st);
+cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
+                                const float *seeds, int n_seeds, const retina_ls_opts *o, const retina_grid *box,
+                                float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, int seeds_per_warp,
+                                int smem_hits,
+                                cudaStream_t st);
+cudaError_t launch_response(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
+                            const float *theta, int n_points, float sigma, int want_derivs, float *out,
+                            cudaStream_t st);
+cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                                  int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
+                                  float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
+                                  cudaStream_t st);
+
+int maxima_blocks(const retina_grid *g);
+int sm_count();
+void count_launches(int n);
+size_t extract_smem_bytes(int n_points);
+
+}  // namespace retina

@@ -1,0 +1,328 @@
+"""Thin Python binding of libretina (include/retina.h): argument marshalling only.
+
+Every function takes and returns torch CUDA tensors, allocates its outputs
+and workspace with torch (device memory and streams are torch's job here),
+calls the C entry point of the same name on the current stream and raises
+``RetinaError`` on a non-zero status.  There is no CPU path: if the compiled
+library is missing the import of this module fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import torch
+
+from . import build as _build
+
+TOY2D = 0
+VELO_SLOPES = 1
+GRID_AUTO, GRID_DIRECT, GRID_SEPARABLE = 0, 1, 2
+MAX_Q = 8
+MAX_EXTRACT_POINTS = 8192
+OPT_LS_SEEDS_PER_WARP, OPT_LS_SMEM_HITS, OPT_GRID_SPLITS = 1, 2, 3
+
+HEADER = os.path.join(_build.INCLUDE, "retina.h")
+
+
+class RetinaError(RuntimeError):
+    def __init__(self, fn: str, code: int, text: str):
+        super().__init__("%s failed: %s (status %d)" % (fn, text, code))
+        self.code = code
+
+
+class _CGrid(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 2), ("step", ctypes.c_float * 2), ("n", ctypes.c_int32 * 2)]
+
+
+class _CLsOpts(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_float * 8), ("c1", ctypes.c_float),
+                ("max_halvings", ctypes.c_int32), ("step_cap_cells", ctypes.c_float)]
+
+
+@dataclass(frozen=True)
+class Grid:
+    """Grid of units / search box: centres lo + (i + 1/2) step, i < n."""
+
+    lo: Tuple[float, float]
+    step: Tuple[float, float]
+    n: Tuple[int, int]
+
+    def c(self) -> _CGrid:
+        g = _CGrid()
+        for a in range(2):
+            g.lo[a] = float(self.lo[a])
+            g.step[a] = float(self.step[a])
+            g.n[a] = int(self.n[a])
+        return g
+
+    @staticmethod
+    def of(wl) -> "Grid":
+        return Grid(tuple(wl.grid_lo), tuple(wl.grid_step), tuple(wl.grid_n))
+
+
+@dataclass(frozen=True)
+class LsOpts:
+    """Local-search options (Algorithm 1, Section 3)."""
+
+    sigma: Tuple[float, ...] = (0.3, 0.175, 0.05)
+    c1: float = 1e-4
+    max_halvings: int = 8
+    step_cap_cells: float = 4.0
+
+    def c(self) -> _CLsOpts:
+        o = _CLsOpts()
+        o.q = len(self.sigma)
+        for j, v in enumerate(self.sigma[:8]):
+            o.sigma[j] = float(v)
+        o.c1 = float(self.c1)
+        o.max_halvings = int(self.max_halvings)
+        o.step_cap_cells = float(self.step_cap_cells)
+        return o
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libretina.so is not built (%s); run paper_1709_08610_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    P, I32, I64, F, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    L.retina_strerror.argtypes = [ctypes.c_int]
+    L.retina_strerror.restype = ctypes.c_char_p
+    L.retina_abi_version.restype = ctypes.c_int
+    L.retina_set_option.argtypes = [I32, I32]
+    L.retina_get_option.argtypes = [I32, P]
+    L.retina_grid_scan_workspace_size.argtypes = [I32, I32, P, I32, I32, P]
+    L.retina_grid_scan.argtypes = [P, I64, P, I32, I32, P, F, F, I32, P, P, P, P, P, I32, P, SZ, P]
+    L.retina_grid_maxima_workspace_size.argtypes = [I32, P, P]
+    L.retina_grid_maxima.argtypes = [P, I32, P, F, P, P, P, P, I32, P, SZ, P]
+    L.retina_response.argtypes = [P, I64, P, I32, I32, P, I32, F, I32, P, P]
+    L.retina_local_search.argtypes = [P, I64, P, I32, I32, P, I32, P, P, P, P, P, P, P]
+    L.retina_extract_tracks.argtypes = [P, P, P, P, I32, I32, P, F, F, P, P, P, P, I32, P]
+    L.retina_grid_response_workspace_size.argtypes = [I32, I32, P, I32, P]
+    L.retina_grid_response.argtypes = [P, I64, P, I32, I32, P, F, I32, P, P, SZ, P]
+    L.retina_launch_count.restype = ctypes.c_uint64
+    L.retina_alu_probe_sink_floats.restype = ctypes.c_int64
+    L.retina_alu_probe.argtypes = [I32, I32, P, P, P]
+    for name in ("retina_set_option", "retina_get_option", "retina_grid_scan_workspace_size", "retina_grid_scan",
+                 "retina_grid_response_workspace_size", "retina_grid_response", "retina_alu_probe",
+                 "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
+                 "retina_local_search", "retina_extract_tracks"):
+        getattr(L, name).restype = ctypes.c_int
+    return L
+
+
+lib = _load()
+
+
+def header_functions() -> list:
+    """Names of the functions include/retina.h declares."""
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(retina_\w+)\s*\(", src, flags=re.M)))
+
+
+def _check(fn: str, code: int):
+    if code != 0:
+        raise RetinaError(fn, code, lib.retina_strerror(code).decode())
+
+
+def _p(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str, last: Optional[int] = None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if last is not None and (t.dim() < 1 or t.shape[-1] != last):
+        raise ValueError("%s must have last dimension %d" % (name, last))
+    return t
+
+
+def set_option(option: int, value: int):
+    _check("retina_set_option", lib.retina_set_option(option, value))
+
+
+def get_option(option: int) -> int:
+    v = ctypes.c_int32()
+    _check("retina_get_option", lib.retina_get_option(option, ctypes.byref(v)))
+    return v.value
+
+
+def grid_scan_workspace_size(n_events: int, model: int, grid: Grid, flags: int = 0, store_R: bool = False) -> int:
+    b = ctypes.c_size_t()
+    g = grid.c()
+    _check("retina_grid_scan_workspace_size",
+           lib.retina_grid_scan_workspace_size(n_events, model, ctypes.byref(g), flags, int(store_R), ctypes.byref(b)))
+    return b.value
+
+
+def grid_scan(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: Grid, sigma: float, R0: float, K: int,
+              flags: int = GRID_AUTO, store_R: bool = False, ws: Optional[torch.Tensor] = None, out=None,
+              stream=None) -> dict:
+    """Eq. 2 on the grid plus strict local maxima >= R0 (grid algorithm steps 2-4)."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    E = offsets.numel() - 1
+    dev = hits.device
+    n0, n1 = grid.n
+    if out is None:
+        out = dict(max_idx=torch.empty((E, K), dtype=torch.int32, device=dev),
+                   max_theta=torch.empty((E, K, 2), dtype=torch.float32, device=dev),
+                   max_R=torch.empty((E, K), dtype=torch.float32, device=dev),
+                   n_max=torch.empty((E,), dtype=torch.int32, device=dev),
+                   R=torch.empty((E, n1, n0), dtype=torch.float32, device=dev) if store_R else None)
+    need = grid_scan_workspace_size(E, model, grid, flags, store_R)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    g = grid.c()
+    _check("retina_grid_scan", lib.retina_grid_scan(
+        _p(hits), hits.shape[0], _p(offsets), E, model, ctypes.byref(g), float(sigma), float(R0), flags,
+        _p(out["R"]), _p(out["max_idx"]), _p(out["max_theta"]), _p(out["max_R"]), _p(out["n_max"]), K,
+        _p(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def grid_response(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: Grid, sigma: float,
+                  flags: int = GRID_AUTO, R_out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """Eq. 2 alone: R [E, n1, n0]."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    E = offsets.numel() - 1
+    n0, n1 = grid.n
+    if R_out is None:
+        R_out = torch.empty((E, n1, n0), dtype=torch.float32, device=hits.device)
+    g = grid.c()
+    b = ctypes.c_size_t()
+    _check("retina_grid_response_workspace_size",
+           lib.retina_grid_response_workspace_size(E, model, ctypes.byref(g), flags, ctypes.byref(b)))
+    if ws is None or ws.numel() < b.value:
+        ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=hits.device)
+    _check("retina_grid_response", lib.retina_grid_response(
+        _p(hits), hits.shape[0], _p(offsets), E, model, ctypes.byref(g), float(sigma), flags, _p(R_out), _p(ws),
+        ws.numel(), _stream(stream)))
+    return R_out
+
+
+def grid_response_workspace_size(n_events: int, model: int, grid: Grid, flags: int = 0) -> int:
+    g = grid.c()
+    b = ctypes.c_size_t()
+    _check("retina_grid_response_workspace_size",
+           lib.retina_grid_response_workspace_size(n_events, model, ctypes.byref(g), flags, ctypes.byref(b)))
+    return b.value
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib.retina_launch_count())
+
+
+def alu_probe(kind: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Launch the FP32 (0), MUFU ex2 (1) or packed FP32x2 (2) throughput probe; returns its op count."""
+    ops = ctypes.c_double()
+    _check("retina_alu_probe", lib.retina_alu_probe(kind, iters, _p(sink), ctypes.byref(ops), _stream(stream)))
+    return ops.value
+
+
+def alu_probe_sink_floats() -> int:
+    return int(lib.retina_alu_probe_sink_floats())
+
+
+def grid_maxima(R: torch.Tensor, grid: Grid, R0: float, K: int, out=None, ws=None, stream=None) -> dict:
+    """Strict 3x3 local maxima >= R0 of a response grid [E, n1, n0]."""
+    _dev(R, torch.float32, "R")
+    E = R.shape[0]
+    dev = R.device
+    b = ctypes.c_size_t()
+    g = grid.c()
+    _check("retina_grid_maxima_workspace_size", lib.retina_grid_maxima_workspace_size(E, ctypes.byref(g),
+                                                                                        ctypes.byref(b)))
+    if ws is None or ws.numel() < b.value:
+        ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = dict(max_idx=torch.empty((E, K), dtype=torch.int32, device=dev),
+               max_theta=torch.empty((E, K, 2), dtype=torch.float32, device=dev),
+               max_R=torch.empty((E, K), dtype=torch.float32, device=dev),
+               n_max=torch.empty((E,), dtype=torch.int32, device=dev))
+    _check("retina_grid_maxima", lib.retina_grid_maxima(
+        _p(R), E, ctypes.byref(g), float(R0), _p(out["max_idx"]), _p(out["max_theta"]), _p(out["max_R"]),
+        _p(out["n_max"]), K, _p(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def response(hits: torch.Tensor, offsets: torch.Tensor, model: int, theta: torch.Tensor, sigma: float,
+             want_derivs: bool = True, stream=None) -> torch.Tensor:
+    """[E, P, 6] = (R, g0, g1, H00, H01, H11) at theta [E, P, 2] (Eq. 1 + derivatives)."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    _dev(theta, torch.float32, "theta", 2)
+    E = offsets.numel() - 1
+    P = theta.shape[-2] if theta.dim() == 3 else theta.shape[0]
+    out = torch.zeros((E, P, 6), dtype=torch.float32, device=hits.device)
+    _check("retina_response", lib.retina_response(_p(hits), hits.shape[0], _p(offsets), E, model, _p(theta), P,
+                                                  float(sigma), int(want_derivs), _p(out), _stream(stream)))
+    return out
+
+
+def local_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds: torch.Tensor, opts: LsOpts,
+                 box: Grid, out=None, n_evals: Optional[torch.Tensor] = None,
+                 stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+    """Algorithm 1's q truncated-Newton updates: (theta [E,n,2], R [E,n], status [E,n] uint8).
+
+    n_evals (optional uint8 [E, n]) receives each seed's number of R-only passes.
+    """
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    _dev(seeds, torch.float32, "seeds", 2)
+    E = offsets.numel() - 1
+    n = seeds.shape[-2]
+    if seeds.numel() != E * n * 2:
+        raise ValueError("seeds must be [E, n_seeds, 2]")
+    dev = hits.device
+    if out is None:
+        out = (torch.empty((E, n, 2), dtype=torch.float32, device=dev),
+               torch.empty((E, n), dtype=torch.float32, device=dev),
+               torch.empty((E, n), dtype=torch.uint8, device=dev))
+    o = opts.c()
+    g = box.c()
+    _check("retina_local_search", lib.retina_local_search(
+        _p(hits), hits.shape[0], _p(offsets), E, model, _p(seeds), n, ctypes.byref(o), ctypes.byref(g),
+        _p(out[0]), _p(out[1]), _p(out[2]), _p(n_evals), _stream(stream)))
+    return out
+
+
+def extract_tracks(theta: torch.Tensor, R: torch.Tensor, status: Optional[torch.Tensor], box: Grid, R0: float,
+                   merge_cells: float, K: int, n_valid: Optional[torch.Tensor] = None, out=None,
+                   stream=None) -> dict:
+    """Cluster + select best above R0 (Algorithm 1): kept points in visiting order."""
+    _dev(theta, torch.float32, "theta", 2)
+    _dev(R, torch.float32, "R")
+    if status is not None:
+        _dev(status, torch.uint8, "status")
+    if n_valid is not None:
+        _dev(n_valid, torch.int32, "n_valid")
+    E = theta.shape[0] if theta.dim() == 3 else 1
+    n = theta.shape[-2]
+    dev = theta.device
+    if out is None:
+        out = dict(tracks=torch.empty((E, K, 2), dtype=torch.float32, device=dev),
+                   track_R=torch.empty((E, K), dtype=torch.float32, device=dev),
+                   track_src=torch.empty((E, K), dtype=torch.int32, device=dev),
+                   n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
+    g = box.c()
+    _check("retina_extract_tracks", lib.retina_extract_tracks(
+        _p(theta), _p(R), _p(status), _p(n_valid), E, n, ctypes.byref(g), float(R0), float(merge_cells),
+        _p(out["tracks"]), _p(out["track_R"]), _p(out["track_src"]), _p(out["n_tracks"]), K, _stream(stream)))
+    return out

@@ -16,6 +16,7 @@ from .events import (  # noqa: F401
     make_velo_event,
     make_event,
     make_batch,
+    batch_of,
     uniform_seeds,
     close_tracks_event,
 )

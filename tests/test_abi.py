@@ -1,0 +1,140 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/retina.h declares, and its host-side validation rejects bad arguments
+before anything is launched (RETINA_EINVAL / RETINA_ENOSPACE)."""
+import ctypes
+
+import pytest
+
+from paper_1709_08610_gb300 import build as rbuild
+
+rbuild.build()
+from paper_1709_08610_gb300 import retina as rt  # noqa: E402
+
+EINVAL, ENOSPACE = 1, 3
+L = rt.lib
+BOGUS = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails validation first
+
+
+def test_exports_every_declared_function():
+    names = rt.header_functions()
+    assert len(names) >= 11
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_version():
+    assert L.retina_abi_version() == 1
+    for c in range(5):
+        assert L.retina_strerror(c)
+    assert b"invalid" in L.retina_strerror(EINVAL)
+
+
+def test_options_roundtrip_and_validation():
+    old = rt.get_option(rt.OPT_LS_SEEDS_PER_WARP)
+    rt.set_option(rt.OPT_LS_SEEDS_PER_WARP, 2)
+    assert rt.get_option(rt.OPT_LS_SEEDS_PER_WARP) == 2
+    rt.set_option(rt.OPT_LS_SEEDS_PER_WARP, old)
+    assert L.retina_set_option(rt.OPT_LS_SEEDS_PER_WARP, 3) == EINVAL
+    assert L.retina_set_option(rt.OPT_LS_SMEM_HITS, -1) == EINVAL
+    assert L.retina_set_option(999, 1) == EINVAL
+
+
+def _grid(lo=(-0.5, -0.5), step=(2 ** -10, 2 ** -10), n=(1024, 1024)):
+    return rt.Grid(lo, step, n).c()
+
+
+def test_workspace_size():
+    b = ctypes.c_size_t()
+    g = _grid()
+    assert L.retina_grid_scan_workspace_size(1, 1, ctypes.byref(g), 0, 0, ctypes.byref(b)) == 0
+    assert b.value >= 1024 * 1024 * 4  # the response grid lives in the workspace when not stored
+    b2 = ctypes.c_size_t()
+    assert L.retina_grid_scan_workspace_size(1, 1, ctypes.byref(g), 0, 1, ctypes.byref(b2)) == 0
+    assert b2.value < b.value
+    bad = _grid(step=(0.0, 1.0))
+    assert L.retina_grid_scan_workspace_size(1, 1, ctypes.byref(bad), 0, 0, ctypes.byref(b)) == EINVAL
+    # separable contraction is defined for the slope model only
+    assert L.retina_grid_scan_workspace_size(1, 0, ctypes.byref(g), 2, 0, ctypes.byref(b)) == EINVAL
+
+
+@pytest.mark.parametrize("sigma,K,model,flags", [(0.0, 8, 1, 0), (-1.0, 8, 1, 0), (float("nan"), 8, 1, 0),
+                                                 (float("inf"), 8, 1, 0), (0.3, 0, 1, 0), (0.3, 8, 7, 0),
+                                                 (0.3, 8, 0, 2), (0.3, 8, 1, 9)])
+def test_grid_scan_rejects(sigma, K, model, flags):
+    g = _grid()
+    rc = L.retina_grid_scan(BOGUS, 10, BOGUS, 1, model, ctypes.byref(g), sigma, 1.0, flags, None, BOGUS, BOGUS,
+                            BOGUS, BOGUS, K, BOGUS, 1 << 40, None)
+    assert rc == EINVAL
+
+
+def test_grid_scan_rejects_misaligned_and_small_workspace():
+    g = _grid()
+    rc = L.retina_grid_scan(ctypes.c_void_p(0x1004), 10, BOGUS, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS,
+                            BOGUS, BOGUS, BOGUS, 8, BOGUS, 1 << 40, None)
+    assert rc == EINVAL
+    rc = L.retina_grid_scan(BOGUS, 10, BOGUS, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS, BOGUS, BOGUS, BOGUS,
+                            8, BOGUS, 16, None)
+    assert rc == ENOSPACE
+    rc = L.retina_grid_scan(BOGUS, 10, None, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS, BOGUS, BOGUS, BOGUS,
+                            8, BOGUS, 1 << 40, None)
+    assert rc == EINVAL
+
+
+def _opts(**kw):
+    o = rt.LsOpts(**kw).c()
+    return o
+
+
+@pytest.mark.parametrize("mut", ["q0", "q9", "sigma0", "sigmanan", "c1neg", "c1one", "halv", "cap0"])
+def test_local_search_rejects(mut):
+    o = _opts()
+    if mut == "q0":
+        o.q = 0
+    elif mut == "q9":
+        o.q = 9
+    elif mut == "sigma0":
+        o.sigma[1] = 0.0
+    elif mut == "sigmanan":
+        o.sigma[2] = float("nan")
+    elif mut == "c1neg":
+        o.c1 = -0.1
+    elif mut == "c1one":
+        o.c1 = 1.0
+    elif mut == "halv":
+        o.max_halvings = 31
+    elif mut == "cap0":
+        o.step_cap_cells = 0.0
+    g = _grid()
+    rc = L.retina_local_search(BOGUS, 10, BOGUS, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), BOGUS, BOGUS,
+                               BOGUS, None, None)
+    assert rc == EINVAL
+
+
+def test_local_search_rejects_null_outputs_and_empty_is_ok():
+    o = _opts()
+    g = _grid()
+    assert L.retina_local_search(BOGUS, 10, BOGUS, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), None, BOGUS,
+                                 BOGUS, None, None) == EINVAL
+    # zero events or zero seeds: nothing to do, nothing launched
+    assert L.retina_local_search(None, 0, None, 0, 1, None, 16, ctypes.byref(o), ctypes.byref(g), None, None, None,
+                                 None, None) == 0
+    assert L.retina_local_search(BOGUS, 10, BOGUS, 1, 1, BOGUS, 0, ctypes.byref(o), ctypes.byref(g), None, None,
+                                 None, None, None) == 0
+
+
+def test_extract_tracks_rejects():
+    g = _grid()
+    call = lambda n_points, merge, K, R0=1.0: L.retina_extract_tracks(
+        BOGUS, BOGUS, None, None, 1, n_points, ctypes.byref(g), R0, merge, BOGUS, BOGUS, None, BOGUS, K, None)
+    assert call(8193, 2.0, 8) == ENOSPACE
+    assert call(16, 0.0, 8) == EINVAL
+    assert call(16, float("nan"), 8) == EINVAL
+    assert call(16, 2.0, 0) == EINVAL
+    assert call(16, 2.0, 8, R0=float("nan")) == EINVAL
+    assert call(16, 1e-3, 8) == EINVAL  # too many merge buckets per axis
+
+
+def test_response_rejects():
+    assert L.retina_response(BOGUS, 10, BOGUS, 1, 1, BOGUS, 4, 0.0, 1, BOGUS, None) == EINVAL
+    assert L.retina_response(BOGUS, 10, BOGUS, 1, 5, BOGUS, 4, 0.3, 1, BOGUS, None) == EINVAL
+    assert L.retina_response(BOGUS, 10, BOGUS, 1, 1, None, 4, 0.3, 1, BOGUS, None) == EINVAL
