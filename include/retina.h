@@ -188,6 +188,37 @@ int retina_grid_maxima(const float *R, int32_t n_events, const retina_grid *g, f
                        void *stream);
 
 /*
+ * retina_grid_maxima_static - retina_grid_maxima without a workspace.
+ *
+ * The paper has no counterpart: this is an interface variant for callers
+ * that cannot allocate device memory - for example a plugin running inside a
+ * host application whose memory manager owns every device allocation, or a
+ * foreign-language caller with no device allocator of its own - and so
+ * cannot supply the workspace the other entry points take.  Same rule,
+ * arguments and outputs as retina_grid_maxima; the outputs are still the
+ * caller's.
+ *
+ * Its scratch (two int32 per 2048-cell block per event) lives in one
+ * library-owned device array of RETINA_STATIC_SCRATCH_BYTES, held by every
+ * GPU that loads the library until the process exits.  Limits and behaviour:
+ * - 2 * n_events * ceil(n0 * n1 / 2048) * 4 bytes must fit in
+ *   RETINA_STATIC_SCRATCH_BYTES (1 MiB: e.g. 256 events of 1024 x 1024 or 64
+ *   of 2048 x 2048); larger requests return RETINA_ENOSPACE, nothing launched.
+ * - The first call on a device looks up the array's device address (with that
+ *   device current, i.e. the CUDA runtime's current device must be the one
+ *   `stream` belongs to); make that first call before any stream capture.
+ * - All calls share the one array, so calls whose kernels overlap on the GPU
+ *   (different streams, no ordering between them) race and give undefined
+ *   results; calls ordered on one stream are safe.  The array keeps the last
+ *   call's contents, and each call writes every part it reads first, so no
+ *   result depends on an earlier call.
+ * - Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define RETINA_STATIC_SCRATCH_BYTES (1 << 20)
+int retina_grid_maxima_static(const float *R, int32_t n_events, const retina_grid *g, float R0, int32_t *max_idx,
+                              float *max_theta, float *max_R, int32_t *n_max, int32_t K, void *stream);
+
+/*
  * retina_response - R, grad R and Hess R at arbitrary points.
  *
  * Paper: Section 2, Eq. 1, and the remark that the gradient and the Hessian

@@ -107,8 +107,10 @@ def _load():
     L.retina_launch_count.restype = ctypes.c_uint64
     L.retina_alu_probe_sink_floats.restype = ctypes.c_int64
     L.retina_alu_probe.argtypes = [I32, I32, P, P, P]
+    L.retina_grid_maxima_static.argtypes = [P, I32, P, F, P, P, P, P, I32, P]
     for name in ("retina_set_option", "retina_get_option", "retina_grid_scan_workspace_size", "retina_grid_scan",
                  "retina_grid_response_workspace_size", "retina_grid_response", "retina_alu_probe",
+                 "retina_grid_maxima_static",
                  "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
                  "retina_local_search", "retina_extract_tracks"):
         getattr(L, name).restype = ctypes.c_int
