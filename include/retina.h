@@ -81,6 +81,10 @@ extern "C" {
 #define RETINA_OPT_LS_SEEDS_PER_WARP 1 /* 1, 2 or 4 seeds per warp (1)          */
 #define RETINA_OPT_LS_SMEM_HITS 2      /* hits staged in shared memory (4096)   */
 #define RETINA_OPT_GRID_SPLITS 3       /* hit slices per grid tile, 0=auto (0)  */
+#define RETINA_OPT_LS_WARPS 4          /* warps per search CTA: 4, 8 or 16 (8)  */
+#define RETINA_OPT_BATCH_SEEDS_PER_WARP 5 /* batched search: 1, 2 or 4 (1)      */
+#define RETINA_OPT_BATCH_WARPS 6       /* batched search CTA warps: 8,16,32 (16) */
+#define RETINA_OPT_BATCH_SMEM_HITS 7   /* batched search staged hits (8192)     */
 
 typedef struct {
     float lo[2];   /* lower edge of the box per axis                      */
@@ -262,13 +266,43 @@ int retina_response(const float *hits, int64_t n_hits, const int64_t *event_offs
  *   status    : uint8 [n_events][n_seeds]: 0 ok, 1 some line search took no
  *               step, 2 final point outside the box, 3 non-finite.
  *   n_evals   : nullable uint8 [n_events][n_seeds]: number of R-only passes
- *               over the hits the seed used (line-search trials plus the
- *               final response); with the q passes of R, grad R and Hess R
- *               this is the seed's exact work, in units of the paper's T0.
+ *               over the hits the seed used (its line-search trials); with
+ *               the q passes of R, grad R and Hess R this is the seed's exact
+ *               work, in units of the paper's T0 (R_out needs no extra pass:
+ *               it is the accepted trial's response, or the last pass's R).
  */
 int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
                         const float *seeds, int32_t n_seeds, const retina_ls_opts *opts, const retina_grid *box,
                         float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, void *stream);
+
+/*
+ * retina_batched_search - Algorithm 1 over a ragged batch, one persistent launch.
+ *
+ * Paper: Algorithm 1 with the Section 3 update, exactly as retina_local_search
+ * (same per-seed arithmetic, bitwise the same results for the same seeds),
+ * for events of uneven hit and seed counts.  Scheduling: a CTA claims events
+ * by an atomic ticket in `order`, stages the event's hits in shared memory
+ * and its warps pull groups of seeds from the event's atomic counter; when
+ * all events are claimed, CTAs help the events still in progress.  No CTA
+ * waits on another; all loops are bounded.
+ *
+ *   seeds       : float32 [n_seeds][2]; event e owns rows
+ *                 seed_offsets[e] .. seed_offsets[e+1]-1 (int64 [n_events+1],
+ *                 device; clamped to [0, n_seeds] like the hit offsets).
+ *   order       : nullable int32 [n_events] (device): claim order of the events
+ *                 (e.g. largest first); entries outside [0, n_events) are
+ *                 skipped; NULL means 0, 1, 2, ...  Each event must appear at
+ *                 most once.
+ *   theta_out, R_out, status, n_evals : per seed, as retina_local_search.
+ *   ws, ws_bytes: >= retina_batched_search_workspace_size(n_events) bytes,
+ *                 256-byte aligned; zeroed by this call with an async memset on
+ *                 `stream` before the kernel (both are stream operations).
+ */
+int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes);
+int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                          int32_t model, const float *seeds, int64_t n_seeds, const int64_t *seed_offsets,
+                          const int32_t *order, const retina_ls_opts *opts, const retina_grid *box, float *theta_out,
+                          float *R_out, uint8_t *status, uint8_t *n_evals, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * retina_extract_tracks - cluster the points and keep the best of each.

@@ -14,6 +14,10 @@ void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order
 static std::atomic<int> g_opt_seeds_per_warp{1};
 static std::atomic<int> g_opt_smem_hits{4096};
 static std::atomic<int> g_opt_grid_splits{0};
+static std::atomic<int> g_opt_ls_warps{8};
+static std::atomic<int> g_opt_batch_spw{1};
+static std::atomic<int> g_opt_batch_warps{16};
+static std::atomic<int> g_opt_batch_smem_hits{8192};
 
 static bool finite_pos(float v) { return isfinite(v) && v > 0.f; }
 
@@ -81,6 +85,22 @@ int retina_set_option(int32_t option, int32_t value) {
             if (value < 0 || value > 64) return RETINA_EINVAL;
             g_opt_grid_splits = value;
             return RETINA_OK;
+        case RETINA_OPT_LS_WARPS:
+            if (value != 4 && value != 8 && value != 16) return RETINA_EINVAL;
+            g_opt_ls_warps = value;
+            return RETINA_OK;
+        case RETINA_OPT_BATCH_SEEDS_PER_WARP:
+            if (value != 1 && value != 2 && value != 4) return RETINA_EINVAL;
+            g_opt_batch_spw = value;
+            return RETINA_OK;
+        case RETINA_OPT_BATCH_WARPS:
+            if (value != 8 && value != 16 && value != 32) return RETINA_EINVAL;
+            g_opt_batch_warps = value;
+            return RETINA_OK;
+        case RETINA_OPT_BATCH_SMEM_HITS:
+            if (value < 0 || value > 12288) return RETINA_EINVAL;
+            g_opt_batch_smem_hits = value;
+            return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -91,6 +111,10 @@ int retina_get_option(int32_t option, int32_t *value) {
         case RETINA_OPT_LS_SEEDS_PER_WARP: *value = g_opt_seeds_per_warp; return RETINA_OK;
         case RETINA_OPT_LS_SMEM_HITS: *value = g_opt_smem_hits; return RETINA_OK;
         case RETINA_OPT_GRID_SPLITS: *value = g_opt_grid_splits; return RETINA_OK;
+        case RETINA_OPT_LS_WARPS: *value = g_opt_ls_warps; return RETINA_OK;
+        case RETINA_OPT_BATCH_SEEDS_PER_WARP: *value = g_opt_batch_spw; return RETINA_OK;
+        case RETINA_OPT_BATCH_WARPS: *value = g_opt_batch_warps; return RETINA_OK;
+        case RETINA_OPT_BATCH_SMEM_HITS: *value = g_opt_batch_smem_hits; return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -214,7 +238,37 @@ int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
     return cuda_status(launch_local_search((const float4 *)hits, n_hits, event_offsets, n_events, model, seeds,
                                            n_seeds, opts, box, theta_out, R_out, status, n_evals, g_opt_seeds_per_warp,
-                                           g_opt_smem_hits, (cudaStream_t)stream));
+                                           g_opt_ls_warps, g_opt_smem_hits, (cudaStream_t)stream));
+}
+
+int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes) {
+    if (!bytes || n_events < 0) return RETINA_EINVAL;
+    *bytes = batched_ws_bytes(n_events);
+    return RETINA_OK;
+}
+
+int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                          int32_t model, const float *seeds, int64_t n_seeds, const int64_t *seed_offsets,
+                          const int32_t *order, const retina_ls_opts *opts, const retina_grid *box, float *theta_out,
+                          float *R_out, uint8_t *status, uint8_t *n_evals, void *ws, size_t ws_bytes, void *stream) {
+    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !opts || !valid_grid(box)) return RETINA_EINVAL;
+    if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (opts->q < 1 || opts->q > RETINA_MAX_Q) return RETINA_EINVAL;
+    for (int j = 0; j < opts->q; ++j)
+        if (!finite_pos(opts->sigma[j])) return RETINA_EINVAL;
+    if (!(opts->c1 >= 0.f && opts->c1 < 1.f)) return RETINA_EINVAL;
+    if (opts->max_halvings < 0 || opts->max_halvings > 30) return RETINA_EINVAL;
+    if (!(opts->step_cap_cells > 0.f)) return RETINA_EINVAL;
+    if (n_seeds > (int64_t)INT32_MAX) return RETINA_EINVAL;
+    if (n_events == 0 || n_seeds == 0) return RETINA_OK;
+    if (!event_offsets || !seed_offsets || !seeds || !theta_out || !R_out || !status) return RETINA_EINVAL;
+    if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
+    if (ws_bytes < batched_ws_bytes(n_events)) return RETINA_ENOSPACE;
+    if (!ws || ((uintptr_t)ws & 255u)) return RETINA_EINVAL;
+    return cuda_status(launch_batched_search((const float4 *)hits, n_hits, event_offsets, n_events, model, seeds,
+                                             n_seeds, seed_offsets, order, opts, box, theta_out, R_out, status,
+                                             n_evals, (int32_t *)ws, g_opt_batch_spw, g_opt_batch_warps,
+                                             g_opt_batch_smem_hits, (cudaStream_t)stream));
 }
 
 int retina_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,

@@ -1,0 +1,169 @@
+// Algorithm 1 over a ragged batch of events in one persistent launch.
+//
+// Work is claimed, never waited for:
+//  * a CTA claims the next event with an atomic ticket (in the caller's
+//    order, e.g. largest first), stages its hits in shared memory once, and
+//    its warps pull groups of P seeds from the event's atomic group counter
+//    until the event is exhausted;
+//  * when every event has been claimed, CTAs help events still in progress
+//    (the first with groups left, scanned by the whole CTA), so one large
+//    event spreads over the whole GPU and the batch's tail balances.
+// No CTA ever waits on another CTA: the only waits are __syncthreads inside a
+// CTA, and every loop is bounded by the number of events and seeds.  The
+// counters live in the caller's workspace and are zeroed by an async memset
+// on the same stream before the launch.
+#include "search_device.cuh"
+
+namespace retina {
+
+struct BatchArgs {
+    const float4 *hits;
+    int64_t n_hits;
+    const int64_t *hit_off;
+    int n_events;
+    const float *seeds;
+    int64_t n_seeds;
+    const int64_t *seed_off;
+    const int32_t *order;
+    int smem_hits;
+    int64_t max_rounds;
+    float *theta_out;
+    float *R_out;
+    uint8_t *status;
+    uint8_t *n_evals;
+    int32_t *counters;  // [0] event ticket, [1] overrun flag, [2 + e] group counter of event e
+};
+
+__device__ __forceinline__ void seed_range(const BatchArgs &a, int e, int64_t &s0, int64_t &s1) {
+    int64_t x = a.seed_off[e], y = a.seed_off[e + 1];
+    x = x < 0 ? 0 : (x > a.n_seeds ? a.n_seeds : x);
+    y = y < x ? x : (y > a.n_seeds ? a.n_seeds : y);
+    s0 = x;
+    s1 = y;
+}
+
+template <int P>
+__device__ __forceinline__ int64_t n_groups_of(const BatchArgs &a, int e) {
+    int64_t s0, s1;
+    seed_range(a, e, s0, s1);
+    return (s1 - s0 + P - 1) / P;
+}
+
+template <int MODEL, int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) batched_search_kernel(BatchArgs a, LsParams prm) {
+    extern __shared__ float4 sh[];
+    __shared__ int cur_e;
+    const int tid = threadIdx.x, lane = tid & 31;
+    int staged = -1;
+    int n_staged = 0;
+    for (int64_t round = 0; round < a.max_rounds; ++round) {
+        // ---- pick an event: the next unclaimed one, else one still in progress
+        if (tid == 0) {
+            const int c = atomicAdd(&a.counters[0], 1);
+            int e = -1;
+            if (c < a.n_events) {
+                e = a.order ? a.order[c] : c;
+                if (e < 0 || e >= a.n_events) e = -2;  // invalid order entry: nothing to do this round
+            }
+            cur_e = e;
+        }
+        __syncthreads();
+        int e = cur_e;
+        __syncthreads();  // every thread has read cur_e before it is written again
+        if (e == -1) {
+            // all claimed: help the first event (from a CTA-dependent start) with groups left
+            if (tid == 0) cur_e = 0x7fffffff;
+            __syncthreads();
+            for (int i = tid; i < a.n_events; i += blockDim.x) {
+                const int ev = (int)((i + (int64_t)blockIdx.x * 7) % a.n_events);
+                const int64_t taken = *((volatile int32_t *)&a.counters[2 + ev]);
+                if (taken < n_groups_of<P>(a, ev)) atomicMin(&cur_e, ev);
+            }
+            __syncthreads();
+            e = cur_e;
+            __syncthreads();
+            if (e == 0x7fffffff) break;  // every event is exhausted
+        }
+        if (e < 0) continue;
+        int64_t hb, he, s0, s1;
+        event_range(a.hit_off, a.n_hits, e, hb, he);
+        seed_range(a, e, s0, s1);
+        const int H = (int)(he - hb);
+        const float4 *gh = a.hits + hb;
+        if (e != staged) {
+            n_staged = H < a.smem_hits ? H : a.smem_hits;
+            for (int k = tid; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
+            staged = e;
+        }
+        __syncthreads();
+        const int64_t groups = (s1 - s0 + P - 1) / P;
+        for (int64_t it = 0; it <= groups; ++it) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&a.counters[2 + e], 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= groups) break;
+            const int64_t s = s0 + (int64_t)g * P;
+            const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
+            search_group<MODEL, P>(sh, gh, n_staged, H, lane, a.seeds + 2 * s, n_live, prm, a.theta_out + 2 * s,
+                                   a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr);
+        }
+        __syncthreads();  // all warps done with the staged hits before the next round
+        if (round + 1 == a.max_rounds && tid == 0) atomicExch(&a.counters[1], 1);
+    }
+}
+
+size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(int32_t) + 255) / 256 * 256; }
+
+template <int MODEL, int P, int WARPS>
+static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, cudaStream_t st) {
+    auto kern = batched_search_kernel<MODEL, P, WARPS>;
+    const size_t smem = (size_t)a.smem_hits * sizeof(float4);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (err != cudaSuccess) return err;
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = per_sm * sm_count();
+    kern<<<grid, WARPS * 32, smem, st>>>(a, prm);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int MODEL, int P>
+static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParams &prm, cudaStream_t st) {
+    if (warps >= 32) return launch_batched_t<MODEL, P, 32>(a, prm, st);
+    if (warps >= 16) return launch_batched_t<MODEL, P, 16>(a, prm, st);
+    return launch_batched_t<MODEL, P, 8>(a, prm, st);
+}
+
+cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, int n_events, int model,
+                                  const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
+                                  const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
+                                  uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
+                                  int smem_hits, cudaStream_t st) {
+    LsParams prm = make_ls_params(o, box);
+    if (smem_hits < 0) smem_hits = 0;
+    if (smem_hits > 12288) smem_hits = 12288;
+    BatchArgs a{hits, n_hits, hit_off, n_events, seeds, n_seeds, seed_off, order, smem_hits,
+                (int64_t)n_events + n_seeds + 2, theta_out, R_out, status, n_evals, counters};
+    cudaError_t err = cudaMemsetAsync(counters, 0, batched_ws_bytes(n_events), st);
+    if (err != cudaSuccess) return err;
+#define RETINA_BATCH_CASE(M, PP) return launch_batched_w<M, PP>(warps, a, prm, st)
+    if (model == RETINA_VELO_SLOPES) {
+        if (seeds_per_warp >= 4) RETINA_BATCH_CASE(RETINA_VELO_SLOPES, 4);
+        if (seeds_per_warp == 2) RETINA_BATCH_CASE(RETINA_VELO_SLOPES, 2);
+        RETINA_BATCH_CASE(RETINA_VELO_SLOPES, 1);
+    } else {
+        if (seeds_per_warp >= 4) RETINA_BATCH_CASE(RETINA_TOY2D, 4);
+        if (seeds_per_warp == 2) RETINA_BATCH_CASE(RETINA_TOY2D, 2);
+        RETINA_BATCH_CASE(RETINA_TOY2D, 1);
+    }
+#undef RETINA_BATCH_CASE
+}
+
+}  // namespace retina

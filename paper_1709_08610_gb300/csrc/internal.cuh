@@ -22,7 +22,7 @@ cudaError_t launch_grid_maxima(const float *R, int n_events, const retina_grid *
 cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                                 const float *seeds, int n_seeds, const retina_ls_opts *o, const retina_grid *box,
                                 float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, int seeds_per_warp,
-                                int smem_hits,
+                                int warps, int smem_hits,
                                 cudaStream_t st);
 cudaError_t launch_response(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                             const float *theta, int n_points, float sigma, int want_derivs, float *out,
@@ -32,6 +32,12 @@ cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint
                                   float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
                                   cudaStream_t st);
 
+cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, int n_events, int model,
+                                  const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
+                                  const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
+                                  uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
+                                  int smem_hits, cudaStream_t st);
+size_t batched_ws_bytes(int n_events);
 int maxima_blocks(const retina_grid *g);
 int sm_count();
 void count_launches(int n);

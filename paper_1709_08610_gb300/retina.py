@@ -23,7 +23,8 @@ VELO_SLOPES = 1
 GRID_AUTO, GRID_DIRECT, GRID_SEPARABLE = 0, 1, 2
 MAX_Q = 8
 MAX_EXTRACT_POINTS = 8192
-OPT_LS_SEEDS_PER_WARP, OPT_LS_SMEM_HITS, OPT_GRID_SPLITS = 1, 2, 3
+OPT_LS_SEEDS_PER_WARP, OPT_LS_SMEM_HITS, OPT_GRID_SPLITS, OPT_LS_WARPS = 1, 2, 3, 4
+OPT_BATCH_SEEDS_PER_WARP, OPT_BATCH_WARPS, OPT_BATCH_SMEM_HITS = 5, 6, 7
 
 HEADER = os.path.join(_build.INCLUDE, "retina.h")
 
@@ -108,9 +109,11 @@ def _load():
     L.retina_alu_probe_sink_floats.restype = ctypes.c_int64
     L.retina_alu_probe.argtypes = [I32, I32, P, P, P]
     L.retina_grid_maxima_static.argtypes = [P, I32, P, F, P, P, P, P, I32, P]
+    L.retina_batched_search_workspace_size.argtypes = [I32, P]
+    L.retina_batched_search.argtypes = [P, I64, P, I32, I32, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
     for name in ("retina_set_option", "retina_get_option", "retina_grid_scan_workspace_size", "retina_grid_scan",
                  "retina_grid_response_workspace_size", "retina_grid_response", "retina_alu_probe",
-                 "retina_grid_maxima_static",
+                 "retina_grid_maxima_static", "retina_batched_search_workspace_size", "retina_batched_search",
                  "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
                  "retina_local_search", "retina_extract_tracks"):
         getattr(L, name).restype = ctypes.c_int
@@ -302,6 +305,47 @@ def local_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds: t
     _check("retina_local_search", lib.retina_local_search(
         _p(hits), hits.shape[0], _p(offsets), E, model, _p(seeds), n, ctypes.byref(o), ctypes.byref(g),
         _p(out[0]), _p(out[1]), _p(out[2]), _p(n_evals), _stream(stream)))
+    return out
+
+
+def batched_search_workspace_size(n_events: int) -> int:
+    b = ctypes.c_size_t()
+    _check("retina_batched_search_workspace_size", lib.retina_batched_search_workspace_size(n_events, ctypes.byref(b)))
+    return b.value
+
+
+def batched_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds: torch.Tensor,
+                   seed_offsets: torch.Tensor, opts: LsOpts, box: Grid, order: Optional[torch.Tensor] = None,
+                   out=None, n_evals: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
+                   stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+    """Algorithm 1 over a ragged batch in one persistent launch.
+
+    seeds [S, 2] float32 with seed_offsets int64 [E + 1]; returns per seed
+    (theta [S, 2], R [S], status [S] uint8).
+    """
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    _dev(seeds, torch.float32, "seeds", 2)
+    _dev(seed_offsets, torch.int64, "seed_offsets")
+    if order is not None:
+        _dev(order, torch.int32, "order")
+    E = offsets.numel() - 1
+    if seed_offsets.numel() != E + 1:
+        raise ValueError("seed_offsets must have n_events + 1 entries")
+    S = seeds.numel() // 2
+    dev = hits.device
+    if out is None:
+        out = (torch.empty((S, 2), dtype=torch.float32, device=dev),
+               torch.empty((S,), dtype=torch.float32, device=dev),
+               torch.empty((S,), dtype=torch.uint8, device=dev))
+    need = batched_search_workspace_size(E)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    o = opts.c()
+    g = box.c()
+    _check("retina_batched_search", lib.retina_batched_search(
+        _p(hits), hits.shape[0], _p(offsets), E, model, _p(seeds), S, _p(seed_offsets), _p(order), ctypes.byref(o),
+        ctypes.byref(g), _p(out[0]), _p(out[1]), _p(out[2]), _p(n_evals), _p(ws), ws.numel(), _stream(stream)))
     return out
 
 
