@@ -245,33 +245,42 @@ def main():
     tr_grid, tr_search = tr_out(), tr_out()
     stream = torch.cuda.current_stream(dev)
 
+    srt = torch.empty_like(hits)
+    boxes = torch.empty((rt.lib.retina_prepare_hits_box_count(H, 1), 8), dtype=torch.float32, device=dev)
+
     def step(evs=None):
+        # S0: spatial order + block boxes; S1-S3: grid response, maxima,
+        # extraction; S4-S6: persistent truncated-Newton search, extraction
         if evs:
             evs[0].record(stream)
-        rt.grid_response(hits, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid)
+        rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes))
         if evs:
             evs[1].record(stream)
+        rt.grid_response(srt, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid, boxes=boxes)
+        if evs:
+            evs[2].record(stream)
         rt.grid_maxima(Rg, grid, R0, K_MAX, out=mx, ws=ws_max)
         rt.extract_tracks(mx["max_theta"], mx["max_R"], None, grid, R0, wl.merge_cells, K_TR,
                           n_valid=mx["n_max"], out=tr_grid)
         if evs:
-            evs[2].record(stream)
-        rt.batched_search(hits, offs, wl.model, seeds, seed_offs, opts, grid, out=ls_out, n_evals=n_evals,
-                          ws=ws_search)
-        if evs:
             evs[3].record(stream)
+        rt.batched_search(srt, offs, wl.model, seeds, seed_offs, opts, grid, out=ls_out, n_evals=n_evals,
+                          ws=ws_search, boxes=boxes)
+        if evs:
+            evs[4].record(stream)
         rt.extract_tracks(ls_out[0].view(1, -1, 2), ls_out[1].view(1, -1), ls_out[2].view(1, -1), grid, R0,
                           wl.merge_cells, K_TR, out=tr_search)
         if evs:
-            evs[4].record(stream)
+            evs[5].record(stream)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # ---- launch shapes picked by the autotuner on this workload and GPU
     tuned = None
     if not args.no_tune:
-        tuned = {"grid": tune.tune_grid(hits, offs, wl.model, grid, wl.sigma_grid),
-                 "search": tune.tune_batched_search(hits, offs, wl.model, seeds, seed_offs, opts, grid)}
+        rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes))
+        tuned = {"grid": tune.tune_grid(srt, offs, wl.model, grid, wl.sigma_grid, boxes=boxes),
+                 "search": tune.tune_batched_search(srt, offs, wl.model, seeds, seed_offs, opts, grid, boxes=boxes)}
 
     # ---- peaks of the FP32 and MUFU pipes, measured live (burst)
     peaks = {}
@@ -297,7 +306,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     clocks = ClockSampler(local_rank) if not args.no_clocks else None
     if world > 1:
         dist.barrier()
@@ -317,9 +326,10 @@ def main():
         dist.barrier()
     clk = clocks.stop() if clocks else None
 
-    stage = np.zeros((args.steps, 4))
+    NST = 5
+    stage = np.zeros((args.steps, NST))
     for k in range(args.steps):
-        for j in range(4):
+        for j in range(NST):
             stage[k, j] = evs[k][j].elapsed_time(evs[k][j + 1])
     step_ms = stage.sum(axis=1)
     total_ms = float(step_ms.sum())
@@ -330,18 +340,25 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms * 1e-3)
 
-    # ---- algorithmic work of the two response kernels
+    # ---- work the two response kernels perform (counted on the device in
+    # one extra step outside the timed region; exact block skipping means
+    # fewer pairs than cells x hits / seeds x hits)
+    rt.work_counters(enable=True, reset=True)
+    step()
+    torch.cuda.synchronize()
+    work = rt.work_counters(enable=False)
     n_ev = n_evals.to(torch.int64).sum().item()
     cells = n0 * n1
-    grid_pairs = cells * H
-    rgh_pairs = wl.n_seeds * len(wl.sigma_schedule) * H
-    r_pairs = n_ev * H
-    grid_ms = float(np.mean(stage[:, 0]))
-    search_ms = float(np.mean(stage[:, 2]))
-    # grid contraction: one FP32 FMA (2 flops) per (cell, hit) pair
+    grid_pairs_all = cells * H                     # every (cell, hit) pair of Eq. 2
+    grid_pairs = work[rt.WORK_GRID]                # pairs in blocks not skipped
+    rgh_pairs, r_pairs = work[rt.WORK_RGH], work[rt.WORK_R]
+    prep_ms = float(np.mean(stage[:, 0]))
+    grid_ms = float(np.mean(stage[:, 1]))
+    search_ms = float(np.mean(stage[:, 3]))
+    # grid contraction: one FP32 FMA (2 flops) per evaluated (cell, hit) pair
     grid_tflops = 2.0 * grid_pairs / (grid_ms * 1e-3) / 1e12
-    # local search: 16 FP32 ops + 1 ex2 per (seed, hit) in a gradient/Hessian
-    # pass, 6 FP32 ops + 1 ex2 in an R-only pass (counts from the kernel source)
+    # search: 16 FP32 ops + 1 ex2 per (seed, hit) pair of a gradient/Hessian
+    # pass, 6 FP32 ops + 1 ex2 per pair of an R pass (from the kernel source)
     search_fp32_ops = 16.0 * rgh_pairs + 6.0 * r_pairs
     search_ex2 = rgh_pairs + r_pairs
     search_fp32_rate = search_fp32_ops / (search_ms * 1e-3)
@@ -351,16 +368,17 @@ def main():
     roof_grid = {"kernel": "grid_sep_kernel (+ slice reduction)", "bound": "alu", "unit": "TFLOP/s",
                  "achieved": grid_tflops, "peak": fma_peak_tflops,
                  "frac": (grid_tflops / fma_peak_tflops) if fma_peak_tflops else None,
-                 "traffic": None, "pairs_per_s": grid_pairs / (grid_ms * 1e-3),
+                 "traffic": None, "pairs_evaluated": grid_pairs, "pairs_total": grid_pairs_all,
+                 "effective_pairs_per_s": grid_pairs_all / (grid_ms * 1e-3),
                  "peak_source": "FP32 FMA rate measured live by retina_alu_probe (burst; the faster of FFMA and "
                                 "packed FFMA2)"}
-    # the search's bound: FP32 issue vs ex2 pipe, whichever is closer to its peak
-    fr_fp32 = (search_fp32_rate / (2 * fma_rate) if fma_rate else None)  # ops vs FMA-pipe ops (1 op per lane slot)
+    fr_fp32 = (search_fp32_rate / (2 * fma_rate) if fma_rate else None)  # vs lane-ops/s (an FMA counts once)
     fr_ex2 = (search_ex2_rate / ex2_peak) if ex2_peak else None
     roof_search = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Gpair/s",
                    "achieved": (rgh_pairs + r_pairs) / (search_ms * 1e-3) / 1e9,
                    "fp32_ops_per_s": search_fp32_rate, "ex2_per_s": search_ex2_rate,
                    "frac_fp32": fr_fp32, "frac_ex2": fr_ex2, "rgh_pairs": rgh_pairs, "r_pairs": r_pairs,
+                   "pairs_total": (wl.n_seeds * len(wl.sigma_schedule) + n_ev) * H,
                    "traffic": None}
     dominant = "grid" if grid_ms >= search_ms else "search"
     roofline = roof_grid if dominant == "grid" else dict(roof_search, frac=max(x for x in (fr_fp32, fr_ex2) if x),
@@ -416,10 +434,11 @@ def main():
             "config": workload_config(wl, H),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "roofline_other": roof_search if dominant == "grid" else roof_grid,
-            "stages_ms": {"grid_response": grid_ms, "grid_maxima_extract": float(np.mean(stage[:, 1])),
-                          "local_search": search_ms, "search_extract": float(np.mean(stage[:, 3]))},
-            "methods_events_per_s": {"grid_scan": 1e3 / (grid_ms + float(np.mean(stage[:, 1]))),
-                                     "local_search": 1e3 / (search_ms + float(np.mean(stage[:, 3])))},
+            "stages_ms": {"prepare_hits": prep_ms, "grid_response": grid_ms,
+                          "grid_maxima_extract": float(np.mean(stage[:, 2])), "local_search": search_ms,
+                          "search_extract": float(np.mean(stage[:, 4]))},
+            "methods_events_per_s": {"grid_scan": 1e3 / (prep_ms + grid_ms + float(np.mean(stage[:, 2]))),
+                                     "local_search": 1e3 / (prep_ms + search_ms + float(np.mean(stage[:, 4])))},
             "tracks_found": {"grid": tr_n[0], "search": tr_n[1]},
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},

@@ -35,6 +35,11 @@
  *   (event_offsets: int64 [n_events + 1], non-decreasing, device memory).
  *   Kernels clamp every offset to [0, n_hits] and treat a decreasing pair as
  *   an empty event, so malformed offsets cannot make them read outside hits.
+ *   boxes: nullable; when given, hits must be the output of
+ *   retina_prepare_hits (each event's hits in its spatial order) and boxes
+ *   its block boxes.  The kernels then skip, per point or per tile, every
+ *   block of 32 hits whose terms of Eq. 1 are all exactly zero in float32,
+ *   so the results are bitwise those of evaluating every hit in that order.
  *   Row layout per model:
  *     RETINA_TOY2D       (x, y, -, -): 2D line y = theta0 * x + theta1 seen by
  *                        detector planes x = const; s = y - theta0 x - theta1
@@ -118,6 +123,22 @@ int retina_get_option(int32_t option, int32_t *value);
  * library's launches in it.  Not part of the paper: instrumentation. */
 uint64_t retina_launch_count(void);
 
+/* Work counters (instrumentation, not part of the paper): when enabled, the
+ * response kernels add the (point or cell, hit) pairs they evaluate, after
+ * block skipping, to device counters:
+ *   [RETINA_WORK_GRID] grid response pairs, [RETINA_WORK_RGH] search pairs of
+ *   R/grad/Hess passes, [RETINA_WORK_R] search pairs of R-only passes.
+ * retina_work_counters(enable, reset, out): enable = 1 / 0 switches counting
+ * on / off for later launches (-1 leaves it), reset = 1 zeroes the counters,
+ * out (nullable, host, RETINA_WORK_KINDS entries) receives their values.
+ * Reset and read are synchronous device copies; counting costs one atomic per
+ * CTA or warp. */
+#define RETINA_WORK_KINDS 4
+#define RETINA_WORK_GRID 0
+#define RETINA_WORK_RGH 1
+#define RETINA_WORK_R 2
+int retina_work_counters(int32_t enable, int32_t reset, uint64_t *out);
+
 /*
  * retina_alu_probe - throughput probe of the arithmetic pipes the retina
  * kernels use (not part of the paper; it supplies the FP32 / SFU peaks of
@@ -134,6 +155,26 @@ uint64_t retina_launch_count(void);
  */
 int64_t retina_alu_probe_sink_floats(void);
 int retina_alu_probe(int32_t kind, int32_t iters, float *sink, double *ops, void *stream);
+
+/*
+ * retina_prepare_hits - spatial order and block boxes for exact skipping.
+ *
+ * Not a step of the paper: an acceleration structure for Eq. 1.  Per event,
+ * sorts the hits into a spatial order and writes them to sorted_out
+ * (float32 [n_hits][4], same event offsets); block b of event e (sorted hits
+ * 32 b .. 32 b + 31) gets an 8-float box in boxes_out row
+ * floor(event_offsets[e] / 32) + e + b.  Slope model: hits ordered by |z|
+ * octave, then Morton order of their slopes (x/z, y/z); box = (min, max of
+ * x/z, min, max of y/z, min, max of |z|, 0, 0).  2D toy: ordered by x band,
+ * then y; box = (xmin, xmax, ymin, ymax, 0, 0, 0, 0).  boxes_out: float32
+ * [retina_prepare_hits_box_count(n_hits, n_events)][8].  A box with a
+ * non-finite value (e.g. a hit at z = 0) is infinite: never skipped.  The
+ * order of hits within an event does not change R beyond float32 summation
+ * order.
+ */
+int64_t retina_prepare_hits_box_count(int64_t n_hits, int32_t n_events);
+int retina_prepare_hits(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                        int32_t model, float *sorted_out, float *boxes_out, void *stream);
 
 /*
  * retina_grid_scan - response on a grid of units and its local maxima.
@@ -164,7 +205,7 @@ int retina_alu_probe(int32_t kind, int32_t iters, float *sink, double *ops, void
  */
 int retina_grid_scan_workspace_size(int32_t n_events, int32_t model, const retina_grid *g, int32_t flags,
                                     int32_t store_R, size_t *bytes);
-int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
+int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events, int32_t model,
                      const retina_grid *g, float sigma, float R0, int32_t flags, float *R_out, int32_t *max_idx,
                      float *max_theta, float *max_R, int32_t *n_max, int32_t K, void *ws, size_t ws_bytes,
                      void *stream);
@@ -176,7 +217,7 @@ int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_off
  */
 int retina_grid_response_workspace_size(int32_t n_events, int32_t model, const retina_grid *g, int32_t flags,
                                         size_t *bytes);
-int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events,
                          int32_t model, const retina_grid *g, float sigma, int32_t flags, float *R_out, void *ws,
                          size_t ws_bytes, void *stream);
 
@@ -271,7 +312,7 @@ int retina_response(const float *hits, int64_t n_hits, const int64_t *event_offs
  *               work, in units of the paper's T0 (R_out needs no extra pass:
  *               it is the accepted trial's response, or the last pass's R).
  */
-int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
+int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events, int32_t model,
                         const float *seeds, int32_t n_seeds, const retina_ls_opts *opts, const retina_grid *box,
                         float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, void *stream);
 
@@ -299,7 +340,7 @@ int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_
  *                 `stream` before the kernel (both are stream operations).
  */
 int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes);
-int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events,
                           int32_t model, const float *seeds, int64_t n_seeds, const int64_t *seed_offsets,
                           const int32_t *order, const retina_ls_opts *opts, const retina_grid *box, float *theta_out,
                           float *R_out, uint8_t *status, uint8_t *n_evals, void *ws, size_t ws_bytes, void *stream);

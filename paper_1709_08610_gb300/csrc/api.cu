@@ -130,7 +130,7 @@ int retina_grid_scan_workspace_size(int32_t n_events, int32_t model, const retin
     return RETINA_OK;
 }
 
-int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events, int32_t model,
+int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events, int32_t model,
                      const retina_grid *g, float sigma, float R0, int32_t flags, float *R_out, int32_t *max_idx,
                      float *max_theta, float *max_R, int32_t *n_max, int32_t K, void *ws, size_t ws_bytes,
                      void *stream) {
@@ -152,8 +152,9 @@ int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_off
     float *partials = (float *)(base + w.part_off);
     int32_t *mws = (int32_t *)(base + w.max_off);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t err = launch_grid_response(p, (const float4 *)hits, n_hits, event_offsets, n_events, model, g, sigma,
-                                           R, partials, st);
+    if (boxes && !aligned16(boxes)) return RETINA_EINVAL;
+    cudaError_t err = launch_grid_response(p, (const float4 *)hits, n_hits, event_offsets, (const float4 *)boxes,
+                                           n_events, model, g, sigma, R, partials, st);
     if (err != cudaSuccess) return RETINA_ECUDA;
     return cuda_status(launch_grid_maxima(R, n_events, g, R0, max_idx, max_theta, max_R, n_max, K, mws, st));
 }
@@ -169,7 +170,7 @@ int retina_grid_response_workspace_size(int32_t n_events, int32_t model, const r
     return RETINA_OK;
 }
 
-int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events,
                          int32_t model, const retina_grid *g, float sigma, int32_t flags, float *R_out, void *ws,
                          size_t ws_bytes, void *stream) {
     if (n_events < 0 || n_hits < 0 || !valid_grid(g) || !finite_pos(sigma)) return RETINA_EINVAL;
@@ -183,8 +184,26 @@ int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event
     const size_t need = round_up(grid_partials_bytes(p, n_events, g), 256);
     if (ws_bytes < need) return RETINA_ENOSPACE;
     if (need > 0 && (!ws || ((uintptr_t)ws & 255u))) return RETINA_EINVAL;
-    return cuda_status(launch_grid_response(p, (const float4 *)hits, n_hits, event_offsets, n_events, model, g, sigma,
-                                            R_out, (float *)ws, (cudaStream_t)stream));
+    if (boxes && !aligned16(boxes)) return RETINA_EINVAL;
+    return cuda_status(launch_grid_response(p, (const float4 *)hits, n_hits, event_offsets, (const float4 *)boxes,
+                                            n_events, model, g, sigma, R_out, (float *)ws, (cudaStream_t)stream));
+}
+
+int64_t retina_prepare_hits_box_count(int64_t n_hits, int32_t n_events) {
+    if (n_hits < 0 || n_events < 0) return -1;
+    return prepared_box_count(n_hits, n_events);
+}
+
+int retina_prepare_hits(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                        int32_t model, float *sorted_out, float *boxes_out, void *stream) {
+    if (n_events < 0 || n_hits < 0) return RETINA_EINVAL;
+    if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (n_events == 0) return RETINA_OK;
+    if (!event_offsets || !boxes_out || !aligned16(boxes_out)) return RETINA_EINVAL;
+    if (n_hits > 0 && (!hits || !sorted_out || !aligned16(hits) || !aligned16(sorted_out))) return RETINA_EINVAL;
+    if (n_hits > 0 && hits == sorted_out) return RETINA_EINVAL;  // not in place
+    return cuda_status(launch_prepare_hits((const float4 *)hits, n_hits, event_offsets, n_events, model,
+                                           (float4 *)sorted_out, (float4 *)boxes_out, (cudaStream_t)stream));
 }
 
 uint64_t retina_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
@@ -220,7 +239,7 @@ int retina_response(const float *hits, int64_t n_hits, const int64_t *event_offs
                                        sigma, want_derivs != 0, out, (cudaStream_t)stream));
 }
 
-int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events,
                         int32_t model, const float *seeds, int32_t n_seeds, const retina_ls_opts *opts,
                         const retina_grid *box, float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals,
                         void *stream) {
@@ -236,7 +255,9 @@ int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_
     if (n_events == 0 || n_seeds == 0) return RETINA_OK;
     if (!event_offsets || !seeds || !theta_out || !R_out || !status) return RETINA_EINVAL;
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
-    return cuda_status(launch_local_search((const float4 *)hits, n_hits, event_offsets, n_events, model, seeds,
+    if (boxes && !aligned16(boxes)) return RETINA_EINVAL;
+    return cuda_status(launch_local_search((const float4 *)hits, n_hits, event_offsets, (const float4 *)boxes,
+                                           n_events, model, seeds,
                                            n_seeds, opts, box, theta_out, R_out, status, n_evals, g_opt_seeds_per_warp,
                                            g_opt_ls_warps, g_opt_smem_hits, (cudaStream_t)stream));
 }
@@ -247,7 +268,7 @@ int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes) {
     return RETINA_OK;
 }
 
-int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events,
                           int32_t model, const float *seeds, int64_t n_seeds, const int64_t *seed_offsets,
                           const int32_t *order, const retina_ls_opts *opts, const retina_grid *box, float *theta_out,
                           float *R_out, uint8_t *status, uint8_t *n_evals, void *ws, size_t ws_bytes, void *stream) {
@@ -265,7 +286,9 @@ int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *even
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
     if (ws_bytes < batched_ws_bytes(n_events)) return RETINA_ENOSPACE;
     if (!ws || ((uintptr_t)ws & 255u)) return RETINA_EINVAL;
-    return cuda_status(launch_batched_search((const float4 *)hits, n_hits, event_offsets, n_events, model, seeds,
+    if (boxes && !aligned16(boxes)) return RETINA_EINVAL;
+    return cuda_status(launch_batched_search((const float4 *)hits, n_hits, event_offsets, (const float4 *)boxes,
+                                             n_events, model, seeds,
                                              n_seeds, seed_offsets, order, opts, box, theta_out, R_out, status,
                                              n_evals, (int32_t *)ws, g_opt_batch_spw, g_opt_batch_warps,
                                              g_opt_batch_smem_hits, (cudaStream_t)stream));

@@ -20,6 +20,7 @@ struct BatchArgs {
     const float4 *hits;
     int64_t n_hits;
     const int64_t *hit_off;
+    const float4 *boxes;
     int n_events;
     const float *seeds;
     int64_t n_seeds;
@@ -32,6 +33,7 @@ struct BatchArgs {
     uint8_t *status;
     uint8_t *n_evals;
     int32_t *counters;  // [0] event ticket, [1] overrun flag, [2 + e] group counter of event e
+    unsigned long long *work;
 };
 
 __device__ __forceinline__ void seed_range(const BatchArgs &a, int e, int64_t &s0, int64_t &s1) {
@@ -49,13 +51,15 @@ __device__ __forceinline__ int64_t n_groups_of(const BatchArgs &a, int e) {
     return (s1 - s0 + P - 1) / P;
 }
 
+// at most 64 registers per thread: 2048 / (32 WARPS) CTAs of WARPS warps fit the register file
 template <int MODEL, int P, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) batched_search_kernel(BatchArgs a, LsParams prm) {
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(BatchArgs a, LsParams prm) {
     extern __shared__ float4 sh[];
     __shared__ int cur_e;
     const int tid = threadIdx.x, lane = tid & 31;
+    float4 *sbox = sh + a.smem_hits;
     int staged = -1;
-    int n_staged = 0;
+    int n_staged = 0, n_sbox = 0;
     for (int64_t round = 0; round < a.max_rounds; ++round) {
         // ---- pick an event: the next unclaimed one, else one still in progress
         if (tid == 0) {
@@ -90,9 +94,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1) batched_search_kernel(BatchArgs
         seed_range(a, e, s0, s1);
         const int H = (int)(he - hb);
         const float4 *gh = a.hits + hb;
+        const float4 *gbox = a.boxes ? a.boxes + 2 * (hb / 32 + e) : nullptr;
         if (e != staged) {
             n_staged = H < a.smem_hits ? H : a.smem_hits;
             for (int k = tid; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
+            const int nblk = (H + 31) >> 5, cap = box_capacity(a.smem_hits);
+            n_sbox = gbox ? (nblk < cap ? nblk : cap) : 0;
+            for (int k = tid; k < 2 * n_sbox; k += blockDim.x) sbox[k] = __ldg(gbox + k);
             staged = e;
         }
         __syncthreads();
@@ -104,8 +112,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) batched_search_kernel(BatchArgs
             if (g >= groups) break;
             const int64_t s = s0 + (int64_t)g * P;
             const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
-            search_group<MODEL, P>(sh, gh, n_staged, H, lane, a.seeds + 2 * s, n_live, prm, a.theta_out + 2 * s,
-                                   a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr);
+            search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, a.seeds + 2 * s, n_live, prm,
+                                   a.theta_out + 2 * s,
+                                   a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work);
         }
         __syncthreads();  // all warps done with the staged hits before the next round
         if (round + 1 == a.max_rounds && tid == 0) atomicExch(&a.counters[1], 1);
@@ -117,13 +126,9 @@ size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(
 template <int MODEL, int P, int WARPS>
 static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, cudaStream_t st) {
     auto kern = batched_search_kernel<MODEL, P, WARPS>;
-    const size_t smem = (size_t)a.smem_hits * sizeof(float4);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (err != cudaSuccess) return err;
-        configured = true;
-    }
+    const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr);
+    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+    if (aerr != cudaSuccess) return aerr;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
     if (err != cudaSuccess) return err;
@@ -141,7 +146,8 @@ static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParam
     return launch_batched_t<MODEL, P, 8>(a, prm, st);
 }
 
-cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, int n_events, int model,
+cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
+                                  int n_events, int model,
                                   const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
                                   const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
                                   uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
@@ -149,8 +155,8 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
     LsParams prm = make_ls_params(o, box);
     if (smem_hits < 0) smem_hits = 0;
     if (smem_hits > 12288) smem_hits = 12288;
-    BatchArgs a{hits, n_hits, hit_off, n_events, seeds, n_seeds, seed_off, order, smem_hits,
-                (int64_t)n_events + n_seeds + 2, theta_out, R_out, status, n_evals, counters};
+    BatchArgs a{hits, n_hits, hit_off, boxes, n_events, seeds, n_seeds, seed_off, order, smem_hits,
+                (int64_t)n_events + n_seeds + 2, theta_out, R_out, status, n_evals, counters, work_counters()};
     cudaError_t err = cudaMemsetAsync(counters, 0, batched_ws_bytes(n_events), st);
     if (err != cudaSuccess) return err;
 #define RETINA_BATCH_CASE(M, PP) return launch_batched_w<M, PP>(warps, a, prm, st)

@@ -230,12 +230,10 @@ cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint
                                   int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
                                   float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
                                   cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(extract_tracks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)extract_smem_bytes(RETINA_MAX_EXTRACT_POINTS));
-        if (err != cudaSuccess) return err;
-        configured = true;
+    {
+        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(extract_tracks_kernel),
+                                               extract_smem_bytes(n_points));
+        if (aerr != cudaSuccess) return aerr;
     }
     ExtractParams prm;
     prm.lo0 = box->lo[0];

@@ -40,12 +40,70 @@ __device__ __forceinline__ void slice_range(const int64_t *off, int64_t n_hits, 
     k1 = k0 + per < he ? k0 + per : he;
 }
 
+// Exact skipping of hit blocks for a whole tile of cells (boxes from
+// retina_prepare_hits): the lower bound, over the tile's parameter range and
+// the block's box, of the exponent s^2 log2(e) / sigma^2 (or of one axis's
+// part of it for the separable panels) must exceed GRID_CULL_EXPONENT, so
+// that every skipped ex2.approx.ftz value is exactly zero (x > 126; 140
+// leaves a margin, and a relative slack of 1e-6 per magnitude covers the
+// rounding of the bound).  Non-finite boxes are never skipped.
+constexpr float GRID_CULL_EXPONENT = 140.f;
+
+// Distance between the intervals [al, ah] and [bl, bh], minus a rounding
+// slack of 1e-6 per magnitude; 0 when they overlap.
+__device__ __forceinline__ float gap_ii(float al, float ah, float bl, float bh) {
+    const float d = fmaxf(fmaxf(bl - ah, al - bh), 0.f);
+    return fmaxf(d - 1e-6f * (fabsf(al) + fabsf(ah) + fabsf(bl) + fabsf(bh)), 0.f);
+}
+
+struct TileRange {
+    float t0l, t0h, t1l, t1h;  // cell-centre range of the tile's valid cells
+};
+
+__device__ __forceinline__ TileRange tile_range(const GridDev &g, int ti0, int tj0, int w0, int w1) {
+    const int i1 = (ti0 + w0 - 1 < g.n0 - 1) ? ti0 + w0 - 1 : g.n0 - 1;
+    const int j1 = (tj0 + w1 - 1 < g.n1 - 1) ? tj0 + w1 - 1 : g.n1 - 1;
+    return TileRange{cell_centre(g.lo0, g.step0, ti0), cell_centre(g.lo0, g.step0, i1),
+                     cell_centre(g.lo1, g.step1, tj0), cell_centre(g.lo1, g.step1, j1)};
+}
+
+// Slope-model boxes (umin, umax, vmin, vmax | |z|min, |z|max): for every
+// cell of the tile and hit of the block, (x - t_x z)^2 = z^2 (u - t_x)^2 >=
+// |z|min^2 gap(t_x range, u range)^2, likewise for y.  Separable panels are
+// all zero when either axis alone exceeds the cut.
+__device__ __forceinline__ bool block_zero_sep(const float4 A, const float4 B, const TileRange &r, float kk) {
+    if (!isfinite(B.x)) return false;
+    const float du = gap_ii(r.t0l, r.t0h, A.x, A.y), dv = gap_ii(r.t1l, r.t1h, A.z, A.w);
+    const float z2k = B.x * B.x * kk;
+    return du * du * z2k > GRID_CULL_EXPONENT || dv * dv * z2k > GRID_CULL_EXPONENT;
+}
+
+template <int MODEL>
+__device__ __forceinline__ bool block_zero_direct(const float4 A, const float4 B, const TileRange &r, float kk) {
+    if (!isfinite(B.x)) return false;
+    if (MODEL == RETINA_VELO_SLOPES) {
+        const float du = gap_ii(r.t0l, r.t0h, A.x, A.y), dv = gap_ii(r.t1l, r.t1h, A.z, A.w);
+        return (du * du + dv * dv) * (B.x * B.x) * kk > GRID_CULL_EXPONENT;
+    }
+    // 2D toy, box (xmin, xmax, ymin, ymax): r = y - alpha x - beta with alpha
+    // in [t0l, t0h] and beta in [t1l, t1h], by interval arithmetic
+    const float p0 = r.t0l * A.x, p1 = r.t0l * A.y, p2 = r.t0h * A.x, p3 = r.t0h * A.y;
+    const float pmin = fminf(fminf(p0, p1), fminf(p2, p3)), pmax = fmaxf(fmaxf(p0, p1), fmaxf(p2, p3));
+    const float lo = A.z - pmax - r.t1h, hi = A.w - pmin - r.t1l;
+    const float d = fmaxf(fmaxf(lo, -hi), 0.f);
+    const float slack = 1e-6f * (fabsf(A.z) + fabsf(A.w) + fabsf(pmin) + fabsf(pmax) + fabsf(r.t1l) + fabsf(r.t1h));
+    const float dd = fmaxf(d - slack, 0.f);
+    return dd * dd * kk > GRID_CULL_EXPONENT;
+}
+
 __global__ void __launch_bounds__(SEP_THREADS, 2)
-grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, GridDev g, float kk,
-                int splits,
-                int tiles0, float *__restrict__ out, int64_t split_stride, int64_t event_stride) {
+grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
+                const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0,
+                float *__restrict__ out, int64_t split_stride, int64_t event_stride,
+                unsigned long long *__restrict__ work) {
     __shared__ __align__(16) float sA[SEP_BK][SEP_BM];
     __shared__ __align__(16) float sB[SEP_BK][SEP_BN];
+    __shared__ unsigned keep_mask[SEP_THREADS / 32];
     const int e = blockIdx.z, s = blockIdx.y;
     const int ti0 = (blockIdx.x % tiles0) * SEP_BM;
     const int tj0 = (blockIdx.x / tiles0) * SEP_BN;
@@ -66,39 +124,69 @@ grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 
-    for (int64_t kb = k0; kb < k1; kb += SEP_BK) {
-        __syncthreads();
-#pragma unroll 4
-        for (int m = 0; m < SEP_BK / 2; ++m) {
-            const int kc = hpar + 2 * m;
-            const int64_t k = kb + kc;
-            float va = 0.f, vb = 0.f;
-            if (k < k1) {
-                const float4 h = __ldg(hits + k);
-                const float u = __fmaf_rn(-t0, h.z, h.x);  // x - t_x z, one rounding
-                const float v = __fmaf_rn(-t1, h.z, h.y);  // y - t_y z
-                va = ex2_mufu(-(u * u) * kk);
-                vb = ex2_mufu(-(v * v) * kk);
-            }
-            sA[kc][ci] = va;
-            sB[kc][ci] = vb;
+    // blocks of this slice that can contribute to this tile, 256 at a time
+    int64_t hb, he;
+    event_range(off, n_hits, e, hb, he);
+    const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
+    const TileRange tr = tile_range(g, ti0, tj0, SEP_BM, SEP_BN);
+    const int64_t n_chunks = (k1 - k0 + SEP_BK - 1) / SEP_BK;
+    const int64_t b_first = (k0 - hb) / SEP_BK;
+    int64_t done_hits = 0;
+    for (int64_t cb = 0; cb < n_chunks; cb += SEP_THREADS) {
+        const int64_t c = cb + t;
+        bool keep = c < n_chunks;
+        if (keep && gbox) {
+            const float4 A = __ldg(gbox + 2 * (b_first + c)), B = __ldg(gbox + 2 * (b_first + c) + 1);
+            keep = !block_zero_sep(A, B, tr, kk);
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncthreads();  // previous window's masks are no longer read
+        if ((t & 31) == 0) keep_mask[t >> 5] = bal;
         __syncthreads();
+        for (int w = 0; w < SEP_THREADS / 32; ++w) {
+            unsigned m = keep_mask[w];
+            while (m) {
+                const int64_t kb = k0 + (cb + 32 * w + __ffs(m) - 1) * SEP_BK;
+                m &= m - 1;
+                done_hits += (k1 - kb) < SEP_BK ? (k1 - kb) : SEP_BK;
+                __syncthreads();
+#pragma unroll 4
+                for (int mm = 0; mm < SEP_BK / 2; ++mm) {
+                    const int kc = hpar + 2 * mm;
+                    const int64_t k = kb + kc;
+                    float va = 0.f, vb = 0.f;
+                    if (k < k1) {
+                        const float4 h = __ldg(hits + k);
+                        const float u = __fmaf_rn(-t0, h.z, h.x);  // x - t_x z, one rounding
+                        const float v = __fmaf_rn(-t1, h.z, h.y);  // y - t_y z
+                        va = ex2_mufu(-(u * u) * kk);
+                        vb = ex2_mufu(-(v * v) * kk);
+                    }
+                    sA[kc][ci] = va;
+                    sB[kc][ci] = vb;
+                }
+                __syncthreads();
 #pragma unroll
-        for (int kc = 0; kc < SEP_BK; ++kc) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&sA[kc][tm * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&sA[kc][64 + tm * 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&sB[kc][tn * 4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&sB[kc][64 + tn * 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                for (int kc = 0; kc < SEP_BK; ++kc) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(&sA[kc][tm * 4]);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(&sA[kc][64 + tm * 4]);
+                    const float4 b0 = *reinterpret_cast<const float4 *>(&sB[kc][tn * 4]);
+                    const float4 b1 = *reinterpret_cast<const float4 *>(&sB[kc][64 + tn * 4]);
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+                    for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+                        for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+                }
+            }
         }
     }
 
+    if (work && t == 0 && done_hits > 0) {
+        const int64_t cw = (g.n0 - ti0 < SEP_BM ? g.n0 - ti0 : SEP_BM), ch = (g.n1 - tj0 < SEP_BN ? g.n1 - tj0 : SEP_BN);
+        atomicAdd(work + RETINA_WORK_GRID, (unsigned long long)(done_hits * cw * ch));
+    }
     float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
     const bool vec = (g.n0 % 4) == 0;
 #pragma unroll
@@ -125,17 +213,24 @@ grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
 
 template <int MODEL>
 __global__ void __launch_bounds__(DIR_THREADS)
-grid_direct_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, GridDev g,
-                   float kk, float sk,
-                   int splits, int tiles0, float *__restrict__ out, int64_t split_stride, int64_t event_stride) {
+grid_direct_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
+                   const float4 *__restrict__ boxes, GridDev g, float kk, float sk, int splits, int tiles0,
+                   float *__restrict__ out, int64_t split_stride, int64_t event_stride,
+                   unsigned long long *__restrict__ work) {
     __shared__ float4 sh[DIR_CHUNK];
+    __shared__ int blk_list[DIR_CHUNK / 32];
+    __shared__ int blk_count;
     const int e = blockIdx.z, s = blockIdx.y;
     const int ti0 = (blockIdx.x % tiles0) * DIR_TILE;
     const int tj0 = (blockIdx.x / tiles0) * DIR_TILE;
     int64_t k0, k1;
-    slice_range(off, n_hits, e, s, splits, 1, k0, k1);
+    slice_range(off, n_hits, e, s, splits, 32, k0, k1);
     const int t = threadIdx.x;
     const int tx = t & 15, ty = t >> 4;
+    int64_t hb, he;
+    event_range(off, n_hits, e, hb, he);
+    const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
+    const TileRange tr = tile_range(g, ti0, tj0, DIR_TILE, DIR_TILE);
     float c0[4], c1[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -149,9 +244,34 @@ grid_direct_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
 
     for (int64_t kb = k0; kb < k1; kb += DIR_CHUNK) {
-        const int n = (int)((k1 - kb) < DIR_CHUNK ? (k1 - kb) : DIR_CHUNK);
+        const int span = (int)((k1 - kb) < DIR_CHUNK ? (k1 - kb) : DIR_CHUNK);
+        const int nb = (span + 31) / 32;
         __syncthreads();
-        for (int i = t; i < n; i += DIR_THREADS) sh[i] = __ldg(hits + kb + i);
+        if (t < 32) {  // ordered list of the chunk's blocks that can contribute
+            bool keep = t < nb;
+            if (keep && gbox) {
+                const int64_t b = (kb - hb) / 32 + t;
+                keep = !block_zero_direct<MODEL>(__ldg(gbox + 2 * b), __ldg(gbox + 2 * b + 1), tr, kk);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) blk_list[__popc(bal & ((1u << t) - 1u))] = t;
+            if (t == 0) blk_count = __popc(bal);
+        }
+        __syncthreads();
+        const int nk = blk_count;
+        int n = 0;
+        int64_t done_hits = 0;
+        for (int q = 0; q < nk; ++q) {  // gather the kept blocks' hits, in order
+            const int b = blk_list[q];
+            const int len = (span - 32 * b) < 32 ? (span - 32 * b) : 32;
+            for (int i = t; i < len; i += DIR_THREADS) sh[n + i] = __ldg(hits + kb + 32 * b + i);
+            n += len;
+        }
+        done_hits += n;
+        if (work && t == 0 && n > 0) {
+            const int64_t cw = (g.n0 - ti0 < DIR_TILE ? g.n0 - ti0 : DIR_TILE), ch = (g.n1 - tj0 < DIR_TILE ? g.n1 - tj0 : DIR_TILE);
+            atomicAdd(work + RETINA_WORK_GRID, (unsigned long long)(n * cw * ch));
+        }
         __syncthreads();
         for (int i = 0; i < n; ++i) {
             const float4 h = sh[i];
@@ -208,17 +328,6 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
 // launchers
 // ---------------------------------------------------------------------------
 
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
 GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int forced_splits) {
     GridPlan p;
     p.separable = (model == RETINA_VELO_SLOPES) && (flags != RETINA_GRID_DIRECT);
@@ -241,7 +350,7 @@ size_t grid_partials_bytes(const GridPlan &p, int n_events, const retina_grid *g
 }
 
 cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t n_hits, const int64_t *off,
-                                 int n_events, int model,
+                                 const float4 *boxes, int n_events, int model,
                                  const retina_grid *g, float sigma, float *R, float *partials, cudaStream_t st) {
     GridDev gd{g->lo[0], g->lo[1], g->step[0], g->step[1], g->n[0], g->n[1]};
     const double kkd = kLog2e / ((double)sigma * (double)sigma);
@@ -252,13 +361,16 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
     const int64_t split_stride = cells * n_events;
     dim3 grid(p.tiles0 * p.tiles1, p.splits, n_events);
     if (p.separable) {
-        grid_sep_kernel<<<grid, SEP_THREADS, 0, st>>>(hits, n_hits, off, gd, kk, p.splits, p.tiles0, dst, split_stride, cells);
+        grid_sep_kernel<<<grid, SEP_THREADS, 0, st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst, split_stride, cells,
+                                                      work_counters());
     } else if (model == RETINA_VELO_SLOPES) {
         grid_direct_kernel<RETINA_VELO_SLOPES>
-            <<<grid, DIR_THREADS, 0, st>>>(hits, n_hits, off, gd, kk, sk, p.splits, p.tiles0, dst, split_stride, cells);
+            <<<grid, DIR_THREADS, 0, st>>>(hits, n_hits, off, boxes, gd, kk, sk, p.splits, p.tiles0, dst, split_stride,
+                                                        cells, work_counters());
     } else {
         grid_direct_kernel<RETINA_TOY2D>
-            <<<grid, DIR_THREADS, 0, st>>>(hits, n_hits, off, gd, kk, sk, p.splits, p.tiles0, dst, split_stride, cells);
+            <<<grid, DIR_THREADS, 0, st>>>(hits, n_hits, off, boxes, gd, kk, sk, p.splits, p.tiles0, dst, split_stride,
+                                                        cells, work_counters());
     }
     count_launches(1);
     cudaError_t err = cudaGetLastError();

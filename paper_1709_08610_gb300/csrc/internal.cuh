@@ -13,14 +13,14 @@ struct GridPlan {
 GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int forced_splits);
 size_t grid_partials_bytes(const GridPlan &p, int n_events, const retina_grid *g);
 cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t n_hits, const int64_t *off,
-                                 int n_events, int model, const retina_grid *g, float sigma, float *R, float *partials,
+                                 const float4 *boxes, int n_events, int model, const retina_grid *g, float sigma, float *R, float *partials,
                                  cudaStream_t st);
 size_t maxima_ws_bytes(int n_events, const retina_grid *g);
 cudaError_t launch_grid_maxima(const float *R, int n_events, const retina_grid *g, float R0, int32_t *max_idx,
                                float *max_theta, float *max_R, int32_t *n_max, int K, int32_t *ws_counts,
                                cudaStream_t st);
-cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
-                                const float *seeds, int n_seeds, const retina_ls_opts *o, const retina_grid *box,
+cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
+                                int n_events, int model, const float *seeds, int n_seeds, const retina_ls_opts *o, const retina_grid *box,
                                 float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, int seeds_per_warp,
                                 int warps, int smem_hits,
                                 cudaStream_t st);
@@ -32,14 +32,20 @@ cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint
                                   float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
                                   cudaStream_t st);
 
-cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, int n_events, int model,
+cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
+                                  int n_events, int model,
                                   const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
                                   const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
                                   uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
                                   int smem_hits, cudaStream_t st);
 size_t batched_ws_bytes(int n_events);
+int64_t prepared_box_count(int64_t n_hits, int n_events);
+cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
+                                float4 *sorted, float4 *boxes, cudaStream_t st);
 int maxima_blocks(const retina_grid *g);
 int sm_count();
+cudaError_t ensure_dynamic_smem(const void *func, size_t bytes);
+unsigned long long *work_counters();
 void count_launches(int n);
 size_t extract_smem_bytes(int n_points);
 

@@ -10,9 +10,10 @@ namespace retina {
 // the CTA's event (blockIdx.y), staged once.
 template <int MODEL, int P, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int n_seeds,
-                    const float *__restrict__ seeds, LsParams prm, int smem_hits, float *__restrict__ theta_out,
-                    float *__restrict__ R_out, uint8_t *__restrict__ status, uint8_t *__restrict__ n_evals) {
+local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
+                    const float4 *__restrict__ boxes, int n_seeds, const float *__restrict__ seeds, LsParams prm,
+                    int smem_hits, float *__restrict__ theta_out, float *__restrict__ R_out,
+                    uint8_t *__restrict__ status, uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work) {
     extern __shared__ float4 sh[];
     const int e = blockIdx.y;
     int64_t hb, he;
@@ -21,6 +22,10 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     const float4 *gh = hits + hb;
     const int n_staged = H < smem_hits ? H : smem_hits;
     for (int k = threadIdx.x; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
+    float4 *sbox = sh + smem_hits;
+    const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
+    const int n_sbox = gbox ? (((H + 31) >> 5) < box_capacity(smem_hits) ? ((H + 31) >> 5) : box_capacity(smem_hits)) : 0;
+    for (int k = threadIdx.x; k < 2 * n_sbox; k += blockDim.x) sbox[k] = __ldg(gbox + k);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -28,8 +33,8 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     if (s_first >= n_seeds) return;
     const int n_live = n_seeds - s_first < P ? n_seeds - s_first : P;
     const int64_t o = (int64_t)e * n_seeds + s_first;
-    search_group<MODEL, P>(sh, gh, n_staged, H, lane, seeds + 2 * o, n_live, prm, theta_out + 2 * o, R_out + o,
-                           status + o, n_evals ? n_evals + o : nullptr);
+    search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, seeds + 2 * o, n_live, prm, theta_out + 2 * o, R_out + o,
+                           status + o, n_evals ? n_evals + o : nullptr, work);
 }
 
 // R (and optionally grad R, Hess R) at arbitrary points: one warp per point.
@@ -93,50 +98,46 @@ LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box) {
 }
 
 template <int MODEL, int P, int WARPS>
-static cudaError_t launch_ls_t(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int n_seeds,
-                               const float *seeds, const LsParams &prm, int smem_hits, float *theta_out, float *R_out,
-                               uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
-    const size_t smem = (size_t)smem_hits * sizeof(float4);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(local_search_kernel<MODEL, P, WARPS>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (err != cudaSuccess) return err;
-        configured = true;
-    }
+static cudaError_t launch_ls_t(const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
+                               int n_events, int n_seeds, const float *seeds, const LsParams &prm, int smem_hits,
+                               float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
+    const size_t smem = search_smem_bytes(smem_hits, boxes != nullptr);
+    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(local_search_kernel<MODEL, P, WARPS>), smem);
+    if (aerr != cudaSuccess) return aerr;
     const int per_block = WARPS * P;
     dim3 grid((n_seeds + per_block - 1) / per_block, n_events);
-    local_search_kernel<MODEL, P, WARPS><<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, n_seeds, seeds, prm,
+    local_search_kernel<MODEL, P, WARPS><<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, boxes, n_seeds, seeds,
+                                                                          prm,
                                                                           smem_hits, theta_out, R_out, status,
-                                                                          n_evals);
+                                                                          n_evals, work_counters());
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int MODEL, int P>
-static cudaError_t launch_ls_w(int warps, const float4 *hits, int64_t n_hits, const int64_t *off, int n_events,
-                               int n_seeds, const float *seeds, const LsParams &prm, int smem_hits, float *theta_out,
-                               float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
+static cudaError_t launch_ls_w(int warps, const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
+                               int n_events, int n_seeds, const float *seeds, const LsParams &prm, int smem_hits,
+                               float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
     if (warps >= 16)
-        return launch_ls_t<MODEL, P, 16>(hits, n_hits, off, n_events, n_seeds, seeds, prm, smem_hits, theta_out,
-                                         R_out, status, n_evals, st);
+        return launch_ls_t<MODEL, P, 16>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits,
+                                         theta_out, R_out, status, n_evals, st);
     if (warps >= 8)
-        return launch_ls_t<MODEL, P, 8>(hits, n_hits, off, n_events, n_seeds, seeds, prm, smem_hits, theta_out, R_out,
-                                        status, n_evals, st);
-    return launch_ls_t<MODEL, P, 4>(hits, n_hits, off, n_events, n_seeds, seeds, prm, smem_hits, theta_out, R_out,
-                                    status, n_evals, st);
+        return launch_ls_t<MODEL, P, 8>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out,
+                                        R_out, status, n_evals, st);
+    return launch_ls_t<MODEL, P, 4>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out,
+                                    R_out, status, n_evals, st);
 }
 
-cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
-                                const float *seeds, int n_seeds, const retina_ls_opts *o, const retina_grid *box,
+cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
+                                int n_events, int model, const float *seeds, int n_seeds, const retina_ls_opts *o, const retina_grid *box,
                                 float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, int seeds_per_warp,
                                 int warps, int smem_hits, cudaStream_t st) {
     LsParams prm = make_ls_params(o, box);
     if (smem_hits < 0) smem_hits = 0;
     if (smem_hits > 12288) smem_hits = 12288;
 #define RETINA_LS_CASE(M, PP)                                                                                     \
-    return launch_ls_w<M, PP>(warps, hits, n_hits, off, n_events, n_seeds, seeds, prm, smem_hits, theta_out, R_out, \
-                              status, n_evals, st)
+    return launch_ls_w<M, PP>(warps, hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out, \
+                              R_out, status, n_evals, st)
     if (model == RETINA_VELO_SLOPES) {
         if (seeds_per_warp >= 4) RETINA_LS_CASE(RETINA_VELO_SLOPES, 4);
         if (seeds_per_warp == 2) RETINA_LS_CASE(RETINA_VELO_SLOPES, 2);

@@ -1,0 +1,150 @@
+// Spatial ordering of each event's hits plus a bounding box per block of 32,
+// so that the response kernels can skip, exactly, blocks whose every term of
+// Eq. 1 is zero in float32.
+//
+// Per event (one CTA, chunks of up to SORT_CAP hits): each hit gets a 32-bit
+// key and the chunk is bitonic-sorted by (key, original index) in shared
+// memory.  Slope model: the key is a band of |z| (octaves from 16 mm) over a
+// Morton code of the hit's slopes (u, v) = (x/z, y/z), and the box of a
+// block is (umin, umax, vmin, vmax, |z|min, |z|max): since
+// s^2 = z^2 |(u, v) - theta|^2, it bounds s^2 from below by
+// |z|min^2 dist(theta, box)^2.  2D toy: the key is a band of x over the
+// quantised y, and the box is (xmin, xmax, ymin, ymax, 0, 0).
+// The sorted hits are written to the output in place of the event's hits
+// (same CSR offsets); block b of event e (sorted hits 32b .. 32b+31) gets a
+// box at index box_base(e) + b with box_base(e) = floor(offsets[e] / 32) + e,
+// which never overlaps the next event's boxes.  A box holding a non-finite
+// value is made infinite, so it is never skipped.
+#include "internal.cuh"
+
+namespace retina {
+
+constexpr int PREP_THREADS = 1024;
+constexpr int SORT_CAP = 16384;
+
+// Spread the 10 low bits of v to the even bit positions 0, 2, ..., 18.
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t quant10(float v, float lo, float hi) {
+    float t = (v - lo) / (hi - lo);
+    t = isfinite(t) ? fminf(fmaxf(t, 0.f), 1.f) : (t > 0.f ? 1.f : 0.f);
+    return (uint32_t)(t * 1023.f);
+}
+
+__device__ __forceinline__ uint32_t hit_key(const float4 h, int model) {
+    if (model == RETINA_VELO_SLOPES) {
+        const float az = fabsf(h.z);
+        uint32_t band = 0;  // |z| octaves: [0,16), [16,32), ..., [512, inf)
+        for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
+        const uint32_t m = spread10(quant10(h.x / h.z, -1.f, 1.f)) | (spread10(quant10(h.y / h.z, -1.f, 1.f)) << 1);
+        return (band << 20) | (m & 0xfffffu);
+    }
+    const uint32_t band = float_order_key(h.x) >> 20;
+    return (band << 20) | (quant10(h.y, -8.f, 8.f) << 10);
+}
+
+__global__ void __launch_bounds__(PREP_THREADS)
+prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int model,
+                    float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
+    extern __shared__ uint64_t keys[];
+    const int e = blockIdx.x, tid = threadIdx.x;
+    int64_t hb, he;
+    event_range(off, n_hits, e, hb, he);
+    const int64_t H = he - hb;
+    const int64_t box_base = (off[e] < 0 ? 0 : (off[e] > n_hits ? n_hits : off[e])) / 32 + e;
+    for (int64_t c0 = 0; c0 < H; c0 += SORT_CAP) {
+        const int n = (int)((H - c0) < SORT_CAP ? (H - c0) : SORT_CAP);
+        int C = 1;
+        while (C < n) C <<= 1;
+        for (int i = tid; i < C; i += PREP_THREADS)
+            keys[i] = i < n ? (((uint64_t)hit_key(__ldg(hits + hb + c0 + i), model) << 32) | (uint32_t)i) : ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= C; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < C; i += PREP_THREADS) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t a = keys[i], b = keys[ixj];
+                        if ((a > b) == ((i & k) == 0)) {
+                            keys[i] = b;
+                            keys[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < n; i += PREP_THREADS) {
+            const int src = (int)(uint32_t)keys[i];
+            sorted[hb + c0 + i] = __ldg(hits + hb + c0 + src);
+        }
+        __syncthreads();
+        // one warp per block of 32 sorted hits (chunks are multiples of 32 but the last):
+        // lane l reads hit 32 b + l, the warp reduces min / max
+        const int nb = (n + 31) / 32;
+        const int lane = tid & 31;
+        for (int b = tid >> 5; b < nb; b += PREP_THREADS / 32) {
+            const int k = b * 32 + lane;
+            float a = INFINITY, c = INFINITY, w = INFINITY, a2 = -INFINITY, c2 = -INFINITY, w2 = -INFINITY;
+            bool finite = true;
+            if (k < n) {
+                const float4 h = sorted[hb + c0 + k];
+                if (model == RETINA_VELO_SLOPES) {
+                    a = h.x / h.z;  // slopes; z = 0 gives a non-finite box
+                    c = h.y / h.z;
+                    w = fabsf(h.z);
+                } else {
+                    a = h.x;
+                    c = h.y;
+                    w = 0.f;
+                }
+                finite = isfinite(a) && isfinite(c) && isfinite(w);
+                a2 = a;
+                c2 = c;
+                w2 = w;
+            }
+            for (int o = 16; o >= 1; o >>= 1) {
+                a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+                c = fminf(c, __shfl_xor_sync(0xffffffffu, c, o));
+                w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
+                a2 = fmaxf(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+                c2 = fmaxf(c2, __shfl_xor_sync(0xffffffffu, c2, o));
+                w2 = fmaxf(w2, __shfl_xor_sync(0xffffffffu, w2, o));
+            }
+            finite = __all_sync(0xffffffffu, finite);
+            if (lane != 0) continue;
+            float xl = a, xh = a2, yl = c, yh = c2, zl = w, zh = w2;
+            if (!finite) {
+                xl = yl = zl = -INFINITY;
+                xh = yh = zh = INFINITY;
+            }
+            const int64_t bi = box_base + (c0 / 32) + b;
+            boxes[2 * bi] = make_float4(xl, xh, yl, yh);
+            boxes[2 * bi + 1] = make_float4(zl, zh, 0.f, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+int64_t prepared_box_count(int64_t n_hits, int n_events) { return n_hits / 32 + n_events + 1; }
+
+cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
+                                float4 *sorted, float4 *boxes, cudaStream_t st) {
+    const size_t smem = (size_t)SORT_CAP * sizeof(uint64_t);
+    {
+        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_kernel), smem);
+        if (aerr != cudaSuccess) return aerr;
+    }
+    prepare_hits_kernel<<<n_events, PREP_THREADS, smem, st>>>(hits, n_hits, off, model, sorted, boxes);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace retina

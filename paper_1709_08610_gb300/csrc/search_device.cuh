@@ -165,6 +165,13 @@ struct LsParams {
 
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box);
 
+// Shared-memory layout of the search kernels: smem_hits hits, then (with
+// boxes) the boxes of the first box_capacity(smem_hits) blocks (2 float4 each).
+__host__ __device__ __forceinline__ int box_capacity(int smem_hits) { return (smem_hits + 31) / 32 + 1; }
+__host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes) {
+    return (size_t)smem_hits * 16 + (with_boxes ? (size_t)box_capacity(smem_hits) * 32 : 0);
+}
+
 // Lane-strided pass over an event's hits: the staged prefix from shared
 // memory (two hits per iteration for independent work), then the rest, if
 // any, straight from global memory through L1.
@@ -181,6 +188,106 @@ __device__ __forceinline__ void for_each_hit(const float4 *__restrict__ sh, cons
     for (; k < H; k += 32) f(__ldg(gh + k));
 }
 
+// Exact skipping of hit blocks (boxes from retina_prepare_hits).  A block
+// can be skipped for a point theta when a lower bound of s^2 * log2(e) /
+// sigma^2 over the block's box exceeds CULL_EXPONENT: then every hit of the
+// block has ex2(-x) with x > 126, which ex2.approx.ftz returns as exactly
+// zero, so its terms add nothing to any sum.  The bound uses interval
+// arithmetic on the box and a relative slack of 1e-6 per magnitude that
+// covers the float32 rounding of the bound itself; 140 leaves a further
+// margin over 126.  Non-finite boxes are never skipped.
+constexpr float CULL_EXPONENT = 140.f;
+
+// Distance from t to the interval [l, h], minus a rounding slack of 1e-6
+// per magnitude; 0 inside.
+__device__ __forceinline__ float gap_pt(float t, float l, float h) {
+    const float d = fmaxf(fmaxf(l - t, t - h), 0.f);
+    return fmaxf(d - 1e-6f * (fabsf(l) + fabsf(h) + fabsf(t)), 0.f);
+}
+
+// True when every hit of the block has s^2 log2(e) / sigma^2 > CULL_EXPONENT
+// at theta = (t0, t1).  Slope model, box (umin, umax, vmin, vmax | |z|min, -):
+// s^2 = z^2 |(u, v) - theta|^2 >= |z|min^2 dist^2.  2D toy, box (xmin, xmax,
+// ymin, ymax): r = y - t0 x - t1 over the box, by interval arithmetic.
+template <int MODEL>
+__device__ __forceinline__ bool box_culled(const float4 A, const float4 B, float t0, float t1, float kk) {
+    if (!isfinite(B.x)) return false;  // boxes with non-finite hits are infinite
+    float bound;
+    if (MODEL == RETINA_VELO_SLOPES) {
+        const float du = gap_pt(t0, A.x, A.y), dv = gap_pt(t1, A.z, A.w);
+        bound = (du * du + dv * dv) * (B.x * B.x) * kk;
+    } else {
+        const float a = t0 * A.x, b = t0 * A.y;
+        const float lo = A.z - t1 - fmaxf(a, b), hi = A.w - t1 - fminf(a, b);
+        const float d = fmaxf(fmaxf(lo, -hi), 0.f);
+        const float dd = fmaxf(d - 1e-6f * (fabsf(A.z) + fabsf(A.w) + 2.f * fabsf(t1) + fabsf(a) + fabsf(b)), 0.f);
+        bound = dd * dd * kk;
+    }
+    return bound > CULL_EXPONENT;
+}
+
+// Pass over the hits that can contribute for the P points (tr0, tr1) of the
+// warp (active[p] selects the points that need this pass).  Without boxes it
+// is for_each_hit.  With boxes, each lane tests one block of a window of 32
+// blocks, the ballot gives the blocks some active point needs, and the warp
+// walks those blocks in increasing order, lane l taking hit 32 b + l: the
+// same per-lane order as the full pass minus blocks whose terms are all
+// exactly zero - so every sum is bitwise the full pass's sum.
+template <typename T, typename F>
+__device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
+                                        int H, int lane, const float4 *__restrict__ sbox,
+                                        const float4 *__restrict__ gbox, int n_sbox, T &&needed, F &&f) {
+    if (!gbox) {
+        for_each_hit(sh, gh, n_staged, H, lane, f);
+        return H;
+    }
+    int visited = 0;
+    const int nblk = (H + 31) >> 5;
+    for (int c = 0; c < nblk; c += 32) {
+        const int b = c + lane;
+        bool keep = false;
+        if (b < nblk) {
+            float4 A, B;
+            if (b < n_sbox) {
+                A = sbox[2 * b];
+                B = sbox[2 * b + 1];
+            } else {
+                A = __ldg(gbox + 2 * b);
+                B = __ldg(gbox + 2 * b + 1);
+            }
+            keep = needed(A, B);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        while (m) {
+            // two kept blocks per iteration: two independent hits per lane
+            const int ba = c + __ffs(m) - 1;
+            m &= m - 1;
+            const int bb = m ? c + __ffs(m) - 1 : -1;
+            m &= m - 1;
+            const int ka = ba * 32 + lane, kb = bb * 32 + lane;
+            visited += (H - ba * 32) < 32 ? (H - ba * 32) : 32;
+            if (bb >= 0) visited += (H - bb * 32) < 32 ? (H - bb * 32) : 32;
+            if (bb >= 0 && bb * 32 + 32 <= n_staged) {
+                const float4 ha = sh[ka], hb = sh[kb];
+                f(ha);
+                f(hb);
+            } else {
+                // block ba may be staged; block bb (if any) is not: it lies past n_staged
+                if (ka < H) {
+                    float4 ha;
+                    if (ba * 32 + 32 <= n_staged)
+                        ha = sh[ka];
+                    else
+                        ha = __ldg(gh + ka);
+                    f(ha);
+                }
+                if (bb >= 0 && kb < H) f(__ldg(gh + kb));
+            }
+        }
+    }
+    return visited;
+}
+
 // Algorithm 1 for the P seeds of one warp: q truncated-Newton updates
 // (gradient/Hessian pass, Newton-CG direction, step cap, Armijo backtracking
 // at bandwidth sigma_j), then R(theta_q; sigma_q), status and the number of
@@ -188,10 +295,13 @@ __device__ __forceinline__ void for_each_hit(const float4 *__restrict__ sh, cons
 // first n_live (<= P) seeds exist.  Warp-uniform control flow throughout.
 template <int MODEL, int P>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
-                                             int n_staged, int H, int lane, const float *__restrict__ seeds,
+                                             int n_staged, int H, int lane, const float4 *__restrict__ sbox,
+                                             const float4 *__restrict__ gbox, int n_sbox,
+                                             const float *__restrict__ seeds,
                                              int n_live, const LsParams &prm, float *__restrict__ theta_out,
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
-                                             uint8_t *__restrict__ n_evals) {
+                                             uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work) {
+    unsigned long long w_rgh = 0, w_r = 0;
     constexpr int NS = Model<MODEL>::NS;
     float th0[P], th1[P], Rfin[P];
     int evals[P];
@@ -215,10 +325,19 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
         for (int p = 0; p < P; ++p)
 #pragma unroll
             for (int i = 0; i < NS; ++i) S[p][i] = 0.f;
-        for_each_hit(sh, gh, n_staged, H, lane, [&](const float4 h) {
+        const int vis = hit_pass(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
+                                 [&](const float4 A, const float4 B) {
+                                     bool need = false;
 #pragma unroll
-            for (int p = 0; p < P; ++p) pair_rgh<MODEL>(h, th0[p], th1[p], kk, S[p]);
-        });
+                                     for (int p = 0; p < P; ++p)
+                                         need |= live[p] && !box_culled<MODEL>(A, B, th0[p], th1[p], kk);
+                                     return need;
+                                 },
+                                           [&](const float4 h) {
+#pragma unroll
+                                               for (int p = 0; p < P; ++p) pair_rgh<MODEL>(h, th0[p], th1[p], kk, S[p]);
+                                           });
+        w_rgh += (unsigned long long)vis * (unsigned long long)n_live;
         float R[P], g0[P], g1[P], pp0[P], pp1[P], slope[P], t[P];
         bool pending[P];
 #pragma unroll
@@ -252,11 +371,23 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 tr1[p] = __fmaf_rn(t[p], pp1[p], th1[p]);
                 Rt[p] = 0.f;
             }
-            for_each_hit(sh, gh, n_staged, H, lane, [&](const float4 h) {
+            const int vis = hit_pass(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
+                                     [&](const float4 A, const float4 B) {
+                                         bool need = false;
 #pragma unroll
-                for (int p = 0; p < P; ++p)
-                    if (pending[p]) Rt[p] += pair_r<MODEL>(h, tr0[p], tr1[p], kk);
-            });
+                                         for (int p = 0; p < P; ++p)
+                                             need |= pending[p] && !box_culled<MODEL>(A, B, tr0[p], tr1[p], kk);
+                                         return need;
+                                     },
+                                               [&](const float4 h) {
+#pragma unroll
+                                                   for (int p = 0; p < P; ++p)
+                                                       if (pending[p]) Rt[p] += pair_r<MODEL>(h, tr0[p], tr1[p], kk);
+                                               });
+            int n_pend = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) n_pend += pending[p] ? 1 : 0;
+            w_r += (unsigned long long)vis * (unsigned long long)n_pend;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 if (!pending[p]) continue;
@@ -280,6 +411,10 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     // After the last update Rfin holds R(theta_q; sigma_q): the accepted
     // trial's response, or the response at the unmoved point - the same sum,
     // in the same order, that a separate evaluation would produce.
+    if (work && lane == 0) {
+        atomicAdd(work + RETINA_WORK_RGH, w_rgh);
+        atomicAdd(work + RETINA_WORK_R, w_r);
+    }
     const float hi0 = prm.box.lo0 + (float)prm.box.n0 * prm.box.step0;
     const float hi1 = prm.box.lo1 + (float)prm.box.n1 * prm.box.step1;
 #pragma unroll

@@ -97,23 +97,28 @@ def _load():
     L.retina_set_option.argtypes = [I32, I32]
     L.retina_get_option.argtypes = [I32, P]
     L.retina_grid_scan_workspace_size.argtypes = [I32, I32, P, I32, I32, P]
-    L.retina_grid_scan.argtypes = [P, I64, P, I32, I32, P, F, F, I32, P, P, P, P, P, I32, P, SZ, P]
+    L.retina_grid_scan.argtypes = [P, I64, P, P, I32, I32, P, F, F, I32, P, P, P, P, P, I32, P, SZ, P]
     L.retina_grid_maxima_workspace_size.argtypes = [I32, P, P]
     L.retina_grid_maxima.argtypes = [P, I32, P, F, P, P, P, P, I32, P, SZ, P]
     L.retina_response.argtypes = [P, I64, P, I32, I32, P, I32, F, I32, P, P]
-    L.retina_local_search.argtypes = [P, I64, P, I32, I32, P, I32, P, P, P, P, P, P, P]
+    L.retina_local_search.argtypes = [P, I64, P, P, I32, I32, P, I32, P, P, P, P, P, P, P]
     L.retina_extract_tracks.argtypes = [P, P, P, P, I32, I32, P, F, F, P, P, P, P, I32, P]
     L.retina_grid_response_workspace_size.argtypes = [I32, I32, P, I32, P]
-    L.retina_grid_response.argtypes = [P, I64, P, I32, I32, P, F, I32, P, P, SZ, P]
+    L.retina_grid_response.argtypes = [P, I64, P, P, I32, I32, P, F, I32, P, P, SZ, P]
+    L.retina_prepare_hits_box_count.argtypes = [I64, I32]
+    L.retina_prepare_hits_box_count.restype = I64
+    L.retina_prepare_hits.argtypes = [P, I64, P, I32, I32, P, P, P]
+    L.retina_work_counters.argtypes = [I32, I32, P]
     L.retina_launch_count.restype = ctypes.c_uint64
     L.retina_alu_probe_sink_floats.restype = ctypes.c_int64
     L.retina_alu_probe.argtypes = [I32, I32, P, P, P]
     L.retina_grid_maxima_static.argtypes = [P, I32, P, F, P, P, P, P, I32, P]
     L.retina_batched_search_workspace_size.argtypes = [I32, P]
-    L.retina_batched_search.argtypes = [P, I64, P, I32, I32, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
+    L.retina_batched_search.argtypes = [P, I64, P, P, I32, I32, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
     for name in ("retina_set_option", "retina_get_option", "retina_grid_scan_workspace_size", "retina_grid_scan",
                  "retina_grid_response_workspace_size", "retina_grid_response", "retina_alu_probe",
                  "retina_grid_maxima_static", "retina_batched_search_workspace_size", "retina_batched_search",
+                 "retina_prepare_hits", "retina_work_counters",
                  "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
                  "retina_local_search", "retina_extract_tracks"):
         getattr(L, name).restype = ctypes.c_int
@@ -175,7 +180,7 @@ def grid_scan_workspace_size(n_events: int, model: int, grid: Grid, flags: int =
 
 def grid_scan(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: Grid, sigma: float, R0: float, K: int,
               flags: int = GRID_AUTO, store_R: bool = False, ws: Optional[torch.Tensor] = None, out=None,
-              stream=None) -> dict:
+              boxes: Optional[torch.Tensor] = None, stream=None) -> dict:
     """Eq. 2 on the grid plus strict local maxima >= R0 (grid algorithm steps 2-4)."""
     _dev(hits, torch.float32, "hits", 4)
     _dev(offsets, torch.int64, "offsets")
@@ -193,7 +198,7 @@ def grid_scan(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: Grid,
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     g = grid.c()
     _check("retina_grid_scan", lib.retina_grid_scan(
-        _p(hits), hits.shape[0], _p(offsets), E, model, ctypes.byref(g), float(sigma), float(R0), flags,
+        _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, ctypes.byref(g), float(sigma), float(R0), flags,
         _p(out["R"]), _p(out["max_idx"]), _p(out["max_theta"]), _p(out["max_R"]), _p(out["n_max"]), K,
         _p(ws), ws.numel(), _stream(stream)))
     return out
@@ -201,7 +206,7 @@ def grid_scan(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: Grid,
 
 def grid_response(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: Grid, sigma: float,
                   flags: int = GRID_AUTO, R_out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
-                  stream=None) -> torch.Tensor:
+                  boxes: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """Eq. 2 alone: R [E, n1, n0]."""
     _dev(hits, torch.float32, "hits", 4)
     _dev(offsets, torch.int64, "offsets")
@@ -216,7 +221,7 @@ def grid_response(hits: torch.Tensor, offsets: torch.Tensor, model: int, grid: G
     if ws is None or ws.numel() < b.value:
         ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=hits.device)
     _check("retina_grid_response", lib.retina_grid_response(
-        _p(hits), hits.shape[0], _p(offsets), E, model, ctypes.byref(g), float(sigma), flags, _p(R_out), _p(ws),
+        _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, ctypes.byref(g), float(sigma), flags, _p(R_out), _p(ws),
         ws.numel(), _stream(stream)))
     return R_out
 
@@ -227,6 +232,16 @@ def grid_response_workspace_size(n_events: int, model: int, grid: Grid, flags: i
     _check("retina_grid_response_workspace_size",
            lib.retina_grid_response_workspace_size(n_events, model, ctypes.byref(g), flags, ctypes.byref(b)))
     return b.value
+
+
+WORK_GRID, WORK_RGH, WORK_R = 0, 1, 2
+
+
+def work_counters(enable: Optional[bool] = None, reset: bool = False) -> list:
+    """Read (and optionally reset / switch) the device work counters."""
+    out = (ctypes.c_uint64 * 4)()
+    _check("retina_work_counters", lib.retina_work_counters(-1 if enable is None else int(enable), int(reset), out))
+    return list(out)
 
 
 def launch_count() -> int:
@@ -243,6 +258,20 @@ def alu_probe(kind: int, iters: int, sink: torch.Tensor, stream=None) -> float:
 
 def alu_probe_sink_floats() -> int:
     return int(lib.retina_alu_probe_sink_floats())
+
+
+def prepare_hits(hits: torch.Tensor, offsets: torch.Tensor, model: int, out=None,
+                 stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Spatially ordered hits and per-32-hit boxes for exact block skipping."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    E = offsets.numel() - 1
+    nb = int(lib.retina_prepare_hits_box_count(hits.shape[0], E))
+    if out is None:
+        out = (torch.empty_like(hits), torch.empty((nb, 8), dtype=torch.float32, device=hits.device))
+    _check("retina_prepare_hits", lib.retina_prepare_hits(_p(hits), hits.shape[0], _p(offsets), E, model, _p(out[0]),
+                                                          _p(out[1]), _stream(stream)))
+    return out
 
 
 def grid_maxima(R: torch.Tensor, grid: Grid, R0: float, K: int, out=None, ws=None, stream=None) -> dict:
@@ -282,7 +311,7 @@ def response(hits: torch.Tensor, offsets: torch.Tensor, model: int, theta: torch
 
 
 def local_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds: torch.Tensor, opts: LsOpts,
-                 box: Grid, out=None, n_evals: Optional[torch.Tensor] = None,
+                 box: Grid, out=None, n_evals: Optional[torch.Tensor] = None, boxes: Optional[torch.Tensor] = None,
                  stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
     """Algorithm 1's q truncated-Newton updates: (theta [E,n,2], R [E,n], status [E,n] uint8).
 
@@ -303,7 +332,7 @@ def local_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds: t
     o = opts.c()
     g = box.c()
     _check("retina_local_search", lib.retina_local_search(
-        _p(hits), hits.shape[0], _p(offsets), E, model, _p(seeds), n, ctypes.byref(o), ctypes.byref(g),
+        _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, _p(seeds), n, ctypes.byref(o), ctypes.byref(g),
         _p(out[0]), _p(out[1]), _p(out[2]), _p(n_evals), _stream(stream)))
     return out
 
@@ -317,7 +346,7 @@ def batched_search_workspace_size(n_events: int) -> int:
 def batched_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds: torch.Tensor,
                    seed_offsets: torch.Tensor, opts: LsOpts, box: Grid, order: Optional[torch.Tensor] = None,
                    out=None, n_evals: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
-                   stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+                   boxes: Optional[torch.Tensor] = None, stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
     """Algorithm 1 over a ragged batch in one persistent launch.
 
     seeds [S, 2] float32 with seed_offsets int64 [E + 1]; returns per seed
@@ -344,7 +373,7 @@ def batched_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds:
     o = opts.c()
     g = box.c()
     _check("retina_batched_search", lib.retina_batched_search(
-        _p(hits), hits.shape[0], _p(offsets), E, model, _p(seeds), S, _p(seed_offsets), _p(order), ctypes.byref(o),
+        _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, _p(seeds), S, _p(seed_offsets), _p(order), ctypes.byref(o),
         ctypes.byref(g), _p(out[0]), _p(out[1]), _p(out[2]), _p(n_evals), _p(ws), ws.numel(), _stream(stream)))
     return out
 

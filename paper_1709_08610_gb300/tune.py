@@ -95,8 +95,8 @@ def tune_local_search(hits, offs, model: int, seeds, opts: "rt.LsOpts", box: "rt
     return res
 
 
-def tune_grid(hits, offs, model: int, grid: "rt.Grid", sigma: float, splits: Iterable[int] = (0, 8, 12, 16, 19, 24, 32),
-              reps: int = 5) -> Dict:
+def tune_grid(hits, offs, model: int, grid: "rt.Grid", sigma: float, splits: Iterable[int] = (0, 4, 8, 12, 16, 19, 24, 32),
+              reps: int = 5, boxes=None) -> Dict:
     """Pick the hit-slice count of the grid response (0 = the library's rule)."""
     E = offs.numel() - 1
     n0, n1 = grid.n
@@ -106,7 +106,8 @@ def tune_grid(hits, offs, model: int, grid: "rt.Grid", sigma: float, splits: Ite
         rt.set_option(rt.OPT_GRID_SPLITS, s)
         ws = torch.empty(max(rt.grid_response_workspace_size(E, model, grid), 1), dtype=torch.uint8,
                          device=hits.device)
-        table[str(s)] = _time(lambda: rt.grid_response(hits, offs, model, grid, sigma, R_out=R, ws=ws), reps=reps)
+        table[str(s)] = _time(lambda: rt.grid_response(hits, offs, model, grid, sigma, R_out=R, ws=ws, boxes=boxes),
+                              reps=reps)
     best = min(table, key=table.get)
     rt.set_option(rt.OPT_GRID_SPLITS, int(best))
     res = {"splits": int(best), "ms": table[best], "table_ms": table}
@@ -116,7 +117,7 @@ def tune_grid(hits, offs, model: int, grid: "rt.Grid", sigma: float, splits: Ite
 
 def tune_batched_search(hits, offs, model: int, seeds, seed_offs, opts: "rt.LsOpts", box: "rt.Grid",
                         spw: Iterable[int] = (1, 2, 4), warps: Iterable[int] = (8, 16, 32),
-                        smem_hits: Iterable[int] = (4096, 8192), reps: int = 5) -> Dict:
+                        smem_hits: Iterable[int] = (4096, 8192), reps: int = 5, boxes=None) -> Dict:
     """Pick seeds-per-warp, warps-per-CTA and staged hits of the persistent search."""
     E = offs.numel() - 1
     S = seeds.numel() // 2
@@ -132,7 +133,8 @@ def tune_batched_search(hits, offs, model: int, seeds, seed_offs, opts: "rt.LsOp
                 rt.set_option(rt.OPT_BATCH_WARPS, w)
                 rt.set_option(rt.OPT_BATCH_SMEM_HITS, h)
                 table["%d,%d,%d" % (p, w, h)] = _time(
-                    lambda: rt.batched_search(hits, offs, model, seeds, seed_offs, opts, box, out=out, ws=ws),
+                    lambda: rt.batched_search(hits, offs, model, seeds, seed_offs, opts, box, out=out, ws=ws,
+                                              boxes=boxes),
                     reps=reps)
     best = min(table, key=table.get)
     p, w, h = (int(x) for x in best.split(","))

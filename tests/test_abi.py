@@ -62,20 +62,20 @@ def test_workspace_size():
                                                  (0.3, 8, 0, 2), (0.3, 8, 1, 9)])
 def test_grid_scan_rejects(sigma, K, model, flags):
     g = _grid()
-    rc = L.retina_grid_scan(BOGUS, 10, BOGUS, 1, model, ctypes.byref(g), sigma, 1.0, flags, None, BOGUS, BOGUS,
+    rc = L.retina_grid_scan(BOGUS, 10, BOGUS, None, 1, model, ctypes.byref(g), sigma, 1.0, flags, None, BOGUS, BOGUS,
                             BOGUS, BOGUS, K, BOGUS, 1 << 40, None)
     assert rc == EINVAL
 
 
 def test_grid_scan_rejects_misaligned_and_small_workspace():
     g = _grid()
-    rc = L.retina_grid_scan(ctypes.c_void_p(0x1004), 10, BOGUS, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS,
+    rc = L.retina_grid_scan(ctypes.c_void_p(0x1004), 10, BOGUS, None, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS,
                             BOGUS, BOGUS, BOGUS, 8, BOGUS, 1 << 40, None)
     assert rc == EINVAL
-    rc = L.retina_grid_scan(BOGUS, 10, BOGUS, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS, BOGUS, BOGUS, BOGUS,
+    rc = L.retina_grid_scan(BOGUS, 10, BOGUS, None, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS, BOGUS, BOGUS, BOGUS,
                             8, BOGUS, 16, None)
     assert rc == ENOSPACE
-    rc = L.retina_grid_scan(BOGUS, 10, None, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS, BOGUS, BOGUS, BOGUS,
+    rc = L.retina_grid_scan(BOGUS, 10, None, None, 1, 1, ctypes.byref(g), 0.3, 1.0, 0, None, BOGUS, BOGUS, BOGUS, BOGUS,
                             8, BOGUS, 1 << 40, None)
     assert rc == EINVAL
 
@@ -105,7 +105,7 @@ def test_local_search_rejects(mut):
     elif mut == "cap0":
         o.step_cap_cells = 0.0
     g = _grid()
-    rc = L.retina_local_search(BOGUS, 10, BOGUS, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), BOGUS, BOGUS,
+    rc = L.retina_local_search(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), BOGUS, BOGUS,
                                BOGUS, None, None)
     assert rc == EINVAL
 
@@ -113,12 +113,12 @@ def test_local_search_rejects(mut):
 def test_local_search_rejects_null_outputs_and_empty_is_ok():
     o = _opts()
     g = _grid()
-    assert L.retina_local_search(BOGUS, 10, BOGUS, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), None, BOGUS,
+    assert L.retina_local_search(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), None, BOGUS,
                                  BOGUS, None, None) == EINVAL
     # zero events or zero seeds: nothing to do, nothing launched
-    assert L.retina_local_search(None, 0, None, 0, 1, None, 16, ctypes.byref(o), ctypes.byref(g), None, None, None,
+    assert L.retina_local_search(None, 0, None, None, 0, 1, None, 16, ctypes.byref(o), ctypes.byref(g), None, None, None,
                                  None, None) == 0
-    assert L.retina_local_search(BOGUS, 10, BOGUS, 1, 1, BOGUS, 0, ctypes.byref(o), ctypes.byref(g), None, None,
+    assert L.retina_local_search(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, 0, ctypes.byref(o), ctypes.byref(g), None, None,
                                  None, None, None) == 0
 
 
@@ -138,3 +138,11 @@ def test_response_rejects():
     assert L.retina_response(BOGUS, 10, BOGUS, 1, 1, BOGUS, 4, 0.0, 1, BOGUS, None) == EINVAL
     assert L.retina_response(BOGUS, 10, BOGUS, 1, 5, BOGUS, 4, 0.3, 1, BOGUS, None) == EINVAL
     assert L.retina_response(BOGUS, 10, BOGUS, 1, 1, None, 4, 0.3, 1, BOGUS, None) == EINVAL
+
+
+def test_prepare_hits_rejects_and_counts():
+    assert L.retina_prepare_hits_box_count(100, 3) == 100 // 32 + 3 + 1
+    assert L.retina_prepare_hits(BOGUS, 10, BOGUS, 1, 5, BOGUS, BOGUS, None) == EINVAL  # model
+    assert L.retina_prepare_hits(BOGUS, 10, BOGUS, 1, 1, BOGUS, BOGUS, None) == EINVAL  # in place
+    assert L.retina_prepare_hits(BOGUS, 10, BOGUS, 1, 1, ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3004),
+                                 None) == EINVAL  # misaligned boxes

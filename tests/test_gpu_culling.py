@@ -1,0 +1,139 @@
+"""Exact block skipping (retina_prepare_hits boxes) on the GPU.
+
+A block of 32 hits is skipped only when every one of its terms of Eq. 1 is
+exactly zero in float32, so with boxes every kernel must return bitwise what
+it returns without boxes on the same (spatially ordered) hits; the prepared
+hits must be a permutation of each event's hits, and each box must bound its
+block.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import WORKLOADS, make_event, batch_of, uniform_seeds
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    from paper_1709_08610_gb300 import build as rbuild
+    rbuild.build()
+    from paper_1709_08610_gb300 import retina
+    return retina
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _batch(model):
+    if model == 1:
+        wl = WORKLOADS["velo"]
+        evs = [make_event(wl, 4, 0, vertex_sigma=(0, 0, 0)), make_event(wl, 4, 1, n_tracks=0, noise_frac=0.0),
+               make_event(wl, 4, 2, n_tracks=700, vertex_sigma=(0, 0, 0)),  # > 16384 hits: two sort chunks
+               make_event(wl, 4, 3, n_tracks=20)]
+    else:
+        wl = WORKLOADS["toy2d"]
+        evs = [make_event(wl, 4, e) for e in range(3)]
+    return wl, evs, batch_of(evs)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_prepared_hits_are_a_permutation_with_bounding_boxes(rt, model):
+    wl, evs, b = _batch(model)
+    srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), model)
+    srt, boxes = srt.cpu().numpy(), boxes.cpu().numpy()
+    for e in range(len(evs)):
+        h0, h1 = b.offsets[e], b.offsets[e + 1]
+        a = b.hits[h0:h1]
+        s = srt[h0:h1]
+        assert np.array_equal(a[np.lexsort(a.T[::-1])], s[np.lexsort(s.T[::-1])])
+        base = h0 // 32 + e
+        for k in range(0, h1 - h0, 32):
+            blk = s[k:k + 32].astype(np.float32)
+            bx = boxes[base + k // 32]
+            if model == 1:  # slopes (float32 division) and |z|
+                u, v, w = blk[:, 0] / blk[:, 2], blk[:, 1] / blk[:, 2], np.abs(blk[:, 2])
+            else:
+                u, v, w = blk[:, 0], blk[:, 1], np.zeros(len(blk), np.float32)
+            assert bx[0] == u.min() and bx[1] == u.max()
+            assert bx[2] == v.min() and bx[3] == v.max()
+            assert bx[4] == w.min() and bx[5] == w.max()
+        if model == 1 and h1 - h0 > 1000:
+            # blocks are spatially coherent: slope boxes of layers |z| >= 64 mm are small
+            bx = boxes[base:base + (h1 - h0) // 32]
+            far = bx[:, 4] >= 64
+            side = np.sqrt((bx[far, 1] - bx[far, 0]) * (bx[far, 3] - bx[far, 2]))
+            assert np.median(side) <= 0.3, np.median(side)
+
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_grid_response_with_boxes_is_bitwise_the_full_sum(rt, flags):
+    wl, evs, b = _batch(1)
+    srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), 1)
+    offs = _dev(b.offsets)
+    grid = rt.Grid.of(wl) if flags == 2 else rt.Grid((-0.25, -0.2), wl.grid_step, (320, 300))
+    R_full = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=flags)
+    R_cull = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=flags, boxes=boxes)
+    assert torch.equal(R_full, R_cull)
+    # and the culled grid still matches the oracle on sampled cells
+    R = R_cull.cpu().numpy()
+    rng = np.random.default_rng(0)
+    c0, c1 = oracle.cell_centres(grid.lo, grid.step, grid.n)
+    for e in (0, 2):
+        idx = np.concatenate([rng.integers(0, R[e].size, 400), np.argsort(R[e].reshape(-1))[-100:]])
+        th = np.stack([c0[idx % grid.n[0]], c1[idx // grid.n[0]]], 1)
+        R_o = oracle.response(evs[e].hits, 1, th, wl.sigma_grid)
+        assert np.all(np.abs(R[e].reshape(-1)[idx] - R_o) <= 1e-5 * R_o + 1e-6)
+
+
+def test_grid_response_toy_with_boxes_is_bitwise_the_full_sum(rt):
+    wl, evs, b = _batch(0)
+    srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), 0)
+    offs = _dev(b.offsets)
+    grid = rt.Grid.of(wl)
+    for sigma in (wl.sigma_grid, 0.004):
+        R_full = rt.grid_response(srt, offs, 0, grid, sigma)
+        R_cull = rt.grid_response(srt, offs, 0, grid, sigma, boxes=boxes)
+        assert torch.equal(R_full, R_cull)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_searches_with_boxes_are_bitwise_the_full_search(rt, model):
+    wl, evs, b = _batch(model)
+    srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), model)
+    offs = _dev(b.offsets)
+    n = 300
+    per = []
+    for e, ev in enumerate(evs):  # per event: half uniform seeds, half on true tracks
+        uni = uniform_seeds(wl, n // 2, 4, e)
+        near = (ev.truth[:, :2][np.arange(n // 2) % len(ev.truth)] if len(ev.truth) else uniform_seeds(wl, n // 2, 5, e))
+        per.append(np.concatenate([uni, near.astype(np.float32)]))
+    S = np.stack(per).astype(np.float32)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    box = rt.Grid.of(wl)
+    full = rt.local_search(srt, offs, model, _dev(S), opts, box)
+    cull = rt.local_search(srt, offs, model, _dev(S), opts, box, boxes=boxes)
+    for x, y in zip(full, cull):
+        assert torch.equal(x, y)
+    so = _dev(np.arange(len(evs) + 1, dtype=np.int64) * n)
+    bfull = rt.batched_search(srt, offs, model, _dev(S.reshape(-1, 2)), so, opts, box)
+    bcull = rt.batched_search(srt, offs, model, _dev(S.reshape(-1, 2)), so, opts, box, boxes=boxes)
+    for x, y, z in zip(bfull, bcull, full):
+        assert torch.equal(x, y)
+        assert torch.equal(x.reshape(z.shape), z)
+
+
+def test_non_finite_hit_blocks_are_never_skipped(rt):
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 6, 0, vertex_sigma=(0, 0, 0))
+    hits = ev.hits.copy()
+    hits[17, 0] = np.nan
+    offs = _dev(np.array([0, len(hits)], np.int64))
+    srt, boxes = rt.prepare_hits(_dev(hits), offs, 1)
+    grid = rt.Grid((-0.1, -0.1), wl.grid_step, (64, 64))
+    R_full = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=1)
+    R_cull = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=1, boxes=boxes)
+    assert torch.isnan(R_full).all() and torch.isnan(R_cull).all()
