@@ -23,6 +23,18 @@ __device__ __forceinline__ float ex2_mufu(float x) {
     return y;
 }
 
+// Packed FP32x2 fused multiply-add, round-to-nearest per lane (each lane is
+// bitwise the scalar __fmaf_rn): acc = a * b + acc on {lo, hi} pairs.
+__device__ __forceinline__ void ffma2_rn(unsigned long long &acc, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
 // Butterfly (xor) sum: every lane ends with the bitwise-identical total,
 // because each level adds the same two operands in either order.
 __device__ __forceinline__ float warp_sum(float v) {

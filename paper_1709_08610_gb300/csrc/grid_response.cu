@@ -118,11 +118,12 @@ grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
     // contraction role: 8 x 8 cells per thread (two 4-wide groups per axis)
     const int tm = t & 15, tn = t >> 4;
 
-    float acc[8][8];
+    // acc2[a][c] packs the accumulators of cells (a, 2c) and (a, 2c + 1)
+    unsigned long long acc2[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+        for (int c = 0; c < 4; ++c) acc2[a][c] = 0ull;
 
     // blocks of this slice that can contribute to this tile, 256 at a time
     int64_t hb, he;
@@ -170,14 +171,17 @@ grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
                 for (int kc = 0; kc < SEP_BK; ++kc) {
                     const float4 a0 = *reinterpret_cast<const float4 *>(&sA[kc][tm * 4]);
                     const float4 a1 = *reinterpret_cast<const float4 *>(&sA[kc][64 + tm * 4]);
-                    const float4 b0 = *reinterpret_cast<const float4 *>(&sB[kc][tn * 4]);
-                    const float4 b1 = *reinterpret_cast<const float4 *>(&sB[kc][64 + tn * 4]);
-                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                    // {b_2c, b_2c+1} pairs for the thread's 8 cells along theta1
+                    const ulonglong2 b03 = *reinterpret_cast<const ulonglong2 *>(&sB[kc][tn * 4]);
+                    const ulonglong2 b47 = *reinterpret_cast<const ulonglong2 *>(&sB[kc][64 + tn * 4]);
+                    const float af[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const unsigned long long bv[4] = {b03.x, b03.y, b47.x, b47.y};
 #pragma unroll
-                    for (int a = 0; a < 8; ++a)
+                    for (int a = 0; a < 8; ++a) {
+                        const unsigned long long aa = pack2(af[a], af[a]);  // {a_i, a_i}
 #pragma unroll
-                        for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+                        for (int c = 0; c < 4; ++c) ffma2_rn(acc2[a][c], aa, bv[c]);
+                    }
                 }
             }
         }
@@ -187,6 +191,14 @@ grid_sep_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
         const int64_t cw = (g.n0 - ti0 < SEP_BM ? g.n0 - ti0 : SEP_BM), ch = (g.n1 - tj0 < SEP_BN ? g.n1 - tj0 : SEP_BN);
         atomicAdd(work + RETINA_WORK_GRID, (unsigned long long)(done_hits * cw * ch));
     }
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[a][2 * c] = __uint_as_float((unsigned)(acc2[a][c] & 0xffffffffull));
+            acc[a][2 * c + 1] = __uint_as_float((unsigned)(acc2[a][c] >> 32));
+        }
     float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
     const bool vec = (g.n0 % 4) == 0;
 #pragma unroll
