@@ -17,7 +17,8 @@ written as the definitions read:
   bfloat16 where the kernels store them.
 * adam - Adam (Kingma & Ba) with bias correction.
 * top_k - the K largest logits per event (ties: lower index first), seeds at
-  the cell centres.
+  the cell centres, or - given cell_centroids - at the mean slope of the hits
+  binned to the chosen cell (its centre when the cell is empty).
 
 Parameter vector layout (4833 values): W1 [16,1,3,3] at 0, b1 [16] at 144,
 W2 [32,16,3,3] at 160, b2 [32] at 4768, W3 [32] at 4800, b3 at 4832.
@@ -64,20 +65,26 @@ def bf16_exact(x) -> np.ndarray:
     return np.where(x == 0, 0.0, np.ldexp(r, e - 8))
 
 
-def slope_histogram(hits: np.ndarray, lo: float = -0.5, hi: float = 0.5, nb: int = NB, zmin: float = 50.0):
-    """(counts int64 [nb, nb] indexed [v_bin, u_bin], feature float64 (bf16 values))."""
+def _binned_slopes(hits, lo, hi, nb, zmin):
+    """(u, v, u_bin, v_bin) of the hits slope_histogram counts (same float32 rule)."""
     h = np.asarray(hits, dtype=np.float32)
     x, y, z = h[:, 0], h[:, 1], h[:, 2]
     keep = np.abs(z) >= np.float32(zmin)
     with np.errstate(divide="ignore", invalid="ignore"):
         u = (x / z).astype(np.float32)
         v = (y / z).astype(np.float32)
-    scale = np.float32(nb / (hi - lo))
-    bu = np.floor((u - np.float32(lo)) * scale)
-    bv = np.floor((v - np.float32(lo)) * scale)
-    ok = keep & np.isfinite(bu) & np.isfinite(bv) & (bu >= 0) & (bu < nb) & (bv >= 0) & (bv < nb)
+        scale = np.float32(nb / (hi - lo))
+        bu = np.floor((u - np.float32(lo)) * scale)
+        bv = np.floor((v - np.float32(lo)) * scale)
+        ok = keep & np.isfinite(bu) & np.isfinite(bv) & (bu >= 0) & (bu < nb) & (bv >= 0) & (bv < nb)
+    return u[ok], v[ok], bu[ok].astype(np.int64), bv[ok].astype(np.int64)
+
+
+def slope_histogram(hits: np.ndarray, lo: float = -0.5, hi: float = 0.5, nb: int = NB, zmin: float = 50.0):
+    """(counts int64 [nb, nb] indexed [v_bin, u_bin], feature float64 (bf16 values))."""
+    _, _, bu, bv = _binned_slopes(hits, lo, hi, nb, zmin)
     counts = np.zeros((nb, nb), dtype=np.int64)
-    np.add.at(counts, (bv[ok].astype(np.int64), bu[ok].astype(np.int64)), 1)
+    np.add.at(counts, (bv, bu), 1)
     return counts, bf16(np.log1p(counts.astype(np.float32)))
 
 
@@ -182,21 +189,30 @@ def adam(params, grad, m, v, step: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def top_k(logits: np.ndarray, K: int, lo: float = -0.5, hi: float = 0.5, nb: int = NB):
+def cell_centroids(hits: np.ndarray, lo: float = -0.5, hi: float = 0.5, nb: int = NB, zmin: float = 50.0):
+    """float64 [nb, nb, 2]: mean (u, v) of the hits binned to each cell (the
+    float32 slopes slope_histogram bins, averaged in double); NaN where the
+    cell is empty."""
+    u, v, bu, bv = _binned_slopes(hits, lo, hi, nb, zmin)
+    su = np.zeros((nb, nb))
+    sv = np.zeros((nb, nb))
+    cnt = np.zeros((nb, nb))
+    np.add.at(su, (bv, bu), u.astype(np.float64))
+    np.add.at(sv, (bv, bu), v.astype(np.float64))
+    np.add.at(cnt, (bv, bu), 1.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.stack([su / cnt, sv / cnt], -1)
+
+
+def top_k(logits: np.ndarray, K: int, lo: float = -0.5, hi: float = 0.5, nb: int = NB, centroids=None):
     """Indices (v_bin * nb + u_bin) of the K largest logits (ties: lower
-    index first) and the seeds (u, v) at their cell centres."""
+    index first) and the seeds (u, v): the cell centres, or the cells' hit
+    centroids (cell_centroids) where a centroid is given and finite."""
     z = np.asarray(logits, dtype=np.float64).reshape(-1)
     order = np.lexsort((np.arange(z.size), -z))[:K]
     w = (hi - lo) / nb
     seeds = np.stack([lo + (order % nb + 0.5) * w, lo + (order // nb + 0.5) * w], 1)
+    if centroids is not None:
+        c = np.asarray(centroids, dtype=np.float64).reshape(-1, 2)[order]
+        seeds = np.where(np.isfinite(c), c, seeds)
     return order, seeds
-
-
-def init_params(seed: int = 0) -> np.ndarray:
-    """He-style initialisation (numpy PCG64), biases zero except the head's
-    prior log-odds."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    W1 = rng.normal(0, np.sqrt(2.0 / 9), (C1, 1, 3, 3))
-    W2 = rng.normal(0, np.sqrt(2.0 / (9 * C1)), (C2, C1, 3, 3))
-    W3 = rng.normal(0, np.sqrt(1.0 / C2), (C2,))
-    return pack(dict(W1=W1, b1=np.zeros(C1), W2=W2, b2=np.zeros(C2), W3=W3, b3=np.array([-3.0]))).astype(np.float32)

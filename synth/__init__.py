@@ -18,5 +18,6 @@ from .events import (  # noqa: F401
     make_batch,
     batch_of,
     uniform_seeds,
+    seednet_init_params,
     close_tracks_event,
 )

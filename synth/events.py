@@ -229,6 +229,18 @@ def batch_of(evs: Sequence[Event]) -> Batch:
                  offsets, list(evs))
 
 
+def seednet_init_params(seed: int = 0) -> np.ndarray:
+    """Initial float32 parameter vector (4833 values) of the seed-proposal
+    network: He-style normal weights (PCG64 keyed by ``seed``), zero biases
+    except the head's, set to the prior log-odds -3.  Layout: W1 [16,1,3,3],
+    b1 [16], W2 [32,16,3,3], b2 [32], W3 [32], b3."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W1 = rng.normal(0, math.sqrt(2.0 / 9), 16 * 9)
+    W2 = rng.normal(0, math.sqrt(2.0 / (9 * 16)), 32 * 16 * 9)
+    W3 = rng.normal(0, math.sqrt(1.0 / 32), 32)
+    return np.concatenate([W1, np.zeros(16), W2, np.zeros(32), W3, [-3.0]]).astype(np.float32)
+
+
 def uniform_seeds(wl: Workload, n: int, run_seed: int, event_id: int) -> np.ndarray:
     """Uniform multistart seeds over the grid box (the prior of Algorithm 1)."""
     rng = _rng(run_seed, event_id, STREAM_SEEDS)

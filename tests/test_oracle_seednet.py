@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import seednet as sn
-from synth import WORKLOADS, make_event
+from synth import WORKLOADS, make_event, seednet_init_params
 
 
 def test_bf16_rounding_matches_torch():
@@ -56,7 +56,7 @@ def test_forward_matches_scipy_correlate():
     ss = pytest.importorskip("scipy.signal")
     rng = np.random.default_rng(1)
     feat = sn.bf16(rng.uniform(0, 3, (64, 64)))
-    p = sn.init_params(3)
+    p = seednet_init_params(3)
     f = sn.forward(feat, p, rounding=False)
     P = sn.unpack(p)
     a1 = np.stack([ss.correlate2d(feat, P["W1"][o, 0], mode="same") + P["b1"][o] for o in range(16)])
@@ -73,7 +73,7 @@ def test_backward_matches_central_differences():
     rng = np.random.default_rng(2)
     feats = [sn.bf16(rng.uniform(0, 2, (64, 64))) for _ in range(2)]
     labels = [(rng.uniform(0, 1, (64, 64)) < 0.02).astype(np.float64) for _ in range(2)]
-    p = sn.init_params(4).astype(np.float64)
+    p = seednet_init_params(4).astype(np.float64)
     pw = sn.pos_weight(np.stack(labels))
 
     def loss(q):
@@ -121,3 +121,40 @@ def test_top_k_ties_and_cell_centres():
     assert order.tolist() == [5, 70, 4095, 7, 100]
     np.testing.assert_allclose(seeds[0], [-0.5 + 5.5 / 64, -0.5 + 0.5 / 64])
     np.testing.assert_allclose(seeds[2], [0.5 - 0.5 / 64, 0.5 - 0.5 / 64])
+
+
+def test_cell_centroids_are_the_mean_of_constructed_slopes():
+    # hits built on chosen slopes inside chosen cells, at several layers and both signs of z:
+    # each centroid is the plain mean of the slopes placed there, every non-empty cell's
+    # centroid lies inside the cell, and empty cells give NaN
+    rng = np.random.default_rng(5)
+    w = 1.0 / 64
+    cells = [(3, 7), (40, 12), (63, 0), (0, 63)]           # (row = v bin, col = u bin)
+    hits, want = [], {}
+    for r, c in cells:
+        n = int(rng.integers(1, 9))
+        uu = -0.5 + (c + rng.uniform(0.05, 0.95, n)) * w
+        vv = -0.5 + (r + rng.uniform(0.05, 0.95, n)) * w
+        zz = rng.choice([-256.0, 64.0, 128.0, 512.0], n)  # powers of two: x / z gives back u exactly
+        uu = (np.float32(uu * zz) / np.float32(zz)).astype(np.float64)
+        vv = (np.float32(vv * zz) / np.float32(zz)).astype(np.float64)
+        for a, b, z in zip(uu, vv, zz):
+            hits.append((a * z, b * z, z, 0.0))
+        want[(r, c)] = (uu.mean(), vv.mean())
+    hits.append((0.0, 0.0, 10.0, 0.0))                     # |z| < zmin: not binned
+    H = np.array(hits, dtype=np.float32)
+    cen = sn.cell_centroids(H[rng.permutation(len(H))])
+    counts, _ = sn.slope_histogram(H)
+    assert np.array_equal(np.isfinite(cen[..., 0]), counts > 0)
+    for (r, c), (mu, mv) in want.items():
+        assert cen[r, c, 0] == pytest.approx(mu, abs=1e-15) and cen[r, c, 1] == pytest.approx(mv, abs=1e-15)
+        assert -0.5 + c * w <= cen[r, c, 0] < -0.5 + (c + 1) * w
+        assert -0.5 + r * w <= cen[r, c, 1] < -0.5 + (r + 1) * w
+    # top_k seeds: centroids where the cell is non-empty, centres elsewhere
+    logits = np.full(64 * 64, -5.0)
+    logits[3 * 64 + 7] = 2.0
+    logits[10] = 1.0                                       # empty cell (0, 10)
+    order, seeds = sn.top_k(logits, 2, centroids=cen)
+    assert list(order) == [3 * 64 + 7, 10]
+    assert tuple(seeds[0]) == tuple(cen[3, 7])
+    assert tuple(seeds[1]) == (-0.5 + 10.5 * w, -0.5 + 0.5 * w)
