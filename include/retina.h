@@ -371,6 +371,124 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
                           float merge_cells, float *tracks, float *track_R, int32_t *track_src,
                           int32_t *n_tracks, int32_t K, void *stream);
 
+/*
+ * Learned seed proposer
+ * ---------------------
+ * Algorithm 1 starts its local searches from initial guesses drawn from a
+ * prior distribution P_theta, which the paper leaves open (a uniform draw
+ * over the box is the plain choice).  These entry points replace that prior by
+ * a small convolutional network that looks at a coarse histogram of the
+ * event's hit slopes and ranks 64 x 64 cells; the K best cells' centres
+ * become the seeds.  The proposer is an extension: the paper has no
+ * counterpart beyond the prior it replaces.  Only slope-model
+ * (RETINA_VELO_SLOPES) hits are supported.
+ *
+ * Network on one event's 64 x 64 image (row = v bin, column = u bin):
+ *   a1 = conv3x3(x; W1, b1) (1 -> 16),  h1 = bf16(relu(a1))
+ *   a2 = conv3x3(h1; W2, b2) (16 -> 32), h2 = bf16(relu(a2))
+ *   z  = sum_o W3[o] h2[o] + b3          (logits, float32)
+ * with 'same' zero padding, stride 1, cross-correlation, every sum in float32
+ * and the weights rounded to bfloat16 (round to nearest even) when read.
+ * Parameters: float32 [RETINA_SEEDNET_PARAMS] master vector,
+ *   W1 [16][1][3][3] at 0, b1 [16] at 144, W2 [32][16][3][3] at 160,
+ *   b2 [32] at 4768, W3 [32] at 4800, b3 at 4832.
+ * bfloat16 arrays are uint16 bit patterns.
+ */
+#define RETINA_SEEDNET_BINS 64
+#define RETINA_SEEDNET_PARAMS 4833
+
+/*
+ * retina_slope_histogram - the network's input image per event.
+ *
+ * For every hit with |z| >= zmin: u = x / z, v = y / z (float32 division),
+ * column floor((u - lo) * s), row floor((v - lo) * s) with s = float32(64 /
+ * (hi - lo)), all in float32; hits outside [0, 64) in either bin are dropped.
+ * features[e][row][col] = bf16(log1pf(count)).  Counts and sums are exact
+ * integers (integer atomics), so no result depends on the hits' order.
+ *
+ *   hits, n_hits, event_offsets : as everywhere (slope-model rows).
+ *   lo < hi finite, zmin >= 0.
+ *   features   : uint16 (bfloat16) [n_events][64][64].
+ *   counts     : nullable int32 [n_events][64][64].
+ *   slope_sums : nullable uint64 [n_events][64][64][2]: per cell, the sums
+ *                over its hits of round(2^32 (t - floor t)) for t = (u - lo) s
+ *                and t = (v - lo) s (the hit's position inside the cell, in
+ *                2^-32 units); with counts, retina_topk_seeds turns them
+ *                into the cell's hit centroid.
+ */
+int retina_slope_histogram(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                           float lo, float hi, float zmin, uint16_t *features, int32_t *counts, uint64_t *slope_sums,
+                           void *stream);
+
+/*
+ * retina_seednet_forward - logits of the 64 x 64 cells of each event.
+ *
+ *   features : uint16 (bfloat16) [n_events][64][64].
+ *   params   : float32 [RETINA_SEEDNET_PARAMS].
+ *   logits   : float32 [n_events][64][64].
+ *   h1       : uint16 (bfloat16) [n_events][16][64][64], required: the first
+ *              activation, also the scratch the second layer reads.
+ *   h2       : nullable uint16 (bfloat16) [n_events][32][64][64].
+ */
+int retina_seednet_forward(const uint16_t *features, int32_t n_events, const float *params, float *logits,
+                           uint16_t *h1, uint16_t *h2, void *stream);
+
+/*
+ * retina_seednet_train_step - one Adam step on binary cross-entropy.
+ *
+ * Loss over the batch's N = n_events * 4096 pixels (y = labels != 0):
+ *   L = (1/N) sum pw y softplus(-z) + (1 - y) softplus(z),
+ *   pw = min(100, (N - #pos) / max(#pos, 1)),
+ * gradient by back-propagation with dL/da2 and dL/da1 stored as bfloat16 and
+ * the weights' bfloat16 rounding passed straight through; every reduction runs
+ * in a fixed order, so the step is deterministic.  Then
+ * retina_seednet_adam(params, adam_m, adam_v, grad, step, ...).
+ *
+ *   labels       : uint8 [n_events][64][64].
+ *   params, adam_m, adam_v : float32 [RETINA_SEEDNET_PARAMS], updated in place
+ *                  (m, v zero before the first step).
+ *   step         : Adam step number, >= 1.
+ *   loss         : nullable float32 [1]: L at the parameters before the step.
+ *   grad         : nullable float32 [RETINA_SEEDNET_PARAMS]: dL/dparams.
+ *   ws, ws_bytes : >= retina_seednet_train_workspace_size(n_events), 256-byte
+ *                  aligned.
+ */
+int retina_seednet_train_workspace_size(int32_t n_events, size_t *bytes);
+int retina_seednet_train_step(const uint16_t *features, const uint8_t *labels, int32_t n_events, float *params,
+                              float *adam_m, float *adam_v, int32_t step, float lr, float beta1, float beta2,
+                              float eps, float *loss, float *grad, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * retina_seednet_adam - one Adam update (Kingma & Ba, bias-corrected), float32:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * All four arrays float32 [RETINA_SEEDNET_PARAMS]; 0 < b1, b2 < 1; step >= 1.
+ */
+int retina_seednet_adam(float *params, float *adam_m, float *adam_v, const float *grad, int32_t step, float lr,
+                        float beta1, float beta2, float eps, void *stream);
+
+/*
+ * retina_topk_seeds - the K cells of largest logit per event as seeds.
+ *
+ * Ranking: larger logit first, equal logits (+0 and -0 alike) by lower cell
+ * index (row * 64 + col), NaN below every number.  Seed of cell (row, col):
+ * with counts and slope_sums (both from retina_slope_histogram with the same
+ * lo, hi) and a non-empty cell, the mean slope of the cell's hits,
+ *   (lo + (col + S_u / (2^32 n)) / s, lo + (row + S_v / (2^32 n)) / s)
+ * computed in double and rounded once to float32; otherwise the cell centre
+ * (lo + (col + 1/2) w, lo + (row + 1/2) w), w = float32((hi - lo) / 64).  A
+ * 64 x 64 cell centre can lie farther from the track it flags than the local
+ * search converges from; the centroid sits on it.
+ *
+ *   logits     : float32 [n_events][64][64].
+ *   K          : 1 .. 4096.
+ *   counts, slope_sums : both NULL or both given (layouts as above).
+ *   seeds      : float32 [n_events][K][2].
+ *   cell_idx   : nullable int32 [n_events][K].
+ */
+int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo, float hi, const int32_t *counts,
+                      const uint64_t *slope_sums, float *seeds, int32_t *cell_idx, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

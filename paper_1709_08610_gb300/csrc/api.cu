@@ -311,4 +311,64 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
                                              tracks, track_R, track_src, n_tracks, K, (cudaStream_t)stream));
 }
 
+int retina_slope_histogram(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                           float lo, float hi, float zmin, uint16_t *features, int32_t *counts, uint64_t *slope_sums,
+                           void *stream) {
+    if (n_events < 0 || n_hits < 0 || !isfinite(lo) || !isfinite(hi) || !(lo < hi) || !(zmin >= 0.f))
+        return RETINA_EINVAL;
+    if (!isfinite(64.f / (hi - lo))) return RETINA_EINVAL;
+    if (n_events == 0) return RETINA_OK;
+    if (!event_offsets || !features) return RETINA_EINVAL;
+    if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
+    return cuda_status(launch_slope_hist((const float4 *)hits, n_hits, event_offsets, n_events, lo, hi, zmin,
+                                         features, counts, (unsigned long long *)slope_sums, (cudaStream_t)stream));
+}
+
+int retina_seednet_forward(const uint16_t *features, int32_t n_events, const float *params, float *logits,
+                           uint16_t *h1, uint16_t *h2, void *stream) {
+    if (n_events < 0 || n_events > 65535) return RETINA_EINVAL;
+    if (n_events == 0) return RETINA_OK;
+    if (!features || !params || !logits || !h1) return RETINA_EINVAL;
+    return cuda_status(launch_seednet_forward(features, n_events, params, logits, h1, h2, (cudaStream_t)stream));
+}
+
+static bool valid_adam(int32_t step, float lr, float b1, float b2, float eps) {
+    return step >= 1 && isfinite(lr) && b1 > 0.f && b1 < 1.f && b2 > 0.f && b2 < 1.f && eps >= 0.f && isfinite(eps);
+}
+
+int retina_seednet_train_workspace_size(int32_t n_events, size_t *bytes) {
+    if (!bytes || n_events < 0 || n_events > 65535) return RETINA_EINVAL;
+    *bytes = seednet_train_ws_bytes(n_events);
+    return RETINA_OK;
+}
+
+int retina_seednet_train_step(const uint16_t *features, const uint8_t *labels, int32_t n_events, float *params,
+                              float *adam_m, float *adam_v, int32_t step, float lr, float beta1, float beta2,
+                              float eps, float *loss, float *grad, void *ws, size_t ws_bytes, void *stream) {
+    if (n_events < 1 || n_events > 65535 || !valid_adam(step, lr, beta1, beta2, eps)) return RETINA_EINVAL;
+    if (!features || !labels || !params || !adam_m || !adam_v) return RETINA_EINVAL;
+    if (ws_bytes < seednet_train_ws_bytes(n_events)) return RETINA_ENOSPACE;
+    if (!ws || ((uintptr_t)ws & 255u)) return RETINA_EINVAL;
+    return cuda_status(launch_seednet_train_step(features, labels, n_events, params, adam_m, adam_v, step, lr, beta1,
+                                                 beta2, eps, loss, grad, ws, (cudaStream_t)stream));
+}
+
+int retina_seednet_adam(float *params, float *adam_m, float *adam_v, const float *grad, int32_t step, float lr,
+                        float beta1, float beta2, float eps, void *stream) {
+    if (!valid_adam(step, lr, beta1, beta2, eps)) return RETINA_EINVAL;
+    if (!params || !adam_m || !adam_v || !grad) return RETINA_EINVAL;
+    return cuda_status(launch_seednet_adam(params, adam_m, adam_v, grad, step, lr, beta1, beta2, eps,
+                                           (cudaStream_t)stream));
+}
+
+int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo, float hi, const int32_t *counts,
+                      const uint64_t *slope_sums, float *seeds, int32_t *cell_idx, void *stream) {
+    if (n_events < 0 || K < 1 || K > RETINA_SEEDNET_BINS * RETINA_SEEDNET_BINS) return RETINA_EINVAL;
+    if (!isfinite(lo) || !isfinite(hi) || !(lo < hi)) return RETINA_EINVAL;
+    if (n_events == 0) return RETINA_OK;
+    if (!logits || !seeds || (counts == nullptr) != (slope_sums == nullptr)) return RETINA_EINVAL;
+    return cuda_status(launch_topk_seeds(logits, n_events, K, lo, hi, counts, (const unsigned long long *)slope_sums,
+                                         seeds, cell_idx, (cudaStream_t)stream));
+}
+
 }  // extern "C"

@@ -1,0 +1,116 @@
+"""Batched track finding over a ragged batch of events, replayable as one CUDA graph.
+
+One step is Algorithm 1 end to end on every event of the batch:
+spatial ordering of the hits (retina_prepare_hits), the starting points -
+either given (a uniform draw from the prior P_theta) or proposed by the
+learned seed network (slope histogram -> network -> top-K hit centroids) -
+the q truncated-Newton updates of all seeds in one persistent launch
+(retina_batched_search), then cluster + select (retina_extract_tracks).
+
+Every buffer is allocated once for a fixed capacity (events, hits, seeds per
+event), so ``capture`` can record the whole step in a CUDA graph and
+``replay`` re-runs it on new inputs copied into ``hits`` / ``offsets``
+(events may change size as long as the total fits the hit capacity).
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import retina as rt
+from .seednet import SeedProposer
+
+
+class BatchTracker:
+    def __init__(self, n_events: int, hit_capacity: int, seeds_per_event: int, box: "rt.Grid", opts: "rt.LsOpts",
+                 R0: float, merge_cells: float = 2.0, max_tracks: int = 1024,
+                 proposer: Optional[SeedProposer] = None, model: int = rt.VELO_SLOPES, device="cuda"):
+        E, H, n = int(n_events), int(hit_capacity), int(seeds_per_event)
+        if proposer is not None and model != rt.VELO_SLOPES:
+            raise ValueError("the learned proposer works on slope-model hits")
+        self.E, self.H, self.n = E, H, n
+        self.box, self.opts, self.R0, self.merge = box, opts, float(R0), float(merge_cells)
+        self.model, self.proposer, self.K = model, proposer, int(max_tracks)
+        dev = torch.device(device)
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.hits = torch.zeros((H, 4), **f32)
+        self.offsets = torch.zeros(E + 1, dtype=torch.int64, device=dev)
+        self.sorted = torch.empty((H, 4), **f32)
+        self.boxes = torch.empty((int(rt.lib.retina_prepare_hits_box_count(H, E)), 8), **f32)
+        self.seeds = torch.zeros((E, n, 2), **f32)
+        self.seed_offsets = torch.arange(E + 1, dtype=torch.int64, device=dev) * n
+        self.search_out = (torch.empty((E * n, 2), **f32), torch.empty((E * n,), **f32),
+                           torch.empty((E * n,), dtype=torch.uint8, device=dev))
+        self.ws = torch.empty(max(rt.batched_search_workspace_size(E), 256), dtype=torch.uint8, device=dev)
+        self.tracks = dict(tracks=torch.empty((E, self.K, 2), **f32), track_R=torch.empty((E, self.K), **f32),
+                           track_src=torch.empty((E, self.K), dtype=torch.int32, device=dev),
+                           n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    def load(self, hits: np.ndarray, offsets: np.ndarray, seeds: Optional[np.ndarray] = None):
+        """Copy a batch (host arrays) into the device buffers."""
+        if hits.shape[0] > self.H or offsets.shape[0] != self.E + 1:
+            raise ValueError("batch does not fit the tracker's capacity")
+        self.hits[:hits.shape[0]].copy_(torch.from_numpy(np.ascontiguousarray(hits, dtype=np.float32)))
+        self.offsets.copy_(torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.int64)))
+        if seeds is not None:
+            self.seeds.copy_(torch.from_numpy(np.ascontiguousarray(seeds, dtype=np.float32)).reshape(self.seeds.shape))
+
+    def step(self, stream=None):
+        """Launch the whole step on the current (or given) stream."""
+        rt.prepare_hits(self.hits, self.offsets, self.model, out=(self.sorted, self.boxes), stream=stream)
+        if self.proposer is not None:
+            self.proposer.propose(self.hits, self.offsets, self.n, seeds=self.seeds, stream=stream)
+        rt.batched_search(self.sorted, self.offsets, self.model, self.seeds.reshape(-1, 2), self.seed_offsets,
+                          self.opts, self.box, out=self.search_out, ws=self.ws, boxes=self.boxes, stream=stream)
+        th, R, st = self.search_out
+        rt.extract_tracks(th.reshape(self.E, self.n, 2), R.reshape(self.E, self.n), st.reshape(self.E, self.n),
+                          self.box, self.R0, self.merge, self.K, out=self.tracks, stream=stream)
+
+    def capture(self):
+        """Record one step in a CUDA graph (after one eager warm-up step)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        return self.graph
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+    def results(self):
+        """Per event: float64 [n_tracks, 2] track parameters (host)."""
+        n = self.tracks["n_tracks"].cpu().numpy()
+        tr = self.tracks["tracks"].cpu().numpy()
+        return [tr[e, :min(int(n[e]), self.K)].astype(np.float64) for e in range(self.E)]
+
+
+def match_efficiency(found, truth, eps: float = 1e-3):
+    """Fraction of truth tracks with a found track within eps (max norm) and
+    the number of found tracks matching none (fakes)."""
+    n_truth = n_hit = n_fake = 0
+    for f, t in zip(found, truth):
+        t = np.asarray(t, dtype=np.float64).reshape(-1, 2)
+        f = np.asarray(f, dtype=np.float64).reshape(-1, 2)
+        n_truth += len(t)
+        if len(f) == 0 or len(t) == 0:
+            n_fake += len(f)
+            continue
+        d = np.abs(f[:, None, :] - t[None, :, :]).max(-1)
+        n_hit += int((d <= eps).any(0).sum())
+        n_fake += int((~(d <= eps).any(1)).sum())
+    return (n_hit / max(n_truth, 1)), n_fake
+
+
+def recovered_fraction(found, reference, eps: float = 1e-3):
+    """Fraction of the reference method's tracks that ``found`` also has (within eps)."""
+    eff, _ = match_efficiency(found, reference, eps)
+    return eff

@@ -115,12 +115,20 @@ def _load():
     L.retina_grid_maxima_static.argtypes = [P, I32, P, F, P, P, P, P, I32, P]
     L.retina_batched_search_workspace_size.argtypes = [I32, P]
     L.retina_batched_search.argtypes = [P, I64, P, P, I32, I32, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
+    L.retina_slope_histogram.argtypes = [P, I64, P, I32, F, F, F, P, P, P, P]
+    L.retina_seednet_forward.argtypes = [P, I32, P, P, P, P, P]
+    L.retina_seednet_train_workspace_size.argtypes = [I32, P]
+    L.retina_seednet_train_step.argtypes = [P, P, I32, P, P, P, I32, F, F, F, F, P, P, P, SZ, P]
+    L.retina_seednet_adam.argtypes = [P, P, P, P, I32, F, F, F, F, P]
+    L.retina_topk_seeds.argtypes = [P, I32, I32, F, F, P, P, P, P, P]
     for name in ("retina_set_option", "retina_get_option", "retina_grid_scan_workspace_size", "retina_grid_scan",
                  "retina_grid_response_workspace_size", "retina_grid_response", "retina_alu_probe",
                  "retina_grid_maxima_static", "retina_batched_search_workspace_size", "retina_batched_search",
                  "retina_prepare_hits", "retina_work_counters",
                  "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
-                 "retina_local_search", "retina_extract_tracks"):
+                 "retina_local_search", "retina_extract_tracks", "retina_slope_histogram",
+                 "retina_seednet_forward", "retina_seednet_train_workspace_size", "retina_seednet_train_step",
+                 "retina_seednet_adam", "retina_topk_seeds"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -401,3 +409,107 @@ def extract_tracks(theta: torch.Tensor, R: torch.Tensor, status: Optional[torch.
         _p(theta), _p(R), _p(status), _p(n_valid), E, n, ctypes.byref(g), float(R0), float(merge_cells),
         _p(out["tracks"]), _p(out["track_R"]), _p(out["track_src"]), _p(out["n_tracks"]), K, _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned seed proposer
+# ---------------------------------------------------------------------------
+SEEDNET_BINS = 64
+SEEDNET_PARAMS = 4833
+
+
+def slope_histogram(hits: torch.Tensor, offsets: torch.Tensor, lo: float = -0.5, hi: float = 0.5,
+                    zmin: float = 50.0, out: Optional[torch.Tensor] = None, counts: bool = False,
+                    sums: bool = False, counts_out: Optional[torch.Tensor] = None,
+                    sums_out: Optional[torch.Tensor] = None, stream=None):
+    """bfloat16 [E, 64, 64] log1p of the slope histogram; with counts / sums also
+    the int32 counts [E, 64, 64] and the int64 (uint64 bits) in-cell position
+    sums [E, 64, 64, 2], returned as (features, counts, sums)."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    E = offsets.numel() - 1
+    dev = hits.device
+    feat = out if out is not None else torch.empty((E, 64, 64), dtype=torch.bfloat16, device=dev)
+    _dev(feat, torch.bfloat16, "out")
+    counts = counts or sums or counts_out is not None or sums_out is not None
+    sums = sums or sums_out is not None
+    cnt = counts_out if counts_out is not None else (
+        torch.empty((E, 64, 64), dtype=torch.int32, device=dev) if counts else None)
+    sm = sums_out if sums_out is not None else (
+        torch.empty((E, 64, 64, 2), dtype=torch.int64, device=dev) if sums else None)
+    if cnt is not None:
+        _dev(cnt, torch.int32, "counts_out")
+    if sm is not None:
+        _dev(sm, torch.int64, "sums_out")
+    _check("retina_slope_histogram", lib.retina_slope_histogram(
+        _p(hits), hits.shape[0], _p(offsets), E, lo, hi, zmin, _p(feat), _p(cnt), _p(sm), _stream(stream)))
+    return (feat, cnt, sm) if counts else feat
+
+
+def seednet_forward(features: torch.Tensor, params: torch.Tensor, logits: Optional[torch.Tensor] = None,
+                    h1: Optional[torch.Tensor] = None, want_h2: bool = False, stream=None):
+    """Logits float32 [E, 64, 64]; with want_h2 also (h1, h2) bfloat16 activations."""
+    _dev(features, torch.bfloat16, "features")
+    _dev(params, torch.float32, "params")
+    if params.numel() != SEEDNET_PARAMS:
+        raise ValueError("params must hold %d values" % SEEDNET_PARAMS)
+    E = features.numel() // 4096
+    dev = features.device
+    logits = logits if logits is not None else torch.empty((E, 64, 64), dtype=torch.float32, device=dev)
+    h1 = h1 if h1 is not None else torch.empty((E, 16, 64, 64), dtype=torch.bfloat16, device=dev)
+    h2 = torch.empty((E, 32, 64, 64), dtype=torch.bfloat16, device=dev) if want_h2 else None
+    _check("retina_seednet_forward", lib.retina_seednet_forward(
+        _p(features), E, _p(params), _p(logits), _p(h1), _p(h2), _stream(stream)))
+    return (logits, h1, h2) if want_h2 else logits
+
+
+def seednet_train_workspace_size(n_events: int) -> int:
+    b = ctypes.c_size_t()
+    _check("retina_seednet_train_workspace_size", lib.retina_seednet_train_workspace_size(n_events, ctypes.byref(b)))
+    return b.value
+
+
+def seednet_train_step(features: torch.Tensor, labels: torch.Tensor, params: torch.Tensor, m: torch.Tensor,
+                       v: torch.Tensor, step: int, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8,
+                       loss: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None,
+                       ws: Optional[torch.Tensor] = None, stream=None):
+    """One Adam step on the weighted BCE; params, m, v updated in place."""
+    _dev(features, torch.bfloat16, "features")
+    _dev(labels, torch.uint8, "labels")
+    for t, n in ((params, "params"), (m, "m"), (v, "v")):
+        _dev(t, torch.float32, n)
+    E = features.numel() // 4096
+    if labels.numel() != E * 4096:
+        raise ValueError("labels must match features")
+    need = seednet_train_workspace_size(E)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=features.device)
+    _check("retina_seednet_train_step", lib.retina_seednet_train_step(
+        _p(features), _p(labels), E, _p(params), _p(m), _p(v), int(step), lr, betas[0], betas[1], eps, _p(loss),
+        _p(grad), _p(ws), ws.numel(), _stream(stream)))
+
+
+def seednet_adam(params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: torch.Tensor, step: int,
+                 lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8, stream=None):
+    for t, n in ((params, "params"), (m, "m"), (v, "v"), (grad, "grad")):
+        _dev(t, torch.float32, n)
+    _check("retina_seednet_adam", lib.retina_seednet_adam(_p(params), _p(m), _p(v), _p(grad), int(step), lr,
+                                                          betas[0], betas[1], eps, _stream(stream)))
+
+
+def topk_seeds(logits: torch.Tensor, K: int, lo: float = -0.5, hi: float = 0.5, counts=None, sums=None,
+               seeds: Optional[torch.Tensor] = None, want_idx: bool = False, stream=None):
+    """float32 [E, K, 2] seeds at the K best cells - their hit centroids when
+    counts and sums (from slope_histogram) are given - and, if asked, the
+    int32 [E, K] cell indices."""
+    _dev(logits, torch.float32, "logits")
+    if counts is not None:
+        _dev(counts, torch.int32, "counts")
+        _dev(sums, torch.int64, "sums")
+    E = logits.numel() // 4096
+    dev = logits.device
+    seeds = seeds if seeds is not None else torch.empty((E, K, 2), dtype=torch.float32, device=dev)
+    idx = torch.empty((E, K), dtype=torch.int32, device=dev) if want_idx else None
+    _check("retina_topk_seeds", lib.retina_topk_seeds(_p(logits), E, K, lo, hi, _p(counts), _p(sums), _p(seeds),
+                                                      _p(idx), _stream(stream)))
+    return (seeds, idx) if want_idx else seeds

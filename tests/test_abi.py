@@ -146,3 +146,40 @@ def test_prepare_hits_rejects_and_counts():
     assert L.retina_prepare_hits(BOGUS, 10, BOGUS, 1, 1, BOGUS, BOGUS, None) == EINVAL  # in place
     assert L.retina_prepare_hits(BOGUS, 10, BOGUS, 1, 1, ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3004),
                                  None) == EINVAL  # misaligned boxes
+
+
+def test_seednet_entries_reject_before_launch():
+    OK = 0
+    # slope histogram: range, zmin, nulls; empty batch is a no-op
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, 0.5, -0.5, 50.0, BOGUS, None, None, None) == EINVAL
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, -0.5, 0.5, -1.0, BOGUS, None, None, None) == EINVAL
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, float("nan"), 0.5, 50.0, BOGUS, None, None, None) == EINVAL
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, -0.5, 0.5, 50.0, None, None, None, None) == EINVAL
+    assert L.retina_slope_histogram(ctypes.c_void_p(0x1004), 10, BOGUS, 1, -0.5, 0.5, 50.0, BOGUS, None, None, None) == EINVAL
+    assert L.retina_slope_histogram(None, 0, None, 0, -0.5, 0.5, 50.0, None, None, None, None) == OK
+    # forward: h1 is required
+    assert L.retina_seednet_forward(BOGUS, 1, BOGUS, BOGUS, None, None, None) == EINVAL
+    assert L.retina_seednet_forward(BOGUS, -1, BOGUS, BOGUS, BOGUS, None, None) == EINVAL
+    assert L.retina_seednet_forward(None, 0, None, None, None, None, None) == OK
+    # training step: Adam hyper-parameters, step, workspace
+    b = ctypes.c_size_t()
+    assert L.retina_seednet_train_workspace_size(4, ctypes.byref(b)) == OK and b.value > 4 * 4096 * 48
+    args = lambda **k: [k.get("feat", BOGUS), BOGUS, k.get("E", 4), BOGUS, BOGUS, BOGUS, k.get("step", 1),
+                        k.get("lr", 1e-3), k.get("b1", 0.9), k.get("b2", 0.999), k.get("eps", 1e-8), None, None,
+                        k.get("ws", ctypes.c_void_p(0x10000)), k.get("wsb", b.value), None]
+    assert L.retina_seednet_train_step(*args(step=0)) == EINVAL
+    assert L.retina_seednet_train_step(*args(b1=1.0)) == EINVAL
+    assert L.retina_seednet_train_step(*args(b2=0.0)) == EINVAL
+    assert L.retina_seednet_train_step(*args(lr=float("inf"))) == EINVAL
+    assert L.retina_seednet_train_step(*args(E=0)) == EINVAL
+    assert L.retina_seednet_train_step(*args(feat=None)) == EINVAL
+    assert L.retina_seednet_train_step(*args(wsb=b.value - 1)) == ENOSPACE
+    assert L.retina_seednet_train_step(*args(ws=ctypes.c_void_p(0x10010))) == EINVAL  # not 256-byte aligned
+    assert L.retina_seednet_adam(BOGUS, BOGUS, BOGUS, BOGUS, 0, 1e-3, 0.9, 0.999, 1e-8, None) == EINVAL
+    assert L.retina_seednet_adam(BOGUS, BOGUS, None, BOGUS, 1, 1e-3, 0.9, 0.999, 1e-8, None) == EINVAL
+    # top-K: K range, box
+    assert L.retina_topk_seeds(BOGUS, 1, 0, -0.5, 0.5, None, None, BOGUS, None, None) == EINVAL
+    assert L.retina_topk_seeds(BOGUS, 1, 4097, -0.5, 0.5, None, None, BOGUS, None, None) == EINVAL
+    assert L.retina_topk_seeds(BOGUS, 1, 16, 0.5, 0.5, None, None, BOGUS, None, None) == EINVAL
+    assert L.retina_topk_seeds(BOGUS, 1, 16, -0.5, 0.5, None, None, None, None, None) == EINVAL
+    assert L.retina_topk_seeds(BOGUS, 1, 16, -0.5, 0.5, BOGUS, None, BOGUS, None, None) == EINVAL  # counts w/o sums
