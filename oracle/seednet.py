@@ -17,8 +17,13 @@ written as the definitions read:
   bfloat16 where the kernels store them.
 * adam - Adam (Kingma & Ba) with bias correction.
 * top_k - the K largest logits per event (ties: lower index first), seeds at
-  the cell centres, or - given cell_centroids - at the mean slope of the hits
-  binned to the chosen cell (its centre when the cell is empty).
+  the cell centres.
+* propose_seeds - the seeds of the learned proposer: walk the cells by
+  decreasing logit; each cell splits into 4 x 4 sub-cells and gives one seed
+  per sub-cell holding at least n_min of its hits (most hits first) at the
+  mean slope of those hits; a cell with no such sub-cell gives one seed at its
+  most populated sub-cell's mean, an empty cell its centre; stop at K seeds.
+  Only the first R_MAX ranked cells are split; later ones give their centre.
 
 Parameter vector layout (4833 values): W1 [16,1,3,3] at 0, b1 [16] at 144,
 W2 [32,16,3,3] at 160, b2 [32] at 4768, W3 [32] at 4800, b3 at 4832.
@@ -189,30 +194,67 @@ def adam(params, grad, m, v, step: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def cell_centroids(hits: np.ndarray, lo: float = -0.5, hi: float = 0.5, nb: int = NB, zmin: float = 50.0):
-    """float64 [nb, nb, 2]: mean (u, v) of the hits binned to each cell (the
-    float32 slopes slope_histogram bins, averaged in double); NaN where the
-    cell is empty."""
-    u, v, bu, bv = _binned_slopes(hits, lo, hi, nb, zmin)
-    su = np.zeros((nb, nb))
-    sv = np.zeros((nb, nb))
-    cnt = np.zeros((nb, nb))
-    np.add.at(su, (bv, bu), u.astype(np.float64))
-    np.add.at(sv, (bv, bu), v.astype(np.float64))
-    np.add.at(cnt, (bv, bu), 1.0)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return np.stack([su / cnt, sv / cnt], -1)
-
-
-def top_k(logits: np.ndarray, K: int, lo: float = -0.5, hi: float = 0.5, nb: int = NB, centroids=None):
+def top_k(logits: np.ndarray, K: int, lo: float = -0.5, hi: float = 0.5, nb: int = NB):
     """Indices (v_bin * nb + u_bin) of the K largest logits (ties: lower
-    index first) and the seeds (u, v): the cell centres, or the cells' hit
-    centroids (cell_centroids) where a centroid is given and finite."""
+    index first) and the seeds (u, v) at their cell centres."""
     z = np.asarray(logits, dtype=np.float64).reshape(-1)
     order = np.lexsort((np.arange(z.size), -z))[:K]
     w = (hi - lo) / nb
     seeds = np.stack([lo + (order % nb + 0.5) * w, lo + (order // nb + 0.5) * w], 1)
-    if centroids is not None:
-        c = np.asarray(centroids, dtype=np.float64).reshape(-1, 2)[order]
-        seeds = np.where(np.isfinite(c), c, seeds)
     return order, seeds
+
+
+SUB = 4          # sub-cells per cell and axis
+R_MAX = 1024     # ranked cells that are split into sub-cells
+
+
+def propose_seeds(logits: np.ndarray, hits: np.ndarray, K: int, lo: float = -0.5, hi: float = 0.5,
+                  nb: int = NB, zmin: float = 50.0, n_min: int = 3):
+    """(seeds float64 [K, 2], cell index [K]) of the learned proposer.
+
+    Sub-cell of a hit: floor of t = (u - lo) * (4 s) in float32, s =
+    float32(nb / (hi - lo)) - four times the histogram's own t, so the cell
+    is exactly the histogram's bin and the sub-cell refines it."""
+    z = np.asarray(logits, dtype=np.float64).reshape(-1)
+    order = np.lexsort((np.arange(z.size), -z))
+    h = np.asarray(hits, dtype=np.float32)
+    keep = np.abs(h[:, 2]) >= np.float32(zmin)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = (h[:, 0] / h[:, 2]).astype(np.float32)
+        v = (h[:, 1] / h[:, 2]).astype(np.float32)
+        s4 = np.float32(nb / (hi - lo)) * np.float32(SUB)
+        fu = np.floor((u - np.float32(lo)) * s4)
+        fv = np.floor((v - np.float32(lo)) * s4)
+        nf = nb * SUB
+        ok = keep & np.isfinite(fu) & np.isfinite(fv) & (fu >= 0) & (fu < nf) & (fv >= 0) & (fv < nf)
+    u, v = u[ok].astype(np.float64), v[ok].astype(np.float64)
+    fu, fv = fu[ok].astype(np.int64), fv[ok].astype(np.int64)
+    cell = (fv // SUB) * nb + fu // SUB
+    sub = (fv % SUB) * SUB + fu % SUB
+    w = (hi - lo) / nb
+    seeds, cells = [], []
+    for r, c in enumerate(order):
+        if len(seeds) == K:
+            break
+        centre = (lo + (c % nb + 0.5) * w, lo + (c // nb + 0.5) * w)
+        if r >= R_MAX:
+            seeds.append(centre)
+            cells.append(c)
+            continue
+        mine = cell == c
+        cnt = np.bincount(sub[mine], minlength=SUB * SUB)
+        ranked = sorted(range(SUB * SUB), key=lambda q: (-cnt[q], q))
+        chosen = [q for q in ranked if cnt[q] >= n_min]
+        if not chosen and cnt.max() >= 1:
+            chosen = ranked[:1]
+        if not chosen:
+            seeds.append(centre)
+            cells.append(c)
+            continue
+        for q in chosen:
+            if len(seeds) == K:
+                break
+            sel = mine & (sub == q)
+            seeds.append((u[sel].mean(), v[sel].mean()))
+            cells.append(c)
+    return np.array(seeds, dtype=np.float64).reshape(-1, 2), np.array(cells, dtype=np.int64)

@@ -123,38 +123,58 @@ def test_top_k_ties_and_cell_centres():
     np.testing.assert_allclose(seeds[2], [0.5 - 0.5 / 64, 0.5 - 0.5 / 64])
 
 
-def test_cell_centroids_are_the_mean_of_constructed_slopes():
-    # hits built on chosen slopes inside chosen cells, at several layers and both signs of z:
-    # each centroid is the plain mean of the slopes placed there, every non-empty cell's
-    # centroid lies inside the cell, and empty cells give NaN
-    rng = np.random.default_rng(5)
-    w = 1.0 / 64
-    cells = [(3, 7), (40, 12), (63, 0), (0, 63)]           # (row = v bin, col = u bin)
-    hits, want = [], {}
-    for r, c in cells:
-        n = int(rng.integers(1, 9))
-        uu = -0.5 + (c + rng.uniform(0.05, 0.95, n)) * w
-        vv = -0.5 + (r + rng.uniform(0.05, 0.95, n)) * w
-        zz = rng.choice([-256.0, 64.0, 128.0, 512.0], n)  # powers of two: x / z gives back u exactly
-        uu = (np.float32(uu * zz) / np.float32(zz)).astype(np.float64)
-        vv = (np.float32(vv * zz) / np.float32(zz)).astype(np.float64)
-        for a, b, z in zip(uu, vv, zz):
-            hits.append((a * z, b * z, z, 0.0))
-        want[(r, c)] = (uu.mean(), vv.mean())
-    hits.append((0.0, 0.0, 10.0, 0.0))                     # |z| < zmin: not binned
-    H = np.array(hits, dtype=np.float32)
-    cen = sn.cell_centroids(H[rng.permutation(len(H))])
-    counts, _ = sn.slope_histogram(H)
-    assert np.array_equal(np.isfinite(cen[..., 0]), counts > 0)
-    for (r, c), (mu, mv) in want.items():
-        assert cen[r, c, 0] == pytest.approx(mu, abs=1e-15) and cen[r, c, 1] == pytest.approx(mv, abs=1e-15)
-        assert -0.5 + c * w <= cen[r, c, 0] < -0.5 + (c + 1) * w
-        assert -0.5 + r * w <= cen[r, c, 1] < -0.5 + (r + 1) * w
-    # top_k seeds: centroids where the cell is non-empty, centres elsewhere
-    logits = np.full(64 * 64, -5.0)
-    logits[3 * 64 + 7] = 2.0
-    logits[10] = 1.0                                       # empty cell (0, 10)
-    order, seeds = sn.top_k(logits, 2, centroids=cen)
-    assert list(order) == [3 * 64 + 7, 10]
-    assert tuple(seeds[0]) == tuple(cen[3, 7])
-    assert tuple(seeds[1]) == (-0.5 + 10.5 * w, -0.5 + 0.5 * w)
+def _hits_at(points, rng):
+    """Hits whose float32 slopes are exactly the given (u, v) (z a power of two)."""
+    rows = []
+    for a, b in points:
+        z = float(rng.choice([-256.0, 64.0, 128.0, 512.0]))
+        rows.append((a * z, b * z, z, 0.0))
+    return np.array(rows, dtype=np.float32)
+
+
+def test_propose_seeds_splits_cells_into_dense_sub_cells():
+    # constructed event: cell A holds two tracks in different sub-cells (5 and 4 hits) plus one
+    # noise hit in a third sub-cell; cell B holds 2 hits in one sub-cell and 1 in another (none
+    # reaches n_min = 3: one seed at the fuller sub-cell); cell C is empty; the rest of the
+    # cells rank below.  Expected seeds follow from the construction alone.
+    rng = np.random.default_rng(9)
+    w, ws = 1.0 / 64, 1.0 / 256
+    A, B, C = (10, 20), (30, 31), (5, 5)                     # (row, col)
+
+    def pt(cell, sr, sc, fr, fc):                           # point at fraction (fr, fc) of sub-cell (sr, sc)
+        r, c = cell
+        return (-0.5 + (4 * c + sc + fc) * ws, -0.5 + (4 * r + sr + fr) * ws)
+
+    t1 = [pt(A, 0, 1, 0.30 + 0.01 * k, 0.40) for k in range(5)]
+    t2 = [pt(A, 3, 2, 0.60, 0.70 - 0.02 * k) for k in range(4)]
+    nz = [pt(A, 2, 0, 0.5, 0.5)]
+    b1 = [pt(B, 1, 1, 0.2, 0.2), pt(B, 1, 1, 0.4, 0.6)]
+    b2 = [pt(B, 2, 3, 0.5, 0.5)]
+    pts = t1 + t2 + nz + b1 + b2
+    H = _hits_at(pts, rng)
+    H = np.concatenate([H, np.array([[1.0, 1.0, 10.0, 0.0]], np.float32)])   # |z| < zmin: ignored
+    exact = np.stack([H[:-1, 0] / H[:-1, 2], H[:-1, 1] / H[:-1, 2]], 1).astype(np.float64)
+    logits = np.full(4096, -9.0)
+    logits[A[0] * 64 + A[1]] = 3.0
+    logits[B[0] * 64 + B[1]] = 2.0
+    logits[C[0] * 64 + C[1]] = 1.0
+    seeds, cells = sn.propose_seeds(logits, H[rng.permutation(len(H))], K=6, n_min=3)
+    assert list(cells) == [A[0] * 64 + A[1]] * 2 + [B[0] * 64 + B[1]] + [C[0] * 64 + C[1]] + [0, 1]
+    np.testing.assert_allclose(seeds[0], exact[0:5].mean(0), rtol=0, atol=1e-15)   # 5 hits first
+    np.testing.assert_allclose(seeds[1], exact[5:9].mean(0), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(seeds[2], exact[10:12].mean(0), rtol=0, atol=1e-15)
+    assert tuple(seeds[3]) == (-0.5 + 5.5 * w, -0.5 + 5.5 * w)                      # empty: centre
+    assert tuple(seeds[4]) == (-0.5 + 0.5 * w, -0.5 + 0.5 * w)                      # next cells by index
+    # K cuts inside a cell; n_min = 1 gives every non-empty sub-cell, fullest first
+    s2, c2 = sn.propose_seeds(logits, H, K=1)
+    assert len(s2) == 1 and c2[0] == A[0] * 64 + A[1]
+    s3, _ = sn.propose_seeds(logits, H, K=5, n_min=1)
+    np.testing.assert_allclose(s3[2], exact[9], atol=1e-15)                          # the lone noise hit
+    np.testing.assert_allclose(s3[3], exact[10:12].mean(0), atol=1e-15)
+    np.testing.assert_allclose(s3[4], exact[12], atol=1e-15)
+    # sub-cells refine the histogram's cells exactly, including hits on cell edges
+    edge = _hits_at([(-0.5 + 7 * w, -0.5 + 9 * w), (-0.5 + 7 * w - ws / 2, 0.0)], rng)
+    counts, _ = sn.slope_histogram(edge)
+    lg = np.zeros(4096)
+    _, ce = sn.propose_seeds(lg - np.arange(4096) * 1e-3 + 10 * counts.reshape(-1), edge, K=2, n_min=1)
+    assert sorted(ce) == sorted(np.flatnonzero(counts.reshape(-1)))
