@@ -403,22 +403,16 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
  * For every hit with |z| >= zmin: u = x / z, v = y / z (float32 division),
  * column floor((u - lo) * s), row floor((v - lo) * s) with s = float32(64 /
  * (hi - lo)), all in float32; hits outside [0, 64) in either bin are dropped.
- * features[e][row][col] = bf16(log1pf(count)).  Counts and sums are exact
- * integers (integer atomics), so no result depends on the hits' order.
+ * features[e][row][col] = bf16(log1pf(count)).  Counts are exact (integer
+ * atomics), so the result does not depend on the hits' order.
  *
  *   hits, n_hits, event_offsets : as everywhere (slope-model rows).
  *   lo < hi finite, zmin >= 0.
- *   features   : uint16 (bfloat16) [n_events][64][64].
- *   counts     : nullable int32 [n_events][64][64].
- *   slope_sums : nullable uint64 [n_events][64][64][2]: per cell, the sums
- *                over its hits of round(2^32 (t - floor t)) for t = (u - lo) s
- *                and t = (v - lo) s (the hit's position inside the cell, in
- *                2^-32 units); with counts, retina_topk_seeds turns them
- *                into the cell's hit centroid.
+ *   features : uint16 (bfloat16) [n_events][64][64].
+ *   counts   : nullable int32 [n_events][64][64].
  */
 int retina_slope_histogram(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
-                           float lo, float hi, float zmin, uint16_t *features, int32_t *counts, uint64_t *slope_sums,
-                           void *stream);
+                           float lo, float hi, float zmin, uint16_t *features, int32_t *counts, void *stream);
 
 /*
  * retina_seednet_forward - logits of the 64 x 64 cells of each event.
@@ -468,26 +462,35 @@ int retina_seednet_adam(float *params, float *adam_m, float *adam_v, const float
                         float beta1, float beta2, float eps, void *stream);
 
 /*
- * retina_topk_seeds - the K cells of largest logit per event as seeds.
+ * retina_topk_seeds - K seeds per event from the ranked cells.
  *
- * Ranking: larger logit first, equal logits (+0 and -0 alike) by lower cell
- * index (row * 64 + col), NaN below every number.  Seed of cell (row, col):
- * with counts and slope_sums (both from retina_slope_histogram with the same
- * lo, hi) and a non-empty cell, the mean slope of the cell's hits,
- *   (lo + (col + S_u / (2^32 n)) / s, lo + (row + S_v / (2^32 n)) / s)
- * computed in double and rounded once to float32; otherwise the cell centre
- * (lo + (col + 1/2) w, lo + (row + 1/2) w), w = float32((hi - lo) / 64).  A
- * 64 x 64 cell centre can lie farther from the track it flags than the local
- * search converges from; the centroid sits on it.
+ * Cells are ranked by logit: larger first, equal logits (+0 and -0 alike)
+ * by lower cell index (row * 64 + col), NaN below every number.
+ * Without hits (hits == NULL): seed j is the centre of the j-th ranked cell,
+ *   (lo + (col + 1/2) w, lo + (row + 1/2) w), w = float32((hi - lo) / 64).
+ * With the event's hits: the ranked cells are walked in order and each gives
+ * seeds until K are out.  A cell splits into 4 x 4 sub-cells (sub-cell of a
+ * hit: floor((u - lo) * 4 s) in float32 with the histogram's s and zmin, so
+ * it refines the histogram's cell exactly); it gives one seed per sub-cell
+ * holding >= min_sub_hits of its hits, fullest first (ties: lower sub-cell
+ * row, then column), else one seed for its fullest non-empty sub-cell, else
+ * (empty) its centre.  A sub-cell's seed is its hits' mean slope, computed
+ * from 2^-32 fixed-point in-sub-cell positions in double and rounded once to
+ * float32.  Only the first 1024 ranked cells are split; later cells give
+ * their centre.  Two tracks often share a 64 x 64 cell while the local search
+ * converges only from a few 1e-3 in slope, hence the split.
  *
- *   logits     : float32 [n_events][64][64].
- *   K          : 1 .. 4096.
- *   counts, slope_sums : both NULL or both given (layouts as above).
- *   seeds      : float32 [n_events][K][2].
- *   cell_idx   : nullable int32 [n_events][K].
+ *   logits      : float32 [n_events][64][64].
+ *   K           : 1 .. 4096.
+ *   zmin, min_sub_hits (>= 1) : as above; lo, hi as for the histogram.
+ *   hits, n_hits, event_offsets : nullable hits (slope-model rows); offsets
+ *                 required with hits.
+ *   seeds       : float32 [n_events][K][2].
+ *   cell_idx    : nullable int32 [n_events][K]: the 64 x 64 cell of each seed.
  */
-int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo, float hi, const int32_t *counts,
-                      const uint64_t *slope_sums, float *seeds, int32_t *cell_idx, void *stream);
+int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo, float hi, float zmin,
+                      int32_t min_sub_hits, const float *hits, int64_t n_hits, const int64_t *event_offsets,
+                      float *seeds, int32_t *cell_idx, void *stream);
 
 #ifdef __cplusplus
 }

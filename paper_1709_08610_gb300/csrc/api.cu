@@ -312,8 +312,7 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
 }
 
 int retina_slope_histogram(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
-                           float lo, float hi, float zmin, uint16_t *features, int32_t *counts, uint64_t *slope_sums,
-                           void *stream) {
+                           float lo, float hi, float zmin, uint16_t *features, int32_t *counts, void *stream) {
     if (n_events < 0 || n_hits < 0 || !isfinite(lo) || !isfinite(hi) || !(lo < hi) || !(zmin >= 0.f))
         return RETINA_EINVAL;
     if (!isfinite(64.f / (hi - lo))) return RETINA_EINVAL;
@@ -321,7 +320,7 @@ int retina_slope_histogram(const float *hits, int64_t n_hits, const int64_t *eve
     if (!event_offsets || !features) return RETINA_EINVAL;
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
     return cuda_status(launch_slope_hist((const float4 *)hits, n_hits, event_offsets, n_events, lo, hi, zmin,
-                                         features, counts, (unsigned long long *)slope_sums, (cudaStream_t)stream));
+                                         features, counts, (cudaStream_t)stream));
 }
 
 int retina_seednet_forward(const uint16_t *features, int32_t n_events, const float *params, float *logits,
@@ -361,14 +360,18 @@ int retina_seednet_adam(float *params, float *adam_m, float *adam_v, const float
                                            (cudaStream_t)stream));
 }
 
-int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo, float hi, const int32_t *counts,
-                      const uint64_t *slope_sums, float *seeds, int32_t *cell_idx, void *stream) {
+int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo, float hi, float zmin,
+                      int32_t min_sub_hits, const float *hits, int64_t n_hits, const int64_t *event_offsets,
+                      float *seeds, int32_t *cell_idx, void *stream) {
     if (n_events < 0 || K < 1 || K > RETINA_SEEDNET_BINS * RETINA_SEEDNET_BINS) return RETINA_EINVAL;
-    if (!isfinite(lo) || !isfinite(hi) || !(lo < hi)) return RETINA_EINVAL;
+    if (!isfinite(lo) || !isfinite(hi) || !(lo < hi) || !isfinite(256.f / (hi - lo))) return RETINA_EINVAL;
+    if (!(zmin >= 0.f) || min_sub_hits < 1 || n_hits < 0) return RETINA_EINVAL;
     if (n_events == 0) return RETINA_OK;
-    if (!logits || !seeds || (counts == nullptr) != (slope_sums == nullptr)) return RETINA_EINVAL;
-    return cuda_status(launch_topk_seeds(logits, n_events, K, lo, hi, counts, (const unsigned long long *)slope_sums,
-                                         seeds, cell_idx, (cudaStream_t)stream));
+    if (!logits || !seeds) return RETINA_EINVAL;
+    if (hits && (!event_offsets || !aligned16(hits))) return RETINA_EINVAL;
+    return cuda_status(launch_propose_seeds(logits, n_events, K, lo, hi, zmin, min_sub_hits, (const float4 *)hits,
+                                            hits ? n_hits : 0, event_offsets, seeds, cell_idx,
+                                            (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -51,8 +51,7 @@ size_t extract_smem_bytes(int n_points);
 
 // learned seed proposer
 cudaError_t launch_slope_hist(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, float lo, float hi,
-                              float zmin, uint16_t *feat, int32_t *counts, unsigned long long *sums,
-                              cudaStream_t st);
+                              float zmin, uint16_t *feat, int32_t *counts, cudaStream_t st);
 cudaError_t launch_seednet_forward(const uint16_t *feat, int n_events, const float *params, float *logits,
                                    uint16_t *h1, uint16_t *h2, cudaStream_t st);
 size_t seednet_train_ws_bytes(int n_events);
@@ -61,7 +60,8 @@ cudaError_t launch_seednet_train_step(const uint16_t *feat, const uint8_t *label
                                       float *loss_out, float *grad_out, void *ws, cudaStream_t st);
 cudaError_t launch_seednet_adam(float *params, float *m, float *v, const float *grad, int step, float lr, float b1,
                                 float b2, float eps, cudaStream_t st);
-cudaError_t launch_topk_seeds(const float *logits, int n_events, int K, float lo, float hi, const int32_t *counts,
-                              const unsigned long long *sums, float *seeds, int32_t *idx, cudaStream_t st);
+cudaError_t launch_propose_seeds(const float *logits, int n_events, int K, float lo, float hi, float zmin, int n_min,
+                                 const float4 *hits, int64_t n_hits, const int64_t *off, float *seeds, int32_t *idx,
+                                 cudaStream_t st);
 
 }  // namespace retina

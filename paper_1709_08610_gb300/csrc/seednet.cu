@@ -35,24 +35,12 @@ __device__ __forceinline__ float bf16_val(uint16_t u) { return __uint_as_float((
 // ---------------------------------------------------------------------------
 // S7: slope histogram
 // ---------------------------------------------------------------------------
-// Per cell: count, and (optionally) the sums of the hits' in-cell positions
-// frac = t - floor(t), t = (u - lo) * s, as 2^-32 fixed point (64-bit integer
-// atomics: the sums, like the counts, do not depend on the hits' order).
-constexpr float FRAC_ONE = 4294967296.f;  // 2^32
-
 __global__ void __launch_bounds__(256)
 slope_hist_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, float lo,
-                  float scale, float zmin, uint16_t *__restrict__ feat, int32_t *__restrict__ counts_out,
-                  unsigned long long *__restrict__ sums_out) {
-    extern __shared__ __align__(16) unsigned char hsm[];
-    int *cnt = reinterpret_cast<int *>(hsm);
-    unsigned long long *su = reinterpret_cast<unsigned long long *>(hsm + SN_PX * sizeof(int));
-    const bool want_sums = sums_out != nullptr;
+                  float scale, float zmin, uint16_t *__restrict__ feat, int32_t *__restrict__ counts_out) {
+    __shared__ int cnt[SN_PX];
     const int e = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < SN_PX; i += blockDim.x) {
-        cnt[i] = 0;
-        if (want_sums) su[2 * i] = su[2 * i + 1] = 0ull;
-    }
+    for (int i = tid; i < SN_PX; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
@@ -60,26 +48,14 @@ slope_hist_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t
         const float4 h = __ldg(hits + k);
         if (!(fabsf(h.z) >= zmin)) continue;
         // decided in float32 exactly as written: u = x / z, bin = floor((u - lo) * scale)
-        const float tu = __fmul_rn(__fsub_rn(__fdiv_rn(h.x, h.z), lo), scale);
-        const float tv = __fmul_rn(__fsub_rn(__fdiv_rn(h.y, h.z), lo), scale);
-        const float bu = floorf(tu), bv = floorf(tv);
-        if (bu >= 0.f && bu < (float)SN && bv >= 0.f && bv < (float)SN) {
-            const int c = (int)bv * SN + (int)bu;
-            atomicAdd(&cnt[c], 1);
-            if (want_sums) {  // t - floor(t) is exact in float32; scaling by 2^32 is exact
-                atomicAdd(&su[2 * c], (unsigned long long)__float2ll_rn(__fsub_rn(tu, bu) * FRAC_ONE));
-                atomicAdd(&su[2 * c + 1], (unsigned long long)__float2ll_rn(__fsub_rn(tv, bv) * FRAC_ONE));
-            }
-        }
+        const float bu = floorf(__fmul_rn(__fsub_rn(__fdiv_rn(h.x, h.z), lo), scale));
+        const float bv = floorf(__fmul_rn(__fsub_rn(__fdiv_rn(h.y, h.z), lo), scale));
+        if (bu >= 0.f && bu < (float)SN && bv >= 0.f && bv < (float)SN) atomicAdd(&cnt[(int)bv * SN + (int)bu], 1);
     }
     __syncthreads();
     for (int i = tid; i < SN_PX; i += blockDim.x) {
         feat[(int64_t)e * SN_PX + i] = bf16_bits(log1pf((float)cnt[i]));
         if (counts_out) counts_out[(int64_t)e * SN_PX + i] = cnt[i];
-        if (want_sums) {
-            sums_out[((int64_t)e * SN_PX + i) * 2] = su[2 * i];
-            sums_out[((int64_t)e * SN_PX + i) * 2 + 1] = su[2 * i + 1];
-        }
     }
 }
 
@@ -378,21 +354,61 @@ __global__ void adam_kernel(float *__restrict__ params, float *__restrict__ m, f
 // ---------------------------------------------------------------------------
 // S9: top-K seeds
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
-topk_seeds_kernel(const float *__restrict__ logits, int K, float lo, float w, float scale,
-                  const int32_t *__restrict__ counts, const unsigned long long *__restrict__ sums,
-                  float *__restrict__ seeds, int32_t *__restrict__ idx_out) {
-    __shared__ uint64_t keys[SN_PX];
+// One CTA (1024 threads) per event.  Cells are ranked by logit (bitonic sort
+// of (order key, index)); with hits, the first R_MAX ranked cells are split
+// into SUB x SUB sub-cells: pass 1 counts each sub-cell's hits, a block scan
+// hands out seed slots (one per sub-cell with >= n_min hits, fullest first;
+// else one for the fullest non-empty sub-cell; else the cell centre), pass 2
+// sums the in-sub-cell positions of the hits of every slot (2^-32 fixed
+// point, integer atomics: order-independent), and each slot's seed is its
+// hits' mean slope.
+constexpr int SUB = 4, R_MAX = 1024, PROP_THREADS = 1024;
+static_assert(R_MAX == PROP_THREADS, "one thread per splittable ranked cell");
+constexpr float FRAC_ONE = 4294967296.f;  // 2^32
+
+size_t propose_smem_bytes(int K) {
+    return (size_t)SN_PX * 8 + (size_t)K * 16 + (size_t)R_MAX * SUB * SUB * 4 + (size_t)K * 12 + 64 * 4 +
+           (size_t)SN_PX * 2;
+}
+
+// sub-cell (fine) bins of a hit, float32 as the histogram: t = (u - lo) * (4 s)
+__device__ __forceinline__ bool fine_bins(const float4 h, float lo, float s4, float zmin, float &tu, float &tv,
+                                          int &fu, int &fv) {
+    if (!(fabsf(h.z) >= zmin)) return false;
+    tu = __fmul_rn(__fsub_rn(__fdiv_rn(h.x, h.z), lo), s4);
+    tv = __fmul_rn(__fsub_rn(__fdiv_rn(h.y, h.z), lo), s4);
+    const float bu = floorf(tu), bv = floorf(tv);
+    if (!(bu >= 0.f && bu < (float)(SN * SUB) && bv >= 0.f && bv < (float)(SN * SUB))) return false;
+    fu = (int)bu;
+    fv = (int)bv;
+    return true;
+}
+
+__global__ void __launch_bounds__(PROP_THREADS)
+propose_seeds_kernel(const float *__restrict__ logits, int K, float lo, float w, float scale, float zmin, int n_min,
+                     const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
+                     float *__restrict__ seeds, int32_t *__restrict__ idx_out) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    uint64_t *keys = reinterpret_cast<uint64_t *>(psm);                          // [4096]
+    unsigned long long *s_sum = reinterpret_cast<unsigned long long *>(keys + SN_PX);  // [K][2]
+    int *sub = reinterpret_cast<int *>(s_sum + 2 * (size_t)K);                   // [R_MAX][16]: counts, then slots
+    int *s_cnt = sub + R_MAX * SUB * SUB;                                        // [K]
+    int *s_cell = s_cnt + K;                                                     // [K]
+    int *s_fine = s_cell + K;                                                    // [K]: fine bin, -1 = centre
+    int *scan = s_fine + K;                                                      // [64]
+    int16_t *rank = reinterpret_cast<int16_t *>(scan + 64);                      // [4096]
     const int e = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < SN_PX; i += 1024) {
+    const float s4 = scale * (float)SUB;
+    for (int i = tid; i < SN_PX; i += PROP_THREADS) {
         const float z = logits[(int64_t)e * SN_PX + i] + 0.f;              // -0 -> +0: equal logits tie
         const uint32_t k = isnan(z) ? 0u : float_order_key(z);            // NaN ranks below every number
         keys[i] = ((uint64_t)(~k) << 32) | (uint32_t)i;                    // larger z first, then lower index
     }
+    for (int i = tid; i < R_MAX * SUB * SUB; i += PROP_THREADS) sub[i] = 0;
     __syncthreads();
     for (int k = 2; k <= SN_PX; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < SN_PX; i += 1024) {
+            for (int i = tid; i < SN_PX; i += PROP_THREADS) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
                     const uint64_t a = keys[i], b = keys[ixj];
@@ -405,21 +421,123 @@ topk_seeds_kernel(const float *__restrict__ logits, int K, float lo, float w, fl
             __syncthreads();
         }
     }
-    for (int q = tid; q < K; q += 1024) {
-        const int i = (int)(uint32_t)keys[q];
+    for (int q = tid; q < SN_PX; q += PROP_THREADS) rank[(int)(uint32_t)keys[q]] = (int16_t)q;
+    __syncthreads();
+    int64_t hb = 0, he = 0;
+    if (hits) event_range(off, n_hits, e, hb, he);
+    // pass 1: hits per sub-cell of the first R_MAX ranked cells
+    for (int64_t k = hb + tid; k < he; k += PROP_THREADS) {
+        float tu, tv;
+        int fu, fv;
+        if (!fine_bins(__ldg(hits + k), lo, s4, zmin, tu, tv, fu, fv)) continue;
+        const int r = rank[(fv / SUB) * SN + fu / SUB];
+        if (r < R_MAX) atomicAdd(&sub[r * SUB * SUB + (fv % SUB) * SUB + fu % SUB], 1);
+    }
+    __syncthreads();
+    // schedule: thread r owns ranked cell r (< R_MAX = blockDim)
+    const int r = tid;
+    const int cell_r = (int)(uint32_t)keys[r];
+    int cnt[SUB * SUB];
+    int nq = 0, best = -1, best_cnt = 0;
+#pragma unroll
+    for (int q = 0; q < SUB * SUB; ++q) {
+        cnt[q] = sub[r * SUB * SUB + q];
+        nq += cnt[q] >= n_min;
+        if (cnt[q] > best_cnt) {  // strict: the lowest sub-cell index wins ties
+            best = q;
+            best_cnt = cnt[q];
+        }
+    }
+    const int thr = nq > 0 ? n_min : (best >= 0 ? best_cnt : INT32_MAX);
+    const int e_r = nq > 0 ? nq : 1;
+    // block exclusive scan of e_r
+    int incl = e_r;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) scan[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = scan[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        scan[32 + lane] = t;  // inclusive scan of the warp totals
+    }
+    __syncthreads();
+    const int off_r = (wid > 0 ? scan[32 + wid - 1] : 0) + incl - e_r;
+    const int total_split = scan[32 + 31];
+    // slots: sub-cells of ranked cell r in order (most hits, then lower index)
+    int k_out = 0;
+#pragma unroll
+    for (int q = 0; q < SUB * SUB; ++q) {
+        int slot = -1;
+        if (cnt[q] >= thr && (nq > 0 || q == best)) {
+            int pos = 0;
+#pragma unroll
+            for (int q2 = 0; q2 < SUB * SUB; ++q2)
+                pos += (cnt[q2] >= thr && (nq > 0 || q2 == best)) &&
+                       (cnt[q2] > cnt[q] || (cnt[q2] == cnt[q] && q2 < q));
+            const int sl = off_r + pos;
+            if (sl < K) {
+                slot = sl;
+                s_cell[sl] = cell_r;
+                s_fine[sl] = ((cell_r / SN) * SUB + q / SUB) * (SN * SUB) + (cell_r % SN) * SUB + q % SUB;
+                s_cnt[sl] = 0;
+                s_sum[2 * sl] = s_sum[2 * sl + 1] = 0ull;
+            }
+            ++k_out;
+        }
+        sub[r * SUB * SUB + q] = slot;  // every thread read its own counts above
+    }
+    if (k_out == 0 && off_r < K) {  // empty cell: its centre
+        s_cell[off_r] = cell_r;
+        s_fine[off_r] = -1;
+    }
+    // cells ranked past R_MAX: their centres
+    for (int q = R_MAX + tid; q < SN_PX; q += PROP_THREADS) {
+        const int sl = total_split + (q - R_MAX);
+        if (sl < K) {
+            s_cell[sl] = (int)(uint32_t)keys[q];
+            s_fine[sl] = -1;
+        }
+    }
+    __syncthreads();
+    // pass 2: position sums of each slot's hits
+    for (int64_t k = hb + tid; k < he; k += PROP_THREADS) {
+        float tu, tv;
+        int fu, fv;
+        if (!fine_bins(__ldg(hits + k), lo, s4, zmin, tu, tv, fu, fv)) continue;
+        const int rr = rank[(fv / SUB) * SN + fu / SUB];
+        if (rr >= R_MAX) continue;
+        const int sl = sub[rr * SUB * SUB + (fv % SUB) * SUB + fu % SUB];
+        if (sl < 0) continue;
+        atomicAdd(&s_cnt[sl], 1);  // t - floor(t) is exact in float32; scaling by 2^32 is exact
+        atomicAdd(&s_sum[2 * sl], (unsigned long long)__float2ll_rn(__fsub_rn(tu, (float)fu) * FRAC_ONE));
+        atomicAdd(&s_sum[2 * sl + 1], (unsigned long long)__float2ll_rn(__fsub_rn(tv, (float)fv) * FRAC_ONE));
+    }
+    __syncthreads();
+    for (int q = tid; q < K; q += PROP_THREADS) {
         const int64_t o = (int64_t)e * K + q;
-        const int col = i % SN, row = i / SN;
-        float su = __fmaf_rn((float)col + 0.5f, w, lo), sv = __fmaf_rn((float)row + 0.5f, w, lo);
-        const int c = counts ? counts[(int64_t)e * SN_PX + i] : 0;
-        if (c > 0) {  // hit centroid: lo + (bin + mean frac) / scale, in double, rounded once
-            const double n = (double)c;
-            const unsigned long long *sp = sums + ((int64_t)e * SN_PX + i) * 2;
-            su = (float)((double)lo + ((double)col + (double)sp[0] / n * 0x1p-32) / (double)scale);
-            sv = (float)((double)lo + ((double)row + (double)sp[1] / n * 0x1p-32) / (double)scale);
+        const int c = s_cell[q], f = s_fine[q], n = s_cnt[q];
+        float su, sv;
+        if (f >= 0 && n > 0) {  // mean slope: lo + (fine bin + mean frac) / (4 s), in double, rounded once
+            const double dn = (double)n;
+            su = (float)((double)lo + ((double)(f % (SN * SUB)) + (double)s_sum[2 * q] / dn * 0x1p-32) / (double)s4);
+            sv = (float)((double)lo + ((double)(f / (SN * SUB)) + (double)s_sum[2 * q + 1] / dn * 0x1p-32) /
+                                          (double)s4);
+        } else {
+            su = __fmaf_rn((float)(c % SN) + 0.5f, w, lo);
+            sv = __fmaf_rn((float)(c / SN) + 0.5f, w, lo);
         }
         seeds[2 * o] = su;
         seeds[2 * o + 1] = sv;
-        if (idx_out) idx_out[o] = i;
+        if (idx_out) idx_out[o] = c;
     }
 }
 
@@ -429,13 +547,8 @@ topk_seeds_kernel(const float *__restrict__ logits, int K, float lo, float w, fl
 static float hist_scale(float lo, float hi) { return (float)((double)SN / ((double)hi - (double)lo)); }
 
 cudaError_t launch_slope_hist(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, float lo, float hi,
-                              float zmin, uint16_t *feat, int32_t *counts, unsigned long long *sums,
-                              cudaStream_t st) {
-    const size_t smem = SN_PX * sizeof(int) + (sums ? SN_PX * 2 * sizeof(unsigned long long) : 0);
-    cudaError_t err = ensure_dynamic_smem(reinterpret_cast<const void *>(slope_hist_kernel), smem);
-    if (err != cudaSuccess) return err;
-    slope_hist_kernel<<<n_events, 256, smem, st>>>(hits, n_hits, off, lo, hist_scale(lo, hi), zmin, feat, counts,
-                                                   sums);
+                              float zmin, uint16_t *feat, int32_t *counts, cudaStream_t st) {
+    slope_hist_kernel<<<n_events, 256, 0, st>>>(hits, n_hits, off, lo, hist_scale(lo, hi), zmin, feat, counts);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -527,10 +640,15 @@ cudaError_t launch_seednet_adam(float *params, float *m, float *v, const float *
     return cudaGetLastError();
 }
 
-cudaError_t launch_topk_seeds(const float *logits, int n_events, int K, float lo, float hi, const int32_t *counts,
-                              const unsigned long long *sums, float *seeds, int32_t *idx, cudaStream_t st) {
+cudaError_t launch_propose_seeds(const float *logits, int n_events, int K, float lo, float hi, float zmin, int n_min,
+                                 const float4 *hits, int64_t n_hits, const int64_t *off, float *seeds, int32_t *idx,
+                                 cudaStream_t st) {
     const float w = (float)(((double)hi - (double)lo) / SN);
-    topk_seeds_kernel<<<n_events, 1024, 0, st>>>(logits, K, lo, w, hist_scale(lo, hi), counts, sums, seeds, idx);
+    const size_t smem = propose_smem_bytes(K);
+    cudaError_t err = ensure_dynamic_smem(reinterpret_cast<const void *>(propose_seeds_kernel), smem);
+    if (err != cudaSuccess) return err;
+    propose_seeds_kernel<<<n_events, PROP_THREADS, smem, st>>>(logits, K, lo, w, hist_scale(lo, hi), zmin, n_min,
+                                                               hits, n_hits, off, seeds, idx);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -115,12 +115,12 @@ def _load():
     L.retina_grid_maxima_static.argtypes = [P, I32, P, F, P, P, P, P, I32, P]
     L.retina_batched_search_workspace_size.argtypes = [I32, P]
     L.retina_batched_search.argtypes = [P, I64, P, P, I32, I32, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
-    L.retina_slope_histogram.argtypes = [P, I64, P, I32, F, F, F, P, P, P, P]
+    L.retina_slope_histogram.argtypes = [P, I64, P, I32, F, F, F, P, P, P]
     L.retina_seednet_forward.argtypes = [P, I32, P, P, P, P, P]
     L.retina_seednet_train_workspace_size.argtypes = [I32, P]
     L.retina_seednet_train_step.argtypes = [P, P, I32, P, P, P, I32, F, F, F, F, P, P, P, SZ, P]
     L.retina_seednet_adam.argtypes = [P, P, P, P, I32, F, F, F, F, P]
-    L.retina_topk_seeds.argtypes = [P, I32, I32, F, F, P, P, P, P, P]
+    L.retina_topk_seeds.argtypes = [P, I32, I32, F, F, F, I32, P, I64, P, P, P, P]
     for name in ("retina_set_option", "retina_get_option", "retina_grid_scan_workspace_size", "retina_grid_scan",
                  "retina_grid_response_workspace_size", "retina_grid_response", "retina_alu_probe",
                  "retina_grid_maxima_static", "retina_batched_search_workspace_size", "retina_batched_search",
@@ -420,30 +420,22 @@ SEEDNET_PARAMS = 4833
 
 def slope_histogram(hits: torch.Tensor, offsets: torch.Tensor, lo: float = -0.5, hi: float = 0.5,
                     zmin: float = 50.0, out: Optional[torch.Tensor] = None, counts: bool = False,
-                    sums: bool = False, counts_out: Optional[torch.Tensor] = None,
-                    sums_out: Optional[torch.Tensor] = None, stream=None):
-    """bfloat16 [E, 64, 64] log1p of the slope histogram; with counts / sums also
-    the int32 counts [E, 64, 64] and the int64 (uint64 bits) in-cell position
-    sums [E, 64, 64, 2], returned as (features, counts, sums)."""
+                    counts_out: Optional[torch.Tensor] = None, stream=None):
+    """bfloat16 [E, 64, 64] log1p of the slope histogram (and the int32 counts if asked)."""
     _dev(hits, torch.float32, "hits", 4)
     _dev(offsets, torch.int64, "offsets")
     E = offsets.numel() - 1
     dev = hits.device
     feat = out if out is not None else torch.empty((E, 64, 64), dtype=torch.bfloat16, device=dev)
     _dev(feat, torch.bfloat16, "out")
-    counts = counts or sums or counts_out is not None or sums_out is not None
-    sums = sums or sums_out is not None
+    counts = counts or counts_out is not None
     cnt = counts_out if counts_out is not None else (
         torch.empty((E, 64, 64), dtype=torch.int32, device=dev) if counts else None)
-    sm = sums_out if sums_out is not None else (
-        torch.empty((E, 64, 64, 2), dtype=torch.int64, device=dev) if sums else None)
     if cnt is not None:
         _dev(cnt, torch.int32, "counts_out")
-    if sm is not None:
-        _dev(sm, torch.int64, "sums_out")
     _check("retina_slope_histogram", lib.retina_slope_histogram(
-        _p(hits), hits.shape[0], _p(offsets), E, lo, hi, zmin, _p(feat), _p(cnt), _p(sm), _stream(stream)))
-    return (feat, cnt, sm) if counts else feat
+        _p(hits), hits.shape[0], _p(offsets), E, lo, hi, zmin, _p(feat), _p(cnt), _stream(stream)))
+    return (feat, cnt) if counts else feat
 
 
 def seednet_forward(features: torch.Tensor, params: torch.Tensor, logits: Optional[torch.Tensor] = None,
@@ -497,19 +489,21 @@ def seednet_adam(params: torch.Tensor, m: torch.Tensor, v: torch.Tensor, grad: t
                                                           betas[0], betas[1], eps, _stream(stream)))
 
 
-def topk_seeds(logits: torch.Tensor, K: int, lo: float = -0.5, hi: float = 0.5, counts=None, sums=None,
-               seeds: Optional[torch.Tensor] = None, want_idx: bool = False, stream=None):
-    """float32 [E, K, 2] seeds at the K best cells - their hit centroids when
-    counts and sums (from slope_histogram) are given - and, if asked, the
-    int32 [E, K] cell indices."""
+def topk_seeds(logits: torch.Tensor, K: int, lo: float = -0.5, hi: float = 0.5, hits=None, offsets=None,
+               zmin: float = 50.0, min_sub_hits: int = 3, seeds: Optional[torch.Tensor] = None,
+               want_idx: bool = False, stream=None):
+    """float32 [E, K, 2] seeds from the ranked cells - cell centres, or with the
+    events' hits the sub-cell hit means - and, if asked, int32 [E, K] cells."""
     _dev(logits, torch.float32, "logits")
-    if counts is not None:
-        _dev(counts, torch.int32, "counts")
-        _dev(sums, torch.int64, "sums")
+    n_hits = 0
+    if hits is not None:
+        _dev(hits, torch.float32, "hits", 4)
+        _dev(offsets, torch.int64, "offsets")
+        n_hits = hits.shape[0]
     E = logits.numel() // 4096
     dev = logits.device
     seeds = seeds if seeds is not None else torch.empty((E, K, 2), dtype=torch.float32, device=dev)
     idx = torch.empty((E, K), dtype=torch.int32, device=dev) if want_idx else None
-    _check("retina_topk_seeds", lib.retina_topk_seeds(_p(logits), E, K, lo, hi, _p(counts), _p(sums), _p(seeds),
-                                                      _p(idx), _stream(stream)))
+    _check("retina_topk_seeds", lib.retina_topk_seeds(_p(logits), E, K, lo, hi, zmin, int(min_sub_hits), _p(hits),
+                                                      n_hits, _p(offsets), _p(seeds), _p(idx), _stream(stream)))
     return (seeds, idx) if want_idx else seeds

@@ -115,19 +115,21 @@ class TrainState:
 
 
 class SeedProposer:
-    """Histogram -> network -> top-K hit-centroid seeds, on the current stream.
+    """Histogram -> network -> ranked cells -> seeds at dense sub-cells, on the
+    current stream.
 
     ``propose`` reuses its buffers while the event count stays the same, so it
     can be captured in a CUDA graph together with the search that follows.
     """
 
-    def __init__(self, params, lo: float = -0.5, hi: float = 0.5, zmin: float = 50.0, device="cuda"):
+    def __init__(self, params, lo: float = -0.5, hi: float = 0.5, zmin: float = 50.0, min_sub_hits: int = 3,
+                 device="cuda"):
         if isinstance(params, np.ndarray):
             params = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).to(device)
         if params.numel() != N_PARAMS:
             raise ValueError("expected %d parameters" % N_PARAMS)
         self.params = params
-        self.lo, self.hi, self.zmin = float(lo), float(hi), float(zmin)
+        self.lo, self.hi, self.zmin, self.min_sub_hits = float(lo), float(hi), float(zmin), int(min_sub_hits)
         self._E = -1
 
     @staticmethod
@@ -138,8 +140,6 @@ class SeedProposer:
     def _buffers(self, E: int, dev):
         if E != self._E:
             self.feat = torch.empty((E, 64, 64), dtype=torch.bfloat16, device=dev)
-            self.counts = torch.empty((E, 64, 64), dtype=torch.int32, device=dev)
-            self.sums = torch.empty((E, 64, 64, 2), dtype=torch.int64, device=dev)
             self.logits = torch.empty((E, 64, 64), dtype=torch.float32, device=dev)
             self.h1 = torch.empty((E, 16, 64, 64), dtype=torch.bfloat16, device=dev)
             self._E = E
@@ -149,8 +149,7 @@ class SeedProposer:
         """float32 [E, K, 2] seeds for the events of (hits, offsets)."""
         E = offsets.numel() - 1
         self._buffers(E, hits.device)
-        rt.slope_histogram(hits, offsets, self.lo, self.hi, self.zmin, out=self.feat, counts_out=self.counts,
-                           sums_out=self.sums, stream=stream)
+        rt.slope_histogram(hits, offsets, self.lo, self.hi, self.zmin, out=self.feat, stream=stream)
         rt.seednet_forward(self.feat, self.params, logits=self.logits, h1=self.h1, stream=stream)
-        return rt.topk_seeds(self.logits, K, self.lo, self.hi, counts=self.counts, sums=self.sums, seeds=seeds,
-                             stream=stream)
+        return rt.topk_seeds(self.logits, K, self.lo, self.hi, hits=hits, offsets=offsets, zmin=self.zmin,
+                             min_sub_hits=self.min_sub_hits, seeds=seeds, stream=stream)

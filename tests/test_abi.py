@@ -151,12 +151,12 @@ def test_prepare_hits_rejects_and_counts():
 def test_seednet_entries_reject_before_launch():
     OK = 0
     # slope histogram: range, zmin, nulls; empty batch is a no-op
-    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, 0.5, -0.5, 50.0, BOGUS, None, None, None) == EINVAL
-    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, -0.5, 0.5, -1.0, BOGUS, None, None, None) == EINVAL
-    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, float("nan"), 0.5, 50.0, BOGUS, None, None, None) == EINVAL
-    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, -0.5, 0.5, 50.0, None, None, None, None) == EINVAL
-    assert L.retina_slope_histogram(ctypes.c_void_p(0x1004), 10, BOGUS, 1, -0.5, 0.5, 50.0, BOGUS, None, None, None) == EINVAL
-    assert L.retina_slope_histogram(None, 0, None, 0, -0.5, 0.5, 50.0, None, None, None, None) == OK
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, 0.5, -0.5, 50.0, BOGUS, None, None) == EINVAL
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, -0.5, 0.5, -1.0, BOGUS, None, None) == EINVAL
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, float("nan"), 0.5, 50.0, BOGUS, None, None) == EINVAL
+    assert L.retina_slope_histogram(BOGUS, 10, BOGUS, 1, -0.5, 0.5, 50.0, None, None, None) == EINVAL
+    assert L.retina_slope_histogram(ctypes.c_void_p(0x1004), 10, BOGUS, 1, -0.5, 0.5, 50.0, BOGUS, None, None) == EINVAL
+    assert L.retina_slope_histogram(None, 0, None, 0, -0.5, 0.5, 50.0, None, None, None) == OK
     # forward: h1 is required
     assert L.retina_seednet_forward(BOGUS, 1, BOGUS, BOGUS, None, None, None) == EINVAL
     assert L.retina_seednet_forward(BOGUS, -1, BOGUS, BOGUS, BOGUS, None, None) == EINVAL
@@ -177,9 +177,13 @@ def test_seednet_entries_reject_before_launch():
     assert L.retina_seednet_train_step(*args(ws=ctypes.c_void_p(0x10010))) == EINVAL  # not 256-byte aligned
     assert L.retina_seednet_adam(BOGUS, BOGUS, BOGUS, BOGUS, 0, 1e-3, 0.9, 0.999, 1e-8, None) == EINVAL
     assert L.retina_seednet_adam(BOGUS, BOGUS, None, BOGUS, 1, 1e-3, 0.9, 0.999, 1e-8, None) == EINVAL
-    # top-K: K range, box
-    assert L.retina_topk_seeds(BOGUS, 1, 0, -0.5, 0.5, None, None, BOGUS, None, None) == EINVAL
-    assert L.retina_topk_seeds(BOGUS, 1, 4097, -0.5, 0.5, None, None, BOGUS, None, None) == EINVAL
-    assert L.retina_topk_seeds(BOGUS, 1, 16, 0.5, 0.5, None, None, BOGUS, None, None) == EINVAL
-    assert L.retina_topk_seeds(BOGUS, 1, 16, -0.5, 0.5, None, None, None, None, None) == EINVAL
-    assert L.retina_topk_seeds(BOGUS, 1, 16, -0.5, 0.5, BOGUS, None, BOGUS, None, None) == EINVAL  # counts w/o sums
+    # top-K: K range, box, n_min, hits without offsets
+    T = lambda *a: L.retina_topk_seeds(*a)
+    assert T(BOGUS, 1, 0, -0.5, 0.5, 50.0, 3, None, 0, None, BOGUS, None, None) == EINVAL
+    assert T(BOGUS, 1, 4097, -0.5, 0.5, 50.0, 3, None, 0, None, BOGUS, None, None) == EINVAL
+    assert T(BOGUS, 1, 16, 0.5, 0.5, 50.0, 3, None, 0, None, BOGUS, None, None) == EINVAL
+    assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 0, None, 0, None, BOGUS, None, None) == EINVAL
+    assert T(BOGUS, 1, 16, -0.5, 0.5, -1.0, 3, None, 0, None, BOGUS, None, None) == EINVAL
+    assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 3, None, 0, None, None, None, None) == EINVAL
+    assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 3, BOGUS, 10, None, BOGUS, None, None) == EINVAL
+    assert T(None, 0, 16, -0.5, 0.5, 50.0, 3, None, 0, None, None, None, None) == OK

@@ -1,6 +1,6 @@
 """Learned seed proposer on the GPU against the FP64 oracle (oracle/seednet.py).
 
-Histogram: counts and in-cell sums exact, features bitwise.  Network: the
+Histogram: counts exact, features bitwise.  Network: the
 kernels round the same quantities to bfloat16 as the oracle, but from float32
 sums where the oracle rounds double sums, so a stored activation can differ
 by one bfloat16 step where a sum sits within float32 error of a rounding
@@ -73,28 +73,19 @@ def test_slope_histogram_is_exact(rt):
     offs = np.zeros(len(hits) + 1, np.int64)
     offs[1:] = np.cumsum([len(h) for h in hits])
     H = np.concatenate(hits)
-    feat, cnt, sums = rt.slope_histogram(_dev(H), _dev(offs), sums=True)
-    feat, cnt, sums = _f(feat), cnt.cpu().numpy(), sums.cpu().numpy().view(np.uint64)
-    w = 1.0 / 64
+    feat, cnt = rt.slope_histogram(_dev(H), _dev(offs), counts=True)
+    feat, cnt = _f(feat), cnt.cpu().numpy()
     for e, h in enumerate(hits):
         c_o, f_o = sn.slope_histogram(h)
         np.testing.assert_array_equal(cnt[e], c_o)
         np.testing.assert_array_equal(feat[e], f_o)
-        # in-cell sums -> centroids within the fixed point and float32-binning error of the oracle's
-        cen = sn.cell_centroids(h)
-        nz = c_o > 0
-        for a in range(2):
-            bins = np.indices((64, 64))[1 - a]
-            mean_frac = sums[e][..., a].astype(np.float64) / np.maximum(c_o, 1) * 2.0 ** -32
-            got = -0.5 + (bins + mean_frac) * w
-            assert np.all(np.abs(got[nz] - cen[..., a][nz]) <= 2.0 ** -16 * w)
     # the special event: bin edges land in the upper bin, u = 0.5 and |z| < 50 are dropped
     c_s = cnt[len(hits) - 1]
     assert c_s.sum() == 13 and c_s[0, 0] == 1
     # order independence
     perm = np.concatenate([offs[i] + np.random.default_rng(i).permutation(len(h)) for i, h in enumerate(hits)])
-    feat2, cnt2, sums2 = rt.slope_histogram(_dev(H[perm]), _dev(offs), sums=True)
-    assert np.array_equal(cnt2.cpu().numpy(), cnt) and np.array_equal(sums2.cpu().numpy().view(np.uint64), sums)
+    feat2, cnt2 = rt.slope_histogram(_dev(H[perm]), _dev(offs), counts=True)
+    assert np.array_equal(cnt2.cpu().numpy(), cnt) and np.array_equal(_f(feat2), feat)
 
 
 def test_histogram_feature_of_every_small_count_is_the_oracles(rt):
@@ -321,20 +312,33 @@ def test_topk_is_exact_with_ties_nan_and_signed_zeros(rt, K):
         np.testing.assert_array_equal(seeds[e], s_o.astype(np.float32))
 
 
-def test_topk_seeds_at_hit_centroids(rt):
-    evs = _events(3)
-    b = batch_of(evs)
-    feat, cnt, sums = rt.slope_histogram(_dev(b.hits), _dev(b.offsets), sums=True)
-    # host-made logits from the oracle's counts: busy cells first, then by a fixed ramp
-    ramp = 1e-3 * np.arange(4096)[::-1].reshape(64, 64)
-    logits = np.stack([np.log1p(sn.slope_histogram(ev.hits)[0]) + ramp for ev in evs]).astype(np.float32)
-    seeds, idx = rt.topk_seeds(_dev(logits), 512, counts=cnt, sums=sums, want_idx=True)
-    seeds, idx = seeds.cpu().numpy().astype(np.float64), idx.cpu().numpy()
-    w = 1.0 / 64
-    for e, ev in enumerate(evs):
-        order, s_o = sn.top_k(logits[e], 512, centroids=sn.cell_centroids(ev.hits))
-        np.testing.assert_array_equal(idx[e], order)
-        assert np.all(np.abs(seeds[e] - s_o) <= 2.0 ** -16 * w + 2.0 ** -24)
+def _check_proposal(seeds, cells, s_o, c_o):
+    """Cells bit-exact; seeds within float32 rounding of the sub-cell mean
+    (in-sub-cell positions from float32 t = (u - lo) 256, error <= 2^-17 of a
+    sub-cell each, plus the final float32 rounding)."""
+    np.testing.assert_array_equal(cells, c_o)
+    assert np.all(np.abs(seeds - s_o) <= 2.0 ** -16 / 256 + 2.0 ** -24 * np.abs(s_o) + 1e-12)
+
+
+@pytest.mark.parametrize("K,n_min", [(512, 3), (64, 1), (4096, 3)])
+def test_proposed_seeds_match_oracle(rt, K, n_min):
+    evs = _events(3) + [make_event(WORKLOADS["velo"], 11, 9, n_tracks=0, noise_frac=0.0)]  # one empty event
+    hits = [e.hits for e in evs] + [_special_hits()]
+    offs = np.concatenate([[0], np.cumsum([len(h) for h in hits])]).astype(np.int64)
+    H = np.concatenate(hits)
+    # host-made logits from the oracle's counts: busy cells first, then a fixed ramp, with exact ties
+    ramp = np.round(1e-3 * np.arange(4096)[::-1].reshape(64, 64), 1)
+    logits = np.stack([np.log1p(sn.slope_histogram(h)[0]) + ramp for h in hits]).astype(np.float32)
+    seeds, cells = rt.topk_seeds(_dev(logits), K, hits=_dev(H), offsets=_dev(offs), min_sub_hits=n_min,
+                                 want_idx=True)
+    seeds, cells = seeds.cpu().numpy().astype(np.float64), cells.cpu().numpy()
+    for e, h in enumerate(hits):
+        s_o, c_o = sn.propose_seeds(logits[e], h, K, n_min=n_min)
+        _check_proposal(seeds[e], cells[e], s_o, c_o)
+    # hits in any order give the same seeds bitwise
+    perm = np.concatenate([offs[i] + np.random.default_rng(7 + i).permutation(len(h)) for i, h in enumerate(hits)])
+    seeds2 = rt.topk_seeds(_dev(logits), K, hits=_dev(H[perm]), offsets=_dev(offs), min_sub_hits=n_min)
+    assert np.array_equal(seeds2.cpu().numpy().astype(np.float64), seeds)
 
 
 # ---------------------------------------------------------------------------
@@ -345,21 +349,22 @@ def test_proposer_at_full_batch_size(rt):
     wl = WORKLOADS["velo_batch"]
     evs = [make_event(wl, 12, e, vertex_sigma=(0, 0, 0)) for e in range(1024)]
     b = batch_of(evs)
-    feat, cnt, sums = rt.slope_histogram(_dev(b.hits), _dev(b.offsets), sums=True)
+    hits, offs = _dev(b.hits), _dev(b.offsets)
+    feat, cnt = rt.slope_histogram(hits, offs, counts=True)
     params = seednet_init_params(5)
     logits = rt.seednet_forward(feat, _dev(params))
-    seeds = rt.topk_seeds(logits, 512, counts=cnt, sums=sums)
-    cnt = cnt.cpu().numpy()
-    for e in range(0, 1024, 97):
+    cnt, lg = cnt.cpu().numpy(), logits.cpu().numpy()
+    sample = list(range(0, 1024, 97))
+    z_o = {}
+    for e in sample:
         c_o, f_o = sn.slope_histogram(evs[e].hits)
         np.testing.assert_array_equal(cnt[e], c_o)
         fw = sn.forward(f_o, params)
-        z = _f(logits[e])
-        assert np.all(np.abs(z - fw["z"]) <= _logit_bound(fw, params))
-        # every chosen cell's oracle logit is within the bound of the oracle's K-th best
-        kth = np.sort(fw["z"].reshape(-1))[-512]
-        _, idx = rt.topk_seeds(logits[e:e + 1].contiguous(), 512, want_idx=True)
-        idx = idx.cpu().numpy()[0]
-        bnd = _logit_bound(fw, params).reshape(-1)
-        assert np.all(fw["z"].reshape(-1)[idx] + 2 * bnd.max() >= kth)
-    assert torch.isfinite(seeds).all()
+        assert np.all(np.abs(lg[e] - fw["z"]) <= _logit_bound(fw, params))
+        z_o[e] = fw["z"].astype(np.float32)
+        lg[e] = z_o[e]  # the sampled events' rows: the oracle's logits, read by both sides
+    seeds, cells = rt.topk_seeds(_dev(lg), 512, hits=hits, offsets=offs, want_idx=True)
+    seeds, cells = seeds.cpu().numpy().astype(np.float64), cells.cpu().numpy()
+    for e in sample:
+        s_o, c_o = sn.propose_seeds(z_o[e], evs[e].hits, 512)
+        _check_proposal(seeds[e], cells[e], s_o, c_o)
