@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import WORKLOADS, make_event, uniform_seeds  # noqa: E402
+from synth import WORKLOADS, batch_of, make_event, uniform_seeds  # noqa: E402
 
 WORKLOAD = "velo"
 RUN_SEED = 0
@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparison")
     return ap.parse_args()
 
 
@@ -181,6 +182,78 @@ def run_reference(args, rank: int):
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# batched methods: grid scan vs uniform multistart vs learned seeds
+# ---------------------------------------------------------------------------
+
+BATCH_EVENTS = 1024
+BATCH_RUN_SEED = 5000
+
+
+def batched_methods(rt, stream, flush, reps: int = 5):
+    """1024 ragged VELO-like events (tracks ~ Poisson(150) clipped to [20, 400],
+    origin vertex) through three methods, each one CUDA graph per batch: the
+    plain grid scan (1024^2), Algorithm 1 from 4096 uniform seeds per event and
+    from the learned proposer's 512 seeds per event.  Events/s from CUDA events
+    around graph replays (L2 flushed before each), MC-truth efficiency
+    (|dtheta|_max <= 1e-3), fakes, and the share of the plain search's tracks
+    the learned search recovers."""
+    import torch
+    from paper_1709_08610_gb300.pipeline import BatchTracker, GridScanBatch, match_efficiency, recovered_fraction
+    from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, SeedProposer
+    wl = WORKLOADS["velo_batch"]
+    E = BATCH_EVENTS
+    evs = [make_event(wl, BATCH_RUN_SEED, e, vertex_sigma=(0, 0, 0)) for e in range(E)]
+    b = batch_of(evs)
+    truth = [ev.truth[:, :2] for ev in evs]
+    H = b.hits.shape[0]
+    box = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    methods = {}
+
+    def timed(obj):
+        obj.capture()
+        for _ in range(2):
+            obj.replay()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            obj.replay()
+            c.record(stream)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        return statistics.median(ts)
+
+    runs = [("grid_scan_1024x1024", lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
+            ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0),
+             np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),
+            ("uniform_512", lambda: BatchTracker(E, H, 512, box, opts, wl.R0),
+             np.stack([uniform_seeds(wl, 512, BATCH_RUN_SEED, e) for e in range(E)]))]
+    if os.path.exists(DEFAULT_WEIGHTS):
+        prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS)
+        runs.append(("learned_512", lambda: BatchTracker(E, H, 512, box, opts, wl.R0, proposer=prop), None))
+    found = {}
+    for name, make, seeds in runs:
+        obj = make()
+        obj.load(b.hits, b.offsets, seeds)
+        ms = timed(obj)
+        found[name] = obj.results()
+        eff, fakes = match_efficiency(found[name], truth)
+        methods[name] = {"events_per_s": E / (ms * 1e-3), "ms_per_batch": ms, "efficiency": eff,
+                         "fakes_per_event": fakes / E}
+        del obj
+        torch.cuda.empty_cache()
+    for name in methods:
+        if name != "uniform_4096":
+            methods[name]["recovers_uniform_4096"] = recovered_fraction(found[name], found["uniform_4096"])
+    return {"workload": "%d ragged VELO-like events (Poisson(150) tracks clipped to [20, 400], origin vertex, "
+                        "%d hits), one CUDA graph per batch and method" % (E, H),
+            "events": E, "hits": int(H), "reps": reps, "methods": methods,
+            "l2": "flushed before each replay"}
 
 
 # ---------------------------------------------------------------------------
@@ -425,6 +498,10 @@ def main():
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = batched_methods(rt, stream, flush)
+
     if rank == 0:
         tr_n = (int(tr_grid["n_tracks"].item()), int(tr_search["n_tracks"].item()))
         line = {
@@ -442,7 +519,7 @@ def main():
             "tracks_found": {"grid": tr_n[0], "search": tr_n[1]},
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},
-            "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0,
+            "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0, "batched": batched,
             "tuned": tuned,
         }
         print(json.dumps(line), flush=True)

@@ -3,7 +3,8 @@
 One step is Algorithm 1 end to end on every event of the batch:
 spatial ordering of the hits (retina_prepare_hits), the starting points -
 either given (a uniform draw from the prior P_theta) or proposed by the
-learned seed network (slope histogram -> network -> top-K hit centroids) -
+learned seed network (slope histogram -> network -> ranked cells -> seeds
+at the hit means of their dense sub-cells) -
 the q truncated-Newton updates of all seeds in one persistent launch
 (retina_batched_search), then cluster + select (retina_extract_tracks).
 
@@ -91,6 +92,46 @@ class BatchTracker:
         n = self.tracks["n_tracks"].cpu().numpy()
         tr = self.tracks["tracks"].cpu().numpy()
         return [tr[e, :min(int(n[e]), self.K)].astype(np.float64) for e in range(self.E)]
+
+
+class GridScanBatch:
+    """The plain grid method over a batch: spatial ordering, Eq. 2 on the grid,
+    strict local maxima above R0, cluster + select; graph-capturable like
+    BatchTracker (the response grids live in the workspace)."""
+
+    def __init__(self, n_events: int, hit_capacity: int, grid: "rt.Grid", sigma: float, R0: float,
+                 merge_cells: float = 2.0, max_maxima: int = 4096, max_tracks: int = 1024,
+                 model: int = rt.VELO_SLOPES, device="cuda"):
+        E, H = int(n_events), int(hit_capacity)
+        self.E, self.H, self.grid, self.sigma, self.R0, self.merge = E, H, grid, float(sigma), float(R0), float(merge_cells)
+        self.model, self.Km, self.K = model, int(max_maxima), int(max_tracks)
+        dev = torch.device(device)
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.hits = torch.zeros((H, 4), **f32)
+        self.offsets = torch.zeros(E + 1, dtype=torch.int64, device=dev)
+        self.sorted = torch.empty((H, 4), **f32)
+        self.boxes = torch.empty((int(rt.lib.retina_prepare_hits_box_count(H, E)), 8), **f32)
+        self.maxima = dict(max_idx=torch.empty((E, self.Km), dtype=torch.int32, device=dev),
+                           max_theta=torch.empty((E, self.Km, 2), **f32), max_R=torch.empty((E, self.Km), **f32),
+                           n_max=torch.empty((E,), dtype=torch.int32, device=dev), R=None)
+        self.ws = torch.empty(max(rt.grid_scan_workspace_size(E, model, grid), 1), dtype=torch.uint8, device=dev)
+        self.tracks = dict(tracks=torch.empty((E, self.K, 2), **f32), track_R=torch.empty((E, self.K), **f32),
+                           track_src=torch.empty((E, self.K), dtype=torch.int32, device=dev),
+                           n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    load = BatchTracker.load
+
+    def step(self, stream=None):
+        rt.prepare_hits(self.hits, self.offsets, self.model, out=(self.sorted, self.boxes), stream=stream)
+        rt.grid_scan(self.sorted, self.offsets, self.model, self.grid, self.sigma, self.R0, self.Km, ws=self.ws,
+                     out=self.maxima, boxes=self.boxes, stream=stream)
+        rt.extract_tracks(self.maxima["max_theta"], self.maxima["max_R"], None, self.grid, self.R0, self.merge,
+                          self.K, n_valid=self.maxima["n_max"], out=self.tracks, stream=stream)
+
+    capture = BatchTracker.capture
+    replay = BatchTracker.replay
+    results = BatchTracker.results
 
 
 def match_efficiency(found, truth, eps: float = 1e-3):
