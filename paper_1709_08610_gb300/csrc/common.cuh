@@ -65,4 +65,58 @@ __device__ __forceinline__ float cell_centre(float lo, float step, int i) {
     return __fmaf_rn((float)i + 0.5f, step, lo);
 }
 
+// Bitonic sort of C = THREADS * R distinct keys held in registers, thread t
+// owning positions t R .. t R + R - 1 (all THREADS threads of the block call
+// it).  Partners closer than R sit in the same thread, closer than 32 R in the
+// same warp (shuffles); farther ones are exchanged through shared memory `x`
+// (C keys).  Element i of a pair (i, i ^ j) inside a run sorted upwards
+// ((i & k) == 0) keeps the smaller key when it is the lower index.
+template <typename T, int R, int THREADS>
+__device__ __forceinline__ void bitonic_sort_regs(T (&v)[R], T *x) {
+    constexpr int C = THREADS * R;
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int k = 2; k <= C; k <<= 1) {
+#pragma unroll 1
+        for (int j = k >> 1; j >= R; j >>= 1) {
+            if (j >= 32 * R) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[t * R + r] = v[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = t * R + r;
+                    const T b = x[i ^ j];
+                    const bool keep_min = ((i & k) == 0) == (i < (i ^ j));
+                    v[r] = keep_min ? (v[r] < b ? v[r] : b) : (v[r] > b ? v[r] : b);
+                }
+                __syncthreads();
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = t * R + r;
+                    const T b = __shfl_xor_sync(0xffffffffu, v[r], j / R);
+                    const bool keep_min = ((i & k) == 0) == (i < (i ^ j));
+                    v[r] = keep_min ? (v[r] < b ? v[r] : b) : (v[r] > b ? v[r] : b);
+                }
+            }
+        }
+        // partners inside the thread: compile-time register indices
+#pragma unroll
+        for (int j = R / 2; j >= 1; j >>= 1) {
+            if (j > (k >> 1)) continue;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r & j) continue;
+                const int i = t * R + r;
+                const T a = v[r], b = v[r | j];
+                if ((a > b) == ((i & k) == 0)) {
+                    v[r] = b;
+                    v[r | j] = a;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace retina

@@ -50,14 +50,14 @@ extern "C" int retina_grid_maxima_static(const float *R, int32_t n_events, const
     if (n_events == 0) return RETINA_OK;
     if (!R || !max_idx || !max_theta || !max_R || !n_max) return RETINA_EINVAL;
     // counts and offsets: 2 int32 per block per event
-    if (maxima_ws_bytes(n_events, g) > (size_t)RETINA_STATIC_SCRATCH_BYTES) return RETINA_ENOSPACE;
+    if (maxima_ordered_ws_bytes(n_events, g) > (size_t)RETINA_STATIC_SCRATCH_BYTES) return RETINA_ENOSPACE;
     int32_t *scratch = static_scratch_for_current_device();
     if (!scratch) return RETINA_ECUDA;
     // Every call overwrites the counts of all its blocks and then all their
     // offsets before reading them, so no part of the scratch has to start at
     // zero and nothing from a previous call is read.
-    return launch_grid_maxima(R, n_events, g, R0, max_idx, max_theta, max_R, n_max, K, scratch,
-                              (cudaStream_t)stream) == cudaSuccess
+    return launch_grid_maxima_ordered(R, n_events, g, R0, max_idx, max_theta, max_R, n_max, K, scratch,
+                                      (cudaStream_t)stream) == cudaSuccess
                ? RETINA_OK
                : RETINA_ECUDA;
 }

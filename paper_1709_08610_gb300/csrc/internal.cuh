@@ -16,6 +16,10 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
                                  const float4 *boxes, int n_events, int model, const retina_grid *g, float sigma, float *R, float *partials,
                                  cudaStream_t st);
 size_t maxima_ws_bytes(int n_events, const retina_grid *g);
+size_t maxima_ordered_ws_bytes(int n_events, const retina_grid *g);
+cudaError_t launch_grid_maxima_ordered(const float *R, int n_events, const retina_grid *g, float R0,
+                                       int32_t *max_idx, float *max_theta, float *max_R, int32_t *n_max, int K,
+                                       int32_t *ws_counts, cudaStream_t st);
 cudaError_t launch_grid_maxima(const float *R, int n_events, const retina_grid *g, float R0, int32_t *max_idx,
                                float *max_theta, float *max_R, int32_t *n_max, int K, int32_t *ws_counts,
                                cudaStream_t st);

@@ -50,6 +50,26 @@ __device__ __forceinline__ uint32_t hit_key(const float4 h, int model) {
     return (band << 20) | (quant10(h.y, -8.f, 8.f) << 10);
 }
 
+// Keys of chunk positions t R + r (padding ~0 sorts last), sorted, then the
+// hits gathered in key order.
+template <int R>
+__device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base, int n, int model,
+                                                float4 *__restrict__ sorted, uint64_t *x) {
+    uint64_t v[R];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = t * R + r;
+        v[r] = i < n ? (((uint64_t)hit_key(__ldg(hits + base + i), model) << 32) | (uint32_t)i) : ~0ull;
+    }
+    bitonic_sort_regs<uint64_t, R, PREP_THREADS>(v, x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = t * R + r;
+        if (i < n) sorted[base + i] = __ldg(hits + base + (int)(uint32_t)v[r]);
+    }
+}
+
 __global__ void __launch_bounds__(PREP_THREADS)
 prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int model,
                     float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
@@ -61,30 +81,17 @@ prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     const int64_t box_base = (off[e] < 0 ? 0 : (off[e] > n_hits ? n_hits : off[e])) / 32 + e;
     for (int64_t c0 = 0; c0 < H; c0 += SORT_CAP) {
         const int n = (int)((H - c0) < SORT_CAP ? (H - c0) : SORT_CAP);
-        int C = 1;
-        while (C < n) C <<= 1;
-        for (int i = tid; i < C; i += PREP_THREADS)
-            keys[i] = i < n ? (((uint64_t)hit_key(__ldg(hits + hb + c0 + i), model) << 32) | (uint32_t)i) : ~0ull;
-        __syncthreads();
-        for (int k = 2; k <= C; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < C; i += PREP_THREADS) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const uint64_t a = keys[i], b = keys[ixj];
-                        if ((a > b) == ((i & k) == 0)) {
-                            keys[i] = b;
-                            keys[ixj] = a;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (int i = tid; i < n; i += PREP_THREADS) {
-            const int src = (int)(uint32_t)keys[i];
-            sorted[hb + c0 + i] = __ldg(hits + hb + c0 + src);
-        }
+        const int64_t base = hb + c0;
+        if (n <= PREP_THREADS)
+            sort_and_gather<1>(hits, base, n, model, sorted, keys);
+        else if (n <= 2 * PREP_THREADS)
+            sort_and_gather<2>(hits, base, n, model, sorted, keys);
+        else if (n <= 4 * PREP_THREADS)
+            sort_and_gather<4>(hits, base, n, model, sorted, keys);
+        else if (n <= 8 * PREP_THREADS)
+            sort_and_gather<8>(hits, base, n, model, sorted, keys);
+        else
+            sort_and_gather<16>(hits, base, n, model, sorted, keys);
         __syncthreads();
         // one warp per block of 32 sorted hits (chunks are multiples of 32 but the last):
         // lane l reads hit 32 b + l, the warp reduces min / max

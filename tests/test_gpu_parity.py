@@ -173,6 +173,25 @@ def test_grid_maxima_exact_on_identical_inputs(rt):
     assert n_max[4] == 0
 
 
+@pytest.mark.parametrize("n,K", [((100, 100), 64), ((150, 150), 3000), ((1024, 600), 5000), ((1024, 600), 16)])
+def test_grid_maxima_exact_on_noise_many_maxima(rt, n, K):
+    """Seeded noise grids hold ~cells/9 strict maxima: the ordering of 1-4k
+    candidates and, past 4096 per event, the exact whole-grid fallback."""
+    rng = np.random.default_rng(n[0] * 7 + K)
+    Rs = [rng.uniform(0, 1, (n[1], n[0])).astype(np.float32) for _ in range(2)]
+    Rs[1] = np.round(Rs[1] * 8) / 8  # exact ties
+    grid = rt.Grid((-0.5, -0.5), (2.0 ** -10, 2.0 ** -10), n)
+    out = rt.grid_maxima(dev(np.stack(Rs).astype(np.float32)), grid, 0.25, K)
+    n_max, idx = out["n_max"].cpu().numpy(), out["max_idx"].cpu().numpy()
+    Rm = out["max_R"].cpu().numpy()
+    for e, R in enumerate(Rs):
+        exp_idx = oracle.grid_maxima(R, 0.25)
+        assert n_max[e] == len(exp_idx)
+        k = min(K, len(exp_idx))
+        assert idx[e, :k].tolist() == exp_idx[:k].tolist()
+        np.testing.assert_array_equal(Rm[e, :k], R.reshape(-1)[exp_idx[:k]])
+
+
 @pytest.mark.parametrize("flags", [1, 2])
 def test_grid_scan_maxima_match_oracle_up_to_ties(rt, flags):
     wl = WORKLOADS["velo"]
