@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparison")
+    ap.add_argument("--serial", action="store_true", help="run the grid and search branches on one stream")
     return ap.parse_args()
 
 
@@ -321,30 +322,38 @@ def main():
     srt = torch.empty_like(hits)
     boxes = torch.empty((rt.lib.retina_prepare_hits_box_count(H, 1), 8), dtype=torch.float32, device=dev)
 
+    # The grid branch and the search branch need only the prepared hits, so
+    # after retina_prepare_hits they run concurrently on two streams (the
+    # search leaves room on every SM through RETINA_OPT_BATCH_CTAS) and join
+    # on the main stream.  Events (timing ones when given) bracket every
+    # stage on the stream it runs on:
+    #   0 start | prepare | 1 | grid | 2 | maxima + extract | 3     (main stream)
+    #   4 | search | 5 | extract | 6                                (search stream)
+    #   join, 7 end                                                 (main stream)
+    stream2 = torch.cuda.Stream(dev) if not args.serial else stream
+    sync_ev = [torch.cuda.Event() for _ in range(8)]
+
     def step(evs=None):
-        # S0: spatial order + block boxes; S1-S3: grid response, maxima,
-        # extraction; S4-S6: persistent truncated-Newton search, extraction
-        if evs:
-            evs[0].record(stream)
-        rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes))
-        if evs:
-            evs[1].record(stream)
-        rt.grid_response(srt, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid, boxes=boxes)
-        if evs:
-            evs[2].record(stream)
-        rt.grid_maxima(Rg, grid, R0, K_MAX, out=mx, ws=ws_max)
-        rt.extract_tracks(mx["max_theta"], mx["max_R"], None, grid, R0, wl.merge_cells, K_TR,
-                          n_valid=mx["n_max"], out=tr_grid)
-        if evs:
-            evs[3].record(stream)
+        ev = evs if evs else sync_ev
+        ev[0].record(stream)
+        rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes), stream=stream)
+        ev[1].record(stream)
+        stream2.wait_event(ev[1])
+        ev[4].record(stream2)
         rt.batched_search(srt, offs, wl.model, seeds, seed_offs, opts, grid, out=ls_out, n_evals=n_evals,
-                          ws=ws_search, boxes=boxes)
-        if evs:
-            evs[4].record(stream)
+                          ws=ws_search, boxes=boxes, stream=stream2)
+        ev[5].record(stream2)
         rt.extract_tracks(ls_out[0].view(1, -1, 2), ls_out[1].view(1, -1), ls_out[2].view(1, -1), grid, R0,
-                          wl.merge_cells, K_TR, out=tr_search)
-        if evs:
-            evs[5].record(stream)
+                          wl.merge_cells, K_TR, out=tr_search, stream=stream2)
+        ev[6].record(stream2)
+        rt.grid_response(srt, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid, boxes=boxes, stream=stream)
+        ev[2].record(stream)
+        rt.grid_maxima(Rg, grid, R0, K_MAX, out=mx, ws=ws_max, stream=stream)
+        rt.extract_tracks(mx["max_theta"], mx["max_R"], None, grid, R0, wl.merge_cells, K_TR,
+                          n_valid=mx["n_max"], out=tr_grid, stream=stream)
+        ev[3].record(stream)
+        stream.wait_event(ev[6])
+        ev[7].record(stream)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -354,6 +363,30 @@ def main():
         rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes))
         tuned = {"grid": tune.tune_grid(srt, offs, wl.model, grid, wl.sigma_grid, boxes=boxes),
                  "search": tune.tune_batched_search(srt, offs, wl.model, seeds, seed_offs, opts, grid, boxes=boxes)}
+
+    # ---- the search's CTA shape when it shares the GPU with the grid branch:
+    # candidates timed on the whole two-stream step (same inputs, outputs)
+    if not args.no_tune and not args.serial:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        cands = [(rt.get_option(rt.OPT_BATCH_WARPS), 0), (16, sms), (8, sms), (8, 2 * sms), (16, 0), (32, 0)]
+        table = {}
+        ev_t = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        for w, c in cands:
+            rt.set_option(rt.OPT_BATCH_WARPS, w)
+            rt.set_option(rt.OPT_BATCH_CTAS, c)
+            for _ in range(3):
+                step()
+            ts = []
+            for _ in range(15):
+                step(ev_t)
+                ev_t[7].synchronize()
+                ts.append(ev_t[0].elapsed_time(ev_t[7]))
+            table["%d,%d" % (w, c)] = statistics.median(ts)
+        best = min(table, key=table.get)
+        w, c = (int(x) for x in best.split(","))
+        rt.set_option(rt.OPT_BATCH_WARPS, w)
+        rt.set_option(rt.OPT_BATCH_CTAS, c)
+        tuned["overlap"] = {"warps": w, "ctas": c, "step_ms": table[best], "table_ms": table}
 
     # ---- peaks of the FP32 and MUFU pipes, measured live (burst)
     peaks = {}
@@ -379,7 +412,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
     clocks = ClockSampler(local_rank) if not args.no_clocks else None
     if world > 1:
         dist.barrier()
@@ -399,12 +432,10 @@ def main():
         dist.barrier()
     clk = clocks.stop() if clocks else None
 
-    NST = 5
-    stage = np.zeros((args.steps, NST))
-    for k in range(args.steps):
-        for j in range(NST):
-            stage[k, j] = evs[k][j].elapsed_time(evs[k][j + 1])
-    step_ms = stage.sum(axis=1)
+    # stages: prepare, grid response, maxima + extract (main stream), search, extract (search stream)
+    pairs = [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6)]
+    stage = np.array([[evs[k][a].elapsed_time(evs[k][b]) for a, b in pairs] for k in range(args.steps)])
+    step_ms = np.array([evs[k][0].elapsed_time(evs[k][7]) for k in range(args.steps)])
     total_ms = float(step_ms.sum())
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -445,17 +476,18 @@ def main():
                  "effective_pairs_per_s": grid_pairs_all / (grid_ms * 1e-3),
                  "peak_source": "FP32 FMA rate measured live by retina_alu_probe (burst; the faster of FFMA and "
                                 "packed FFMA2)"}
-    fr_fp32 = (search_fp32_rate / (2 * fma_rate) if fma_rate else None)  # vs lane-ops/s (an FMA counts once)
+    # FP32 lane instructions (an FMA counts once) against the measured lane-FMA rate, and ex2 against MUFU
+    fr_fp32 = (search_fp32_rate / fma_rate) if fma_rate else None
     fr_ex2 = (search_ex2_rate / ex2_peak) if ex2_peak else None
-    roof_search = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Gpair/s",
-                   "achieved": (rgh_pairs + r_pairs) / (search_ms * 1e-3) / 1e9,
-                   "fp32_ops_per_s": search_fp32_rate, "ex2_per_s": search_ex2_rate,
-                   "frac_fp32": fr_fp32, "frac_ex2": fr_ex2, "rgh_pairs": rgh_pairs, "r_pairs": r_pairs,
+    roof_search = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Tlane-op/s",
+                   "achieved": search_fp32_rate / 1e12, "peak": (fma_rate / 1e12) if fma_rate else None,
+                   "frac": fr_fp32, "traffic": None,
+                   "pairs_per_s": (rgh_pairs + r_pairs) / (search_ms * 1e-3),
+                   "ex2_per_s": search_ex2_rate, "frac_ex2": fr_ex2, "rgh_pairs": rgh_pairs, "r_pairs": r_pairs,
                    "pairs_total": (wl.n_seeds * len(wl.sigma_schedule) + n_ev) * H,
-                   "traffic": None}
+                   "peak_source": "FP32 lane-FMA rate measured live by retina_alu_probe (burst)"}
     dominant = "grid" if grid_ms >= search_ms else "search"
-    roofline = roof_grid if dominant == "grid" else dict(roof_search, frac=max(x for x in (fr_fp32, fr_ex2) if x),
-                                                          peak=None, unit="Gpair/s")
+    roofline = roof_grid if dominant == "grid" else roof_search
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -508,7 +540,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(wl, H),
+            "config": dict(workload_config(wl, H),
+                           branches="one stream" if args.serial else
+                           "grid branch and search branch on two concurrent streams after the shared hit ordering"),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "roofline_other": roof_search if dominant == "grid" else roof_grid,
             "stages_ms": {"prepare_hits": prep_ms, "grid_response": grid_ms,

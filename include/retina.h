@@ -90,6 +90,9 @@ extern "C" {
 #define RETINA_OPT_BATCH_SEEDS_PER_WARP 5 /* batched search: 1, 2 or 4 (1)      */
 #define RETINA_OPT_BATCH_WARPS 6       /* batched search CTA warps: 8,16,32 (16) */
 #define RETINA_OPT_BATCH_SMEM_HITS 7   /* batched search staged hits (8192)     */
+#define RETINA_OPT_BATCH_CTAS 8        /* batched search CTAs, 0 = fill the GPU (0);
+                                          fewer leave room for kernels running
+                                          concurrently on other streams          */
 
 typedef struct {
     float lo[2];   /* lower edge of the box per axis                      */

@@ -18,6 +18,7 @@ static std::atomic<int> g_opt_ls_warps{8};
 static std::atomic<int> g_opt_batch_spw{1};
 static std::atomic<int> g_opt_batch_warps{16};
 static std::atomic<int> g_opt_batch_smem_hits{8192};
+static std::atomic<int> g_opt_batch_ctas{0};
 
 static bool finite_pos(float v) { return isfinite(v) && v > 0.f; }
 
@@ -101,6 +102,10 @@ int retina_set_option(int32_t option, int32_t value) {
             if (value < 0 || value > 12288) return RETINA_EINVAL;
             g_opt_batch_smem_hits = value;
             return RETINA_OK;
+        case RETINA_OPT_BATCH_CTAS:
+            if (value < 0 || value > (1 << 20)) return RETINA_EINVAL;
+            g_opt_batch_ctas = value;
+            return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -115,6 +120,7 @@ int retina_get_option(int32_t option, int32_t *value) {
         case RETINA_OPT_BATCH_SEEDS_PER_WARP: *value = g_opt_batch_spw; return RETINA_OK;
         case RETINA_OPT_BATCH_WARPS: *value = g_opt_batch_warps; return RETINA_OK;
         case RETINA_OPT_BATCH_SMEM_HITS: *value = g_opt_batch_smem_hits; return RETINA_OK;
+        case RETINA_OPT_BATCH_CTAS: *value = g_opt_batch_ctas; return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -291,7 +297,7 @@ int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *even
                                              n_events, model, seeds,
                                              n_seeds, seed_offsets, order, opts, box, theta_out, R_out, status,
                                              n_evals, (int32_t *)ws, g_opt_batch_spw, g_opt_batch_warps,
-                                             g_opt_batch_smem_hits, (cudaStream_t)stream));
+                                             g_opt_batch_smem_hits, g_opt_batch_ctas, (cudaStream_t)stream));
 }
 
 int retina_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
 size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(int32_t) + 255) / 256 * 256; }
 
 template <int MODEL, int P, int WARPS>
-static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, cudaStream_t st) {
+static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
     auto kern = batched_search_kernel<MODEL, P, WARPS>;
     const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr);
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
@@ -133,17 +133,19 @@ static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, cud
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
-    const int grid = per_sm * sm_count();
+    // persistent: as many CTAs as fit at once, or fewer when the caller leaves room for concurrent kernels
+    const int fill = per_sm * sm_count();
+    const int grid = (ctas > 0 && ctas < fill) ? ctas : fill;
     kern<<<grid, WARPS * 32, smem, st>>>(a, prm);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int MODEL, int P>
-static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParams &prm, cudaStream_t st) {
-    if (warps >= 32) return launch_batched_t<MODEL, P, 32>(a, prm, st);
-    if (warps >= 16) return launch_batched_t<MODEL, P, 16>(a, prm, st);
-    return launch_batched_t<MODEL, P, 8>(a, prm, st);
+static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
+    if (warps >= 32) return launch_batched_t<MODEL, P, 32>(a, prm, ctas, st);
+    if (warps >= 16) return launch_batched_t<MODEL, P, 16>(a, prm, ctas, st);
+    return launch_batched_t<MODEL, P, 8>(a, prm, ctas, st);
 }
 
 cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
@@ -151,7 +153,7 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
                                   const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
                                   const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
                                   uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
-                                  int smem_hits, cudaStream_t st) {
+                                  int smem_hits, int ctas, cudaStream_t st) {
     LsParams prm = make_ls_params(o, box);
     if (smem_hits < 0) smem_hits = 0;
     if (smem_hits > 12288) smem_hits = 12288;
@@ -159,7 +161,7 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
                 (int64_t)n_events + n_seeds + 2, theta_out, R_out, status, n_evals, counters, work_counters()};
     cudaError_t err = cudaMemsetAsync(counters, 0, batched_ws_bytes(n_events), st);
     if (err != cudaSuccess) return err;
-#define RETINA_BATCH_CASE(M, PP) return launch_batched_w<M, PP>(warps, a, prm, st)
+#define RETINA_BATCH_CASE(M, PP) return launch_batched_w<M, PP>(warps, a, prm, ctas, st)
     if (model == RETINA_VELO_SLOPES) {
         if (seeds_per_warp >= 4) RETINA_BATCH_CASE(RETINA_VELO_SLOPES, 4);
         if (seeds_per_warp == 2) RETINA_BATCH_CASE(RETINA_VELO_SLOPES, 2);

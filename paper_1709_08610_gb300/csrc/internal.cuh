@@ -41,7 +41,7 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
                                   const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
                                   const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
                                   uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
-                                  int smem_hits, cudaStream_t st);
+                                  int smem_hits, int ctas, cudaStream_t st);
 size_t batched_ws_bytes(int n_events);
 int64_t prepared_box_count(int64_t n_hits, int n_events);
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,

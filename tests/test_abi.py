@@ -37,6 +37,10 @@ def test_options_roundtrip_and_validation():
     assert L.retina_set_option(rt.OPT_LS_SEEDS_PER_WARP, 3) == EINVAL
     assert L.retina_set_option(rt.OPT_LS_SMEM_HITS, -1) == EINVAL
     assert L.retina_set_option(999, 1) == EINVAL
+    rt.set_option(rt.OPT_BATCH_CTAS, 152)
+    assert rt.get_option(rt.OPT_BATCH_CTAS) == 152
+    rt.set_option(rt.OPT_BATCH_CTAS, 0)
+    assert L.retina_set_option(rt.OPT_BATCH_CTAS, -1) == EINVAL
 
 
 def _grid(lo=(-0.5, -0.5), step=(2 ** -10, 2 ** -10), n=(1024, 1024)):
