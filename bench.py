@@ -193,18 +193,18 @@ BATCH_EVENTS = 1024
 BATCH_RUN_SEED = 5000
 
 
-def batched_methods(rt, stream, flush, reps: int = 5):
-    """1024 ragged VELO-like events (tracks ~ Poisson(150) clipped to [20, 400],
-    origin vertex) through three methods, each one CUDA graph per batch: the
-    plain grid scan (1024^2), Algorithm 1 from 4096 uniform seeds per event and
-    from the learned proposer's 512 seeds per event.  Events/s from CUDA events
-    around graph replays (L2 flushed before each), MC-truth efficiency
-    (|dtheta|_max <= 1e-3), fakes, and the share of the plain search's tracks
-    the learned search recovers."""
+def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: int = 512, reps: int = 5):
+    """1024 ragged VELO-like events with the vertex at the origin through three
+    methods, each replayed as one CUDA graph per batch: the plain grid scan,
+    Algorithm 1 from 4096 uniform seeds per event (and from as many uniform
+    seeds as the learned variant uses) and from the learned proposer's seeds.
+    Events/s from CUDA events around graph replays (L2 flushed before each),
+    MC-truth efficiency (|dtheta|_max <= 1e-3), fakes per event, and the share
+    of the plain 4096-seed search's tracks each method recovers."""
     import torch
     from paper_1709_08610_gb300.pipeline import BatchTracker, GridScanBatch, match_efficiency, recovered_fraction
     from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, SeedProposer
-    wl = WORKLOADS["velo_batch"]
+    wl = WORKLOADS[workload]
     E = BATCH_EVENTS
     evs = [make_event(wl, BATCH_RUN_SEED, e, vertex_sigma=(0, 0, 0)) for e in range(E)]
     b = batch_of(evs)
@@ -229,14 +229,16 @@ def batched_methods(rt, stream, flush, reps: int = 5):
             ts.append(a.elapsed_time(c))
         return statistics.median(ts)
 
-    runs = [("grid_scan_1024x1024", lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
+    n0, n1 = wl.grid_n
+    runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
             ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0),
              np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),
-            ("uniform_512", lambda: BatchTracker(E, H, 512, box, opts, wl.R0),
-             np.stack([uniform_seeds(wl, 512, BATCH_RUN_SEED, e) for e in range(E)]))]
+            ("uniform_%d" % learned_k, lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0),
+             np.stack([uniform_seeds(wl, learned_k, BATCH_RUN_SEED, e) for e in range(E)]))]
     if os.path.exists(DEFAULT_WEIGHTS):
         prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS)
-        runs.append(("learned_512", lambda: BatchTracker(E, H, 512, box, opts, wl.R0, proposer=prop), None))
+        runs.append(("learned_%d" % learned_k,
+                     lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, proposer=prop), None))
     found = {}
     for name, make, seeds in runs:
         obj = make()
@@ -251,8 +253,10 @@ def batched_methods(rt, stream, flush, reps: int = 5):
     for name in methods:
         if name != "uniform_4096":
             methods[name]["recovers_uniform_4096"] = recovered_fraction(found[name], found["uniform_4096"])
-    return {"workload": "%d ragged VELO-like events (Poisson(150) tracks clipped to [20, 400], origin vertex, "
-                        "%d hits), one CUDA graph per batch and method" % (E, H),
+    gen = wl.gen
+    return {"workload": "%d ragged VELO-like events (tracks ~ Poisson(%g) clipped to [%g, %g], origin vertex, "
+                        "%d hits), grid %dx%d; one CUDA graph per batch and method"
+                        % ((E,) + tuple(gen["n_tracks"]) + (H, n0, n1)),
             "events": E, "hits": int(H), "reps": reps, "methods": methods,
             "l2": "flushed before each replay"}
 
@@ -433,7 +437,8 @@ def main():
     clk = clocks.stop() if clocks else None
 
     # stages: prepare, grid response, maxima + extract (main stream), search, extract (search stream)
-    pairs = [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6)]
+    # (one stream: the search branch is enqueued first, so the grid response runs from event 6 to 2)
+    pairs = [(0, 1), (6, 2) if args.serial else (1, 2), (2, 3), (4, 5), (5, 6)]
     stage = np.array([[evs[k][a].elapsed_time(evs[k][b]) for a, b in pairs] for k in range(args.steps)])
     step_ms = np.array([evs[k][0].elapsed_time(evs[k][7]) for k in range(args.steps)])
     total_ms = float(step_ms.sum())
@@ -530,9 +535,18 @@ def main():
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
-    batched = None
+    batched = stress = None
     if world == 1 and not args.no_batched:
+        # launch shapes tuned for one event do not carry over to 1024: the grid's
+        # hit-slice count goes back to the library's rule (one slice at this
+        # many tiles: no partials buffer) and the search fills the GPU
+        saved = {o: rt.get_option(o) for o in (rt.OPT_GRID_SPLITS, rt.OPT_BATCH_CTAS)}
+        rt.set_option(rt.OPT_GRID_SPLITS, 0)
+        rt.set_option(rt.OPT_BATCH_CTAS, 0)
         batched = batched_methods(rt, stream, flush)
+        stress = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
+        for o, v in saved.items():
+            rt.set_option(o, v)
 
     if rank == 0:
         tr_n = (int(tr_grid["n_tracks"].item()), int(tr_search["n_tracks"].item()))
@@ -554,6 +568,7 @@ def main():
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},
             "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0, "batched": batched,
+            "batched_stress": stress,
             "tuned": tuned,
         }
         print(json.dumps(line), flush=True)
