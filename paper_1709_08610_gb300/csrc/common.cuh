@@ -35,6 +35,25 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     return r;
 }
 
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Packed FP32x2 a * b + c and a * b, round-to-nearest per lane (each lane is
+// bitwise the scalar __fmaf_rn / __fmul_rn).
+__device__ __forceinline__ unsigned long long fma2_rn(unsigned long long a, unsigned long long b,
+                                                      unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Butterfly (xor) sum: every lane ends with the bitwise-identical total,
 // because each level adds the same two operands in either order.
 __device__ __forceinline__ float warp_sum(float v) {

@@ -3,13 +3,15 @@
 // Eq. 1 is zero in float32.
 //
 // Per event (one CTA, chunks of up to SORT_CAP hits): each hit gets a 32-bit
-// key and the chunk is bitonic-sorted by (key, original index) in shared
-// memory.  Slope model: the key is a band of |z| (octaves from 16 mm) over a
-// Morton code of the hit's slopes (u, v) = (x/z, y/z), and the box of a
-// block is (umin, umax, vmin, vmax, |z|min, |z|max): since
+// key - a 17-bit spatial code above its 13-bit index in the chunk, so keys are
+// distinct and the order is deterministic - and the chunk is sorted by key.
+// Slope model: the code is a band of |z| (octaves from 16 mm) over a 14-bit
+// Morton code of the hit's slopes (u, v) = (x/z, y/z) quantised on [-1, 1],
+// and the box of a block is (umin, umax, vmin, vmax, |z|min, |z|max): since
 // s^2 = z^2 |(u, v) - theta|^2, it bounds s^2 from below by
-// |z|min^2 dist(theta, box)^2.  2D toy: the key is a band of x over the
-// quantised y, and the box is (xmin, xmax, ymin, ymax, 0, 0).
+// |z|min^2 dist(theta, box)^2.  2D toy: the code is a band of x over the
+// quantised y, and the box is (xmin, xmax, ymin, ymax, 0, 0).  The code only
+// orders the hits; the boxes use the exact float32 values.
 // The sorted hits are written to the output in place of the event's hits
 // (same CSR offsets); block b of event e (sorted hits 32b .. 32b+31) gets a
 // box at index box_base(e) + b with box_base(e) = floor(offsets[e] / 32) + e,
@@ -20,60 +22,61 @@
 namespace retina {
 
 constexpr int PREP_THREADS = 1024;
-constexpr int SORT_CAP = 16384;
+constexpr int IDX_BITS = 13;
+constexpr int SORT_CAP = 1 << IDX_BITS;  // 8192 hits per chunk
 
-// Spread the 10 low bits of v to the even bit positions 0, 2, ..., 18.
-__device__ __forceinline__ uint32_t spread10(uint32_t v) {
-    v &= 0x3ffu;
-    v = (v | (v << 8)) & 0x00ff00ffu;
-    v = (v | (v << 4)) & 0x0f0f0f0fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
+// Spread the 7 low bits of v to the even bit positions 0, 2, ..., 12.
+__device__ __forceinline__ uint32_t spread7(uint32_t v) {
+    v &= 0x7fu;
+    v = (v | (v << 4)) & 0x0f0fu;
+    v = (v | (v << 2)) & 0x3333u;
+    v = (v | (v << 1)) & 0x5555u;
     return v;
 }
 
-__device__ __forceinline__ uint32_t quant10(float v, float lo, float hi) {
-    float t = (v - lo) / (hi - lo);
+__device__ __forceinline__ uint32_t quant7(float v, float lo, float inv_range) {
+    float t = (v - lo) * inv_range;
     t = isfinite(t) ? fminf(fmaxf(t, 0.f), 1.f) : (t > 0.f ? 1.f : 0.f);
-    return (uint32_t)(t * 1023.f);
+    return (uint32_t)(t * 127.f);
 }
 
-__device__ __forceinline__ uint32_t hit_key(const float4 h, int model) {
+// 17-bit spatial code of a hit (only orders the hits; any value is valid)
+__device__ __forceinline__ uint32_t hit_code(const float4 h, int model) {
     if (model == RETINA_VELO_SLOPES) {
         const float az = fabsf(h.z);
         uint32_t band = 0;  // |z| octaves: [0,16), [16,32), ..., [512, inf)
         for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
-        const uint32_t m = spread10(quant10(h.x / h.z, -1.f, 1.f)) | (spread10(quant10(h.y / h.z, -1.f, 1.f)) << 1);
-        return (band << 20) | (m & 0xfffffu);
+        const float rz = __frcp_rn(h.z);
+        const uint32_t m = spread7(quant7(h.x * rz, -1.f, 0.5f)) | (spread7(quant7(h.y * rz, -1.f, 0.5f)) << 1);
+        return (band << 14) | m;
     }
-    const uint32_t band = float_order_key(h.x) >> 20;
-    return (band << 20) | (quant10(h.y, -8.f, 8.f) << 10);
+    return ((float_order_key(h.x) >> 25) << 7) | quant7(h.y, -8.f, 1.f / 16.f);
 }
 
 // Keys of chunk positions t R + r (padding ~0 sorts last), sorted, then the
 // hits gathered in key order.
 template <int R>
 __device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base, int n, int model,
-                                                float4 *__restrict__ sorted, uint64_t *x) {
-    uint64_t v[R];
+                                                float4 *__restrict__ sorted, uint32_t *x) {
+    uint32_t v[R];
     const int t = threadIdx.x;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t * R + r;
-        v[r] = i < n ? (((uint64_t)hit_key(__ldg(hits + base + i), model) << 32) | (uint32_t)i) : ~0ull;
+        v[r] = i < n ? ((hit_code(__ldg(hits + base + i), model) << IDX_BITS) | (uint32_t)i) : 0xffffffffu;
     }
-    bitonic_sort_regs<uint64_t, R, PREP_THREADS>(v, x);
+    bitonic_sort_regs<uint32_t, R, PREP_THREADS>(v, x);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t * R + r;
-        if (i < n) sorted[base + i] = __ldg(hits + base + (int)(uint32_t)v[r]);
+        if (i < n) sorted[base + i] = __ldg(hits + base + (int)(v[r] & (SORT_CAP - 1)));
     }
 }
 
 __global__ void __launch_bounds__(PREP_THREADS)
 prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int model,
                     float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
-    extern __shared__ uint64_t keys[];
+    extern __shared__ uint32_t keys[];
     const int e = blockIdx.x, tid = threadIdx.x;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
@@ -88,10 +91,8 @@ prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
             sort_and_gather<2>(hits, base, n, model, sorted, keys);
         else if (n <= 4 * PREP_THREADS)
             sort_and_gather<4>(hits, base, n, model, sorted, keys);
-        else if (n <= 8 * PREP_THREADS)
-            sort_and_gather<8>(hits, base, n, model, sorted, keys);
         else
-            sort_and_gather<16>(hits, base, n, model, sorted, keys);
+            sort_and_gather<8>(hits, base, n, model, sorted, keys);
         __syncthreads();
         // one warp per block of 32 sorted hits (chunks are multiples of 32 but the last):
         // lane l reads hit 32 b + l, the warp reduces min / max
@@ -144,7 +145,7 @@ int64_t prepared_box_count(int64_t n_hits, int n_events) { return n_hits / 32 + 
 
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                                 float4 *sorted, float4 *boxes, cudaStream_t st) {
-    const size_t smem = (size_t)SORT_CAP * sizeof(uint64_t);
+    const size_t smem = (size_t)SORT_CAP * sizeof(uint32_t);
     {
         cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_kernel), smem);
         if (aerr != cudaSuccess) return aerr;

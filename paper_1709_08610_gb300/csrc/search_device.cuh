@@ -75,6 +75,115 @@ __device__ __forceinline__ float pair_r(const float4 h, float t0, float t1, floa
     }
 }
 
+// Accumulators of the RGH sums of one point.  Slope model: S0 scalar and the
+// pairs (S1, S2), (S3, S4), (S5, S6) as packed FP32x2 registers, so one packed
+// FMA updates two sums; every sum receives exactly pair_rgh's operations in
+// the same order (S6 += ez2 is fma(ez2, 1, S6), the same rounding as the
+// add), so the totals are bitwise pair_rgh's.  add2 evaluates two hits with
+// their per-hit arithmetic packed across the hits, then accumulates hit a
+// before hit b.  2D toy: plain pair_rgh.
+template <int MODEL>
+struct RghAcc {
+    float S[Model<MODEL>::NS];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < Model<MODEL>::NS; ++i) S[i] = 0.f;
+    }
+    __device__ __forceinline__ void add(const float4 h, float t0, float t1, float kk) {
+        pair_rgh<MODEL>(h, t0, t1, kk, S);
+    }
+    __device__ __forceinline__ void add2(const float4 a, const float4 b, float t0, float t1, float kk) {
+        pair_rgh<MODEL>(a, t0, t1, kk, S);
+        pair_rgh<MODEL>(b, t0, t1, kk, S);
+    }
+    __device__ __forceinline__ void sums(float *out) const {
+#pragma unroll
+        for (int i = 0; i < Model<MODEL>::NS; ++i) out[i] = S[i];
+    }
+};
+
+template <>
+struct RghAcc<RETINA_VELO_SLOPES> {
+    float s0;
+    unsigned long long a12, a34, a56;
+    __device__ __forceinline__ void zero() {
+        s0 = 0.f;
+        a12 = a34 = a56 = 0ull;  // +0.f in both halves
+    }
+    // one hit given its residual pair r = (rx, ry), e and z
+    __device__ __forceinline__ void acc(unsigned long long r, float ry, float e, float ez, float ez2) {
+        s0 += e;
+        a12 = fma2_rn(pack2(ez, ez), r, a12);           // (ez rx, ez ry)
+        float w_rx, w_ry;
+        unpack2(mul2_rn(pack2(ez2, ez2), r), w_rx, w_ry);  // (ez2 rx, ez2 ry)
+        a34 = fma2_rn(pack2(w_rx, w_rx), r, a34);       // (ez2rx rx, ez2rx ry)
+        a56 = fma2_rn(pack2(w_ry, ez2), pack2(ry, 1.f), a56);  // (ez2ry ry, ez2)
+    }
+    __device__ __forceinline__ void add(const float4 h, float t0, float t1, float kk) {
+        const unsigned long long r = fma2_rn(pack2(-t0, -t1), pack2(h.z, h.z), pack2(h.x, h.y));
+        float rx, ry;
+        unpack2(r, rx, ry);
+        const float s2 = __fmaf_rn(rx, rx, ry * ry);
+        const float e = ex2_mufu(-s2 * kk);
+        const float ez = e * h.z;
+        acc(r, ry, e, ez, ez * h.z);
+    }
+    __device__ __forceinline__ void add2(const float4 a, const float4 b, float t0, float t1, float kk) {
+        const unsigned long long mt = pack2(-t0, -t1);
+        const unsigned long long ra = fma2_rn(mt, pack2(a.z, a.z), pack2(a.x, a.y));
+        const unsigned long long rb = fma2_rn(mt, pack2(b.z, b.z), pack2(b.x, b.y));
+        float rxa, rya, rxb, ryb;
+        unpack2(ra, rxa, rya);
+        unpack2(rb, rxb, ryb);
+        const unsigned long long yy = mul2_rn(pack2(rya, ryb), pack2(rya, ryb));
+        const unsigned long long s2 = fma2_rn(pack2(rxa, rxb), pack2(rxa, rxb), yy);
+        float xa, xb;  // -s2 * kk, as s2 * (-kk): the same rounding
+        unpack2(mul2_rn(s2, pack2(-kk, -kk)), xa, xb);
+        const float ea = ex2_mufu(xa), eb = ex2_mufu(xb);
+        const unsigned long long zz = pack2(a.z, b.z);
+        const unsigned long long ez = mul2_rn(pack2(ea, eb), zz);
+        const unsigned long long ez2 = mul2_rn(ez, zz);
+        float eza, ezb, ez2a, ez2b;
+        unpack2(ez, eza, ezb);
+        unpack2(ez2, ez2a, ez2b);
+        acc(ra, rya, ea, eza, ez2a);
+        acc(rb, ryb, eb, ezb, ez2b);
+    }
+    __device__ __forceinline__ void sums(float *out) const {
+        float v1, v2, v3, v4, v5, v6;
+        unpack2(a12, v1, v2);
+        unpack2(a34, v3, v4);
+        unpack2(a56, v5, v6);
+        out[0] = s0;
+        out[1] = v1;
+        out[2] = v2;
+        out[3] = v3;
+        out[4] = v4;
+        out[5] = v5;
+        out[6] = v6;
+    }
+};
+
+// R-only terms of two hits, added to Rt in the order a, b (bitwise pair_r's).
+template <int MODEL>
+__device__ __forceinline__ void pair_r2(const float4 a, const float4 b, float t0, float t1, float kk, float &Rt) {
+    if (MODEL == RETINA_VELO_SLOPES) {
+        const unsigned long long mt = pack2(-t0, -t1);
+        float rxa, rya, rxb, ryb;
+        unpack2(fma2_rn(mt, pack2(a.z, a.z), pack2(a.x, a.y)), rxa, rya);
+        unpack2(fma2_rn(mt, pack2(b.z, b.z), pack2(b.x, b.y)), rxb, ryb);
+        const unsigned long long yy = mul2_rn(pack2(rya, ryb), pack2(rya, ryb));
+        const unsigned long long s2 = fma2_rn(pack2(rxa, rxb), pack2(rxa, rxb), yy);
+        float xa, xb;
+        unpack2(mul2_rn(s2, pack2(-kk, -kk)), xa, xb);
+        Rt += ex2_mufu(xa);
+        Rt += ex2_mufu(xb);
+    } else {
+        Rt += pair_r<MODEL>(a, t0, t1, kk);
+        Rt += pair_r<MODEL>(b, t0, t1, kk);
+    }
+}
+
 template <int MODEL>
 __device__ __forceinline__ void sums_to_rgh(const float *S, float k, float &R, float &g0, float &g1, float &H00,
                                             float &H01, float &H11) {
@@ -175,15 +284,11 @@ __host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool
 // Lane-strided pass over an event's hits: the staged prefix from shared
 // memory (two hits per iteration for independent work), then the rest, if
 // any, straight from global memory through L1.
-template <typename F>
+template <typename F, typename F2>
 __device__ __forceinline__ void for_each_hit(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
-                                             int n_staged, int H, int lane, F &&f) {
+                                             int n_staged, int H, int lane, F &&f, F2 &&f2) {
     int k = lane;
-    for (; k + 32 < n_staged; k += 64) {
-        const float4 a = sh[k], b = sh[k + 32];
-        f(a);
-        f(b);
-    }
+    for (; k + 32 < n_staged; k += 64) f2(sh[k], sh[k + 32]);
     for (; k < n_staged; k += 32) f(sh[k]);
     for (; k < H; k += 32) f(__ldg(gh + k));
 }
@@ -233,12 +338,12 @@ __device__ __forceinline__ bool box_culled(const float4 A, const float4 B, float
 // walks those blocks in increasing order, lane l taking hit 32 b + l: the
 // same per-lane order as the full pass minus blocks whose terms are all
 // exactly zero - so every sum is bitwise the full pass's sum.
-template <typename T, typename F>
+template <typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                         int H, int lane, const float4 *__restrict__ sbox,
-                                        const float4 *__restrict__ gbox, int n_sbox, T &&needed, F &&f) {
+                                        const float4 *__restrict__ gbox, int n_sbox, T &&needed, F &&f, F2 &&f2) {
     if (!gbox) {
-        for_each_hit(sh, gh, n_staged, H, lane, f);
+        for_each_hit(sh, gh, n_staged, H, lane, f, f2);
         return H;
     }
     int visited = 0;
@@ -268,9 +373,7 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
             visited += (H - ba * 32) < 32 ? (H - ba * 32) : 32;
             if (bb >= 0) visited += (H - bb * 32) < 32 ? (H - bb * 32) : 32;
             if (bb >= 0 && bb * 32 + 32 <= n_staged) {
-                const float4 ha = sh[ka], hb = sh[kb];
-                f(ha);
-                f(hb);
+                f2(sh[ka], sh[kb]);
             } else {
                 // block ba may be staged; block bb (if any) is not: it lies past n_staged
                 if (ka < H) {
@@ -320,11 +423,9 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     for (int j = 0; j < prm.q; ++j) {
         const float kk = prm.kk[j], k = prm.k[j];
         // (R, g, H) at the current points
-        float S[P][NS];
+        RghAcc<MODEL> acc[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p)
-#pragma unroll
-            for (int i = 0; i < NS; ++i) S[p][i] = 0.f;
+        for (int p = 0; p < P; ++p) acc[p].zero();
         const int vis = hit_pass(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
                                  [&](const float4 A, const float4 B) {
                                      bool need = false;
@@ -333,10 +434,17 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                          need |= live[p] && !box_culled<MODEL>(A, B, th0[p], th1[p], kk);
                                      return need;
                                  },
-                                           [&](const float4 h) {
+                                 [&](const float4 h) {
 #pragma unroll
-                                               for (int p = 0; p < P; ++p) pair_rgh<MODEL>(h, th0[p], th1[p], kk, S[p]);
-                                           });
+                                     for (int p = 0; p < P; ++p) acc[p].add(h, th0[p], th1[p], kk);
+                                 },
+                                 [&](const float4 a, const float4 b) {
+#pragma unroll
+                                     for (int p = 0; p < P; ++p) acc[p].add2(a, b, th0[p], th1[p], kk);
+                                 });
+        float S[P][NS];
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[p].sums(S[p]);
         w_rgh += (unsigned long long)vis * (unsigned long long)n_live;
         float R[P], g0[P], g1[P], pp0[P], pp1[P], slope[P], t[P];
         bool pending[P];
@@ -379,11 +487,16 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                              need |= pending[p] && !box_culled<MODEL>(A, B, tr0[p], tr1[p], kk);
                                          return need;
                                      },
-                                               [&](const float4 h) {
+                                     [&](const float4 h) {
 #pragma unroll
-                                                   for (int p = 0; p < P; ++p)
-                                                       if (pending[p]) Rt[p] += pair_r<MODEL>(h, tr0[p], tr1[p], kk);
-                                               });
+                                         for (int p = 0; p < P; ++p)
+                                             if (pending[p]) Rt[p] += pair_r<MODEL>(h, tr0[p], tr1[p], kk);
+                                     },
+                                     [&](const float4 a, const float4 b) {
+#pragma unroll
+                                         for (int p = 0; p < P; ++p)
+                                             if (pending[p]) pair_r2<MODEL>(a, b, tr0[p], tr1[p], kk, Rt[p]);
+                                     });
             int n_pend = 0;
 #pragma unroll
             for (int p = 0; p < P; ++p) n_pend += pending[p] ? 1 : 0;
