@@ -147,6 +147,8 @@ cudaError_t launch_grid_maxima_ordered(const float *R, int n_events, const retin
 constexpr int CAND_CAP = 4096;          // candidates listed per event
 constexpr int ORDER_THREADS = 1024;
 
+// Four cells per thread (one 16-byte load when rows are a multiple of 4 cells
+// long); the neighbourhood is read only for cells >= R0.
 __global__ void __launch_bounds__(MAX_THREADS)
 maxima_detect_kernel(const float *__restrict__ Rall, int n0, int n1, float R0, int32_t *__restrict__ cand_count,
                      int32_t *__restrict__ cand) {
@@ -154,11 +156,23 @@ maxima_detect_kernel(const float *__restrict__ Rall, int n0, int n1, float R0, i
     const int64_t cells = (int64_t)n0 * n1;
     const float *R = Rall + (int64_t)e * cells;
     const int lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)blockIdx.x * MAX_BLOCK_CELLS;
-#pragma unroll 1
-    for (int m = 0; m < MAX_PER_THREAD; ++m) {
-        const int64_t c = base + (int64_t)m * MAX_THREADS + threadIdx.x;
-        const bool sel = c < cells && is_selected(R, n0, n1, c, R0);
+    const int64_t c0 = 4 * ((int64_t)blockIdx.x * MAX_THREADS + threadIdx.x);
+    float v[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    if ((n0 & 3) == 0 && c0 + 3 < cells) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(R + c0));
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (c0 + u < cells) v[u] = __ldg(R + c0 + u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t c = c0 + u;
+        const bool sel = (v[u] >= R0) && c < cells && is_selected(R, n0, n1, c, R0);
         const unsigned bal = __ballot_sync(0xffffffffu, sel);
         if (bal == 0u) continue;
         int first = 0;
@@ -255,8 +269,9 @@ cudaError_t launch_grid_maxima(const float *R, int n_events, const retina_grid *
     cudaError_t err = cudaMemsetAsync(cand_count, 0, (size_t)n_events * sizeof(int32_t), st);
     if (err != cudaSuccess) return err;
     GridDev gd{g->lo[0], g->lo[1], g->step[0], g->step[1], g->n[0], g->n[1]};
-    maxima_detect_kernel<<<dim3(maxima_blocks(g), n_events), MAX_THREADS, 0, st>>>(R, g->n[0], g->n[1], R0,
-                                                                                 cand_count, cand);
+    const int64_t cells = (int64_t)g->n[0] * g->n[1];
+    const int dblk = (int)((cells + 4 * MAX_THREADS - 1) / (4 * MAX_THREADS));
+    maxima_detect_kernel<<<dim3(dblk, n_events), MAX_THREADS, 0, st>>>(R, g->n[0], g->n[1], R0, cand_count, cand);
     maxima_order_kernel<<<n_events, ORDER_THREADS, 0, st>>>(R, gd, R0, cand_count, cand, K, max_idx, max_theta,
                                                             max_R, n_max);
     count_launches(2);

@@ -75,13 +75,10 @@ __device__ __forceinline__ float pair_r(const float4 h, float t0, float t1, floa
     }
 }
 
-// Accumulators of the RGH sums of one point.  Slope model: S0 scalar and the
-// pairs (S1, S2), (S3, S4), (S5, S6) as packed FP32x2 registers, so one packed
-// FMA updates two sums; every sum receives exactly pair_rgh's operations in
-// the same order (S6 += ez2 is fma(ez2, 1, S6), the same rounding as the
-// add), so the totals are bitwise pair_rgh's.  add2 evaluates two hits with
-// their per-hit arithmetic packed across the hits, then accumulates hit a
-// before hit b.  2D toy: plain pair_rgh.
+// Accumulators of the RGH sums of one point (add2: hit a, then hit b).
+// Packing the pair arithmetic into FP32x2 instructions was measured slower
+// here (register pressure and operand moves outweighed the saved issue
+// slots), so the sums use the scalar pair_rgh.
 template <int MODEL>
 struct RghAcc {
     float S[Model<MODEL>::NS];
@@ -102,86 +99,11 @@ struct RghAcc {
     }
 };
 
-template <>
-struct RghAcc<RETINA_VELO_SLOPES> {
-    float s0;
-    unsigned long long a12, a34, a56;
-    __device__ __forceinline__ void zero() {
-        s0 = 0.f;
-        a12 = a34 = a56 = 0ull;  // +0.f in both halves
-    }
-    // one hit given its residual pair r = (rx, ry), e and z
-    __device__ __forceinline__ void acc(unsigned long long r, float ry, float e, float ez, float ez2) {
-        s0 += e;
-        a12 = fma2_rn(pack2(ez, ez), r, a12);           // (ez rx, ez ry)
-        float w_rx, w_ry;
-        unpack2(mul2_rn(pack2(ez2, ez2), r), w_rx, w_ry);  // (ez2 rx, ez2 ry)
-        a34 = fma2_rn(pack2(w_rx, w_rx), r, a34);       // (ez2rx rx, ez2rx ry)
-        a56 = fma2_rn(pack2(w_ry, ez2), pack2(ry, 1.f), a56);  // (ez2ry ry, ez2)
-    }
-    __device__ __forceinline__ void add(const float4 h, float t0, float t1, float kk) {
-        const unsigned long long r = fma2_rn(pack2(-t0, -t1), pack2(h.z, h.z), pack2(h.x, h.y));
-        float rx, ry;
-        unpack2(r, rx, ry);
-        const float s2 = __fmaf_rn(rx, rx, ry * ry);
-        const float e = ex2_mufu(-s2 * kk);
-        const float ez = e * h.z;
-        acc(r, ry, e, ez, ez * h.z);
-    }
-    __device__ __forceinline__ void add2(const float4 a, const float4 b, float t0, float t1, float kk) {
-        const unsigned long long mt = pack2(-t0, -t1);
-        const unsigned long long ra = fma2_rn(mt, pack2(a.z, a.z), pack2(a.x, a.y));
-        const unsigned long long rb = fma2_rn(mt, pack2(b.z, b.z), pack2(b.x, b.y));
-        float rxa, rya, rxb, ryb;
-        unpack2(ra, rxa, rya);
-        unpack2(rb, rxb, ryb);
-        const unsigned long long yy = mul2_rn(pack2(rya, ryb), pack2(rya, ryb));
-        const unsigned long long s2 = fma2_rn(pack2(rxa, rxb), pack2(rxa, rxb), yy);
-        float xa, xb;  // -s2 * kk, as s2 * (-kk): the same rounding
-        unpack2(mul2_rn(s2, pack2(-kk, -kk)), xa, xb);
-        const float ea = ex2_mufu(xa), eb = ex2_mufu(xb);
-        const unsigned long long zz = pack2(a.z, b.z);
-        const unsigned long long ez = mul2_rn(pack2(ea, eb), zz);
-        const unsigned long long ez2 = mul2_rn(ez, zz);
-        float eza, ezb, ez2a, ez2b;
-        unpack2(ez, eza, ezb);
-        unpack2(ez2, ez2a, ez2b);
-        acc(ra, rya, ea, eza, ez2a);
-        acc(rb, ryb, eb, ezb, ez2b);
-    }
-    __device__ __forceinline__ void sums(float *out) const {
-        float v1, v2, v3, v4, v5, v6;
-        unpack2(a12, v1, v2);
-        unpack2(a34, v3, v4);
-        unpack2(a56, v5, v6);
-        out[0] = s0;
-        out[1] = v1;
-        out[2] = v2;
-        out[3] = v3;
-        out[4] = v4;
-        out[5] = v5;
-        out[6] = v6;
-    }
-};
-
-// R-only terms of two hits, added to Rt in the order a, b (bitwise pair_r's).
+// R-only terms of two hits, added to Rt in the order a, b.
 template <int MODEL>
 __device__ __forceinline__ void pair_r2(const float4 a, const float4 b, float t0, float t1, float kk, float &Rt) {
-    if (MODEL == RETINA_VELO_SLOPES) {
-        const unsigned long long mt = pack2(-t0, -t1);
-        float rxa, rya, rxb, ryb;
-        unpack2(fma2_rn(mt, pack2(a.z, a.z), pack2(a.x, a.y)), rxa, rya);
-        unpack2(fma2_rn(mt, pack2(b.z, b.z), pack2(b.x, b.y)), rxb, ryb);
-        const unsigned long long yy = mul2_rn(pack2(rya, ryb), pack2(rya, ryb));
-        const unsigned long long s2 = fma2_rn(pack2(rxa, rxb), pack2(rxa, rxb), yy);
-        float xa, xb;
-        unpack2(mul2_rn(s2, pack2(-kk, -kk)), xa, xb);
-        Rt += ex2_mufu(xa);
-        Rt += ex2_mufu(xb);
-    } else {
-        Rt += pair_r<MODEL>(a, t0, t1, kk);
-        Rt += pair_r<MODEL>(b, t0, t1, kk);
-    }
+    Rt += pair_r<MODEL>(a, t0, t1, kk);
+    Rt += pair_r<MODEL>(b, t0, t1, kk);
 }
 
 template <int MODEL>
