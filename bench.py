@@ -334,7 +334,9 @@ def main():
     #   0 start | prepare | 1 | grid | 2 | maxima + extract | 3     (main stream)
     #   4 | search | 5 | extract | 6                                (search stream)
     #   join, 7 end                                                 (main stream)
-    stream2 = torch.cuda.Stream(dev) if not args.serial else stream
+    # the search branch is the longer one: its stream gets the higher priority,
+    # so its kernels' CTAs go first whenever an SM frees up
+    stream2 = torch.cuda.Stream(dev, priority=-1) if not args.serial else stream
     sync_ev = [torch.cuda.Event() for _ in range(8)]
 
     def step(evs=None):
