@@ -93,6 +93,9 @@ extern "C" {
 #define RETINA_OPT_BATCH_CTAS 8        /* batched search CTAs, 0 = fill the GPU (0);
                                           fewer leave room for kernels running
                                           concurrently on other streams          */
+#define RETINA_OPT_SEEDNET_TC 9        /* seed net's second convolution on the
+                                          tcgen05 tensor cores (1) or the FP32
+                                          CUDA cores (0)                          */
 
 typedef struct {
     float lo[2];   /* lower edge of the box per axis                      */
@@ -120,6 +123,12 @@ int retina_abi_version(void);
  * Returns RETINA_EINVAL for an unknown option or an out-of-range value. */
 int retina_set_option(int32_t option, int32_t value);
 int retina_get_option(int32_t option, int32_t *value);
+
+/* Device-side error flag of the library (on the current device): kernels set
+ * it to 1 when one of their bounded waits expires (their outputs are then
+ * not valid) instead of hanging or trapping.  flag (nullable, host) receives
+ * it; reset = 1 clears it.  Synchronous device copies. */
+int retina_device_error(int32_t *flag, int32_t reset);
 
 /* Number of kernels this library has launched in this process (all entry
  * points, all threads); callers difference it around a region to count the

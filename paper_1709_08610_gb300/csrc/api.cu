@@ -19,6 +19,12 @@ static std::atomic<int> g_opt_batch_spw{1};
 static std::atomic<int> g_opt_batch_warps{16};
 static std::atomic<int> g_opt_batch_smem_hits{8192};
 static std::atomic<int> g_opt_batch_ctas{0};
+static std::atomic<int> g_opt_seednet_tc{0};
+
+int option_value(int option) {
+    int32_t v = 0;
+    return retina_get_option(option, &v) == RETINA_OK ? v : 0;
+}
 
 static bool finite_pos(float v) { return isfinite(v) && v > 0.f; }
 
@@ -106,6 +112,10 @@ int retina_set_option(int32_t option, int32_t value) {
             if (value < 0 || value > (1 << 20)) return RETINA_EINVAL;
             g_opt_batch_ctas = value;
             return RETINA_OK;
+        case RETINA_OPT_SEEDNET_TC:
+            if (value != 0 && value != 1) return RETINA_EINVAL;
+            g_opt_seednet_tc = value;
+            return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -121,6 +131,7 @@ int retina_get_option(int32_t option, int32_t *value) {
         case RETINA_OPT_BATCH_WARPS: *value = g_opt_batch_warps; return RETINA_OK;
         case RETINA_OPT_BATCH_SMEM_HITS: *value = g_opt_batch_smem_hits; return RETINA_OK;
         case RETINA_OPT_BATCH_CTAS: *value = g_opt_batch_ctas; return RETINA_OK;
+        case RETINA_OPT_SEEDNET_TC: *value = g_opt_seednet_tc; return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }

@@ -50,6 +50,10 @@ int maxima_blocks(const retina_grid *g);
 int sm_count();
 cudaError_t ensure_dynamic_smem(const void *func, size_t bytes);
 unsigned long long *work_counters();
+int32_t *device_error_flag();
+int option_value(int option);
+cudaError_t launch_conv2_head_tc(const uint16_t *h1, int n_events, const float *params, uint16_t *h2, float *logits,
+                                 int32_t *err, cudaStream_t st);
 void count_launches(int n);
 size_t extract_smem_bytes(int n_points);
 

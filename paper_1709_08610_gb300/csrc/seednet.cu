@@ -557,8 +557,14 @@ cudaError_t launch_seednet_forward(const uint16_t *feat, int n_events, const flo
                                    uint16_t *h1, uint16_t *h2, cudaStream_t st) {
     dim3 grid(n_events, TILES);
     conv1_kernel<<<grid, SN_THREADS, 0, st>>>(feat, params, h1);
-    const size_t smem = (size_t)CONV2_SMEM_FLOATS * sizeof(float);
+    count_launches(1);
     cudaError_t err;
+    if (option_value(RETINA_OPT_SEEDNET_TC)) {
+        int32_t *flag = device_error_flag();
+        if (!flag) return cudaErrorInvalidSymbol;
+        return launch_conv2_head_tc(h1, n_events, params, h2, logits, flag, st);
+    }
+    const size_t smem = (size_t)CONV2_SMEM_FLOATS * sizeof(float);
     if (h2) {
         err = ensure_dynamic_smem(reinterpret_cast<const void *>(conv2_head_kernel<true>), smem);
         if (err != cudaSuccess) return err;
@@ -568,7 +574,7 @@ cudaError_t launch_seednet_forward(const uint16_t *feat, int n_events, const flo
         if (err != cudaSuccess) return err;
         conv2_head_kernel<false><<<grid, SN_THREADS, smem, st>>>(h1, params, nullptr, logits);
     }
-    count_launches(2);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -27,9 +27,39 @@ unsigned long long *work_counters() {
     return g_work_ptr[dev];
 }
 
+// Device-side error flag of the library: set (to 1) by a kernel whose
+// bounded wait expired; read and cleared with retina_device_error.
+static __device__ int32_t g_dev_error;
+static int32_t *g_err_ptr[64] = {nullptr};
+
+int32_t *device_error_flag() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_work_mu);
+    if (!g_err_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dev_error) != cudaSuccess) return nullptr;
+        g_err_ptr[dev] = static_cast<int32_t *>(p);
+    }
+    return g_err_ptr[dev];
+}
+
 }  // namespace retina
 
 using namespace retina;
+
+extern "C" int retina_device_error(int32_t *flag, int32_t reset) {
+    if (flag) {
+        int32_t v = 0;
+        if (cudaMemcpyFromSymbol(&v, g_dev_error, sizeof(v)) != cudaSuccess) return RETINA_ECUDA;
+        *flag = v;
+    }
+    if (reset) {
+        const int32_t zero = 0;
+        if (cudaMemcpyToSymbol(g_dev_error, &zero, sizeof(zero)) != cudaSuccess) return RETINA_ECUDA;
+    }
+    return RETINA_OK;
+}
 
 extern "C" int retina_work_counters(int32_t enable, int32_t reset, uint64_t *out) {
     if (reset) {

@@ -25,6 +25,7 @@ MAX_Q = 8
 MAX_EXTRACT_POINTS = 8192
 OPT_LS_SEEDS_PER_WARP, OPT_LS_SMEM_HITS, OPT_GRID_SPLITS, OPT_LS_WARPS = 1, 2, 3, 4
 OPT_BATCH_SEEDS_PER_WARP, OPT_BATCH_WARPS, OPT_BATCH_SMEM_HITS, OPT_BATCH_CTAS = 5, 6, 7, 8
+OPT_SEEDNET_TC = 9
 
 HEADER = os.path.join(_build.INCLUDE, "retina.h")
 
@@ -109,6 +110,7 @@ def _load():
     L.retina_prepare_hits_box_count.restype = I64
     L.retina_prepare_hits.argtypes = [P, I64, P, I32, I32, P, P, P]
     L.retina_work_counters.argtypes = [I32, I32, P]
+    L.retina_device_error.argtypes = [P, I32]
     L.retina_launch_count.restype = ctypes.c_uint64
     L.retina_alu_probe_sink_floats.restype = ctypes.c_int64
     L.retina_alu_probe.argtypes = [I32, I32, P, P, P]
@@ -128,7 +130,7 @@ def _load():
                  "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
                  "retina_local_search", "retina_extract_tracks", "retina_slope_histogram",
                  "retina_seednet_forward", "retina_seednet_train_workspace_size", "retina_seednet_train_step",
-                 "retina_seednet_adam", "retina_topk_seeds"):
+                 "retina_seednet_adam", "retina_topk_seeds", "retina_device_error"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -250,6 +252,13 @@ def work_counters(enable: Optional[bool] = None, reset: bool = False) -> list:
     out = (ctypes.c_uint64 * 4)()
     _check("retina_work_counters", lib.retina_work_counters(-1 if enable is None else int(enable), int(reset), out))
     return list(out)
+
+
+def device_error(reset: bool = False) -> int:
+    """The library's device-side error flag (1 after a kernel's bounded wait expired)."""
+    v = ctypes.c_int32()
+    _check("retina_device_error", lib.retina_device_error(ctypes.byref(v), int(reset)))
+    return v.value
 
 
 def launch_count() -> int:

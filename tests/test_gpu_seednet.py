@@ -35,6 +35,18 @@ def rt():
     return retina
 
 
+@pytest.fixture(params=[0, 1], ids=["cuda_cores", "tensor_cores"])
+def conv2_path(rt, request):
+    """The second convolution on the FP32 CUDA cores or the tcgen05 tensor cores."""
+    old = rt.get_option(rt.OPT_SEEDNET_TC)
+    rt.set_option(rt.OPT_SEEDNET_TC, request.param)
+    rt.device_error(reset=True)
+    yield request.param
+    torch.cuda.synchronize()
+    rt.set_option(rt.OPT_SEEDNET_TC, old)
+    assert rt.device_error() == 0
+
+
 def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
@@ -130,7 +142,7 @@ def _logit_bound(fw, params):
 
 
 @pytest.mark.parametrize("pseed,scale", [(7, 1.0), (8, 3.0)])
-def test_forward_matches_oracle(rt, pseed, scale):
+def test_forward_matches_oracle(rt, conv2_path, pseed, scale):
     evs = _events(3)
     b = batch_of(evs)
     feat = rt.slope_histogram(_dev(b.hits), _dev(b.offsets))
@@ -203,7 +215,7 @@ def _grad_abs_scale(fws, labels, params, pw):
 BLOCKS = dict(W1=(0, 144), b1=(144, 160), W2=(160, 4768), b2=(4768, 4800), W3=(4800, 4832), b3=(4832, 4833))
 
 
-def test_train_step_gradient_and_loss_match_oracle(rt):
+def test_train_step_gradient_and_loss_match_oracle(rt, conv2_path):
     evs = _events(4)
     b = batch_of(evs)
     feat = rt.slope_histogram(_dev(b.hits), _dev(b.offsets))
@@ -345,7 +357,7 @@ def test_proposed_seeds_match_oracle(rt, K, n_min):
 # full size: 1024 ragged events (the batched workload's shapes), sampled
 # ---------------------------------------------------------------------------
 
-def test_proposer_at_full_batch_size(rt):
+def test_proposer_at_full_batch_size(rt, conv2_path):
     wl = WORKLOADS["velo_batch"]
     evs = [make_event(wl, 12, e, vertex_sigma=(0, 0, 0)) for e in range(1024)]
     b = batch_of(evs)
