@@ -95,7 +95,7 @@ extern "C" {
                                           concurrently on other streams          */
 #define RETINA_OPT_SEEDNET_TC 9        /* seed net's second convolution on the
                                           tcgen05 tensor cores (1) or the FP32
-                                          CUDA cores (0)                          */
+                                          CUDA cores (0); default 1               */
 
 typedef struct {
     float lo[2];   /* lower edge of the box per axis                      */

@@ -177,7 +177,7 @@ conv2_head_tc_kernel(const uint16_t *__restrict__ h1, const float *__restrict__ 
         const bool ok = mbar_wait(bar_addr, phase);
         phase ^= 1u;
         tc_fence_after();
-        if (!ok) {
+        if (!__syncthreads_and(ok)) {  // every thread leaves together
             failed = true;
             break;
         }
