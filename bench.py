@@ -230,15 +230,18 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         return statistics.median(ts)
 
     n0, n1 = wl.grid_n
+    # throughput-bound batches: spatially ordered seeds, two per warp (measured
+    # ~16 % faster than one per warp on 1024 events)
+    shape = dict(sort_seeds=True, seeds_per_warp=2)
     runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
-            ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0),
+            ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0, **shape),
              np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),
-            ("uniform_%d" % learned_k, lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0),
+            ("uniform_%d" % learned_k, lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, **shape),
              np.stack([uniform_seeds(wl, learned_k, BATCH_RUN_SEED, e) for e in range(E)]))]
     if os.path.exists(DEFAULT_WEIGHTS):
         prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS)
         runs.append(("learned_%d" % learned_k,
-                     lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, proposer=prop), None))
+                     lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, proposer=prop, **shape), None))
     found = {}
     for name, make, seeds in runs:
         obj = make()

@@ -358,6 +358,24 @@ int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *even
                           float *R_out, uint8_t *status, uint8_t *n_evals, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * retina_sort_seeds - spatial order of each event's starting points.
+ *
+ * Algorithm 1 treats its starting points independently, so their order is
+ * free; consecutive points close in theta need mostly the same hit blocks,
+ * which lets retina_batched_search with RETINA_OPT_BATCH_SEEDS_PER_WARP > 1
+ * share block tests and hit loads.  Per event (rows seed_offsets[e] ..
+ * seed_offsets[e+1]-1, in chunks of 8192): sorted by a Morton code of the
+ * position in `box` quantised to 9 bits per axis (outside points clamp to the
+ * edge, non-finite ones go last), then by original position.  Results of a
+ * search on the sorted points belong to the sorted order; perm maps back.
+ *
+ *   seeds, sorted_out : float32 [n_seeds][2], 8-byte aligned, not the same array.
+ *   perm_out  : nullable int32 [n_seeds]: original row of each sorted row.
+ */
+int retina_sort_seeds(const float *seeds, int64_t n_seeds, const int64_t *seed_offsets, int32_t n_events,
+                      const retina_grid *box, float *sorted_out, int32_t *perm_out, void *stream);
+
+/*
  * retina_extract_tracks - cluster the points and keep the best of each.
  *
  * Paper: Algorithm 1, "cluster solutions" and "for each cluster select the

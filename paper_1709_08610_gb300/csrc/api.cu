@@ -311,6 +311,16 @@ int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *even
                                              g_opt_batch_smem_hits, g_opt_batch_ctas, (cudaStream_t)stream));
 }
 
+int retina_sort_seeds(const float *seeds, int64_t n_seeds, const int64_t *seed_offsets, int32_t n_events,
+                      const retina_grid *box, float *sorted_out, int32_t *perm_out, void *stream) {
+    if (n_events < 0 || n_seeds < 0 || !valid_grid(box)) return RETINA_EINVAL;
+    if (n_events == 0 || n_seeds == 0) return RETINA_OK;
+    if (!seeds || !seed_offsets || !sorted_out || seeds == sorted_out) return RETINA_EINVAL;
+    if (((uintptr_t)seeds & 7u) || ((uintptr_t)sorted_out & 7u)) return RETINA_EINVAL;
+    return cuda_status(launch_sort_seeds(seeds, n_seeds, seed_offsets, n_events, box, sorted_out, perm_out,
+                                         (cudaStream_t)stream));
+}
+
 int retina_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
                           int32_t n_events, int32_t n_points, const retina_grid *box, float R0, float merge_cells,
                           float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int32_t K,

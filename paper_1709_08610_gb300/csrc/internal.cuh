@@ -47,6 +47,8 @@ int64_t prepared_box_count(int64_t n_hits, int n_events);
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                                 float4 *sorted, float4 *boxes, cudaStream_t st);
 int maxima_blocks(const retina_grid *g);
+cudaError_t launch_sort_seeds(const float *seeds, int64_t n_seeds, const int64_t *off, int n_events,
+                              const retina_grid *box, float *out, int32_t *perm, cudaStream_t st);
 int sm_count();
 cudaError_t ensure_dynamic_smem(const void *func, size_t bytes);
 unsigned long long *work_counters();

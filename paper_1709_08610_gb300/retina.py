@@ -111,6 +111,7 @@ def _load():
     L.retina_prepare_hits.argtypes = [P, I64, P, I32, I32, P, P, P]
     L.retina_work_counters.argtypes = [I32, I32, P]
     L.retina_device_error.argtypes = [P, I32]
+    L.retina_sort_seeds.argtypes = [P, I64, P, I32, P, P, P, P]
     L.retina_launch_count.restype = ctypes.c_uint64
     L.retina_alu_probe_sink_floats.restype = ctypes.c_int64
     L.retina_alu_probe.argtypes = [I32, I32, P, P, P]
@@ -130,7 +131,8 @@ def _load():
                  "retina_grid_maxima_workspace_size", "retina_grid_maxima", "retina_response",
                  "retina_local_search", "retina_extract_tracks", "retina_slope_histogram",
                  "retina_seednet_forward", "retina_seednet_train_workspace_size", "retina_seednet_train_step",
-                 "retina_seednet_adam", "retina_topk_seeds", "retina_device_error"):
+                 "retina_seednet_adam", "retina_topk_seeds", "retina_device_error",
+                 "retina_sort_seeds"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -393,6 +395,22 @@ def batched_search(hits: torch.Tensor, offsets: torch.Tensor, model: int, seeds:
         _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, _p(seeds), S, _p(seed_offsets), _p(order), ctypes.byref(o),
         ctypes.byref(g), _p(out[0]), _p(out[1]), _p(out[2]), _p(n_evals), _p(ws), ws.numel(), _stream(stream)))
     return out
+
+
+def sort_seeds(seeds: torch.Tensor, seed_offsets: torch.Tensor, box: Grid, out: Optional[torch.Tensor] = None,
+               perm: Optional[torch.Tensor] = None, want_perm: bool = False, stream=None):
+    """Seeds [S, 2] in spatial order per event (and the int32 map to the original rows if asked)."""
+    _dev(seeds, torch.float32, "seeds", 2)
+    _dev(seed_offsets, torch.int64, "seed_offsets")
+    E = seed_offsets.numel() - 1
+    S = seeds.numel() // 2
+    out = out if out is not None else torch.empty_like(seeds)
+    if want_perm and perm is None:
+        perm = torch.empty((S,), dtype=torch.int32, device=seeds.device)
+    g = box.c()
+    _check("retina_sort_seeds", lib.retina_sort_seeds(_p(seeds), S, _p(seed_offsets), E, ctypes.byref(g), _p(out),
+                                                      _p(perm), _stream(stream)))
+    return (out, perm) if (want_perm or perm is not None) else out
 
 
 def extract_tracks(theta: torch.Tensor, R: torch.Tensor, status: Optional[torch.Tensor], box: Grid, R0: float,

@@ -191,3 +191,13 @@ def test_seednet_entries_reject_before_launch():
     assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 3, None, 0, None, None, None, None) == EINVAL
     assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 3, BOGUS, 10, None, BOGUS, None, None) == EINVAL
     assert T(None, 0, 16, -0.5, 0.5, 50.0, 3, None, 0, None, None, None, None) == OK
+
+
+def test_sort_seeds_rejects_before_launch():
+    g = rt.Grid((-0.5, -0.5), (2 ** -10, 2 ** -10), (1024, 1024)).c()
+    bad = rt.Grid((-0.5, -0.5), (0.0, 2 ** -10), (1024, 1024)).c()
+    assert L.retina_sort_seeds(BOGUS, 10, BOGUS, 1, ctypes.byref(bad), ctypes.c_void_p(0x2000), None, None) == EINVAL
+    assert L.retina_sort_seeds(BOGUS, 10, BOGUS, 1, ctypes.byref(g), BOGUS, None, None) == EINVAL  # in place
+    assert L.retina_sort_seeds(ctypes.c_void_p(0x1004), 10, BOGUS, 1, ctypes.byref(g), ctypes.c_void_p(0x2000),
+                               None, None) == EINVAL  # misaligned
+    assert L.retina_sort_seeds(None, 0, None, 0, ctypes.byref(g), None, None, None) == 0

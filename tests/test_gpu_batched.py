@@ -143,3 +143,48 @@ def test_batched_search_replays_in_a_cuda_graph(rt):
         torch.cuda.synchronize()
         for x, y in zip(eager, out):
             np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+def _morton9(S, box):
+    """Host restatement of the documented seed key (9-bit Morton code in the box)."""
+    lo = np.asarray(box.lo, np.float32)
+    inv = (1.0 / (np.asarray(box.n, np.float64) * np.asarray(box.step, np.float64))).astype(np.float32)
+    q = (S.astype(np.float32) - lo) * inv
+    qi = np.where(q > 0, np.where(q < 1, np.floor(q * np.float32(512)).astype(np.int64) & 511, 511), 0)
+
+    def spread(v):
+        out = np.zeros_like(v)
+        for i in range(9):
+            out |= ((v >> i) & 1) << (2 * i)
+        return out
+    return spread(qi[:, 0]) | (spread(qi[:, 1]) << 1)
+
+
+def test_sorted_seeds_are_a_spatial_permutation_and_search_results_follow_them(rt):
+    wl, evs, b, seeds, so = _ragged(4)
+    seeds = seeds.copy()
+    seeds[3] = np.nan                       # a non-finite point goes last in its event
+    box = rt.Grid.of(wl)
+    srt, perm = rt.sort_seeds(_dev(seeds), _dev(so), box, want_perm=True)
+    srt, perm = srt.cpu().numpy(), perm.cpu().numpy()
+    for e in range(len(evs)):
+        s0, s1 = so[e], so[e + 1]
+        p = perm[s0:s1]
+        assert sorted(p.tolist()) == list(range(s0, s1))
+        np.testing.assert_array_equal(srt[s0:s1], seeds[p])
+        fin = np.isfinite(seeds[p]).all(1)
+        key = np.where(fin, _morton9(seeds[p], box), 1 << 18) * (1 << 13) + (p - s0)
+        assert np.all(np.diff(key) > 0)
+    # the search is per seed: on sorted points with two seeds per warp, every
+    # result is bitwise the unsorted one-seed-per-warp result of the same point
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    ref = rt.batched_search(_dev(b.hits), _dev(b.offsets), 1, _dev(seeds), _dev(so), opts, box)
+    old = rt.get_option(rt.OPT_BATCH_SEEDS_PER_WARP)
+    rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, 2)
+    try:
+        got = rt.batched_search(_dev(b.hits), _dev(b.offsets), 1, _dev(srt), _dev(so), opts, box)
+    finally:
+        rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, old)
+    for x, y in zip(ref, got):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        np.testing.assert_array_equal(x[perm], y)
