@@ -75,6 +75,8 @@ extern "C" {
 #define RETINA_GRID_AUTO 0
 #define RETINA_GRID_DIRECT 1    /* force the per-pair exp kernel           */
 #define RETINA_GRID_SEPARABLE 2 /* force exp(-u^2-v^2)=exp(-u^2)exp(-v^2)   */
+#define RETINA_GRID_TENSOR 3    /* the separable contraction on the tcgen05
+                                   tensor cores (3 x TF32 split products)    */
                                 /* contraction (RETINA_VELO_SLOPES only)     */
 
 /* maximum number of local-search updates q */
@@ -93,6 +95,9 @@ extern "C" {
 #define RETINA_OPT_BATCH_CTAS 8        /* batched search CTAs, 0 = fill the GPU (0);
                                           fewer leave room for kernels running
                                           concurrently on other streams          */
+#define RETINA_OPT_GRID_TC 10          /* RETINA_GRID_AUTO on slope-model grids
+                                          picks the tensor-core contraction (1)
+                                          or the CUDA-core one (0); default 0   */
 #define RETINA_OPT_SEEDNET_TC 9        /* seed net's second convolution on the
                                           tcgen05 tensor cores (1) or the FP32
                                           CUDA cores (0); default 1               */

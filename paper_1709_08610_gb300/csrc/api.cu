@@ -20,6 +20,7 @@ static std::atomic<int> g_opt_batch_warps{16};
 static std::atomic<int> g_opt_batch_smem_hits{8192};
 static std::atomic<int> g_opt_batch_ctas{0};
 static std::atomic<int> g_opt_seednet_tc{1};
+static std::atomic<int> g_opt_grid_tc{0};
 
 int option_value(int option) {
     int32_t v = 0;
@@ -116,6 +117,10 @@ int retina_set_option(int32_t option, int32_t value) {
             if (value != 0 && value != 1) return RETINA_EINVAL;
             g_opt_seednet_tc = value;
             return RETINA_OK;
+        case RETINA_OPT_GRID_TC:
+            if (value != 0 && value != 1) return RETINA_EINVAL;
+            g_opt_grid_tc = value;
+            return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -132,6 +137,7 @@ int retina_get_option(int32_t option, int32_t *value) {
         case RETINA_OPT_BATCH_SMEM_HITS: *value = g_opt_batch_smem_hits; return RETINA_OK;
         case RETINA_OPT_BATCH_CTAS: *value = g_opt_batch_ctas; return RETINA_OK;
         case RETINA_OPT_SEEDNET_TC: *value = g_opt_seednet_tc; return RETINA_OK;
+        case RETINA_OPT_GRID_TC: *value = g_opt_grid_tc; return RETINA_OK;
         default: return RETINA_EINVAL;
     }
 }
@@ -140,8 +146,8 @@ int retina_grid_scan_workspace_size(int32_t n_events, int32_t model, const retin
                                     int32_t store_R, size_t *bytes) {
     if (!bytes || n_events < 0 || !valid_grid(g)) return RETINA_EINVAL;
     if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
-    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_SEPARABLE) return RETINA_EINVAL;
-    if (flags == RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_TENSOR) return RETINA_EINVAL;
+    if (flags >= RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
     const GridPlan p = plan_grid(n_events, model, g, flags, g_opt_grid_splits);
     *bytes = grid_ws_layout(p, n_events, g, store_R != 0).total;
     return RETINA_OK;
@@ -154,8 +160,8 @@ int retina_grid_scan(const float *hits, int64_t n_hits, const int64_t *event_off
     if (n_events < 0 || n_hits < 0 || !valid_grid(g) || !finite_pos(sigma) || isnan(R0) || K < 1)
         return RETINA_EINVAL;
     if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
-    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_SEPARABLE) return RETINA_EINVAL;
-    if (flags == RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_TENSOR) return RETINA_EINVAL;
+    if (flags >= RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
     if (n_events == 0) return RETINA_OK;
     if (!event_offsets || !max_idx || !max_theta || !max_R || !n_max) return RETINA_EINVAL;
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
@@ -180,8 +186,8 @@ int retina_grid_response_workspace_size(int32_t n_events, int32_t model, const r
                                         size_t *bytes) {
     if (!bytes || n_events < 0 || !valid_grid(g)) return RETINA_EINVAL;
     if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
-    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_SEPARABLE) return RETINA_EINVAL;
-    if (flags == RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_TENSOR) return RETINA_EINVAL;
+    if (flags >= RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
     const GridPlan p = plan_grid(n_events, model, g, flags, g_opt_grid_splits);
     *bytes = round_up(grid_partials_bytes(p, n_events, g), 256);
     return RETINA_OK;
@@ -192,8 +198,8 @@ int retina_grid_response(const float *hits, int64_t n_hits, const int64_t *event
                          size_t ws_bytes, void *stream) {
     if (n_events < 0 || n_hits < 0 || !valid_grid(g) || !finite_pos(sigma)) return RETINA_EINVAL;
     if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
-    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_SEPARABLE) return RETINA_EINVAL;
-    if (flags == RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (flags < RETINA_GRID_AUTO || flags > RETINA_GRID_TENSOR) return RETINA_EINVAL;
+    if (flags >= RETINA_GRID_SEPARABLE && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
     if (n_events == 0) return RETINA_OK;
     if (!event_offsets || !R_out || !aligned16(R_out)) return RETINA_EINVAL;
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;

@@ -22,7 +22,7 @@
 // (tile, slice, event)) so that a single event fills the GPU; slice partial
 // grids are then summed in fixed slice order by reduce_partials_kernel, so
 // results are deterministic.
-#include "internal.cuh"
+#include "grid_device.cuh"
 
 namespace retina {
 
@@ -38,44 +38,6 @@ __device__ __forceinline__ void slice_range(const int64_t *off, int64_t n_hits, 
     per = (per + align - 1) / align * align;
     k0 = hb + (int64_t)s * per;
     k1 = k0 + per < he ? k0 + per : he;
-}
-
-// Exact skipping of hit blocks for a whole tile of cells (boxes from
-// retina_prepare_hits): the lower bound, over the tile's parameter range and
-// the block's box, of the exponent s^2 log2(e) / sigma^2 (or of one axis's
-// part of it for the separable panels) must exceed GRID_CULL_EXPONENT, so
-// that every skipped ex2.approx.ftz value is exactly zero (x > 126; 140
-// leaves a margin, and a relative slack of 1e-6 per magnitude covers the
-// rounding of the bound).  Non-finite boxes are never skipped.
-constexpr float GRID_CULL_EXPONENT = 140.f;
-
-// Distance between the intervals [al, ah] and [bl, bh], minus a rounding
-// slack of 1e-6 per magnitude; 0 when they overlap.
-__device__ __forceinline__ float gap_ii(float al, float ah, float bl, float bh) {
-    const float d = fmaxf(fmaxf(bl - ah, al - bh), 0.f);
-    return fmaxf(d - 1e-6f * (fabsf(al) + fabsf(ah) + fabsf(bl) + fabsf(bh)), 0.f);
-}
-
-struct TileRange {
-    float t0l, t0h, t1l, t1h;  // cell-centre range of the tile's valid cells
-};
-
-__device__ __forceinline__ TileRange tile_range(const GridDev &g, int ti0, int tj0, int w0, int w1) {
-    const int i1 = (ti0 + w0 - 1 < g.n0 - 1) ? ti0 + w0 - 1 : g.n0 - 1;
-    const int j1 = (tj0 + w1 - 1 < g.n1 - 1) ? tj0 + w1 - 1 : g.n1 - 1;
-    return TileRange{cell_centre(g.lo0, g.step0, ti0), cell_centre(g.lo0, g.step0, i1),
-                     cell_centre(g.lo1, g.step1, tj0), cell_centre(g.lo1, g.step1, j1)};
-}
-
-// Slope-model boxes (umin, umax, vmin, vmax | |z|min, |z|max): for every
-// cell of the tile and hit of the block, (x - t_x z)^2 = z^2 (u - t_x)^2 >=
-// |z|min^2 gap(t_x range, u range)^2, likewise for y.  Separable panels are
-// all zero when either axis alone exceeds the cut.
-__device__ __forceinline__ bool block_zero_sep(const float4 A, const float4 B, const TileRange &r, float kk) {
-    if (!isfinite(B.x)) return false;
-    const float du = gap_ii(r.t0l, r.t0h, A.x, A.y), dv = gap_ii(r.t1l, r.t1h, A.z, A.w);
-    const float z2k = B.x * B.x * kk;
-    return du * du * z2k > GRID_CULL_EXPONENT || dv * dv * z2k > GRID_CULL_EXPONENT;
 }
 
 template <int MODEL>
@@ -368,11 +330,13 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
 GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int forced_splits) {
     GridPlan p;
     p.separable = (model == RETINA_VELO_SLOPES) && (flags != RETINA_GRID_DIRECT);
+    p.tc = p.separable && (flags == RETINA_GRID_TENSOR ||
+                           (flags == RETINA_GRID_AUTO && option_value(RETINA_OPT_GRID_TC) != 0));
     const int tile = p.separable ? SEP_BM : DIR_TILE;
     p.tiles0 = (g->n[0] + tile - 1) / tile;
     p.tiles1 = (g->n[1] + tile - 1) / tile;
     const int64_t ctas = (int64_t)p.tiles0 * p.tiles1 * (n_events > 0 ? n_events : 1);
-    const int per_sm = p.separable ? 2 : 4;
+    const int per_sm = p.tc ? 3 : (p.separable ? 2 : 4);
     const int64_t target = 4LL * sm_count() * per_sm;
     int64_t s = (target + ctas - 1) / ctas;
     if (s < 1) s = 1;
@@ -397,7 +361,14 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
     float *dst = p.splits > 1 ? partials : R;
     const int64_t split_stride = cells * n_events;
     dim3 grid(p.tiles0 * p.tiles1, p.splits, n_events);
-    if (p.separable) {
+    if (p.tc) {
+        int32_t *flag = device_error_flag();
+        if (!flag) return cudaErrorInvalidSymbol;
+        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(grid_tc_kernel), grid_tc_smem_bytes());
+        if (aerr != cudaSuccess) return aerr;
+        grid_tc_kernel<<<grid, 256, grid_tc_smem_bytes(), st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst,
+                                                                split_stride, cells, work_counters(), flag);
+    } else if (p.separable) {
         grid_sep_kernel<<<grid, SEP_THREADS, 0, st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst, split_stride, cells,
                                                       work_counters());
     } else if (model == RETINA_VELO_SLOPES) {

@@ -1,0 +1,261 @@
+// Grid response of the slope model (Eq. 2) as a tensor-core contraction
+// (tcgen05, kind::tf32, sm_103a).
+//
+// For an axis-aligned (t_x, t_y) grid, exp(-s^2/sigma^2) factorises:
+//   R[j][i] = sum_k A[i][k] B[j][k],  A[i][k] = ex2(-(x_k - t_x,i z_k)^2 kk),
+//                                      B[j][k] = ex2(-(y_k - t_y,j z_k)^2 kk)
+// (the same exponentials, formed the same way, as grid_sep_kernel).  A CTA owns
+// a 128 x 128 tile of cells; for every 32-hit block that can contribute to the
+// tile (exact block skipping, as grid_sep_kernel) it builds the two 128 x 32
+// FP32 panels and accumulates A B^T into a 128 x 128 FP32 accumulator in
+// tensor memory with TF32 MMAs (M = N = 128, K = 8).  TF32 keeps 10 mantissa
+// bits, so each panel is split into hi = (value with its 13 low mantissa bits
+// cleared) and lo = value - hi (exact), and three products hi.hi + hi.lo +
+// lo.hi are accumulated: every product is then within ~2^-19 of the FP32
+// product, and since all terms are positive R keeps that relative accuracy.
+// One thread issues the MMAs and commits them to an mbarrier; waits are
+// bounded (expiry sets the library's device error flag).
+#include "grid_device.cuh"
+
+namespace retina {
+
+namespace {
+
+constexpr int GT_BM = 128, GT_BN = 128, GT_BK = 32, GT_THREADS = 256;
+constexpr int GT_NCOLS = 128;                    // TMEM columns: the tile's 128 theta_1 cells
+constexpr int PANEL_BYTES = GT_BM * GT_BK * 4;   // 16 KB
+constexpr int OFF_AHI = 0, OFF_ALO = PANEL_BYTES, OFF_BHI = 2 * PANEL_BYTES, OFF_BLO = 3 * PANEL_BYTES;
+constexpr int OFF_MASK = 4 * PANEL_BYTES;        // keep masks of the current window (8 x u32)
+constexpr int OFF_BAR = OFF_MASK + 32;           // mbarrier (8 B) + TMEM address (4 B)
+constexpr int GT_SMEM = OFF_BAR + 16;
+constexpr uint32_t GT_WAIT_LIMIT = 1u << 24;
+
+// kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (format 2 at bits 7-9 and
+// 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t GT_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// no-swizzle K-major descriptor; core matrices 8 rows x 16 bytes
+__device__ __forceinline__ uint64_t gt_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// byte offset of element (row m, hit k) of a 128 x 32 FP32 K-major panel:
+// core matrix (m / 8, k / 4) at (m / 8) * 1024 + (k / 4) * 128
+__device__ __forceinline__ int panel_off(int m, int k) { return (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4; }
+
+__device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    lo = v - hi;  // exact: v and hi share sign and exponent
+}
+
+__device__ __forceinline__ bool gt_try_wait(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool gt_wait(uint32_t addr, uint32_t parity) {
+    for (uint32_t i = 0; i < GT_WAIT_LIMIT; ++i)
+        if (gt_try_wait(addr, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void gt_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(GT_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void gt_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+// Grid over (tiles, hit slices, events) as grid_sep_kernel; same partial layout.
+__global__ void __launch_bounds__(GT_THREADS, 1)
+grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
+               const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0, float *__restrict__ out,
+               int64_t split_stride, int64_t event_stride, unsigned long long *__restrict__ work,
+               int32_t *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    unsigned *keep_mask = reinterpret_cast<unsigned *>(gsm + OFF_MASK);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(gsm + OFF_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gsm + OFF_BAR + 8);
+    const uint32_t bar_addr = smem_addr(bar);
+    const int e = blockIdx.z, s = blockIdx.y;
+    const int ti0 = (blockIdx.x % tiles0) * GT_BM;
+    const int tj0 = (blockIdx.x / tiles0) * GT_BN;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    int64_t k0, k1;
+    {
+        int64_t hb, he;
+        event_range(off, n_hits, e, hb, he);
+        const int64_t H = he - hb;
+        int64_t per = (H + splits - 1) / splits;
+        per = (per + GT_BK - 1) / GT_BK * GT_BK;
+        k0 = hb + (int64_t)s * per;
+        k1 = k0 + per < he ? k0 + per : he;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(GT_NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_addr), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // panel role: one cell per axis, every other hit of the block
+    const int ci = t & (GT_BM - 1), hpar = t >> 7;
+    const float t0 = cell_centre(g.lo0, g.step0, ti0 + ci);
+    const float t1 = cell_centre(g.lo1, g.step1, tj0 + ci);
+
+    int64_t hb, he;
+    event_range(off, n_hits, e, hb, he);
+    const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
+    const TileRange tr = tile_range(g, ti0, tj0, GT_BM, GT_BN);
+    const int64_t n_chunks = (k1 - k0 + GT_BK - 1) / GT_BK;
+    const int64_t b_first = (k0 - hb) / GT_BK;
+    int64_t done_hits = 0;
+    uint32_t phase = 0;
+    bool any = false, failed = false;
+    for (int64_t cb = 0; cb < n_chunks && !failed; cb += GT_THREADS) {
+        const int64_t c = cb + t;
+        bool keep = c < n_chunks;
+        if (keep && gbox) {
+            const float4 A = __ldg(gbox + 2 * (b_first + c)), B = __ldg(gbox + 2 * (b_first + c) + 1);
+            keep = !block_zero_sep(A, B, tr, kk);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncthreads();  // previous window's masks are no longer read
+        if (lane == 0) keep_mask[warp] = bal;
+        __syncthreads();
+        for (int w = 0; w < GT_THREADS / 32 && !failed; ++w) {
+            unsigned m = keep_mask[w];
+            while (m) {
+                const int64_t kb = k0 + (cb + 32 * w + __ffs(m) - 1) * GT_BK;
+                m &= m - 1;
+                done_hits += (k1 - kb) < GT_BK ? (k1 - kb) : GT_BK;
+                // panels (the previous block's MMAs have completed: waited below)
+#pragma unroll 4
+                for (int mm = 0; mm < GT_BK / 2; ++mm) {
+                    const int kc = hpar + 2 * mm;
+                    const int64_t k = kb + kc;
+                    float va = 0.f, vb = 0.f;
+                    if (k < k1) {
+                        const float4 h = __ldg(hits + k);
+                        const float u = __fmaf_rn(-t0, h.z, h.x);  // x - t_x z, one rounding
+                        const float v = __fmaf_rn(-t1, h.z, h.y);  // y - t_y z
+                        va = ex2_mufu(-(u * u) * kk);
+                        vb = ex2_mufu(-(v * v) * kk);
+                    }
+                    float ah, al, bh, bl;
+                    split_tf32(va, ah, al);
+                    split_tf32(vb, bh, bl);
+                    const int o = panel_off(ci, kc);
+                    *reinterpret_cast<float *>(gsm + OFF_AHI + o) = ah;
+                    *reinterpret_cast<float *>(gsm + OFF_ALO + o) = al;
+                    *reinterpret_cast<float *>(gsm + OFF_BHI + o) = bh;
+                    *reinterpret_cast<float *>(gsm + OFF_BLO + o) = bl;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (t == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = smem_addr(gsm);
+#pragma unroll
+                    for (int ks = 0; ks < GT_BK / 8; ++ks) {  // K = 8 per MMA: two core matrices
+                        const uint64_t ah = gt_desc(base + OFF_AHI + ks * 256, 128, 1024);
+                        const uint64_t al = gt_desc(base + OFF_ALO + ks * 256, 128, 1024);
+                        const uint64_t bh = gt_desc(base + OFF_BHI + ks * 256, 128, 1024);
+                        const uint64_t bl = gt_desc(base + OFF_BLO + ks * 256, 128, 1024);
+                        gt_mma(tmem, ah, bh, (any || ks > 0) ? 1u : 0u);
+                        gt_mma(tmem, ah, bl, 1u);
+                        gt_mma(tmem, al, bh, 1u);
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_addr)
+                        : "memory");
+                }
+                any = true;
+                const bool ok = gt_wait(bar_addr, phase);
+                phase ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (!__syncthreads_and(ok)) {
+                    failed = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (failed) {
+        if (t == 0) atomicExch(err, 1);
+        gt_wait(bar_addr, phase ^ 1u);  // bounded: let the last MMAs finish before freeing TMEM
+    } else {
+        if (work && t == 0 && done_hits > 0) {
+            const int64_t cw = (g.n0 - ti0 < GT_BM ? g.n0 - ti0 : GT_BM), ch = (g.n1 - tj0 < GT_BN ? g.n1 - tj0 : GT_BN);
+            atomicAdd(work + RETINA_WORK_GRID, (unsigned long long)(done_hits * cw * ch));
+        }
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (theta_0 cells) and
+        // columns 64 (w / 4) .. + 63 (theta_1 cells)
+        const int q = warp & 3, half = warp >> 2;
+        const int i = ti0 + 32 * q + lane;
+        float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            float v[32];
+            if (any) {
+                gt_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * half + 32 * part), v);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) v[c] = 0.f;
+            }
+            if (i < g.n0) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int j = tj0 + 64 * half + 32 * part + c;
+                    if (j < g.n1) dst[(int64_t)j * g.n0 + i] = v[c];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_NCOLS));
+    }
+}
+
+size_t grid_tc_smem_bytes() { return GT_SMEM; }
+
+}  // namespace retina

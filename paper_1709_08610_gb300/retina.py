@@ -20,12 +20,13 @@ from . import build as _build
 
 TOY2D = 0
 VELO_SLOPES = 1
-GRID_AUTO, GRID_DIRECT, GRID_SEPARABLE = 0, 1, 2
+GRID_AUTO, GRID_DIRECT, GRID_SEPARABLE, GRID_TENSOR = 0, 1, 2, 3
 MAX_Q = 8
 MAX_EXTRACT_POINTS = 8192
 OPT_LS_SEEDS_PER_WARP, OPT_LS_SMEM_HITS, OPT_GRID_SPLITS, OPT_LS_WARPS = 1, 2, 3, 4
 OPT_BATCH_SEEDS_PER_WARP, OPT_BATCH_WARPS, OPT_BATCH_SMEM_HITS, OPT_BATCH_CTAS = 5, 6, 7, 8
 OPT_SEEDNET_TC = 9
+OPT_GRID_TC = 10
 
 HEADER = os.path.join(_build.INCLUDE, "retina.h")
 

@@ -69,7 +69,7 @@ def test_prepared_hits_are_a_permutation_with_bounding_boxes(rt, model):
             assert np.median(side) <= 0.3, np.median(side)
 
 
-@pytest.mark.parametrize("flags", [1, 2])
+@pytest.mark.parametrize("flags", [1, 2, 3])
 def test_grid_response_with_boxes_is_bitwise_the_full_sum(rt, flags):
     wl, evs, b = _batch(1)
     srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), 1)

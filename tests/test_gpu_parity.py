@@ -100,7 +100,7 @@ def test_grid_response_toy_full_grid(rt, flags):
     assert np.all(np.abs(R_g - R_o) <= R_REL * R_o + R_ABS)
 
 
-@pytest.mark.parametrize("flags", [1, 2])
+@pytest.mark.parametrize("flags", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(192, 160), (131, 67), (256, 256)])
 def test_grid_response_velo_window_ragged(rt, flags, shape):
     # windows spanning several tiles with ragged edges, three ragged events (one empty)
@@ -118,7 +118,7 @@ def test_grid_response_velo_window_ragged(rt, flags, shape):
     assert out["n_max"].cpu().numpy()[2] == 0
 
 
-@pytest.mark.parametrize("flags", [1, 2])
+@pytest.mark.parametrize("flags", [1, 2, 3])
 def test_grid_response_full_size_sampled(rt, flags):
     # the full 1024^2 slope grid of the single-event workload, in the bench's
     # launch configuration; 3000 sampled cells against the oracle one by one
@@ -192,7 +192,7 @@ def test_grid_maxima_exact_on_noise_many_maxima(rt, n, K):
         np.testing.assert_array_equal(Rm[e, :k], R.reshape(-1)[exp_idx[:k]])
 
 
-@pytest.mark.parametrize("flags", [1, 2])
+@pytest.mark.parametrize("flags", [1, 2, 3])
 def test_grid_scan_maxima_match_oracle_up_to_ties(rt, flags):
     wl = WORKLOADS["velo"]
     lo, step, n = _window(wl, 300, 300, 384, 384)
