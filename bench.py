@@ -232,7 +232,7 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
     n0, n1 = wl.grid_n
     # throughput-bound batches: spatially ordered seeds, two per warp (measured
     # ~16 % faster than one per warp on 1024 events)
-    shape = dict(sort_seeds=True, seeds_per_warp=2)
+    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32)
     runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
             ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0, **shape),
              np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),

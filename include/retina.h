@@ -97,7 +97,7 @@ extern "C" {
                                           concurrently on other streams          */
 #define RETINA_OPT_GRID_TC 10          /* RETINA_GRID_AUTO on slope-model grids
                                           picks the tensor-core contraction (1)
-                                          or the CUDA-core one (0); default 0   */
+                                          or the CUDA-core one (0); default 1   */
 #define RETINA_OPT_SEEDNET_TC 9        /* seed net's second convolution on the
                                           tcgen05 tensor cores (1) or the FP32
                                           CUDA cores (0); default 1               */

@@ -20,7 +20,7 @@ static std::atomic<int> g_opt_batch_warps{16};
 static std::atomic<int> g_opt_batch_smem_hits{8192};
 static std::atomic<int> g_opt_batch_ctas{0};
 static std::atomic<int> g_opt_seednet_tc{1};
-static std::atomic<int> g_opt_grid_tc{0};
+static std::atomic<int> g_opt_grid_tc{1};
 
 int option_value(int option) {
     int32_t v = 0;

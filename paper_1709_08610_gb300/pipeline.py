@@ -28,11 +28,13 @@ class BatchTracker:
     def __init__(self, n_events: int, hit_capacity: int, seeds_per_event: int, box: "rt.Grid", opts: "rt.LsOpts",
                  R0: float, merge_cells: float = 2.0, max_tracks: int = 1024,
                  proposer: Optional[SeedProposer] = None, model: int = rt.VELO_SLOPES,
-                 sort_seeds: bool = False, seeds_per_warp: Optional[int] = None, device="cuda"):
+                 sort_seeds: bool = False, seeds_per_warp: Optional[int] = None, warps: Optional[int] = None,
+                 device="cuda"):
         """sort_seeds orders each event's starting points spatially before the
-        search (retina_sort_seeds), and seeds_per_warp sets the search's
-        RETINA_OPT_BATCH_SEEDS_PER_WARP for this tracker's launches (the
-        option is process-wide; the tracker restores it after each launch)."""
+        search (retina_sort_seeds); seeds_per_warp and warps set the search's
+        RETINA_OPT_BATCH_SEEDS_PER_WARP / RETINA_OPT_BATCH_WARPS for this
+        tracker's launches (the options are process-wide; the tracker restores
+        them after each launch)."""
         E, H, n = int(n_events), int(hit_capacity), int(seeds_per_event)
         if proposer is not None and model != rt.VELO_SLOPES:
             raise ValueError("the learned proposer works on slope-model hits")
@@ -46,7 +48,7 @@ class BatchTracker:
         self.sorted = torch.empty((H, 4), **f32)
         self.boxes = torch.empty((int(rt.lib.retina_prepare_hits_box_count(H, E)), 8), **f32)
         self.seeds = torch.zeros((E, n, 2), **f32)
-        self.sort, self.spw = bool(sort_seeds), seeds_per_warp
+        self.sort, self.spw, self.warps = bool(sort_seeds), seeds_per_warp, warps
         self.seeds_sorted = torch.zeros((E * n, 2), **f32) if self.sort else None
         self.seed_offsets = torch.arange(E + 1, dtype=torch.int64, device=dev) * n
         self.search_out = (torch.empty((E * n, 2), **f32), torch.empty((E * n,), **f32),
@@ -75,14 +77,16 @@ class BatchTracker:
         if self.sort:
             rt.sort_seeds(seeds, self.seed_offsets, self.box, out=self.seeds_sorted, stream=stream)
             seeds = self.seeds_sorted
-        old = rt.get_option(rt.OPT_BATCH_SEEDS_PER_WARP)
-        if self.spw:
-            rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, self.spw)
+        shape = [(o, v) for o, v in ((rt.OPT_BATCH_SEEDS_PER_WARP, self.spw), (rt.OPT_BATCH_WARPS, self.warps)) if v]
+        old = [(o, rt.get_option(o)) for o, _ in shape]
+        for o, v in shape:
+            rt.set_option(o, v)
         try:
             rt.batched_search(self.sorted, self.offsets, self.model, seeds, self.seed_offsets, self.opts, self.box,
                               out=self.search_out, ws=self.ws, boxes=self.boxes, stream=stream)
         finally:
-            rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, old)
+            for o, v in old:
+                rt.set_option(o, v)
         th, R, st = self.search_out
         rt.extract_tracks(th.reshape(self.E, self.n, 2), R.reshape(self.E, self.n), st.reshape(self.E, self.n),
                           self.box, self.R0, self.merge, self.K, out=self.tracks, stream=stream)
