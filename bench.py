@@ -66,6 +66,15 @@ def workload_config(wl, n_hits):
     }
 
 
+def measured_peaks() -> dict:
+    """The machine's measured peaks (HBM copy, dense BF16 GEMM), if the file is there."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -230,9 +239,10 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         return statistics.median(ts)
 
     n0, n1 = wl.grid_n
-    # throughput-bound batches: spatially ordered seeds, two per warp (measured
-    # ~16 % faster than one per warp on 1024 events)
-    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32)
+    # throughput-bound batches: spatially ordered seeds, two per warp, 32-warp
+    # CTAs staging up to 12288 hits (measured fastest on both batch workloads:
+    # ~16 % over one unordered seed per warp, more on high-multiplicity events)
+    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
     runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
             ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0, **shape),
              np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),
@@ -479,13 +489,28 @@ def main():
     search_ex2_rate = search_ex2 / (search_ms * 1e-3)
     fma_peak_tflops = 2.0 * fma_rate / 1e12 if fma_rate else None
     ex2_peak = peaks.get("ex2")
-    roof_grid = {"kernel": "grid_sep_kernel (+ slice reduction)", "bound": "alu", "unit": "TFLOP/s",
-                 "achieved": grid_tflops, "peak": fma_peak_tflops,
-                 "frac": (grid_tflops / fma_peak_tflops) if fma_peak_tflops else None,
-                 "traffic": None, "pairs_evaluated": grid_pairs, "pairs_total": grid_pairs_all,
-                 "effective_pairs_per_s": grid_pairs_all / (grid_ms * 1e-3),
-                 "peak_source": "FP32 FMA rate measured live by retina_alu_probe (burst; the faster of FFMA and "
-                                "packed FFMA2)"}
+    if rt.get_option(rt.OPT_GRID_TC):
+        # tensor-core contraction: each FP32-accurate product is three TF32 MMA
+        # products, so the peak for the algorithmic FP32 flops is the TF32 peak / 3;
+        # TF32 peak = measured dense BF16 (burst) x the nominal TF32 / BF16 ratio (1.1 / 2.25)
+        bf16 = measured_peaks().get("bf16_tflops")
+        tf32 = bf16 * (1.1 / 2.25) if bf16 else None
+        roof_grid = {"kernel": "grid_tc_kernel (+ slice reduction)", "bound": "tensor", "unit": "TFLOP/s",
+                     "achieved": grid_tflops, "peak": (tf32 / 3) if tf32 else None,
+                     "frac": (grid_tflops / (tf32 / 3)) if tf32 else None, "traffic": None,
+                     "pairs_evaluated": grid_pairs, "pairs_total": grid_pairs_all,
+                     "effective_pairs_per_s": grid_pairs_all / (grid_ms * 1e-3),
+                     "tf32_tflops_executed": 3 * grid_tflops,
+                     "peak_source": "of measured: MEASURED_PEAKS bf16_tflops (burst) x 1.1/2.25 (nominal TF32/BF16) "
+                                    "/ 3 (split products per FP32-accurate product)"}
+    else:
+        roof_grid = {"kernel": "grid_sep_kernel (+ slice reduction)", "bound": "alu", "unit": "TFLOP/s",
+                     "achieved": grid_tflops, "peak": fma_peak_tflops,
+                     "frac": (grid_tflops / fma_peak_tflops) if fma_peak_tflops else None,
+                     "traffic": None, "pairs_evaluated": grid_pairs, "pairs_total": grid_pairs_all,
+                     "effective_pairs_per_s": grid_pairs_all / (grid_ms * 1e-3),
+                     "peak_source": "FP32 FMA rate measured live by retina_alu_probe (burst; the faster of FFMA "
+                                    "and packed FFMA2)"}
     # FP32 lane instructions (an FMA counts once) against the measured lane-FMA rate, and ex2 against MUFU
     fr_fp32 = (search_fp32_rate / fma_rate) if fma_rate else None
     fr_ex2 = (search_ex2_rate / ex2_peak) if ex2_peak else None

@@ -134,10 +134,13 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    // panel role: one cell per axis, every other hit of the block
-    const int ci = t & (GT_BM - 1), hpar = t >> 7;
-    const float t0 = cell_centre(g.lo0, g.step0, ti0 + ci);
-    const float t1 = cell_centre(g.lo1, g.step1, tj0 + ci);
+    // panel role: lane l of warp w owns cells m = 8 (2w + a) + l / 4 (a = 0, 1)
+    // and hits k = 4 j + l % 4 (j = 0..7), so the 32 lanes of every store
+    // hit 32 different banks of the core-matrix layout
+    const int lm = lane >> 2, lk = lane & 3;
+    const int m0 = 16 * warp + lm, m1 = m0 + 8;
+    const float t0a = cell_centre(g.lo0, g.step0, ti0 + m0), t0b = cell_centre(g.lo0, g.step0, ti0 + m1);
+    const float t1a = cell_centre(g.lo1, g.step1, tj0 + m0), t1b = cell_centre(g.lo1, g.step1, tj0 + m1);
 
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
@@ -166,26 +169,35 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                 m &= m - 1;
                 done_hits += (k1 - kb) < GT_BK ? (k1 - kb) : GT_BK;
                 // panels (the previous block's MMAs have completed: waited below)
-#pragma unroll 4
-                for (int mm = 0; mm < GT_BK / 2; ++mm) {
-                    const int kc = hpar + 2 * mm;
+#pragma unroll 2
+                for (int j = 0; j < GT_BK / 4; ++j) {
+                    const int kc = 4 * j + lk;
                     const int64_t k = kb + kc;
-                    float va = 0.f, vb = 0.f;
+                    float va0 = 0.f, va1 = 0.f, vb0 = 0.f, vb1 = 0.f;
                     if (k < k1) {
                         const float4 h = __ldg(hits + k);
-                        const float u = __fmaf_rn(-t0, h.z, h.x);  // x - t_x z, one rounding
-                        const float v = __fmaf_rn(-t1, h.z, h.y);  // y - t_y z
-                        va = ex2_mufu(-(u * u) * kk);
-                        vb = ex2_mufu(-(v * v) * kk);
+                        // x - t_x z, y - t_y z with one rounding each, as grid_sep_kernel
+                        const float u0 = __fmaf_rn(-t0a, h.z, h.x), u1 = __fmaf_rn(-t0b, h.z, h.x);
+                        const float v0 = __fmaf_rn(-t1a, h.z, h.y), v1 = __fmaf_rn(-t1b, h.z, h.y);
+                        va0 = ex2_mufu(-(u0 * u0) * kk);
+                        va1 = ex2_mufu(-(u1 * u1) * kk);
+                        vb0 = ex2_mufu(-(v0 * v0) * kk);
+                        vb1 = ex2_mufu(-(v1 * v1) * kk);
                     }
-                    float ah, al, bh, bl;
-                    split_tf32(va, ah, al);
-                    split_tf32(vb, bh, bl);
-                    const int o = panel_off(ci, kc);
-                    *reinterpret_cast<float *>(gsm + OFF_AHI + o) = ah;
-                    *reinterpret_cast<float *>(gsm + OFF_ALO + o) = al;
-                    *reinterpret_cast<float *>(gsm + OFF_BHI + o) = bh;
-                    *reinterpret_cast<float *>(gsm + OFF_BLO + o) = bl;
+                    float hi, lo;
+                    const int o0 = panel_off(m0, kc), o1 = panel_off(m1, kc);
+                    split_tf32(va0, hi, lo);
+                    *reinterpret_cast<float *>(gsm + OFF_AHI + o0) = hi;
+                    *reinterpret_cast<float *>(gsm + OFF_ALO + o0) = lo;
+                    split_tf32(va1, hi, lo);
+                    *reinterpret_cast<float *>(gsm + OFF_AHI + o1) = hi;
+                    *reinterpret_cast<float *>(gsm + OFF_ALO + o1) = lo;
+                    split_tf32(vb0, hi, lo);
+                    *reinterpret_cast<float *>(gsm + OFF_BHI + o0) = hi;
+                    *reinterpret_cast<float *>(gsm + OFF_BLO + o0) = lo;
+                    split_tf32(vb1, hi, lo);
+                    *reinterpret_cast<float *>(gsm + OFF_BHI + o1) = hi;
+                    *reinterpret_cast<float *>(gsm + OFF_BLO + o1) = lo;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();

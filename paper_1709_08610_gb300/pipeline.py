@@ -29,10 +29,10 @@ class BatchTracker:
                  R0: float, merge_cells: float = 2.0, max_tracks: int = 1024,
                  proposer: Optional[SeedProposer] = None, model: int = rt.VELO_SLOPES,
                  sort_seeds: bool = False, seeds_per_warp: Optional[int] = None, warps: Optional[int] = None,
-                 device="cuda"):
+                 smem_hits: Optional[int] = None, device="cuda"):
         """sort_seeds orders each event's starting points spatially before the
-        search (retina_sort_seeds); seeds_per_warp and warps set the search's
-        RETINA_OPT_BATCH_SEEDS_PER_WARP / RETINA_OPT_BATCH_WARPS for this
+        search (retina_sort_seeds); seeds_per_warp, warps and smem_hits set the
+        search's RETINA_OPT_BATCH_SEEDS_PER_WARP / _WARPS / _SMEM_HITS for this
         tracker's launches (the options are process-wide; the tracker restores
         them after each launch)."""
         E, H, n = int(n_events), int(hit_capacity), int(seeds_per_event)
@@ -48,7 +48,7 @@ class BatchTracker:
         self.sorted = torch.empty((H, 4), **f32)
         self.boxes = torch.empty((int(rt.lib.retina_prepare_hits_box_count(H, E)), 8), **f32)
         self.seeds = torch.zeros((E, n, 2), **f32)
-        self.sort, self.spw, self.warps = bool(sort_seeds), seeds_per_warp, warps
+        self.sort, self.spw, self.warps, self.smem_hits = bool(sort_seeds), seeds_per_warp, warps, smem_hits
         self.seeds_sorted = torch.zeros((E * n, 2), **f32) if self.sort else None
         self.seed_offsets = torch.arange(E + 1, dtype=torch.int64, device=dev) * n
         self.search_out = (torch.empty((E * n, 2), **f32), torch.empty((E * n,), **f32),
@@ -77,7 +77,8 @@ class BatchTracker:
         if self.sort:
             rt.sort_seeds(seeds, self.seed_offsets, self.box, out=self.seeds_sorted, stream=stream)
             seeds = self.seeds_sorted
-        shape = [(o, v) for o, v in ((rt.OPT_BATCH_SEEDS_PER_WARP, self.spw), (rt.OPT_BATCH_WARPS, self.warps)) if v]
+        shape = [(o, v) for o, v in ((rt.OPT_BATCH_SEEDS_PER_WARP, self.spw), (rt.OPT_BATCH_WARPS, self.warps),
+                                     (rt.OPT_BATCH_SMEM_HITS, self.smem_hits)) if v]
         old = [(o, rt.get_option(o)) for o, _ in shape]
         for o, v in shape:
             rt.set_option(o, v)
