@@ -261,6 +261,17 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         eff, fakes = match_efficiency(found[name], truth)
         methods[name] = {"events_per_s": E / (ms * 1e-3), "ms_per_batch": ms, "efficiency": eff,
                          "fakes_per_event": fakes / E}
+        if isinstance(obj, BatchTracker):
+            # search work of one (eager) step, counted on the device; over the whole
+            # batch time this is a lower bound on the search kernel's own rate
+            rt.work_counters(enable=True, reset=True)
+            obj.step()
+            torch.cuda.synchronize()
+            w = rt.work_counters(enable=False)
+            pairs = w[rt.WORK_RGH] + w[rt.WORK_R]
+            methods[name]["search_pairs_per_batch"] = int(pairs)
+            methods[name]["search_fp32_lane_ops_per_s_lower_bound"] = \
+                (16.0 * w[rt.WORK_RGH] + 6.0 * w[rt.WORK_R]) / (ms * 1e-3)
         del obj
         torch.cuda.empty_cache()
     for name in methods:
