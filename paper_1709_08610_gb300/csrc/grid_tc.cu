@@ -25,7 +25,8 @@ constexpr int GT_BM = 128, GT_BN = 128, GT_BK = 32, GT_THREADS = 256;
 constexpr int GT_NCOLS = 128;                    // TMEM columns: the tile's 128 theta_1 cells
 constexpr int PANEL_BYTES = GT_BM * GT_BK * 4;   // 16 KB
 constexpr int OFF_AHI = 0, OFF_ALO = PANEL_BYTES, OFF_BHI = 2 * PANEL_BYTES, OFF_BLO = 3 * PANEL_BYTES;
-constexpr int OFF_MASK = 4 * PANEL_BYTES;        // keep masks of the current window (8 x u32)
+constexpr int OFF_HITS = 4 * PANEL_BYTES;        // the current block's 32 hits (float4)
+constexpr int OFF_MASK = OFF_HITS + GT_BK * 16;  // keep masks of the current window (8 x u32)
 constexpr int OFF_BAR = OFF_MASK + 32;           // mbarrier (8 B) + TMEM address (4 B)
 constexpr int GT_SMEM = OFF_BAR + 16;
 constexpr uint32_t GT_WAIT_LIMIT = 1u << 24;
@@ -168,14 +169,19 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                 const int64_t kb = k0 + (cb + 32 * w + __ffs(m) - 1) * GT_BK;
                 m &= m - 1;
                 done_hits += (k1 - kb) < GT_BK ? (k1 - kb) : GT_BK;
-                // panels (the previous block's MMAs have completed: waited below)
+                // the block's hits, staged once (the previous block's panels are no longer read:
+                // its MMAs completed before the barrier that ended its iteration)
+                float4 *sh = reinterpret_cast<float4 *>(gsm + OFF_HITS);
+                if (t < GT_BK) sh[t] = kb + t < k1 ? __ldg(hits + kb + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncthreads();
+                // panels
 #pragma unroll 2
                 for (int j = 0; j < GT_BK / 4; ++j) {
                     const int kc = 4 * j + lk;
                     const int64_t k = kb + kc;
                     float va0 = 0.f, va1 = 0.f, vb0 = 0.f, vb1 = 0.f;
                     if (k < k1) {
-                        const float4 h = __ldg(hits + k);
+                        const float4 h = sh[kc];
                         // x - t_x z, y - t_y z with one rounding each, as grid_sep_kernel
                         const float u0 = __fmaf_rn(-t0a, h.z, h.x), u1 = __fmaf_rn(-t0b, h.z, h.x);
                         const float v0 = __fmaf_rn(-t1a, h.z, h.y), v1 = __fmaf_rn(-t1b, h.z, h.y);

@@ -137,14 +137,21 @@ conv2_head_tc_kernel(const uint16_t *__restrict__ h1, const float *__restrict__ 
 
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int e = tile >> 5, r0 = (tile & 31) * 2;
-        // halo[hr][hc][ch] (rows r0-1..r0+2, cols -1..64), zero outside the image; global reads
-        // run along the columns of one channel row
-        for (int idx = tid; idx < 4 * 16 * 66; idx += TC_THREADS) {
-            const int hc = idx % 66, ch = (idx / 66) & 15, hr = idx / (66 * 16);
+        // halo[hr][hc][ch] (rows r0-1..r0+2, cols -1..64), zero outside the image: each item is
+        // one pixel's 8-channel group, gathered from the 8 channel planes (loads coalesced along
+        // the columns) and stored as one 16-byte vector
+        for (int idx = tid; idx < 4 * 2 * 66; idx += TC_THREADS) {
+            const int hc = idx % 66, grp = (idx / 66) & 1, hr = idx / (66 * 2);
             const int r = r0 - 1 + hr, c = hc - 1;
-            uint16_t v = 0;
-            if (r >= 0 && r < 64 && c >= 0 && c < 64) v = h1[(((int64_t)e * 16 + ch) * 64 + r) * 64 + c];
-            halo[(hr * 66 + hc) * 16 + ch] = v;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (r >= 0 && r < 64 && c >= 0 && c < 64) {
+                const uint16_t *src = h1 + (((int64_t)e * 16 + 8 * grp) * 64 + r) * 64 + c;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = (uint32_t)src[(2 * q) * 4096] | ((uint32_t)src[(2 * q + 1) * 4096] << 16);
+            }
+            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(halo) + (hr * 66 + hc) * 32 + grp * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
         __syncthreads();
         // A_t[m][8j..8j+7] = halo[(m/64 + dy)][(m%64 + dx)][8j..8j+7], 16-byte chunks
