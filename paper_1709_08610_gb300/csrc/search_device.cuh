@@ -260,7 +260,7 @@ __device__ __forceinline__ bool box_culled(const float4 A, const float4 B, float
 // walks those blocks in increasing order, lane l taking hit 32 b + l: the
 // same per-lane order as the full pass minus blocks whose terms are all
 // exactly zero - so every sum is bitwise the full pass's sum.
-template <typename T, typename F, typename F2>
+template <bool FOUR, typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                         int H, int lane, const float4 *__restrict__ sbox,
                                         const float4 *__restrict__ gbox, int n_sbox, T &&needed, F &&f, F2 &&f2) {
@@ -285,15 +285,12 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
             keep = needed(A, B);
         }
         unsigned m = __ballot_sync(0xffffffffu, keep);
-        while (m) {
-            // two kept blocks per iteration: two independent hits per lane
-            const int ba = c + __ffs(m) - 1;
-            m &= m - 1;
-            const int bb = m ? c + __ffs(m) - 1 : -1;
-            m &= m - 1;
+        // hits visited: 32 per kept block, the event's last block holding H - 32 (nblk - 1)
+        visited += 32 * __popc(m);
+        if (nblk - 1 - c < 32 && ((m >> (nblk - 1 - c)) & 1u)) visited -= 32 * nblk - H;
+        // blocks in increasing order, lane l taking hit 32 b + l of each
+        auto pair = [&](int ba, int bb) {  // bb = -1: ba alone
             const int ka = ba * 32 + lane, kb = bb * 32 + lane;
-            visited += (H - ba * 32) < 32 ? (H - ba * 32) : 32;
-            if (bb >= 0) visited += (H - bb * 32) < 32 ? (H - bb * 32) : 32;
             if (bb >= 0 && bb * 32 + 32 <= n_staged) {
                 f2(sh[ka], sh[kb]);
             } else {
@@ -307,6 +304,31 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
                     f(ha);
                 }
                 if (bb >= 0 && kb < H) f(__ldg(gh + kb));
+            }
+        };
+        while (m) {
+            const int ba = c + __ffs(m) - 1;
+            m &= m - 1;
+            const int bb = m ? c + __ffs(m) - 1 : -1;
+            m &= m - 1;
+            if (FOUR && m && bb * 32 + 32 <= n_staged) {
+                // four kept blocks per iteration when they are staged: four hits per lane in flight
+                // (measured faster for one seed per warp, slower for two: register pressure)
+                const int bc = c + __ffs(m) - 1;
+                m &= m - 1;
+                const int bd = m ? c + __ffs(m) - 1 : -1;
+                m &= m - 1;
+                if (bd >= 0 && bd * 32 + 32 <= n_staged) {
+                    const float4 ha = sh[ba * 32 + lane], hb = sh[bb * 32 + lane];
+                    const float4 hc = sh[bc * 32 + lane], hd = sh[bd * 32 + lane];
+                    f2(ha, hb);
+                    f2(hc, hd);
+                } else {
+                    pair(ba, bb);
+                    pair(bc, bd);
+                }
+            } else {
+                pair(ba, bb);
             }
         }
     }
@@ -348,7 +370,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
         RghAcc<MODEL> acc[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) acc[p].zero();
-        const int vis = hit_pass(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
+        const int vis = hit_pass<P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
                                  [&](const float4 A, const float4 B) {
                                      bool need = false;
 #pragma unroll
@@ -401,7 +423,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 tr1[p] = __fmaf_rn(t[p], pp1[p], th1[p]);
                 Rt[p] = 0.f;
             }
-            const int vis = hit_pass(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
+            const int vis = hit_pass<P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
                                      [&](const float4 A, const float4 B) {
                                          bool need = false;
 #pragma unroll
