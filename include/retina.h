@@ -95,10 +95,9 @@ extern "C" {
 #define RETINA_OPT_BATCH_CTAS 8        /* batched search CTAs, 0 = fill the GPU (0);
                                           fewer leave room for kernels running
                                           concurrently on other streams          */
-#define RETINA_OPT_GRID_TC 10          /* RETINA_GRID_AUTO on slope-model grids:
-                                          tensor-core contraction with one (1) or
-                                          two pipelined (2) panel buffers, or the
-                                          CUDA-core one (0); default 1            */
+#define RETINA_OPT_GRID_TC 10          /* RETINA_GRID_AUTO on slope-model grids
+                                          picks the tensor-core contraction (1)
+                                          or the CUDA-core one (0); default 1   */
 #define RETINA_OPT_SEEDNET_TC 9        /* seed net's second convolution on the
                                           tcgen05 tensor cores (1) or the FP32
                                           CUDA cores (0); default 1               */

@@ -118,7 +118,7 @@ int retina_set_option(int32_t option, int32_t value) {
             g_opt_seednet_tc = value;
             return RETINA_OK;
         case RETINA_OPT_GRID_TC:
-            if (value < 0 || value > 2) return RETINA_EINVAL;
+            if (value != 0 && value != 1) return RETINA_EINVAL;
             g_opt_grid_tc = value;
             return RETINA_OK;
         default: return RETINA_EINVAL;

@@ -49,9 +49,4 @@ __global__ void grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, 
                                float *__restrict__ out, int64_t split_stride, int64_t event_stride,
                                unsigned long long *__restrict__ work, int32_t *__restrict__ err);
 
-__global__ void grid_tc2_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
-                                const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0,
-                                float *__restrict__ out, int64_t split_stride, int64_t event_stride,
-                                unsigned long long *__restrict__ work, int32_t *__restrict__ err);
-
 }  // namespace retina

@@ -330,16 +330,13 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int split
 GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int forced_splits) {
     GridPlan p;
     p.separable = (model == RETINA_VELO_SLOPES) && (flags != RETINA_GRID_DIRECT);
-    // tensor-core variant: 0 none, 1 one panel buffer, 2 two panel buffers (pipelined)
-    const int opt = option_value(RETINA_OPT_GRID_TC);
-    p.tc = !p.separable ? 0
-           : flags == RETINA_GRID_TENSOR ? (opt == 2 ? 2 : 1)
-           : flags == RETINA_GRID_AUTO ? opt : 0;
+    p.tc = p.separable && (flags == RETINA_GRID_TENSOR ||
+                           (flags == RETINA_GRID_AUTO && option_value(RETINA_OPT_GRID_TC) != 0));
     const int tile = p.separable ? SEP_BM : DIR_TILE;
     p.tiles0 = (g->n[0] + tile - 1) / tile;
     p.tiles1 = (g->n[1] + tile - 1) / tile;
     const int64_t ctas = (int64_t)p.tiles0 * p.tiles1 * (n_events > 0 ? n_events : 1);
-    const int per_sm = p.tc == 2 ? 1 : p.tc ? 3 : (p.separable ? 2 : 4);
+    const int per_sm = p.tc ? 3 : (p.separable ? 2 : 4);
     const int64_t target = 4LL * sm_count() * per_sm;
     int64_t s = (target + ctas - 1) / ctas;
     if (s < 1) s = 1;
@@ -364,14 +361,7 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
     float *dst = p.splits > 1 ? partials : R;
     const int64_t split_stride = cells * n_events;
     dim3 grid(p.tiles0 * p.tiles1, p.splits, n_events);
-    if (p.tc == 2) {
-        int32_t *flag = device_error_flag();
-        if (!flag) return cudaErrorInvalidSymbol;
-        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(grid_tc2_kernel), grid_tc2_smem_bytes());
-        if (aerr != cudaSuccess) return aerr;
-        grid_tc2_kernel<<<grid, 512, grid_tc2_smem_bytes(), st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0,
-                                                                  dst, split_stride, cells, work_counters(), flag);
-    } else if (p.tc) {
+    if (p.tc) {
         int32_t *flag = device_error_flag();
         if (!flag) return cudaErrorInvalidSymbol;
         cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(grid_tc_kernel), grid_tc_smem_bytes());

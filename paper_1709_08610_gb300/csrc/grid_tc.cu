@@ -276,189 +276,4 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
 
 size_t grid_tc_smem_bytes() { return GT_SMEM; }
 
-// ---------------------------------------------------------------------------
-// Pipelined variant: two panel buffers, 512 threads.  The MMAs of one kept
-// block run while the next block's panels are built into the other buffer;
-// a buffer is rebuilt only after the MMAs that read it have completed (one
-// mbarrier per buffer, armed by tcgen05.commit).  Same panels, same MMAs in
-// the same order as grid_tc_kernel, so the same sums.
-// ---------------------------------------------------------------------------
-namespace {
-constexpr int G2_THREADS = 512;
-constexpr int G2_BUF = 4 * PANEL_BYTES;                // Ahi, Alo, Bhi, Blo
-constexpr int G2_OFF_HITS = 2 * G2_BUF;
-constexpr int G2_OFF_MASK = G2_OFF_HITS + GT_BK * 16;
-constexpr int G2_OFF_BAR = G2_OFF_MASK + 64;           // two mbarriers + TMEM address
-constexpr int G2_SMEM = G2_OFF_BAR + 32;
-}  // namespace
-
-__global__ void __launch_bounds__(G2_THREADS, 1)
-grid_tc2_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
-                const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0, float *__restrict__ out,
-                int64_t split_stride, int64_t event_stride, unsigned long long *__restrict__ work,
-                int32_t *__restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char gsm[];
-    unsigned *keep_mask = reinterpret_cast<unsigned *>(gsm + G2_OFF_MASK);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(gsm + G2_OFF_BAR);  // bar[0], bar[1]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gsm + G2_OFF_BAR + 16);
-    float4 *sh = reinterpret_cast<float4 *>(gsm + G2_OFF_HITS);
-    const uint32_t bar0 = smem_addr(bar), bar1 = smem_addr(bar + 1);
-    const int e = blockIdx.z, s = blockIdx.y;
-    const int ti0 = (blockIdx.x % tiles0) * GT_BM;
-    const int tj0 = (blockIdx.x / tiles0) * GT_BN;
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    int64_t hb, he;
-    event_range(off, n_hits, e, hb, he);
-    int64_t k0, k1;
-    {
-        const int64_t H = he - hb;
-        int64_t per = (H + splits - 1) / splits;
-        per = (per + GT_BK - 1) / GT_BK * GT_BK;
-        k0 = hb + (int64_t)s * per;
-        k1 = k0 + per < he ? k0 + per : he;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(GT_NCOLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-
-    // panel role: lane l of warp w owns cell m = 8 w + l / 4 on each axis and
-    // hits k = 4 j + l % 4 (j = 0..7): the 32 lanes of every store hit 32 banks
-    const int m = 8 * warp + (lane >> 2), lk = lane & 3;
-    const float t0 = cell_centre(g.lo0, g.step0, ti0 + m);
-    const float t1 = cell_centre(g.lo1, g.step1, tj0 + m);
-
-    const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
-    const TileRange tr = tile_range(g, ti0, tj0, GT_BM, GT_BN);
-    const int64_t n_chunks = (k1 - k0 + GT_BK - 1) / GT_BK;
-    const int64_t b_first = (k0 - hb) / GT_BK;
-    int64_t done_hits = 0;
-    int n = 0;  // kept blocks issued so far
-    bool failed = false;
-    for (int64_t cb = 0; cb < n_chunks && !failed; cb += G2_THREADS) {
-        const int64_t c = cb + t;
-        bool keep = c < n_chunks;
-        if (keep && gbox) {
-            const float4 A = __ldg(gbox + 2 * (b_first + c)), B = __ldg(gbox + 2 * (b_first + c) + 1);
-            keep = !block_zero_sep(A, B, tr, kk);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        __syncthreads();  // previous window's masks are no longer read
-        if (lane == 0) keep_mask[warp] = bal;
-        __syncthreads();
-        for (int w = 0; w < G2_THREADS / 32 && !failed; ++w) {
-            unsigned mk = keep_mask[w];
-            while (mk) {
-                const int64_t kb = k0 + (cb + 32 * w + __ffs(mk) - 1) * GT_BK;
-                mk &= mk - 1;
-                done_hits += (k1 - kb) < GT_BK ? (k1 - kb) : GT_BK;
-                const int buf = n & 1;
-                const uint32_t bb = buf ? bar1 : bar0;
-                // the buffer's previous MMAs (block n - 2) must be done before it is rebuilt
-                bool ok = true;
-                if (n >= 2) ok = gt_wait(bb, (uint32_t)(((n >> 1) - 1) & 1));
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (t < GT_BK) sh[t] = kb + t < k1 ? __ldg(hits + kb + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!__syncthreads_and(ok)) {
-                    failed = true;
-                    break;
-                }
-                unsigned char *P = gsm + buf * G2_BUF;
-#pragma unroll 4
-                for (int j = 0; j < GT_BK / 4; ++j) {
-                    const int kc = 4 * j + lk;
-                    float va = 0.f, vb = 0.f;
-                    if (kb + kc < k1) {
-                        const float4 h = sh[kc];
-                        // x - t_x z, y - t_y z with one rounding each, as grid_sep_kernel
-                        const float u = __fmaf_rn(-t0, h.z, h.x), v = __fmaf_rn(-t1, h.z, h.y);
-                        va = ex2_mufu(-(u * u) * kk);
-                        vb = ex2_mufu(-(v * v) * kk);
-                    }
-                    float hi, lo;
-                    const int o = panel_off(m, kc);
-                    split_tf32(va, hi, lo);
-                    *reinterpret_cast<float *>(P + OFF_AHI + o) = hi;
-                    *reinterpret_cast<float *>(P + OFF_ALO + o) = lo;
-                    split_tf32(vb, hi, lo);
-                    *reinterpret_cast<float *>(P + OFF_BHI + o) = hi;
-                    *reinterpret_cast<float *>(P + OFF_BLO + o) = lo;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                if (t == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t base = smem_addr(P);
-#pragma unroll
-                    for (int ks = 0; ks < GT_BK / 8; ++ks) {
-                        const uint64_t ah = gt_desc(base + OFF_AHI + ks * 256, 128, 1024);
-                        const uint64_t al = gt_desc(base + OFF_ALO + ks * 256, 128, 1024);
-                        const uint64_t bh = gt_desc(base + OFF_BHI + ks * 256, 128, 1024);
-                        const uint64_t bl = gt_desc(base + OFF_BLO + ks * 256, 128, 1024);
-                        gt_mma(tmem, ah, bh, (n > 0 || ks > 0) ? 1u : 0u);
-                        gt_mma(tmem, ah, bl, 1u);
-                        gt_mma(tmem, al, bh, 1u);
-                    }
-                    asm volatile(
-                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bb)
-                        : "memory");
-                }
-                ++n;
-            }
-        }
-    }
-    // the last commit covers every MMA issued before it
-    bool ok = true;
-    if (n > 0) {
-        const int last = n - 1;
-        ok = gt_wait((last & 1) ? bar1 : bar0, (uint32_t)((last >> 1) & 1));
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!__syncthreads_and(ok) || failed) {
-        if (t == 0) atomicExch(err, 1);
-    } else {
-        if (work && t == 0 && done_hits > 0) {
-            const int64_t cw = (g.n0 - ti0 < GT_BM ? g.n0 - ti0 : GT_BM), ch = (g.n1 - tj0 < GT_BN ? g.n1 - tj0 : GT_BN);
-            atomicAdd(work + RETINA_WORK_GRID, (unsigned long long)(done_hits * cw * ch));
-        }
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (theta_0 cells) and
-        // columns 32 (w / 4) .. + 31 (theta_1 cells)
-        const int q = warp & 3, cq = warp >> 2;
-        const int i = ti0 + 32 * q + lane;
-        float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
-        float v[32];
-        if (n > 0) {
-            gt_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * cq), v);
-        } else {
-#pragma unroll
-            for (int cc = 0; cc < 32; ++cc) v[cc] = 0.f;
-        }
-        if (i < g.n0) {
-#pragma unroll
-            for (int cc = 0; cc < 32; ++cc) {
-                const int j = tj0 + 32 * cq + cc;
-                if (j < g.n1) dst[(int64_t)j * g.n0 + i] = v[cc];
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_NCOLS));
-    }
-}
-
-size_t grid_tc2_smem_bytes() { return G2_SMEM; }
-
 }  // namespace retina

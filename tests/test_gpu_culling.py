@@ -137,26 +137,3 @@ def test_non_finite_hit_blocks_are_never_skipped(rt):
     R_full = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=1)
     R_cull = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=1, boxes=boxes)
     assert torch.isnan(R_full).all() and torch.isnan(R_cull).all()
-
-
-@pytest.mark.parametrize("variant", [1, 2])
-def test_tensor_core_grid_variants_agree_bitwise(rt, variant):
-    """The one-buffer and the pipelined tensor-core contractions issue the same
-    MMAs on the same panels in the same order: bitwise the same grid, with and
-    without block skipping, on ragged windows and the full grid."""
-    wl, evs, b = _batch(1)
-    srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), 1)
-    offs = _dev(b.offsets)
-    old = rt.get_option(rt.OPT_GRID_TC)
-    try:
-        for grid in (rt.Grid.of(wl), rt.Grid((-0.25, -0.2), wl.grid_step, (320, 300))):
-            res = {}
-            for v in (1, variant):
-                rt.set_option(rt.OPT_GRID_TC, v)
-                res[v] = [rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=0, boxes=bx) for bx in (None, boxes)]
-            for x, y in zip(res[1], res[variant]):
-                assert torch.equal(x, y)
-            assert torch.equal(res[variant][0], res[variant][1])
-    finally:
-        rt.set_option(rt.OPT_GRID_TC, old)
-    assert rt.device_error() == 0
