@@ -163,16 +163,30 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
         __syncthreads();  // previous window's masks are no longer read
         if (lane == 0) keep_mask[warp] = bal;
         __syncthreads();
-        for (int w = 0; w < GT_THREADS / 32 && !failed; ++w) {
-            unsigned m = keep_mask[w];
-            while (m) {
-                const int64_t kb = k0 + (cb + 32 * w + __ffs(m) - 1) * GT_BK;
-                m &= m - 1;
+        // kept blocks of the window in order; block `nxt`'s hits are loaded into
+        // registers while the current block's MMAs run
+        auto next_kept = [&](int after) -> int {  // first kept block index > after, or -1
+            for (int w = (after + 1) >> 5; w < GT_THREADS / 32; ++w) {
+                const int bit = (after + 1) - 32 * w;
+                const unsigned mw = keep_mask[w] & (bit > 0 ? (~0u << bit) : ~0u);
+                if (mw) return 32 * w + __ffs(mw) - 1;
+            }
+            return -1;
+        };
+        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cur = next_kept(-1);
+        if (cur >= 0 && t < GT_BK) {
+            const int64_t kb = k0 + (cb + cur) * GT_BK;
+            if (kb + t < k1) pre = __ldg(hits + kb + t);
+        }
+        while (cur >= 0 && !failed) {
+            {
+                const int64_t kb = k0 + (cb + cur) * GT_BK;
                 done_hits += (k1 - kb) < GT_BK ? (k1 - kb) : GT_BK;
-                // the block's hits, staged once (the previous block's panels are no longer read:
-                // its MMAs completed before the barrier that ended its iteration)
+                // the block's hits (the previous block's panels are no longer read: its
+                // MMAs completed before the barrier that ended its iteration)
                 float4 *sh = reinterpret_cast<float4 *>(gsm + OFF_HITS);
-                if (t < GT_BK) sh[t] = kb + t < k1 ? __ldg(hits + kb + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < GT_BK) sh[t] = pre;
                 __syncthreads();
                 // panels
 #pragma unroll 2
@@ -225,6 +239,12 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                         : "memory");
                 }
                 any = true;
+                const int nxt = next_kept(cur);
+                pre = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (nxt >= 0 && t < GT_BK) {
+                    const int64_t kn = k0 + (cb + nxt) * GT_BK;
+                    if (kn + t < k1) pre = __ldg(hits + kn + t);
+                }
                 const bool ok = gt_wait(bar_addr, phase);
                 phase ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -232,6 +252,7 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                     failed = true;
                     break;
                 }
+                cur = nxt;
             }
         }
     }
