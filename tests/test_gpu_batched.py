@@ -188,3 +188,23 @@ def test_sorted_seeds_are_a_spatial_permutation_and_search_results_follow_them(r
     for x, y in zip(ref, got):
         x, y = x.cpu().numpy(), y.cpu().numpy()
         np.testing.assert_array_equal(x[perm], y)
+
+
+def test_sorted_seeds_in_chunks_of_8192(rt):
+    """Events with more than 8192 points are ordered chunk by chunk (each chunk
+    a spatially sorted permutation of its own rows)."""
+    wl = WORKLOADS["velo"]
+    box = rt.Grid.of(wl)
+    n = [10000, 8192, 1, 0, 20000]
+    S = np.concatenate([uniform_seeds(wl, k, 7, e) for e, k in enumerate(n)]).astype(np.float32)
+    so = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+    srt, perm = rt.sort_seeds(_dev(S), _dev(so), box, want_perm=True)
+    srt, perm = srt.cpu().numpy(), perm.cpu().numpy()
+    np.testing.assert_array_equal(srt, S[perm])
+    for e in range(len(n)):
+        for c0 in range(so[e], so[e + 1], 8192):
+            c1 = min(c0 + 8192, so[e + 1])
+            p = perm[c0:c1]
+            assert sorted(p.tolist()) == list(range(c0, c1))
+            key = _morton9(S[p], box) * (1 << 13) + (p - c0)
+            assert np.all(np.diff(key) > 0)
