@@ -66,6 +66,23 @@ def workload_config(wl, n_hits):
     }
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over the ranks (replicas: the job lasts as long as its
+    slowest rank); the value itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_events_per_s(world: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank processes one event per step."""
+    return world * steps / (total_ms * 1e-3)
+
+
 def measured_peaks() -> dict:
     """The machine's measured peaks (HBM copy, dense BF16 GEMM), if the file is there."""
     try:
@@ -467,13 +484,9 @@ def main():
     pairs = [(0, 1), (6, 2) if args.serial else (1, 2), (2, 3), (4, 5), (5, 6)]
     stage = np.array([[evs[k][a].elapsed_time(evs[k][b]) for a, b in pairs] for k in range(args.steps)])
     step_ms = np.array([evs[k][0].elapsed_time(evs[k][7]) for k in range(args.steps)])
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(step_ms.sum()), dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms * 1e-3)
+    value = replica_events_per_s(world, args.steps, total_ms)
 
     # ---- work the two response kernels perform (counted on the device in
     # one extra step outside the timed region; exact block skipping means
