@@ -32,7 +32,7 @@ def test_max_over_ranks_and_whole_job_throughput_with_two_gloo_ranks():
     with socket.socket() as sk:
         sk.bind(("127.0.0.1", 0))
         port = sk.getsockname()[1]
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     for r in range(2):
         m, v = out[r]
