@@ -442,7 +442,24 @@ def test_search_and_extract_full_size_track_sets(rt, vertex):
         if ties.sum() == 0:
             assert _sets_match(found_g, found_o, TH_CELLS, wl.grid_step), (len(found_g), len(found_o))
         else:
-            pytest.skip("%d near-tie candidates on this event" % ties.sum())
+            # several track sets are correct: every oracle track farther than
+            # twice the merge distance (one suppression chain) from each near-tie
+            # candidate is found by the GPU, and every GPU track from a seed
+            # without a near-tie decision sits at that seed's oracle end point
+            step = np.asarray(wl.grid_step)
+
+            def dist(a, b):
+                if len(a) == 0 or len(b) == 0:
+                    return np.full(len(a), np.inf)
+                return np.max(np.abs(a[:, None, :] - b[None, :, :]) / step, axis=2).min(axis=1)
+
+            firm = dist(found_o, th_o[ties]) > 2 * wl.merge_cells
+            assert firm.sum() >= 0.9 * len(found_o)
+            assert np.all(dist(found_o[firm], found_g) <= TH_CELLS)
+            src = off_tr["track_src"].cpu().numpy()[0, :ng]
+            sure = ~ties[src]
+            d_src = np.max(np.abs(found_g[sure] - th_o[src[sure]]) / step, axis=1)
+            assert np.all(d_src <= TH_CELLS)
 
 
 def test_grid_scan_full_size_track_sets(rt):
