@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
     __shared__ int cur_e;
     const int tid = threadIdx.x, lane = tid & 31;
     float4 *sbox = sh + a.smem_hits;
+    int *list = kept_list(sh, a.smem_hits, tid >> 5);
     int staged = -1;
     int n_staged = 0, n_sbox = 0;
     for (int64_t round = 0; round < a.max_rounds; ++round) {
@@ -100,7 +101,12 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             for (int k = tid; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
             const int nblk = (H + 31) >> 5, cap = box_capacity(a.smem_hits);
             n_sbox = gbox ? (nblk < cap ? nblk : cap) : 0;
-            for (int k = tid; k < 2 * n_sbox; k += blockDim.x) sbox[k] = __ldg(gbox + k);
+            for (int k = tid; k < n_sbox; k += blockDim.x) {
+                float4 A = __ldg(gbox + 2 * k), B = __ldg(gbox + 2 * k + 1);
+                search_box<MODEL>(A, B);
+                sbox[2 * k] = A;
+                sbox[2 * k + 1] = B;
+            }
             staged = e;
         }
         __syncthreads();
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             if (g >= groups) break;
             const int64_t s = s0 + (int64_t)g * P;
             const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
-            search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, a.seeds + 2 * s, n_live, prm,
+            search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, list, a.seeds + 2 * s, n_live, prm,
                                    a.theta_out + 2 * s,
                                    a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work);
         }
@@ -126,7 +132,7 @@ size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(
 template <int MODEL, int P, int WARPS>
 static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
     auto kern = batched_search_kernel<MODEL, P, WARPS>;
-    const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr);
+    const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS);
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (aerr != cudaSuccess) return aerr;
     int per_sm = 0;

@@ -25,7 +25,12 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     float4 *sbox = sh + smem_hits;
     const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
     const int n_sbox = gbox ? (((H + 31) >> 5) < box_capacity(smem_hits) ? ((H + 31) >> 5) : box_capacity(smem_hits)) : 0;
-    for (int k = threadIdx.x; k < 2 * n_sbox; k += blockDim.x) sbox[k] = __ldg(gbox + k);
+    for (int k = threadIdx.x; k < n_sbox; k += blockDim.x) {
+        float4 A = __ldg(gbox + 2 * k), B = __ldg(gbox + 2 * k + 1);
+        search_box<MODEL>(A, B);
+        sbox[2 * k] = A;
+        sbox[2 * k + 1] = B;
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -33,7 +38,8 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     if (s_first >= n_seeds) return;
     const int n_live = n_seeds - s_first < P ? n_seeds - s_first : P;
     const int64_t o = (int64_t)e * n_seeds + s_first;
-    search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, seeds + 2 * o, n_live, prm, theta_out + 2 * o, R_out + o,
+    search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, kept_list(sh, smem_hits, warp), seeds + 2 * o,
+                           n_live, prm, theta_out + 2 * o, R_out + o,
                            status + o, n_evals ? n_evals + o : nullptr, work);
 }
 
@@ -89,6 +95,7 @@ LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box) {
         const double s = j < o->q ? (double)o->sigma[j] : 1.0;
         prm.kk[j] = (float)(kLog2e / (s * s));
         prm.k[j] = (float)(1.0 / (s * s));
+        prm.cull[j] = (float)((double)CULL_EXPONENT / (double)prm.kk[j]);
     }
     prm.c1 = o->c1;
     prm.max_halvings = o->max_halvings;
@@ -101,7 +108,7 @@ template <int MODEL, int P, int WARPS>
 static cudaError_t launch_ls_t(const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
                                int n_events, int n_seeds, const float *seeds, const LsParams &prm, int smem_hits,
                                float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
-    const size_t smem = search_smem_bytes(smem_hits, boxes != nullptr);
+    const size_t smem = search_smem_bytes(smem_hits, boxes != nullptr, WARPS);
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(local_search_kernel<MODEL, P, WARPS>), smem);
     if (aerr != cudaSuccess) return aerr;
     const int per_block = WARPS * P;

@@ -188,6 +188,7 @@ struct LsParams {
     int q;
     float kk[RETINA_MAX_Q];  // log2(e) / sigma_j^2
     float k[RETINA_MAX_Q];   // 1 / sigma_j^2
+    float cull[RETINA_MAX_Q];  // CULL_EXPONENT / kk[j]: skipping threshold on |z|min^2 dist^2
     float c1;
     int max_halvings;
     float cap;
@@ -197,10 +198,16 @@ struct LsParams {
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box);
 
 // Shared-memory layout of the search kernels: smem_hits hits, then (with
-// boxes) the boxes of the first box_capacity(smem_hits) blocks (2 float4 each).
+// boxes) the boxes of the first box_capacity(smem_hits) blocks (2 float4 each,
+// in search_box form), then one list of KEPT_CHUNK kept-block offsets per warp.
+constexpr int KEPT_CHUNK = 128;  // blocks tested per chunk of a pass (4 per lane)
 __host__ __device__ __forceinline__ int box_capacity(int smem_hits) { return (smem_hits + 31) / 32 + 1; }
-__host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes) {
-    return (size_t)smem_hits * 16 + (with_boxes ? (size_t)box_capacity(smem_hits) * 32 : 0);
+__host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes, int warps) {
+    return (size_t)smem_hits * 16 +
+           (with_boxes ? (size_t)box_capacity(smem_hits) * 32 + (size_t)warps * KEPT_CHUNK * sizeof(int) : 0);
+}
+__device__ __forceinline__ int *kept_list(float4 *sh, int smem_hits, int warp) {
+    return reinterpret_cast<int *>(sh + smem_hits + 2 * box_capacity(smem_hits)) + warp * KEPT_CHUNK;
 }
 
 // Lane-strided pass over an event's hits: the staged prefix from shared
@@ -219,118 +226,136 @@ __device__ __forceinline__ void for_each_hit(const float4 *__restrict__ sh, cons
 // can be skipped for a point theta when a lower bound of s^2 * log2(e) /
 // sigma^2 over the block's box exceeds CULL_EXPONENT: then every hit of the
 // block has ex2(-x) with x > 126, which ex2.approx.ftz returns as exactly
-// zero, so its terms add nothing to any sum.  The bound uses interval
-// arithmetic on the box and a relative slack of 1e-6 per magnitude that
-// covers the float32 rounding of the bound itself; 140 leaves a further
-// margin over 126.  Non-finite boxes are never skipped.
+// zero, so its terms add nothing to any sum.  140 leaves a margin over 126
+// that covers every relative rounding of the bound (a few float32 ulps).
 constexpr float CULL_EXPONENT = 140.f;
 
-// Distance from t to the interval [l, h], minus a rounding slack of 1e-6
-// per magnitude; 0 inside.
-__device__ __forceinline__ float gap_pt(float t, float l, float h) {
-    const float d = fmaxf(fmaxf(l - t, t - h), 0.f);
-    return fmaxf(d - 1e-6f * (fabsf(l) + fabsf(h) + fabsf(t)), 0.f);
-}
-
-// True when every hit of the block has s^2 log2(e) / sigma^2 > CULL_EXPONENT
-// at theta = (t0, t1).  Slope model, box (umin, umax, vmin, vmax | |z|min, -):
-// s^2 = z^2 |(u, v) - theta|^2 >= |z|min^2 dist^2.  2D toy, box (xmin, xmax,
-// ymin, ymax): r = y - t0 x - t1 over the box, by interval arithmetic.
+// A block box as the search tests it, made once when the box is staged.
+// Slope model, box (umin, umax, vmin, vmax | |z|min, ...): the slope
+// intervals are widened by S = 1e-6 max|bound|, sixteen times the float32
+// rounding of x / z when the box was built, so every hit's exact slope lies
+// inside; B.x becomes |z|min^2.  A box with a non-finite value becomes the
+// whole plane with B.x = 0, which the test never skips.  2D toy: unchanged.
 template <int MODEL>
-__device__ __forceinline__ bool box_culled(const float4 A, const float4 B, float t0, float t1, float kk) {
-    if (!isfinite(B.x)) return false;  // boxes with non-finite hits are infinite
-    float bound;
+__device__ __forceinline__ void search_box(float4 &A, float4 &B) {
     if (MODEL == RETINA_VELO_SLOPES) {
-        const float du = gap_pt(t0, A.x, A.y), dv = gap_pt(t1, A.z, A.w);
-        bound = (du * du + dv * dv) * (B.x * B.x) * kk;
-    } else {
-        const float a = t0 * A.x, b = t0 * A.y;
-        const float lo = A.z - t1 - fmaxf(a, b), hi = A.w - t1 - fminf(a, b);
-        const float d = fmaxf(fmaxf(lo, -hi), 0.f);
-        const float dd = fmaxf(d - 1e-6f * (fabsf(A.z) + fabsf(A.w) + 2.f * fabsf(t1) + fabsf(a) + fabsf(b)), 0.f);
-        bound = dd * dd * kk;
+        const bool fin = isfinite(A.x) && isfinite(A.y) && isfinite(A.z) && isfinite(A.w) && isfinite(B.x);
+        const float S = 1e-6f * fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(A.z), fabsf(A.w)));
+        A = fin ? make_float4(A.x - S, A.y + S, A.z - S, A.w + S) : make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
+        B.x = fin ? B.x * B.x : 0.f;
     }
-    return bound > CULL_EXPONENT;
 }
 
-// Pass over the hits that can contribute for the P points (tr0, tr1) of the
-// warp (active[p] selects the points that need this pass).  Without boxes it
-// is for_each_hit.  With boxes, each lane tests one block of a window of 32
-// blocks, the ballot gives the blocks some active point needs, and the warp
-// walks those blocks in increasing order, lane l taking hit 32 b + l: the
-// same per-lane order as the full pass minus blocks whose terms are all
-// exactly zero - so every sum is bitwise the full pass's sum.
-template <bool FOUR, typename T, typename F, typename F2>
+// One point's constants for the skipping test of one pass.  Slope model:
+// c = CULL_EXPONENT / kk, the threshold on dist^2 |z|min^2 (infinite, never
+// skip, around a non-finite point, whose full sums may be NaN).  2D toy: c = kk.
+struct CullPt {
+    float t0, t1, c;
+};
+template <int MODEL>
+__device__ __forceinline__ CullPt cull_pt(float t0, float t1, float kk, float cull) {
+    if (MODEL == RETINA_VELO_SLOPES) return CullPt{t0, t1, (isfinite(t0) && isfinite(t1)) ? cull : INFINITY};
+    return CullPt{t0, t1, kk};
+}
+
+// True when every hit of the block (box in search_box form) has
+// s^2 log2(e) / sigma^2 > CULL_EXPONENT at the point.  Slope model:
+// s^2 = z^2 |(u, v) - theta|^2 >= |z|min^2 dist^2, each distance with one
+// rounding (relative).  2D toy, box (xmin, xmax, ymin, ymax): r = y - t0 x - t1
+// over the box by interval arithmetic, less a slack of 1e-6 per magnitude
+// for the rounding of the bound itself.
+template <int MODEL>
+__device__ __forceinline__ bool box_culled(const float4 A, const float4 B, const CullPt &p) {
+    if (MODEL == RETINA_VELO_SLOPES) {
+        const float du = fmaxf(fmaxf(A.x - p.t0, p.t0 - A.y), 0.f);
+        const float dv = fmaxf(fmaxf(A.z - p.t1, p.t1 - A.w), 0.f);
+        return __fmaf_rn(du, du, dv * dv) * B.x > p.c;
+    } else {
+        if (!isfinite(B.x)) return false;  // boxes with non-finite hits are infinite
+        const float a = p.t0 * A.x, b = p.t0 * A.y;
+        const float lo = A.z - p.t1 - fmaxf(a, b), hi = A.w - p.t1 - fminf(a, b);
+        const float d = fmaxf(fmaxf(lo, -hi), 0.f);
+        const float dd = fmaxf(d - 1e-6f * (fabsf(A.z) + fabsf(A.w) + 2.f * fabsf(p.t1) + fabsf(a) + fabsf(b)), 0.f);
+        return dd * dd * p.c > CULL_EXPONENT;
+    }
+}
+
+// Pass over the hits that can contribute for the P points of the warp.
+// Without boxes it is for_each_hit.  With boxes, each chunk of KEPT_CHUNK
+// blocks is tested at once (lane l tests blocks l, l + 32, l + 64, l + 96 of
+// the chunk: four independent tests), the ballots give the blocks some
+// point needs, in increasing order, as offsets in the warp's list, and the
+// warp walks the list, lane l taking hit 32 b + l of each block: the same
+// per-lane order as the full pass minus blocks whose terms are all exactly
+// zero - so every sum is bitwise the full pass's sum.  Returns the hits
+// visited (for the work counters).
+template <int MODEL, bool FOUR, typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                         int H, int lane, const float4 *__restrict__ sbox,
-                                        const float4 *__restrict__ gbox, int n_sbox, T &&needed, F &&f, F2 &&f2) {
+                                        const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
+                                        T &&needed, F &&f, F2 &&f2) {
     if (!gbox) {
         for_each_hit(sh, gh, n_staged, H, lane, f, f2);
         return H;
     }
     int visited = 0;
     const int nblk = (H + 31) >> 5;
-    for (int c = 0; c < nblk; c += 32) {
-        const int b = c + lane;
-        bool keep = false;
-        if (b < nblk) {
-            float4 A, B;
-            if (b < n_sbox) {
-                A = sbox[2 * b];
-                B = sbox[2 * b + 1];
-            } else {
-                A = __ldg(gbox + 2 * b);
-                B = __ldg(gbox + 2 * b + 1);
-            }
-            keep = needed(A, B);
-        }
-        unsigned m = __ballot_sync(0xffffffffu, keep);
-        // hits visited: 32 per kept block, the event's last block holding H - 32 (nblk - 1)
-        visited += 32 * __popc(m);
-        if (nblk - 1 - c < 32 && ((m >> (nblk - 1 - c)) & 1u)) visited -= 32 * nblk - H;
-        // blocks in increasing order, lane l taking hit 32 b + l of each
-        auto pair = [&](int ba, int bb) {  // bb = -1: ba alone
-            const int ka = ba * 32 + lane, kb = bb * 32 + lane;
-            if (bb >= 0 && bb * 32 + 32 <= n_staged) {
-                f2(sh[ka], sh[kb]);
-            } else {
-                // block ba may be staged; block bb (if any) is not: it lies past n_staged
-                if (ka < H) {
-                    float4 ha;
-                    if (ba * 32 + 32 <= n_staged)
-                        ha = sh[ka];
-                    else
-                        ha = __ldg(gh + ka);
-                    f(ha);
-                }
-                if (bb >= 0 && kb < H) f(__ldg(gh + kb));
-            }
-        };
-        while (m) {
-            const int ba = c + __ffs(m) - 1;
-            m &= m - 1;
-            const int bb = m ? c + __ffs(m) - 1 : -1;
-            m &= m - 1;
-            if (FOUR && m && bb * 32 + 32 <= n_staged) {
-                // four kept blocks per iteration when they are staged: four hits per lane in flight
-                // (measured faster for one seed per warp, slower for two: register pressure)
-                const int bc = c + __ffs(m) - 1;
-                m &= m - 1;
-                const int bd = m ? c + __ffs(m) - 1 : -1;
-                m &= m - 1;
-                if (bd >= 0 && bd * 32 + 32 <= n_staged) {
-                    const float4 ha = sh[ba * 32 + lane], hb = sh[bb * 32 + lane];
-                    const float4 hc = sh[bc * 32 + lane], hd = sh[bd * 32 + lane];
-                    f2(ha, hb);
-                    f2(hc, hd);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < nblk; c0 += KEPT_CHUNK) {
+        bool keep[KEPT_CHUNK / 32];
+#pragma unroll
+        for (int w = 0; w < KEPT_CHUNK / 32; ++w) {
+            const int b = c0 + 32 * w + lane;
+            keep[w] = false;
+            if (b < nblk) {
+                float4 A, B;
+                if (b < n_sbox) {
+                    A = sbox[2 * b];
+                    B = sbox[2 * b + 1];
                 } else {
-                    pair(ba, bb);
-                    pair(bc, bd);
+                    A = __ldg(gbox + 2 * b);
+                    B = __ldg(gbox + 2 * b + 1);
+                    search_box<MODEL>(A, B);
                 }
-            } else {
-                pair(ba, bb);
+                keep[w] = needed(A, B);
             }
         }
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < KEPT_CHUNK / 32; ++w) {
+            const unsigned m = __ballot_sync(0xffffffffu, keep[w]);
+            if (keep[w]) list[cnt + __popc(m & lt)] = (c0 + 32 * w + lane) * 32;
+            cnt += __popc(m);
+        }
+        __syncwarp();
+        if (cnt == 0) continue;
+        // hits visited: 32 per kept block, the event's last block holding H - 32 (nblk - 1)
+        const int last = list[cnt - 1];
+        visited += 32 * cnt - (last == 32 * (nblk - 1) ? 32 * nblk - H : 0);
+        // blocks held whole in shared memory form a prefix of the list
+        const int n_fast = last + 32 <= n_staged ? cnt : (cnt > 1 && list[cnt - 2] + 32 <= n_staged ? cnt - 1 : 0);
+        int i = 0;
+        if (FOUR) {
+            for (; i + 4 <= n_fast; i += 4) {
+                const int4 q = *reinterpret_cast<const int4 *>(list + i);
+                const float4 ha = sh[q.x + lane], hb = sh[q.y + lane];
+                const float4 hc = sh[q.z + lane], hd = sh[q.w + lane];
+                f2(ha, hb);
+                f2(hc, hd);
+            }
+        }
+        for (; i + 2 <= n_fast; i += 2) {
+            const int2 q = *reinterpret_cast<const int2 *>(list + i);
+            f2(sh[q.x + lane], sh[q.y + lane]);
+        }
+        for (; i < cnt; ++i) {
+            const int k = list[i] + lane;
+            if (k < n_staged)
+                f(sh[k]);
+            else if (k < H)
+                f(__ldg(gh + k));
+        }
+        __syncwarp();  // the list is rewritten by the next chunk
     }
     return visited;
 }
@@ -343,7 +368,7 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
 template <int MODEL, int P>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
                                              int n_staged, int H, int lane, const float4 *__restrict__ sbox,
-                                             const float4 *__restrict__ gbox, int n_sbox,
+                                             const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
                                              const float *__restrict__ seeds,
                                              int n_live, const LsParams &prm, float *__restrict__ theta_out,
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
@@ -365,17 +390,20 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     }
 
     for (int j = 0; j < prm.q; ++j) {
-        const float kk = prm.kk[j], k = prm.k[j];
+        const float kk = prm.kk[j], k = prm.k[j], cull = prm.cull[j];
         // (R, g, H) at the current points
         RghAcc<MODEL> acc[P];
+        CullPt cp[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) acc[p].zero();
-        const int vis = hit_pass<P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
+        for (int p = 0; p < P; ++p) {
+            acc[p].zero();
+            cp[p] = cull_pt<MODEL>(th0[p], th1[p], kk, cull);
+        }
+        const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, list,
                                  [&](const float4 A, const float4 B) {
                                      bool need = false;
 #pragma unroll
-                                     for (int p = 0; p < P; ++p)
-                                         need |= live[p] && !box_culled<MODEL>(A, B, th0[p], th1[p], kk);
+                                     for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, B, cp[p]);
                                      return need;
                                  },
                                  [&](const float4 h) {
@@ -417,18 +445,20 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             for (int p = 0; p < P; ++p) any |= pending[p];
             if (!any) break;
             float tr0[P], tr1[P], Rt[P];
+            CullPt ct[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 tr0[p] = __fmaf_rn(t[p], pp0[p], th0[p]);
                 tr1[p] = __fmaf_rn(t[p], pp1[p], th1[p]);
                 Rt[p] = 0.f;
+                ct[p] = cull_pt<MODEL>(tr0[p], tr1[p], kk, cull);
             }
-            const int vis = hit_pass<P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox,
+            const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, list,
                                      [&](const float4 A, const float4 B) {
                                          bool need = false;
 #pragma unroll
                                          for (int p = 0; p < P; ++p)
-                                             need |= pending[p] && !box_culled<MODEL>(A, B, tr0[p], tr1[p], kk);
+                                             need |= pending[p] && !box_culled<MODEL>(A, B, ct[p]);
                                          return need;
                                      },
                                      [&](const float4 h) {
