@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparison")
     ap.add_argument("--serial", action="store_true", help="run the grid and search branches on one stream")
+    ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph instead of enqueueing "
+                                                         "its kernels one by one")
     return ap.parse_args()
 
 
@@ -64,6 +66,22 @@ def workload_config(wl, n_hits):
         "l2": "flushed between timed steps (256 MiB write outside the timed events)",
         "parallelism": "replicas (one event per rank, no collective on the data path)",
     }
+
+
+_libcuda = None
+
+
+def record_in_graph(event, stream) -> None:
+    """Record a timing event on a capturing stream as an event node of the
+    graph (CU_EVENT_RECORD_EXTERNAL), so that every replay records it."""
+    import ctypes
+    global _libcuda
+    if _libcuda is None:
+        _libcuda = ctypes.CDLL("libcuda.so.1")
+        _libcuda.cuEventRecordWithFlags.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint]
+    r = _libcuda.cuEventRecordWithFlags(event.cuda_event, stream.cuda_stream, 1)
+    if r != 0:
+        raise RuntimeError("cuEventRecordWithFlags failed: %d" % r)
 
 
 def max_over_ranks(value: float, device) -> float:
@@ -278,6 +296,28 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         eff, fakes = match_efficiency(found[name], truth)
         methods[name] = {"events_per_s": E / (ms * 1e-3), "ms_per_batch": ms, "efficiency": eff,
                          "fakes_per_event": fakes / E}
+        if isinstance(obj, GridScanBatch):
+            # the grid scan alone (response + maxima, eager, after the hit ordering), with
+            # its evaluated (cell, hit) pairs counted on the device: 2 flops per pair
+            obj.step()
+            rt.work_counters(enable=True, reset=True)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            rt.grid_scan(obj.sorted, obj.offsets, obj.model, obj.grid, obj.sigma, obj.R0, obj.Km, ws=obj.ws,
+                         out=obj.maxima, boxes=obj.boxes, stream=stream)
+            c.record(stream)
+            c.synchronize()
+            w = rt.work_counters(enable=False)
+            t_ms = a.elapsed_time(c)
+            tflops = 2.0 * w[rt.WORK_GRID] / (t_ms * 1e-3) / 1e12
+            bf16 = measured_peaks().get("bf16_tflops")
+            methods[name]["grid_scan_ms"] = t_ms
+            methods[name]["grid_pairs_evaluated"] = int(w[rt.WORK_GRID])
+            methods[name]["grid_pairs_total"] = int(n0 * n1 * H)
+            methods[name]["grid_tflops"] = tflops
+            if bf16 and rt.get_option(rt.OPT_GRID_TC):
+                methods[name]["grid_frac_of_3xtf32_peak"] = tflops / (bf16 * (1.1 / 2.25) / 3)
         if isinstance(obj, BatchTracker):
             # search work of one (eager) step, counted on the device; over the whole
             # batch time this is a lower bound on the search kernel's own rate
@@ -370,39 +410,92 @@ def main():
     # The grid branch and the search branch need only the prepared hits, so
     # after retina_prepare_hits they run concurrently on two streams (the
     # search leaves room on every SM through RETINA_OPT_BATCH_CTAS) and join
-    # on the main stream.  Events (timing ones when given) bracket every
-    # stage on the stream it runs on:
+    # on the main stream.  Timing events, when given, bracket every stage on
+    # the stream it runs on:
     #   0 start | prepare | 1 | grid | 2 | maxima + extract | 3     (main stream)
     #   4 | search | 5 | extract | 6                                (search stream)
     #   join, 7 end                                                 (main stream)
     # the search branch is the longer one: its stream gets the higher priority,
-    # so its kernels' CTAs go first whenever an SM frees up
-    stream2 = torch.cuda.Stream(dev, priority=-1) if not args.serial else stream
-    sync_ev = [torch.cuda.Event() for _ in range(8)]
+    # so its kernels' CTAs go first whenever an SM frees up.  The timed steps
+    # enqueue the kernels one by one; --graph replays the step as one CUDA
+    # graph instead (captured on its own stream, the timing events as event
+    # nodes of the graph) - measured about 4 % slower on this step: launched
+    # together, the grid branch's CTAs take SMs the search branch gets first
+    # when the host enqueues the search before the grid.
+    stream2 = torch.cuda.Stream(dev, priority=-1)
+    fork_ev, join_ev = torch.cuda.Event(), torch.cuda.Event()
 
-    def step(evs=None):
-        ev = evs if evs else sync_ev
-        ev[0].record(stream)
-        rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes), stream=stream)
-        ev[1].record(stream)
-        stream2.wait_event(ev[1])
-        ev[4].record(stream2)
+    def step(evs=None, main=None, in_graph=False):
+        s1 = stream if main is None else main
+        s2 = s1 if args.serial else stream2
+
+        def mark(i, st):
+            if evs is not None:
+                if in_graph:
+                    record_in_graph(evs[i], st)
+                else:
+                    evs[i].record(st)
+
+        mark(0, s1)
+        rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes), stream=s1)
+        mark(1, s1)
+        if s2 is not s1:
+            fork_ev.record(s1)
+            s2.wait_event(fork_ev)
+        mark(4, s2)
         rt.batched_search(srt, offs, wl.model, seeds, seed_offs, opts, grid, out=ls_out, n_evals=n_evals,
-                          ws=ws_search, boxes=boxes, stream=stream2)
-        ev[5].record(stream2)
+                          ws=ws_search, boxes=boxes, stream=s2)
+        mark(5, s2)
         rt.extract_tracks(ls_out[0].view(1, -1, 2), ls_out[1].view(1, -1), ls_out[2].view(1, -1), grid, R0,
-                          wl.merge_cells, K_TR, out=tr_search, stream=stream2)
-        ev[6].record(stream2)
-        rt.grid_response(srt, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid, boxes=boxes, stream=stream)
-        ev[2].record(stream)
-        rt.grid_maxima(Rg, grid, R0, K_MAX, out=mx, ws=ws_max, stream=stream)
+                          wl.merge_cells, K_TR, out=tr_search, stream=s2)
+        mark(6, s2)
+        rt.grid_response(srt, offs, wl.model, grid, wl.sigma_grid, R_out=Rg, ws=ws_grid, boxes=boxes, stream=s1)
+        mark(2, s1)
+        rt.grid_maxima(Rg, grid, R0, K_MAX, out=mx, ws=ws_max, stream=s1)
         rt.extract_tracks(mx["max_theta"], mx["max_R"], None, grid, R0, wl.merge_cells, K_TR,
-                          n_valid=mx["n_max"], out=tr_grid, stream=stream)
-        ev[3].record(stream)
-        stream.wait_event(ev[6])
-        ev[7].record(stream)
+                          n_valid=mx["n_max"], out=tr_grid, stream=s1)
+        mark(3, s1)
+        if s2 is not s1:
+            join_ev.record(s2)
+            s1.wait_event(join_ev)
+        mark(7, s1)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    cap_stream = torch.cuda.Stream(dev)
+    ev_g = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    for e_ in ev_g:
+        e_.record(stream)  # create the events before they are captured
+    torch.cuda.synchronize()
+
+    def capture():
+        """The step as one CUDA graph with the current launch options; returns
+        the graph and the number of our kernels in it."""
+        step()  # eager once: kernel attributes set before capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        n0_ = rt.launch_count()
+        with torch.cuda.graph(g, stream=cap_stream, capture_error_mode="thread_local"):
+            step(ev_g, main=cap_stream, in_graph=True)
+        return g, rt.launch_count() - n0_
+
+    def timed_steps(g, n, evs_eager=None):
+        """n steps behind an L2 flush each; per step the device times of the 8
+        marks (ms from mark 0).  Graph steps read their event nodes after each
+        replay (one synchronize per step, outside the timed marks)."""
+        out = np.zeros((n, 8))
+        for k in range(n):
+            flush.zero_()
+            if g is not None:
+                g.replay()
+                ev_g[7].synchronize()
+                out[k] = [ev_g[0].elapsed_time(ev_g[i]) if i else 0.0 for i in range(8)]
+            else:
+                step(evs_eager[k])
+        if g is None:
+            torch.cuda.synchronize()
+            for k in range(n):
+                out[k] = [evs_eager[k][0].elapsed_time(evs_eager[k][i]) if i else 0.0 for i in range(8)]
+        return out
 
     # ---- launch shapes picked by the autotuner on this workload and GPU
     tuned = None
@@ -412,25 +505,28 @@ def main():
                  "search": tune.tune_batched_search(srt, offs, wl.model, seeds, seed_offs, opts, grid, boxes=boxes)}
 
     # ---- the search's CTA shape when it shares the GPU with the grid branch:
-    # candidates timed on the whole two-stream step (same inputs, outputs)
+    # candidates timed on the whole two-stream step, run as the timed region
+    # runs it (graph replays behind the L2 flush)
     if not args.no_tune and not args.serial:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         cands = [(32, 0), (32, 3 * sms // 4), (32, sms // 2), (16, 0), (16, 3 * sms // 2), (16, sms),
                  (8, 2 * sms), (8, sms)]
         table = {}
-        # timed as the timed region times a step: enqueued back to back behind
-        # the L2 flush, one event pair per step, a single synchronize at the end
-        ev_t = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(15)]
         for w, c in cands:
             rt.set_option(rt.OPT_BATCH_WARPS, w)
             rt.set_option(rt.OPT_BATCH_CTAS, c)
-            for _ in range(3):
-                step()
-            for k in range(15):
-                flush.zero_()
-                step(ev_t[k])
-            torch.cuda.synchronize()
-            table["%d,%d" % (w, c)] = statistics.median(ev[0].elapsed_time(ev[7]) for ev in ev_t)
+            if not args.graph:
+                g_c = None
+                evs_c = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(15)]
+                for _ in range(3):
+                    step()
+            else:
+                g_c, _ = capture()
+                evs_c = None
+                for _ in range(3):
+                    g_c.replay()
+            table["%d,%d" % (w, c)] = float(np.median(timed_steps(g_c, 15, evs_c)[:, 7]))
+            del g_c
         best = min(table, key=table.get)
         w, c = (int(x) for x in best.split(","))
         rt.set_option(rt.OPT_BATCH_WARPS, w)
@@ -455,13 +551,18 @@ def main():
             peaks[name] = best
     fma_rate = max(peaks.get("ffma", 0.0), peaks.get("ffma2", 0.0))
 
-    # ---- warm-up
+    # ---- the step graph, then warm-up
+    graph, kernels_per_step = capture() if args.graph else (None, 0)
     for _ in range(max(args.warmup, 3)):
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
     torch.cuda.synchronize()
 
     # ---- timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    evs = None if graph is not None else [[torch.cuda.Event(enable_timing=True) for _ in range(8)]
+                                          for _ in range(args.steps)]
     clocks = ClockSampler(local_rank) if not args.no_clocks else None
     if world > 1:
         dist.barrier()
@@ -471,12 +572,10 @@ def main():
         time.sleep(0.3)
     launches0 = rt.launch_count()
     t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        step(evs[k])
+    marks = timed_steps(graph, args.steps, evs)
     torch.cuda.synchronize()
     t_wall1 = time.perf_counter()
-    launches = rt.launch_count() - launches0
+    launches = rt.launch_count() - launches0 + kernels_per_step * args.steps
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
@@ -484,8 +583,8 @@ def main():
     # stages: prepare, grid response, maxima + extract (main stream), search, extract (search stream)
     # (one stream: the search branch is enqueued first, so the grid response runs from event 6 to 2)
     pairs = [(0, 1), (6, 2) if args.serial else (1, 2), (2, 3), (4, 5), (5, 6)]
-    stage = np.array([[evs[k][a].elapsed_time(evs[k][b]) for a, b in pairs] for k in range(args.steps)])
-    step_ms = np.array([evs[k][0].elapsed_time(evs[k][7]) for k in range(args.steps)])
+    stage = np.stack([marks[:, b] - marks[:, a] for a, b in pairs], axis=1)
+    step_ms = marks[:, 7]
     total_ms = max_over_ranks(float(step_ms.sum()), dev)
     ms_per_step = total_ms / args.steps
     value = replica_events_per_s(world, args.steps, total_ms)
@@ -564,7 +663,10 @@ def main():
         for _ in range(n_e2e):
             hits.copy_(hits_h, non_blocking=True)
             seeds.copy_(seeds_h, non_blocking=True)
-            step()
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
             for k2 in out_h:
                 out_h[k2].copy_(tr_search[k2], non_blocking=True)
                 outg_h[k2].copy_(tr_grid[k2], non_blocking=True)
@@ -575,7 +677,9 @@ def main():
         h2d = hits_h.numel() * 4 + seeds_h.numel() * 4
         e2e = {"value": world * 1e3 / e2e_ms, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
-               "note": "includes the flush-free step plus pinned host<->device copies, timed with CUDA events"}
+               "note": "back-to-back steps (%s) with the pinned host->device copy of the hits and seeds and the "
+                       "device->host copy of both track lists in every step, timed with CUDA events"
+                       % ("eager launches" if graph is None else "one graph replay per step")}
 
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None
@@ -612,7 +716,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(wl, H),
                            branches="one stream" if args.serial else
-                           "grid branch and search branch on two concurrent streams after the shared hit ordering"),
+                           "grid branch and search branch on two concurrent streams after the shared hit ordering",
+                           launch="kernels enqueued one by one" if graph is None else
+                           "one CUDA graph replay per step (%d kernels)" % kernels_per_step),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "roofline_other": roof_search if dominant == "grid" else roof_grid,
             "stages_ms": {"prepare_hits": prep_ms, "grid_response": grid_ms,

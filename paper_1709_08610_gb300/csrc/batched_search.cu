@@ -142,9 +142,10 @@ static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, int
     // persistent: as many CTAs as fit at once, or fewer when the caller leaves room for concurrent kernels
     const int fill = per_sm * sm_count();
     const int grid = (ctas > 0 && ctas < fill) ? ctas : fill;
-    kern<<<grid, WARPS * 32, smem, st>>>(a, prm);
+    PrioLaunch L(dim3(grid), dim3(WARPS * 32), smem, st);
+    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, kern, a, prm);
     count_launches(1);
-    return cudaGetLastError();
+    return lerr != cudaSuccess ? lerr : cudaGetLastError();
 }
 
 template <int MODEL, int P>

@@ -60,6 +60,35 @@ __device__ void bitonic_sort(uint64_t *keys, int C) {
     }
 }
 
+// Sort keys[0, C) in place (C a power of two, all EX_THREADS threads call it):
+// from 1024 keys on, in registers (bitonic_sort_regs, keys as its exchange
+// buffer); shorter runs with the plain shared-memory network.
+template <int R>
+__device__ __forceinline__ void sort_keys_regs(uint64_t *keys) {
+    uint64_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = keys[threadIdx.x * R + r];
+    __syncthreads();
+    bitonic_sort_regs<uint64_t, R, EX_THREADS>(v, keys);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) keys[threadIdx.x * R + r] = v[r];
+    __syncthreads();
+}
+
+__device__ void sort_keys(uint64_t *keys, int C) {
+    if (C == EX_THREADS)
+        sort_keys_regs<1>(keys);
+    else if (C == 2 * EX_THREADS)
+        sort_keys_regs<2>(keys);
+    else if (C == 4 * EX_THREADS)
+        sort_keys_regs<4>(keys);
+    else if (C == 8 * EX_THREADS)
+        sort_keys_regs<8>(keys);
+    else
+        bitonic_sort(keys, C);
+}
+
 __device__ __forceinline__ int lower_bound_u64(const uint64_t *keys, int n, uint64_t x) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -123,7 +152,7 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     for (int i = nc + tid; i < C; i += EX_THREADS) keys[i] = ~0ull;
     __syncthreads();
     // 2. rank order
-    bitonic_sort(keys, C);
+    sort_keys(keys, C);
     for (int r = tid; r < nc; r += EX_THREADS) {
         const int i = (int)(uint32_t)keys[r];
         const int64_t o = base + i;
@@ -145,7 +174,7 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
         }
     }
     __syncthreads();
-    bitonic_sort(keys, C);
+    sort_keys(keys, C);
     // 4. rounds
     for (int round = 0; round <= nc + 1; ++round) {
         bool undecided = false;
@@ -250,10 +279,11 @@ cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint
     int C = 1;
     while (C < n_points) C <<= 1;
     prm.cap = C;
-    extract_tracks_kernel<<<n_events, EX_THREADS, extract_smem_bytes(n_points), st>>>(
-        theta, R, status, n_valid, prm, tracks, track_R, track_src, n_tracks);
+    PrioLaunch L(dim3(n_events), dim3(EX_THREADS), extract_smem_bytes(n_points), st);
+    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel, theta, R, status, n_valid, prm, tracks,
+                                                track_R, track_src, n_tracks);
     count_launches(1);
-    return cudaGetLastError();
+    return lerr != cudaSuccess ? lerr : cudaGetLastError();
 }
 
 }  // namespace retina

@@ -96,7 +96,8 @@ __device__ __forceinline__ void gt_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-// Grid over (tiles, hit slices, events) as grid_sep_kernel; same partial layout.
+// Grid over (tiles, hit slices, events) and partial layout as grid_sep_kernel;
+// the slices interleave 32-hit blocks instead of cutting contiguous ranges.
 __global__ void __launch_bounds__(GT_THREADS, 1)
 grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
                const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0, float *__restrict__ out,
@@ -111,16 +112,6 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
     const int ti0 = (blockIdx.x % tiles0) * GT_BM;
     const int tj0 = (blockIdx.x / tiles0) * GT_BN;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    int64_t k0, k1;
-    {
-        int64_t hb, he;
-        event_range(off, n_hits, e, hb, he);
-        const int64_t H = he - hb;
-        int64_t per = (H + splits - 1) / splits;
-        per = (per + GT_BK - 1) / GT_BK * GT_BK;
-        k0 = hb + (int64_t)s * per;
-        k1 = k0 + per < he ? k0 + per : he;
-    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                      "r"(GT_NCOLS));
@@ -143,12 +134,16 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
     const float t0a = cell_centre(g.lo0, g.step0, ti0 + m0), t0b = cell_centre(g.lo0, g.step0, ti0 + m1);
     const float t1a = cell_centre(g.lo1, g.step1, tj0 + m0), t1b = cell_centre(g.lo1, g.step1, tj0 + m1);
 
+    // slice s takes the event's 32-hit blocks s, s + splits, s + 2 splits, ...:
+    // the blocks a tile keeps cluster in the hits' spatial order, and
+    // interleaving spreads them evenly over the tile's slices
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
+    const int64_t nblk = (he - hb + GT_BK - 1) / GT_BK;
     const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
     const TileRange tr = tile_range(g, ti0, tj0, GT_BM, GT_BN);
-    const int64_t n_chunks = (k1 - k0 + GT_BK - 1) / GT_BK;
-    const int64_t b_first = (k0 - hb) / GT_BK;
+    const int64_t n_chunks = nblk > s ? (nblk - s + splits - 1) / splits : 0;
+    auto block_of = [&](int64_t c) -> int64_t { return (int64_t)s + c * splits; };
     int64_t done_hits = 0;
     uint32_t phase = 0;
     bool any = false, failed = false;
@@ -156,7 +151,7 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
         const int64_t c = cb + t;
         bool keep = c < n_chunks;
         if (keep && gbox) {
-            const float4 A = __ldg(gbox + 2 * (b_first + c)), B = __ldg(gbox + 2 * (b_first + c) + 1);
+            const float4 A = __ldg(gbox + 2 * block_of(c)), B = __ldg(gbox + 2 * block_of(c) + 1);
             keep = !block_zero_sep(A, B, tr, kk);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -176,13 +171,13 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
         float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
         int cur = next_kept(-1);
         if (cur >= 0 && t < GT_BK) {
-            const int64_t kb = k0 + (cb + cur) * GT_BK;
-            if (kb + t < k1) pre = __ldg(hits + kb + t);
+            const int64_t kb = hb + block_of(cb + cur) * GT_BK;
+            if (kb + t < he) pre = __ldg(hits + kb + t);
         }
         while (cur >= 0 && !failed) {
             {
-                const int64_t kb = k0 + (cb + cur) * GT_BK;
-                done_hits += (k1 - kb) < GT_BK ? (k1 - kb) : GT_BK;
+                const int64_t kb = hb + block_of(cb + cur) * GT_BK;
+                done_hits += (he - kb) < GT_BK ? (he - kb) : GT_BK;
                 // the block's hits (the previous block's panels are no longer read: its
                 // MMAs completed before the barrier that ended its iteration)
                 float4 *sh = reinterpret_cast<float4 *>(gsm + OFF_HITS);
@@ -194,7 +189,7 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                     const int kc = 4 * j + lk;
                     const int64_t k = kb + kc;
                     float va0 = 0.f, va1 = 0.f, vb0 = 0.f, vb1 = 0.f;
-                    if (k < k1) {
+                    if (k < he) {
                         const float4 h = sh[kc];
                         // x - t_x z, y - t_y z with one rounding each, as grid_sep_kernel
                         const float u0 = __fmaf_rn(-t0a, h.z, h.x), u1 = __fmaf_rn(-t0b, h.z, h.x);
@@ -242,8 +237,8 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                 const int nxt = next_kept(cur);
                 pre = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (nxt >= 0 && t < GT_BK) {
-                    const int64_t kn = k0 + (cb + nxt) * GT_BK;
-                    if (kn + t < k1) pre = __ldg(hits + kn + t);
+                    const int64_t kn = hb + block_of(cb + nxt) * GT_BK;
+                    if (kn + t < he) pre = __ldg(hits + kn + t);
                 }
                 const bool ok = gt_wait(bar_addr, phase);
                 phase ^= 1u;

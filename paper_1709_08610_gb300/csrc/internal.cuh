@@ -61,6 +61,29 @@ cudaError_t launch_conv2_head_tc(const uint16_t *h1, int n_events, const float *
 void count_launches(int n);
 size_t extract_smem_bytes(int n_points);
 
+// A launch configuration that carries the stream's priority as a launch
+// attribute, so that a CUDA graph captured from the stream keeps it on the
+// kernel node.  Use in place (cfg.attrs points into the object).
+struct PrioLaunch {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr;
+    PrioLaunch(dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+        int prio = 0;
+        if (cudaStreamGetPriority(st, &prio) != cudaSuccess) prio = 0;
+        cfg = cudaLaunchConfig_t{};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        attr.id = cudaLaunchAttributePriority;
+        attr.val.priority = prio;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+    }
+    PrioLaunch(const PrioLaunch &) = delete;
+    PrioLaunch &operator=(const PrioLaunch &) = delete;
+};
+
 // learned seed proposer
 cudaError_t launch_slope_hist(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, float lo, float hi,
                               float zmin, uint16_t *feat, int32_t *counts, cudaStream_t st);
