@@ -198,16 +198,25 @@ struct LsParams {
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box);
 
 // Shared-memory layout of the search kernels: smem_hits hits, then (with
-// boxes) the boxes of the first box_capacity(smem_hits) blocks (2 float4 each,
-// in search_box form), then one list of KEPT_CHUNK kept-block offsets per warp.
+// boxes) the boxes of the first box_capacity(smem_hits) blocks in search_box
+// form as two arrays (the slope bounds, float4, then the |z|min^2 terms,
+// padded to a multiple of 4 floats; lanes reading consecutive blocks touch
+// consecutive words), then one list of KEPT_CHUNK kept-block offsets per warp.
 constexpr int KEPT_CHUNK = 128;  // blocks tested per chunk of a pass (4 per lane)
 __host__ __device__ __forceinline__ int box_capacity(int smem_hits) { return (smem_hits + 31) / 32 + 1; }
+__host__ __device__ __forceinline__ int box_capacity4(int smem_hits) { return (box_capacity(smem_hits) + 3) & ~3; }
 __host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes, int warps) {
     return (size_t)smem_hits * 16 +
-           (with_boxes ? (size_t)box_capacity(smem_hits) * 32 + (size_t)warps * KEPT_CHUNK * sizeof(int) : 0);
+           (with_boxes ? (size_t)box_capacity(smem_hits) * 16 + (size_t)box_capacity4(smem_hits) * 4 +
+                             (size_t)warps * KEPT_CHUNK * sizeof(int)
+                       : 0);
+}
+__device__ __forceinline__ float4 *staged_box_bounds(float4 *sh, int smem_hits) { return sh + smem_hits; }
+__device__ __forceinline__ float *staged_box_z2(float4 *sh, int smem_hits) {
+    return reinterpret_cast<float *>(sh + smem_hits + box_capacity(smem_hits));
 }
 __device__ __forceinline__ int *kept_list(float4 *sh, int smem_hits, int warp) {
-    return reinterpret_cast<int *>(sh + smem_hits + 2 * box_capacity(smem_hits)) + warp * KEPT_CHUNK;
+    return reinterpret_cast<int *>(staged_box_z2(sh, smem_hits) + box_capacity4(smem_hits)) + warp * KEPT_CHUNK;
 }
 
 // Lane-strided pass over an event's hits: the staged prefix from shared
@@ -234,16 +243,18 @@ constexpr float CULL_EXPONENT = 140.f;
 // Slope model, box (umin, umax, vmin, vmax | |z|min, ...): the slope
 // intervals are widened by S = 1e-6 max|bound|, sixteen times the float32
 // rounding of x / z when the box was built, so every hit's exact slope lies
-// inside; B.x becomes |z|min^2.  A box with a non-finite value becomes the
-// whole plane with B.x = 0, which the test never skips.  2D toy: unchanged.
+// inside; the returned weight is |z|min^2.  A box with a non-finite value
+// becomes the whole plane with weight 0, which the test never skips.  2D toy:
+// A unchanged, weight = B.x (0, or -inf for a non-finite box).
 template <int MODEL>
-__device__ __forceinline__ void search_box(float4 &A, float4 &B) {
+__device__ __forceinline__ float search_box(float4 &A, const float4 B) {
     if (MODEL == RETINA_VELO_SLOPES) {
         const bool fin = isfinite(A.x) && isfinite(A.y) && isfinite(A.z) && isfinite(A.w) && isfinite(B.x);
         const float S = 1e-6f * fmaxf(fmaxf(fabsf(A.x), fabsf(A.y)), fmaxf(fabsf(A.z), fabsf(A.w)));
         A = fin ? make_float4(A.x - S, A.y + S, A.z - S, A.w + S) : make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
-        B.x = fin ? B.x * B.x : 0.f;
+        return fin ? B.x * B.x : 0.f;
     }
+    return B.x;
 }
 
 // One point's constants for the skipping test of one pass.  Slope model:
@@ -265,13 +276,13 @@ __device__ __forceinline__ CullPt cull_pt(float t0, float t1, float kk, float cu
 // over the box by interval arithmetic, less a slack of 1e-6 per magnitude
 // for the rounding of the bound itself.
 template <int MODEL>
-__device__ __forceinline__ bool box_culled(const float4 A, const float4 B, const CullPt &p) {
+__device__ __forceinline__ bool box_culled(const float4 A, const float w, const CullPt &p) {
     if (MODEL == RETINA_VELO_SLOPES) {
         const float du = fmaxf(fmaxf(A.x - p.t0, p.t0 - A.y), 0.f);
         const float dv = fmaxf(fmaxf(A.z - p.t1, p.t1 - A.w), 0.f);
-        return __fmaf_rn(du, du, dv * dv) * B.x > p.c;
+        return __fmaf_rn(du, du, dv * dv) * w > p.c;
     } else {
-        if (!isfinite(B.x)) return false;  // boxes with non-finite hits are infinite
+        if (!isfinite(w)) return false;  // boxes with non-finite hits are infinite
         const float a = p.t0 * A.x, b = p.t0 * A.y;
         const float lo = A.z - p.t1 - fmaxf(a, b), hi = A.w - p.t1 - fminf(a, b);
         const float d = fmaxf(fmaxf(lo, -hi), 0.f);
@@ -291,7 +302,7 @@ __device__ __forceinline__ bool box_culled(const float4 A, const float4 B, const
 // visited (for the work counters).
 template <int MODEL, bool FOUR, typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
-                                        int H, int lane, const float4 *__restrict__ sbox,
+                                        int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
                                         const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
                                         T &&needed, F &&f, F2 &&f2) {
     if (!gbox) {
@@ -308,16 +319,16 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
             const int b = c0 + 32 * w + lane;
             keep[w] = false;
             if (b < nblk) {
-                float4 A, B;
+                float4 A;
+                float z2;
                 if (b < n_sbox) {
-                    A = sbox[2 * b];
-                    B = sbox[2 * b + 1];
+                    A = sbox[b];
+                    z2 = sz2[b];
                 } else {
                     A = __ldg(gbox + 2 * b);
-                    B = __ldg(gbox + 2 * b + 1);
-                    search_box<MODEL>(A, B);
+                    z2 = search_box<MODEL>(A, __ldg(gbox + 2 * b + 1));
                 }
-                keep[w] = needed(A, B);
+                keep[w] = needed(A, z2);
             }
         }
         int cnt = 0;
@@ -368,7 +379,8 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
 template <int MODEL, int P>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
                                              int n_staged, int H, int lane, const float4 *__restrict__ sbox,
-                                             const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
+                                             const float *__restrict__ sz2, const float4 *__restrict__ gbox,
+                                             int n_sbox, int *__restrict__ list,
                                              const float *__restrict__ seeds,
                                              int n_live, const LsParams &prm, float *__restrict__ theta_out,
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
@@ -399,11 +411,11 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             acc[p].zero();
             cp[p] = cull_pt<MODEL>(th0[p], th1[p], kk, cull);
         }
-        const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, list,
-                                 [&](const float4 A, const float4 B) {
+        const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                                 [&](const float4 A, const float z2) {
                                      bool need = false;
 #pragma unroll
-                                     for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, B, cp[p]);
+                                     for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, z2, cp[p]);
                                      return need;
                                  },
                                  [&](const float4 h) {
@@ -453,12 +465,12 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 Rt[p] = 0.f;
                 ct[p] = cull_pt<MODEL>(tr0[p], tr1[p], kk, cull);
             }
-            const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, gbox, n_sbox, list,
-                                     [&](const float4 A, const float4 B) {
+            const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                                     [&](const float4 A, const float z2) {
                                          bool need = false;
 #pragma unroll
                                          for (int p = 0; p < P; ++p)
-                                             need |= pending[p] && !box_culled<MODEL>(A, B, ct[p]);
+                                             need |= pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
                                          return need;
                                      },
                                      [&](const float4 h) {
