@@ -69,23 +69,37 @@ def test_batched_matches_per_launch_search_bitwise(rt):
     assert np.all(R[so[2]:so[3]] == 0.0)  # empty event
 
 
+@pytest.mark.parametrize("with_boxes", [False, True])
 @pytest.mark.parametrize("spw,warps", [(1, 8), (2, 16), (4, 32), (1, 32)])
-def test_batched_results_independent_of_order_and_shape(rt, spw, warps):
+def test_batched_results_independent_of_order_and_shape(rt, spw, warps, with_boxes):
+    # one, two or four seeds per warp (shared block tests and hit loads, the
+    # union of the seeds' kept blocks): the accepted trials, every sum and the
+    # trial counts must agree bit for bit, with exact block skipping on or off
     wl, evs, b, seeds, so = _ragged(1)
     opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
     box = rt.Grid.of(wl)
-    ref = rt.batched_search(_dev(b.hits), _dev(b.offsets), 1, _dev(seeds), _dev(so), opts, box)
+    offs = _dev(b.offsets)
+    hits, bx = rt.prepare_hits(_dev(b.hits), offs, 1)
+    boxes = bx if with_boxes else None
+    S = len(seeds)
+    ev_ref = torch.empty(S, dtype=torch.uint8, device="cuda")
     old = (rt.get_option(rt.OPT_BATCH_SEEDS_PER_WARP), rt.get_option(rt.OPT_BATCH_WARPS))
-    rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, spw)
-    rt.set_option(rt.OPT_BATCH_WARPS, warps)
     try:
+        rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, 2)
+        ref = rt.batched_search(hits, offs, 1, _dev(seeds), _dev(so), opts, box, n_evals=ev_ref)
+        rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, spw)
+        rt.set_option(rt.OPT_BATCH_WARPS, warps)
         order = _dev(np.array([3, 0, 4, 1, 2], np.int32))
-        got = rt.batched_search(_dev(b.hits), _dev(b.offsets), 1, _dev(seeds), _dev(so), opts, box, order=order)
+        ev_got = torch.empty(S, dtype=torch.uint8, device="cuda")
+        got = rt.batched_search(hits, offs, 1, _dev(seeds), _dev(so), opts, box, order=order, n_evals=ev_got,
+                                boxes=boxes)
     finally:
         rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, old[0])
         rt.set_option(rt.OPT_BATCH_WARPS, old[1])
     for x, y in zip(ref, got):
         np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+    np.testing.assert_array_equal(ev_ref.cpu().numpy(), ev_got.cpu().numpy())
+    assert ev_ref.max().item() > 3  # some seeds backtrack (3 = one trial per update)
 
 
 def test_batched_matches_oracle_per_event(rt):
