@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparison")
     ap.add_argument("--serial", action="store_true", help="run the grid and search branches on one stream")
+    ap.add_argument("--shape", default=None, metavar="P,W,H,C,S",
+                    help="fixed launch shape instead of the autotuner's (profiling runs): search seeds per warp, "
+                         "warps per CTA, staged hits, CTA cap, grid hit slices")
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph instead of enqueueing "
                                                          "its kernels one by one")
     return ap.parse_args()
@@ -499,6 +502,13 @@ def main():
 
     # ---- launch shapes picked by the autotuner on this workload and GPU
     tuned = None
+    if args.shape:
+        p_, w_, h_, c_, s_ = (int(x) for x in args.shape.split(","))
+        for o, v in ((rt.OPT_BATCH_SEEDS_PER_WARP, p_), (rt.OPT_BATCH_WARPS, w_), (rt.OPT_BATCH_SMEM_HITS, h_),
+                     (rt.OPT_BATCH_CTAS, c_), (rt.OPT_GRID_SPLITS, s_)):
+            rt.set_option(o, v)
+        tuned = {"fixed_shape": args.shape}
+        args.no_tune = True
     if not args.no_tune:
         rt.prepare_hits(hits, offs, wl.model, out=(srt, boxes))
         tuned = {"grid": tune.tune_grid(srt, offs, wl.model, grid, wl.sigma_grid, boxes=boxes),
