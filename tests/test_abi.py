@@ -41,6 +41,12 @@ def test_options_roundtrip_and_validation():
     assert rt.get_option(rt.OPT_BATCH_CTAS) == 152
     rt.set_option(rt.OPT_BATCH_CTAS, 0)
     assert L.retina_set_option(rt.OPT_BATCH_CTAS, -1) == EINVAL
+    for o in (rt.OPT_GRID_TC, rt.OPT_SEEDNET_TC):
+        assert rt.get_option(o) == 1  # defaults
+        rt.set_option(o, 0)
+        assert rt.get_option(o) == 0
+        rt.set_option(o, 1)
+        assert L.retina_set_option(o, 2) == EINVAL
 
 
 def _grid(lo=(-0.5, -0.5), step=(2 ** -10, 2 ** -10), n=(1024, 1024)):
