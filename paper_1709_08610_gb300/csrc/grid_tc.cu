@@ -240,10 +240,16 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                     const int64_t kn = hb + block_of(cb + nxt) * GT_BK;
                     if (kn + t < he) pre = __ldg(hits + kn + t);
                 }
-                const bool ok = gt_wait(bar_addr, phase);
+                // one thread waits for the MMAs (the others at the barrier, not polling shared memory)
+                bool ok = true;
+                if (t == 0) {
+                    ok = gt_wait(bar_addr, phase);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                }
                 phase ^= 1u;
+                const bool all_ok = __syncthreads_and(ok);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (!__syncthreads_and(ok)) {
+                if (!all_ok) {
                     failed = true;
                     break;
                 }

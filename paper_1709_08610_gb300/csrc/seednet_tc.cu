@@ -141,7 +141,8 @@ conv2_head_tc_kernel(const uint16_t *__restrict__ h1, const float *__restrict__ 
         // one pixel's 8-channel group, gathered from the 8 channel planes (loads coalesced along
         // the columns) and stored as one 16-byte vector
         for (int idx = tid; idx < 4 * 2 * 66; idx += TC_THREADS) {
-            const int hc = idx % 66, grp = (idx / 66) & 1, hr = idx / (66 * 2);
+            // lanes take consecutive 16-byte chunks (pixel, channel group): conflict-free stores
+            const int grp = idx & 1, hc = (idx >> 1) % 66, hr = (idx >> 1) / 66;
             const int r = r0 - 1 + hr, c = hc - 1;
             uint32_t w[4] = {0u, 0u, 0u, 0u};
             if (r >= 0 && r < 64 && c >= 0 && c < 64) {
@@ -181,10 +182,16 @@ conv2_head_tc_kernel(const uint16_t *__restrict__ h1, const float *__restrict__ 
                              bar_addr)
                          : "memory");
         }
-        const bool ok = mbar_wait(bar_addr, phase);
+        // one thread waits for the MMAs (the others at the barrier, not polling shared memory)
+        bool ok = true;
+        if (tid == 0) {
+            ok = mbar_wait(bar_addr, phase);
+            tc_fence_before();
+        }
         phase ^= 1u;
+        const bool all_ok = __syncthreads_and(ok);
         tc_fence_after();
-        if (!__syncthreads_and(ok)) {  // every thread leaves together
+        if (!all_ok) {  // every thread leaves together
             failed = true;
             break;
         }
