@@ -71,6 +71,43 @@ def workload_config(wl, n_hits):
     }
 
 
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "paper_1709_08610_gb300", "csrc")
+# sources each profiled kernel is compiled from, and the committed ncu summary
+# holding its DRAM traffic per launch
+PROFILED = {
+    "batched_search_kernel": (("search_device.cuh", "batched_search.cu", "common.cuh", "internal.cuh"),
+                              "profiles/batched_search_kernel_velo_single_event.md"),
+    "grid_tc_kernel": (("grid_tc.cu", "grid_device.cuh", "common.cuh", "internal.cuh"),
+                       "profiles/grid_tc_kernel_velo_1024x1024.md"),
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in PROFILED[kernel][0]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed
+    ncu summary of the kernel - None when the kernel's sources changed since
+    that capture (the summary records their sha256) or there is none."""
+    import re
+    path = os.path.join(HERE, PROFILED[kernel][1])
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"source sha256: ([0-9a-f]{64})", text)
+    m_tr = re.search(r"traffic bytes per launch: (\d+)", text)
+    if not (m_sha and m_tr) or m_sha.group(1) != kernel_source_sha(kernel):
+        return None
+    return int(m_tr.group(1))
+
+
 _libcuda = None
 
 
@@ -632,7 +669,8 @@ def main():
         tf32 = bf16 * (1.1 / 2.25) if bf16 else None
         roof_grid = {"kernel": "grid_tc_kernel (+ slice reduction)", "bound": "tensor", "unit": "TFLOP/s",
                      "achieved": grid_tflops, "peak": (tf32 / 3) if tf32 else None,
-                     "frac": (grid_tflops / (tf32 / 3)) if tf32 else None, "traffic": None,
+                     "frac": (grid_tflops / (tf32 / 3)) if tf32 else None,
+                     "traffic": profiled_traffic("grid_tc_kernel"),
                      "pairs_evaluated": grid_pairs, "pairs_total": grid_pairs_all,
                      "effective_pairs_per_s": grid_pairs_all / (grid_ms * 1e-3),
                      "tf32_tflops_executed": 3 * grid_tflops,
@@ -651,7 +689,7 @@ def main():
     fr_ex2 = (search_ex2_rate / ex2_peak) if ex2_peak else None
     roof_search = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Tlane-op/s",
                    "achieved": search_fp32_rate / 1e12, "peak": (fma_rate / 1e12) if fma_rate else None,
-                   "frac": fr_fp32, "traffic": None,
+                   "frac": fr_fp32, "traffic": profiled_traffic("batched_search_kernel"),
                    "pairs_per_s": (rgh_pairs + r_pairs) / (search_ms * 1e-3),
                    "ex2_per_s": search_ex2_rate, "frac_ex2": fr_ex2, "rgh_pairs": rgh_pairs, "r_pairs": r_pairs,
                    "pairs_total": (wl.n_seeds * len(wl.sigma_schedule) + n_ev) * H,
