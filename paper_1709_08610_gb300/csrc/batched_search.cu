@@ -56,6 +56,7 @@ template <int MODEL, int P, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(BatchArgs a, LsParams prm) {
     extern __shared__ float4 sh[];
     __shared__ int cur_e;
+    pdl_release();  // the track extraction may be scheduled once every CTA has started
     const int tid = threadIdx.x, lane = tid & 31;
     float4 *sbox = staged_box_bounds(sh, a.smem_hits);
     float *sz2 = staged_box_z2(sh, a.smem_hits);

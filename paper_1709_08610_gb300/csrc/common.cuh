@@ -16,6 +16,14 @@ struct GridDev {
     int n0, n1;
 };
 
+// Programmatic dependent launch: a kernel launched with the
+// programmatic-serialization attribute may start while the previous kernel in
+// its stream finishes; it must wait (pdl_wait) before it reads that kernel's
+// output.  pdl_release lets the next such kernel be scheduled once every CTA
+// of this one has started.  Both are no-ops for plain launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // 2^x on the MUFU (SFU) pipe, denormal results flushed to zero.
 __device__ __forceinline__ float ex2_mufu(float x) {
     float y;

@@ -124,6 +124,7 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     __shared__ int warp_tot[EX_THREADS / 32];
     __shared__ int run;
 
+    pdl_wait();  // may be launched while the kernel producing its points finishes
     const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int n = prm.n_points;
     if (n_valid) {
@@ -296,7 +297,7 @@ cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint
     int C = 1;
     while (C < n_points) C <<= 1;
     prm.cap = C;
-    PrioLaunch L(dim3(n_events), dim3(EX_THREADS), extract_smem_bytes(n_points), st);
+    PrioLaunch L(dim3(n_events), dim3(EX_THREADS), extract_smem_bytes(n_points), st, true);
     const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel, theta, R, status, n_valid, prm, tracks,
                                                 track_R, track_src, n_tracks);
     count_launches(1);

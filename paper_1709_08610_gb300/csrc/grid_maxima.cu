@@ -152,6 +152,7 @@ constexpr int ORDER_THREADS = 1024;
 __global__ void __launch_bounds__(MAX_THREADS)
 maxima_detect_kernel(const float *__restrict__ Rall, int n0, int n1, float R0, int32_t *__restrict__ cand_count,
                      int32_t *__restrict__ cand) {
+    pdl_release();
     const int e = blockIdx.y;
     const int64_t cells = (int64_t)n0 * n1;
     const float *R = Rall + (int64_t)e * cells;
@@ -210,6 +211,8 @@ maxima_order_kernel(const float *__restrict__ Rall, GridDev g, float R0, const i
                     float *__restrict__ max_theta, float *__restrict__ max_R, int32_t *__restrict__ n_max) {
     __shared__ uint32_t x[CAND_CAP];
     __shared__ int warp_tot[ORDER_THREADS / 32];
+    pdl_wait();  // launched as a dependent of maxima_detect_kernel
+    pdl_release();
     const int e = blockIdx.x, t = threadIdx.x;
     const int64_t cells = (int64_t)g.n0 * g.n1;
     const float *R = Rall + (int64_t)e * cells;
@@ -272,10 +275,13 @@ cudaError_t launch_grid_maxima(const float *R, int n_events, const retina_grid *
     const int64_t cells = (int64_t)g->n[0] * g->n[1];
     const int dblk = (int)((cells + 4 * MAX_THREADS - 1) / (4 * MAX_THREADS));
     maxima_detect_kernel<<<dim3(dblk, n_events), MAX_THREADS, 0, st>>>(R, g->n[0], g->n[1], R0, cand_count, cand);
-    maxima_order_kernel<<<n_events, ORDER_THREADS, 0, st>>>(R, gd, R0, cand_count, cand, K, max_idx, max_theta,
-                                                            max_R, n_max);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    PrioLaunch L(dim3(n_events), dim3(ORDER_THREADS), 0, st, true);
+    err = cudaLaunchKernelEx(&L.cfg, maxima_order_kernel, R, gd, R0, (const int32_t *)cand_count,
+                             (const int32_t *)cand, K, max_idx, max_theta, max_R, n_max);
     count_launches(2);
-    return cudaGetLastError();
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 }  // namespace retina

@@ -294,6 +294,7 @@ grid_direct_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_
 // before their adds so that they overlap; the adds keep slice order.
 __global__ void reduce_partials_kernel(const float *__restrict__ part, int splits, int64_t split_stride, int64_t n,
                                        float *__restrict__ R) {
+    pdl_wait();  // launched as a dependent of the slice kernel
     const int64_t n4 = (split_stride % 4 == 0) ? n / 4 : 0;
     const float4 *p4 = reinterpret_cast<const float4 *>(part);
     const int64_t st4 = split_stride / 4;
@@ -390,8 +391,9 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
         const int cap = sm_count() * 8;
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        reduce_partials_kernel<<<blocks, 256, 0, st>>>(partials, p.splits, split_stride, n, R);
-        err = cudaGetLastError();
+        PrioLaunch L(dim3(blocks), dim3(256), 0, st, true);
+        err = cudaLaunchKernelEx(&L.cfg, reduce_partials_kernel, (const float *)partials, p.splits, split_stride, n, R);
+        if (err == cudaSuccess) err = cudaGetLastError();
     }
     return err;
 }

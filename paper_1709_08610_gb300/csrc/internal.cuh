@@ -63,11 +63,13 @@ size_t extract_smem_bytes(int n_points);
 
 // A launch configuration that carries the stream's priority as a launch
 // attribute, so that a CUDA graph captured from the stream keeps it on the
-// kernel node.  Use in place (cfg.attrs points into the object).
+// kernel node, and optionally programmatic stream serialization (the kernel
+// calls pdl_wait before reading its predecessor's output).  Use in place
+// (cfg.attrs points into the object).
 struct PrioLaunch {
     cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute attr;
-    PrioLaunch(dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    cudaLaunchAttribute attr[2];
+    PrioLaunch(dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl = false) {
         int prio = 0;
         if (cudaStreamGetPriority(st, &prio) != cudaSuccess) prio = 0;
         cfg = cudaLaunchConfig_t{};
@@ -75,10 +77,12 @@ struct PrioLaunch {
         cfg.blockDim = block;
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
-        attr.id = cudaLaunchAttributePriority;
-        attr.val.priority = prio;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
+        attr[0].id = cudaLaunchAttributePriority;
+        attr[0].val.priority = prio;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = pdl ? 2 : 1;
     }
     PrioLaunch(const PrioLaunch &) = delete;
     PrioLaunch &operator=(const PrioLaunch &) = delete;
