@@ -165,6 +165,61 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     }
     __syncthreads();
     const int nc = nc_s;
+    if (nc <= 64) {
+        // few candidates: one warp applies the sequential definition directly -
+        // rank order by a register sort, then ranks in order, each kept unless it
+        // conflicts with a kept one (lane l tests ranks l and l + 32)
+        if (warp != 0) return;
+        uint64_t v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) v[q] = 2 * lane + q < nc ? keys[2 * lane + q] : ~0ull;
+        bitonic_sort_regs<uint64_t, 2, 32>(v, keys);
+        // rank r = 2 lane + q holds v[q]; lane l keeps ranks l and l + 32 for the tests
+        float a0[2], a1[2];
+        int si[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;  // rank r sits in lane r / 2, slot r % 2
+            const uint64_t k0 = __shfl_sync(0xffffffffu, v[0], r >> 1), k1 = __shfl_sync(0xffffffffu, v[1], r >> 1);
+            const uint64_t kr = (r & 1) ? k1 : k0;
+            si[h] = (int)(uint32_t)kr;
+            a0[h] = a1[h] = 0.f;
+            if (r < nc) {
+                const int64_t o = base + si[h];
+                a0[h] = theta[2 * o];
+                a1[h] = theta[2 * o + 1];
+            }
+        }
+        unsigned kept0 = 0u, kept1 = 0u;  // bit l: rank l (kept0) or l + 32 (kept1) kept
+        for (int r = 0; r < nc; ++r) {
+            const int h = r >> 5, l = r & 31;
+            const float b0 = __shfl_sync(0xffffffffu, h ? a0[1] : a0[0], l);
+            const float b1 = __shfl_sync(0xffffffffu, h ? a1[1] : a1[0], l);
+            const bool c0 = ((kept0 >> lane) & 1u) && abs_diff_lt(a0[0], b0, prm.c0) && abs_diff_lt(a1[0], b1, prm.c1);
+            const bool c1 = ((kept1 >> lane) & 1u) && abs_diff_lt(a0[1], b0, prm.c0) && abs_diff_lt(a1[1], b1, prm.c1);
+            if (!__any_sync(0xffffffffu, c0 || c1)) {
+                if (h) kept1 |= 1u << l;
+                else kept0 |= 1u << l;
+            }
+        }
+        // kept ranks in rank order
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;
+            if (!(((h ? kept1 : kept0) >> lane) & 1u)) continue;
+            const int pos = (h ? __popc(kept0) : 0) + __popc((h ? kept1 : kept0) & ((1u << lane) - 1u));
+            if (pos < prm.K) {
+                const int64_t o = (int64_t)e * prm.K + pos;
+                tracks[2 * o] = a0[h];
+                tracks[2 * o + 1] = a1[h];
+                track_R[o] = R[base + si[h]];
+                if (track_src) track_src[o] = si[h];
+            }
+            (void)r;
+        }
+        if (lane == 0) n_tracks[e] = __popc(kept0) + __popc(kept1);
+        return;
+    }
     int C = 1;
     while (C < nc) C <<= 1;
     for (int i = nc + tid; i < C; i += EX_THREADS) keys[i] = ~0ull;

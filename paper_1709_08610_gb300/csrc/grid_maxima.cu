@@ -219,6 +219,20 @@ maxima_order_kernel(const float *__restrict__ Rall, GridDev g, float R0, const i
     const int total = cand_count[e];
     if (t == 0) n_max[e] = total;
     const int32_t *ce = cand + (int64_t)e * CAND_CAP;
+    if (total <= 64) {
+        // few candidates: one warp sorts them in registers
+        if (t >= 32) return;
+        uint32_t v[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) v[r] = 2 * t + r < total ? (uint32_t)ce[2 * t + r] : 0xffffffffu;
+        bitonic_sort_regs<uint32_t, 2, 32>(v, x);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int q = 2 * t + r;
+            if (q < total && q < K) write_maximum(R, g, (int64_t)e * K + q, v[r], max_idx, max_theta, max_R);
+        }
+        return;
+    }
     if (total <= CAND_CAP) {
         // sorted by linear index; thread t holds ranks t RK .. t RK + RK - 1
 #define RETINA_ORDER_CASE(RK)                                                          \

@@ -382,7 +382,7 @@ def test_extract_tracks_exact_random_clusters_and_edges(rt):
     # the merge distance, n_valid, K truncation and an all-rejected event
     rng = np.random.default_rng(11)
     lo, step, n = (-1.0, -1.0), (2 ** -6, 2 ** -6), (128, 128)
-    E, P = 4, 3000
+    E, P = 6, 3000
     centres = rng.uniform(-1.0, 1.0, (E, 60, 2))
     th = centres[np.arange(E)[:, None], rng.integers(0, 60, (E, P))] + rng.normal(0, 2 * step[0], (E, P, 2))
     th = np.round(th / (step[0] / 8)) * (step[0] / 8)  # on a lattice: exact merge-distance hits
@@ -392,18 +392,26 @@ def test_extract_tracks_exact_random_clusters_and_edges(rt):
     st = rng.integers(0, 4, (E, P)).astype(np.uint8)
     R[3] = 0.0
     th = th.astype(np.float32)
-    nv = np.array([P, 2500, 17, P], np.int32)
-    K = 100
-    out = rt.extract_tracks(dev(th), dev(R), dev(st), rt.Grid(lo, step, n), 5.0, 2.0, K, n_valid=dev(nv))
-    n_tr = out["n_tracks"].cpu().numpy()
-    src = out["track_src"].cpu().numpy()
-    for e in range(E):
+    # events 2, 4 and 5 keep at most 64 candidates (one warp decides them)
+    nv = np.array([P, 2500, 17, P, 100, 140], np.int32)
+    n_cand = []
+    for K in (100, 8):
+        out = rt.extract_tracks(dev(th), dev(R), dev(st), rt.Grid(lo, step, n), 5.0, 2.0, K, n_valid=dev(nv))
+        n_tr = out["n_tracks"].cpu().numpy()
+        src = out["track_src"].cpu().numpy()
+        for e in range(E):
+            m = nv[e]
+            keep = oracle.extract_tracks(th[e, :m], R[e, :m], st[e, :m], lo, step, n, 5.0, 2.0)
+            assert n_tr[e] == len(keep)
+            k = min(K, len(keep))
+            assert src[e, :k].tolist() == keep[:k].tolist()
+        assert n_tr[0] > K and n_tr[3] == 0
+    for e in (4, 5):
         m = nv[e]
-        keep = oracle.extract_tracks(th[e, :m], R[e, :m], st[e, :m], lo, step, n, 5.0, 2.0)
-        assert n_tr[e] == len(keep)
-        k = min(K, len(keep))
-        assert src[e, :k].tolist() == keep[:k].tolist()
-    assert n_tr[0] > K and n_tr[3] == 0
+        ok = (st[e, :m] <= 1) & (R[e, :m] >= 5.0) & np.all((th[e, :m] >= -1.0) & (th[e, :m] < 1.0), axis=1)
+        n_cand.append(int(ok.sum()))
+    assert 32 < n_cand[0] <= 64 and 32 < n_cand[1] <= 64, n_cand  # both halves of the warp's ranks
+    assert n_tr[4] > 8  # truncation at K inside the one-warp path
 
 
 # ---------------------------------------------------------------------------
