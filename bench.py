@@ -556,12 +556,17 @@ def main():
     # runs it (graph replays behind the L2 flush)
     if not args.no_tune and not args.serial:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        cands = [(32, 0), (32, 3 * sms // 4), (32, sms // 2), (16, 0), (16, 3 * sms // 2), (16, sms),
-                 (8, 2 * sms), (8, sms)]
+        # search CTA shape x grid hit slices (the grid alone prefers more slices
+        # than it can use while the search holds most SMs)
+        g0 = rt.get_option(rt.OPT_GRID_SPLITS)
+        cands = [(w, c, sp) for (w, c) in ((32, 0), (32, 3 * sms // 4), (32, sms // 2), (16, 0),
+                                            (16, 3 * sms // 2), (16, sms), (8, 2 * sms))
+                 for sp in sorted({g0, 4, 8})]
         table = {}
-        for w, c in cands:
+        for w, c, sp in cands:
             rt.set_option(rt.OPT_BATCH_WARPS, w)
             rt.set_option(rt.OPT_BATCH_CTAS, c)
+            rt.set_option(rt.OPT_GRID_SPLITS, sp)
             if not args.graph:
                 g_c = None
                 evs_c = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(15)]
@@ -572,13 +577,14 @@ def main():
                 evs_c = None
                 for _ in range(3):
                     g_c.replay()
-            table["%d,%d" % (w, c)] = float(np.median(timed_steps(g_c, 15, evs_c)[:, 7]))
+            table["%d,%d,%d" % (w, c, sp)] = float(np.median(timed_steps(g_c, 15, evs_c)[:, 7]))
             del g_c
         best = min(table, key=table.get)
-        w, c = (int(x) for x in best.split(","))
+        w, c, sp = (int(x) for x in best.split(","))
         rt.set_option(rt.OPT_BATCH_WARPS, w)
         rt.set_option(rt.OPT_BATCH_CTAS, c)
-        tuned["overlap"] = {"warps": w, "ctas": c, "step_ms": table[best], "table_ms": table}
+        rt.set_option(rt.OPT_GRID_SPLITS, sp)
+        tuned["overlap"] = {"warps": w, "ctas": c, "grid_splits": sp, "step_ms": table[best], "table_ms": table}
 
     # ---- peaks of the FP32 and MUFU pipes, measured live (burst)
     peaks = {}
