@@ -703,37 +703,95 @@ def main():
     dominant = "grid" if grid_ms >= search_ms else "search"
     roofline = roof_grid if dominant == "grid" else roof_search
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step copies
+    # the event's hits and seeds in from pinned host memory, runs the whole path
+    # through the native executor (retina_pipeline_run: one call enqueues every
+    # launch of the step, the two branches on two streams) - or replays the step
+    # graph with --graph - and copies both track lists out to pinned host memory
     e2e = None
     if rank == 0 or True:
         hits_h = torch.from_numpy(ev.hits).pin_memory()
         seeds_h = torch.from_numpy(seeds_np).view(-1, 2).pin_memory()
-        out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in tr_search.items()}
-        outg_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in tr_grid.items()}
         n_e2e = max(10, min(args.steps, 200))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(n_e2e):
-            hits.copy_(hits_h, non_blocking=True)
-            seeds.copy_(seeds_h, non_blocking=True)
-            if graph is not None:
+        keys = ("tracks", "track_R", "n_tracks")
+
+        def host_like(r):
+            return {m: {k2: torch.empty(r[m][k2].shape, dtype=r[m][k2].dtype).pin_memory() for k2 in keys}
+                    for m in r}
+
+        def copy_out(dst, src):
+            for m in dst:
+                for k2 in keys:
+                    dst[m][k2].copy_(src[m][k2], non_blocking=True)
+
+        if graph is not None:
+            res = {"search": tr_search, "grid": tr_grid}
+            out_h = host_like(res)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(n_e2e):
+                hits.copy_(hits_h, non_blocking=True)
+                seeds.copy_(seeds_h, non_blocking=True)
                 graph.replay()
-            else:
-                step()
-            for k2 in out_h:
-                out_h[k2].copy_(tr_search[k2], non_blocking=True)
-                outg_h[k2].copy_(tr_grid[k2], non_blocking=True)
-        b.record(stream)
+                copy_out(out_h, res)
+            b.record(stream)
+        else:
+            # two sets of device inputs and outputs: a copy stream brings step k + 1's
+            # event in and takes step k - 1's track lists out while step k runs
+            pipe = rt.Pipeline(wl.model, grid, wl.sigma_grid, R0, opts, wl.merge_cells, max_events=1, max_hits=H,
+                               seeds_per_event=wl.n_seeds, max_maxima=K_MAX, max_tracks=K_TR)
+            hits_d, seeds_d = [hits, torch.empty_like(hits)], [seeds, torch.empty_like(seeds)]
+            res_d = [pipe.run(hits, offs, seeds), pipe.run(hits, offs, seeds)]
+            out_h = host_like(res_d[0])
+            cs = torch.cuda.Stream(dev)
+            in_ready, done, read = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+            torch.cuda.synchronize()
+            a.record(stream)
+            cs.wait_event(a)
+
+            def copy_in(i):
+                cs.wait_event(done[i])  # the step that last read buffer i has finished
+                with torch.cuda.stream(cs):
+                    hits_d[i].copy_(hits_h, non_blocking=True)
+                    seeds_d[i].copy_(seeds_h, non_blocking=True)
+                in_ready[i].record(cs)
+
+            copy_in(0)
+            for k in range(n_e2e):
+                i = k % 2
+                if k + 1 < n_e2e:
+                    copy_in(1 - i)
+                stream.wait_event(in_ready[i])
+                stream.wait_event(read[i])  # track lists of step k - 2 copied out
+                pipe.run(hits_d[i], offs, seeds_d[i], out=res_d[i])
+                done[i].record(stream)
+                cs.wait_event(done[i])
+                with torch.cuda.stream(cs):
+                    copy_out(out_h, res_d[i])
+                read[i].record(cs)
+            stream.wait_stream(cs)
+            b.record(stream)
         b.synchronize()
         e2e_ms = a.elapsed_time(b) / n_e2e
-        d2h = sum(v.numel() * v.element_size() for v in out_h.values()) * 2
+        # the executor's track lists are the step's (same launchers, same options)
+        for m, ref in (("search", tr_search), ("grid", tr_grid)):
+            nt = int(out_h[m]["n_tracks"][0])
+            assert nt == int(ref["n_tracks"][0].item())
+            k = min(nt, K_TR)
+            assert torch.equal(out_h[m]["tracks"][0, :k], ref["tracks"][0, :k].cpu())
+        d2h = sum(v.numel() * v.element_size() for m in out_h for v in out_h[m].values())
         h2d = hits_h.numel() * 4 + seeds_h.numel() * 4
         e2e = {"value": world * 1e3 / e2e_ms, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
-               "note": "back-to-back steps (%s) with the pinned host->device copy of the hits and seeds and the "
-                       "device->host copy of both track lists in every step, timed with CUDA events"
-                       % ("eager launches" if graph is None else "one graph replay per step")}
+               "note": "%s; every step copies its hits and seeds in from pinned host memory and both track lists "
+                       "out to pinned host memory, timed with CUDA events"
+                       % ("one step-graph replay per step, copies in stream order" if graph is not None else
+                          "retina_pipeline_run (native executor) per step, copies on a second stream "
+                          "overlapping the neighbouring steps (two input and output buffer sets), steps back to "
+                          "back without an L2 flush as in a stream of events")}
+        if graph is None:
+            pipe.close()
 
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None

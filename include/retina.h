@@ -527,6 +527,68 @@ int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo
                       int32_t min_sub_hits, const float *hits, int64_t n_hits, const int64_t *event_offsets,
                       float *seeds, int32_t *cell_idx, void *stream);
 
+/*
+ * retina_pipeline_* - one call per batch of events for the whole path.
+ *
+ * Not a step of the paper: a native executor.  retina_pipeline_run enqueues
+ * on the caller's stream the hit ordering (retina_prepare_hits), then, on two
+ * concurrent streams, the grid method (retina_grid_response,
+ * retina_grid_maxima, retina_extract_tracks of the maxima) and Algorithm 1
+ * from the caller's starting points (retina_batched_search and
+ * retina_extract_tracks, on a high-priority stream the pipeline owns), and
+ * joins both back into the caller's stream.  Results are those of the
+ * separate calls with the same launch options.  The pipeline owns its stream,
+ * events and device workspace, allocated by retina_pipeline_create for the
+ * configured capacities; runs allocate nothing.  Runs of one pipeline must be
+ * ordered (one stream, or synchronised): they share the workspace.
+ *
+ * retina_pipeline_config:
+ *   model, grid, sigma_grid, R0 : the grid method (as retina_grid_scan).
+ *   opts        : Algorithm 1's options (as retina_batched_search); grid is
+ *                 also the search's box.
+ *   merge_cells : extraction merge distance in cells (both methods).
+ *   max_events, max_hits : capacities of a run.
+ *   seeds_per_event : S, every event's number of starting points.
+ *   max_maxima  : maxima kept per event by the grid method (K of
+ *                 retina_grid_maxima), 1 .. 8192.
+ *   max_tracks  : tracks written per event and method (K of
+ *                 retina_extract_tracks).
+ * retina_pipeline_create validates the configuration before allocating
+ * (RETINA_EINVAL, nothing allocated) and returns RETINA_ECUDA when an
+ * allocation fails.
+ * retina_pipeline_run:
+ *   hits, n_hits, event_offsets, n_events : as retina_prepare_hits
+ *                 (n_events <= max_events, n_hits <= max_hits).
+ *   seeds       : float32 [n_events][S][2].
+ *   grid_tracks, grid_track_R, grid_n_tracks : float32 [n_events][max_tracks][2],
+ *                 float32 [n_events][max_tracks], int32 [n_events].
+ *   search_tracks, search_track_R, search_n_tracks : the same for the search.
+ *   Returns RETINA_ENOSPACE (nothing launched) when the grid's hit-slice
+ *   partials for the current RETINA_OPT_GRID_SPLITS exceed the workspace.
+ */
+typedef struct {
+    int32_t model;
+    retina_grid grid;
+    float sigma_grid;
+    float R0;
+    float merge_cells;
+    retina_ls_opts opts;
+    int32_t max_events;
+    int64_t max_hits;
+    int32_t seeds_per_event;
+    int32_t max_maxima;
+    int32_t max_tracks;
+} retina_pipeline_config;
+
+typedef struct retina_pipeline retina_pipeline;
+
+int retina_pipeline_create(const retina_pipeline_config *config, retina_pipeline **out);
+int retina_pipeline_run(retina_pipeline *p, const float *hits, int64_t n_hits, const int64_t *event_offsets,
+                        int32_t n_events, const float *seeds, float *grid_tracks, float *grid_track_R,
+                        int32_t *grid_n_tracks, float *search_tracks, float *search_track_R,
+                        int32_t *search_n_tracks, void *stream);
+int retina_pipeline_destroy(retina_pipeline *p);
+
 #ifdef __cplusplus
 }
 #endif

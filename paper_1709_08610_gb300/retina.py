@@ -87,12 +87,22 @@ class LsOpts:
         return o
 
 
+class _CPipelineConfig(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("grid", _CGrid), ("sigma_grid", ctypes.c_float), ("R0", ctypes.c_float),
+                ("merge_cells", ctypes.c_float), ("opts", _CLsOpts), ("max_events", ctypes.c_int32),
+                ("max_hits", ctypes.c_int64), ("seeds_per_event", ctypes.c_int32), ("max_maxima", ctypes.c_int32),
+                ("max_tracks", ctypes.c_int32)]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
         raise ImportError("libretina.so is not built (%s); run paper_1709_08610_gb300.build.build()" % path)
     L = ctypes.CDLL(path)
     P, I32, I64, F, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    L.retina_pipeline_create.argtypes = [P, P]
+    L.retina_pipeline_run.argtypes = [P, P, I64, P, I32, P, P, P, P, P, P, P, P]
+    L.retina_pipeline_destroy.argtypes = [P]
     L.retina_strerror.argtypes = [ctypes.c_int]
     L.retina_strerror.restype = ctypes.c_char_p
     L.retina_abi_version.restype = ctypes.c_int
@@ -535,3 +545,56 @@ def topk_seeds(logits: torch.Tensor, K: int, lo: float = -0.5, hi: float = 0.5, 
     _check("retina_topk_seeds", lib.retina_topk_seeds(_p(logits), E, K, lo, hi, zmin, int(min_sub_hits), _p(hits),
                                                       n_hits, _p(offsets), _p(seeds), _p(idx), _stream(stream)))
     return (seeds, idx) if want_idx else seeds
+
+
+class Pipeline:
+    """The whole path for a batch of events in one native call
+    (retina_pipeline_*): hit ordering, then the grid method and Algorithm 1
+    from the given starting points on two concurrent streams.  Owns its
+    device workspace (allocated here, for the given capacities)."""
+
+    def __init__(self, model: int, grid: Grid, sigma_grid: float, R0: float, opts: LsOpts, merge_cells: float,
+                 max_events: int, max_hits: int, seeds_per_event: int, max_maxima: int = 4096,
+                 max_tracks: int = 1024):
+        c = _CPipelineConfig()
+        c.model, c.grid, c.sigma_grid, c.R0, c.merge_cells = model, grid.c(), sigma_grid, R0, merge_cells
+        c.opts = opts.c()
+        c.max_events, c.max_hits, c.seeds_per_event = max_events, max_hits, seeds_per_event
+        c.max_maxima, c.max_tracks = max_maxima, max_tracks
+        self.S, self.K, self.max_events = int(seeds_per_event), int(max_tracks), int(max_events)
+        h = ctypes.c_void_p()
+        _check("retina_pipeline_create", lib.retina_pipeline_create(ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, hits: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor, out=None, stream=None) -> dict:
+        """seeds [n_events * S, 2]; returns {"grid": {...}, "search": {...}} with
+        tracks [E, K, 2], track_R [E, K], n_tracks [E] per method."""
+        if not self._h:
+            raise RuntimeError("pipeline closed")
+        _dev(hits, torch.float32, "hits", 4)
+        _dev(offsets, torch.int64, "offsets")
+        _dev(seeds, torch.float32, "seeds", 2)
+        E = offsets.numel() - 1
+        if seeds.numel() != 2 * E * self.S:
+            raise ValueError("seeds must hold n_events * seeds_per_event points")
+        dev = hits.device
+        if out is None:
+            out = {m: dict(tracks=torch.empty((E, self.K, 2), dtype=torch.float32, device=dev),
+                           track_R=torch.empty((E, self.K), dtype=torch.float32, device=dev),
+                           n_tracks=torch.empty((E,), dtype=torch.int32, device=dev)) for m in ("grid", "search")}
+        g, s = out["grid"], out["search"]
+        _check("retina_pipeline_run", lib.retina_pipeline_run(
+            self._h, _p(hits), hits.shape[0], _p(offsets), E, _p(seeds), _p(g["tracks"]), _p(g["track_R"]),
+            _p(g["n_tracks"]), _p(s["tracks"]), _p(s["track_R"]), _p(s["n_tracks"]), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.retina_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -207,3 +207,31 @@ def test_sort_seeds_rejects_before_launch():
     assert L.retina_sort_seeds(ctypes.c_void_p(0x1004), 10, BOGUS, 1, ctypes.byref(g), ctypes.c_void_p(0x2000),
                                None, None) == EINVAL  # misaligned
     assert L.retina_sort_seeds(None, 0, None, 0, ctypes.byref(g), None, None, None) == 0
+
+
+def test_pipeline_config_validation_needs_no_gpu():
+    import ctypes
+
+    def cfg(**kw):
+        c = rt._CPipelineConfig()
+        c.model, c.grid, c.sigma_grid, c.R0, c.merge_cells = 1, _grid(), 0.378, 11.7, 2.0
+        c.opts = rt.LsOpts().c()
+        c.max_events, c.max_hits, c.seeds_per_event, c.max_maxima, c.max_tracks = 1, 4096, 8192, 8192, 4096
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    h = ctypes.c_void_p()
+    bad = [dict(model=7), dict(sigma_grid=0.0), dict(R0=float("nan")), dict(merge_cells=-1.0),
+           dict(max_events=0), dict(max_hits=-1), dict(seeds_per_event=0), dict(seeds_per_event=8193),
+           dict(max_maxima=0), dict(max_maxima=9000), dict(max_tracks=0), dict(merge_cells=1e-3)]
+    for kw in bad:
+        assert L.retina_pipeline_create(ctypes.byref(cfg(**kw)), ctypes.byref(h)) == EINVAL, kw
+        assert h.value is None
+    c = cfg()
+    c.opts.q = 0
+    assert L.retina_pipeline_create(ctypes.byref(c), ctypes.byref(h)) == EINVAL
+    assert L.retina_pipeline_create(None, ctypes.byref(h)) == EINVAL
+    assert L.retina_pipeline_create(ctypes.byref(cfg()), None) == EINVAL
+    assert L.retina_pipeline_destroy(None) == EINVAL
+    assert L.retina_pipeline_run(None, None, 0, None, 1, None, None, None, None, None, None, None, None) == EINVAL
