@@ -367,8 +367,10 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
         if (!flag) return cudaErrorInvalidSymbol;
         cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(grid_tc_kernel), grid_tc_smem_bytes());
         if (aerr != cudaSuccess) return aerr;
-        grid_tc_kernel<<<grid, 256, grid_tc_smem_bytes(), st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst,
-                                                                split_stride, cells, work_counters(), flag);
+        PrioLaunch L(grid, dim3(256), grid_tc_smem_bytes(), st, true);
+        cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, grid_tc_kernel, hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0,
+                                              dst, split_stride, cells, work_counters(), flag);
+        if (lerr != cudaSuccess) return lerr;
     } else if (p.separable) {
         grid_sep_kernel<<<grid, SEP_THREADS, 0, st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst, split_stride, cells,
                                                       work_counters());

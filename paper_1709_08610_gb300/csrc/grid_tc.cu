@@ -105,6 +105,7 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                int32_t *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char gsm[];
     pdl_release();  // the slice reduction may be scheduled once every CTA has started
+    pdl_wait();     // may be launched while the hit ordering finishes
     unsigned *keep_mask = reinterpret_cast<unsigned *>(gsm + OFF_MASK);
     uint64_t *bar = reinterpret_cast<uint64_t *>(gsm + OFF_BAR);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(gsm + OFF_BAR + 8);

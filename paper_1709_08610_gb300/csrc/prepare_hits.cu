@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(PREP_THREADS)
 prepare_hits_cluster_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
                             int model, float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
     __shared__ uint32_t x[SORT_CAP / CL];
+    pdl_release();  // the grid kernel may be scheduled once every CTA has started
     const int e = blockIdx.x / CL, rank = blockIdx.x % CL;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
