@@ -108,6 +108,8 @@ def profiled_traffic(kernel: str):
     return int(m_tr.group(1))
 
 
+TUNE_STEPS = 41  # timed steps per launch-shape candidate of the two-stream step (median)
+
 _libcuda = None
 
 
@@ -569,7 +571,7 @@ def main():
             rt.set_option(rt.OPT_GRID_SPLITS, sp)
             if not args.graph:
                 g_c = None
-                evs_c = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(15)]
+                evs_c = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(TUNE_STEPS)]
                 for _ in range(3):
                     step()
             else:
@@ -577,7 +579,7 @@ def main():
                 evs_c = None
                 for _ in range(3):
                     g_c.replay()
-            table["%d,%d,%d" % (w, c, sp)] = float(np.median(timed_steps(g_c, 15, evs_c)[:, 7]))
+            table["%d,%d,%d" % (w, c, sp)] = float(np.median(timed_steps(g_c, TUNE_STEPS, evs_c)[:, 7]))
             del g_c
         best = min(table, key=table.get)
         w, c, sp = (int(x) for x in best.split(","))
