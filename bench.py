@@ -218,13 +218,30 @@ def oracle_step_sample(ev, wl, seeds, row_frac: int, seed_frac: int):
     idx = oracle.grid_maxima(R, wl.R0)
     c0, c1 = oracle.cell_centres(wl.grid_lo, wl.grid_step, (n0, rows))
     gth = np.stack([c0[idx % n0], c1[idx // n0]], 1)
-    oracle.extract_tracks(gth, R.reshape(-1)[idx], None, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0, wl.merge_cells)
+    keep_g = oracle.extract_tracks(gth, R.reshape(-1)[idx], None, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0,
+                                   wl.merge_cells)
     t1 = time.perf_counter()
     th, Rs, st, m = oracle.local_search(ev.hits, wl.model, seeds[:ns], wl.sigma_schedule, wl.grid_lo, wl.grid_step,
                                         wl.grid_n)
-    oracle.extract_tracks(th, Rs, st, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0, wl.merge_cells)
+    keep_s = oracle.extract_tracks(th, Rs, st, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0, wl.merge_cells)
     t2 = time.perf_counter()
-    return (t1 - t0) * (n1 / rows) + (t2 - t1) * (len(seeds) / ns), (t2 - t0)
+    tracks = {"grid": gth[keep_g], "search": th[keep_s]} if (rows == n1 and ns == len(seeds)) else None
+    return (t1 - t0) * (n1 / rows) + (t2 - t1) * (len(seeds) / ns), (t2 - t0), tracks
+
+
+def oracle_agreement(oracle_tracks, gpu_tracks, step, tol_cells: float = 1e-3) -> dict:
+    """Track-set agreement with the oracle on the same event: the share of the
+    oracle's tracks the GPU finds within tol_cells grid steps (max norm), and
+    the GPU tracks matching none of the oracle's."""
+    o = np.asarray(oracle_tracks, np.float64).reshape(-1, 2)
+    g = np.asarray(gpu_tracks, np.float64).reshape(-1, 2)
+    if len(o) == 0 or len(g) == 0:
+        return {"oracle_tracks": len(o), "gpu_tracks": len(g), "efficiency_vs_oracle": 1.0 if len(o) == 0 else 0.0,
+                "unmatched_gpu_tracks": len(g)}
+    d = np.max(np.abs(o[:, None, :] - g[None, :, :]) / np.asarray(step), axis=2)
+    return {"oracle_tracks": len(o), "gpu_tracks": len(g),
+            "efficiency_vs_oracle": float((d.min(axis=1) <= tol_cells).mean()),
+            "unmatched_gpu_tracks": int((d.min(axis=0) > tol_cells).sum())}
 
 
 def oracle_threads() -> int:
@@ -241,7 +258,7 @@ def run_reference(args, rank: int):
     ev = make_event(wl, RUN_SEED, 0)
     seeds = uniform_seeds(wl, wl.n_seeds, RUN_SEED, 0)
     # size each step's sample so the whole --steps/--warmup run takes ~90 s
-    _, probe_wall = oracle_step_sample(ev, wl, seeds, 64, 64)
+    _, probe_wall, _ = oracle_step_sample(ev, wl, seeds, 64, 64)
     t_full = probe_wall * 64.0
     frac = min(1.0, max(1.0 / 1024, 90.0 / max(1, args.steps + max(args.warmup, 0)) / max(t_full, 1e-6)))
     row_frac = int(min(wl.grid_n[1], max(1, round(1.0 / frac))))
@@ -251,7 +268,7 @@ def run_reference(args, rank: int):
     est = []
     cpu_s = 0.0
     for _ in range(args.steps):
-        e, c = oracle_step_sample(ev, wl, seeds, row_frac, seed_frac)
+        e, c, _ = oracle_step_sample(ev, wl, seeds, row_frac, seed_frac)
         est.append(e)
         cpu_s += c
     sec_per_event = float(np.mean(est))
@@ -802,10 +819,16 @@ def main():
         oracle.build()
         ests, wall = [], 0.0
         while wall < 10.0 and len(ests) < 20:
-            est, w = oracle_step_sample(ev, wl, seeds_np, 1, 1)
+            est, w, o_tracks = oracle_step_sample(ev, wl, seeds_np, 1, 1)
             ests.append(est)
             wall += w
+        # the timed steps' track lists against the oracle's on the same event
+        agreement = {}
+        for m, tr in (("grid", tr_grid), ("search", tr_search)):
+            nt = min(int(tr["n_tracks"][0].item()), K_TR)
+            agreement[m] = oracle_agreement(o_tracks[m], tr["tracks"][0, :nt].cpu().numpy(), wl.grid_step)
         cpu = {"value": len(ests) / sum(ests), "unit": "events/s", "cores": oracle_threads(), "kind": "oracle",
+               "track_agreement": agreement,
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
