@@ -269,6 +269,16 @@ __device__ __forceinline__ CullPt cull_pt(float t0, float t1, float kk, float cu
     return CullPt{t0, t1, kk};
 }
 
+// Constants for skipping a block only when it is skippable at both of two
+// bandwidths (a pass that sums at both).
+template <int MODEL>
+__device__ __forceinline__ CullPt cull_pt_union(float t0, float t1, float kk_a, float cull_a, float kk_b,
+                                                float cull_b) {
+    if (MODEL == RETINA_VELO_SLOPES)
+        return CullPt{t0, t1, (isfinite(t0) && isfinite(t1)) ? fmaxf(cull_a, cull_b) : INFINITY};
+    return CullPt{t0, t1, fminf(kk_a, kk_b)};
+}
+
 // True when every hit of the block (box in search_box form) has
 // s^2 log2(e) / sigma^2 > CULL_EXPONENT at the point.  Slope model:
 // s^2 = z^2 |(u, v) - theta|^2 >= |z|min^2 dist^2, each distance with one
@@ -371,6 +381,131 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
     return visited;
 }
 
+// Algorithm 1 for one seed per warp (the latency-bound shape), with the same
+// arithmetic as search_group<MODEL, 1> in fewer passes: the first line-search
+// trial of update j (t = 1) is the point update j + 1 starts from whenever it
+// is accepted - 91 % of the time on the VELO-like events - so that pass also
+// accumulates the gradient/Hessian sums at bandwidth sigma_{j+1}, and update
+// j + 1 uses them instead of a pass of its own.  The pass skips a block only
+// when it is skippable at both bandwidths, so each sum gets exactly the terms
+// of its own pass plus exact zeros, in the same per-lane order: every result,
+// status and trial count is bitwise search_group's.
+template <int MODEL>
+__device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
+                                           int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
+                                           const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
+                                           const float *__restrict__ seeds, const LsParams &prm,
+                                           float *__restrict__ theta_out, float *__restrict__ R_out,
+                                           uint8_t *__restrict__ status, uint8_t *__restrict__ n_evals,
+                                           unsigned long long *__restrict__ work) {
+    unsigned long long w_rgh = 0, w_r = 0;
+    constexpr int NS = Model<MODEL>::NS;
+    float th0 = seeds[0], th1 = seeds[1], Rfin = 0.f;
+    int evals = 0;
+    bool failed = false;
+    float S[NS];
+    bool have = false;  // S holds the sums at (theta, sigma_j) from the previous update's first trial
+    for (int j = 0; j < prm.q; ++j) {
+        const float kk = prm.kk[j], k = prm.k[j], cull = prm.cull[j];
+        if (!have) {
+            RghAcc<MODEL> acc;
+            acc.zero();
+            const CullPt cp = cull_pt<MODEL>(th0, th1, kk, cull);
+            const int vis = hit_pass<MODEL, true>(
+                sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, cp); },
+                [&](const float4 h) { acc.add(h, th0, th1, kk); },
+                [&](const float4 a, const float4 b) { acc.add2(a, b, th0, th1, kk); });
+            acc.sums(S);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) S[i] = warp_sum(S[i]);
+            w_rgh += (unsigned long long)vis;
+        }
+        have = false;
+        float R, g0, g1, H00, H01, H11, pp0, pp1;
+        sums_to_rgh<MODEL>(S, k, R, g0, g1, H00, H01, H11);
+        newton_cg(g0, g1, H00, H01, H11, pp0, pp1);
+        const float cells = fmaxf(fabsf(pp0) / prm.box.step0, fabsf(pp1) / prm.box.step1);
+        if (cells > prm.cap) {
+            const float sc = prm.cap / cells;
+            pp0 *= sc;
+            pp1 *= sc;
+        }
+        const float slope = g0 * pp0 + g1 * pp1;
+        float t = 1.f;
+        bool pending = true;
+        Rfin = R;  // R at the point if no step is accepted
+        const bool fuse = j + 1 < prm.q;
+        for (int hv = 0; hv <= prm.max_halvings && pending; ++hv) {
+            const float tr0 = __fmaf_rn(t, pp0, th0), tr1 = __fmaf_rn(t, pp1, th1);
+            float Rt = 0.f;
+            int vis;
+            if (hv == 0 && fuse) {
+                const float kk2 = prm.kk[j + 1];
+                const CullPt ct = cull_pt_union<MODEL>(tr0, tr1, kk, cull, kk2, prm.cull[j + 1]);
+                RghAcc<MODEL> acc;
+                acc.zero();
+                vis = hit_pass<MODEL, true>(
+                    sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                    [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
+                    [&](const float4 h) {
+                        Rt += pair_r<MODEL>(h, tr0, tr1, kk);
+                        acc.add(h, tr0, tr1, kk2);
+                    },
+                    [&](const float4 a, const float4 b) {
+                        pair_r2<MODEL>(a, b, tr0, tr1, kk, Rt);
+                        acc.add2(a, b, tr0, tr1, kk2);
+                    });
+                acc.sums(S);
+                w_rgh += (unsigned long long)vis;
+            } else {
+                const CullPt ct = cull_pt<MODEL>(tr0, tr1, kk, cull);
+                vis = hit_pass<MODEL, true>(
+                    sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                    [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
+                    [&](const float4 h) { Rt += pair_r<MODEL>(h, tr0, tr1, kk); },
+                    [&](const float4 a, const float4 b) { pair_r2<MODEL>(a, b, tr0, tr1, kk, Rt); });
+            }
+            w_r += (unsigned long long)vis;
+            ++evals;
+            const float rt = warp_sum(Rt);
+            if (rt >= R + prm.c1 * t * slope) {
+                th0 = tr0;
+                th1 = tr1;
+                Rfin = rt;  // R at the accepted point, this update's bandwidth
+                pending = false;
+                if (hv == 0 && fuse) {
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) S[i] = warp_sum(S[i]);
+                    have = true;  // the next update's sums at the accepted point
+                }
+            } else {
+                t *= 0.5f;
+            }
+        }
+        if (pending) failed = true;
+    }
+    if (work && lane == 0) {
+        atomicAdd(work + RETINA_WORK_RGH, w_rgh);
+        atomicAdd(work + RETINA_WORK_R, w_r);
+    }
+    if (lane != 0) return;
+    const float hi0 = prm.box.lo0 + (float)prm.box.n0 * prm.box.step0;
+    const float hi1 = prm.box.lo1 + (float)prm.box.n1 * prm.box.step1;
+    uint8_t st;
+    if (!(isfinite(th0) && isfinite(th1) && isfinite(Rfin)))
+        st = 3;
+    else if (!(th0 >= prm.box.lo0 && th0 < hi0 && th1 >= prm.box.lo1 && th1 < hi1))
+        st = 2;
+    else
+        st = failed ? 1 : 0;
+    theta_out[0] = th0;
+    theta_out[1] = th1;
+    R_out[0] = Rfin;
+    status[0] = st;
+    if (n_evals) n_evals[0] = (uint8_t)(evals < 255 ? evals : 255);
+}
+
 // Algorithm 1 for the P seeds of one warp: q truncated-Newton updates
 // (gradient/Hessian pass, Newton-CG direction, step cap, Armijo backtracking
 // at bandwidth sigma_j), then R(theta_q; sigma_q), status and the number of
@@ -385,6 +520,11 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                              int n_live, const LsParams &prm, float *__restrict__ theta_out,
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
                                              uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work) {
+    if constexpr (P == 1) {
+        search_one<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, seeds, prm, theta_out, R_out,
+                          status, n_evals, work);
+        return;
+    }
     unsigned long long w_rgh = 0, w_r = 0;
     constexpr int NS = Model<MODEL>::NS;
     float th0[P], th1[P], Rfin[P];
