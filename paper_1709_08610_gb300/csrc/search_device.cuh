@@ -398,7 +398,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                                            float *__restrict__ theta_out, float *__restrict__ R_out,
                                            uint8_t *__restrict__ status, uint8_t *__restrict__ n_evals,
                                            unsigned long long *__restrict__ work) {
-    unsigned long long w_rgh = 0, w_r = 0;
+    uint32_t w_rgh = 0, w_r = 0;  // hits visited (fewer than 2^32 per seed)
     constexpr int NS = Model<MODEL>::NS;
     float th0 = seeds[0], th1 = seeds[1], Rfin = 0.f;
     int evals = 0;
@@ -419,7 +419,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
             acc.sums(S);
 #pragma unroll
             for (int i = 0; i < NS; ++i) S[i] = warp_sum(S[i]);
-            w_rgh += (unsigned long long)vis;
+            w_rgh += (uint32_t)vis;
         }
         have = false;
         float R, g0, g1, H00, H01, H11, pp0, pp1;
@@ -457,7 +457,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                         acc.add2(a, b, tr0, tr1, kk2);
                     });
                 acc.sums(S);
-                w_rgh += (unsigned long long)vis;
+                w_rgh += (uint32_t)vis;
             } else {
                 const CullPt ct = cull_pt<MODEL>(tr0, tr1, kk, cull);
                 vis = hit_pass<MODEL, true>(
@@ -466,7 +466,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                     [&](const float4 h) { Rt += pair_r<MODEL>(h, tr0, tr1, kk); },
                     [&](const float4 a, const float4 b) { pair_r2<MODEL>(a, b, tr0, tr1, kk, Rt); });
             }
-            w_r += (unsigned long long)vis;
+            w_r += (uint32_t)vis;
             ++evals;
             const float rt = warp_sum(Rt);
             if (rt >= R + prm.c1 * t * slope) {
@@ -486,8 +486,8 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         if (pending) failed = true;
     }
     if (work && lane == 0) {
-        atomicAdd(work + RETINA_WORK_RGH, w_rgh);
-        atomicAdd(work + RETINA_WORK_R, w_r);
+        atomicAdd(work + RETINA_WORK_RGH, (unsigned long long)w_rgh);
+        atomicAdd(work + RETINA_WORK_R, (unsigned long long)w_r);
     }
     if (lane != 0) return;
     const float hi0 = prm.box.lo0 + (float)prm.box.n0 * prm.box.step0;
