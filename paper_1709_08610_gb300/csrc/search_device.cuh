@@ -525,7 +525,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                           status, n_evals, work);
         return;
     }
-    unsigned long long w_rgh = 0, w_r = 0;
+    uint32_t w_rgh = 0, w_r = 0;  // (point, hit) pairs visited (fewer than 2^32 per group)
     constexpr int NS = Model<MODEL>::NS;
     float th0[P], th1[P], Rfin[P];
     int evals[P];
@@ -569,7 +569,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
         float S[P][NS];
 #pragma unroll
         for (int p = 0; p < P; ++p) acc[p].sums(S[p]);
-        w_rgh += (unsigned long long)vis * (unsigned long long)n_live;
+        w_rgh += (uint32_t)vis * (uint32_t)n_live;
         float R[P], g0[P], g1[P], pp0[P], pp1[P], slope[P], t[P];
         bool pending[P];
 #pragma unroll
@@ -626,7 +626,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             int n_pend = 0;
 #pragma unroll
             for (int p = 0; p < P; ++p) n_pend += pending[p] ? 1 : 0;
-            w_r += (unsigned long long)vis * (unsigned long long)n_pend;
+            w_r += (uint32_t)vis * (uint32_t)n_pend;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 if (!pending[p]) continue;
@@ -651,8 +651,8 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     // trial's response, or the response at the unmoved point - the same sum,
     // in the same order, that a separate evaluation would produce.
     if (work && lane == 0) {
-        atomicAdd(work + RETINA_WORK_RGH, w_rgh);
-        atomicAdd(work + RETINA_WORK_R, w_r);
+        atomicAdd(work + RETINA_WORK_RGH, (unsigned long long)w_rgh);
+        atomicAdd(work + RETINA_WORK_R, (unsigned long long)w_r);
     }
     const float hi0 = prm.box.lo0 + (float)prm.box.n0 * prm.box.step0;
     const float hi1 = prm.box.lo1 + (float)prm.box.n1 * prm.box.step1;
