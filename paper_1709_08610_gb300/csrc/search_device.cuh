@@ -460,7 +460,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                 w_rgh += (uint32_t)vis;
             } else {
                 const CullPt ct = cull_pt<MODEL>(tr0, tr1, kk, cull);
-                vis = hit_pass<MODEL, true>(
+                vis = hit_pass<MODEL, false>(
                     sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
                     [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
                     [&](const float4 h) { Rt += pair_r<MODEL>(h, tr0, tr1, kk); },
