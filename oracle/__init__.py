@@ -16,6 +16,9 @@ Functions and the passages they follow (arXiv:1709.08610):
   local maxima at or above R0.
 * :func:`local_search` - Algorithm 1 with the truncated Newton update and the
   annealed sigma schedule of Section 3.
+* :func:`refine_maxima` - step 4 of the grid algorithm (estimate the track
+  parameters of each selected cluster), read as Section 3's truncated-Newton
+  updates at the grid's bandwidth started from each maximum's cell centre.
 * :func:`extract_tracks` - the last two lines of Algorithm 1: cluster the
   converged points and keep the best of each cluster above R0.
 """
@@ -181,6 +184,31 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     lib().or_local_search(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
                           _ptr(th), _ptr(R), _ptr(st), _ptr(m))
     return th, R, st, m
+
+
+def maxima_centres(idx, lo, step, n) -> np.ndarray:
+    """Cell centres [m, 2] of grid maxima given as linear indices i1 * n0 + i0."""
+    idx = np.asarray(idx, dtype=np.int64).reshape(-1)
+    c0, c1 = cell_centres(lo, step, n)
+    return np.stack([c0[idx % int(n[0])], c1[idx // int(n[0])]], 1)
+
+
+def refine_maxima(hits, model: int, theta_c, sigma: float, lo, step, n, iters: int = 4,
+                  step_cap_cells: float = 1.0, c1: float = 1e-4, max_halvings: int = 8):
+    """Step 4 of the grid algorithm (Section 2): the track parameters of each
+    selected cluster, estimated from its maximum's cell centre theta_c [m, 2]
+    by ``iters`` truncated-Newton updates of Section 3 (Newton-CG direction,
+    step capped to step_cap_cells, Armijo backtracking) at the grid's own
+    bandwidth ``sigma``.  The updates are Algorithm 1's, so this is
+    :func:`local_search` with the constant schedule (sigma,) * iters started
+    from the centres; lo / step / n are the grid the maxima come from.
+
+    Returns (theta [m, 2] float64, R [m] at sigma, status [m] uint8, margin [m]).
+    """
+    if not 1 <= iters <= 8:
+        raise ValueError("1 <= iters <= 8")
+    return local_search(hits, model, np.asarray(theta_c, dtype=np.float32).reshape(-1, 2), [float(sigma)] * iters,
+                        lo, step, n, c1=c1, max_halvings=max_halvings, step_cap_cells=step_cap_cells)
 
 
 def extract_tracks(theta, R, status, lo, step, n, R0: float, merge_cells: float = 2.0) -> np.ndarray:

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from synth import WORKLOADS, make_event, make_toy2d_event, close_tracks_event, uniform_seeds
+from synth.events import TOY_PLANES_X
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")))
 E1, E4 = math.exp(-1.0), math.exp(-4.0)
@@ -348,6 +349,117 @@ def test_grid_maxima_near_search_maxima():
     assert np.all(st <= 1)
     assert np.mean(d <= 1.0) >= 0.9
     assert np.all(Rs >= R.reshape(-1)[idx] * (1 - 1e-12))
+
+
+# --------------------------------------------------------------------------
+# Step 4 of the grid algorithm: parameter estimates refined from the maxima
+# --------------------------------------------------------------------------
+
+def _noiseless_track(model, offset_cells):
+    """Hits exactly on one track whose parameters sit offset_cells from the
+    centre of grid cell (37, 21) of a 64 x 64 window; returns (hits, truth,
+    lo, step, n, sigma)."""
+    if model == 1:
+        wl = WORKLOADS["velo"]
+        zs = np.array([-300.0 + 42.0 * p for p in range(26)])
+    else:
+        wl = WORKLOADS["toy2d"]
+        zs = np.asarray(TOY_PLANES_X, dtype=np.float64)
+    step = np.asarray(wl.grid_step)
+    lo = np.array([wl.grid_lo[0] + 400 * step[0], wl.grid_lo[1] + 40 * step[1]]) if model == 1 else \
+        np.array([wl.grid_lo[0] + 70 * step[0], wl.grid_lo[1] + 60 * step[1]])
+    n = (64, 64)
+    t = lo + (np.array([37, 21]) + 0.5 + np.asarray(offset_cells)) * step
+    if model == 1:
+        hits = np.stack([t[0] * zs, t[1] * zs, zs, 0 * zs], 1).astype(np.float32)
+    else:
+        hits = np.stack([zs, t[0] * zs + t[1], 0 * zs, 0 * zs], 1).astype(np.float32)
+    return hits, t, lo, step, n, wl.sigma_grid
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("offset", [(0.3, -0.22), (-0.41, 0.12), (0.0, 0.0)])
+def test_refinement_recovers_noiseless_track_exactly(model, offset):
+    # All hits on one track: R is largest, and equals the number of hits, at
+    # the track's parameters (Eq. 1 with s = 0 for every hit).  Slope model:
+    # the grid's only maximum is the cell holding the track, offset from its
+    # centre by the chosen fraction of a cell.  2D toy: the peak is a ridge
+    # (the planes are all at x > 0), on which the grid can have several
+    # discrete maxima; the highest is refined.  The refined estimate lands on
+    # the track to the float32 rounding of the hits, with R = N.
+    hits, t, lo, step, n, sigma = _noiseless_track(model, offset)
+    N = hits.shape[0]
+    R = oracle.grid_response(hits, model, lo, step, n, sigma)
+    idx = oracle.grid_maxima(R, 0.5 * N)
+    if model == 1:
+        assert list(idx) == [21 * n[0] + 37]
+    idx = idx[[int(np.argmax(R.reshape(-1)[idx]))]]
+    c = oracle.maxima_centres(idx, lo, step, n)
+    if model == 1:
+        np.testing.assert_allclose((t - c[0]) / step, offset, atol=1e-9)
+    iters = 4 if model == 1 else 8
+    th, Rr, st, m = oracle.refine_maxima(hits, model, c, sigma, lo, step, n, iters=iters)
+    assert st[0] == 0
+    assert np.max(np.abs(th[0] - t)) <= 1e-8
+    assert Rr[0] == pytest.approx(N, rel=1e-8)
+    if np.any(c[0] != t):
+        assert Rr[0] > R.reshape(-1)[idx[0]]
+
+
+def test_refinement_never_lowers_R_and_respects_the_cap():
+    # Every update accepts only an Armijo increase (or stays): R at the
+    # refined point >= R at the cell centre; each of the iters steps is at most
+    # step_cap_cells cells in the infinity norm.
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 5, 1, vertex_sigma=(0, 0, 0))
+    lo = (wl.grid_lo[0] + 448 * wl.grid_step[0], wl.grid_lo[1] + 448 * wl.grid_step[1])
+    n = (128, 128)
+    R = oracle.grid_response(ev.hits, 1, lo, wl.grid_step, n, wl.sigma_grid)
+    idx = oracle.grid_maxima(R, wl.R0)
+    assert len(idx) >= 3
+    c = oracle.maxima_centres(idx, lo, wl.grid_step, n)
+    for iters, cap in ((1, 0.25), (3, 0.5), (4, 1.0)):
+        th, Rr, st, m = oracle.refine_maxima(ev.hits, 1, c, wl.sigma_grid, lo, wl.grid_step, n, iters=iters,
+                                             step_cap_cells=cap)
+        assert np.all(st <= 2)
+        assert np.all(Rr >= R.reshape(-1)[idx] * (1 - 1e-12))
+        d = np.max(np.abs(th - c) / np.asarray(wl.grid_step), axis=1)
+        assert np.all(d <= iters * cap * (1 + 1e-9)), d
+
+
+def test_refined_maxima_agree_with_brute_force_fine_grid():
+    # On a noisy event, each refined estimate that is a converged maximum
+    # (negative-definite Hessian) is where R peaks on a fine grid of 1/32
+    # cell around it, and R there is not exceeded by any fine-grid point.
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 3, 0, vertex_sigma=(0, 0, 0))
+    tr = ev.truth[np.argsort(np.abs(ev.truth[:, 0]) + np.abs(ev.truth[:, 1]))[0], :2]
+    i0 = int(np.floor((tr[0] - wl.grid_lo[0]) / wl.grid_step[0])) - 32
+    i1 = int(np.floor((tr[1] - wl.grid_lo[1]) / wl.grid_step[1])) - 32
+    step = np.asarray(wl.grid_step)
+    lo = (wl.grid_lo[0] + i0 * step[0], wl.grid_lo[1] + i1 * step[1])
+    n = (64, 64)
+    R = oracle.grid_response(ev.hits, 1, lo, step, n, wl.sigma_grid)
+    idx = oracle.grid_maxima(R, wl.R0)
+    c = oracle.maxima_centres(idx, lo, step, n)
+    th, Rr, st, m = oracle.refine_maxima(ev.hits, 1, c, wl.sigma_grid, lo, step, n, iters=4)
+    fine = step / 32
+    n_conv = 0
+    for k in range(len(idx)):
+        o = oracle.rgh(ev.hits, 1, th[k], wl.sigma_grid)
+        if st[k] != 0 or not np.all(np.linalg.eigvalsh(o["hess"]) < 0):
+            continue
+        n_conv += 1
+        flo = (th[k][0] - 32.5 * fine[0], th[k][1] - 32.5 * fine[1])
+        Rf = oracle.grid_response(ev.hits, 1, flo, fine, (65, 65), wl.sigma_grid)
+        j1, j0 = np.unravel_index(np.argmax(Rf), Rf.shape)
+        best = np.array([flo[0] + (j0 + 0.5) * fine[0], flo[1] + (j1 + 0.5) * fine[1]])
+        assert np.all(np.abs(best - th[k]) <= fine * (1 + 1e-9)), (k, (best - th[k]) / fine)
+        assert Rf.max() <= Rr[k] * (1 + 1e-9)
+    assert n_conv >= 10
+    # the estimate of the chosen track is closer to it than its cell centre
+    k = int(np.argmin(np.max(np.abs(c - tr) / step, axis=1)))
+    assert np.max(np.abs(th[k] - tr)) < np.max(np.abs(c[k] - tr))
 
 
 def test_figure2_close_tracks_split_and_merge():
