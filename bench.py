@@ -298,14 +298,17 @@ BATCH_RUN_SEED = 5000
 
 def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: int = 512, reps: int = 5):
     """1024 ragged VELO-like events with the vertex at the origin through three
-    methods, each replayed as one CUDA graph per batch: the plain grid scan,
-    Algorithm 1 from 4096 uniform seeds per event (and from as many uniform
-    seeds as the learned variant uses) and from the learned proposer's seeds.
-    Events/s from CUDA events around graph replays (L2 flushed before each),
-    MC-truth efficiency (|dtheta|_max <= 1e-3), fakes per event, and the share
-    of the plain 4096-seed search's tracks each method recovers."""
+    methods, each replayed as one CUDA graph per batch: the plain grid scan
+    (with and without the refinement of its maxima), Algorithm 1 from 4096
+    uniform seeds per event (and from as many uniform seeds as the learned
+    variant uses) and from the learned proposer's seeds.  Events/s from CUDA
+    events around graph replays (L2 flushed before each), MC-truth efficiency
+    (|dtheta|_max <= 1e-3), fakes per event, the resolution of the matched
+    tracks (|dtheta| per axis in grid cells) and the share of the plain
+    4096-seed search's tracks each method recovers."""
     import torch
-    from paper_1709_08610_gb300.pipeline import BatchTracker, GridScanBatch, match_efficiency, recovered_fraction
+    from paper_1709_08610_gb300.pipeline import (BatchTracker, GridScanBatch, match_efficiency, match_residuals,
+                                                 recovered_fraction)
     from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, SeedProposer
     wl = WORKLOADS[workload]
     E = BATCH_EVENTS
@@ -338,6 +341,8 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
     # ~16 % over one unordered seed per warp, more on high-multiplicity events)
     shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
     runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
+            ("grid_scan_%dx%d_refined" % (n0, n1),
+             lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0, refine_iters=4), None),
             ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0, **shape),
              np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),
             ("uniform_%d" % learned_k, lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, **shape),
@@ -353,9 +358,12 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         ms = timed(obj)
         found[name] = obj.results()
         eff, fakes = match_efficiency(found[name], truth)
+        res = match_residuals(found[name], truth) / np.asarray(wl.grid_step)
         methods[name] = {"events_per_s": E / (ms * 1e-3), "ms_per_batch": ms, "efficiency": eff,
-                         "fakes_per_event": fakes / E}
-        if isinstance(obj, GridScanBatch):
+                         "fakes_per_event": fakes / E,
+                         "resolution_cells": {"rms": float(np.sqrt(np.mean(res ** 2))) if res.size else None,
+                                              "median": float(np.median(res)) if res.size else None}}
+        if isinstance(obj, GridScanBatch) and obj.ropts is None:
             # the grid scan alone (response + maxima, eager, after the hit ordering), with
             # its evaluated (cell, hit) pairs counted on the device: 2 flops per pair
             obj.step()

@@ -334,6 +334,50 @@ int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_
                         float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, void *stream);
 
 /*
+ * retina_refine_maxima - track parameters of each grid cluster, refined from
+ * its maximum.
+ *
+ * Paper: Section 2, step 4 of the grid algorithm (for each selected cluster,
+ * estimate the track parameters).  The estimate starts from the cluster's
+ * maximum - its cell centre, as retina_grid_scan / retina_grid_maxima write
+ * it in max_theta - and takes opts->q truncated-Newton updates of Section 3,
+ * exactly the update of retina_local_search (steps 1-4 there), so each
+ * point's result is bitwise what retina_local_search gives for the same
+ * start, opts and box.  The reading behind the defaults of the bindings:
+ * opts->sigma[j] = the grid's own bandwidth for every j, q = 4 updates, each
+ * step capped to 1 cell; at that bandwidth the peak is about one cell wide
+ * and Newton converges from anywhere inside the cell.  Scheduling is
+ * retina_batched_search's (one persistent launch; its RETINA_OPT_BATCH_*
+ * options set the launch shape), with each event's points taken from a row
+ * of theta_c instead of a ragged array.
+ *
+ *   theta_c   : float32 [n_events][K][2] starting points (the maxima's cell
+ *               centres); only the first min(n_max[e], K) rows of event e are
+ *               read (n_max[e] may exceed K, as the grid entry points write
+ *               it; negative counts as 0).
+ *   n_max     : int32 [n_events], device.
+ *   opts, box : host pointers, as in retina_local_search; box is the grid
+ *               the maxima come from (step cap in its cells, status 2).
+ *   theta_out : float32 [n_events][K][2];  R_out: float32 [n_events][K]
+ *               (response at opts->sigma[q-1]);  status: uint8 [n_events][K]
+ *               with retina_local_search's codes.  Only the rows that are
+ *               read are written; the others keep their contents.  Outputs
+ *               must not overlap theta_c.
+ *   boxes     : nullable block boxes from retina_prepare_hits (exact
+ *               skipping, as in retina_local_search).
+ *   ws        : device workspace of retina_refine_maxima_workspace_size bytes
+ *               (256-byte aligned), used as retina_batched_search uses its own.
+ * Returns RETINA_EINVAL for bad sizes, options or null pointers,
+ * RETINA_ENOSPACE for a short workspace (nothing launched in either case);
+ * n_events == 0 or K == 0 is a no-op.
+ */
+int retina_refine_maxima_workspace_size(int32_t n_events, size_t *bytes);
+int retina_refine_maxima(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes,
+                         int32_t n_events, int32_t model, const float *theta_c, const int32_t *n_max, int32_t K,
+                         const retina_ls_opts *opts, const retina_grid *box, float *theta_out, float *R_out,
+                         uint8_t *status, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * retina_batched_search - Algorithm 1 over a ragged batch, one persistent launch.
  *
  * Paper: Algorithm 1 with the Section 3 update, exactly as retina_local_search

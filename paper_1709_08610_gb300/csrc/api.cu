@@ -262,18 +262,21 @@ int retina_response(const float *hits, int64_t n_hits, const int64_t *event_offs
                                        sigma, want_derivs != 0, out, (cudaStream_t)stream));
 }
 
+static bool valid_ls_opts(const retina_ls_opts *opts) {
+    if (!opts || opts->q < 1 || opts->q > RETINA_MAX_Q) return false;
+    for (int j = 0; j < opts->q; ++j)
+        if (!finite_pos(opts->sigma[j])) return false;
+    if (!(opts->c1 >= 0.f && opts->c1 < 1.f)) return false;
+    if (opts->max_halvings < 0 || opts->max_halvings > 30) return false;
+    return opts->step_cap_cells > 0.f;
+}
+
 int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes, int32_t n_events,
                         int32_t model, const float *seeds, int32_t n_seeds, const retina_ls_opts *opts,
                         const retina_grid *box, float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals,
                         void *stream) {
-    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !opts || !valid_grid(box)) return RETINA_EINVAL;
+    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !valid_ls_opts(opts) || !valid_grid(box)) return RETINA_EINVAL;
     if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
-    if (opts->q < 1 || opts->q > RETINA_MAX_Q) return RETINA_EINVAL;
-    for (int j = 0; j < opts->q; ++j)
-        if (!finite_pos(opts->sigma[j])) return RETINA_EINVAL;
-    if (!(opts->c1 >= 0.f && opts->c1 < 1.f)) return RETINA_EINVAL;
-    if (opts->max_halvings < 0 || opts->max_halvings > 30) return RETINA_EINVAL;
-    if (!(opts->step_cap_cells > 0.f)) return RETINA_EINVAL;
     if (n_events > 65535) return RETINA_EINVAL;
     if (n_events == 0 || n_seeds == 0) return RETINA_OK;
     if (!event_offsets || !seeds || !theta_out || !R_out || !status) return RETINA_EINVAL;
@@ -283,6 +286,31 @@ int retina_local_search(const float *hits, int64_t n_hits, const int64_t *event_
                                            n_events, model, seeds,
                                            n_seeds, opts, box, theta_out, R_out, status, n_evals, g_opt_seeds_per_warp,
                                            g_opt_ls_warps, g_opt_smem_hits, (cudaStream_t)stream));
+}
+
+int retina_refine_maxima_workspace_size(int32_t n_events, size_t *bytes) {
+    if (!bytes || n_events < 0) return RETINA_EINVAL;
+    *bytes = batched_ws_bytes(n_events);
+    return RETINA_OK;
+}
+
+int retina_refine_maxima(const float *hits, int64_t n_hits, const int64_t *event_offsets, const float *boxes,
+                         int32_t n_events, int32_t model, const float *theta_c, const int32_t *n_max, int32_t K,
+                         const retina_ls_opts *opts, const retina_grid *box, float *theta_out, float *R_out,
+                         uint8_t *status, void *ws, size_t ws_bytes, void *stream) {
+    if (n_events < 0 || K < 0 || n_hits < 0 || !valid_ls_opts(opts) || !valid_grid(box)) return RETINA_EINVAL;
+    if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
+    if (n_events > 65535) return RETINA_EINVAL;
+    if (n_events == 0 || K == 0) return RETINA_OK;
+    if (!event_offsets || !theta_c || !n_max || !theta_out || !R_out || !status) return RETINA_EINVAL;
+    if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
+    if (boxes && !aligned16(boxes)) return RETINA_EINVAL;
+    if (ws_bytes < batched_ws_bytes(n_events)) return RETINA_ENOSPACE;
+    if (!ws || ((uintptr_t)ws & 255u)) return RETINA_EINVAL;
+    return cuda_status(launch_refine_maxima((const float4 *)hits, n_hits, event_offsets, (const float4 *)boxes,
+                                            n_events, model, theta_c, n_max, K, opts, box, theta_out, R_out, status,
+                                            (int32_t *)ws, g_opt_batch_spw, g_opt_batch_warps, g_opt_batch_smem_hits,
+                                            g_opt_batch_ctas, (cudaStream_t)stream));
 }
 
 int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes) {
@@ -295,14 +323,8 @@ int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *even
                           int32_t model, const float *seeds, int64_t n_seeds, const int64_t *seed_offsets,
                           const int32_t *order, const retina_ls_opts *opts, const retina_grid *box, float *theta_out,
                           float *R_out, uint8_t *status, uint8_t *n_evals, void *ws, size_t ws_bytes, void *stream) {
-    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !opts || !valid_grid(box)) return RETINA_EINVAL;
+    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !valid_ls_opts(opts) || !valid_grid(box)) return RETINA_EINVAL;
     if (model != RETINA_TOY2D && model != RETINA_VELO_SLOPES) return RETINA_EINVAL;
-    if (opts->q < 1 || opts->q > RETINA_MAX_Q) return RETINA_EINVAL;
-    for (int j = 0; j < opts->q; ++j)
-        if (!finite_pos(opts->sigma[j])) return RETINA_EINVAL;
-    if (!(opts->c1 >= 0.f && opts->c1 < 1.f)) return RETINA_EINVAL;
-    if (opts->max_halvings < 0 || opts->max_halvings > 30) return RETINA_EINVAL;
-    if (!(opts->step_cap_cells > 0.f)) return RETINA_EINVAL;
     if (n_seeds > (int64_t)INT32_MAX) return RETINA_EINVAL;
     if (n_events == 0 || n_seeds == 0) return RETINA_OK;
     if (!event_offsets || !seed_offsets || !seeds || !theta_out || !R_out || !status) return RETINA_EINVAL;

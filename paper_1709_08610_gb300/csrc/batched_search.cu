@@ -12,6 +12,10 @@
 // CTA, and every loop is bounded by the number of events and seeds.  The
 // counters live in the caller's workspace and are zeroed by an async memset
 // on the same stream before the launch.
+//
+// The same kernel refines grid maxima (step 4 of the grid algorithm): the
+// starting points are then rows of a [n_events][stride] array with a count
+// per event, instead of a ragged array with offsets.
 #include "search_device.cuh"
 
 namespace retina {
@@ -34,10 +38,20 @@ struct BatchArgs {
     uint8_t *n_evals;
     int32_t *counters;  // [0] event ticket, [1] overrun flag, [2 + e] group counter of event e
     unsigned long long *work;
+    const int32_t *seed_count;  // non-null: event e's seeds are e * seed_stride + [0, seed_count[e])
+    int64_t seed_stride;
 };
 
 __device__ __forceinline__ void seed_range(const BatchArgs &a, int e, int64_t &s0, int64_t &s1) {
-    int64_t x = a.seed_off[e], y = a.seed_off[e + 1];
+    int64_t x, y;
+    if (a.seed_count) {
+        const int64_t c = a.seed_count[e];
+        x = (int64_t)e * a.seed_stride;
+        y = x + (c < 0 ? 0 : (c > a.seed_stride ? a.seed_stride : c));
+    } else {
+        x = a.seed_off[e];
+        y = a.seed_off[e + 1];
+    }
     x = x < 0 ? 0 : (x > a.n_seeds ? a.n_seeds : x);
     y = y < x ? x : (y > a.n_seeds ? a.n_seeds : y);
     s0 = x;
@@ -156,18 +170,14 @@ static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParam
     return launch_batched_t<MODEL, P, 8>(a, prm, ctas, st);
 }
 
-cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
-                                  int n_events, int model,
-                                  const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
-                                  const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
-                                  uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
-                                  int smem_hits, int ctas, cudaStream_t st) {
+static cudaError_t launch_batched(BatchArgs &a, int model, const retina_ls_opts *o, const retina_grid *box,
+                                  int seeds_per_warp, int warps, int ctas, cudaStream_t st) {
     LsParams prm = make_ls_params(o, box);
-    if (smem_hits < 0) smem_hits = 0;
-    if (smem_hits > 12288) smem_hits = 12288;
-    BatchArgs a{hits, n_hits, hit_off, boxes, n_events, seeds, n_seeds, seed_off, order, smem_hits,
-                (int64_t)n_events + n_seeds + 2, theta_out, R_out, status, n_evals, counters, work_counters()};
-    cudaError_t err = cudaMemsetAsync(counters, 0, batched_ws_bytes(n_events), st);
+    if (a.smem_hits < 0) a.smem_hits = 0;
+    if (a.smem_hits > 12288) a.smem_hits = 12288;
+    a.max_rounds = (int64_t)a.n_events + a.n_seeds + 2;
+    a.work = work_counters();
+    cudaError_t err = cudaMemsetAsync(a.counters, 0, batched_ws_bytes(a.n_events), st);
     if (err != cudaSuccess) return err;
 #define RETINA_BATCH_CASE(M, PP) return launch_batched_w<M, PP>(warps, a, prm, ctas, st)
     if (model == RETINA_VELO_SLOPES) {
@@ -180,6 +190,27 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
         RETINA_BATCH_CASE(RETINA_TOY2D, 1);
     }
 #undef RETINA_BATCH_CASE
+}
+
+cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
+                                  int n_events, int model,
+                                  const float *seeds, int64_t n_seeds, const int64_t *seed_off, const int32_t *order,
+                                  const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
+                                  uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
+                                  int smem_hits, int ctas, cudaStream_t st) {
+    BatchArgs a{hits, n_hits, hit_off, boxes, n_events, seeds, n_seeds, seed_off, order, smem_hits, 0,
+                theta_out, R_out, status, n_evals, counters, nullptr, nullptr, 0};
+    return launch_batched(a, model, o, box, seeds_per_warp, warps, ctas, st);
+}
+
+cudaError_t launch_refine_maxima(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
+                                 int n_events, int model, const float *theta_c, const int32_t *n_max, int K,
+                                 const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
+                                 uint8_t *status, int32_t *counters, int seeds_per_warp, int warps, int smem_hits,
+                                 int ctas, cudaStream_t st) {
+    BatchArgs a{hits, n_hits, hit_off, boxes, n_events, theta_c, (int64_t)n_events * K, nullptr, nullptr, smem_hits,
+                0, theta_out, R_out, status, nullptr, counters, nullptr, n_max, (int64_t)K};
+    return launch_batched(a, model, o, box, seeds_per_warp, warps, ctas, st);
 }
 
 }  // namespace retina

@@ -43,6 +43,11 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
                                   const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
                                   uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
                                   int smem_hits, int ctas, cudaStream_t st);
+cudaError_t launch_refine_maxima(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
+                                 int n_events, int model, const float *theta_c, const int32_t *n_max, int K,
+                                 const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
+                                 uint8_t *status, int32_t *counters, int seeds_per_warp, int warps, int smem_hits,
+                                 int ctas, cudaStream_t st);
 size_t batched_ws_bytes(int n_events);
 int64_t prepared_box_count(int64_t n_hits, int n_events);
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,

@@ -118,15 +118,20 @@ class BatchTracker:
 
 class GridScanBatch:
     """The plain grid method over a batch: spatial ordering, Eq. 2 on the grid,
-    strict local maxima above R0, cluster + select; graph-capturable like
-    BatchTracker (the response grids live in the workspace)."""
+    strict local maxima above R0, optionally the refinement of each maximum
+    (step 4: ``refine_iters`` truncated-Newton updates at the grid's
+    bandwidth, each capped to ``refine_cap_cells``), cluster + select;
+    graph-capturable like BatchTracker (the response grids live in the
+    workspace)."""
 
     def __init__(self, n_events: int, hit_capacity: int, grid: "rt.Grid", sigma: float, R0: float,
                  merge_cells: float = 2.0, max_maxima: int = 4096, max_tracks: int = 1024,
-                 model: int = rt.VELO_SLOPES, device="cuda"):
+                 model: int = rt.VELO_SLOPES, refine_iters: int = 0, refine_cap_cells: float = 1.0,
+                 device="cuda"):
         E, H = int(n_events), int(hit_capacity)
         self.E, self.H, self.grid, self.sigma, self.R0, self.merge = E, H, grid, float(sigma), float(R0), float(merge_cells)
         self.model, self.Km, self.K = model, int(max_maxima), int(max_tracks)
+        self.ropts = rt.refine_opts(self.sigma, refine_iters, refine_cap_cells) if refine_iters > 0 else None
         dev = torch.device(device)
         f32 = dict(dtype=torch.float32, device=dev)
         self.hits = torch.zeros((H, 4), **f32)
@@ -137,6 +142,11 @@ class GridScanBatch:
                            max_theta=torch.empty((E, self.Km, 2), **f32), max_R=torch.empty((E, self.Km), **f32),
                            n_max=torch.empty((E,), dtype=torch.int32, device=dev), R=None)
         self.ws = torch.empty(max(rt.grid_scan_workspace_size(E, model, grid), 1), dtype=torch.uint8, device=dev)
+        self.refined = None if self.ropts is None else (
+            torch.empty((E, self.Km, 2), **f32), torch.empty((E, self.Km), **f32),
+            torch.empty((E, self.Km), dtype=torch.uint8, device=dev))
+        self.refine_ws = None if self.ropts is None else \
+            torch.empty(max(rt.refine_maxima_workspace_size(E), 256), dtype=torch.uint8, device=dev)
         self.tracks = dict(tracks=torch.empty((E, self.K, 2), **f32), track_R=torch.empty((E, self.K), **f32),
                            track_src=torch.empty((E, self.K), dtype=torch.int32, device=dev),
                            n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
@@ -148,8 +158,15 @@ class GridScanBatch:
         rt.prepare_hits(self.hits, self.offsets, self.model, out=(self.sorted, self.boxes), stream=stream)
         rt.grid_scan(self.sorted, self.offsets, self.model, self.grid, self.sigma, self.R0, self.Km, ws=self.ws,
                      out=self.maxima, boxes=self.boxes, stream=stream)
-        rt.extract_tracks(self.maxima["max_theta"], self.maxima["max_R"], None, self.grid, self.R0, self.merge,
-                          self.K, n_valid=self.maxima["n_max"], out=self.tracks, stream=stream)
+        m = self.maxima
+        if self.ropts is None:
+            th, R, st = m["max_theta"], m["max_R"], None
+        else:
+            th, R, st = rt.refine_maxima(self.sorted, self.offsets, self.model, m["max_theta"], m["n_max"],
+                                         self.ropts, self.grid, out=self.refined, ws=self.refine_ws,
+                                         boxes=self.boxes, stream=stream)
+        rt.extract_tracks(th, R, st, self.grid, self.R0, self.merge, self.K, n_valid=m["n_max"], out=self.tracks,
+                          stream=stream)
 
     capture = BatchTracker.capture
     replay = BatchTracker.replay
@@ -171,6 +188,22 @@ def match_efficiency(found, truth, eps: float = 1e-3):
         n_hit += int((d <= eps).any(0).sum())
         n_fake += int((~(d <= eps).any(1)).sum())
     return (n_hit / max(n_truth, 1)), n_fake
+
+
+def match_residuals(found, truth, eps: float = 1e-3) -> np.ndarray:
+    """|found - truth| per axis [n, 2] of every truth track's nearest found
+    track (max norm), for the truth tracks matched within eps."""
+    out = []
+    for f, t in zip(found, truth):
+        t = np.asarray(t, dtype=np.float64).reshape(-1, 2)
+        f = np.asarray(f, dtype=np.float64).reshape(-1, 2)
+        if len(f) == 0 or len(t) == 0:
+            continue
+        d = np.abs(f[:, None, :] - t[None, :, :])
+        j = d.max(-1).argmin(0)
+        near = d[j, np.arange(len(t))]
+        out.append(near[near.max(-1) <= eps])
+    return np.concatenate(out) if out else np.zeros((0, 2))
 
 
 def recovered_fraction(found, reference, eps: float = 1e-3):

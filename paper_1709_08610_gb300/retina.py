@@ -114,6 +114,8 @@ def _load():
     L.retina_grid_maxima.argtypes = [P, I32, P, F, P, P, P, P, I32, P, SZ, P]
     L.retina_response.argtypes = [P, I64, P, I32, I32, P, I32, F, I32, P, P]
     L.retina_local_search.argtypes = [P, I64, P, P, I32, I32, P, I32, P, P, P, P, P, P, P]
+    L.retina_refine_maxima_workspace_size.argtypes = [I32, P]
+    L.retina_refine_maxima.argtypes = [P, I64, P, P, I32, I32, P, P, I32, P, P, P, P, P, P, SZ, P]
     L.retina_extract_tracks.argtypes = [P, P, P, P, I32, I32, P, F, F, P, P, P, P, I32, P]
     L.retina_grid_response_workspace_size.argtypes = [I32, I32, P, I32, P]
     L.retina_grid_response.argtypes = [P, I64, P, P, I32, I32, P, F, I32, P, P, SZ, P]
@@ -337,6 +339,49 @@ def response(hits: torch.Tensor, offsets: torch.Tensor, model: int, theta: torch
     out = torch.zeros((E, P, 6), dtype=torch.float32, device=hits.device)
     _check("retina_response", lib.retina_response(_p(hits), hits.shape[0], _p(offsets), E, model, _p(theta), P,
                                                   float(sigma), int(want_derivs), _p(out), _stream(stream)))
+    return out
+
+
+def refine_opts(sigma_grid: float, iters: int = 4, step_cap_cells: float = 1.0) -> LsOpts:
+    """Options of the grid-maximum refinement: ``iters`` updates at the grid's
+    own bandwidth, each step capped to ``step_cap_cells`` cells."""
+    return LsOpts(sigma=(float(sigma_grid),) * int(iters), step_cap_cells=float(step_cap_cells))
+
+
+def refine_maxima_workspace_size(n_events: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check("retina_refine_maxima_workspace_size", lib.retina_refine_maxima_workspace_size(n_events, ctypes.byref(b)))
+    return b.value
+
+
+def refine_maxima(hits: torch.Tensor, offsets: torch.Tensor, model: int, theta_c: torch.Tensor,
+                  n_max: torch.Tensor, opts: LsOpts, box: Grid, out=None, ws: Optional[torch.Tensor] = None,
+                  boxes: Optional[torch.Tensor] = None, stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+    """Step 4 of the grid algorithm: the first min(n_max[e], K) points of
+    theta_c [E, K, 2] refined by opts' truncated-Newton updates; returns
+    (theta [E, K, 2], R [E, K], status [E, K] uint8), rows past the count
+    untouched."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    _dev(theta_c, torch.float32, "theta_c", 2)
+    _dev(n_max, torch.int32, "n_max")
+    E = offsets.numel() - 1
+    K = theta_c.shape[-2]
+    if theta_c.numel() != E * K * 2 or n_max.numel() != E:
+        raise ValueError("theta_c must be [E, K, 2] and n_max [E]")
+    dev = hits.device
+    if out is None:
+        out = (torch.empty((E, K, 2), dtype=torch.float32, device=dev),
+               torch.empty((E, K), dtype=torch.float32, device=dev),
+               torch.empty((E, K), dtype=torch.uint8, device=dev))
+    need = refine_maxima_workspace_size(E)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    o = opts.c()
+    g = box.c()
+    _check("retina_refine_maxima", lib.retina_refine_maxima(
+        _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, _p(theta_c), _p(n_max), K, ctypes.byref(o),
+        ctypes.byref(g), _p(out[0]), _p(out[1]), _p(out[2]), _p(ws), ws.numel(), _stream(stream)))
     return out
 
 

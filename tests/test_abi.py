@@ -13,6 +13,7 @@ from paper_1709_08610_gb300 import retina as rt  # noqa: E402
 EINVAL, ENOSPACE = 1, 3
 L = rt.lib
 BOGUS = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails validation first
+WS = ctypes.c_void_p(0x2000)  # a 256-byte-aligned bogus workspace, equally never dereferenced
 
 
 def test_exports_every_declared_function():
@@ -130,6 +131,57 @@ def test_local_search_rejects_null_outputs_and_empty_is_ok():
                                  None, None) == 0
     assert L.retina_local_search(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, 0, ctypes.byref(o), ctypes.byref(g), None, None,
                                  None, None, None) == 0
+
+
+@pytest.mark.parametrize("mut", ["q0", "sigmanan", "c1one", "cap0", "K", "events", "model", "misaligned"])
+def test_refine_maxima_rejects(mut):
+    o = _opts()
+    g = _grid()
+    args = dict(hits=BOGUS, n_hits=10, E=1, model=1, K=16)
+    if mut == "q0":
+        o.q = 0
+    elif mut == "sigmanan":
+        o.sigma[0] = float("nan")
+    elif mut == "c1one":
+        o.c1 = 1.0
+    elif mut == "cap0":
+        o.step_cap_cells = 0.0
+    elif mut == "K":
+        args["K"] = -1
+    elif mut == "events":
+        args["E"] = 65536
+    elif mut == "model":
+        args["model"] = 7
+    elif mut == "misaligned":
+        args["hits"] = ctypes.c_void_p(0x1004)
+    rc = L.retina_refine_maxima(args["hits"], args["n_hits"], BOGUS, None, args["E"], args["model"], BOGUS, BOGUS,
+                                args["K"], ctypes.byref(o), ctypes.byref(g), BOGUS, BOGUS, BOGUS, WS, 1 << 20, None)
+    assert rc == EINVAL
+
+
+def test_refine_maxima_rejects_null_pointers_and_empty_is_ok():
+    o = _opts()
+    g = _grid()
+    for k in range(6):
+        ptrs = [BOGUS] * 5 + [WS]
+        ptrs[k] = None  # theta_c, n_max, theta_out, R_out, status, workspace
+        assert L.retina_refine_maxima(BOGUS, 10, BOGUS, None, 1, 1, ptrs[0], ptrs[1], 16, ctypes.byref(o),
+                                      ctypes.byref(g), ptrs[2], ptrs[3], ptrs[4], ptrs[5], 1 << 20, None) == EINVAL
+    assert L.retina_refine_maxima(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, BOGUS, 16, None, ctypes.byref(g), BOGUS,
+                                  BOGUS, BOGUS, WS, 1 << 20, None) == EINVAL
+    # misaligned or short workspace
+    assert L.retina_refine_maxima(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, BOGUS, 16, ctypes.byref(o), ctypes.byref(g),
+                                  BOGUS, BOGUS, BOGUS, ctypes.c_void_p(0x2010), 1 << 20, None) == EINVAL
+    need = ctypes.c_size_t(0)
+    assert L.retina_refine_maxima_workspace_size(3, ctypes.byref(need)) == 0 and need.value >= 5 * 4
+    assert L.retina_refine_maxima(BOGUS, 10, BOGUS, None, 3, 1, BOGUS, BOGUS, 16, ctypes.byref(o), ctypes.byref(g),
+                                  BOGUS, BOGUS, BOGUS, WS, need.value - 1, None) == ENOSPACE
+    assert L.retina_refine_maxima_workspace_size(-1, ctypes.byref(need)) == EINVAL
+    # zero events or K = 0: nothing to do, nothing launched
+    assert L.retina_refine_maxima(None, 0, None, None, 0, 1, None, None, 16, ctypes.byref(o), ctypes.byref(g), None,
+                                  None, None, None, 0, None) == 0
+    assert L.retina_refine_maxima(BOGUS, 10, BOGUS, None, 1, 1, None, None, 0, ctypes.byref(o), ctypes.byref(g), None,
+                                  None, None, None, 0, None) == 0
 
 
 def test_extract_tracks_rejects():
