@@ -49,7 +49,7 @@ class _Grid(ctypes.Structure):
 
 class _LsOpts(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_double * 8), ("c1", ctypes.c_double),
-                ("max_halvings", ctypes.c_int32), ("step_cap_cells", ctypes.c_double)]
+                ("max_halvings", ctypes.c_int32), ("step_cap_cells", ctypes.c_double), ("update", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -158,12 +158,23 @@ def grid_maxima(R: np.ndarray, R0: float, cap: Optional[int] = None, with_margin
     return (out, cnt, margin) if with_margin else out
 
 
+UPDATE_TRUNCATED_NEWTON, UPDATE_STEEPEST_ASCENT, UPDATE_MODIFIED_NEWTON = 0, 1, 2
+
+
 def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, step, n,
-                 c1: float = 1e-4, max_halvings: int = 8, step_cap_cells: float = 4.0):
-    """Algorithm 1's q truncated-Newton updates for every seed.
+                 c1: float = 1e-4, max_halvings: int = 8, step_cap_cells: float = 4.0, update: int = 0):
+    """Algorithm 1's q updates for every seed.
+
+    update picks the direction of each update: 0 the truncated Newton
+    direction of Section 3 (the paper's choice), or one of the other methods
+    Section 3 says were examined, read as 1 steepest ascent (p = grad R) and
+    2 Newton with a modified Hessian (-Hess R shifted to be positive
+    definite); the step cap and Armijo backtracking are common to all.
 
     Returns (theta [n, 2] float64, R_final [n], status [n] uint8, margin [n]).
     """
+    if update not in (0, 1, 2):
+        raise ValueError("update must be 0, 1 or 2")
     h = _hits(hits)
     s = np.ascontiguousarray(seeds, dtype=np.float32).reshape(-1, 2)
     o = _LsOpts()
@@ -175,6 +186,7 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     o.c1 = float(c1)
     o.max_halvings = int(max_halvings)
     o.step_cap_cells = float(step_cap_cells)
+    o.update = int(update)
     g = make_grid(lo, step, n)
     ns = s.shape[0]
     th = np.zeros((ns, 2))

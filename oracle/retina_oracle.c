@@ -184,6 +184,8 @@ typedef struct {
     double c1;               /* Armijo sufficient-increase constant                 */
     int32_t max_halvings;    /* backtracking halvings after the unit step           */
     double step_cap_cells;   /* cap on ||p / step||_inf, in grid cells              */
+    int32_t update;          /* direction: 0 truncated Newton, 1 steepest ascent,    */
+                             /* 2 Newton with a shifted (modified) Hessian          */
 } or_ls_opts;
 
 /*
@@ -243,6 +245,39 @@ static void newton_cg_direction(const double g[2], const double H[3], const doub
 }
 
 /*
+ * Newton direction with a modified Hessian (Nocedal & Wright, Section 3.4):
+ * B = -H is shifted by tau I, tau = max(0, delta - mu1), mu1 <= mu2 the
+ * eigenvalues of B and delta = 1e-3 max(|mu1|, |mu2|), so that B + tau I is
+ * positive definite with smallest eigenvalue >= delta; p solves
+ * (B + tau I) p = g.  Where -H is already positive definite beyond delta this
+ * is the plain Newton step.  B = 0 (no curvature) gives p = g.  *margin gets
+ * the distance of the shift test mu1 < delta from its threshold, in units of
+ * 1e-4 of the sum of absolute Hessian terms.
+ */
+static void modified_newton_direction(const double g[2], const double H[3], const double Habs[3], double p[2],
+                                      double *margin) {
+    const double a = -H[0], b = -H[1], c = -H[2];
+    const double mid = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + b * b);
+    const double mu1 = mid - rad, mu2 = mid + rad;
+    const double delta = 1e-3 * fmax(fabs(mu1), fabs(mu2));
+    {
+        const double tol = 1e-4 * (Habs[0] + 2.0 * Habs[1] + Habs[2]);
+        const double m = tol > 0.0 ? fabs(mu1 - delta) / tol : 0.0;
+        if (m < *margin) *margin = m;
+    }
+    if (!(delta > 0.0)) {
+        p[0] = g[0];
+        p[1] = g[1];
+        return;
+    }
+    const double tau = mu1 < delta ? delta - mu1 : 0.0;
+    const double a2 = a + tau, c2 = c + tau;
+    const double det = a2 * c2 - b * b;
+    p[0] = (c2 * g[0] - b * g[1]) / det;
+    p[1] = (a2 * g[1] - b * g[0]) / det;
+}
+
+/*
  * One seed through Algorithm 1's q updates.  Returns the status:
  * 0 ok, 1 some line search accepted no step, 2 final point outside the box,
  * 3 non-finite.  *margin receives the smallest distance of any discrete
@@ -267,7 +302,14 @@ static int search_one(const float *hits, int64_t n_hits, int model, const float 
         const double gabs[2] = {rgh[7], rgh[8]};
         const double Habs[3] = {rgh[9], rgh[10], rgh[11]};
         double p[2];
-        newton_cg_direction(g, H, gabs, Habs, p, margin);
+        if (o->update == 1) {         /* steepest ascent: the gradient itself */
+            p[0] = g[0];
+            p[1] = g[1];
+        } else if (o->update == 2) {
+            modified_newton_direction(g, H, Habs, p, margin);
+        } else {
+            newton_cg_direction(g, H, gabs, Habs, p, margin);
+        }
         /* cap the step length, measured in grid cells */
         const double cells = fmax(fabs(p[0]) / box->step[0], fabs(p[1]) / box->step[1]);
         if (cells > o->step_cap_cells) {

@@ -300,6 +300,142 @@ def test_newton_overshoot_backtracks_by_armijo_brute_force(c1):
     assert {1e-4: 1.0, 0.3: 1.0, 0.6: 0.5, 0.9: 0.125}[c1] == t_expect
 
 
+def _one_velo_hit_start(offset_widths):
+    hits = np.array([[12.5, -25.0, 100.0, 0.0]], np.float32)
+    sigma = 0.25
+    w = sigma / 100.0
+    s32 = np.array([[0.125 + offset_widths * w, -0.25]], np.float32)
+    return hits, sigma, w, s32, s32[0].astype(np.float64)
+
+
+def _armijo_t(hits, model, th0, p, sigma, c1, R0, g):
+    for h in range(9):
+        t = 0.5 ** h
+        if oracle.response(hits, model, [th0 + t * p], sigma)[0] >= R0 + c1 * t * (g @ p):
+            return t
+    return None
+
+
+@pytest.mark.parametrize("c1", [1e-4, 0.3])
+def test_steepest_ascent_takes_the_capped_gradient(c1):
+    # Inside the peak (0.3 widths off along t_x, where the truncated Newton
+    # direction would be the Newton step) the steepest-ascent update moves
+    # along grad R itself, scaled down to the step cap, by the first
+    # step length passing the Armijo test (found by brute force).
+    hits, sigma, w, s32, th0 = _one_velo_hit_start(0.3)
+    step = (2 ** -10, 2 ** -10)
+    out = oracle.rgh(hits, 1, th0, sigma)
+    g = out["grad"]
+    cap = 0.25
+    p = g * cap / np.max(np.abs(g) / np.asarray(step))
+    t = _armijo_t(hits, 1, th0, p, sigma, c1, out["R"], g)
+    assert t is not None
+    th, R, st, m = oracle.local_search(hits, 1, s32, [sigma], (-0.5, -0.5), step, (1024, 1024),
+                                       step_cap_cells=cap, c1=c1, update=1)
+    assert st[0] == 0
+    np.testing.assert_allclose(th[0], th0 + t * p, rtol=0, atol=1e-15)
+    # the truncated Newton direction differs here (it is -H^-1 g, not along g scaled)
+    th_n, _, _, _ = oracle.local_search(hits, 1, s32, [sigma], (-0.5, -0.5), step, (1024, 1024),
+                                        step_cap_cells=1e9, c1=c1)
+    assert not np.allclose(th_n[0], th[0])
+
+
+@pytest.mark.parametrize("c1", [1e-4, 0.6])
+@pytest.mark.parametrize("model", [0, 1])
+def test_modified_newton_is_the_newton_step_where_the_peak_is_concave(c1, model):
+    # -Hess R positive definite (inside the peak): no shift, p = -H^-1 g
+    # (numpy.linalg.solve), then Armijo by brute force.  Slope model: one hit
+    # (diagonal Hessian); 2D toy: a noiseless line seen at x = 1..10, whose
+    # Hessian couples the two parameters.
+    if model == 1:
+        hits, sigma, w, s32, th0 = _one_velo_hit_start(0.3)
+        lo, step, n = (-0.5, -0.5), (2 ** -10,) * 2, (1024, 1024)
+    else:
+        xs = np.arange(1, 11, dtype=np.float64)
+        hits = np.stack([xs, 0.1 * xs - 0.2, 0 * xs, 0 * xs], 1).astype(np.float32)
+        sigma = 0.05
+        s32 = np.array([[0.1 + 0.002, -0.2 - 0.006]], np.float32)
+        th0 = s32[0].astype(np.float64)
+        lo, step, n = (-1, -1), (2 ** -8,) * 2, (512, 512)
+    out = oracle.rgh(hits, model, th0, sigma)
+    g, H = out["grad"], out["hess"]
+    assert np.all(np.linalg.eigvalsh(-H) > 0)
+    assert model == 1 or abs(H[0, 1]) > 0.5 * np.sqrt(H[0, 0] * H[1, 1])
+    p = np.linalg.solve(-H, g)
+    t = _armijo_t(hits, model, th0, p, sigma, c1, out["R"], g)
+    th, R, st, m = oracle.local_search(hits, model, s32, [sigma], lo, step, n,
+                                       step_cap_cells=1e9, c1=c1, update=2)
+    if t is None:
+        assert st[0] == 1 and np.all(th[0] == th0)
+    else:
+        np.testing.assert_allclose(th[0], th0 + t * p, rtol=0, atol=1e-14)
+
+
+def test_modified_newton_in_a_rank_one_convex_tail_is_the_capped_gradient_step():
+    # One toy hit: Hess R = e (4k^2 r^2 - 2k) v v^T with v = (x, 1), so in the
+    # convex tail (4 k r^2 > 2) -H has eigenvalues (mu1 < 0, 0) with g along v.
+    # The shift leaves eigenvalue delta along v, so p = g / delta points along
+    # g and, being far longer than the cap, is capped: exactly the
+    # steepest-ascent update (worked by hand from the definitions).
+    hits = np.array([[2.0, 0.0, 0.0, 0.0]], np.float32)
+    sigma = 0.25
+    start = np.array([[0.05, 0.3]], np.float32)
+    th0 = start[0].astype(np.float64)
+    out = oracle.rgh(hits, 0, th0, sigma)
+    r = 0.0 - th0[0] * 2.0 - th0[1]
+    assert 4 * r * r / sigma ** 2 > 2
+    step = (2 ** -8, 2 ** -8)
+    args = (hits, 0, start, [sigma], (-1, -1), step, (512, 512))
+    th2, R2, st2, _ = oracle.local_search(*args, step_cap_cells=2.0, update=2)
+    th1, R1, st1, _ = oracle.local_search(*args, step_cap_cells=2.0, update=1)
+    np.testing.assert_allclose(th2[0], th1[0], rtol=0, atol=1e-12)
+    assert st1[0] == st2[0] == 0 and R2[0] > out["R"]
+
+
+@pytest.mark.parametrize("update", [1, 2])
+def test_alternative_updates_on_a_noiseless_track(update):
+    # Modified Newton converges quadratically inside the peak (it is Newton
+    # there); steepest ascent converges too, linearly at best.  Both never
+    # lower R at a fixed bandwidth (Armijo).
+    zs = np.array([-300.0 + 42.0 * p for p in range(26)])
+    t = np.array([0.07, -0.045])
+    hits = np.stack([t[0] * zs, t[1] * zs, zs, 0 * zs], 1).astype(np.float32)
+    sigma = 0.3
+    w = sigma / math.sqrt(np.mean(zs ** 2))
+    seeds = np.array([t + np.array([0.08, -0.05]) * w], np.float32)
+    errs, Rs = [np.max(np.abs(seeds[0] - t))], [oracle.response(hits, 1, seeds.astype(float), sigma)[0]]
+    qs = (1, 2, 3) if update == 2 else (2, 4, 8)
+    for q in qs:
+        th, R, st, m = oracle.local_search(hits, 1, seeds, [sigma] * q, (-0.5, -0.5), (2 ** -10,) * 2, (1024, 1024),
+                                           step_cap_cells=0.5, update=update)
+        errs.append(np.max(np.abs(th[0] - t)))
+        Rs.append(R[0])
+    assert all(b >= a * (1 - 1e-15) for a, b in zip(Rs, Rs[1:]))
+    if update == 2:
+        for k in range(3):
+            assert errs[k + 1] <= 2.0 * errs[k] ** 2 / w + 1e-9
+        assert errs[3] < 1e-8
+    else:
+        assert errs[-1] < 0.2 * errs[0]
+
+
+@pytest.mark.parametrize("update", [0, 1, 2])
+def test_every_update_never_lowers_R_at_a_fixed_bandwidth(update):
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 8, 0, vertex_sigma=(0, 0, 0))
+    rng = np.random.default_rng(8)
+    seeds = (ev.truth[rng.integers(0, len(ev.truth), 200), :2] + rng.normal(0, 3, (200, 2)) * 2 ** -10)
+    seeds = seeds.astype(np.float32)
+    sigma = 0.175
+    R0 = oracle.response(ev.hits, 1, seeds.astype(float), sigma)
+    th, R, st, m = oracle.local_search(ev.hits, 1, seeds, [sigma] * 3, wl.grid_lo, wl.grid_step, wl.grid_n,
+                                       update=update)
+    ok = st <= 1
+    assert ok.sum() >= 190
+    assert np.all(R[ok] >= R0[ok] * (1 - 1e-12))
+    assert np.mean(R[ok] > R0[ok]) > 0.9
+
+
 def test_search_maxima_agree_with_brute_force_fine_grid():
     # tiny event (3 tracks, ~30 hits): every converged point with R >= R0 is a
     # local maximum of R to within a fine-grid step around it.
