@@ -296,7 +296,8 @@ BATCH_EVENTS = 1024
 BATCH_RUN_SEED = 5000
 
 
-def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: int = 512, reps: int = 5):
+def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: int = 512, reps: int = 5,
+                    comparisons: bool = False):
     """1024 ragged VELO-like events with the vertex at the origin through three
     methods, each replayed as one CUDA graph per batch: the plain grid scan
     (with and without the refinement of its maxima), Algorithm 1 from 4096
@@ -305,10 +306,14 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
     events around graph replays (L2 flushed before each), MC-truth efficiency
     (|dtheta|_max <= 1e-3), fakes per event, the resolution of the matched
     tracks (|dtheta| per axis in grid cells) and the share of the plain
-    4096-seed search's tracks each method recovers."""
+    4096-seed search's tracks each method recovers.  With ``comparisons``:
+    the same searches with the steepest-ascent and modified-Newton updates,
+    and the seed budgets of the paper's experiment, n = alpha n_grid / (C0 q)
+    with its C0 = 30 and q = 3, at alpha = 1/3 and 1/10, with efficiencies
+    binned by the events' track multiplicity (the shape of its Fig. 3)."""
     import torch
-    from paper_1709_08610_gb300.pipeline import (BatchTracker, GridScanBatch, match_efficiency, match_residuals,
-                                                 recovered_fraction)
+    from paper_1709_08610_gb300.pipeline import (BatchTracker, GridScanBatch, efficiency_by_multiplicity,
+                                                 match_efficiency, match_residuals, recovered_fraction)
     from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, SeedProposer
     wl = WORKLOADS[workload]
     E = BATCH_EVENTS
@@ -340,17 +345,32 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
     # CTAs staging up to 12288 hits (measured fastest on both batch workloads:
     # ~16 % over one unordered seed per warp, more on high-multiplicity events)
     shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    seeds4096 = np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])
     runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
             ("grid_scan_%dx%d_refined" % (n0, n1),
              lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0, refine_iters=4), None),
-            ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0, **shape),
-             np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])),
+            ("uniform_4096", lambda: BatchTracker(E, H, 4096, box, opts, wl.R0, **shape), seeds4096),
             ("uniform_%d" % learned_k, lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, **shape),
              np.stack([uniform_seeds(wl, learned_k, BATCH_RUN_SEED, e) for e in range(E)]))]
-    if os.path.exists(DEFAULT_WEIGHTS):
-        prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS)
+    prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS) if os.path.exists(DEFAULT_WEIGHTS) else None
+    if prop is not None:
         runs.append(("learned_%d" % learned_k,
                      lambda: BatchTracker(E, H, learned_k, box, opts, wl.R0, proposer=prop, **shape), None))
+    if comparisons:
+        for upd, tag in ((rt.UPDATE_STEEPEST_ASCENT, "steepest_ascent"), (rt.UPDATE_MODIFIED_NEWTON, "modified_newton")):
+            o = rt.LsOpts(sigma=tuple(wl.sigma_schedule), update=upd)
+            runs.append(("uniform_4096_" + tag, lambda o=o: BatchTracker(E, H, 4096, box, o, wl.R0, **shape),
+                         seeds4096))
+            if prop is not None:
+                runs.append(("learned_%d_%s" % (learned_k, tag),
+                             lambda o=o: BatchTracker(E, H, learned_k, box, o, wl.R0, proposer=prop, **shape), None))
+        for alpha, tag in ((1.0 / 3.0, "1/3"), (0.1, "1/10")):
+            n = int(round(alpha * n0 * n1 / (30 * 3)))
+            runs.append(("alpha_%s_uniform_%d" % (tag, n), lambda n=n: BatchTracker(E, H, n, box, opts, wl.R0, **shape),
+                         np.stack([uniform_seeds(wl, n, BATCH_RUN_SEED, e) for e in range(E)])))
+            if prop is not None:
+                runs.append(("alpha_%s_learned_%d" % (tag, n),
+                             lambda n=n: BatchTracker(E, H, n, box, opts, wl.R0, proposer=prop, **shape), None))
     found = {}
     for name, make, seeds in runs:
         obj = make()
@@ -359,10 +379,12 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         found[name] = obj.results()
         eff, fakes = match_efficiency(found[name], truth)
         res = match_residuals(found[name], truth) / np.asarray(wl.grid_step)
+        by_mult = efficiency_by_multiplicity(found[name], truth, (20, 75, 150, 225, 401))
         methods[name] = {"events_per_s": E / (ms * 1e-3), "ms_per_batch": ms, "efficiency": eff,
                          "fakes_per_event": fakes / E,
                          "resolution_cells": {"rms": float(np.sqrt(np.mean(res ** 2))) if res.size else None,
-                                              "median": float(np.median(res)) if res.size else None}}
+                                              "median": float(np.median(res)) if res.size else None},
+                         "efficiency_by_tracks": {k: round(v["efficiency"], 4) for k, v in by_mult.items()}}
         if isinstance(obj, GridScanBatch) and obj.ropts is None:
             # the grid scan alone (response + maxima, eager, after the hit ordering), with
             # its evaluated (cell, hit) pairs counted on the device: 2 flops per pair
@@ -848,7 +870,7 @@ def main():
         saved = {o: rt.get_option(o) for o in (rt.OPT_GRID_SPLITS, rt.OPT_BATCH_CTAS)}
         rt.set_option(rt.OPT_GRID_SPLITS, 0)
         rt.set_option(rt.OPT_BATCH_CTAS, 0)
-        batched = batched_methods(rt, stream, flush)
+        batched = batched_methods(rt, stream, flush, comparisons=True)
         stress = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
         for o, v in saved.items():
             rt.set_option(o, v)

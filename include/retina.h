@@ -115,7 +115,25 @@ typedef struct {
     float c1;             /* Armijo sufficient-increase constant, in [0, 1)    */
     int32_t max_halvings; /* backtracking halvings after t = 1, 0 .. 30        */
     float step_cap_cells; /* cap on max_a |p_a| / step_a, > 0                  */
+    int32_t update;       /* direction of each update (RETINA_UPDATE_*); 0, the */
+                          /* paper's truncated Newton, when zero-initialised   */
 } retina_ls_opts;
+
+/*
+ * Update directions (retina_ls_opts.update).  Section 3 reports truncated
+ * Newton as the best of the methods it examined; the other two are the
+ * textbook alternatives, for comparison.  All three share the step cap and
+ * the Armijo backtracking.
+ *   RETINA_UPDATE_TRUNCATED_NEWTON  Newton-CG (retina_local_search, step 2).
+ *   RETINA_UPDATE_STEEPEST_ASCENT   p = grad R.
+ *   RETINA_UPDATE_MODIFIED_NEWTON   p solves (B + tau I) p = grad R with
+ *       B = -Hess R, tau = max(0, delta - mu1), mu1 <= mu2 the eigenvalues of
+ *       B, delta = 1e-3 max(|mu1|, |mu2|) (Nocedal & Wright, Section 3.4);
+ *       B = 0 gives p = grad R.
+ */
+#define RETINA_UPDATE_TRUNCATED_NEWTON 0
+#define RETINA_UPDATE_STEEPEST_ASCENT 1
+#define RETINA_UPDATE_MODIFIED_NEWTON 2
 
 /* Human-readable text for a status code (static storage). */
 const char *retina_strerror(int code);

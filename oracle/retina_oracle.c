@@ -252,7 +252,10 @@ static void newton_cg_direction(const double g[2], const double H[3], const doub
  * (B + tau I) p = g.  Where -H is already positive definite beyond delta this
  * is the plain Newton step.  B = 0 (no curvature) gives p = g.  *margin gets
  * the distance of the shift test mu1 < delta from its threshold, in units of
- * 1e-4 of the sum of absolute Hessian terms.
+ * 1e-4 of the sum of absolute Hessian terms; a shifted step counts as a tie
+ * (margin 0): B + tau I then has condition number >= 1e3, so the direction
+ * moves by more than the FP32 Hessian tolerance can bound, and a path through
+ * it is not one that a float32 evaluation is expected to reproduce.
  */
 static void modified_newton_direction(const double g[2], const double H[3], const double Habs[3], double p[2],
                                       double *margin) {
@@ -271,6 +274,7 @@ static void modified_newton_direction(const double g[2], const double H[3], cons
         return;
     }
     const double tau = mu1 < delta ? delta - mu1 : 0.0;
+    if (tau > 0.0) *margin = 0.0;
     const double a2 = a + tau, c2 = c + tau;
     const double det = a2 * c2 - b * b;
     p[0] = (c2 * g[0] - b * g[1]) / det;

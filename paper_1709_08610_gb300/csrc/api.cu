@@ -77,7 +77,7 @@ const char *retina_strerror(int code) {
     }
 }
 
-int retina_abi_version(void) { return 1; }
+int retina_abi_version(void) { return 2; }
 
 int retina_set_option(int32_t option, int32_t value) {
     switch (option) {
@@ -268,6 +268,7 @@ static bool valid_ls_opts(const retina_ls_opts *opts) {
         if (!finite_pos(opts->sigma[j])) return false;
     if (!(opts->c1 >= 0.f && opts->c1 < 1.f)) return false;
     if (opts->max_halvings < 0 || opts->max_halvings > 30) return false;
+    if (opts->update < RETINA_UPDATE_TRUNCATED_NEWTON || opts->update > RETINA_UPDATE_MODIFIED_NEWTON) return false;
     return opts->step_cap_cells > 0.f;
 }
 

@@ -91,6 +91,7 @@ response_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box) {
     LsParams prm;
     prm.q = o->q;
+    prm.update = o->update;
     for (int j = 0; j < RETINA_MAX_Q; ++j) {
         const double s = j < o->q ? (double)o->sigma[j] : 1.0;
         prm.kk[j] = (float)(kLog2e / (s * s));

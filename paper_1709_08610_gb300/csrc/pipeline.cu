@@ -47,6 +47,7 @@ bool valid_config(const retina_pipeline_config &c) {
         if (!finite_pos(o.sigma[j])) return false;
     if (!(o.c1 >= 0.f && o.c1 < 1.f) || o.max_halvings < 0 || o.max_halvings > 30 || !(o.step_cap_cells > 0.f))
         return false;
+    if (o.update < RETINA_UPDATE_TRUNCATED_NEWTON || o.update > RETINA_UPDATE_MODIFIED_NEWTON) return false;
     if (c.max_events < 1 || c.max_hits < 0 || c.max_tracks < 1) return false;
     if (c.seeds_per_event < 1 || c.seeds_per_event > RETINA_MAX_EXTRACT_POINTS) return false;
     if (c.max_maxima < 1 || c.max_maxima > RETINA_MAX_EXTRACT_POINTS) return false;

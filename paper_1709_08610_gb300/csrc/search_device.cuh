@@ -184,8 +184,51 @@ __device__ __forceinline__ void newton_cg(float g0, float g1, float H00, float H
     p1 = z1;
 }
 
+// Newton direction with a modified Hessian (Nocedal & Wright, Section 3.4):
+// B = -H shifted by tau I, tau = max(0, delta - mu1), mu1 <= mu2 the
+// eigenvalues of B, delta = 1e-3 max(|mu1|, |mu2|); p solves
+// (B + tau I) p = g, or p = g when B = 0.  B and g are scaled by the same
+// power of two (B's largest entry into [1/2, 1)), which leaves p unchanged
+// and keeps the squares of the eigenvalue formula in range.
+__device__ __forceinline__ void modified_newton(float g0, float g1, float H00, float H01, float H11, float &p0,
+                                                float &p1) {
+    const float m = fmaxf(fmaxf(fabsf(H00), fabsf(H11)), fabsf(H01));
+    if (!(m > 0.f) || !isfinite(m)) {
+        p0 = g0;
+        p1 = g1;
+        return;
+    }
+    int ex;
+    frexpf(m, &ex);
+    const float c = ldexpf(1.f, -ex);
+    const float a = -H00 * c, b = -H01 * c, d = -H11 * c;
+    const float mid = 0.5f * (a + d), rad = sqrtf(0.25f * (a - d) * (a - d) + b * b);
+    const float mu1 = mid - rad, mu2 = mid + rad;
+    const float delta = 1e-3f * fmaxf(fabsf(mu1), fabsf(mu2));
+    const float tau = mu1 < delta ? delta - mu1 : 0.f;
+    const float a2 = a + tau, d2 = d + tau;
+    const float det = a2 * d2 - b * b;
+    const float sg0 = g0 * c, sg1 = g1 * c;
+    p0 = (d2 * sg0 - b * sg1) / det;
+    p1 = (a2 * sg1 - b * sg0) / det;
+}
+
+// The direction of one update (retina_ls_opts.update; warp-uniform).
+__device__ __forceinline__ void update_direction(int update, float g0, float g1, float H00, float H01, float H11,
+                                                 float &p0, float &p1) {
+    if (update == RETINA_UPDATE_STEEPEST_ASCENT) {
+        p0 = g0;
+        p1 = g1;
+    } else if (update == RETINA_UPDATE_MODIFIED_NEWTON) {
+        modified_newton(g0, g1, H00, H01, H11, p0, p1);
+    } else {
+        newton_cg(g0, g1, H00, H01, H11, p0, p1);
+    }
+}
+
 struct LsParams {
     int q;
+    int update;  // RETINA_UPDATE_*
     float kk[RETINA_MAX_Q];  // log2(e) / sigma_j^2
     float k[RETINA_MAX_Q];   // 1 / sigma_j^2
     float cull[RETINA_MAX_Q];  // CULL_EXPONENT / kk[j]: skipping threshold on |z|min^2 dist^2
@@ -424,7 +467,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         have = false;
         float R, g0, g1, H00, H01, H11, pp0, pp1;
         sums_to_rgh<MODEL>(S, k, R, g0, g1, H00, H01, H11);
-        newton_cg(g0, g1, H00, H01, H11, pp0, pp1);
+        update_direction(prm.update, g0, g1, H00, H01, H11, pp0, pp1);
         const float cells = fmaxf(fabsf(pp0) / prm.box.step0, fabsf(pp1) / prm.box.step1);
         if (cells > prm.cap) {
             const float sc = prm.cap / cells;
@@ -578,7 +621,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             for (int i = 0; i < NS; ++i) S[p][i] = warp_sum(S[p][i]);
             float H00, H01, H11;
             sums_to_rgh<MODEL>(S[p], k, R[p], g0[p], g1[p], H00, H01, H11);
-            newton_cg(g0[p], g1[p], H00, H01, H11, pp0[p], pp1[p]);
+            update_direction(prm.update, g0[p], g1[p], H00, H01, H11, pp0[p], pp1[p]);
             const float cells = fmaxf(fabsf(pp0[p]) / prm.box.step0, fabsf(pp1[p]) / prm.box.step1);
             if (cells > prm.cap) {
                 const float sc = prm.cap / cells;

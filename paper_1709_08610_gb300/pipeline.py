@@ -213,6 +213,20 @@ def match_residuals(found, truth, eps: float = 1e-3) -> np.ndarray:
     return np.concatenate(out) if out else np.zeros((0, 2))
 
 
+def efficiency_by_multiplicity(found, truth, edges, eps: float = 1e-3) -> dict:
+    """MC efficiency over the events whose number of truth tracks lies in
+    [edges[i], edges[i+1]), keyed "lo-hi" (the shape of the paper's Fig. 3:
+    efficiency against the number of reconstructible tracks)."""
+    out = {}
+    n = np.array([len(np.asarray(t).reshape(-1, 2)) for t in truth])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = [i for i in range(len(truth)) if lo <= n[i] < hi]
+        if sel:
+            eff, _ = match_efficiency([found[i] for i in sel], [truth[i] for i in sel], eps)
+            out["%d-%d" % (lo, hi)] = {"events": len(sel), "efficiency": eff}
+    return out
+
+
 def recovered_fraction(found, reference, eps: float = 1e-3):
     """Fraction of the reference method's tracks that ``found`` also has (within eps)."""
     eff, _ = match_efficiency(found, reference, eps)

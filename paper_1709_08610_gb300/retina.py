@@ -25,6 +25,7 @@ MAX_Q = 8
 MAX_EXTRACT_POINTS = 8192
 OPT_LS_SEEDS_PER_WARP, OPT_LS_SMEM_HITS, OPT_GRID_SPLITS, OPT_LS_WARPS = 1, 2, 3, 4
 OPT_BATCH_SEEDS_PER_WARP, OPT_BATCH_WARPS, OPT_BATCH_SMEM_HITS, OPT_BATCH_CTAS = 5, 6, 7, 8
+UPDATE_TRUNCATED_NEWTON, UPDATE_STEEPEST_ASCENT, UPDATE_MODIFIED_NEWTON = 0, 1, 2
 OPT_SEEDNET_TC = 9
 OPT_GRID_TC = 10
 
@@ -43,7 +44,7 @@ class _CGrid(ctypes.Structure):
 
 class _CLsOpts(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_float * 8), ("c1", ctypes.c_float),
-                ("max_halvings", ctypes.c_int32), ("step_cap_cells", ctypes.c_float)]
+                ("max_halvings", ctypes.c_int32), ("step_cap_cells", ctypes.c_float), ("update", ctypes.c_int32)]
 
 
 @dataclass(frozen=True)
@@ -75,6 +76,7 @@ class LsOpts:
     c1: float = 1e-4
     max_halvings: int = 8
     step_cap_cells: float = 4.0
+    update: int = 0  # UPDATE_TRUNCATED_NEWTON / UPDATE_STEEPEST_ASCENT / UPDATE_MODIFIED_NEWTON
 
     def c(self) -> _CLsOpts:
         o = _CLsOpts()
@@ -84,6 +86,7 @@ class LsOpts:
         o.c1 = float(self.c1)
         o.max_halvings = int(self.max_halvings)
         o.step_cap_cells = float(self.step_cap_cells)
+        o.update = int(self.update)
         return o
 
 

@@ -24,7 +24,7 @@ def test_exports_every_declared_function():
 
 
 def test_strerror_and_version():
-    assert L.retina_abi_version() == 1
+    assert L.retina_abi_version() == 2
     for c in range(5):
         assert L.retina_strerror(c)
     assert b"invalid" in L.retina_strerror(EINVAL)
@@ -96,7 +96,7 @@ def _opts(**kw):
     return o
 
 
-@pytest.mark.parametrize("mut", ["q0", "q9", "sigma0", "sigmanan", "c1neg", "c1one", "halv", "cap0"])
+@pytest.mark.parametrize("mut", ["q0", "q9", "sigma0", "sigmanan", "c1neg", "c1one", "halv", "cap0", "upd-1", "upd3"])
 def test_local_search_rejects(mut):
     o = _opts()
     if mut == "q0":
@@ -115,6 +115,10 @@ def test_local_search_rejects(mut):
         o.max_halvings = 31
     elif mut == "cap0":
         o.step_cap_cells = 0.0
+    elif mut == "upd-1":
+        o.update = -1
+    elif mut == "upd3":
+        o.update = 3
     g = _grid()
     rc = L.retina_local_search(BOGUS, 10, BOGUS, None, 1, 1, BOGUS, 16, ctypes.byref(o), ctypes.byref(g), BOGUS, BOGUS,
                                BOGUS, None, None)

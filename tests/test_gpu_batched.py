@@ -51,9 +51,10 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_batched_matches_per_launch_search_bitwise(rt):
+@pytest.mark.parametrize("update", [0, 1, 2])
+def test_batched_matches_per_launch_search_bitwise(rt, update):
     wl, evs, b, seeds, so = _ragged()
-    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule), update=update)
     box = rt.Grid.of(wl)
     th, R, st = rt.batched_search(_dev(b.hits), _dev(b.offsets), 1, _dev(seeds), _dev(so), opts, box)
     th, R, st = th.cpu().numpy(), R.cpu().numpy(), st.cpu().numpy()

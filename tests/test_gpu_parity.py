@@ -227,12 +227,13 @@ def test_grid_scan_toy_matches_oracle(rt):
 # local search (Algorithm 1 + truncated Newton)
 # ---------------------------------------------------------------------------
 
-def _search_both(rt, wl, ev, seeds, sigma=None):
+def _search_both(rt, wl, ev, seeds, sigma=None, update=0):
     sig = tuple(wl.sigma_schedule if sigma is None else sigma)
     off = np.array([0, ev.n_hits], np.int64)
-    th_g, R_g, st_g = rt.local_search(dev(ev.hits), dev(off), wl.model, dev(seeds[None]), rt.LsOpts(sigma=sig),
-                                      rt.Grid.of(wl))
-    th_o, R_o, st_o, m_o = oracle.local_search(ev.hits, wl.model, seeds, sig, wl.grid_lo, wl.grid_step, wl.grid_n)
+    th_g, R_g, st_g = rt.local_search(dev(ev.hits), dev(off), wl.model, dev(seeds[None]),
+                                      rt.LsOpts(sigma=sig, update=update), rt.Grid.of(wl))
+    th_o, R_o, st_o, m_o = oracle.local_search(ev.hits, wl.model, seeds, sig, wl.grid_lo, wl.grid_step, wl.grid_n,
+                                               update=update)
     return (th_g.cpu().numpy()[0].astype(float), R_g.cpu().numpy()[0].astype(float), st_g.cpu().numpy()[0],
             th_o, R_o, st_o, m_o)
 
@@ -297,6 +298,58 @@ def test_local_search_velo_matches_oracle(rt, spw):
         rt.set_option(rt.OPT_LS_SEEDS_PER_WARP, old)
     _, n_conv = _check_search(wl, ev, *res, min_robust=600)
     assert n_conv >= 100
+
+
+@pytest.mark.parametrize("update", [1, 2])
+@pytest.mark.parametrize("wl_name", ["toy2d", "velo"])
+def test_local_search_alternative_updates_match_oracle(rt, update, wl_name):
+    # steepest ascent (1) and Newton with a modified Hessian (2): the same
+    # robust-decision and converged-point parity as the truncated Newton search
+    wl = WORKLOADS[wl_name]
+    if wl_name == "velo":
+        ev = velo0(0, 2)
+        rng = np.random.default_rng(6)
+        near = ev.truth[:, :2][rng.integers(0, len(ev.truth), 500)] + rng.normal(0, 3, (500, 2)) * 2 ** -10
+        seeds = np.concatenate([near, uniform_seeds(wl, 201, 0, 2)]).astype(np.float32)
+    else:
+        ev = make_event(wl, 0, 5)
+        seeds = uniform_seeds(wl, wl.n_seeds, 0, 5)
+    res = _search_both(rt, wl, ev, seeds, update=update)
+    if update == 1:
+        _check_search(wl, ev, *res, min_robust=len(seeds) // 4)
+        return
+    # Modified Newton: a shifted step (indefinite Hessian, the usual case far
+    # from a peak) solves a system of condition number >= 1e3, so its path is
+    # not reproducible in float32 and the oracle counts it as a tie; robust
+    # seeds are the few that never shifted.  Every converged oracle point is
+    # compared instead: most float32 paths reach the same maximum (within
+    # 0.05 cell), and there they agree to 1e-3 cell (or the displacement the
+    # FP32 gradient tolerance allows on an ill-conditioned peak) and R to its
+    # tolerance.
+    th_g, R_g, st_g, th_o, R_o, st_o, m_o = res
+    robust = m_o >= 1.0
+    assert np.all(st_g[robust] == st_o[robust])
+    step = np.asarray(wl.grid_step)
+    sq = wl.sigma_schedule[-1]
+    conv, same = 0, 0
+    for i in np.flatnonzero(st_o <= 1):
+        o = oracle.rgh(ev.hits, wl.model, th_o[i], sq)
+        H, g = o["hess"], o["grad"]
+        if not np.all(np.linalg.eigvalsh(H) < 0):
+            continue
+        Hi = np.linalg.inv(H)
+        if np.max(np.abs(Hi @ g) / step) > 0.05:
+            continue
+        conv += 1
+        if np.max(np.abs(th_g[i] - th_o[i]) / step) > 0.05:
+            continue
+        same += 1
+        d = np.maximum(TH_CELLS * step, np.abs(Hi) @ (GH_REL * o["grad_abs"]))
+        assert np.all(np.abs(th_g[i] - th_o[i]) <= d), (i, (th_g[i] - th_o[i]) / step)
+        tol = R_REL * R_o[i] + R_ABS + np.abs(g) @ d + np.abs(H).max() * (d @ d)
+        assert abs(R_g[i] - R_o[i]) <= tol, (i, R_g[i], R_o[i], tol)
+    assert conv >= (100 if wl_name == "velo" else 10), conv
+    assert same >= 0.8 * conv, (same, conv)
 
 
 def test_local_search_hits_beyond_shared_memory(rt):
