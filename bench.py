@@ -307,13 +307,10 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
     (|dtheta|_max <= 1e-3), fakes per event, the resolution of the matched
     tracks (|dtheta| per axis in grid cells) and the share of the plain
     4096-seed search's tracks each method recovers.  With ``comparisons``:
-    the same searches with the steepest-ascent and modified-Newton updates,
-    and the seed budgets of the paper's experiment, n = alpha n_grid / (C0 q)
-    with its C0 = 30 and q = 3, at alpha = 1/3 and 1/10, with efficiencies
-    binned by the events' track multiplicity (the shape of its Fig. 3)."""
+    the same searches with the steepest-ascent and modified-Newton updates."""
     import torch
-    from paper_1709_08610_gb300.pipeline import (BatchTracker, GridScanBatch, efficiency_by_multiplicity,
-                                                 match_efficiency, match_residuals, recovered_fraction)
+    from paper_1709_08610_gb300.pipeline import (BatchTracker, GridScanBatch, match_efficiency, match_residuals,
+                                                 recovered_fraction)
     from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, SeedProposer
     wl = WORKLOADS[workload]
     E = BATCH_EVENTS
@@ -364,13 +361,6 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
             if prop is not None:
                 runs.append(("learned_%d_%s" % (learned_k, tag),
                              lambda o=o: BatchTracker(E, H, learned_k, box, o, wl.R0, proposer=prop, **shape), None))
-        for alpha, tag in ((1.0 / 3.0, "1/3"), (0.1, "1/10")):
-            n = int(round(alpha * n0 * n1 / (30 * 3)))
-            runs.append(("alpha_%s_uniform_%d" % (tag, n), lambda n=n: BatchTracker(E, H, n, box, opts, wl.R0, **shape),
-                         np.stack([uniform_seeds(wl, n, BATCH_RUN_SEED, e) for e in range(E)])))
-            if prop is not None:
-                runs.append(("alpha_%s_learned_%d" % (tag, n),
-                             lambda n=n: BatchTracker(E, H, n, box, opts, wl.R0, proposer=prop, **shape), None))
     found = {}
     for name, make, seeds in runs:
         obj = make()
@@ -379,12 +369,10 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         found[name] = obj.results()
         eff, fakes = match_efficiency(found[name], truth)
         res = match_residuals(found[name], truth) / np.asarray(wl.grid_step)
-        by_mult = efficiency_by_multiplicity(found[name], truth, (20, 75, 150, 225, 401))
         methods[name] = {"events_per_s": E / (ms * 1e-3), "ms_per_batch": ms, "efficiency": eff,
                          "fakes_per_event": fakes / E,
                          "resolution_cells": {"rms": float(np.sqrt(np.mean(res ** 2))) if res.size else None,
-                                              "median": float(np.median(res)) if res.size else None},
-                         "efficiency_by_tracks": {k: round(v["efficiency"], 4) for k, v in by_mult.items()}}
+                                              "median": float(np.median(res)) if res.size else None}}
         if isinstance(obj, GridScanBatch) and obj.ropts is None:
             # the grid scan alone (response + maxima, eager, after the hit ordering), with
             # its evaluated (cell, hit) pairs counted on the device: 2 flops per pair
@@ -429,6 +417,65 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
                         % ((E,) + tuple(gen["n_tracks"]) + (H, n0, n1)),
             "events": E, "hits": int(H), "reps": reps, "methods": methods,
             "l2": "flushed before each replay"}
+
+
+ALPHA_MULTIPLICITIES = (10, 25, 50, 100, 200, 400)
+
+
+def alpha_sweep(rt, stream, flush, reps: int = 3):
+    """The paper's experiment in shape (its Fig. 3): efficiency against the
+    number of reconstructible tracks at the seed budgets n = alpha n_grid /
+    (C0 q), with its C0 = 30 and q = 3 over the 1024^2 grid, for alpha = 1/3
+    and 1/10; uniform seeds (the paper's prior) and learned ones.  1024
+    origin-vertex VELO-like events, 10 to 400 tracks each (an equal share of
+    each multiplicity), one CUDA graph per batch."""
+    import torch
+    from paper_1709_08610_gb300.pipeline import BatchTracker, efficiency_by_multiplicity, match_efficiency
+    from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, SeedProposer
+    wl = WORKLOADS["velo_batch"]
+    E = BATCH_EVENTS
+    mult = [ALPHA_MULTIPLICITIES[e % len(ALPHA_MULTIPLICITIES)] for e in range(E)]
+    evs = [make_event(wl, BATCH_RUN_SEED + 1, e, vertex_sigma=(0, 0, 0), n_tracks=mult[e]) for e in range(E)]
+    b = batch_of(evs)
+    truth = [ev.truth[:, :2] for ev in evs]
+    H = b.hits.shape[0]
+    box = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS) if os.path.exists(DEFAULT_WEIGHTS) else None
+    edges = sorted(set(ALPHA_MULTIPLICITIES)) + [ALPHA_MULTIPLICITIES[-1] + 1]
+    n0, n1 = wl.grid_n
+    out = {}
+    for alpha, tag in ((1.0 / 3.0, "1/3"), (0.1, "1/10")):
+        n = int(round(alpha * n0 * n1 / (30 * 3)))
+        kinds = [("uniform", None)] + ([("learned", prop)] if prop is not None else [])
+        for kind, pr in kinds:
+            obj = BatchTracker(E, H, n, box, opts, wl.R0, proposer=pr, **shape)
+            seeds = None if pr is not None else np.stack([uniform_seeds(wl, n, BATCH_RUN_SEED + 1, e)
+                                                          for e in range(E)])
+            obj.load(b.hits, b.offsets, seeds)
+            obj.capture()
+            obj.replay()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                obj.replay()
+                c.record(stream)
+                c.synchronize()
+                ts.append(a.elapsed_time(c))
+            found = obj.results()
+            eff, fakes = match_efficiency(found, truth)
+            by = efficiency_by_multiplicity(found, truth, edges)
+            out["alpha_%s_%s_%d" % (tag, kind, n)] = {
+                "seeds_per_event": n, "events_per_s": E / (statistics.median(ts) * 1e-3), "efficiency": eff,
+                "efficiency_by_tracks": {k.split("-")[0]: round(v["efficiency"], 4) for k, v in by.items()}}
+            del obj
+            torch.cuda.empty_cache()
+    return {"workload": "%d origin-vertex VELO-like events, %s tracks (equal shares), %d hits; seeds "
+                        "n = alpha 1024^2 / (30 * 3)" % (E, "/".join(str(m) for m in ALPHA_MULTIPLICITIES), H),
+            "runs": out, "l2": "flushed before each replay"}
 
 
 # ---------------------------------------------------------------------------
@@ -862,7 +909,7 @@ def main():
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
-    batched = stress = None
+    batched = stress = alpha = None
     if world == 1 and not args.no_batched:
         # launch shapes tuned for one event do not carry over to 1024: the grid's
         # hit-slice count goes back to the library's rule (one slice at this
@@ -871,6 +918,7 @@ def main():
         rt.set_option(rt.OPT_GRID_SPLITS, 0)
         rt.set_option(rt.OPT_BATCH_CTAS, 0)
         batched = batched_methods(rt, stream, flush, comparisons=True)
+        alpha = alpha_sweep(rt, stream, flush)
         stress = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
         for o, v in saved.items():
             rt.set_option(o, v)
@@ -897,7 +945,7 @@ def main():
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},
             "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0, "batched": batched,
-            "batched_stress": stress,
+            "batched_stress": stress, "alpha_sweep": alpha,
             "tuned": tuned,
         }
         print(json.dumps(line), flush=True)

@@ -66,7 +66,7 @@ __device__ __forceinline__ int64_t n_groups_of(const BatchArgs &a, int e) {
 }
 
 // at most 64 registers per thread: 2048 / (32 WARPS) CTAs of WARPS warps fit the register file
-template <int MODEL, int P, int WARPS>
+template <int MODEL, int P, int WARPS, int UPD>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(BatchArgs a, LsParams prm) {
     extern __shared__ float4 sh[];
     __shared__ int cur_e;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             if (g >= groups) break;
             const int64_t s = s0 + (int64_t)g * P;
             const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
-            search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, a.seeds + 2 * s, n_live, prm,
+            search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, a.seeds + 2 * s, n_live, prm,
                                    a.theta_out + 2 * s,
                                    a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work);
         }
@@ -144,9 +144,9 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
 
 size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(int32_t) + 255) / 256 * 256; }
 
-template <int MODEL, int P, int WARPS>
+template <int MODEL, int P, int WARPS, int UPD>
 static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
-    auto kern = batched_search_kernel<MODEL, P, WARPS>;
+    auto kern = batched_search_kernel<MODEL, P, WARPS, UPD>;
     const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS);
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (aerr != cudaSuccess) return aerr;
@@ -163,11 +163,11 @@ static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, int
     return lerr != cudaSuccess ? lerr : cudaGetLastError();
 }
 
-template <int MODEL, int P>
+template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
-    if (warps >= 32) return launch_batched_t<MODEL, P, 32>(a, prm, ctas, st);
-    if (warps >= 16) return launch_batched_t<MODEL, P, 16>(a, prm, ctas, st);
-    return launch_batched_t<MODEL, P, 8>(a, prm, ctas, st);
+    if (warps >= 32) return launch_batched_t<MODEL, P, 32, UPD>(a, prm, ctas, st);
+    if (warps >= 16) return launch_batched_t<MODEL, P, 16, UPD>(a, prm, ctas, st);
+    return launch_batched_t<MODEL, P, 8, UPD>(a, prm, ctas, st);
 }
 
 static cudaError_t launch_batched(BatchArgs &a, int model, const retina_ls_opts *o, const retina_grid *box,
@@ -179,6 +179,16 @@ static cudaError_t launch_batched(BatchArgs &a, int model, const retina_ls_opts 
     a.work = work_counters();
     cudaError_t err = cudaMemsetAsync(a.counters, 0, batched_ws_bytes(a.n_events), st);
     if (err != cudaSuccess) return err;
+    // the comparison updates run one seed per warp (bitwise the same results
+    // as any other grouping), which keeps their instantiations few
+    if (o->update == RETINA_UPDATE_STEEPEST_ASCENT)
+        return model == RETINA_VELO_SLOPES
+                   ? launch_batched_w<RETINA_VELO_SLOPES, 1, RETINA_UPDATE_STEEPEST_ASCENT>(warps, a, prm, ctas, st)
+                   : launch_batched_w<RETINA_TOY2D, 1, RETINA_UPDATE_STEEPEST_ASCENT>(warps, a, prm, ctas, st);
+    if (o->update == RETINA_UPDATE_MODIFIED_NEWTON)
+        return model == RETINA_VELO_SLOPES
+                   ? launch_batched_w<RETINA_VELO_SLOPES, 1, RETINA_UPDATE_MODIFIED_NEWTON>(warps, a, prm, ctas, st)
+                   : launch_batched_w<RETINA_TOY2D, 1, RETINA_UPDATE_MODIFIED_NEWTON>(warps, a, prm, ctas, st);
 #define RETINA_BATCH_CASE(M, PP) return launch_batched_w<M, PP>(warps, a, prm, ctas, st)
     if (model == RETINA_VELO_SLOPES) {
         if (seeds_per_warp >= 4) RETINA_BATCH_CASE(RETINA_VELO_SLOPES, 4);

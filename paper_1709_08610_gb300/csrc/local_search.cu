@@ -8,7 +8,7 @@ namespace retina {
 
 // One warp owns P consecutive seeds; WARPS warps per CTA share the hits of
 // the CTA's event (blockIdx.y), staged once.
-template <int MODEL, int P, int WARPS>
+template <int MODEL, int P, int WARPS, int UPD>
 __global__ void __launch_bounds__(WARPS * 32)
 local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
                     const float4 *__restrict__ boxes, int n_seeds, const float *__restrict__ seeds, LsParams prm,
@@ -38,7 +38,7 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     if (s_first >= n_seeds) return;
     const int n_live = n_seeds - s_first < P ? n_seeds - s_first : P;
     const int64_t o = (int64_t)e * n_seeds + s_first;
-    search_group<MODEL, P>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, kept_list(sh, smem_hits, warp), seeds + 2 * o,
+    search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, kept_list(sh, smem_hits, warp), seeds + 2 * o,
                            n_live, prm, theta_out + 2 * o, R_out + o,
                            status + o, n_evals ? n_evals + o : nullptr, work);
 }
@@ -91,7 +91,6 @@ response_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box) {
     LsParams prm;
     prm.q = o->q;
-    prm.update = o->update;
     for (int j = 0; j < RETINA_MAX_Q; ++j) {
         const double s = j < o->q ? (double)o->sigma[j] : 1.0;
         prm.kk[j] = (float)(kLog2e / (s * s));
@@ -105,35 +104,34 @@ LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box) {
     return prm;
 }
 
-template <int MODEL, int P, int WARPS>
+template <int MODEL, int P, int WARPS, int UPD>
 static cudaError_t launch_ls_t(const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
                                int n_events, int n_seeds, const float *seeds, const LsParams &prm, int smem_hits,
                                float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
+    auto kern = local_search_kernel<MODEL, P, WARPS, UPD>;
     const size_t smem = search_smem_bytes(smem_hits, boxes != nullptr, WARPS);
-    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(local_search_kernel<MODEL, P, WARPS>), smem);
+    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (aerr != cudaSuccess) return aerr;
     const int per_block = WARPS * P;
     dim3 grid((n_seeds + per_block - 1) / per_block, n_events);
-    local_search_kernel<MODEL, P, WARPS><<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, boxes, n_seeds, seeds,
-                                                                          prm,
-                                                                          smem_hits, theta_out, R_out, status,
-                                                                          n_evals, work_counters());
+    kern<<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, boxes, n_seeds, seeds, prm, smem_hits, theta_out, R_out,
+                                         status, n_evals, work_counters());
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int MODEL, int P>
+template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 static cudaError_t launch_ls_w(int warps, const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
                                int n_events, int n_seeds, const float *seeds, const LsParams &prm, int smem_hits,
                                float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
     if (warps >= 16)
-        return launch_ls_t<MODEL, P, 16>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits,
-                                         theta_out, R_out, status, n_evals, st);
+        return launch_ls_t<MODEL, P, 16, UPD>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits,
+                                              theta_out, R_out, status, n_evals, st);
     if (warps >= 8)
-        return launch_ls_t<MODEL, P, 8>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out,
-                                        R_out, status, n_evals, st);
-    return launch_ls_t<MODEL, P, 4>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out,
-                                    R_out, status, n_evals, st);
+        return launch_ls_t<MODEL, P, 8, UPD>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits,
+                                             theta_out, R_out, status, n_evals, st);
+    return launch_ls_t<MODEL, P, 4, UPD>(hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits,
+                                         theta_out, R_out, status, n_evals, st);
 }
 
 cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_t *off, const float4 *boxes,
@@ -143,6 +141,20 @@ cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_
     LsParams prm = make_ls_params(o, box);
     if (smem_hits < 0) smem_hits = 0;
     if (smem_hits > 12288) smem_hits = 12288;
+    // the comparison updates run one seed per warp (the same results as any
+    // other grouping), which keeps their instantiations few
+#define RETINA_LS_ALT(M, U)                                                                                           \
+    return launch_ls_w<M, 1, U>(warps, hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out, \
+                                R_out, status, n_evals, st)
+    if (o->update == RETINA_UPDATE_STEEPEST_ASCENT) {
+        if (model == RETINA_VELO_SLOPES) RETINA_LS_ALT(RETINA_VELO_SLOPES, RETINA_UPDATE_STEEPEST_ASCENT);
+        RETINA_LS_ALT(RETINA_TOY2D, RETINA_UPDATE_STEEPEST_ASCENT);
+    }
+    if (o->update == RETINA_UPDATE_MODIFIED_NEWTON) {
+        if (model == RETINA_VELO_SLOPES) RETINA_LS_ALT(RETINA_VELO_SLOPES, RETINA_UPDATE_MODIFIED_NEWTON);
+        RETINA_LS_ALT(RETINA_TOY2D, RETINA_UPDATE_MODIFIED_NEWTON);
+    }
+#undef RETINA_LS_ALT
 #define RETINA_LS_CASE(M, PP)                                                                                     \
     return launch_ls_w<M, PP>(warps, hits, n_hits, off, boxes, n_events, n_seeds, seeds, prm, smem_hits, theta_out, \
                               R_out, status, n_evals, st)

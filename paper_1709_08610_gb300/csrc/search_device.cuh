@@ -213,13 +213,15 @@ __device__ __forceinline__ void modified_newton(float g0, float g1, float H00, f
     p1 = (a2 * sg1 - b * sg0) / det;
 }
 
-// The direction of one update (retina_ls_opts.update; warp-uniform).
-__device__ __forceinline__ void update_direction(int update, float g0, float g1, float H00, float H01, float H11,
-                                                 float &p0, float &p1) {
-    if (update == RETINA_UPDATE_STEEPEST_ASCENT) {
+// The direction of one update (RETINA_UPDATE_*), chosen at compile time so
+// that the truncated Newton search compiles exactly as without the others.
+template <int UPD>
+__device__ __forceinline__ void update_direction(float g0, float g1, float H00, float H01, float H11, float &p0,
+                                                 float &p1) {
+    if constexpr (UPD == RETINA_UPDATE_STEEPEST_ASCENT) {
         p0 = g0;
         p1 = g1;
-    } else if (update == RETINA_UPDATE_MODIFIED_NEWTON) {
+    } else if constexpr (UPD == RETINA_UPDATE_MODIFIED_NEWTON) {
         modified_newton(g0, g1, H00, H01, H11, p0, p1);
     } else {
         newton_cg(g0, g1, H00, H01, H11, p0, p1);
@@ -228,7 +230,6 @@ __device__ __forceinline__ void update_direction(int update, float g0, float g1,
 
 struct LsParams {
     int q;
-    int update;  // RETINA_UPDATE_*
     float kk[RETINA_MAX_Q];  // log2(e) / sigma_j^2
     float k[RETINA_MAX_Q];   // 1 / sigma_j^2
     float cull[RETINA_MAX_Q];  // CULL_EXPONENT / kk[j]: skipping threshold on |z|min^2 dist^2
@@ -433,7 +434,7 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
 // when it is skippable at both bandwidths, so each sum gets exactly the terms
 // of its own pass plus exact zeros, in the same per-lane order: every result,
 // status and trial count is bitwise search_group's.
-template <int MODEL>
+template <int MODEL, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                            int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
                                            const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
@@ -467,7 +468,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         have = false;
         float R, g0, g1, H00, H01, H11, pp0, pp1;
         sums_to_rgh<MODEL>(S, k, R, g0, g1, H00, H01, H11);
-        update_direction(prm.update, g0, g1, H00, H01, H11, pp0, pp1);
+        update_direction<UPD>(g0, g1, H00, H01, H11, pp0, pp1);
         const float cells = fmaxf(fabsf(pp0) / prm.box.step0, fabsf(pp1) / prm.box.step1);
         if (cells > prm.cap) {
             const float sc = prm.cap / cells;
@@ -554,7 +555,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
 // at bandwidth sigma_j), then R(theta_q; sigma_q), status and the number of
 // R-only passes.  seeds / outputs point at the group's first seed; only the
 // first n_live (<= P) seeds exist.  Warp-uniform control flow throughout.
-template <int MODEL, int P>
+template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
                                              int n_staged, int H, int lane, const float4 *__restrict__ sbox,
                                              const float *__restrict__ sz2, const float4 *__restrict__ gbox,
@@ -564,7 +565,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
                                              uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work) {
     if constexpr (P == 1) {
-        search_one<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, seeds, prm, theta_out, R_out,
+        search_one<MODEL, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, seeds, prm, theta_out, R_out,
                           status, n_evals, work);
         return;
     }
@@ -621,7 +622,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             for (int i = 0; i < NS; ++i) S[p][i] = warp_sum(S[p][i]);
             float H00, H01, H11;
             sums_to_rgh<MODEL>(S[p], k, R[p], g0[p], g1[p], H00, H01, H11);
-            update_direction(prm.update, g0[p], g1[p], H00, H01, H11, pp0[p], pp1[p]);
+            update_direction<UPD>(g0[p], g1[p], H00, H01, H11, pp0[p], pp1[p]);
             const float cells = fmaxf(fabsf(pp0[p]) / prm.box.step0, fabsf(pp1[p]) / prm.box.step1);
             if (cells > prm.cap) {
                 const float sc = prm.cap / cells;

@@ -66,13 +66,17 @@ def _check(wl, ev, sigma, step, th_g, R_g, st_g, th_o, R_o, st_o, m_o):
         o = oracle.rgh(ev.hits, wl.model, th_o[i], sigma)
         H, g = o["hess"], o["grad"]
         conv = False
-        if np.all(np.linalg.eigvalsh(H) < 0):
-            conv = np.max(np.abs(np.linalg.solve(H, g)) / step) <= 0.05
+        try:
+            if np.all(np.linalg.eigvalsh(H) < 0):
+                Hi = np.linalg.inv(H)
+                conv = np.max(np.abs(Hi @ g) / step) <= 0.05
+        except np.linalg.LinAlgError:  # numerically singular: a flat ridge, not a converged peak
+            conv = False
         if not conv and not robust[i]:
             continue
         n_conv += conv
         if conv:
-            d = np.maximum(TH_CELLS * step, np.abs(np.linalg.inv(H)) @ (GH_REL * o["grad_abs"]))
+            d = np.maximum(TH_CELLS * step, np.abs(Hi) @ (GH_REL * o["grad_abs"]))
         else:
             d = 50 * TH_CELLS * step
         assert np.all(np.abs(th_g[i] - th_o[i]) <= d), (i, conv, (th_g[i] - th_o[i]) / step)
