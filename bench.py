@@ -478,6 +478,70 @@ def alpha_sweep(rt, stream, flush, reps: int = 3):
             "runs": out, "l2": "flushed before each replay"}
 
 
+SVELO_MULTIPLICITIES = (50, 100, 150, 200, 250, 300, 350)
+
+
+def svelo_sweep(rt, stream, flush, reps: int = 3):
+    """The paper's experiment in its own geometry: sVELO events (20 disks,
+    eta ~ U[1, 6], p_hit 0.5, Poisson(250) noise) with 50 to 350
+    reconstructible tracks; a track counts as found when an estimate lies
+    within 1e-3 rad of it in the paper's two angles.  Methods: the 2048^2 grid
+    scan (plain and refined) and Algorithm 1 from uniform seeds at the
+    paper's budgets n = alpha n_grid / (C0 q), C0 = 30, q = 3, with n_grid
+    the cells of side 1e-3 rad over the angular acceptance (|angle| <= 0.705
+    rad, the eta = 1 edge)."""
+    import torch
+    from paper_1709_08610_gb300.pipeline import BatchTracker, GridScanBatch, efficiency_by_multiplicity, \
+        match_efficiency
+    from synth import slopes_to_angles
+    wl = WORKLOADS["svelo"]
+    E = BATCH_EVENTS
+    mult = [SVELO_MULTIPLICITIES[e % len(SVELO_MULTIPLICITIES)] for e in range(E)]
+    evs = [make_event(wl, BATCH_RUN_SEED + 2, e, n_tracks=mult[e]) for e in range(E)]
+    b = batch_of(evs)
+    truth = [slopes_to_angles(ev.truth[:, 0], ev.truth[:, 1]) for ev in evs]
+    H = b.hits.shape[0]
+    box = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    edges = list(SVELO_MULTIPLICITIES) + [SVELO_MULTIPLICITIES[-1] + 1]
+    n_grid = (2 * 0.705 / 1e-3) ** 2
+    runs = [("grid_scan_2048x2048", lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
+            ("grid_scan_2048x2048_refined", lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0, refine_iters=4),
+             None)]
+    for alpha, tag in ((1.0 / 3.0, "1/3"), (0.1, "1/10")):
+        n = int(round(alpha * n_grid / (30 * 3)))
+        runs.append(("alpha_%s_uniform_%d" % (tag, n), lambda n=n: BatchTracker(E, H, n, box, opts, wl.R0, **shape),
+                     np.stack([uniform_seeds(wl, n, BATCH_RUN_SEED + 2, e) for e in range(E)])))
+    out = {}
+    for name, make, seeds in runs:
+        obj = make()
+        obj.load(b.hits, b.offsets, seeds)
+        obj.capture()
+        obj.replay()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            obj.replay()
+            c.record(stream)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        found = [slopes_to_angles(f[:, 0], f[:, 1]) if len(f) else np.zeros((0, 2)) for f in obj.results()]
+        eff, fakes = match_efficiency(found, truth)
+        by = efficiency_by_multiplicity(found, truth, edges)
+        out[name] = {"events_per_s": E / (statistics.median(ts) * 1e-3), "efficiency": eff,
+                     "fakes_per_event": fakes / E,
+                     "efficiency_by_tracks": {k.split("-")[0]: round(v["efficiency"], 4) for k, v in by.items()}}
+        del obj
+        torch.cuda.empty_cache()
+    return {"workload": "%d sVELO events (20 disks 8-42 mm over 700 mm, eta ~ U[1, 6], p_hit 0.5, Poisson(250) "
+                        "noise), %s reconstructible tracks (equal shares), %d hits; found = within 1e-3 rad in "
+                        "the paper's angles" % (E, "/".join(str(m) for m in SVELO_MULTIPLICITIES), H),
+            "runs": out, "l2": "flushed before each replay"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -909,7 +973,7 @@ def main():
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
-    batched = stress = alpha = None
+    batched = stress = alpha = svelo = None
     if world == 1 and not args.no_batched:
         # launch shapes tuned for one event do not carry over to 1024: the grid's
         # hit-slice count goes back to the library's rule (one slice at this
@@ -919,6 +983,7 @@ def main():
         rt.set_option(rt.OPT_BATCH_CTAS, 0)
         batched = batched_methods(rt, stream, flush, comparisons=True)
         alpha = alpha_sweep(rt, stream, flush)
+        svelo = svelo_sweep(rt, stream, flush)
         stress = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
         for o, v in saved.items():
             rt.set_option(o, v)
@@ -945,7 +1010,7 @@ def main():
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},
             "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0, "batched": batched,
-            "batched_stress": stress, "alpha_sweep": alpha,
+            "batched_stress": stress, "alpha_sweep": alpha, "svelo_sweep": svelo,
             "tuned": tuned,
         }
         print(json.dumps(line), flush=True)

@@ -12,6 +12,9 @@ from .events import (  # noqa: F401
     Workload,
     WORKLOADS,
     VELO_PLANES_Z,
+    SVELO_PLANES_Z,
+    make_svelo_event,
+    slopes_to_angles,
     make_toy2d_event,
     make_velo_event,
     make_event,

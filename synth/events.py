@@ -34,6 +34,10 @@ STREAM_SEEDS = 1
 
 # 26 equally spaced layers covering z in [-300, 750] mm inclusive (42 mm pitch).
 VELO_PLANES_Z = np.array([-300.0 + 42.0 * p for p in range(26)], dtype=np.float64)
+# The paper's sVELO: 20 disk layers equally spaced within 700 mm (read as z = 35, 70, ..., 700 mm,
+# none at the vertex), each an annulus 8 mm <= r <= 42 mm.
+SVELO_PLANES_Z = np.array([35.0 * (p + 1) for p in range(20)], dtype=np.float64)
+SVELO_R_INNER, SVELO_R_OUTER = 8.0, 42.0
 TOY_PLANES_X = np.arange(1, 11, dtype=np.float64)
 
 
@@ -207,9 +211,78 @@ def close_tracks_event(run_seed: int = 0, smear: float = 1e-2, n_planes: int = 2
     return Event(MODEL_TOY2D, hits, np.concatenate(ls).astype(np.int32), truth)
 
 
+def slopes_to_angles(u, v) -> np.ndarray:
+    """The paper's two angles (x = t sin(theta), y = t cos(theta) sin(phi),
+    z = t cos(theta) cos(phi)) of the lines through the origin with slopes
+    (u, v) = (x / z, y / z), z > 0; returns [..., 2] = (theta, phi)."""
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    n = np.sqrt(1.0 + u * u + v * v)
+    return np.stack([np.arcsin(u / n), np.arctan2(v, np.ones_like(v))], -1)
+
+
+def make_svelo_event(run_seed: int, event_id: int, n_tracks: int = 200, p_hit: float = 0.5,
+                     hit_sigma: float = 0.01, eta_range: Tuple[float, float] = (1.0, 6.0),
+                     noise_mean: float = 250.0, n_min: int = 2,
+                     planes_z: Sequence[float] = SVELO_PLANES_Z) -> Event:
+    """The paper's sVELO event (Section 4): straight tracks from the origin
+    with pseudo-rapidity eta ~ U[1, 6] and azimuth phi ~ U[0, 2 pi); each
+    disk layer (8 <= r <= 42 mm) a track crosses records a hit with
+    probability p_hit, x and y measured with N(0, hit_sigma) errors; a track
+    with fewer than n_min hits is undetectable and its hits count as noise;
+    Poisson(noise_mean) noise hits, each on a uniformly chosen layer and
+    uniform over the annulus.  Tracks are drawn until ``n_tracks`` of them are
+    reconstructible (>= n_min hits); only those are truth tracks, as slopes
+    (u, v) = (x / z, y / z) in columns 0-1 (use slopes_to_angles for the
+    paper's angles) and their hit count in column 5."""
+    rng = _rng(run_seed, event_id, STREAM_EVENT)
+    pz = np.asarray(planes_z, dtype=np.float64)
+    r2_in, r2_out = SVELO_R_INNER ** 2, SVELO_R_OUTER ** 2
+    xs, ys, zs, ls, truth = [], [], [], [], []
+    n_rec = 0
+    for _ in range(100 * max(int(n_tracks), 1) + 1000):
+        if n_rec >= n_tracks:
+            break
+        eta = rng.uniform(eta_range[0], eta_range[1])
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        tan_p = math.tan(2.0 * math.atan(math.exp(-eta)))
+        u, v = tan_p * math.cos(phi), tan_p * math.sin(phi)
+        r = tan_p * pz
+        inside = (r * r >= r2_in) & (r * r <= r2_out)
+        fired = inside & (rng.uniform(0.0, 1.0, pz.size) < p_hit)
+        err = rng.normal(0.0, hit_sigma, (pz.size, 2))
+        k = np.flatnonzero(fired)
+        rec = k.size >= n_min
+        xs.append(u * pz[k] + err[k, 0])
+        ys.append(v * pz[k] + err[k, 1])
+        zs.append(pz[k])
+        ls.append(np.full(k.size, n_rec if rec else -1, dtype=np.int64))
+        if rec:
+            truth.append((u, v, 0.0, 0.0, 0.0, float(k.size)))
+            n_rec += 1
+    n_noise = int(rng.poisson(noise_mean))
+    nz = pz[rng.integers(0, pz.size, n_noise)]
+    nr = np.sqrt(rng.uniform(r2_in, r2_out, n_noise))
+    na = rng.uniform(0.0, 2.0 * math.pi, n_noise)
+    xs.append(nr * np.cos(na))
+    ys.append(nr * np.sin(na))
+    zs.append(nz)
+    ls.append(-np.ones(n_noise, dtype=np.int64))
+    xs, ys, zs, labels = (np.concatenate(a) for a in (xs, ys, zs, ls))
+    perm = rng.permutation(xs.size)
+    hits = np.zeros((xs.size, 4), dtype=np.float32)
+    hits[:, 0] = xs[perm]
+    hits[:, 1] = ys[perm]
+    hits[:, 2] = zs[perm]
+    tr = np.array(truth, dtype=np.float64).reshape(-1, 6)
+    return Event(MODEL_VELO_SLOPES, hits, labels[perm].astype(np.int32), tr)
+
+
 def make_event(wl: Workload, run_seed: int, event_id: int, **over) -> Event:
     kw = dict(wl.gen)
     kw.update(over)
+    if kw.pop("generator", None) == "svelo":
+        return make_svelo_event(run_seed, event_id, **kw)
     if wl.model == MODEL_TOY2D:
         return make_toy2d_event(run_seed, event_id, **kw)
     return make_velo_event(run_seed, event_id, **kw)
@@ -289,6 +362,14 @@ WORKLOADS: Dict[str, Workload] = {
         sigma_grid=2.0 ** -10 * _z_rms(), sigma_schedule=_VELO_SCHEDULE,
         R0=0.5 * 26 * 0.9, n_seeds=4096, n_events=1024,
         gen=dict(n_tracks=(150, 20, 400))),
+    # The paper's sVELO (20 disks, eta ~ U[1, 6], p_hit 0.5, Poisson(250) noise), slopes up to
+    # tan(2 atan(e^-1)) = 0.85; 2048^2 grid over [-1, 1]^2; R0 keeps lines through >= 2 hits.
+    "svelo": Workload(
+        name="svelo", model=MODEL_VELO_SLOPES,
+        grid_lo=(-1.0, -1.0), grid_step=(2.0 ** -10, 2.0 ** -10), grid_n=(2048, 2048),
+        sigma_grid=2.0 ** -10 * float(math.sqrt(np.mean(SVELO_PLANES_Z ** 2))), sigma_schedule=_VELO_SCHEDULE,
+        R0=1.5, n_seeds=4096, n_events=1024,
+        gen=dict(generator="svelo", n_tracks=200)),
     # High multiplicity: ~600 tracks/event, 15 % noise, 2048^2 grid.
     "velo_stress": Workload(
         name="velo_stress", model=MODEL_VELO_SLOPES,

@@ -355,6 +355,18 @@ def test_local_search_alternative_updates_match_oracle(rt, update, wl_name):
     assert same >= 0.8 * conv, (same, conv)
 
 
+def test_local_search_svelo_matches_oracle(rt):
+    # the paper's own sVELO geometry (20 disks, p_hit 0.5, Poisson(250) noise)
+    wl = WORKLOADS["svelo"]
+    ev = make_event(wl, 0, 0)
+    rng = np.random.default_rng(7)
+    near = ev.truth[:, :2][rng.integers(0, len(ev.truth), 600)] + rng.normal(0, 3, (600, 2)) * 2 ** -10
+    seeds = np.concatenate([near, uniform_seeds(wl, 301, 0, 0)]).astype(np.float32)
+    res = _search_both(rt, wl, ev, seeds)
+    _, n_conv = _check_search(wl, ev, *res, min_robust=450)
+    assert n_conv >= 100
+
+
 def test_local_search_hits_beyond_shared_memory(rt):
     # hits past the staged capacity are read from global memory: same results
     wl = WORKLOADS["velo"]
