@@ -363,8 +363,8 @@ def test_local_search_svelo_matches_oracle(rt):
     near = ev.truth[:, :2][rng.integers(0, len(ev.truth), 600)] + rng.normal(0, 3, (600, 2)) * 2 ** -10
     seeds = np.concatenate([near, uniform_seeds(wl, 301, 0, 0)]).astype(np.float32)
     res = _search_both(rt, wl, ev, seeds)
-    _, n_conv = _check_search(wl, ev, *res, min_robust=450)
-    assert n_conv >= 100
+    _, n_conv = _check_search(wl, ev, *res, min_robust=400)  # the oracle finds 447 robust, 179 converged
+    assert n_conv >= 150
 
 
 def test_local_search_hits_beyond_shared_memory(rt):
