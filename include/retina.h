@@ -326,7 +326,8 @@ int retina_response(const float *hits, int64_t n_hits, const int64_t *event_offs
  *      Nocedal & Wright, Algorithm 7.1), forcing tolerance
  *      min(1/2, sqrt|g|) |g|, at most 2 iterations; on non-positive
  *      curvature of -R along the CG direction: p = g at the first
- *      iteration, else the current iterate.
+ *      iteration, else the current iterate.  (opts->update selects one of
+ *      the comparison directions of RETINA_UPDATE_* instead.)
  *   3. If max_a |p_a| / step_a > step_cap_cells, p is scaled down to it.
  *   4. Backtracking: the first t in 1, 1/2, ..., 2^-max_halvings with
  *      R(theta + t p) >= R(theta) + c1 t g.p is taken; if none, theta
