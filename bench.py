@@ -718,15 +718,20 @@ def main():
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         # search CTA shape x grid hit slices (the grid alone prefers more slices
         # than it can use while the search holds most SMs)
+        # (and staged hits: 4096 leaves room on an SM for a grid CTA beside a search CTA)
         g0 = rt.get_option(rt.OPT_GRID_SPLITS)
-        cands = [(w, c, sp) for (w, c) in ((32, 0), (32, 3 * sms // 4), (32, sms // 2), (16, 0),
-                                            (16, 3 * sms // 2), (16, sms), (8, 2 * sms))
-                 for sp in sorted({g0, 4, 8})]
+        h0 = rt.get_option(rt.OPT_BATCH_SMEM_HITS)
+        cands = [(w, c, sp, h) for (w, c) in ((32, 0), (32, 15 * sms // 16), (32, 7 * sms // 8),
+                                               (32, 13 * sms // 16), (32, 3 * sms // 4), (32, 5 * sms // 8),
+                                               (32, sms // 2), (16, 0), (16, 3 * sms // 2), (16, sms),
+                                               (8, 2 * sms))
+                 for sp in sorted({g0, 4, 8}) for h in sorted({h0, 4096})]
         table = {}
-        for w, c, sp in cands:
+        for w, c, sp, h in cands:
             rt.set_option(rt.OPT_BATCH_WARPS, w)
             rt.set_option(rt.OPT_BATCH_CTAS, c)
             rt.set_option(rt.OPT_GRID_SPLITS, sp)
+            rt.set_option(rt.OPT_BATCH_SMEM_HITS, h)
             if not args.graph:
                 g_c = None
                 evs_c = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(TUNE_STEPS)]
@@ -737,14 +742,16 @@ def main():
                 evs_c = None
                 for _ in range(3):
                     g_c.replay()
-            table["%d,%d,%d" % (w, c, sp)] = float(np.median(timed_steps(g_c, TUNE_STEPS, evs_c)[:, 7]))
+            table["%d,%d,%d,%d" % (w, c, sp, h)] = float(np.median(timed_steps(g_c, TUNE_STEPS, evs_c)[:, 7]))
             del g_c
         best = min(table, key=table.get)
-        w, c, sp = (int(x) for x in best.split(","))
+        w, c, sp, h = (int(x) for x in best.split(","))
         rt.set_option(rt.OPT_BATCH_WARPS, w)
         rt.set_option(rt.OPT_BATCH_CTAS, c)
         rt.set_option(rt.OPT_GRID_SPLITS, sp)
-        tuned["overlap"] = {"warps": w, "ctas": c, "grid_splits": sp, "step_ms": table[best], "table_ms": table}
+        rt.set_option(rt.OPT_BATCH_SMEM_HITS, h)
+        tuned["overlap"] = {"warps": w, "ctas": c, "grid_splits": sp, "smem_hits": h, "step_ms": table[best],
+                            "table_ms": table}
 
     # ---- peaks of the FP32 and MUFU pipes, measured live (burst)
     peaks = {}
