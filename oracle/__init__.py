@@ -21,6 +21,9 @@ Functions and the passages they follow (arXiv:1709.08610):
   updates at the grid's bandwidth started from each maximum's cell centre.
 * :func:`extract_tracks` - the last two lines of Algorithm 1: cluster the
   converged points and keep the best of each cluster above R0.
+* :func:`rgh4`, :func:`response4`, :func:`local_search4` - Eq. 1, its
+  derivatives and Algorithm 1's truncated-Newton updates for a four-parameter
+  straight track (x0, y0, t_x, t_y) that need not pass through the origin.
 """
 from __future__ import annotations
 
@@ -83,6 +86,10 @@ def lib():
             L.or_local_search.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, P, P, P, P]
             L.or_extract_tracks.argtypes = [P, P, P, I64, P, D, D, P, I64]
             L.or_extract_tracks.restype = I64
+            L.or_rgh4.argtypes = [P, I64, P, D, P]
+            L.or_response4.argtypes = [P, I64, P, D]
+            L.or_response4.restype = D
+            L.or_local_search4.argtypes = [P, I64, P, I64, P, P, P, P, P]
             _LIB = L
     return _LIB
 
@@ -195,6 +202,68 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     m = np.zeros(ns)
     lib().or_local_search(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
                           _ptr(th), _ptr(R), _ptr(st), _ptr(m))
+    return th, R, st, m
+
+
+class _Ls4Opts(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_double * 8), ("c1", ctypes.c_double),
+                ("max_halvings", ctypes.c_int32), ("scale", ctypes.c_double * 4), ("step_cap", ctypes.c_double)]
+
+
+_TRI4 = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+
+
+def _sym4(v) -> np.ndarray:
+    H = np.zeros((4, 4))
+    for i, (a, b) in enumerate(_TRI4):
+        H[a, b] = H[b, a] = v[i]
+    return H
+
+
+def rgh4(hits, theta, sigma: float) -> dict:
+    """R, grad R [4], Hess R [4, 4] of the four-parameter track (x0, y0, t_x,
+    t_y), crossing the layer z at (x0 + t_x z, y0 + t_y z) (Eq. 1)."""
+    h = _hits(hits)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(4)
+    out = np.zeros(29)
+    lib().or_rgh4(_ptr(h), h.shape[0], _ptr(th), float(sigma), _ptr(out))
+    return dict(R=out[0], grad=out[1:5].copy(), hess=_sym4(out[5:15]), grad_abs=out[15:19].copy(),
+                hess_abs=_sym4(out[19:29]))
+
+
+def response4(hits, theta, sigma: float) -> float:
+    h = _hits(hits)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(4)
+    return lib().or_response4(_ptr(h), h.shape[0], _ptr(th), float(sigma))
+
+
+def local_search4(hits, seeds, sigma_schedule: Sequence[float], scale: Sequence[float], step_cap: float = 4.0,
+                  c1: float = 1e-4, max_halvings: int = 8):
+    """Algorithm 1's q truncated-Newton updates (Newton-CG in four dimensions,
+    at most four CG iterations) for four-parameter seeds [n, 4]; the step is
+    capped to max_a |p_a| / scale_a <= step_cap.
+
+    Returns (theta [n, 4] float64, R_final [n], status [n] uint8, margin [n]).
+    """
+    h = _hits(hits)
+    s = np.ascontiguousarray(seeds, dtype=np.float32).reshape(-1, 4)
+    o = _Ls4Opts()
+    o.q = len(sigma_schedule)
+    if not 1 <= o.q <= 8:
+        raise ValueError("1 <= q <= 8")
+    for j, v in enumerate(sigma_schedule):
+        o.sigma[j] = float(v)
+    o.c1 = float(c1)
+    o.max_halvings = int(max_halvings)
+    for a in range(4):
+        o.scale[a] = float(scale[a])
+    o.step_cap = float(step_cap)
+    ns = s.shape[0]
+    th = np.zeros((ns, 4))
+    R = np.zeros(ns)
+    st = np.zeros(ns, dtype=np.uint8)
+    m = np.zeros(ns)
+    lib().or_local_search4(_ptr(h), h.shape[0], _ptr(s), ns, ctypes.byref(o), _ptr(th), _ptr(R), _ptr(st), _ptr(m))
     return th, R, st, m
 
 

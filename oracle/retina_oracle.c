@@ -430,3 +430,199 @@ int64_t or_extract_tracks(const double *theta, const double *R, const uint8_t *s
     free(cand);
     return nk;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Four-parameter straight track: a line that need not pass through the     */
+/* origin, so a vertex displaced along z (or across it) is representable.   */
+/*   theta = (x0, y0, t_x, t_y): the track crosses the layer z = const at     */
+/*   (x0 + t_x z, y0 + t_y z), so r = (x - x0 - t_x z, y - y0 - t_y z) and     */
+/*   dr/dtheta = -[[1, 0, z, 0], [0, 1, 0, z]]; with J = -dr/dtheta the        */
+/*   derivatives of Eq. 1 take the same form as above:                        */
+/*     grad R = (2 / sigma^2) sum_k e_k J_k^T r_k                             */
+/*     Hess R = sum_k e_k [ (4 / sigma^4) (J_k^T r_k)(J_k^T r_k)^T             */
+/*                          - (2 / sigma^2) J_k^T J_k ].                      */
+/* ------------------------------------------------------------------------ */
+
+/* Upper-triangle index of (a, b), a <= b, in the order 00 01 02 03 11 12 13 22 23 33. */
+static int tri4(int a, int b) {
+    static const int base[4] = {0, 4, 7, 9};
+    return base[a] + (b - a);
+}
+
+/*
+ * out[0] = R, out[1..4] = grad, out[5..14] = Hess (upper triangle, tri4
+ * order), out[15..18] = sum of |gradient terms|, out[19..28] = sum of
+ * |Hessian terms| (the scales of the FP32 parity tolerances).
+ */
+void or_rgh4(const float *hits, int64_t n_hits, const double th[4], double sigma, double *out) {
+    const double k = 1.0 / (sigma * sigma);
+    memset(out, 0, sizeof(double) * 29);
+    for (int64_t i = 0; i < n_hits; ++i) {
+        const float *h = hits + 4 * i;
+        const double z = (double)h[2];
+        const double r[2] = {(double)h[0] - th[0] - th[2] * z, (double)h[1] - th[1] - th[3] * z};
+        const double e = exp(-(r[0] * r[0] + r[1] * r[1]) * k);
+        /* J^T r and J^T J with J = [[1, 0, z, 0], [0, 1, 0, z]] */
+        const double Jr[4] = {r[0], r[1], z * r[0], z * r[1]};
+        double JJ[4][4] = {{1.0, 0.0, z, 0.0}, {0.0, 1.0, 0.0, z}, {z, 0.0, z * z, 0.0}, {0.0, z, 0.0, z * z}};
+        out[0] += e;
+        for (int a = 0; a < 4; ++a) {
+            const double t = 2.0 * k * e * Jr[a];
+            out[1 + a] += t;
+            out[15 + a] += fabs(t);
+        }
+        for (int a = 0; a < 4; ++a)
+            for (int b = a; b < 4; ++b) {
+                const double t1 = 4.0 * k * k * e * Jr[a] * Jr[b];
+                const double t2 = 2.0 * k * e * JJ[a][b];
+                out[5 + tri4(a, b)] += t1 - t2;
+                out[19 + tri4(a, b)] += fabs(t1) + fabs(t2);
+            }
+    }
+}
+
+double or_response4(const float *hits, int64_t n_hits, const double th[4], double sigma) {
+    const double k = 1.0 / (sigma * sigma);
+    double R = 0.0;
+    for (int64_t i = 0; i < n_hits; ++i) {
+        const float *h = hits + 4 * i;
+        const double z = (double)h[2];
+        const double r0 = (double)h[0] - th[0] - th[2] * z, r1 = (double)h[1] - th[1] - th[3] * z;
+        R += exp(-(r0 * r0 + r1 * r1) * k);
+    }
+    return R;
+}
+
+typedef struct {
+    int32_t q;             /* updates per seed                                   */
+    double sigma[8];       /* bandwidth at update j                              */
+    double c1;             /* Armijo sufficient-increase constant                */
+    int32_t max_halvings;  /* backtracking halvings after the unit step          */
+    double scale[4];       /* unit of each parameter for the step cap            */
+    double step_cap;       /* cap on max_a |p_a| / scale_a                        */
+} or_ls4_opts;
+
+static double sym4(const double *Hu, int a, int b) { return a <= b ? Hu[tri4(a, b)] : Hu[tri4(b, a)]; }
+
+/*
+ * Newton-CG direction in four dimensions (Nocedal & Wright, Algorithm 7.1)
+ * for maximising R: CG on B p = g with B = -Hess R from p = 0, forcing
+ * tolerance min(1/2, sqrt|g|) |g|, at most 4 iterations (the dimension);
+ * non-positive curvature along d returns g at the first iteration, else
+ * the current iterate.  *margin as for the 2D direction.
+ */
+static void newton_cg_direction4(const double g[4], const double Hu[10], const double gabs[4],
+                                 const double Habs[10], double p[4], double *margin) {
+    double B[4][4], hscale = 0.0, gsum = 0.0;
+    for (int a = 0; a < 4; ++a) {
+        gsum += gabs[a];
+        for (int b = 0; b < 4; ++b) {
+            B[a][b] = -sym4(Hu, a, b);
+            hscale += sym4(Habs, a, b);
+        }
+    }
+    double gn = 0.0;
+    for (int a = 0; a < 4; ++a) gn += g[a] * g[a];
+    gn = sqrt(gn);
+    const double eps = fmin(0.5, sqrt(gn)) * gn;
+    double z[4] = {0, 0, 0, 0}, r[4], d[4];
+    for (int a = 0; a < 4; ++a) {
+        r[a] = -g[a];
+        d[a] = g[a];
+    }
+    for (int it = 0; it < 4; ++it) {
+        double Bd[4], dBd = 0.0, dd = 0.0;
+        for (int a = 0; a < 4; ++a) {
+            Bd[a] = 0.0;
+            for (int b = 0; b < 4; ++b) Bd[a] += B[a][b] * d[b];
+            dBd += d[a] * Bd[a];
+            dd += d[a] * d[a];
+        }
+        {
+            const double tol = 1e-4 * hscale * dd;
+            const double m = tol > 0.0 ? fabs(dBd) / tol : 0.0;
+            if (m < *margin) *margin = m;
+        }
+        if (dBd <= 0.0) {
+            for (int a = 0; a < 4; ++a) p[a] = it == 0 ? g[a] : z[a];
+            return;
+        }
+        double rr = 0.0;
+        for (int a = 0; a < 4; ++a) rr += r[a] * r[a];
+        const double alpha = rr / dBd;
+        double rn[4], rnn2 = 0.0;
+        for (int a = 0; a < 4; ++a) {
+            z[a] += alpha * d[a];
+            rn[a] = r[a] + alpha * Bd[a];
+            rnn2 += rn[a] * rn[a];
+        }
+        {
+            const double tol = 1e-4 * gsum;
+            const double m = tol > 0.0 ? fabs(sqrt(rnn2) - eps) / tol : 0.0;
+            if (m < *margin) *margin = m;
+        }
+        if (sqrt(rnn2) < eps) break;
+        const double beta = rnn2 / rr;
+        for (int a = 0; a < 4; ++a) {
+            d[a] = -rn[a] + beta * d[a];
+            r[a] = rn[a];
+        }
+    }
+    for (int a = 0; a < 4; ++a) p[a] = z[a];
+}
+
+/*
+ * Algorithm 1's q updates for four-parameter seeds [n][4] (float32 starts):
+ * Newton-CG direction, step cap max_a |p_a| / scale_a <= step_cap, Armijo
+ * backtracking.  status: 0 ok, 1 some line search accepted no step, 3
+ * non-finite; R_out = R(theta_q; sigma_q); margin as in or_local_search.
+ */
+void or_local_search4(const float *hits, int64_t n_hits, const float *seeds, int64_t n_seeds, const or_ls4_opts *o,
+                      double *theta_out, double *R_out, uint8_t *status, double *margin_out) {
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n_seeds; ++i) {
+        double th[4], margin = INFINITY;
+        int st = 0;
+        for (int a = 0; a < 4; ++a) th[a] = (double)seeds[4 * i + a];
+        for (int j = 0; j < o->q; ++j) {
+            const double sigma = o->sigma[j];
+            double v[29];
+            or_rgh4(hits, n_hits, th, sigma, v);
+            const double R = v[0];
+            double p[4];
+            newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, p, &margin);
+            double cells = 0.0;
+            for (int a = 0; a < 4; ++a) cells = fmax(cells, fabs(p[a]) / o->scale[a]);
+            if (cells > o->step_cap)
+                for (int a = 0; a < 4; ++a) p[a] *= o->step_cap / cells;
+            double slope = 0.0;
+            for (int a = 0; a < 4; ++a) slope += v[1 + a] * p[a];
+            double t = 1.0;
+            int accepted = 0;
+            for (int hv = 0; hv <= o->max_halvings; ++hv) {
+                double trial[4];
+                for (int a = 0; a < 4; ++a) trial[a] = th[a] + t * p[a];
+                const double Rt = or_response4(hits, n_hits, trial, sigma);
+                const double need = R + o->c1 * t * slope;
+                const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
+                const double m = fabs(Rt - need) / tol;
+                if (m < margin) margin = m;
+                if (Rt >= need) {
+                    for (int a = 0; a < 4; ++a) th[a] = trial[a];
+                    accepted = 1;
+                    break;
+                }
+                t *= 0.5;
+            }
+            if (!accepted) st = 1;
+        }
+        R_out[i] = or_response4(hits, n_hits, th, o->sigma[o->q - 1]);
+        int finite = isfinite(R_out[i]);
+        for (int a = 0; a < 4; ++a) {
+            theta_out[4 * i + a] = th[a];
+            finite = finite && isfinite(th[a]);
+        }
+        status[i] = (uint8_t)(finite ? st : 3);
+        if (margin_out) margin_out[i] = margin;
+    }
+}

@@ -1,0 +1,121 @@
+"""Pins of the four-parameter track model of the oracle (x0, y0, t_x, t_y):
+the track crosses the layer z at (x0 + t_x z, y0 + t_y z).  Checked against
+the pinned two-parameter slope model, translation invariance, closed forms on
+the track, central differences and the convergence of the Newton search."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import WORKLOADS, make_event
+
+ZS = np.array([-300.0 + 42.0 * p for p in range(26)])
+
+
+def _event():
+    return make_event(WORKLOADS["velo"], 21, 0, vertex_sigma=(0, 0, 0)).hits
+
+
+@pytest.mark.parametrize("sigma", [0.05, 0.3])
+def test_reduces_to_the_slope_model_through_the_origin(sigma):
+    h = _event()
+    rng = np.random.default_rng(0)
+    for t in rng.uniform(-0.2, 0.2, (5, 2)):
+        a = oracle.rgh4(h, [0.0, 0.0, t[0], t[1]], sigma)
+        b = oracle.rgh(h, 1, t, sigma)
+        assert a["R"] == pytest.approx(b["R"], rel=1e-13, abs=1e-300)
+        np.testing.assert_allclose(a["grad"][2:], b["grad"], rtol=1e-12, atol=1e-12 * b["grad_abs"].sum())
+        np.testing.assert_allclose(a["hess"][2:, 2:], b["hess"], rtol=1e-12, atol=1e-12 * b["hess_abs"].sum())
+
+
+def test_an_offset_equals_shifting_the_hits():
+    # R(x0, y0, t; hits) = R(0, 0, t; hits - (x0, y0)): the offsets enter only through the residual
+    h = _event()[:400].astype(np.float64)
+    x0, y0, t = 0.75, -0.5, (0.03, -0.02)
+    hs = h.copy()
+    hs[:, 0] -= x0
+    hs[:, 1] -= y0
+    a = oracle.rgh4(h.astype(np.float32), [x0, y0, t[0], t[1]], 0.3)
+    # float32 hits on both sides: compare through the shifted float32 copy's exact values
+    a2 = oracle.rgh4(hs.astype(np.float32), [0.0, 0.0, t[0], t[1]], 0.3)
+    assert a["R"] == pytest.approx(a2["R"], rel=1e-6)
+    np.testing.assert_allclose(a["grad"], a2["grad"], rtol=1e-4, atol=1e-6 * a["grad_abs"].sum())
+
+
+def test_on_the_track_R_is_N_gradient_zero_and_hessian_closed_form():
+    # dyadic parameters and integer layers: every hit is exact in float32, so
+    # every residual is exactly zero
+    x0, y0, tx, ty = 0.375, -0.25, 0.0625, -0.03125
+    h = np.stack([x0 + tx * ZS, y0 + ty * ZS, ZS, 0 * ZS], 1).astype(np.float32)
+    assert np.all(h[:, 0].astype(np.float64) == x0 + tx * ZS)
+    th = np.array([x0, y0, tx, ty])
+    sigma = 0.3
+    k = 1.0 / sigma ** 2
+    out = oracle.rgh4(h, th, sigma)
+    z = ZS
+    assert out["R"] == len(ZS)
+    assert np.all(out["grad"] == 0.0)
+    JJ = np.array([[len(z), 0, z.sum(), 0], [0, len(z), 0, z.sum()],
+                   [z.sum(), 0, (z * z).sum(), 0], [0, z.sum(), 0, (z * z).sum()]])
+    np.testing.assert_allclose(out["hess"], -2 * k * JJ, rtol=1e-13)
+
+
+def test_gradient_and_hessian_match_central_differences():
+    h = _event()
+    rng = np.random.default_rng(2)
+    sigma = 0.3
+    for _ in range(4):
+        th = np.array([rng.normal(0, 0.05), rng.normal(0, 0.05), rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)])
+        out = oracle.rgh4(h, th, sigma)
+        steps = np.array([1e-5, 1e-5, 2e-8, 2e-8])
+        for a in range(4):
+            e = np.zeros(4)
+            e[a] = steps[a]
+            fd = (oracle.response4(h, th + e, sigma) - oracle.response4(h, th - e, sigma)) / (2 * steps[a])
+            assert fd == pytest.approx(out["grad"][a], rel=1e-4, abs=1e-6 * out["grad_abs"].sum())
+            gp = oracle.rgh4(h, th + e, sigma)["grad"]
+            gm = oracle.rgh4(h, th - e, sigma)["grad"]
+            np.testing.assert_allclose((gp - gm) / (2 * steps[a]), out["hess"][a], rtol=1e-3,
+                                       atol=1e-5 * out["hess_abs"].sum())
+
+
+def test_search_recovers_a_track_from_a_displaced_vertex():
+    # a noiseless track from a vertex at z = 60 mm (x0 = -t_x 60, ...): the slope
+    # model through the origin cannot reach R = N, the four-parameter search does.
+    # Offsets and slopes are strongly coupled (the layers are not centred on
+    # z = 0), so the truncated CG resolves the stiff slope directions first and
+    # the offsets a few updates later; R never decreases.
+    x0, y0, tx, ty = -0.07 * 60.0 + 0.2, 0.045 * 60.0 - 0.1, 0.07, -0.045
+    h = np.stack([x0 + tx * ZS, y0 + ty * ZS, ZS, 0 * ZS], 1).astype(np.float32)
+    truth = np.array([x0, y0, tx, ty])
+    sigma = 0.3
+    scale = (0.05, 0.05, 2 ** -10, 2 ** -10)
+    start = truth + np.array([0.02, -0.015, 4e-5, -3e-5])
+    seeds = start.astype(np.float32)[None]
+    errs = [np.max(np.abs(seeds[0] - truth) / scale)]
+    Rs = [oracle.response4(h, seeds[0].astype(np.float64), sigma)]
+    for q in range(1, 7):
+        th, R, st, m = oracle.local_search4(h, seeds, [sigma] * q, scale)
+        assert st[0] == 0
+        errs.append(np.max(np.abs(th[0] - truth) / scale))
+        Rs.append(R[0])
+    assert all(b >= a for a, b in zip(Rs, Rs[1:]))
+    assert errs[3] < 0.05 * errs[0] and errs[6] < 1e-5
+    assert Rs[-1] == pytest.approx(len(ZS), rel=1e-9)
+    # the two-parameter model's best over a fine slope grid stays well below N
+    R2 = oracle.grid_response(h, 1, (tx - 0.01, ty - 0.01), (1e-4, 1e-4), (200, 200), sigma)
+    assert R2.max() < 0.8 * len(ZS)
+
+
+def test_search_steps_never_lower_R_at_a_fixed_bandwidth():
+    h = _event()
+    ev_truth = make_event(WORKLOADS["velo"], 21, 0, vertex_sigma=(0, 0, 0)).truth
+    rng = np.random.default_rng(4)
+    t = ev_truth[rng.integers(0, len(ev_truth), 100), :2] + rng.normal(0, 2e-3, (100, 2))
+    seeds = np.concatenate([rng.normal(0, 0.05, (100, 2)), t], 1).astype(np.float32)
+    R0 = np.array([oracle.response4(h, s.astype(np.float64), 0.175) for s in seeds])
+    th, R, st, m = oracle.local_search4(h, seeds, [0.175] * 3, (0.05, 0.05, 2 ** -10, 2 ** -10))
+    ok = st <= 1
+    assert ok.sum() >= 95
+    assert np.all(R[ok] >= R0[ok] * (1 - 1e-12))
