@@ -86,8 +86,8 @@ def lib():
             L.or_local_search.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, P, P, P, P]
             L.or_extract_tracks.argtypes = [P, P, P, I64, P, D, D, P, I64]
             L.or_extract_tracks.restype = I64
-            L.or_rgh4.argtypes = [P, I64, P, D, P]
-            L.or_response4.argtypes = [P, I64, P, D]
+            L.or_rgh4.argtypes = [P, I64, P, D, D, P]
+            L.or_response4.argtypes = [P, I64, P, D, D]
             L.or_response4.restype = D
             L.or_local_search4.argtypes = [P, I64, P, I64, P, P, P, P, P]
             _LIB = L
@@ -207,7 +207,8 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
 
 class _Ls4Opts(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_double * 8), ("c1", ctypes.c_double),
-                ("max_halvings", ctypes.c_int32), ("scale", ctypes.c_double * 4), ("step_cap", ctypes.c_double)]
+                ("max_halvings", ctypes.c_int32), ("scale", ctypes.c_double * 4), ("step_cap", ctypes.c_double),
+                ("zref", ctypes.c_double)]
 
 
 _TRI4 = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
@@ -220,25 +221,26 @@ def _sym4(v) -> np.ndarray:
     return H
 
 
-def rgh4(hits, theta, sigma: float) -> dict:
+def rgh4(hits, theta, sigma: float, zref: float = 0.0) -> dict:
     """R, grad R [4], Hess R [4, 4] of the four-parameter track (x0, y0, t_x,
-    t_y), crossing the layer z at (x0 + t_x z, y0 + t_y z) (Eq. 1)."""
+    t_y) at the reference plane zref, crossing the layer z at
+    (x0 + t_x (z - zref), y0 + t_y (z - zref)) (Eq. 1)."""
     h = _hits(hits)
     th = np.ascontiguousarray(theta, dtype=np.float64).reshape(4)
     out = np.zeros(29)
-    lib().or_rgh4(_ptr(h), h.shape[0], _ptr(th), float(sigma), _ptr(out))
+    lib().or_rgh4(_ptr(h), h.shape[0], _ptr(th), float(zref), float(sigma), _ptr(out))
     return dict(R=out[0], grad=out[1:5].copy(), hess=_sym4(out[5:15]), grad_abs=out[15:19].copy(),
                 hess_abs=_sym4(out[19:29]))
 
 
-def response4(hits, theta, sigma: float) -> float:
+def response4(hits, theta, sigma: float, zref: float = 0.0) -> float:
     h = _hits(hits)
     th = np.ascontiguousarray(theta, dtype=np.float64).reshape(4)
-    return lib().or_response4(_ptr(h), h.shape[0], _ptr(th), float(sigma))
+    return lib().or_response4(_ptr(h), h.shape[0], _ptr(th), float(zref), float(sigma))
 
 
 def local_search4(hits, seeds, sigma_schedule: Sequence[float], scale: Sequence[float], step_cap: float = 4.0,
-                  c1: float = 1e-4, max_halvings: int = 8):
+                  c1: float = 1e-4, max_halvings: int = 8, zref: float = 0.0):
     """Algorithm 1's q truncated-Newton updates (Newton-CG in four dimensions,
     at most four CG iterations) for four-parameter seeds [n, 4]; the step is
     capped to max_a |p_a| / scale_a <= step_cap.
@@ -258,6 +260,7 @@ def local_search4(hits, seeds, sigma_schedule: Sequence[float], scale: Sequence[
     for a in range(4):
         o.scale[a] = float(scale[a])
     o.step_cap = float(step_cap)
+    o.zref = float(zref)
     ns = s.shape[0]
     th = np.zeros((ns, 4))
     R = np.zeros(ns)

@@ -434,13 +434,18 @@ int64_t or_extract_tracks(const double *theta, const double *R, const uint8_t *s
 /* ------------------------------------------------------------------------ */
 /* Four-parameter straight track: a line that need not pass through the     */
 /* origin, so a vertex displaced along z (or across it) is representable.   */
-/*   theta = (x0, y0, t_x, t_y): the track crosses the layer z = const at     */
-/*   (x0 + t_x z, y0 + t_y z), so r = (x - x0 - t_x z, y - y0 - t_y z) and     */
-/*   dr/dtheta = -[[1, 0, z, 0], [0, 1, 0, z]]; with J = -dr/dtheta the        */
+/*   theta = (x0, y0, t_x, t_y) at a reference plane z_ref: the track crosses */
+/*   the layer z at (x0 + t_x w, y0 + t_y w), w = z - z_ref, so               */
+/*   r = (x - x0 - t_x w, y - y0 - t_y w) and                                 */
+/*   dr/dtheta = -[[1, 0, w, 0], [0, 1, 0, w]]; with J = -dr/dtheta the        */
 /*   derivatives of Eq. 1 take the same form as above:                        */
 /*     grad R = (2 / sigma^2) sum_k e_k J_k^T r_k                             */
 /*     Hess R = sum_k e_k [ (4 / sigma^4) (J_k^T r_k)(J_k^T r_k)^T             */
 /*                          - (2 / sigma^2) J_k^T J_k ].                      */
+/* z_ref = the layers' mean z makes sum w = 0 over a full track, which        */
+/* decouples offsets from slopes in J^T J (the truncated Newton then needs   */
+/* a few updates, not tens); z_ref = 0 is the line through the origin's      */
+/* parametrisation with two extra offsets.                                  */
 /* ------------------------------------------------------------------------ */
 
 /* Upper-triangle index of (a, b), a <= b, in the order 00 01 02 03 11 12 13 22 23 33. */
@@ -454,12 +459,12 @@ static int tri4(int a, int b) {
  * order), out[15..18] = sum of |gradient terms|, out[19..28] = sum of
  * |Hessian terms| (the scales of the FP32 parity tolerances).
  */
-void or_rgh4(const float *hits, int64_t n_hits, const double th[4], double sigma, double *out) {
+void or_rgh4(const float *hits, int64_t n_hits, const double th[4], double zref, double sigma, double *out) {
     const double k = 1.0 / (sigma * sigma);
     memset(out, 0, sizeof(double) * 29);
     for (int64_t i = 0; i < n_hits; ++i) {
         const float *h = hits + 4 * i;
-        const double z = (double)h[2];
+        const double z = (double)h[2] - zref;
         const double r[2] = {(double)h[0] - th[0] - th[2] * z, (double)h[1] - th[1] - th[3] * z};
         const double e = exp(-(r[0] * r[0] + r[1] * r[1]) * k);
         /* J^T r and J^T J with J = [[1, 0, z, 0], [0, 1, 0, z]] */
@@ -481,12 +486,12 @@ void or_rgh4(const float *hits, int64_t n_hits, const double th[4], double sigma
     }
 }
 
-double or_response4(const float *hits, int64_t n_hits, const double th[4], double sigma) {
+double or_response4(const float *hits, int64_t n_hits, const double th[4], double zref, double sigma) {
     const double k = 1.0 / (sigma * sigma);
     double R = 0.0;
     for (int64_t i = 0; i < n_hits; ++i) {
         const float *h = hits + 4 * i;
-        const double z = (double)h[2];
+        const double z = (double)h[2] - zref;
         const double r0 = (double)h[0] - th[0] - th[2] * z, r1 = (double)h[1] - th[1] - th[3] * z;
         R += exp(-(r0 * r0 + r1 * r1) * k);
     }
@@ -500,25 +505,31 @@ typedef struct {
     int32_t max_halvings;  /* backtracking halvings after the unit step          */
     double scale[4];       /* unit of each parameter for the step cap            */
     double step_cap;       /* cap on max_a |p_a| / scale_a                        */
+    double zref;           /* reference plane of the offsets                      */
 } or_ls4_opts;
 
 static double sym4(const double *Hu, int a, int b) { return a <= b ? Hu[tri4(a, b)] : Hu[tri4(b, a)]; }
 
 /*
  * Newton-CG direction in four dimensions (Nocedal & Wright, Algorithm 7.1)
- * for maximising R: CG on B p = g with B = -Hess R from p = 0, forcing
- * tolerance min(1/2, sqrt|g|) |g|, at most 4 iterations (the dimension);
- * non-positive curvature along d returns g at the first iteration, else
- * the current iterate.  *margin as for the 2D direction.
+ * for maximising R, in the variables scaled by the parameters' units D =
+ * diag(scale) (offsets in mm and slopes differ by three orders of
+ * magnitude; unscaled, the forcing term stops CG before the offsets move):
+ * CG on (D B D) y = D g with B = -Hess R from y = 0, forcing tolerance
+ * min(1/2, sqrt|D g|) |D g|, at most 4 iterations (the dimension);
+ * non-positive curvature along d returns y = D g at the first iteration,
+ * else the current iterate; p = D y.  *margin as for the 2D direction, on
+ * the scaled quantities.
  */
-static void newton_cg_direction4(const double g[4], const double Hu[10], const double gabs[4],
-                                 const double Habs[10], double p[4], double *margin) {
-    double B[4][4], hscale = 0.0, gsum = 0.0;
+static void newton_cg_direction4(const double g_in[4], const double Hu[10], const double gabs_in[4],
+                                 const double Habs[10], const double scale[4], double p[4], double *margin) {
+    double B[4][4], g[4], hscale = 0.0, gsum = 0.0;
     for (int a = 0; a < 4; ++a) {
-        gsum += gabs[a];
+        g[a] = scale[a] * g_in[a];
+        gsum += scale[a] * gabs_in[a];
         for (int b = 0; b < 4; ++b) {
-            B[a][b] = -sym4(Hu, a, b);
-            hscale += sym4(Habs, a, b);
+            B[a][b] = -scale[a] * sym4(Hu, a, b) * scale[b];
+            hscale += scale[a] * sym4(Habs, a, b) * scale[b];
         }
     }
     double gn = 0.0;
@@ -544,7 +555,7 @@ static void newton_cg_direction4(const double g[4], const double Hu[10], const d
             if (m < *margin) *margin = m;
         }
         if (dBd <= 0.0) {
-            for (int a = 0; a < 4; ++a) p[a] = it == 0 ? g[a] : z[a];
+            for (int a = 0; a < 4; ++a) p[a] = scale[a] * (it == 0 ? g[a] : z[a]);
             return;
         }
         double rr = 0.0;
@@ -568,7 +579,7 @@ static void newton_cg_direction4(const double g[4], const double Hu[10], const d
             r[a] = rn[a];
         }
     }
-    for (int a = 0; a < 4; ++a) p[a] = z[a];
+    for (int a = 0; a < 4; ++a) p[a] = scale[a] * z[a];
 }
 
 /*
@@ -587,10 +598,10 @@ void or_local_search4(const float *hits, int64_t n_hits, const float *seeds, int
         for (int j = 0; j < o->q; ++j) {
             const double sigma = o->sigma[j];
             double v[29];
-            or_rgh4(hits, n_hits, th, sigma, v);
+            or_rgh4(hits, n_hits, th, o->zref, sigma, v);
             const double R = v[0];
             double p[4];
-            newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, p, &margin);
+            newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, o->scale, p, &margin);
             double cells = 0.0;
             for (int a = 0; a < 4; ++a) cells = fmax(cells, fabs(p[a]) / o->scale[a]);
             if (cells > o->step_cap)
@@ -602,7 +613,7 @@ void or_local_search4(const float *hits, int64_t n_hits, const float *seeds, int
             for (int hv = 0; hv <= o->max_halvings; ++hv) {
                 double trial[4];
                 for (int a = 0; a < 4; ++a) trial[a] = th[a] + t * p[a];
-                const double Rt = or_response4(hits, n_hits, trial, sigma);
+                const double Rt = or_response4(hits, n_hits, trial, o->zref, sigma);
                 const double need = R + o->c1 * t * slope;
                 const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
                 const double m = fabs(Rt - need) / tol;
@@ -616,7 +627,7 @@ void or_local_search4(const float *hits, int64_t n_hits, const float *seeds, int
             }
             if (!accepted) st = 1;
         }
-        R_out[i] = or_response4(hits, n_hits, th, o->sigma[o->q - 1]);
+        R_out[i] = or_response4(hits, n_hits, th, o->zref, o->sigma[o->q - 1]);
         int finite = isfinite(R_out[i]);
         for (int a = 0; a < 4; ++a) {
             theta_out[4 * i + a] = th[a];

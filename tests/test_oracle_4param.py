@@ -119,3 +119,44 @@ def test_search_steps_never_lower_R_at_a_fixed_bandwidth():
     ok = st <= 1
     assert ok.sum() >= 95
     assert np.all(R[ok] >= R0[ok] * (1 - 1e-12))
+
+
+def test_reference_plane_is_a_reparametrisation():
+    # (x0, y0) at z_ref is (x0 - t_x z_ref, y0 - t_y z_ref) at z = 0: same R, and
+    # the slope derivatives at fixed reference offsets follow the chain rule
+    h = _event()
+    th = np.array([0.3, -0.2, 0.04, -0.03])
+    zr = 225.0
+    th0 = np.array([th[0] - th[2] * zr, th[1] - th[3] * zr, th[2], th[3]])
+    a = oracle.rgh4(h, th, 0.3, zref=zr)
+    b = oracle.rgh4(h, th0, 0.3)
+    assert a["R"] == pytest.approx(b["R"], rel=1e-12)
+    # d/dt_x at fixed x0(z_ref) = d/dt_x at fixed x0(0) + d/dx0 * d x0(0)/d t_x = g_t - z_ref g_x0
+    np.testing.assert_allclose(a["grad"][:2], b["grad"][:2], rtol=1e-9, atol=1e-9 * b["grad_abs"].sum())
+    np.testing.assert_allclose(a["grad"][2:], b["grad"][2:] - zr * b["grad"][:2], rtol=1e-7,
+                               atol=1e-9 * b["grad_abs"].sum() * zr)
+
+
+def test_centred_reference_plane_decouples_and_converges():
+    # z_ref = the layers' mean z: sum (z - z_ref) = 0 on a full track, so the
+    # Hessian on the track is block-diagonal.  In units of about one peak width
+    # per parameter the scaled Newton-CG moves offsets and slopes together;
+    # its forcing tolerance (1/2 of |g| while |g| > 1/4) makes the early steps
+    # inexact, so the error falls geometrically (here by 0.63, 0.30, 0.30, 0.14,
+    # ... per update) before the last steps land on the track
+    zr = float(ZS.mean())
+    x0, y0, tx, ty = 0.375, -0.25, 0.0625, -0.03125
+    h = np.stack([x0 + tx * (ZS - zr), y0 + ty * (ZS - zr), ZS, 0 * ZS], 1).astype(np.float32)
+    out = oracle.rgh4(h, [x0, y0, tx, ty], 0.3, zref=zr)
+    assert out["R"] == len(ZS)
+    assert abs(out["hess"][0, 2]) <= 1e-12 * abs(out["hess"][2, 2])
+    assert abs(out["hess"][1, 3]) <= 1e-12 * abs(out["hess"][3, 3])
+    scale = (0.25, 0.25, 2 ** -10, 2 ** -10)
+    start = np.array([[x0 + 0.04, y0 - 0.03, tx + 6e-4, ty - 5e-4]], np.float32)
+    errs = [np.max(np.abs(start[0] - [x0, y0, tx, ty]) / scale)]
+    for q in range(1, 9):
+        th, R, st, m = oracle.local_search4(h, start, [0.3] * q, scale, zref=zr)
+        assert st[0] == 0
+        errs.append(np.max(np.abs(th[0] - [x0, y0, tx, ty]) / scale))
+    assert all(b <= 0.7 * a for a, b in zip(errs[:6], errs[1:7]))
+    assert errs[8] < 1e-4
