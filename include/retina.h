@@ -397,6 +397,49 @@ int retina_refine_maxima(const float *hits, int64_t n_hits, const int64_t *event
                          uint8_t *status, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * retina_local_search4 - Algorithm 1 for a four-parameter straight track.
+ *
+ * Paper: Algorithm 1 with the truncated Newton update of Section 3, for the
+ * track theta = (x0, y0, t_x, t_y) at the reference plane z_ref, crossing
+ * the layer z at (x0 + t_x w, y0 + t_y w), w = z - z_ref: a line that need
+ * not pass through the origin, so a smeared vertex is representable.  s is
+ * the in-layer distance of Eq. 1 as for the slope model.  z_ref at the
+ * layers' mean z decouples offsets from slopes.  Update j at sigma_j:
+ *   1. R, grad R (4) and Hess R (4 x 4) at theta, one pass over the hits.
+ *   2. Newton-CG (Nocedal & Wright, Algorithm 7.1) in the variables scaled
+ *      by D = diag(scale): CG on (D B D) y = D g, B = -Hess R, from y = 0,
+ *      forcing tolerance min(1/2, sqrt|D g|) |D g|, at most 4 iterations;
+ *      non-positive curvature: y = D g at the first iteration, else the
+ *      current iterate; p = D y.
+ *   3. If max_a |p_a| / scale_a > step_cap, p is scaled down to it.
+ *   4. Armijo backtracking as in retina_local_search.
+ * No block skipping (slope-model boxes do not bound offsets); hits are
+ * staged per event in shared memory (RETINA_OPT_LS_SMEM_HITS), the rest read
+ * from global memory.
+ *
+ *   seeds     : float32 [n_events][n_seeds][4] starting points.
+ *   opts      : host pointer (below).
+ *   theta_out : float32 [n_events][n_seeds][4];  R_out: float32
+ *               [n_events][n_seeds] at sigma_q;  status: uint8
+ *               [n_events][n_seeds]: 0 ok, 1 some line search took no step,
+ *               3 non-finite.
+ * Returns RETINA_EINVAL for bad sizes, options or null pointers (nothing
+ * launched); n_events == 0 or n_seeds == 0 is a no-op.
+ */
+typedef struct {
+    int32_t q;            /* updates per seed, 1 .. RETINA_MAX_Q              */
+    float sigma[8];       /* bandwidth at update j                            */
+    float c1;             /* Armijo sufficient-increase constant, in [0, 1)  */
+    int32_t max_halvings; /* backtracking halvings after t = 1, 0 .. 30      */
+    float scale[4];       /* unit of each parameter (CG scaling, step cap), > 0 */
+    float step_cap;       /* cap on max_a |p_a| / scale_a, > 0               */
+    float zref;           /* reference plane of the offsets (finite)         */
+} retina_ls4_opts;
+int retina_local_search4(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                         const float *seeds, int32_t n_seeds, const retina_ls4_opts *opts, float *theta_out,
+                         float *R_out, uint8_t *status, void *stream);
+
+/*
  * retina_batched_search - Algorithm 1 over a ragged batch, one persistent launch.
  *
  * Paper: Algorithm 1 with the Section 3 update, exactly as retina_local_search

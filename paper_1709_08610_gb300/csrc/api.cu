@@ -314,6 +314,25 @@ int retina_refine_maxima(const float *hits, int64_t n_hits, const int64_t *event
                                             g_opt_batch_ctas, (cudaStream_t)stream));
 }
 
+int retina_local_search4(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                         const float *seeds, int32_t n_seeds, const retina_ls4_opts *opts, float *theta_out,
+                         float *R_out, uint8_t *status, void *stream) {
+    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !opts) return RETINA_EINVAL;
+    if (opts->q < 1 || opts->q > RETINA_MAX_Q) return RETINA_EINVAL;
+    for (int j = 0; j < opts->q; ++j)
+        if (!finite_pos(opts->sigma[j])) return RETINA_EINVAL;
+    if (!(opts->c1 >= 0.f && opts->c1 < 1.f) || opts->max_halvings < 0 || opts->max_halvings > 30) return RETINA_EINVAL;
+    for (int a = 0; a < 4; ++a)
+        if (!finite_pos(opts->scale[a])) return RETINA_EINVAL;
+    if (!(opts->step_cap > 0.f) || !isfinite(opts->zref)) return RETINA_EINVAL;
+    if (n_events > 65535) return RETINA_EINVAL;
+    if (n_events == 0 || n_seeds == 0) return RETINA_OK;
+    if (!event_offsets || !seeds || !theta_out || !R_out || !status) return RETINA_EINVAL;
+    if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
+    return cuda_status(launch_local_search4((const float4 *)hits, n_hits, event_offsets, n_events, seeds, n_seeds,
+                                            opts, theta_out, R_out, status, g_opt_smem_hits, (cudaStream_t)stream));
+}
+
 int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes) {
     if (!bytes || n_events < 0) return RETINA_EINVAL;
     *bytes = batched_ws_bytes(n_events);

@@ -49,6 +49,9 @@ cudaError_t launch_refine_maxima(const float4 *hits, int64_t n_hits, const int64
                                  uint8_t *status, int32_t *counters, int seeds_per_warp, int warps, int smem_hits,
                                  int ctas, cudaStream_t st);
 size_t batched_ws_bytes(int n_events);
+cudaError_t launch_local_search4(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events,
+                                 const float *seeds, int n_seeds, const retina_ls4_opts *o, float *theta_out,
+                                 float *R_out, uint8_t *status, int smem_hits, cudaStream_t st);
 int64_t prepared_box_count(int64_t n_hits, int n_events);
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                                 float4 *sorted, float4 *boxes, cudaStream_t st);

@@ -90,6 +90,39 @@ class LsOpts:
         return o
 
 
+class _CLs4Opts(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("sigma", ctypes.c_float * 8), ("c1", ctypes.c_float),
+                ("max_halvings", ctypes.c_int32), ("scale", ctypes.c_float * 4), ("step_cap", ctypes.c_float),
+                ("zref", ctypes.c_float)]
+
+
+@dataclass(frozen=True)
+class LsOpts4:
+    """Options of the four-parameter search (x0, y0, t_x, t_y) at the plane
+    ``zref``; ``scale`` is each parameter's unit (about one peak width: CG
+    scaling and step cap)."""
+
+    sigma: Tuple[float, ...] = (0.3, 0.175, 0.05)
+    scale: Tuple[float, float, float, float] = (0.25, 0.25, 2.0 ** -10, 2.0 ** -10)
+    step_cap: float = 4.0
+    zref: float = 0.0
+    c1: float = 1e-4
+    max_halvings: int = 8
+
+    def c(self) -> _CLs4Opts:
+        o = _CLs4Opts()
+        o.q = len(self.sigma)
+        for j, v in enumerate(self.sigma[:8]):
+            o.sigma[j] = float(v)
+        o.c1 = float(self.c1)
+        o.max_halvings = int(self.max_halvings)
+        for a in range(4):
+            o.scale[a] = float(self.scale[a])
+        o.step_cap = float(self.step_cap)
+        o.zref = float(self.zref)
+        return o
+
+
 class _CPipelineConfig(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("grid", _CGrid), ("sigma_grid", ctypes.c_float), ("R0", ctypes.c_float),
                 ("merge_cells", ctypes.c_float), ("opts", _CLsOpts), ("max_events", ctypes.c_int32),
@@ -118,6 +151,7 @@ def _load():
     L.retina_response.argtypes = [P, I64, P, I32, I32, P, I32, F, I32, P, P]
     L.retina_local_search.argtypes = [P, I64, P, P, I32, I32, P, I32, P, P, P, P, P, P, P]
     L.retina_refine_maxima_workspace_size.argtypes = [I32, P]
+    L.retina_local_search4.argtypes = [P, I64, P, I32, P, I32, P, P, P, P, P]
     L.retina_refine_maxima.argtypes = [P, I64, P, P, I32, I32, P, P, I32, P, P, P, P, P, P, SZ, P]
     L.retina_extract_tracks.argtypes = [P, P, P, P, I32, I32, P, F, F, P, P, P, P, I32, P]
     L.retina_grid_response_workspace_size.argtypes = [I32, I32, P, I32, P]
@@ -385,6 +419,29 @@ def refine_maxima(hits: torch.Tensor, offsets: torch.Tensor, model: int, theta_c
     _check("retina_refine_maxima", lib.retina_refine_maxima(
         _p(hits), hits.shape[0], _p(offsets), _p(boxes), E, model, _p(theta_c), _p(n_max), K, ctypes.byref(o),
         ctypes.byref(g), _p(out[0]), _p(out[1]), _p(out[2]), _p(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def local_search4(hits: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor, opts: LsOpts4, out=None,
+                  stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+    """Algorithm 1 for four-parameter tracks: seeds [E, n, 4] ->
+    (theta [E, n, 4], R [E, n], status [E, n] uint8)."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    _dev(seeds, torch.float32, "seeds", 4)
+    E = offsets.numel() - 1
+    n = seeds.shape[-2]
+    if seeds.numel() != E * n * 4:
+        raise ValueError("seeds must be [E, n_seeds, 4]")
+    dev = hits.device
+    if out is None:
+        out = (torch.empty((E, n, 4), dtype=torch.float32, device=dev),
+               torch.empty((E, n), dtype=torch.float32, device=dev),
+               torch.empty((E, n), dtype=torch.uint8, device=dev))
+    o = opts.c()
+    _check("retina_local_search4", lib.retina_local_search4(
+        _p(hits), hits.shape[0], _p(offsets), E, _p(seeds), n, ctypes.byref(o), _p(out[0]), _p(out[1]), _p(out[2]),
+        _stream(stream)))
     return out
 
 

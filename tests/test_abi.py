@@ -188,6 +188,39 @@ def test_refine_maxima_rejects_null_pointers_and_empty_is_ok():
                                   None, None, None, 0, None) == 0
 
 
+@pytest.mark.parametrize("mut", ["q0", "sigmanan", "c1one", "halv", "scale0", "capneg", "zrefinf", "events"])
+def test_local_search4_rejects(mut):
+    o = rt.LsOpts4().c()
+    E = 1
+    if mut == "q0":
+        o.q = 0
+    elif mut == "sigmanan":
+        o.sigma[0] = float("nan")
+    elif mut == "c1one":
+        o.c1 = 1.0
+    elif mut == "halv":
+        o.max_halvings = 31
+    elif mut == "scale0":
+        o.scale[2] = 0.0
+    elif mut == "capneg":
+        o.step_cap = -1.0
+    elif mut == "zrefinf":
+        o.zref = float("inf")
+    elif mut == "events":
+        E = 65536
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, E, BOGUS, 16, ctypes.byref(o), BOGUS, BOGUS, BOGUS,
+                                  None) == EINVAL
+
+
+def test_local_search4_null_outputs_and_empty():
+    o = rt.LsOpts4().c()
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, BOGUS, 16, ctypes.byref(o), None, BOGUS, BOGUS,
+                                  None) == EINVAL
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, BOGUS, 16, None, BOGUS, BOGUS, BOGUS, None) == EINVAL
+    assert L.retina_local_search4(None, 0, None, 0, None, 16, ctypes.byref(o), None, None, None, None) == 0
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, None, 0, ctypes.byref(o), None, None, None, None) == 0
+
+
 def test_extract_tracks_rejects():
     g = _grid()
     call = lambda n_points, merge, K, R0=1.0: L.retina_extract_tracks(
