@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import WORKLOADS, batch_of, make_event, uniform_seeds  # noqa: E402
+from synth import VELO_PLANES_Z, WORKLOADS, batch_of, make_event, uniform_seeds  # noqa: E402
 
 WORKLOAD = "velo"
 RUN_SEED = 0
@@ -476,6 +476,48 @@ def alpha_sweep(rt, stream, flush, reps: int = 3):
     return {"workload": "%d origin-vertex VELO-like events, %s tracks (equal shares), %d hits; seeds "
                         "n = alpha 1024^2 / (30 * 3)" % (E, "/".join(str(m) for m in ALPHA_MULTIPLICITIES), H),
             "runs": out, "l2": "flushed before each replay"}
+
+
+def search4_measure(rt, stream, flush, ev, wl, n_seeds: int = 8192, reps: int = 20):
+    """The four-parameter search (x0, y0, t_x, t_y at z_ref = the layers' mean
+    z) on the step's event, whose vertex is smeared (the two-parameter model
+    cannot fit its tracks): n_seeds seeds with uniform slopes and zero offsets,
+    the paper's three bandwidths; kernel time (median over reps launches, L2
+    flushed before each) and the share of MC tracks with a converged seed
+    (status <= 1, R >= R0) within 1e-3 in slope and 0.1 mm in offset."""
+    import torch
+    zref = float(np.mean(VELO_PLANES_Z))
+    t = ev.truth[:, :2]
+    v = ev.truth[:, 2:5]
+    truth4 = np.stack([v[:, 0] + t[:, 0] * (zref - v[:, 2]), v[:, 1] + t[:, 1] * (zref - v[:, 2]), t[:, 0], t[:, 1]], 1)
+    sl = uniform_seeds(wl, n_seeds, RUN_SEED, 4)
+    seeds = np.concatenate([np.zeros((n_seeds, 2), np.float32), sl], 1)[None]
+    hits = torch.from_numpy(ev.hits).cuda()
+    offs = torch.tensor([0, ev.n_hits], dtype=torch.int64, device="cuda")
+    sd = torch.from_numpy(np.ascontiguousarray(seeds)).cuda()
+    opts = rt.LsOpts4(sigma=tuple(wl.sigma_schedule), zref=zref)
+    out = rt.local_search4(hits, offs, sd, opts, stream=stream)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rt.local_search4(hits, offs, sd, opts, out=out, stream=stream)
+        c.record(stream)
+        c.synchronize()
+        ts.append(a.elapsed_time(c))
+    th, R, st = (x.cpu().numpy()[0] for x in out)
+    ok = (st <= 1) & (R >= wl.R0)
+    tol = np.array([0.1, 0.1, 1e-3, 1e-3])
+    found = 0
+    if ok.any():
+        d = np.max(np.abs(th[ok][:, None, :].astype(np.float64) - truth4[None]) / tol, axis=2)
+        found = int((d.min(axis=0) <= 1.0).sum())
+    ms = statistics.median(ts)
+    return {"workload": "the step's event (smeared vertex), %d seeds: uniform slopes, zero offsets at z_ref = %g mm"
+                        % (n_seeds, zref),
+            "ms": ms, "seeds_per_s": n_seeds / (ms * 1e-3), "mc_efficiency": found / len(truth4),
+            "converged_above_R0": int(ok.sum()), "l2": "flushed before each launch"}
 
 
 SVELO_MULTIPLICITIES = (50, 100, 150, 200, 250, 300, 350)
@@ -980,7 +1022,9 @@ def main():
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
-    batched = stress = alpha = svelo = None
+    batched = stress = alpha = svelo = search4 = None
+    if world == 1:
+        search4 = search4_measure(rt, stream, flush, ev, wl)
     if world == 1 and not args.no_batched:
         # launch shapes tuned for one event do not carry over to 1024: the grid's
         # hit-slice count goes back to the library's rule (one slice at this
@@ -1017,7 +1061,7 @@ def main():
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},
             "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0, "batched": batched,
-            "batched_stress": stress, "alpha_sweep": alpha, "svelo_sweep": svelo,
+            "batched_stress": stress, "alpha_sweep": alpha, "svelo_sweep": svelo, "search4": search4,
             "tuned": tuned,
         }
         print(json.dumps(line), flush=True)
