@@ -324,3 +324,16 @@ def test_pipeline_config_validation_needs_no_gpu():
     assert L.retina_pipeline_create(ctypes.byref(cfg()), None) == EINVAL
     assert L.retina_pipeline_destroy(None) == EINVAL
     assert L.retina_pipeline_run(None, None, 0, None, 1, None, None, None, None, None, None, None, None) == EINVAL
+
+
+def test_option_structs_marshal_every_field():
+    o = rt.LsOpts(sigma=(0.4, 0.2), c1=0.25, max_halvings=5, step_cap_cells=2.5, update=rt.UPDATE_MODIFIED_NEWTON).c()
+    assert (o.q, list(o.sigma)[:2], o.max_halvings, o.update) == (2, [pytest.approx(0.4), pytest.approx(0.2)], 5, 2)
+    assert o.c1 == pytest.approx(0.25) and o.step_cap_cells == pytest.approx(2.5)
+    r = rt.refine_opts(0.378, iters=3, step_cap_cells=0.5)
+    assert r.sigma == (0.378,) * 3 and r.step_cap_cells == 0.5 and r.update == rt.UPDATE_TRUNCATED_NEWTON
+    f = rt.LsOpts4(sigma=(0.3, 0.05), scale=(0.25, 0.5, 1e-3, 2e-3), step_cap=3.0, zref=225.0).c()
+    assert f.q == 2 and list(f.scale) == [pytest.approx(v) for v in (0.25, 0.5, 1e-3, 2e-3)]
+    assert f.step_cap == pytest.approx(3.0) and f.zref == pytest.approx(225.0)
+    # the C struct sizes the library expects (host pointers read field by field)
+    assert ctypes.sizeof(type(f)) == 4 * (1 + 8 + 1 + 1 + 4 + 1 + 1)

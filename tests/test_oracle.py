@@ -613,3 +613,13 @@ def test_figure2_close_tracks_split_and_merge():
         assert counts[1e-3] > 4
         assert counts[1e-2] == 2
         assert counts[1e-1] == 1
+
+
+def test_oracle_option_ranges_are_enforced():
+    h = np.zeros((1, 4), np.float32)
+    with pytest.raises(ValueError):
+        oracle.local_search(h, 1, np.zeros((1, 2), np.float32), [0.3], (0, 0), (1, 1), (2, 2), update=3)
+    with pytest.raises(ValueError):
+        oracle.refine_maxima(h, 1, np.zeros((1, 2)), 0.3, (0, 0), (1, 1), (2, 2), iters=0)
+    with pytest.raises(ValueError):
+        oracle.local_search4(h, np.zeros((1, 4), np.float32), [0.3] * 9, (1, 1, 1, 1))
