@@ -284,6 +284,8 @@ int retina_grid_maxima(const float *R, int32_t n_events, const retina_grid *g, f
  * - 2 * n_events * ceil(n0 * n1 / 2048) * 4 bytes must fit in
  *   RETINA_STATIC_SCRATCH_BYTES (1 MiB: e.g. 256 events of 1024 x 1024 or 64
  *   of 2048 x 2048); larger requests return RETINA_ENOSPACE, nothing launched.
+ * - n_events above 65535 returns RETINA_EINVAL, nothing launched (as for
+ *   retina_grid_maxima).
  * - The first call on a device looks up the array's device address (with that
  *   device current, i.e. the CUDA runtime's current device must be the one
  *   `stream` belongs to); make that first call before any stream capture.

@@ -90,6 +90,13 @@ def lib():
             L.or_response4.argtypes = [P, I64, P, D, D]
             L.or_response4.restype = D
             L.or_local_search4.argtypes = [P, I64, P, I64, P, P, P, P, P]
+            U64 = ctypes.c_uint64
+            L.or_local_search_perturbed.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, D, U64, I64, P, P, P, P]
+            L.or_local_search4_perturbed.argtypes = [P, I64, P, I64, P, D, U64, I64, P, P, P, P]
+            L.or_splitmix64.argtypes = [P]
+            L.or_splitmix64.restype = U64
+            L.or_perturb_u.argtypes = [U64, I64, ctypes.c_int, ctypes.c_int]
+            L.or_perturb_u.restype = D
             _LIB = L
     return _LIB
 
@@ -169,7 +176,8 @@ UPDATE_TRUNCATED_NEWTON, UPDATE_STEEPEST_ASCENT, UPDATE_MODIFIED_NEWTON = 0, 1, 
 
 
 def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, step, n,
-                 c1: float = 1e-4, max_halvings: int = 8, step_cap_cells: float = 4.0, update: int = 0):
+                 c1: float = 1e-4, max_halvings: int = 8, step_cap_cells: float = 4.0, update: int = 0,
+                 perturb: Optional[Tuple[float, int]] = None):
     """Algorithm 1's q updates for every seed.
 
     update picks the direction of each update: 0 the truncated Newton
@@ -177,6 +185,11 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     Section 3 says were examined, read as 1 steepest ascent (p = grad R) and
     2 Newton with a modified Hessian (-Hess R shifted to be positive
     definite); the step cap and Armijo backtracking are common to all.
+
+    perturb = (level, key) runs a perturbed replica: R, the gradient and the
+    Hessian at each update and R at each trial are displaced by level * u
+    times their parity tolerance, u in [-1, 1) drawn per (key, seed, update,
+    quantity) (see :func:`path_conditioning`).
 
     Returns (theta [n, 2] float64, R_final [n], status [n] uint8, margin [n]).
     """
@@ -200,9 +213,52 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     R = np.zeros(ns)
     st = np.zeros(ns, dtype=np.uint8)
     m = np.zeros(ns)
-    lib().or_local_search(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
-                          _ptr(th), _ptr(R), _ptr(st), _ptr(m))
+    if perturb is None:
+        lib().or_local_search(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
+                              _ptr(th), _ptr(R), _ptr(st), _ptr(m))
+    else:
+        lib().or_local_search_perturbed(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
+                                        float(perturb[0]), int(perturb[1]) & (2 ** 64 - 1), 0,
+                                        _ptr(th), _ptr(R), _ptr(st), _ptr(m))
     return th, R, st, m
+
+
+PERTURB_KEYS = (0x5EED0001, 0x5EED0002, 0x5EED0003, 0x5EED0004)
+
+
+def splitmix64(state: int, n: int):
+    """The first n outputs of the oracle's SplitMix64 from ``state``."""
+    st = ctypes.c_uint64(state & (2 ** 64 - 1))
+    return [lib().or_splitmix64(ctypes.byref(st)) for _ in range(n)]
+
+
+def perturb_u(key: int, seed_index: int, update: int, quantity: int) -> float:
+    return lib().or_perturb_u(key & (2 ** 64 - 1), seed_index, update, quantity)
+
+
+def path_conditioning(run, base, tol, keys: Sequence[int] = PERTURB_KEYS, level: float = 1.0):
+    """Which search paths float32 arithmetic is expected to reproduce.
+
+    ``run(perturb)`` runs the oracle search (perturb None or (level, key)) and
+    returns (theta, R, status, margin); ``base`` is its unperturbed result.
+    A path is well conditioned when every perturbed replica - every quantity
+    the CUDA path sums in float32 displaced by up to ``level`` times its
+    parity tolerance - ends with the same status and within ``tol`` (absolute,
+    per parameter; an array broadcastable to theta's shape, e.g. the
+    comparison tolerance of each seed) of the unperturbed end point.
+    Returns (stable [n] bool, replica end points [reps, n, d], replica
+    statuses [reps, n]).
+    """
+    th0, _, st0, _ = base
+    tol = np.broadcast_to(np.asarray(tol, dtype=np.float64), th0.shape)
+    stable = np.ones(len(st0), dtype=bool)
+    ends, sts = [], []
+    for k in keys:
+        th, _, st, _ = run((level, k))
+        ends.append(th)
+        sts.append(st)
+        stable &= (st == st0) & np.all(np.abs(th - th0) <= tol, axis=1)
+    return stable, np.stack(ends), np.stack(sts)
 
 
 class _Ls4Opts(ctypes.Structure):
@@ -240,7 +296,8 @@ def response4(hits, theta, sigma: float, zref: float = 0.0) -> float:
 
 
 def local_search4(hits, seeds, sigma_schedule: Sequence[float], scale: Sequence[float], step_cap: float = 4.0,
-                  c1: float = 1e-4, max_halvings: int = 8, zref: float = 0.0):
+                  c1: float = 1e-4, max_halvings: int = 8, zref: float = 0.0,
+                  perturb: Optional[Tuple[float, int]] = None):
     """Algorithm 1's q truncated-Newton updates (Newton-CG in four dimensions,
     at most four CG iterations) for four-parameter seeds [n, 4]; the step is
     capped to max_a |p_a| / scale_a <= step_cap.
@@ -266,7 +323,12 @@ def local_search4(hits, seeds, sigma_schedule: Sequence[float], scale: Sequence[
     R = np.zeros(ns)
     st = np.zeros(ns, dtype=np.uint8)
     m = np.zeros(ns)
-    lib().or_local_search4(_ptr(h), h.shape[0], _ptr(s), ns, ctypes.byref(o), _ptr(th), _ptr(R), _ptr(st), _ptr(m))
+    if perturb is None:
+        lib().or_local_search4(_ptr(h), h.shape[0], _ptr(s), ns, ctypes.byref(o), _ptr(th), _ptr(R), _ptr(st),
+                               _ptr(m))
+    else:
+        lib().or_local_search4_perturbed(_ptr(h), h.shape[0], _ptr(s), ns, ctypes.byref(o), float(perturb[0]),
+                                         int(perturb[1]) & (2 ** 64 - 1), 0, _ptr(th), _ptr(R), _ptr(st), _ptr(m))
     return th, R, st, m
 
 

@@ -189,6 +189,51 @@ typedef struct {
 } or_ls_opts;
 
 /*
+ * Perturbed replicas of a search (path conditioning; test infrastructure).
+ * A search whose discrete decisions all clear their thresholds can still
+ * end at a point that float32 arithmetic cannot pin down: a step that solves
+ * a badly conditioned system (the shifted modified-Newton step has
+ * condition >= 1e3) or a long walk along a flat ridge amplifies the rounding
+ * of the sums it uses.  To tell such paths apart the oracle can rerun a seed
+ * with every quantity the CUDA path computes in float32 - R, the gradient and
+ * the Hessian at each update, R at each line-search trial - displaced by
+ * level * u times its parity tolerance (R: 1e-5 |R| + 1e-6; gradient and
+ * Hessian entries: 1e-4 of the sum of the absolute values of their terms),
+ * with u in [-1, 1) drawn for each (replica key, seed, update, quantity) from
+ * the SplitMix64 generator (Steele, Lea & Flood, OOPSLA 2014).  A path is
+ * well conditioned when such replicas end where the unperturbed one ends.
+ * level = 0 reproduces the plain search bit for bit.
+ */
+typedef struct {
+    double level;
+    uint64_t key;
+} or_perturb;
+
+/* SplitMix64: the state advances by the golden-ratio increment and the
+ * output is the state passed through the published 64-bit finaliser. */
+uint64_t or_splitmix64(uint64_t *state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* u in [-1, 1) for quantity c of update j of seed i under replica key. */
+double or_perturb_u(uint64_t key, int64_t i, int j, int c) {
+    uint64_t st = key;
+    const uint64_t a = or_splitmix64(&st);
+    st = a ^ ((uint64_t)i * 0x100000ULL + (uint64_t)j * 0x100ULL + (uint64_t)c);
+    const uint64_t h = or_splitmix64(&st);
+    return (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+/* quantity indices: 0 R, 1-2 gradient, 3-5 Hessian (00 01 11), 16 + h trial h's R */
+static double perturbed(const or_perturb *pt, int64_t i, int j, int c, double v, double tol) {
+    if (!pt || pt->level == 0.0) return v;
+    return v + pt->level * tol * or_perturb_u(pt->key, i, j, c);
+}
+
+/*
  * One truncated Newton direction (Newton-CG, Nocedal & Wright Alg. 7.1)
  * for maximising R, i.e. minimising f = -R with gradient -g and Hessian
  * B = -H.  CG on B p = g from p = 0, forcing tolerance
@@ -252,10 +297,10 @@ static void newton_cg_direction(const double g[2], const double H[3], const doub
  * (B + tau I) p = g.  Where -H is already positive definite beyond delta this
  * is the plain Newton step.  B = 0 (no curvature) gives p = g.  *margin gets
  * the distance of the shift test mu1 < delta from its threshold, in units of
- * 1e-4 of the sum of absolute Hessian terms; a shifted step counts as a tie
- * (margin 0): B + tau I then has condition number >= 1e3, so the direction
- * moves by more than the FP32 Hessian tolerance can bound, and a path through
- * it is not one that a float32 evaluation is expected to reproduce.
+ * 1e-4 of the sum of absolute Hessian terms.  A shifted step is otherwise an
+ * ordinary decision: B + tau I then has condition number >= 1e3, so the
+ * direction can move by more than the Hessian tolerance bounds; whether that
+ * changes where the path ends is what the perturbed replicas measure.
  */
 static void modified_newton_direction(const double g[2], const double H[3], const double Habs[3], double p[2],
                                       double *margin) {
@@ -274,7 +319,6 @@ static void modified_newton_direction(const double g[2], const double H[3], cons
         return;
     }
     const double tau = mu1 < delta ? delta - mu1 : 0.0;
-    if (tau > 0.0) *margin = 0.0;
     const double a2 = a + tau, c2 = c + tau;
     const double det = a2 * c2 - b * b;
     p[0] = (c2 * g[0] - b * g[1]) / det;
@@ -292,7 +336,8 @@ static void modified_newton_direction(const double g[2], const double H[3], cons
  * from ties (margin < 1).
  */
 static int search_one(const float *hits, int64_t n_hits, int model, const float seed[2], const or_ls_opts *o,
-                      const or_grid *box, double theta_out[2], double *R_out, double *margin) {
+                      const or_grid *box, double theta_out[2], double *R_out, double *margin,
+                      const or_perturb *pt, int64_t seed_index) {
     double th[2] = {(double)seed[0], (double)seed[1]};
     int status = 0;
     *margin = INFINITY;
@@ -300,11 +345,15 @@ static int search_one(const float *hits, int64_t n_hits, int model, const float 
         const double sigma = o->sigma[j];
         double rgh[12];
         or_rgh(hits, n_hits, model, th, sigma, rgh);
-        const double R = rgh[0];
-        const double g[2] = {rgh[1], rgh[2]};
-        const double H[3] = {rgh[3], rgh[4], rgh[5]};
         const double gabs[2] = {rgh[7], rgh[8]};
         const double Habs[3] = {rgh[9], rgh[10], rgh[11]};
+        const int64_t si = seed_index;
+        const double R = perturbed(pt, si, j, 0, rgh[0], 1e-5 * fabs(rgh[0]) + 1e-6);
+        const double g[2] = {perturbed(pt, si, j, 1, rgh[1], 1e-4 * gabs[0]),
+                             perturbed(pt, si, j, 2, rgh[2], 1e-4 * gabs[1])};
+        const double H[3] = {perturbed(pt, si, j, 3, rgh[3], 1e-4 * Habs[0]),
+                             perturbed(pt, si, j, 4, rgh[4], 1e-4 * Habs[1]),
+                             perturbed(pt, si, j, 5, rgh[5], 1e-4 * Habs[2])};
         double p[2];
         if (o->update == 1) {         /* steepest ascent: the gradient itself */
             p[0] = g[0];
@@ -327,7 +376,8 @@ static int search_one(const float *hits, int64_t n_hits, int model, const float 
         int accepted = 0;
         for (int h = 0; h <= o->max_halvings; ++h) {
             const double trial[2] = {th[0] + t * p[0], th[1] + t * p[1]};
-            const double Rt = or_response(hits, n_hits, model, trial, sigma);
+            const double Rt0 = or_response(hits, n_hits, model, trial, sigma);
+            const double Rt = perturbed(pt, seed_index, j, 16 + h, Rt0, 1e-5 * fabs(Rt0) + 1e-6);
             const double need = R + o->c1 * t * slope;
             const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
             const double m = fabs(Rt - need) / tol;
@@ -361,7 +411,24 @@ void or_local_search(const float *hits, int64_t n_hits, int model, const float *
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t i = 0; i < n_seeds; ++i) {
         double m;
-        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, theta_out + 2 * i, R_out + i, &m);
+        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, theta_out + 2 * i, R_out + i, &m,
+                                        NULL, i);
+        if (margin_out) margin_out[i] = m;
+    }
+}
+
+/* or_local_search with the perturbation (level, key) applied; seed i draws
+ * its displacements under index index_base + i. */
+void or_local_search_perturbed(const float *hits, int64_t n_hits, int model, const float *seeds, int64_t n_seeds,
+                               const or_ls_opts *o, const or_grid *box, double level, uint64_t key,
+                               int64_t index_base, double *theta_out, double *R_out, uint8_t *status,
+                               double *margin_out) {
+    const or_perturb pt = {level, key};
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n_seeds; ++i) {
+        double m;
+        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, theta_out + 2 * i, R_out + i, &m,
+                                        &pt, index_base + i);
         if (margin_out) margin_out[i] = m;
     }
 }
@@ -583,57 +650,85 @@ static void newton_cg_direction4(const double g_in[4], const double Hu[10], cons
 }
 
 /*
- * Algorithm 1's q updates for four-parameter seeds [n][4] (float32 starts):
+ * Algorithm 1's q updates for one four-parameter seed (float32 start):
  * Newton-CG direction, step cap max_a |p_a| / scale_a <= step_cap, Armijo
- * backtracking.  status: 0 ok, 1 some line search accepted no step, 3
- * non-finite; R_out = R(theta_q; sigma_q); margin as in or_local_search.
+ * backtracking; pt (nullable) displaces R, the gradient, the Hessian and
+ * the trial responses as for the two-parameter search (quantities 0 R,
+ * 1-4 gradient, 5-14 Hessian, 32 + h trial h).  Returns the status: 0 ok,
+ * 1 some line search accepted no step, 3 non-finite.
+ */
+static int search4_one(const float *hits, int64_t n_hits, const float *seed, const or_ls4_opts *o,
+                       const or_perturb *pt, int64_t si, double th[4], double *R_out, double *margin) {
+    int st = 0;
+    *margin = INFINITY;
+    for (int a = 0; a < 4; ++a) th[a] = (double)seed[a];
+    for (int j = 0; j < o->q; ++j) {
+        const double sigma = o->sigma[j];
+        double v[29];
+        or_rgh4(hits, n_hits, th, o->zref, sigma, v);
+        v[0] = perturbed(pt, si, j, 0, v[0], 1e-5 * fabs(v[0]) + 1e-6);
+        for (int a = 0; a < 4; ++a) v[1 + a] = perturbed(pt, si, j, 1 + a, v[1 + a], 1e-4 * v[15 + a]);
+        for (int e = 0; e < 10; ++e) v[5 + e] = perturbed(pt, si, j, 5 + e, v[5 + e], 1e-4 * v[19 + e]);
+        const double R = v[0];
+        double p[4];
+        newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, o->scale, p, margin);
+        double cells = 0.0;
+        for (int a = 0; a < 4; ++a) cells = fmax(cells, fabs(p[a]) / o->scale[a]);
+        if (cells > o->step_cap)
+            for (int a = 0; a < 4; ++a) p[a] *= o->step_cap / cells;
+        double slope = 0.0;
+        for (int a = 0; a < 4; ++a) slope += v[1 + a] * p[a];
+        double t = 1.0;
+        int accepted = 0;
+        for (int hv = 0; hv <= o->max_halvings; ++hv) {
+            double trial[4];
+            for (int a = 0; a < 4; ++a) trial[a] = th[a] + t * p[a];
+            const double Rt0 = or_response4(hits, n_hits, trial, o->zref, sigma);
+            const double Rt = perturbed(pt, si, j, 32 + hv, Rt0, 1e-5 * fabs(Rt0) + 1e-6);
+            const double need = R + o->c1 * t * slope;
+            const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
+            const double m = fabs(Rt - need) / tol;
+            if (m < *margin) *margin = m;
+            if (Rt >= need) {
+                for (int a = 0; a < 4; ++a) th[a] = trial[a];
+                accepted = 1;
+                break;
+            }
+            t *= 0.5;
+        }
+        if (!accepted) st = 1;
+    }
+    *R_out = or_response4(hits, n_hits, th, o->zref, o->sigma[o->q - 1]);
+    int finite = isfinite(*R_out);
+    for (int a = 0; a < 4; ++a) finite = finite && isfinite(th[a]);
+    return finite ? st : 3;
+}
+
+/*
+ * Algorithm 1's q updates for four-parameter seeds [n][4]; R_out =
+ * R(theta_q; sigma_q); margin as in or_local_search.
  */
 void or_local_search4(const float *hits, int64_t n_hits, const float *seeds, int64_t n_seeds, const or_ls4_opts *o,
                       double *theta_out, double *R_out, uint8_t *status, double *margin_out) {
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t i = 0; i < n_seeds; ++i) {
-        double th[4], margin = INFINITY;
-        int st = 0;
-        for (int a = 0; a < 4; ++a) th[a] = (double)seeds[4 * i + a];
-        for (int j = 0; j < o->q; ++j) {
-            const double sigma = o->sigma[j];
-            double v[29];
-            or_rgh4(hits, n_hits, th, o->zref, sigma, v);
-            const double R = v[0];
-            double p[4];
-            newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, o->scale, p, &margin);
-            double cells = 0.0;
-            for (int a = 0; a < 4; ++a) cells = fmax(cells, fabs(p[a]) / o->scale[a]);
-            if (cells > o->step_cap)
-                for (int a = 0; a < 4; ++a) p[a] *= o->step_cap / cells;
-            double slope = 0.0;
-            for (int a = 0; a < 4; ++a) slope += v[1 + a] * p[a];
-            double t = 1.0;
-            int accepted = 0;
-            for (int hv = 0; hv <= o->max_halvings; ++hv) {
-                double trial[4];
-                for (int a = 0; a < 4; ++a) trial[a] = th[a] + t * p[a];
-                const double Rt = or_response4(hits, n_hits, trial, o->zref, sigma);
-                const double need = R + o->c1 * t * slope;
-                const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
-                const double m = fabs(Rt - need) / tol;
-                if (m < margin) margin = m;
-                if (Rt >= need) {
-                    for (int a = 0; a < 4; ++a) th[a] = trial[a];
-                    accepted = 1;
-                    break;
-                }
-                t *= 0.5;
-            }
-            if (!accepted) st = 1;
-        }
-        R_out[i] = or_response4(hits, n_hits, th, o->zref, o->sigma[o->q - 1]);
-        int finite = isfinite(R_out[i]);
-        for (int a = 0; a < 4; ++a) {
-            theta_out[4 * i + a] = th[a];
-            finite = finite && isfinite(th[a]);
-        }
-        status[i] = (uint8_t)(finite ? st : 3);
-        if (margin_out) margin_out[i] = margin;
+        double m;
+        status[i] = (uint8_t)search4_one(hits, n_hits, seeds + 4 * i, o, NULL, i, theta_out + 4 * i, R_out + i, &m);
+        if (margin_out) margin_out[i] = m;
+    }
+}
+
+/* or_local_search4 with the perturbation (level, key); seed i draws under
+ * index index_base + i. */
+void or_local_search4_perturbed(const float *hits, int64_t n_hits, const float *seeds, int64_t n_seeds,
+                                const or_ls4_opts *o, double level, uint64_t key, int64_t index_base,
+                                double *theta_out, double *R_out, uint8_t *status, double *margin_out) {
+    const or_perturb pt = {level, key};
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n_seeds; ++i) {
+        double m;
+        status[i] = (uint8_t)search4_one(hits, n_hits, seeds + 4 * i, o, &pt, index_base + i, theta_out + 4 * i,
+                                         R_out + i, &m);
+        if (margin_out) margin_out[i] = m;
     }
 }

@@ -43,7 +43,8 @@ using namespace retina;
 extern "C" int retina_grid_maxima_static(const float *R, int32_t n_events, const retina_grid *g, float R0,
                                          int32_t *max_idx, float *max_theta, float *max_R, int32_t *n_max, int32_t K,
                                          void *stream) {
-    if (n_events < 0 || !g || isnan(R0) || K < 1) return RETINA_EINVAL;
+    // the per-event launches put events on gridDim.y (at most 65535)
+    if (n_events < 0 || n_events > 65535 || !g || isnan(R0) || K < 1) return RETINA_EINVAL;
     for (int a = 0; a < 2; ++a)
         if (!isfinite(g->lo[a]) || !(isfinite(g->step[a]) && g->step[a] > 0.f) || g->n[a] <= 0) return RETINA_EINVAL;
     if ((int64_t)g->n[0] * (int64_t)g->n[1] > (int64_t)INT32_MAX) return RETINA_EINVAL;

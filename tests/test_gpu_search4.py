@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+from parity_rules import check_conditioned
 from synth import WORKLOADS, make_event
 
 pytestmark = pytest.mark.gpu
@@ -16,7 +17,7 @@ TH_UNITS = 1e-3
 SCALE = (0.25, 0.25, 2.0 ** -10, 2.0 ** -10)
 SIGMA = (0.3, 0.175, 0.05, 0.05, 0.05)
 ZREF = 225.0  # the mean z of the 26 layers
-CONV_MIN = 120  # the oracle ends 152 of the 400 seeds at a converged maximum
+CONV_MIN = 80  # the oracle ends 103 robust, well-conditioned seeds of 400 at converged maxima
 
 
 @pytest.fixture(scope="module")
@@ -38,46 +39,36 @@ def _event_and_seeds():
     return ev, truth4, seeds.astype(np.float32)
 
 
-def _converged(ev, th, sigma):
-    o = oracle.rgh4(ev.hits, th, sigma, zref=ZREF)
-    H, g = o["hess"], o["grad"]
-    if not np.all(np.linalg.eigvalsh(H) < 0):
-        return None
-    try:
-        Hi = np.linalg.inv(H)
-    except np.linalg.LinAlgError:
-        return None
-    if np.max(np.abs(Hi @ g) / np.asarray(SCALE)) > 0.05:
-        return None
-    return o, Hi
+def _converged_at(ev):
+    def at(th):
+        o = oracle.rgh4(ev.hits, th, SIGMA[-1], zref=ZREF)
+        H, g = o["hess"], o["grad"]
+        if not np.all(np.linalg.eigvalsh(H) < 0):
+            return None
+        try:
+            if np.max(np.abs(np.linalg.solve(H, g)) / np.asarray(SCALE)) > 0.05:
+                return None
+        except np.linalg.LinAlgError:
+            return None
+        return g, H, o["grad_abs"]
+    return at
 
 
 def test_search4_matches_oracle_on_a_smeared_vertex_event(rt):
+    # point-wise parity on every robust seed whose path the oracle's perturbed
+    # replicas show to be well conditioned; ill-conditioned paths must end in
+    # the region the replicas reach (check_conditioned, shared with the
+    # modified-Newton parity test)
     ev, truth4, seeds = _event_and_seeds()
     off = torch.tensor([0, ev.n_hits], dtype=torch.int64, device="cuda")
     th_g, R_g, st_g = rt.local_search4(torch.from_numpy(ev.hits).cuda(), off, torch.from_numpy(seeds).cuda()[None],
                                        rt.LsOpts4(sigma=SIGMA, scale=SCALE, zref=ZREF))
     th_g, R_g, st_g = th_g.cpu().numpy()[0].astype(float), R_g.cpu().numpy()[0].astype(float), st_g.cpu().numpy()[0]
-    th_o, R_o, st_o, m_o = oracle.local_search4(ev.hits, seeds, SIGMA, SCALE, zref=ZREF)
-    robust = m_o >= 1.0
-    assert np.all(st_g[robust] == st_o[robust])
-    scale = np.asarray(SCALE)
-    conv = same = 0
-    for i in np.flatnonzero(st_o <= 1):
-        c = _converged(ev, th_o[i], SIGMA[-1])
-        if c is None:
-            continue
-        o, Hi = c
-        conv += 1
-        if np.max(np.abs(th_g[i] - th_o[i]) / scale) > 0.05:
-            continue
-        same += 1
-        d = np.maximum(TH_UNITS * scale, np.abs(Hi) @ (GH_REL * o["grad_abs"]))
-        assert np.all(np.abs(th_g[i] - th_o[i]) <= d), (i, (th_g[i] - th_o[i]) / scale)
-        tol = R_REL * R_o[i] + R_ABS + np.abs(o["grad"]) @ d + np.abs(o["hess"]).max() * (d @ d)
-        assert abs(R_g[i] - R_o[i]) <= tol, (i, R_g[i], R_o[i], tol)
-    assert conv >= CONV_MIN, conv
-    assert same >= 0.9 * conv, (same, conv)
+
+    def run(pt):
+        return oracle.local_search4(ev.hits, seeds, SIGMA, SCALE, zref=ZREF, perturb=pt)
+
+    check_conditioned(th_g, R_g, st_g, run(None), run, SCALE, _converged_at(ev), min_firm_conv=CONV_MIN)
 
 
 def test_search4_edge_cases(rt):

@@ -623,3 +623,57 @@ def test_oracle_option_ranges_are_enforced():
         oracle.refine_maxima(h, 1, np.zeros((1, 2)), 0.3, (0, 0), (1, 1), (2, 2), iters=0)
     with pytest.raises(ValueError):
         oracle.local_search4(h, np.zeros((1, 4), np.float32), [0.3] * 9, (1, 1, 1, 1))
+
+
+# --------------------------------------------------------------------------
+# perturbed replicas (path conditioning of the parity tests)
+# --------------------------------------------------------------------------
+
+def test_splitmix64_matches_its_published_outputs():
+    # SplitMix64 (Steele, Lea & Flood 2014) from state 0: its first outputs
+    assert oracle.splitmix64(0, 3) == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = [oracle.perturb_u(k, i, j, c) for k in (1, 2) for i in range(50) for j in range(3) for c in range(6)]
+    assert all(-1.0 <= x < 1.0 for x in u)
+    assert abs(np.mean(u)) < 0.1 and 0.25 < np.var(u) < 0.42  # ~ U[-1, 1): variance 1/3
+    assert oracle.perturb_u(7, 3, 1, 2) == oracle.perturb_u(7, 3, 1, 2) != oracle.perturb_u(8, 3, 1, 2)
+
+
+@pytest.mark.parametrize("update", [0, 2])
+def test_level_zero_replica_is_the_plain_search(update):
+    wl = WORKLOADS["velo"]
+    ev = make_event(wl, 0, 3, vertex_sigma=(0, 0, 0))
+    seeds = uniform_seeds(wl, 64, 0, 3)
+    args = (ev.hits, 1, seeds, wl.sigma_schedule, wl.grid_lo, wl.grid_step, wl.grid_n)
+    base = oracle.local_search(*args, update=update)
+    zero = oracle.local_search(*args, update=update, perturb=(0.0, 12345))
+    for a, b in zip(base, zero):
+        assert np.array_equal(a, b)
+    one = oracle.local_search(*args, update=update, perturb=(1.0, 12345))
+    assert not np.array_equal(base[0], one[0])  # the displacement reaches the path
+
+
+def test_replicas_split_at_a_symmetric_saddle_and_agree_on_a_clean_peak():
+    # two noiseless tracks at slopes (+-a, 0): the midpoint (0, 0) has an exactly
+    # zero gradient by symmetry, so the unperturbed search stays there, while
+    # replicas whose gradient is displaced within its tolerance leave it towards
+    # either track - an ill-conditioned path; a seed near one track converges
+    # onto it in every replica - a well-conditioned one
+    a = 2.0 ** -8
+    z = np.array([-300.0 + 42.0 * p for p in range(26)])
+    hits = np.concatenate([np.stack([s * a * z, 0 * z, z, 0 * z], 1) for s in (1.0, -1.0)]).astype(np.float32)
+    lo, step, n = (-0.5, -0.5), (2.0 ** -10, 2.0 ** -10), (1024, 1024)
+    sig = (0.3, 0.175, 0.05)
+    seeds = np.array([[0.0, 0.0], [a + 2 ** -12, 2 ** -12]], np.float32)
+
+    def run(pt):
+        return oracle.local_search(hits, 1, seeds, sig, lo, step, n, perturb=pt)
+
+    base = run(None)
+    # the gradient there is zero up to rounding (~1e-13): the search stays at the saddle
+    assert np.max(np.abs(base[0][0])) < 1e-12
+    assert np.max(np.abs(base[0][1] - [a, 0.0])) < 1e-6
+    stable, ends, sts = oracle.path_conditioning(run, base, 1e-3 * np.asarray(step))
+    assert stable.tolist() == [False, True]
+    assert np.all(np.max(np.abs(ends[:, 1] - base[0][1]), axis=1) < 1e-6)
+    # replicas leave the saddle for both tracks
+    assert ends[:, 0, 0].min() < -0.9 * a and ends[:, 0, 0].max() > 0.9 * a

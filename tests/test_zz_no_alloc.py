@@ -8,9 +8,12 @@ The test calls it through the C ABI twice in a row, on different inputs, and
 checks each result against retina_grid_maxima (which takes a caller
 workspace) on the same input: the selection is integer work on identical
 float32 inputs, so the tolerance used throughout the tests for such outputs
-applies - exact equality.  It also checks that an input too large for the
-fixed scratch is refused with RETINA_ENOSPACE.  The file name makes pytest
-collect it last.
+applies - exact equality.  A 2048 x 2048 case (2048 cell blocks per event,
+more than one pass of the per-event scan) with fewer output slots than
+maxima is also compared with the FP64 oracle's selection on the same values.
+It checks that an input too large for the fixed scratch is refused with
+RETINA_ENOSPACE and too many events with RETINA_EINVAL.  The file name makes
+pytest collect it last.
 """
 import ctypes
 
@@ -18,9 +21,11 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
+
 pytestmark = pytest.mark.gpu
 
-ENOSPACE = 3
+EINVAL, ENOSPACE = 1, 3
 
 
 @pytest.fixture(scope="module")
@@ -82,6 +87,31 @@ def test_static_scratch_maxima_match_workspace_entry_point_on_two_calls(rt):
         _same(ref, got, K)
 
 
+def test_static_scratch_2048_grid_scan_carry_and_truncation(rt):
+    # 2048^2 cells = 2048 blocks of 2048 cells per event: the per-event scan
+    # runs over two 1024-block chunks and carries the first chunk's total;
+    # K below the number of maxima keeps the first K in cell-index order
+    n = 2048
+    # bumps on a noisy plateau above R0: local maxima all over the grid
+    g = torch.Generator(device="cpu").manual_seed(9)
+    R = _field(2, n, n, 3) + 1.0 + 1e-3 * torch.rand((2, n, n), generator=g).cuda()
+    grid = rt.Grid((-0.5, -0.5), (2 ** -11, 2 ** -11), (n, n))
+    R0, K = 0.5, 300
+    for _ in range(2):
+        rc, got = _static_call(rt, R, grid, R0, K)
+        assert rc == 0, rt.lib.retina_strerror(rc)
+        ref = rt.grid_maxima(R, grid, R0, K)
+        torch.cuda.synchronize()
+        _same(ref, got, K)
+    Rh = R.cpu().numpy()
+    for e in range(2):
+        exp, cnt, _ = oracle.grid_maxima(Rh[e], R0, with_margin=True)
+        assert cnt > K and int(got["n_max"][e]) == cnt
+        # both chunks of the scan hold maxima
+        assert exp.min() < 1024 * 2048 and exp.max() >= 1024 * 2048
+        assert got["max_idx"][e].cpu().numpy().tolist() == exp[:K].tolist()
+
+
 def test_static_scratch_refuses_inputs_beyond_its_size(rt):
     # 2 int32 per 2048-cell block per event: 100 events of 2048^2 need 1.6 MB > 1 MiB
     grid = rt.Grid((-0.5, -0.5), (2 ** -11, 2 ** -11), (2048, 2048))
@@ -90,3 +120,7 @@ def test_static_scratch_refuses_inputs_beyond_its_size(rt):
     p = ctypes.c_void_p(dummy.data_ptr())
     rc = rt.lib.retina_grid_maxima_static(p, 100, ctypes.byref(g), 1.0, p, p, p, p, 8, None)
     assert rc == ENOSPACE
+    # more events than one launch dimension holds: refused before any launch
+    small = rt.Grid((-0.5, -0.5), (0.25, 0.25), (4, 4)).c()
+    rc = rt.lib.retina_grid_maxima_static(p, 65536, ctypes.byref(small), 1.0, p, p, p, p, 8, None)
+    assert rc == EINVAL
