@@ -1,18 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the Artificial Retina hot path on GB300 (one JSON line on rank 0).
 
-A step is one pass of the whole hot path over one synthetic VELO-like event
-(150 straight tracks, 26 layers, ~3.9k hits): the 1024 x 1024 grid scan
-(Eq. 2 + maxima, grid algorithm of Section 2), the 8192-seed truncated-Newton
-multistart search (Algorithm 1 with the Section 3 update), and the
-cluster / select extraction of both candidate sets.  ``value`` is events per
-second of that step over all ranks (each rank runs its own event: replicas,
-weak scaling).
+Headline: a step is Algorithm 1 with learned starting points over one batch
+of 1024 high-multiplicity VELO-like events (Poisson(600) tracks, 15 % noise,
+~16.8k hits per event, vertex at the origin): the hit ordering, the learned
+proposer (slope histogram, small conv net, top-2048 seeds per event), the
+seeds' spatial order, the persistent batched truncated-Newton search
+(Section 3's update and sigma schedule) and the cluster / select extraction,
+replayed as one CUDA graph by the native tracker (retina_tracker_*).
+``value`` is events per second over all ranks (each rank its own batch:
+replicas, weak scaling).  The line also carries the search kernel against
+the FP32 lane rate measured live, the MC efficiency, the end-to-end rate from
+host buffers, and the FP64 oracle on a sample of the same events (time and
+efficiency).  ``extras`` holds the other workloads: the single-event step
+(1024^2 grid scan + 8192-seed search, smeared and origin vertex), the 2D
+toy, the four-parameter search, the 1024-event method comparison, the
+alpha-budget sweep and the paper's sVELO experiment.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this
-method has) on the host cores, on a bounded sample of the same step.
+method has) on the host cores, on a bounded sample of the headline batch.
 """
 from __future__ import annotations
 
@@ -35,21 +43,24 @@ from synth import VELO_PLANES_Z, WORKLOADS, batch_of, make_event, uniform_seeds 
 
 WORKLOAD = "velo"
 RUN_SEED = 0
-METRIC = "events/s (grid scan + truncated-Newton search + extraction, one VELO-like event per step)"
+METRIC = ("events/s (learned-seed batched local search at >= 95% of the oracle's track efficiency: hit "
+          "ordering, proposer, top-2048 seeds, truncated-Newton search, extraction; 1024 high-multiplicity events "
+          "per step)")
 L2_FLUSH_BYTES = 256 << 20
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparisons")
+    ap.add_argument("--no-extras", action="store_true", help="the headline alone (no other workloads)")
     ap.add_argument("--serial", action="store_true", help="run the grid and search branches on one stream")
     ap.add_argument("--shape", default=None, metavar="P,W,H,C,S",
                     help="fixed launch shape instead of the autotuner's (profiling runs): search seeds per warp, "
@@ -77,7 +88,9 @@ CSRC = os.path.join(HERE, "paper_1709_08610_gb300", "csrc")
 # holding its DRAM traffic per launch
 PROFILED = {
     "batched_search_kernel": (("search_device.cuh", "batched_search.cu", "common.cuh", "internal.cuh"),
-                              "profiles/batched_search_kernel_velo_single_event.md"),
+                              "profiles/batched_search_kernel_velo_stress_1024_events.md"),
+    "batched_search_kernel/single": (("search_device.cuh", "batched_search.cu", "common.cuh", "internal.cuh"),
+                                     "profiles/batched_search_kernel_velo_single_event.md"),
     "grid_tc_kernel": (("grid_tc.cu", "grid_device.cuh", "common.cuh", "internal.cuh"),
                        "profiles/grid_tc_kernel_velo_1024x1024.md"),
 }
@@ -247,45 +260,6 @@ def oracle_agreement(oracle_tracks, gpu_tracks, step, tol_cells: float = 1e-3) -
 def oracle_threads() -> int:
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
-
-
-def run_reference(args, rank: int):
-    if rank != 0:
-        return
-    import oracle
-    oracle.build()
-    wl = WORKLOADS[WORKLOAD]
-    ev = make_event(wl, RUN_SEED, 0)
-    seeds = uniform_seeds(wl, wl.n_seeds, RUN_SEED, 0)
-    # size each step's sample so the whole --steps/--warmup run takes ~90 s
-    _, probe_wall, _ = oracle_step_sample(ev, wl, seeds, 64, 64)
-    t_full = probe_wall * 64.0
-    frac = min(1.0, max(1.0 / 1024, 90.0 / max(1, args.steps + max(args.warmup, 0)) / max(t_full, 1e-6)))
-    row_frac = int(min(wl.grid_n[1], max(1, round(1.0 / frac))))
-    seed_frac = int(min(wl.n_seeds, max(1, round(1.0 / frac))))
-    for _ in range(max(args.warmup, 0)):
-        oracle_step_sample(ev, wl, seeds, row_frac, seed_frac)
-    est = []
-    cpu_s = 0.0
-    for _ in range(args.steps):
-        e, c, _ = oracle_step_sample(ev, wl, seeds, row_frac, seed_frac)
-        est.append(e)
-        cpu_s += c
-    sec_per_event = float(np.mean(est))
-    value = 1.0 / sec_per_event
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_event, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(wl, ev.n_hits),
-        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle_threads(), "kind": "oracle",
-                         "sample": "per step: 1/%d of the grid rows (%d x %d cells) and 1/%d of the seeds (%d), "
-                                   "extrapolated to the whole event" % (row_frac, wl.grid_n[0],
-                                                                        wl.grid_n[1] // row_frac, seed_frac,
-                                                                        wl.n_seeds // seed_frac)},
-        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -588,28 +562,17 @@ def svelo_sweep(rt, stream, flush, reps: int = 3):
 # our arm
 # ---------------------------------------------------------------------------
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank)
-        return
-
+def single_event_step(rt, tune, args, dev, rank, peaks, vertex_sigma=None, with_cpu=False, steps=400):
+    """The single-event step (one VELO-like event: the 1024 x 1024 grid scan,
+    the 8192-seed truncated-Newton search and the extraction of both, the two
+    branches on concurrent streams after the shared hit ordering), timed over
+    ``steps`` steps behind an L2 flush each; launch shapes from the
+    autotuner; the end-to-end rate through the native executor with host
+    copies; with ``with_cpu`` the oracle on the same event (time and track
+    agreement)."""
     import torch
-    import torch.distributed as dist
-    from paper_1709_08610_gb300 import build as rbuild
-    rbuild.build()
-    from paper_1709_08610_gb300 import retina as rt
-    from paper_1709_08610_gb300 import tune
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
     wl = WORKLOADS[WORKLOAD]
-    ev = make_event(wl, RUN_SEED, rank)
+    ev = make_event(wl, RUN_SEED, rank, **({} if vertex_sigma is None else {"vertex_sigma": vertex_sigma}))
     seeds_np = uniform_seeds(wl, wl.n_seeds, RUN_SEED, rank)
     H = ev.n_hits
     grid = rt.Grid.of(wl)
@@ -795,61 +758,33 @@ def main():
         tuned["overlap"] = {"warps": w, "ctas": c, "grid_splits": sp, "smem_hits": h, "step_ms": table[best],
                             "table_ms": table}
 
-    # ---- peaks of the FP32 and MUFU pipes, measured live (burst)
-    peaks = {}
-    if not args.no_probe:
-        sink = torch.empty(rt.alu_probe_sink_floats(), dtype=torch.float32, device=dev)
-        for kind, name, iters in ((0, "ffma", 4096), (2, "ffma2", 4096), (1, "ex2", 1024)):
-            rt.alu_probe(kind, 64, sink)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            best = None
-            for _ in range(3):
-                a.record(stream)
-                ops = rt.alu_probe(kind, iters, sink)
-                b.record(stream)
-                b.synchronize()
-                r = ops / (a.elapsed_time(b) * 1e-3)
-                best = r if best is None else max(best, r)
-            peaks[name] = best
     fma_rate = max(peaks.get("ffma", 0.0), peaks.get("ffma2", 0.0))
 
     # ---- the step graph, then warm-up
     graph, kernels_per_step = capture() if args.graph else (None, 0)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(5):
         if graph is not None:
             graph.replay()
         else:
             step()
     torch.cuda.synchronize()
 
-    # ---- timed region
+    # ---- timed steps
     evs = None if graph is not None else [[torch.cuda.Event(enable_timing=True) for _ in range(8)]
-                                          for _ in range(args.steps)]
-    clocks = ClockSampler(local_rank) if not args.no_clocks else None
-    if world > 1:
-        dist.barrier()
+                                          for _ in range(steps)]
     torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
     launches0 = rt.launch_count()
-    t_wall0 = time.perf_counter()
-    marks = timed_steps(graph, args.steps, evs)
+    marks = timed_steps(graph, steps, evs)
     torch.cuda.synchronize()
-    t_wall1 = time.perf_counter()
-    launches = rt.launch_count() - launches0 + kernels_per_step * args.steps
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop() if clocks else None
+    launches = rt.launch_count() - launches0 + kernels_per_step * steps
 
     # stages: prepare, grid response, maxima + extract (main stream), search, extract (search stream)
     # (one stream: the search branch is enqueued first, so the grid response runs from event 6 to 2)
     pairs = [(0, 1), (6, 2) if args.serial else (1, 2), (2, 3), (4, 5), (5, 6)]
     stage = np.stack([marks[:, b] - marks[:, a] for a, b in pairs], axis=1)
     step_ms = marks[:, 7]
-    total_ms = max_over_ranks(float(step_ms.sum()), dev)
-    ms_per_step = total_ms / args.steps
-    value = replica_events_per_s(world, args.steps, total_ms)
+    ms_per_step = float(step_ms.mean())
+    value = 1e3 / ms_per_step
 
     # ---- work the two response kernels perform (counted on the device in
     # one extra step outside the timed region; exact block skipping means
@@ -904,7 +839,7 @@ def main():
     fr_ex2 = (search_ex2_rate / ex2_peak) if ex2_peak else None
     roof_search = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Tlane-op/s",
                    "achieved": search_fp32_rate / 1e12, "peak": (fma_rate / 1e12) if fma_rate else None,
-                   "frac": fr_fp32, "traffic": profiled_traffic("batched_search_kernel"),
+                   "frac": fr_fp32, "traffic": profiled_traffic("batched_search_kernel/single"),
                    "pairs_per_s": (rgh_pairs + r_pairs) / (search_ms * 1e-3),
                    "ex2_per_s": search_ex2_rate, "frac_ex2": fr_ex2, "rgh_pairs": rgh_pairs, "r_pairs": r_pairs,
                    "pairs_total": (wl.n_seeds * len(wl.sigma_schedule) + n_ev) * H,
@@ -918,10 +853,10 @@ def main():
     # launch of the step, the two branches on two streams) - or replays the step
     # graph with --graph - and copies both track lists out to pinned host memory
     e2e = None
-    if rank == 0 or True:
+    if True:
         hits_h = torch.from_numpy(ev.hits).pin_memory()
         seeds_h = torch.from_numpy(seeds_np).view(-1, 2).pin_memory()
-        n_e2e = max(10, min(args.steps, 200))
+        n_e2e = 200
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         keys = ("tracks", "track_R", "n_tracks")
 
@@ -991,7 +926,7 @@ def main():
             assert torch.equal(out_h[m]["tracks"][0, :k], ref["tracks"][0, :k].cpu())
         d2h = sum(v.numel() * v.element_size() for m in out_h for v in out_h[m].values())
         h2d = hits_h.numel() * 4 + seeds_h.numel() * 4
-        e2e = {"value": world * 1e3 / e2e_ms, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": 1e3 / e2e_ms, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                "note": "%s; every step copies its hits and seeds in from pinned host memory and both track lists "
                        "out to pinned host memory, timed with CUDA events"
@@ -1004,7 +939,7 @@ def main():
 
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if with_cpu:
         import oracle
         oracle.build()
         ests, wall = [], 0.0
@@ -1022,47 +957,426 @@ def main():
                "sample": "%d whole steps of the same event (grid %d x %d, %d seeds), %.1f s of CPU work"
                          % (len(ests), n0, n1, wl.n_seeds, wall)}
 
-    batched = stress = alpha = svelo = search4 = None
-    if world == 1:
-        search4 = search4_measure(rt, stream, flush, ev, wl)
-    if world == 1 and not args.no_batched:
-        # launch shapes tuned for one event do not carry over to 1024: the grid's
-        # hit-slice count goes back to the library's rule (one slice at this
-        # many tiles: no partials buffer) and the search fills the GPU
-        saved = {o: rt.get_option(o) for o in (rt.OPT_GRID_SPLITS, rt.OPT_BATCH_CTAS)}
-        rt.set_option(rt.OPT_GRID_SPLITS, 0)
-        rt.set_option(rt.OPT_BATCH_CTAS, 0)
-        batched = batched_methods(rt, stream, flush, comparisons=True)
-        alpha = alpha_sweep(rt, stream, flush)
-        svelo = svelo_sweep(rt, stream, flush)
-        stress = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
-        for o, v in saved.items():
+    tr_n = (int(tr_grid["n_tracks"].item()), int(tr_search["n_tracks"].item()))
+    return {
+        "workload": workload_config(wl, H)["workload"] + ("" if vertex_sigma is None else
+                                                          " (vertex at the origin)"),
+        "events_per_s": value, "ms_per_step": ms_per_step, "steps": steps, "e2e": e2e,
+        "gpu_launches_per_step": launches / steps, "roofline": roofline,
+        "roofline_other": roof_search if dominant == "grid" else roof_grid,
+        "stages_ms": {"prepare_hits": prep_ms, "grid_response": grid_ms,
+                      "grid_maxima_extract": float(np.mean(stage[:, 2])), "local_search": search_ms,
+                      "search_extract": float(np.mean(stage[:, 4]))},
+        "methods_events_per_s": {"grid_scan": 1e3 / (prep_ms + grid_ms + float(np.mean(stage[:, 2]))),
+                                 "local_search": 1e3 / (prep_ms + search_ms + float(np.mean(stage[:, 4])))},
+        "tracks_found": {"grid": tr_n[0], "search": tr_n[1]}, "cpu_oracle": cpu, "tuned": tuned,
+        "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+        "branches": "one stream" if args.serial else
+                    "grid branch and search branch on two concurrent streams after the shared hit ordering",
+        "launch": "kernels enqueued one by one" if graph is None else
+                  "one CUDA graph replay per step (%d kernels)" % kernels_per_step,
+    }
+
+
+# ---------------------------------------------------------------------------
+# headline: the learned-seed batched search on the high-multiplicity batch
+# ---------------------------------------------------------------------------
+
+HEADLINE = "velo_stress"
+HEADLINE_EVENTS = 1024
+HEADLINE_SEEDS = 2048
+HEADLINE_TRACKS = 1024
+HEADLINE_RUN_SEED = 7000
+
+
+def headline_batch(rank: int = 0):
+    """1024 high-multiplicity VELO-like events with the vertex at the origin
+    (each rank its own batch)."""
+    wl = WORKLOADS[HEADLINE]
+    evs = [make_event(wl, HEADLINE_RUN_SEED + 1000 * rank, e, vertex_sigma=(0, 0, 0)) for e in range(HEADLINE_EVENTS)]
+    return wl, evs, batch_of(evs)
+
+
+def headline_config(wl, n_hits: int) -> dict:
+    gen = wl.gen
+    E = HEADLINE_EVENTS
+    return {
+        "workload": "velo_stress: %d high-multiplicity VELO-like events per step (tracks ~ Poisson(%g) clipped to "
+                    "[%g, %g], 15%% noise hits, 26 layers at z=-300..750 mm, 90%% layer efficiency, vertex at the "
+                    "origin; %d hits, %.0f per event); learned seed proposer (64x64 slope histogram, conv 1->16->32 + "
+                    "1x1 head, top-%d seeds per event at dense sub-cells), spatial seed order, persistent batched "
+                    "truncated-Newton search (q=3, sigma 0.3/0.175/0.05 mm), cluster/select extraction; one CUDA "
+                    "graph per step" % ((E,) + tuple(gen["n_tracks"]) + (n_hits, n_hits / E, HEADLINE_SEEDS)),
+        "events": E, "seeds_per_event": HEADLINE_SEEDS, "hits": int(n_hits), "q": len(wl.sigma_schedule),
+        "box": {"lo": list(wl.grid_lo), "step": list(wl.grid_step), "n": list(wl.grid_n)},
+        "l2": "inputs larger than L2 (%.0f MB of hits) and L2 flushed between timed steps (256 MiB write outside "
+              "the timed events)" % (n_hits * 16 / 1e6),
+        "parallelism": "replicas (one batch per rank, no collective on the data path)",
+    }
+
+
+def oracle_learned_event(ev, wl, params, n_seeds: int, seed_frac: int = 1):
+    """The oracle's learned-seed pipeline on one event (FP64 histogram and
+    network, its own top-n seeds, the C oracle's search on 1/seed_frac of
+    them, extraction); returns (seconds extrapolated to all n seeds, seconds
+    spent, tracks [m, 2] or None when sampled)."""
+    import oracle
+    from oracle import seednet as sn
+    t0 = time.perf_counter()
+    _, feat = sn.slope_histogram(ev.hits)
+    z = sn.forward(feat, params)["z"].astype(np.float32)
+    seeds, _ = sn.propose_seeds(z, ev.hits, n_seeds)
+    t1 = time.perf_counter()
+    ns = max(1, n_seeds // max(1, seed_frac))
+    th, R, st, _ = oracle.local_search(ev.hits, 1, seeds[:ns], wl.sigma_schedule, wl.grid_lo, wl.grid_step, wl.grid_n)
+    keep = oracle.extract_tracks(th, R, st, wl.grid_lo, wl.grid_step, wl.grid_n, wl.R0, wl.merge_cells)
+    t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1) * (n_seeds / ns), t2 - t0, (th[keep] if ns == n_seeds else None)
+
+
+def run_reference(args, rank: int):
+    """The reference arm: the FP64 oracle's learned-seed pipeline on the host
+    cores, each step one event of the headline batch with a fraction of its
+    seeds (extrapolated), sized so the whole run takes about 90 s."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, read_checkpoint
+    oracle.build()
+    wl = WORKLOADS[HEADLINE]
+    evs = [make_event(wl, HEADLINE_RUN_SEED, e, vertex_sigma=(0, 0, 0)) for e in range(8)]
+    params = read_checkpoint(DEFAULT_WEIGHTS)[1]["params"]
+    full, _, _ = oracle_learned_event(evs[0], wl, params, HEADLINE_SEEDS, 16)
+    budget = 90.0 / max(1, args.steps + max(args.warmup, 0))
+    seed_frac = int(min(HEADLINE_SEEDS, max(1, np.ceil(full / max(budget, 1e-3)))))
+    for k in range(max(args.warmup, 0)):
+        oracle_learned_event(evs[k % len(evs)], wl, params, HEADLINE_SEEDS, seed_frac)
+    est = [oracle_learned_event(evs[k % len(evs)], wl, params, HEADLINE_SEEDS, seed_frac)[0] for k in range(args.steps)]
+    value = 1.0 / float(np.mean(est))
+    H_mean = float(np.mean([ev.n_hits for ev in evs]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * HEADLINE_EVENTS / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": headline_config(wl, int(H_mean * HEADLINE_EVENTS)),
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": oracle_threads(), "kind": "oracle",
+                         "sample": "per step one event of the batch (%.0f hits on average) with 1/%d of its %d "
+                                   "learned seeds searched (the proposer in full), extrapolated to the whole event"
+                                   % (H_mean, seed_frac, HEADLINE_SEEDS)},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def probe_peaks(rt, stream) -> dict:
+    """FP32 (FFMA, packed FFMA2) and MUFU ex2 throughput, measured live (burst)."""
+    import torch
+    peaks = {}
+    sink = torch.empty(rt.alu_probe_sink_floats(), dtype=torch.float32, device="cuda")
+    for kind, name, iters in ((0, "ffma", 4096), (2, "ffma2", 4096), (1, "ex2", 1024)):
+        rt.alu_probe(kind, 64, sink)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(3):
+            a.record(stream)
+            ops = rt.alu_probe(kind, iters, sink)
+            b.record(stream)
+            b.synchronize()
+            r = ops / (a.elapsed_time(b) * 1e-3)
+            best = r if best is None else max(best, r)
+        peaks[name] = best
+    return peaks
+
+
+def headline(rt, args, dev, rank, world, peaks, local_rank):
+    """The learned-seed batched search through the native tracker: events/s
+    over the timed steps (device time from the tracker's stage marks, inside
+    the graph replays), the search kernel against the FP32 lane rate, MC
+    efficiency, the end-to-end rate from host buffers, and (rank 0, one GPU)
+    the oracle on a sample of the same events."""
+    import torch
+    import torch.distributed as dist
+    from paper_1709_08610_gb300.pipeline import match_efficiency
+    from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, read_checkpoint
+    wl, evs, b = headline_batch(rank)
+    E, S, K = HEADLINE_EVENTS, HEADLINE_SEEDS, HEADLINE_TRACKS
+    H = int(b.hits.shape[0])
+    params = read_checkpoint(DEFAULT_WEIGHTS)[1]["params"]
+    box = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    # throughput-bound batch: two spatially ordered seeds per warp, 32-warp CTAs, 12288 staged hits
+    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    tr = rt.Tracker(box, opts, wl.R0, wl.merge_cells, E, H, S, max_tracks=K, params=params, **shape)
+    tr.load(b.hits, b.offsets)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    tr.set_marks(marks)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    n0 = rt.launch_count()
+    tr.step(E, stream)  # records the graph, then replays it
+    torch.cuda.synchronize()
+    kernels_per_step = rt.launch_count() - n0
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        tr.step(E, stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    clocks = ClockSampler(local_rank) if not args.no_clocks else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    st_ms = np.zeros((args.steps, 5))
+    for k in range(args.steps):
+        flush.zero_()
+        tr.step(E, stream)
+        marks[5].synchronize()
+        st_ms[k] = [marks[i].elapsed_time(marks[i + 1]) for i in range(5)]
+    torch.cuda.synchronize()
+    t_wall1 = time.perf_counter()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = st_ms.sum(axis=1)
+    total_ms = max_over_ranks(float(step_ms.sum()), dev)
+    ms_per_step = total_ms / args.steps
+    value = world * E * args.steps / (total_ms * 1e-3)
+    found = tr.results(E)
+
+    # ---- work of the search kernel, counted on the device in one eager step of a
+    # second tracker (same launches, same results - checked bit for bit)
+    tc = rt.Tracker(box, opts, wl.R0, wl.merge_cells, E, H, S, max_tracks=K, params=params, use_graph=False, **shape)
+    tc.load(b.hits, b.offsets)
+    rt.work_counters(enable=True, reset=True)
+    tc.step(E, stream)
+    torch.cuda.synchronize()
+    w = rt.work_counters(enable=False)
+    assert torch.equal(tc.n_tracks, tr.n_tracks) and torch.equal(tc.tracks, tr.tracks)
+    tc.close()
+    rgh, rr = int(w[rt.WORK_RGH]), int(w[rt.WORK_R])
+    search_ms = float(st_ms[:, 3].mean())
+    fma_rate = max(peaks.get("ffma", 0.0), peaks.get("ffma2", 0.0))
+    lane_ops = 15.0 * rgh + 5.0 * rr  # FP32 operations per pair (an FMA counts once): RGH 15, R alone 5
+    achieved = lane_ops / (search_ms * 1e-3)
+    ex2_rate = (rgh + rr) / (search_ms * 1e-3)
+    roofline = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Tlane-op/s",
+                "achieved": achieved / 1e12, "peak": fma_rate / 1e12 if fma_rate else None,
+                "frac": achieved / fma_rate if fma_rate else None,
+                "traffic": profiled_traffic("batched_search_kernel"),
+                "rgh_pairs": rgh, "r_pairs": rr, "pairs_per_s": (rgh + rr) / (search_ms * 1e-3),
+                "ex2_per_s": ex2_rate, "frac_ex2": ex2_rate / peaks["ex2"] if peaks.get("ex2") else None,
+                "kernel_ms": search_ms,
+                "work_unit": "15 FP32 lane operations per (seed, hit) pair of a gradient/Hessian pass and 5 per "
+                             "pair of an R-only (line-search) pass, pairs counted on the device after exact block "
+                             "skipping",
+                "peak_source": "FP32 lane-FMA rate measured live by retina_alu_probe (burst; the faster of FFMA and "
+                               "packed FFMA2); no FP32 figure is on record in MEASURED_PEAKS.json"}
+    truth = [ev.truth[:, :2] for ev in evs]
+    eff, fakes = match_efficiency(found, truth)
+
+    # ---- end to end through the public API from host buffers: every step copies
+    # the batch's hits and offsets in from page-locked host memory, replays the
+    # step, and copies every event's track list out (retina_tracker_run_host)
+    hits_h = torch.from_numpy(b.hits).pin_memory()
+    offs_h = torch.from_numpy(b.offsets).pin_memory()
+    out_h = dict(tracks=torch.empty((E, K, 2), dtype=torch.float32).pin_memory(),
+                 track_R=torch.empty((E, K), dtype=torch.float32).pin_memory(),
+                 n_tracks=torch.empty((E,), dtype=torch.int32).pin_memory())
+    tr.set_marks(None)
+    tr.run_host(hits_h, offs_h, out_h, stream=stream)  # records the graph again (without marks)
+    torch.cuda.synchronize()
+    n_e2e = max(5, min(args.steps, 20))
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n_e2e):
+        tr.run_host(hits_h, offs_h, out_h, stream=stream)
+    c.record(stream)
+    c.synchronize()
+    e2e_ms = a.elapsed_time(c) / n_e2e
+    assert torch.equal(out_h["n_tracks"], tr.n_tracks.cpu())
+    h2d = hits_h.numel() * 4 + offs_h.numel() * 8
+    d2h = sum(v.numel() * v.element_size() for v in out_h.values())
+    e2e = {"value": world * E / (max_over_ranks(e2e_ms, dev) * 1e-3), "unit": "events/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+           "note": "retina_tracker_run_host per step: the batch's hits and offsets copied in from page-locked host "
+                   "memory, the step's graph replayed, every event's track list (tracks, R, count) copied out to "
+                   "page-locked host memory, in stream order, timed with CUDA events; steps back to back"}
+
+    # ---- the oracle on a sample of the same events (rank 0, one GPU)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        est, wall, o_tracks = [], 0.0, []
+        while wall < 15.0 and len(est) < 32:
+            e_, w_, t_ = oracle_learned_event(evs[len(est)], wl, params, S)
+            est.append(e_)
+            wall += w_
+            o_tracks.append(t_)
+        n_o = len(est)
+        eff_o, fakes_o = match_efficiency(o_tracks, truth[:n_o])
+        eff_g, fakes_g = match_efficiency(found[:n_o], truth[:n_o])
+        agree, _ = match_efficiency(found[:n_o], o_tracks)  # oracle tracks the GPU also finds (1e-3)
+        extra_g, _ = match_efficiency(o_tracks, found[:n_o])
+        cpu = {"value": n_o / sum(est), "unit": "events/s", "cores": oracle_threads(), "kind": "oracle",
+               "sample": "the first %d events of the batch, each through the oracle's whole learned-seed pipeline "
+                         "(FP64 proposer, its own top-%d seeds, the C oracle's search of all of them, extraction), "
+                         "%.1f s of CPU work" % (n_o, S, wall),
+               "efficiency": {"events": n_o, "oracle_mc_efficiency": eff_o, "gpu_mc_efficiency": eff_g,
+                              "gpu_over_oracle": eff_g / eff_o if eff_o else None,
+                              "oracle_fakes_per_event": fakes_o / n_o, "gpu_fakes_per_event": fakes_g / n_o,
+                              "oracle_tracks_found_by_gpu": agree, "gpu_tracks_found_by_oracle": extra_g,
+                              "match": "|dtheta|_max <= 1e-3 in slope"}}
+    tr.close()
+    return {
+        "value": value, "ms_per_step": ms_per_step, "config": headline_config(wl, H), "e2e": e2e,
+        "gpu_launches": int(kernels_per_step * args.steps), "kernels_per_step": int(kernels_per_step),
+        "roofline": roofline, "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0,
+        "stages_ms": {n: float(st_ms[:, i].mean()) for i, n in enumerate(
+            ("prepare_hits", "proposer", "sort_seeds", "search", "extract"))},
+        "mc_efficiency": eff, "fakes_per_event": fakes / E,
+        "tracks_per_event": float(np.mean([len(f) for f in found])),
+        "truth_tracks_per_event": float(np.mean([len(t) for t in truth])),
+    }
+
+
+def toy_step(rt, steps: int = 400, with_cpu: bool = True):
+    """The 2D straight-line toy (one event per step): the 200 x 200 grid scan,
+    the 256-seed search and the extraction of both, enqueued on one stream,
+    with the oracle's track lists on the same event."""
+    import torch
+    wl = WORKLOADS["toy2d"]
+    ev = make_event(wl, RUN_SEED, 0)
+    seeds_np = uniform_seeds(wl, wl.n_seeds, RUN_SEED, 0)
+    hits = torch.from_numpy(ev.hits).cuda()
+    offs = torch.tensor([0, ev.n_hits], dtype=torch.int64, device="cuda")
+    seeds = torch.from_numpy(seeds_np).cuda()[None]
+    grid = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    R0 = float(np.float32(wl.R0))
+
+    def step():
+        g = rt.grid_scan(hits, offs, 0, grid, wl.sigma_grid, R0, 1024)
+        tg = rt.extract_tracks(g["max_theta"], g["max_R"], None, grid, R0, wl.merge_cells, 256, n_valid=g["n_max"])
+        th, R, st = rt.local_search(hits, offs, 0, seeds, opts, grid)
+        ts = rt.extract_tracks(th, R, st, grid, R0, wl.merge_cells, 256)
+        return tg, ts
+
+    for _ in range(5):
+        step()
+    torch.cuda.synchronize()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        tg, ts = step()
+    c.record()
+    c.synchronize()
+    ms = a.elapsed_time(c) / steps
+    out = {"workload": "toy2d: one 2D straight-line event per step (10 tracks y = alpha x + beta, 10 planes, 20%% "
+                       "noise, %d hits); 200x200 grid scan (sigma %.4f) + 256-seed truncated-Newton search + "
+                       "extraction of both, one stream, back to back" % (ev.n_hits, wl.sigma_grid),
+           "events_per_s": 1e3 / ms, "ms_per_step": ms, "steps": steps,
+           "tracks_found": {"grid": int(tg["n_tracks"].item()), "search": int(ts["n_tracks"].item())}}
+    if with_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        R = oracle.grid_response(ev.hits, 0, wl.grid_lo, wl.grid_step, wl.grid_n, wl.sigma_grid)
+        idx = oracle.grid_maxima(R, wl.R0)
+        cen = oracle.maxima_centres(idx, wl.grid_lo, wl.grid_step, wl.grid_n)
+        kg = oracle.extract_tracks(cen, R.reshape(-1)[idx], None, wl.grid_lo, wl.grid_step, wl.grid_n, R0,
+                                   wl.merge_cells)
+        th, Rs, st, _ = oracle.local_search(ev.hits, 0, seeds_np, wl.sigma_schedule, wl.grid_lo, wl.grid_step,
+                                            wl.grid_n)
+        ks = oracle.extract_tracks(th, Rs, st, wl.grid_lo, wl.grid_step, wl.grid_n, R0, wl.merge_cells)
+        t1 = time.perf_counter()
+        out["cpu_oracle"] = {"events_per_s": 1.0 / (t1 - t0), "cores": oracle_threads(), "track_agreement": {
+            "grid": oracle_agreement(cen[kg], tg["tracks"][0, :int(tg["n_tracks"].item())].cpu().numpy(),
+                                     wl.grid_step),
+            "search": oracle_agreement(th[ks], ts["tracks"][0, :int(ts["n_tracks"].item())].cpu().numpy(),
+                                       wl.grid_step)}}
+    return out
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1709_08610_gb300 import build as rbuild
+    rbuild.build()
+    from paper_1709_08610_gb300 import retina as rt
+    from paper_1709_08610_gb300 import tune
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    peaks = {} if args.no_probe else probe_peaks(rt, stream)
+    options = (rt.OPT_LS_SEEDS_PER_WARP, rt.OPT_LS_SMEM_HITS, rt.OPT_GRID_SPLITS, rt.OPT_LS_WARPS,
+               rt.OPT_BATCH_SEEDS_PER_WARP, rt.OPT_BATCH_WARPS, rt.OPT_BATCH_SMEM_HITS, rt.OPT_BATCH_CTAS,
+               rt.OPT_SEEDNET_TC, rt.OPT_GRID_TC)
+    defaults = {o: rt.get_option(o) for o in options}
+
+    def restore():
+        for o, v in defaults.items():
             rt.set_option(o, v)
 
+    head = headline(rt, args, dev, rank, world, peaks, local_rank)
+
+    extras = {}
+    if world == 1 and not args.no_extras:
+        with_cpu = not args.no_cpu_baseline
+        # the single-event step (grid scan + 8192-seed search + both extractions) as
+        # generated (smeared vertex) and with the vertex at the origin
+        extras["single_event_velo"] = single_event_step(rt, tune, args, dev, rank, peaks, with_cpu=with_cpu)
+        restore()
+        extras["single_event_velo_origin"] = single_event_step(rt, tune, args, dev, rank, peaks,
+                                                               vertex_sigma=(0, 0, 0), with_cpu=with_cpu)
+        restore()
+        extras["toy2d"] = toy_step(rt, with_cpu=with_cpu)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        wl2 = WORKLOADS["velo"]
+        extras["search4"] = search4_measure(rt, stream, flush, make_event(wl2, RUN_SEED, rank), wl2)
+        if not args.no_batched:
+            # the library's launch rules for batches: one grid hit slice at this many
+            # tiles, the search filling the GPU
+            rt.set_option(rt.OPT_GRID_SPLITS, 0)
+            rt.set_option(rt.OPT_BATCH_CTAS, 0)
+            extras["batched"] = batched_methods(rt, stream, flush, comparisons=True)
+            extras["alpha_sweep"] = alpha_sweep(rt, stream, flush)
+            extras["svelo_sweep"] = svelo_sweep(rt, stream, flush)
+            extras["batched_stress"] = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
+            restore()
+
     if rank == 0:
-        tr_n = (int(tr_grid["n_tracks"].item()), int(tr_search["n_tracks"].item()))
+        cfg = head["config"]
         line = {
-            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(wl, H),
-                           branches="one stream" if args.serial else
-                           "grid branch and search branch on two concurrent streams after the shared hit ordering",
-                           launch="kernels enqueued one by one" if graph is None else
-                           "one CUDA graph replay per step (%d kernels)" % kernels_per_step),
-            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "roofline_other": roof_search if dominant == "grid" else roof_grid,
-            "stages_ms": {"prepare_hits": prep_ms, "grid_response": grid_ms,
-                          "grid_maxima_extract": float(np.mean(stage[:, 2])), "local_search": search_ms,
-                          "search_extract": float(np.mean(stage[:, 4]))},
-            "methods_events_per_s": {"grid_scan": 1e3 / (prep_ms + grid_ms + float(np.mean(stage[:, 2]))),
-                                     "local_search": 1e3 / (prep_ms + search_ms + float(np.mean(stage[:, 4])))},
-            "tracks_found": {"grid": tr_n[0], "search": tr_n[1]},
+            "metric": METRIC, "value": head["value"], "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator of the workload's stated "
+                                                         "distributions; no dataset)",
+            "config": cfg, "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"],
+            "cpu_baseline": head["cpu_baseline"], "clocks": head["clocks"],
+            "efficiency": {"mc_efficiency": head["mc_efficiency"], "fakes_per_event": head["fakes_per_event"],
+                           "tracks_per_event": head["tracks_per_event"],
+                           "truth_tracks_per_event": head["truth_tracks_per_event"],
+                           "vs_oracle": (head["cpu_baseline"] or {}).get("efficiency")},
+            "stages_ms": head["stages_ms"], "kernels_per_step": head["kernels_per_step"],
+            "wall_s_timed": head["wall_s_timed"],
             "peaks_measured": {"ffma_per_s": peaks.get("ffma"), "ffma2_per_s": peaks.get("ffma2"),
                                "ex2_per_s": peaks.get("ex2")},
-            "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0, "batched": batched,
-            "batched_stress": stress, "alpha_sweep": alpha, "svelo_sweep": svelo, "search4": search4,
-            "tuned": tuned,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

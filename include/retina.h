@@ -697,6 +697,102 @@ int retina_pipeline_run(retina_pipeline *p, const float *hits, int64_t n_hits, c
                         int32_t *search_n_tracks, void *stream);
 int retina_pipeline_destroy(retina_pipeline *p);
 
+/*
+ * retina_tracker_* - Algorithm 1 over a batch of events in one call, replayed
+ * as one CUDA graph.
+ *
+ * Paper: Algorithm 1 (starting points from a prior, the Section 3 updates,
+ * cluster / select) over many events; the tracker itself is not a step of
+ * the paper but a native executor of the batched search.  A step is: the hit
+ * ordering (retina_prepare_hits); the starting points - the learned
+ * proposer (retina_slope_histogram over [-0.5, 0.5)^2 with |z| >= 50,
+ * retina_seednet_forward, retina_topk_seeds with 3 hits per sub-cell) when
+ * the tracker was created with network parameters, else the caller's; their
+ * spatial order (retina_sort_seeds) when configured; the persistent batched
+ * search (retina_batched_search); cluster / select (retina_extract_tracks).
+ * Slope-model (RETINA_VELO_SLOPES) hits only.  The tracker owns its input and
+ * output buffers and its workspace, allocated by retina_tracker_create for
+ * the configured capacities; steps allocate nothing.  The first step with a
+ * given event count and search launch shape records the step's launches in a
+ * CUDA graph (when use_graph is set); later steps with the same count and
+ * shape replay it.  Steps of one tracker must be ordered (one stream, or
+ * synchronised): they share the buffers.
+ *
+ * retina_tracker_config:
+ *   box         : the search box and grid step (step cap, in-box test,
+ *                 extraction), as retina_batched_search's box.
+ *   opts        : Algorithm 1's options (as retina_batched_search).
+ *   R0, merge_cells : extraction (as retina_extract_tracks).
+ *   max_events (1 .. 65535), max_hits : capacities of a step.
+ *   seeds_per_event : S, every event's starting points (1 .. 8192).
+ *   max_tracks  : tracks written per event (K of retina_extract_tracks).
+ *   sort_seeds  : 1 = order each event's starting points spatially first.
+ *   seeds_per_warp (0, 1, 2, 4), warps (0, 8, 16, 32), smem_hits (0 .. 12288),
+ *   ctas        : the batched search's launch shape; 0 = the process-wide
+ *                 option (RETINA_OPT_BATCH_*) in force at the step.
+ *   use_graph   : 1 = record / replay CUDA graphs, 0 = enqueue the launches.
+ * retina_tracker_create(config, seednet_params, &t): seednet_params is NULL
+ *   (the caller supplies starting points) or float32 [RETINA_SEEDNET_PARAMS]
+ *   in host or device memory, copied at creation.  RETINA_EINVAL (nothing
+ *   allocated) for an invalid configuration, RETINA_ECUDA when an allocation
+ *   fails.
+ * retina_tracker_buffers: device addresses of the owned buffers - hits
+ *   float32 [max_hits][4], event_offsets int64 [max_events + 1], seeds
+ *   float32 [max_events][S][2] (written by the proposer in learned mode),
+ *   tracks float32 [max_events][max_tracks][2], track_R float32
+ *   [max_events][max_tracks], n_tracks int32 [max_events] (as
+ *   retina_extract_tracks).  Any pointer argument may be NULL.
+ * retina_tracker_step(t, n_events, stream): one step on the owned input
+ *   buffers (which the caller filled: hits and offsets of n_events events,
+ *   offsets[n_events] <= max_hits; seeds unless learned), outputs in the owned
+ *   output buffers.
+ * retina_tracker_set_marks(t, events, n): n = RETINA_TRACKER_MARKS cudaEvent_t
+ *   handles (created by the caller, with timing for durations) that every
+ *   later step records - as event nodes of its graph - before the hit
+ *   ordering (0), after it (1), after the starting points (2), after their
+ *   ordering (3), after the search (4) and after cluster / select (5); n = 0
+ *   removes them.  The events stay the caller's; a graph recorded earlier is
+ *   recorded again at the next step.
+ * retina_tracker_run_host: one step from host memory - copies n_hits hits,
+ *   n_events + 1 offsets and (caller seeds only) n_events * S seeds in,
+ *   steps, copies n_events rows of tracks, track_R and n_tracks out, all
+ *   enqueued on `stream` in that order; the call returns before the copies
+ *   finish: synchronise the stream before reading the host outputs.  Host
+ *   buffers should be page-locked for the copies to be asynchronous.  The
+ *   offsets are checked on the host (non-decreasing, within [0, n_hits]):
+ *   RETINA_EINVAL, nothing enqueued.
+ */
+typedef struct {
+    retina_grid box;
+    retina_ls_opts opts;
+    float R0;
+    float merge_cells;
+    int32_t max_events;
+    int64_t max_hits;
+    int32_t seeds_per_event;
+    int32_t max_tracks;
+    int32_t sort_seeds;
+    int32_t seeds_per_warp;
+    int32_t warps;
+    int32_t smem_hits;
+    int32_t ctas;
+    int32_t use_graph;
+} retina_tracker_config;
+
+typedef struct retina_tracker retina_tracker;
+
+#define RETINA_TRACKER_MARKS 6
+
+int retina_tracker_create(const retina_tracker_config *config, const float *seednet_params, retina_tracker **out);
+int retina_tracker_buffers(retina_tracker *t, float **hits, int64_t **event_offsets, float **seeds, float **tracks,
+                           float **track_R, int32_t **n_tracks);
+int retina_tracker_set_marks(retina_tracker *t, void *const *events, int32_t n);
+int retina_tracker_step(retina_tracker *t, int32_t n_events, void *stream);
+int retina_tracker_run_host(retina_tracker *t, const float *hits, int64_t n_hits, const int64_t *event_offsets,
+                            int32_t n_events, const float *seeds, float *tracks, float *track_R, int32_t *n_tracks,
+                            void *stream);
+int retina_tracker_destroy(retina_tracker *t);
+
 #ifdef __cplusplus
 }
 #endif

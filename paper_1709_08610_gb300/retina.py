@@ -14,6 +14,7 @@ import re
 from dataclasses import dataclass
 from typing import Optional, Sequence, Tuple
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -130,6 +131,14 @@ class _CPipelineConfig(ctypes.Structure):
                 ("max_tracks", ctypes.c_int32)]
 
 
+class _CTrackerConfig(ctypes.Structure):
+    _fields_ = [("box", _CGrid), ("opts", _CLsOpts), ("R0", ctypes.c_float), ("merge_cells", ctypes.c_float),
+                ("max_events", ctypes.c_int32), ("max_hits", ctypes.c_int64), ("seeds_per_event", ctypes.c_int32),
+                ("max_tracks", ctypes.c_int32), ("sort_seeds", ctypes.c_int32), ("seeds_per_warp", ctypes.c_int32),
+                ("warps", ctypes.c_int32), ("smem_hits", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -139,6 +148,12 @@ def _load():
     L.retina_pipeline_create.argtypes = [P, P]
     L.retina_pipeline_run.argtypes = [P, P, I64, P, I32, P, P, P, P, P, P, P, P]
     L.retina_pipeline_destroy.argtypes = [P]
+    L.retina_tracker_create.argtypes = [P, P, P]
+    L.retina_tracker_buffers.argtypes = [P, P, P, P, P, P, P]
+    L.retina_tracker_step.argtypes = [P, I32, P]
+    L.retina_tracker_set_marks.argtypes = [P, P, I32]
+    L.retina_tracker_run_host.argtypes = [P, P, I64, P, I32, P, P, P, P, P]
+    L.retina_tracker_destroy.argtypes = [P]
     L.retina_strerror.argtypes = [ctypes.c_int]
     L.retina_strerror.restype = ctypes.c_char_p
     L.retina_abi_version.restype = ctypes.c_int
@@ -696,6 +711,124 @@ class Pipeline:
     def close(self):
         if getattr(self, "_h", None):
             lib.retina_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+class Tracker:
+    """Algorithm 1 over a batch of events in one native call
+    (retina_tracker_*): hit ordering, the learned proposer's starting points
+    (when ``params`` are given) or the caller's, their spatial order, the
+    persistent batched search and cluster / select, replayed as one CUDA
+    graph.  The tracker owns its input / output buffers (``hits``,
+    ``offsets``, ``seeds``, ``tracks``, ``track_R``, ``n_tracks`` are torch
+    views of them)."""
+
+    def __init__(self, box: Grid, opts: LsOpts, R0: float, merge_cells: float, max_events: int, max_hits: int,
+                 seeds_per_event: int, max_tracks: int = 1024, params=None, sort_seeds: bool = True,
+                 seeds_per_warp: int = 0, warps: int = 0, smem_hits: int = 0, ctas: int = 0, use_graph: bool = True):
+        c = _CTrackerConfig()
+        c.box, c.opts, c.R0, c.merge_cells = box.c(), opts.c(), float(R0), float(merge_cells)
+        c.max_events, c.max_hits, c.seeds_per_event, c.max_tracks = max_events, max_hits, seeds_per_event, max_tracks
+        c.sort_seeds, c.seeds_per_warp, c.warps, c.smem_hits, c.ctas = int(sort_seeds), seeds_per_warp, warps, \
+            smem_hits, ctas
+        c.use_graph = int(use_graph)
+        self.E, self.H, self.S, self.K = int(max_events), int(max_hits), int(seeds_per_event), int(max_tracks)
+        self.learned = params is not None
+        keep = None
+        if params is not None:
+            keep = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float32)) if isinstance(params, np.ndarray) \
+                else params.to(torch.float32).contiguous()
+            if keep.numel() != 4833:
+                raise ValueError("expected 4833 network parameters")
+        h = ctypes.c_void_p()
+        _check("retina_tracker_create", lib.retina_tracker_create(ctypes.byref(c), _p(keep), ctypes.byref(h)))
+        self._h = h
+        ptrs = [ctypes.c_void_p() for _ in range(6)]
+        _check("retina_tracker_buffers", lib.retina_tracker_buffers(self._h, *[ctypes.byref(x) for x in ptrs]))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        E, H, S, K = self.E, self.H, self.S, self.K
+        view = lambda p, shape, t: torch.as_tensor(_DeviceArray(p.value, shape, t), device=dev)
+        self.hits = view(ptrs[0], (H, 4), "<f4")
+        self.offsets = view(ptrs[1], (E + 1,), "<i8")
+        self.seeds = view(ptrs[2], (E, S, 2), "<f4")
+        self.tracks = view(ptrs[3], (E, K, 2), "<f4")
+        self.track_R = view(ptrs[4], (E, K), "<f4")
+        self.n_tracks = view(ptrs[5], (E,), "<i4")
+
+    def load(self, hits, offsets, seeds=None):
+        """Copy a batch (host arrays or tensors) into the owned input buffers;
+        returns the number of events."""
+        hits = torch.as_tensor(np.ascontiguousarray(hits, dtype=np.float32)) if isinstance(hits, np.ndarray) else hits
+        offsets = torch.as_tensor(np.ascontiguousarray(offsets, dtype=np.int64)) \
+            if isinstance(offsets, np.ndarray) else offsets
+        E = offsets.numel() - 1
+        if hits.shape[0] > self.H or not 0 <= E <= self.E:
+            raise ValueError("batch does not fit the tracker's capacity")
+        self.hits[:hits.shape[0]].copy_(hits)
+        self.offsets[:E + 1].copy_(offsets)
+        if seeds is not None:
+            seeds = torch.as_tensor(np.ascontiguousarray(seeds, dtype=np.float32)) \
+                if isinstance(seeds, np.ndarray) else seeds
+            self.seeds[:E].copy_(seeds.reshape(E, self.S, 2))
+        return E
+
+    def set_marks(self, events):
+        """Stage marks recorded by every later step (6 torch.cuda.Event: before
+        the hit ordering, after it, after the starting points, after their
+        ordering, after the search, after cluster / select), or None."""
+        if events is None:
+            _check("retina_tracker_set_marks", lib.retina_tracker_set_marks(self._h, None, 0))
+            self._marks = None
+            return
+        if len(events) != 6:
+            raise ValueError("6 events")
+        for e in events:  # the handles exist once recorded
+            e.record()
+        arr = (ctypes.c_void_p * 6)(*[e.cuda_event for e in events])
+        _check("retina_tracker_set_marks", lib.retina_tracker_set_marks(self._h, arr, 6))
+        self._marks = list(events)
+
+    def step(self, n_events: int, stream=None):
+        _check("retina_tracker_step", lib.retina_tracker_step(self._h, int(n_events), _stream(stream)))
+
+    def run_host(self, hits: torch.Tensor, offsets: torch.Tensor, out: dict, seeds: Optional[torch.Tensor] = None,
+                 stream=None):
+        """One step from host tensors (page-locked for asynchronous copies):
+        hits [n_hits, 4] float32, offsets [E + 1] int64, seeds [E, S, 2]
+        (caller seeds only); out holds host tensors tracks [>= E, K, 2],
+        track_R [>= E, K], n_tracks [>= E].  Enqueued on the stream: synchronise
+        before reading ``out``."""
+        for t, dt, name in ((hits, torch.float32, "hits"), (offsets, torch.int64, "offsets")):
+            if t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous host %s tensor" % (name, dt))
+        E = offsets.numel() - 1
+        _check("retina_tracker_run_host", lib.retina_tracker_run_host(
+            self._h, _p(hits), hits.shape[0], _p(offsets), E, _p(seeds), _p(out["tracks"]), _p(out["track_R"]),
+            _p(out["n_tracks"]), _stream(stream)))
+
+    def results(self, n_events: int):
+        """Per event: float64 [n_tracks, 2] track parameters (host)."""
+        n = self.n_tracks[:n_events].cpu().numpy()
+        tr = self.tracks[:n_events].cpu().numpy()
+        return [tr[e, :min(int(n[e]), self.K)].astype(np.float64) for e in range(n_events)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.retina_tracker_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -337,3 +337,28 @@ def test_option_structs_marshal_every_field():
     assert f.step_cap == pytest.approx(3.0) and f.zref == pytest.approx(225.0)
     # the C struct sizes the library expects (host pointers read field by field)
     assert ctypes.sizeof(type(f)) == 4 * (1 + 8 + 1 + 1 + 4 + 1 + 1)
+
+
+def test_tracker_configuration_is_validated_before_allocating():
+    good = rt._CTrackerConfig()
+    good.box = rt.Grid((-0.5, -0.5), (2 ** -10, 2 ** -10), (1024, 1024)).c()
+    good.opts = rt.LsOpts().c()
+    good.R0, good.merge_cells = 11.7, 2.0
+    good.max_events, good.max_hits, good.seeds_per_event, good.max_tracks = 4, 1000, 512, 64
+    good.use_graph = 1
+    h = ctypes.c_void_p()
+    assert L.retina_tracker_create(None, None, ctypes.byref(h)) == EINVAL
+    for field, value in (("max_events", 0), ("max_events", 65536), ("seeds_per_event", 0),
+                         ("seeds_per_event", 8193), ("max_tracks", 0), ("max_hits", -1), ("sort_seeds", 2),
+                         ("seeds_per_warp", 3), ("warps", 12), ("smem_hits", 12289), ("merge_cells", 0.0),
+                         ("R0", float("nan"))):
+        c = rt._CTrackerConfig.from_buffer_copy(good)
+        setattr(c, field, value)
+        assert L.retina_tracker_create(ctypes.byref(c), None, ctypes.byref(h)) == EINVAL, field
+        assert not h.value
+    c = rt._CTrackerConfig.from_buffer_copy(good)
+    c.opts.q = 0
+    assert L.retina_tracker_create(ctypes.byref(c), None, ctypes.byref(h)) == EINVAL
+    assert L.retina_tracker_step(None, 1, None) == EINVAL
+    assert L.retina_tracker_run_host(None, None, 0, None, 1, None, None, None, None, None) == EINVAL
+    assert L.retina_tracker_destroy(None) == EINVAL
