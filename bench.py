@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched method comparisons")
     ap.add_argument("--no-extras", action="store_true", help="the headline alone (no other workloads)")
+    ap.add_argument("--events", type=int, default=None,
+                    help="events per headline batch (profiling runs; default: the workload's 1024)")
     ap.add_argument("--serial", action="store_true", help="run the grid and search branches on one stream")
     ap.add_argument("--shape", default=None, metavar="P,W,H,C,S",
                     help="fixed launch shape instead of the autotuner's (profiling runs): search seeds per warp, "
@@ -989,17 +991,16 @@ HEADLINE_TRACKS = 1024
 HEADLINE_RUN_SEED = 7000
 
 
-def headline_batch(rank: int = 0):
+def headline_batch(rank: int = 0, n_events: int = HEADLINE_EVENTS):
     """1024 high-multiplicity VELO-like events with the vertex at the origin
     (each rank its own batch)."""
     wl = WORKLOADS[HEADLINE]
-    evs = [make_event(wl, HEADLINE_RUN_SEED + 1000 * rank, e, vertex_sigma=(0, 0, 0)) for e in range(HEADLINE_EVENTS)]
+    evs = [make_event(wl, HEADLINE_RUN_SEED + 1000 * rank, e, vertex_sigma=(0, 0, 0)) for e in range(n_events)]
     return wl, evs, batch_of(evs)
 
 
-def headline_config(wl, n_hits: int) -> dict:
+def headline_config(wl, n_hits: int, E: int = HEADLINE_EVENTS) -> dict:
     gen = wl.gen
-    E = HEADLINE_EVENTS
     return {
         "workload": "velo_stress: %d high-multiplicity VELO-like events per step (tracks ~ Poisson(%g) clipped to "
                     "[%g, %g], 15%% noise hits, 26 layers at z=-300..750 mm, 90%% layer efficiency, vertex at the "
@@ -1098,8 +1099,8 @@ def headline(rt, args, dev, rank, world, peaks, local_rank):
     import torch.distributed as dist
     from paper_1709_08610_gb300.pipeline import match_efficiency
     from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, read_checkpoint
-    wl, evs, b = headline_batch(rank)
-    E, S, K = HEADLINE_EVENTS, HEADLINE_SEEDS, HEADLINE_TRACKS
+    wl, evs, b = headline_batch(rank, args.events or HEADLINE_EVENTS)
+    E, S, K = len(evs), HEADLINE_SEEDS, HEADLINE_TRACKS
     H = int(b.hits.shape[0])
     params = read_checkpoint(DEFAULT_WEIGHTS)[1]["params"]
     box = rt.Grid.of(wl)
@@ -1233,7 +1234,7 @@ def headline(rt, args, dev, rank, world, peaks, local_rank):
                               "match": "|dtheta|_max <= 1e-3 in slope"}}
     tr.close()
     return {
-        "value": value, "ms_per_step": ms_per_step, "config": headline_config(wl, H), "e2e": e2e,
+        "value": value, "ms_per_step": ms_per_step, "config": headline_config(wl, H, E), "e2e": e2e,
         "gpu_launches": int(kernels_per_step * args.steps), "kernels_per_step": int(kernels_per_step),
         "roofline": roofline, "clocks": clk, "cpu_baseline": cpu, "wall_s_timed": t_wall1 - t_wall0,
         "stages_ms": {n: float(st_ms[:, i].mean()) for i, n in enumerate(

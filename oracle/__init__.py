@@ -223,7 +223,9 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     return th, R, st, m
 
 
-PERTURB_KEYS = (0x5EED0001, 0x5EED0002, 0x5EED0003, 0x5EED0004)
+# replica keys: a path near a decision boundary is crossed by about half of
+# the replicas, so 16 leave a chance of 2^-16 of missing one
+PERTURB_KEYS = tuple(0x5EED0001 + i for i in range(16))
 
 
 def splitmix64(state: int, n: int):

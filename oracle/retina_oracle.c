@@ -241,10 +241,11 @@ static double perturbed(const or_perturb *pt, int64_t i, int j, int c, double v,
  * iteration: fall back to the steepest-ascent direction g) and after at
  * most 2 iterations (the dimension).  *margin gets the smallest distance of
  * a branch test from its threshold, in units of the FP32 parity tolerance
- * of the quantities compared (1e-4 of the sum of absolute terms).
+ * of the quantities compared: 1e-4 of the sum of absolute terms plus the
+ * absolute floor of each gradient (gfloor) or Hessian (hfloor) entry.
  */
 static void newton_cg_direction(const double g[2], const double H[3], const double gabs[2],
-                                const double Habs[3], double p[2], double *margin) {
+                                const double Habs[3], double gfloor, double hfloor, double p[2], double *margin) {
     const double B00 = -H[0], B01 = -H[1], B11 = -H[2];
     const double gn = sqrt(g[0] * g[0] + g[1] * g[1]);
     const double eps = fmin(0.5, sqrt(gn)) * gn;
@@ -258,7 +259,7 @@ static void newton_cg_direction(const double g[2], const double H[3], const doub
         const double dBd = d[0] * Bd0 + d[1] * Bd1;
         const double dd = d[0] * d[0] + d[1] * d[1];
         {
-            const double tol = 1e-4 * hscale * dd;
+            const double tol = (1e-4 * hscale + 4.0 * hfloor) * dd;
             const double m = tol > 0.0 ? fabs(dBd) / tol : 0.0;
             if (m < *margin) *margin = m;
         }
@@ -274,7 +275,7 @@ static void newton_cg_direction(const double g[2], const double H[3], const doub
         double rn[2] = {r[0] + alpha * Bd0, r[1] + alpha * Bd1};
         const double rnn = sqrt(rn[0] * rn[0] + rn[1] * rn[1]);
         if (it == 0) {
-            const double tol = 1e-4 * (gabs[0] + gabs[1]);
+            const double tol = 1e-4 * (gabs[0] + gabs[1]) + 2.0 * gfloor;
             const double m = tol > 0.0 ? fabs(rnn - eps) / tol : 0.0;
             if (m < *margin) *margin = m;
         }
@@ -297,19 +298,20 @@ static void newton_cg_direction(const double g[2], const double H[3], const doub
  * (B + tau I) p = g.  Where -H is already positive definite beyond delta this
  * is the plain Newton step.  B = 0 (no curvature) gives p = g.  *margin gets
  * the distance of the shift test mu1 < delta from its threshold, in units of
- * 1e-4 of the sum of absolute Hessian terms.  A shifted step is otherwise an
+ * 1e-4 of the sum of absolute Hessian terms plus each entry's absolute floor
+ * hfloor.  A shifted step is otherwise an
  * ordinary decision: B + tau I then has condition number >= 1e3, so the
  * direction can move by more than the Hessian tolerance bounds; whether that
  * changes where the path ends is what the perturbed replicas measure.
  */
-static void modified_newton_direction(const double g[2], const double H[3], const double Habs[3], double p[2],
-                                      double *margin) {
+static void modified_newton_direction(const double g[2], const double H[3], const double Habs[3], double hfloor,
+                                      double p[2], double *margin) {
     const double a = -H[0], b = -H[1], c = -H[2];
     const double mid = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + b * b);
     const double mu1 = mid - rad, mu2 = mid + rad;
     const double delta = 1e-3 * fmax(fabs(mu1), fabs(mu2));
     {
-        const double tol = 1e-4 * (Habs[0] + 2.0 * Habs[1] + Habs[2]);
+        const double tol = 1e-4 * (Habs[0] + 2.0 * Habs[1] + Habs[2]) + 4.0 * hfloor;
         const double m = tol > 0.0 ? fabs(mu1 - delta) / tol : 0.0;
         if (m < *margin) *margin = m;
     }
@@ -331,12 +333,16 @@ static void modified_newton_direction(const double g[2], const double H[3], cons
  * 3 non-finite.  *margin receives the smallest distance of any discrete
  * decision (curvature sign, CG stop, Armijo test, box test) from its
  * threshold, in units of the FP32 parity tolerance of the compared values
- * (R: 1e-5 R + 1e-6; gradient / Hessian: 1e-4 of the absolute terms;
- * theta: 1e-3 of a cell), so that callers can tell genuine disagreements
- * from ties (margin < 1).
+ * (R: 1e-5 R + 1e-6; gradient / Hessian: 1e-4 of the absolute terms plus
+ * floors of 1e-6 of their scale at unit response - one hit at residual
+ * sigma: 2 sigma |J|max / sigma^2 for the gradient, 2 |J|max^2 / sigma^2 for
+ * the Hessian, |J|max the largest Jacobian entry over the event's hits,
+ * jmax - below which float32 sums, whose exponentials flush to zero under
+ * 2^-126, carry no information; theta: 1e-3 of a cell), so that callers can
+ * tell genuine disagreements from ties (margin < 1).
  */
 static int search_one(const float *hits, int64_t n_hits, int model, const float seed[2], const or_ls_opts *o,
-                      const or_grid *box, double theta_out[2], double *R_out, double *margin,
+                      const or_grid *box, double jmax, double theta_out[2], double *R_out, double *margin,
                       const or_perturb *pt, int64_t seed_index) {
     double th[2] = {(double)seed[0], (double)seed[1]};
     int status = 0;
@@ -347,21 +353,23 @@ static int search_one(const float *hits, int64_t n_hits, int model, const float 
         or_rgh(hits, n_hits, model, th, sigma, rgh);
         const double gabs[2] = {rgh[7], rgh[8]};
         const double Habs[3] = {rgh[9], rgh[10], rgh[11]};
+        const double k = 1.0 / (sigma * sigma);
+        const double gfloor = 1e-6 * 2.0 * k * sigma * jmax, hfloor = 1e-6 * 2.0 * k * jmax * jmax;
         const int64_t si = seed_index;
         const double R = perturbed(pt, si, j, 0, rgh[0], 1e-5 * fabs(rgh[0]) + 1e-6);
-        const double g[2] = {perturbed(pt, si, j, 1, rgh[1], 1e-4 * gabs[0]),
-                             perturbed(pt, si, j, 2, rgh[2], 1e-4 * gabs[1])};
-        const double H[3] = {perturbed(pt, si, j, 3, rgh[3], 1e-4 * Habs[0]),
-                             perturbed(pt, si, j, 4, rgh[4], 1e-4 * Habs[1]),
-                             perturbed(pt, si, j, 5, rgh[5], 1e-4 * Habs[2])};
+        const double g[2] = {perturbed(pt, si, j, 1, rgh[1], 1e-4 * gabs[0] + gfloor),
+                             perturbed(pt, si, j, 2, rgh[2], 1e-4 * gabs[1] + gfloor)};
+        const double H[3] = {perturbed(pt, si, j, 3, rgh[3], 1e-4 * Habs[0] + hfloor),
+                             perturbed(pt, si, j, 4, rgh[4], 1e-4 * Habs[1] + hfloor),
+                             perturbed(pt, si, j, 5, rgh[5], 1e-4 * Habs[2] + hfloor)};
         double p[2];
         if (o->update == 1) {         /* steepest ascent: the gradient itself */
             p[0] = g[0];
             p[1] = g[1];
         } else if (o->update == 2) {
-            modified_newton_direction(g, H, Habs, p, margin);
+            modified_newton_direction(g, H, Habs, hfloor, p, margin);
         } else {
-            newton_cg_direction(g, H, gabs, Habs, p, margin);
+            newton_cg_direction(g, H, gabs, Habs, gfloor, hfloor, p, margin);
         }
         /* cap the step length, measured in grid cells */
         const double cells = fmax(fabs(p[0]) / box->step[0], fabs(p[1]) / box->step[1]);
@@ -405,14 +413,26 @@ static int search_one(const float *hits, int64_t n_hits, int model, const float 
     return status;
 }
 
+/* The largest Jacobian entry over the hits: |z| (slope model) or
+ * max(|x|, 1) (2D toy), the scale of the gradient / Hessian floors. */
+static double jacobian_max(const float *hits, int64_t n_hits, int model) {
+    double m = model == OR_TOY2D ? 1.0 : 0.0;
+    for (int64_t k = 0; k < n_hits; ++k) {
+        const double v = fabs((double)hits[4 * k + (model == OR_TOY2D ? 0 : 2)]);
+        if (v > m) m = v;
+    }
+    return m;
+}
+
 void or_local_search(const float *hits, int64_t n_hits, int model, const float *seeds, int64_t n_seeds,
                      const or_ls_opts *o, const or_grid *box, double *theta_out, double *R_out, uint8_t *status,
                      double *margin_out) {
+    const double jmax = jacobian_max(hits, n_hits, model);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t i = 0; i < n_seeds; ++i) {
         double m;
-        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, theta_out + 2 * i, R_out + i, &m,
-                                        NULL, i);
+        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, jmax, theta_out + 2 * i,
+                                        R_out + i, &m, NULL, i);
         if (margin_out) margin_out[i] = m;
     }
 }
@@ -424,11 +444,12 @@ void or_local_search_perturbed(const float *hits, int64_t n_hits, int model, con
                                int64_t index_base, double *theta_out, double *R_out, uint8_t *status,
                                double *margin_out) {
     const or_perturb pt = {level, key};
+    const double jmax = jacobian_max(hits, n_hits, model);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t i = 0; i < n_seeds; ++i) {
         double m;
-        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, theta_out + 2 * i, R_out + i, &m,
-                                        &pt, index_base + i);
+        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, jmax, theta_out + 2 * i,
+                                        R_out + i, &m, &pt, index_base + i);
         if (margin_out) margin_out[i] = m;
     }
 }
@@ -586,17 +607,19 @@ static double sym4(const double *Hu, int a, int b) { return a <= b ? Hu[tri4(a, 
  * min(1/2, sqrt|D g|) |D g|, at most 4 iterations (the dimension);
  * non-positive curvature along d returns y = D g at the first iteration,
  * else the current iterate; p = D y.  *margin as for the 2D direction, on
- * the scaled quantities.
+ * the scaled quantities (gfloor, hfloor: the absolute floors of the gradient
+ * and Hessian entries, hfloor in tri4 order).
  */
 static void newton_cg_direction4(const double g_in[4], const double Hu[10], const double gabs_in[4],
-                                 const double Habs[10], const double scale[4], double p[4], double *margin) {
+                                 const double Habs[10], const double gfloor[4], const double hfloor[10],
+                                 const double scale[4], double p[4], double *margin) {
     double B[4][4], g[4], hscale = 0.0, gsum = 0.0;
     for (int a = 0; a < 4; ++a) {
         g[a] = scale[a] * g_in[a];
-        gsum += scale[a] * gabs_in[a];
+        gsum += scale[a] * (gabs_in[a] + 1e4 * gfloor[a]);
         for (int b = 0; b < 4; ++b) {
             B[a][b] = -scale[a] * sym4(Hu, a, b) * scale[b];
-            hscale += scale[a] * sym4(Habs, a, b) * scale[b];
+            hscale += scale[a] * (sym4(Habs, a, b) + 1e4 * sym4(hfloor, a, b)) * scale[b];
         }
     }
     double gn = 0.0;
@@ -661,17 +684,29 @@ static int search4_one(const float *hits, int64_t n_hits, const float *seed, con
                        const or_perturb *pt, int64_t si, double th[4], double *R_out, double *margin) {
     int st = 0;
     *margin = INFINITY;
+    /* the largest Jacobian entry per parameter: 1 for the offsets, |z - zref| for the slopes */
+    double jm[4] = {1.0, 1.0, 0.0, 0.0};
+    for (int64_t k = 0; k < n_hits; ++k) {
+        const double w = fabs((double)hits[4 * k + 2] - o->zref);
+        if (w > jm[2]) jm[2] = jm[3] = w;
+    }
     for (int a = 0; a < 4; ++a) th[a] = (double)seed[a];
     for (int j = 0; j < o->q; ++j) {
         const double sigma = o->sigma[j];
+        const double k = 1.0 / (sigma * sigma);
+        double gfloor[4], hfloor[10];
+        for (int a = 0; a < 4; ++a) {
+            gfloor[a] = 1e-6 * 2.0 * k * sigma * jm[a];
+            for (int b = a; b < 4; ++b) hfloor[tri4(a, b)] = 1e-6 * 2.0 * k * jm[a] * jm[b];
+        }
         double v[29];
         or_rgh4(hits, n_hits, th, o->zref, sigma, v);
         v[0] = perturbed(pt, si, j, 0, v[0], 1e-5 * fabs(v[0]) + 1e-6);
-        for (int a = 0; a < 4; ++a) v[1 + a] = perturbed(pt, si, j, 1 + a, v[1 + a], 1e-4 * v[15 + a]);
-        for (int e = 0; e < 10; ++e) v[5 + e] = perturbed(pt, si, j, 5 + e, v[5 + e], 1e-4 * v[19 + e]);
+        for (int a = 0; a < 4; ++a) v[1 + a] = perturbed(pt, si, j, 1 + a, v[1 + a], 1e-4 * v[15 + a] + gfloor[a]);
+        for (int e = 0; e < 10; ++e) v[5 + e] = perturbed(pt, si, j, 5 + e, v[5 + e], 1e-4 * v[19 + e] + hfloor[e]);
         const double R = v[0];
         double p[4];
-        newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, o->scale, p, margin);
+        newton_cg_direction4(v + 1, v + 5, v + 15, v + 19, gfloor, hfloor, o->scale, p, margin);
         double cells = 0.0;
         for (int a = 0; a < 4; ++a) cells = fmax(cells, fabs(p[a]) / o->scale[a]);
         if (cells > o->step_cap)

@@ -508,7 +508,7 @@ def _search_sets(rt, wl, ev, seeds):
     def run(pt):
         return oracle.local_search(ev.hits, wl.model, seeds, sig, *box, perturb=pt)
 
-    stable, _, _ = oracle.path_conditioning(run, (th_o, R_o, st_o, m_o), tol)
+    stable, _, _ = oracle.path_conditioning(run, (th_o, R_o, st_o, m_o), tol, keys=oracle.PERTURB_KEYS[:8])
     tie = (m_o < 1.0) | ~stable
     comps, tied, compared = compare_track_sets(th_o, R_o, cand_o | (near0 & (st_o <= 1)), th_g, R_g, cand_g, tie,
                                                keep_o, src_g, tol, wl.grid_step, wl.merge_cells, R0=R0)
