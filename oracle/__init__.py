@@ -93,6 +93,12 @@ def lib():
             U64 = ctypes.c_uint64
             L.or_local_search_perturbed.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, D, U64, I64, P, P, P, P]
             L.or_local_search4_perturbed.argtypes = [P, I64, P, I64, P, D, U64, I64, P, P, P, P]
+            L.or_local_search_counted.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, P, P, P, P]
+            L.or_pair_seeds4.argtypes = [P, I64, P, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_float, P, I64]
+            L.or_pair_seeds4.restype = I64
+            L.or_extract_tracks4.argtypes = [P, P, P, I64, P, P, D, D, P, I64]
+            L.or_extract_tracks4.restype = I64
             L.or_splitmix64.argtypes = [P]
             L.or_splitmix64.restype = U64
             L.or_perturb_u.argtypes = [U64, I64, ctypes.c_int, ctypes.c_int]
@@ -177,7 +183,7 @@ UPDATE_TRUNCATED_NEWTON, UPDATE_STEEPEST_ASCENT, UPDATE_MODIFIED_NEWTON = 0, 1, 
 
 def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, step, n,
                  c1: float = 1e-4, max_halvings: int = 8, step_cap_cells: float = 4.0, update: int = 0,
-                 perturb: Optional[Tuple[float, int]] = None):
+                 perturb: Optional[Tuple[float, int]] = None, count_trials: bool = False):
     """Algorithm 1's q updates for every seed.
 
     update picks the direction of each update: 0 the truncated Newton
@@ -191,7 +197,9 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     times their parity tolerance, u in [-1, 1) drawn per (key, seed, update,
     quantity) (see :func:`path_conditioning`).
 
-    Returns (theta [n, 2] float64, R_final [n], status [n] uint8, margin [n]).
+    Returns (theta [n, 2] float64, R_final [n], status [n] uint8, margin [n]);
+    with count_trials, (theta, R_final, status, trials [n]): the responses
+    each seed's line searches evaluated.
     """
     if update not in (0, 1, 2):
         raise ValueError("update must be 0, 1 or 2")
@@ -213,6 +221,11 @@ def local_search(hits, model: int, seeds, sigma_schedule: Sequence[float], lo, s
     R = np.zeros(ns)
     st = np.zeros(ns, dtype=np.uint8)
     m = np.zeros(ns)
+    if count_trials:
+        tr = np.zeros(ns, dtype=np.int32)
+        lib().or_local_search_counted(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
+                                      _ptr(th), _ptr(R), _ptr(st), _ptr(tr))
+        return th, R, st, tr
     if perturb is None:
         lib().or_local_search(_ptr(h), h.shape[0], model, _ptr(s), ns, ctypes.byref(o), ctypes.byref(g),
                               _ptr(th), _ptr(R), _ptr(st), _ptr(m))
@@ -332,6 +345,37 @@ def local_search4(hits, seeds, sigma_schedule: Sequence[float], scale: Sequence[
         lib().or_local_search4_perturbed(_ptr(h), h.shape[0], _ptr(s), ns, ctypes.byref(o), float(perturb[0]),
                                          int(perturb[1]) & (2 ** 64 - 1), 0, _ptr(th), _ptr(R), _ptr(st), _ptr(m))
     return th, R, st, m
+
+
+def pair_seeds4(hits, layer_pairs, dz_tol: float, d_max: float, zc_range, zref: float,
+                cap: Optional[int] = None):
+    """Starting points of the four-parameter search from hit pairs on the
+    given layer pairs [(z_a, z_b), ...] (see or_pair_seeds4): lines through
+    two hits passing within d_max of the z axis at zc_range[0] <= z_c <=
+    zc_range[1], as (x0, y0, t_x, t_y) at zref, in pair order; float32
+    decisions.  Returns (seeds float32 [m, 4], number kept (>= m))."""
+    h = _hits(hits)
+    lz = np.ascontiguousarray(np.asarray(layer_pairs, dtype=np.float32).reshape(-1, 2))
+    n = int(cap) if cap is not None else 1 << 20
+    out = np.zeros((max(n, 1), 4), dtype=np.float32)
+    cnt = lib().or_pair_seeds4(_ptr(h), h.shape[0], _ptr(lz), lz.shape[0], float(dz_tol), float(d_max),
+                               float(zc_range[0]), float(zc_range[1]), float(zref), _ptr(out), n)
+    return out[:min(cnt, n)].copy(), int(cnt)
+
+
+def extract_tracks4(theta, R, status, lo, step, n, units, R0: float, merge_units: float = 2.0) -> np.ndarray:
+    """Indices of the kept four-parameter points, in decreasing-R order
+    (cluster + select with max_a |dtheta_a| / units_a < merge_units as the
+    conflict; slopes inside the slope box lo / step / n)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 4)
+    Rr = np.ascontiguousarray(R, dtype=np.float64).reshape(-1)
+    st = None if status is None else np.ascontiguousarray(status, dtype=np.uint8).reshape(-1)
+    u = np.ascontiguousarray(units, dtype=np.float64).reshape(4)
+    g = make_grid(lo, step, n)
+    keep = np.zeros(max(len(Rr), 1), dtype=np.int64)
+    cnt = lib().or_extract_tracks4(_ptr(th), _ptr(Rr), _ptr(st), len(Rr), ctypes.byref(g), _ptr(u), float(R0),
+                                   float(merge_units), _ptr(keep), len(keep))
+    return keep[:cnt].copy()
 
 
 def maxima_centres(idx, lo, step, n) -> np.ndarray:

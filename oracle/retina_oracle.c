@@ -343,7 +343,7 @@ static void modified_newton_direction(const double g[2], const double H[3], cons
  */
 static int search_one(const float *hits, int64_t n_hits, int model, const float seed[2], const or_ls_opts *o,
                       const or_grid *box, double jmax, double theta_out[2], double *R_out, double *margin,
-                      const or_perturb *pt, int64_t seed_index) {
+                      const or_perturb *pt, int64_t seed_index, int32_t *trials) {
     double th[2] = {(double)seed[0], (double)seed[1]};
     int status = 0;
     *margin = INFINITY;
@@ -385,6 +385,7 @@ static int search_one(const float *hits, int64_t n_hits, int model, const float 
         for (int h = 0; h <= o->max_halvings; ++h) {
             const double trial[2] = {th[0] + t * p[0], th[1] + t * p[1]};
             const double Rt0 = or_response(hits, n_hits, model, trial, sigma);
+            if (trials) ++*trials;
             const double Rt = perturbed(pt, seed_index, j, 16 + h, Rt0, 1e-5 * fabs(Rt0) + 1e-6);
             const double need = R + o->c1 * t * slope;
             const double tol = 1e-5 * (fabs(R) + fabs(Rt)) + 2e-6;
@@ -432,7 +433,7 @@ void or_local_search(const float *hits, int64_t n_hits, int model, const float *
     for (int64_t i = 0; i < n_seeds; ++i) {
         double m;
         status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, jmax, theta_out + 2 * i,
-                                        R_out + i, &m, NULL, i);
+                                        R_out + i, &m, NULL, i, NULL);
         if (margin_out) margin_out[i] = m;
     }
 }
@@ -449,8 +450,23 @@ void or_local_search_perturbed(const float *hits, int64_t n_hits, int model, con
     for (int64_t i = 0; i < n_seeds; ++i) {
         double m;
         status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, jmax, theta_out + 2 * i,
-                                        R_out + i, &m, &pt, index_base + i);
+                                        R_out + i, &m, &pt, index_base + i, NULL);
         if (margin_out) margin_out[i] = m;
+    }
+}
+
+/* or_local_search that also counts each seed's line-search trials (the
+ * responses evaluated besides the q gradient / Hessian evaluations). */
+void or_local_search_counted(const float *hits, int64_t n_hits, int model, const float *seeds, int64_t n_seeds,
+                             const or_ls_opts *o, const or_grid *box, double *theta_out, double *R_out,
+                             uint8_t *status, int32_t *trials_out) {
+    const double jmax = jacobian_max(hits, n_hits, model);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n_seeds; ++i) {
+        double m;
+        trials_out[i] = 0;
+        status[i] = (uint8_t)search_one(hits, n_hits, model, seeds + 2 * i, o, box, jmax, theta_out + 2 * i,
+                                        R_out + i, &m, NULL, i, trials_out + i);
     }
 }
 
@@ -766,4 +782,119 @@ void or_local_search4_perturbed(const float *hits, int64_t n_hits, const float *
                                          R_out + i, &m);
         if (margin_out) margin_out[i] = m;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Starting points of the four-parameter search from pairs of hits (our    */
+/* reading; the paper leaves the prior P_theta open and has no four-       */
+/* parameter search).  Every track comes from the beam line, so a pair of  */
+/* its hits on two layers spans a line that passes close to the z axis    */
+/* inside the luminous region; a pair of hits from different tracks rarely */
+/* does.  The decisions are taken in float32 with one rounding per         */
+/* operation, in the order written (the CUDA path takes them the same way, */
+/* so that the same pairs are kept on both sides).                         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For each layer pair p (z_a = layer_z[2 p], z_b = layer_z[2 p + 1]), in
+ * order, every hit i with |z_i - z_a| <= dz_tol and every hit j with
+ * |z_j - z_b| <= dz_tol, both in increasing index order (i outer): the line
+ * through h_i and h_j has slopes t = (x_j - x_i, y_j - y_i) / (z_j - z_i);
+ * its transverse distance to the z axis is |x_i t_y - y_i t_x| / |t| and it
+ * comes closest at z_c = z_i - (x_i t_x + y_i t_y) / |t|^2.  The pair is kept
+ * when |t|^2 > 0, (x_i t_y - y_i t_x)^2 <= d_max^2 |t|^2 and
+ * zc_lo <= z_c <= zc_hi; its seed is (x0, y0, t_x, t_y) at zref,
+ * x0 = x_i + t_x (zref - z_i).  Writes the first `cap` seeds [cap][4] in
+ * that order; returns how many pairs were kept (may exceed cap).
+ */
+int64_t or_pair_seeds4(const float *hits, int64_t n_hits, const float *layer_z, int32_t n_pairs, float dz_tol,
+                       float d_max, float zc_lo, float zc_hi, float zref, float *seeds_out, int64_t cap) {
+    int64_t count = 0;
+    const float dm2 = d_max * d_max;
+    for (int32_t p = 0; p < n_pairs; ++p) {
+        const float za = layer_z[2 * p], zb = layer_z[2 * p + 1];
+        for (int64_t i = 0; i < n_hits; ++i) {
+            const float xi = hits[4 * i], yi = hits[4 * i + 1], zi = hits[4 * i + 2];
+            if (!(fabsf(zi - za) <= dz_tol)) continue;
+            for (int64_t j = 0; j < n_hits; ++j) {
+                const float xj = hits[4 * j], yj = hits[4 * j + 1], zj = hits[4 * j + 2];
+                if (!(fabsf(zj - zb) <= dz_tol)) continue;
+                const float dz = zj - zi;
+                const float tx = (xj - xi) / dz;
+                const float ty = (yj - yi) / dz;
+                const float txx = tx * tx, tyy = ty * ty;
+                const float tt = txx + tyy;
+                if (!(tt > 0.0f)) continue;
+                const float cp = xi * ty, cq = yi * tx;
+                const float c = cp - cq;
+                const float lhs = c * c, rhs = dm2 * tt;
+                if (!(lhs <= rhs)) continue;
+                const float ua = xi * tx, ub = yi * ty;
+                const float u = ua + ub;
+                const float zc = zi - u / tt;
+                if (!(zc >= zc_lo && zc <= zc_hi)) continue;
+                if (count < cap) {
+                    const float w = zref - zi;
+                    const float px = tx * w, py = ty * w;
+                    seeds_out[4 * count] = xi + px;
+                    seeds_out[4 * count + 1] = yi + py;
+                    seeds_out[4 * count + 2] = tx;
+                    seeds_out[4 * count + 3] = ty;
+                }
+                ++count;
+            }
+        }
+    }
+    return count;
+}
+
+/*
+ * Cluster / select for four-parameter points (the last two lines of
+ * Algorithm 1 with theta = (x0, y0, t_x, t_y)): points with status 0 or 1,
+ * finite, slopes inside the slope box [lo, lo + n step) and R >= R0 are
+ * candidates, visited by decreasing R (ties: lower index first); a candidate
+ * is kept when, for every point kept before it,
+ * max_a |theta_a - theta_kept_a| / unit_a >= merge_units.  Writes the kept
+ * indices in that order (first cap of them); returns how many were kept.
+ */
+int64_t or_extract_tracks4(const double *theta, const double *R, const uint8_t *status, int64_t n_points,
+                           const or_grid *slope_box, const double unit[4], double R0, double merge_units,
+                           int64_t *keep_out, int64_t cap) {
+    or_rank *cand = (or_rank *)malloc(sizeof(or_rank) * (size_t)(n_points > 0 ? n_points : 1));
+    int64_t nc = 0;
+    for (int64_t i = 0; i < n_points; ++i) {
+        if (status && status[i] > 1) continue;
+        int ok = isfinite(R[i]);
+        for (int a = 0; a < 4; ++a) ok = ok && isfinite(theta[4 * i + a]);
+        if (!ok) continue;
+        for (int a = 0; a < 2; ++a) {
+            const double v = theta[4 * i + 2 + a];
+            const double lo = slope_box->lo[a], hi = slope_box->lo[a] + (double)slope_box->n[a] * slope_box->step[a];
+            if (!(v >= lo && v < hi)) ok = 0;
+        }
+        if (!ok || !(R[i] >= R0)) continue;
+        cand[nc].R = R[i];
+        cand[nc].idx = i;
+        ++nc;
+    }
+    qsort(cand, (size_t)nc, sizeof(or_rank), rank_cmp);
+    int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    int64_t nk = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t i = cand[c].idx;
+        int keep = 1;
+        for (int64_t k = 0; k < nk && keep; ++k) {
+            const int64_t j = kept[k];
+            double d = 0.0;
+            for (int a = 0; a < 4; ++a) d = fmax(d, fabs(theta[4 * i + a] - theta[4 * j + a]) / unit[a]);
+            if (d < merge_units) keep = 0;
+        }
+        if (keep) {
+            if (nk < cap) keep_out[nk] = i;
+            kept[nk++] = i;
+        }
+    }
+    free(kept);
+    free(cand);
+    return nk;
 }

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
     const int tid = threadIdx.x, lane = tid & 31;
     float4 *sbox = staged_box_bounds(sh, a.smem_hits);
     float *sz2 = staged_box_z2(sh, a.smem_hits);
+    float4 *ssb = staged_super_bounds(sh, a.smem_hits);
+    float *ssz2 = staged_super_z2(sh, a.smem_hits);
     int *list = kept_list(sh, a.smem_hits, tid >> 5);
     int staged = -1;
     int n_staged = 0, n_sbox = 0;
@@ -117,11 +119,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             for (int k = tid; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
             const int nblk = (H + 31) >> 5, cap = box_capacity(a.smem_hits);
             n_sbox = gbox ? (nblk < cap ? nblk : cap) : 0;
-            for (int k = tid; k < n_sbox; k += blockDim.x) {
-                float4 A = __ldg(gbox + 2 * k);
-                sz2[k] = search_box<MODEL>(A, __ldg(gbox + 2 * k + 1));
-                sbox[k] = A;
-            }
+            stage_boxes<MODEL>(gbox, n_sbox, sbox, sz2, ssb, ssz2, tid, blockDim.x);
             staged = e;
         }
         __syncthreads();
@@ -133,7 +131,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             if (g >= groups) break;
             const int64_t s = s0 + (int64_t)g * P;
             const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
-            search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, a.seeds + 2 * s, n_live, prm,
+            search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, a.seeds + 2 * s, n_live, prm,
                                    a.theta_out + 2 * s,
                                    a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work);
         }

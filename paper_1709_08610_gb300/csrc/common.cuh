@@ -47,8 +47,8 @@ __device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// Packed FP32x2 a * b + c and a * b, round-to-nearest per lane (each lane is
-// bitwise the scalar __fmaf_rn / __fmul_rn).
+// Packed FP32x2 a * b + c, a * b and a + b, round-to-nearest per lane (each
+// lane is bitwise the scalar __fmaf_rn / __fmul_rn / __fadd_rn).
 __device__ __forceinline__ unsigned long long fma2_rn(unsigned long long a, unsigned long long b,
                                                       unsigned long long c) {
     unsigned long long d;
@@ -59,6 +59,12 @@ __device__ __forceinline__ unsigned long long fma2_rn(unsigned long long a, unsi
 __device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsigned long long b) {
     unsigned long long d;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long add2_rn(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 

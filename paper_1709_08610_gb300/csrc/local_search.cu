@@ -24,13 +24,11 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     for (int k = threadIdx.x; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
     float4 *sbox = staged_box_bounds(sh, smem_hits);
     float *sz2 = staged_box_z2(sh, smem_hits);
+    float4 *ssb = staged_super_bounds(sh, smem_hits);
+    float *ssz2 = staged_super_z2(sh, smem_hits);
     const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
     const int n_sbox = gbox ? (((H + 31) >> 5) < box_capacity(smem_hits) ? ((H + 31) >> 5) : box_capacity(smem_hits)) : 0;
-    for (int k = threadIdx.x; k < n_sbox; k += blockDim.x) {
-        float4 A = __ldg(gbox + 2 * k);
-        sz2[k] = search_box<MODEL>(A, __ldg(gbox + 2 * k + 1));
-        sbox[k] = A;
-    }
+    stage_boxes<MODEL>(gbox, n_sbox, sbox, sz2, ssb, ssz2, threadIdx.x, blockDim.x);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -38,7 +36,7 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     if (s_first >= n_seeds) return;
     const int n_live = n_seeds - s_first < P ? n_seeds - s_first : P;
     const int64_t o = (int64_t)e * n_seeds + s_first;
-    search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, kept_list(sh, smem_hits, warp), seeds + 2 * o,
+    search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, kept_list(sh, smem_hits, warp), seeds + 2 * o,
                            n_live, prm, theta_out + 2 * o, R_out + o,
                            status + o, n_evals ? n_evals + o : nullptr, work);
 }

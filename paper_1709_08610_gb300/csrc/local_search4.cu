@@ -156,9 +156,11 @@ local_search4_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int6
         for (int i = 0; i < 16; ++i) S[i] = 0.f;
         for (int i = lane; i < H; i += 32) {
             const float4 h = i < n_staged ? sh[i] : __ldg(gh + i);
+            // x - t_x w rounded once (about x0 + r0), then the exact
+            // difference to x0: the error is a rounding of |x0|, not of |x|
             const float w = h.z - prm.zref;
-            const float r0 = h.x - __fmaf_rn(th[2], w, th[0]);
-            const float r1 = h.y - __fmaf_rn(th[3], w, th[1]);
+            const float r0 = __fsub_rn(__fmaf_rn(-th[2], w, h.x), th[0]);
+            const float r1 = __fsub_rn(__fmaf_rn(-th[3], w, h.y), th[1]);
             const float ev = ex2_mufu(-__fmaf_rn(r0, r0, r1 * r1) * kk);
             const float ez = ev * w, ez2 = ez * w;
             S[0] += ev;
@@ -208,8 +210,8 @@ local_search4_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int6
             for (int i = lane; i < H; i += 32) {
                 const float4 h = i < n_staged ? sh[i] : __ldg(gh + i);
                 const float w = h.z - prm.zref;
-                const float r0 = h.x - __fmaf_rn(tr[2], w, tr[0]);
-                const float r1 = h.y - __fmaf_rn(tr[3], w, tr[1]);
+                const float r0 = __fsub_rn(__fmaf_rn(-tr[2], w, h.x), tr[0]);
+                const float r1 = __fsub_rn(__fmaf_rn(-tr[3], w, h.y), tr[1]);
                 Rt += ex2_mufu(-__fmaf_rn(r0, r0, r1 * r1) * kk);
             }
             Rt = warp_sum(Rt);

@@ -32,34 +32,36 @@ struct Model {
 template <int MODEL>
 __device__ __forceinline__ void pair_rgh(const float4 h, float t0, float t1, float kk, float *S) {
     if (MODEL == RETINA_VELO_SLOPES) {
+        // every operation rounded explicitly (no contraction), so that the
+        // packed two-seed form (RghAcc2) gives bitwise the same sums
         const float rx = __fmaf_rn(-t0, h.z, h.x);
         const float ry = __fmaf_rn(-t1, h.z, h.y);
-        const float s2 = __fmaf_rn(rx, rx, ry * ry);
-        const float e = ex2_mufu(-s2 * kk);
-        const float ez = e * h.z;
-        const float ez2 = ez * h.z;
-        const float ez2rx = ez2 * rx;
-        S[0] += e;
+        const float s2 = __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+        const float e = ex2_mufu(__fmul_rn(s2, -kk));
+        const float ez = __fmul_rn(e, h.z);
+        const float ez2 = __fmul_rn(ez, h.z);
+        const float ez2rx = __fmul_rn(ez2, rx);
+        S[0] = __fadd_rn(S[0], e);
         S[1] = __fmaf_rn(ez, rx, S[1]);
         S[2] = __fmaf_rn(ez, ry, S[2]);
         S[3] = __fmaf_rn(ez2rx, rx, S[3]);
         S[4] = __fmaf_rn(ez2rx, ry, S[4]);
-        S[5] = __fmaf_rn(ez2 * ry, ry, S[5]);
-        S[6] += ez2;
+        S[5] = __fmaf_rn(__fmul_rn(ez2, ry), ry, S[5]);
+        S[6] = __fadd_rn(S[6], ez2);
     } else {
-        const float r = __fmaf_rn(-t0, h.x, h.y) - t1;
-        const float e = ex2_mufu(-(r * r) * kk);
-        const float er = e * r;
-        const float erx = er * h.x;
-        const float ex = e * h.x;
-        S[0] += e;
-        S[1] += erx;
-        S[2] += er;
-        S[3] = __fmaf_rn(erx * r, h.x, S[3]);
+        const float r = __fsub_rn(__fmaf_rn(-t0, h.x, h.y), t1);
+        const float e = ex2_mufu(__fmul_rn(__fmul_rn(r, r), -kk));
+        const float er = __fmul_rn(e, r);
+        const float erx = __fmul_rn(er, h.x);
+        const float ex = __fmul_rn(e, h.x);
+        S[0] = __fadd_rn(S[0], e);
+        S[1] = __fadd_rn(S[1], erx);
+        S[2] = __fadd_rn(S[2], er);
+        S[3] = __fmaf_rn(__fmul_rn(erx, r), h.x, S[3]);
         S[4] = __fmaf_rn(erx, r, S[4]);
         S[5] = __fmaf_rn(er, r, S[5]);
         S[6] = __fmaf_rn(ex, h.x, S[6]);
-        S[7] += ex;
+        S[7] = __fadd_rn(S[7], ex);
     }
 }
 
@@ -68,10 +70,10 @@ __device__ __forceinline__ float pair_r(const float4 h, float t0, float t1, floa
     if (MODEL == RETINA_VELO_SLOPES) {
         const float rx = __fmaf_rn(-t0, h.z, h.x);
         const float ry = __fmaf_rn(-t1, h.z, h.y);
-        return ex2_mufu(-__fmaf_rn(rx, rx, ry * ry) * kk);
+        return ex2_mufu(__fmul_rn(__fmaf_rn(rx, rx, __fmul_rn(ry, ry)), -kk));
     } else {
-        const float r = __fmaf_rn(-t0, h.x, h.y) - t1;
-        return ex2_mufu(-(r * r) * kk);
+        const float r = __fsub_rn(__fmaf_rn(-t0, h.x, h.y), t1);
+        return ex2_mufu(__fmul_rn(__fmul_rn(r, r), -kk));
     }
 }
 
@@ -102,8 +104,63 @@ struct RghAcc {
 // R-only terms of two hits, added to Rt in the order a, b.
 template <int MODEL>
 __device__ __forceinline__ void pair_r2(const float4 a, const float4 b, float t0, float t1, float kk, float &Rt) {
-    Rt += pair_r<MODEL>(a, t0, t1, kk);
-    Rt += pair_r<MODEL>(b, t0, t1, kk);
+    Rt = __fadd_rn(Rt, pair_r<MODEL>(a, t0, t1, kk));
+    Rt = __fadd_rn(Rt, pair_r<MODEL>(b, t0, t1, kk));
+}
+
+// The RGH sums of two points (seeds a and b of a warp) over the same hits, in
+// packed FP32x2 arithmetic: lane lo is seed a, hi is seed b, and each packed
+// operation rounds every lane exactly as the scalar operation of pair_rgh
+// does, so the sums are bitwise RghAcc's (slope model only).  One packed
+// instruction does the work of two scalar ones; the hit's coordinates are
+// broadcast into both lanes.
+struct RghAcc2 {
+    unsigned long long S[7];
+    unsigned long long nt0, nt1, nkk;  // (-t0a, -t0b), (-t1a, -t1b), (-kk, -kk)
+    __device__ __forceinline__ void set(float t0a, float t1a, float t0b, float t1b, float kk) {
+        nt0 = pack2(-t0a, -t0b);
+        nt1 = pack2(-t1a, -t1b);
+        nkk = pack2(-kk, -kk);
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) S[i] = 0ull;
+    }
+    __device__ __forceinline__ void add(const float4 h) {
+        const unsigned long long X = pack2(h.x, h.x), Y = pack2(h.y, h.y), Z = pack2(h.z, h.z);
+        const unsigned long long rx = fma2_rn(nt0, Z, X);
+        const unsigned long long ry = fma2_rn(nt1, Z, Y);
+        const unsigned long long s2 = fma2_rn(rx, rx, mul2_rn(ry, ry));
+        float a0, a1;
+        unpack2(mul2_rn(s2, nkk), a0, a1);
+        const unsigned long long e = pack2(ex2_mufu(a0), ex2_mufu(a1));
+        const unsigned long long ez = mul2_rn(e, Z);
+        const unsigned long long ez2 = mul2_rn(ez, Z);
+        const unsigned long long ez2rx = mul2_rn(ez2, rx);
+        S[0] = add2_rn(S[0], e);
+        S[1] = fma2_rn(ez, rx, S[1]);
+        S[2] = fma2_rn(ez, ry, S[2]);
+        S[3] = fma2_rn(ez2rx, rx, S[3]);
+        S[4] = fma2_rn(ez2rx, ry, S[4]);
+        S[5] = fma2_rn(mul2_rn(ez2, ry), ry, S[5]);
+        S[6] = add2_rn(S[6], ez2);
+    }
+    __device__ __forceinline__ void sums(float *a, float *b) const {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) unpack2(S[i], a[i], b[i]);
+    }
+};
+
+// R-only terms of one hit for two points in packed form, added to the packed
+// Rt (lo: point a, hi: point b); bitwise pair_r + __fadd_rn per lane.
+__device__ __forceinline__ void pair_r_x2(const float4 h, unsigned long long nt0, unsigned long long nt1,
+                                          unsigned long long nkk, unsigned long long &Rt) {
+    const unsigned long long X = pack2(h.x, h.x), Y = pack2(h.y, h.y), Z = pack2(h.z, h.z);
+    const unsigned long long rx = fma2_rn(nt0, Z, X);
+    const unsigned long long ry = fma2_rn(nt1, Z, Y);
+    float a0, a1;
+    unpack2(mul2_rn(fma2_rn(rx, rx, mul2_rn(ry, ry)), nkk), a0, a1);
+    Rt = add2_rn(Rt, pack2(ex2_mufu(a0), ex2_mufu(a1)));
 }
 
 template <int MODEL>
@@ -245,22 +302,32 @@ LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box);
 // boxes) the boxes of the first box_capacity(smem_hits) blocks in search_box
 // form as two arrays (the slope bounds, float4, then the |z|min^2 terms,
 // padded to a multiple of 4 floats; lanes reading consecutive blocks touch
-// consecutive words), then one list of KEPT_CHUNK kept-block offsets per warp.
-constexpr int KEPT_CHUNK = 128;  // blocks tested per chunk of a pass (4 per lane)
+// consecutive words), the same two arrays for superblocks (the union of 4
+// consecutive blocks' boxes), then per warp one list of KEPT_CHUNK
+// kept-block offsets and 32 superblock slots.
+constexpr int KEPT_CHUNK = 128;  // blocks tested per chunk of a pass (4 per lane, or 1 superblock per lane)
 __host__ __device__ __forceinline__ int box_capacity(int smem_hits) { return (smem_hits + 31) / 32 + 1; }
 __host__ __device__ __forceinline__ int box_capacity4(int smem_hits) { return (box_capacity(smem_hits) + 3) & ~3; }
+__host__ __device__ __forceinline__ int super_capacity4(int smem_hits) { return ((box_capacity4(smem_hits) >> 2) + 3) & ~3; }
 __host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes, int warps) {
     return (size_t)smem_hits * 16 +
            (with_boxes ? (size_t)box_capacity(smem_hits) * 16 + (size_t)box_capacity4(smem_hits) * 4 +
-                             (size_t)warps * KEPT_CHUNK * sizeof(int)
+                             (size_t)super_capacity4(smem_hits) * 20 + (size_t)warps * (KEPT_CHUNK + 32) * sizeof(int)
                        : 0);
 }
 __device__ __forceinline__ float4 *staged_box_bounds(float4 *sh, int smem_hits) { return sh + smem_hits; }
 __device__ __forceinline__ float *staged_box_z2(float4 *sh, int smem_hits) {
     return reinterpret_cast<float *>(sh + smem_hits + box_capacity(smem_hits));
 }
+__device__ __forceinline__ float4 *staged_super_bounds(float4 *sh, int smem_hits) {
+    return reinterpret_cast<float4 *>(staged_box_z2(sh, smem_hits) + box_capacity4(smem_hits));
+}
+__device__ __forceinline__ float *staged_super_z2(float4 *sh, int smem_hits) {
+    return reinterpret_cast<float *>(staged_super_bounds(sh, smem_hits) + super_capacity4(smem_hits));
+}
 __device__ __forceinline__ int *kept_list(float4 *sh, int smem_hits, int warp) {
-    return reinterpret_cast<int *>(staged_box_z2(sh, smem_hits) + box_capacity4(smem_hits)) + warp * KEPT_CHUNK;
+    return reinterpret_cast<int *>(staged_super_z2(sh, smem_hits) + super_capacity4(smem_hits)) +
+           warp * (KEPT_CHUNK + 32);
 }
 
 // Lane-strided pass over an event's hits: the staged prefix from shared
@@ -299,6 +366,45 @@ __device__ __forceinline__ float search_box(float4 &A, const float4 B) {
         return fin ? B.x * B.x : 0.f;
     }
     return B.x;
+}
+
+// Stage the boxes of blocks [0, n_sbox) of an event in search_box form and,
+// for the slope model, the boxes of their superblocks (4 consecutive blocks;
+// the last may hold fewer): the union of the slope bounds and the smallest
+// |z|min^2.  A superblock box contains each of its blocks' boxes, so its
+// lower bound on the exponent is at most theirs: skipping the superblock
+// skips only blocks the per-block test skips.  All threads of the CTA call
+// it (thread tid of nthreads); the caller synchronises.
+template <int MODEL>
+__device__ __forceinline__ void stage_boxes(const float4 *__restrict__ gbox, int n_sbox, float4 *sbox, float *sz2,
+                                            float4 *ssb, float *ssz2, int tid, int nthreads) {
+    if (MODEL != RETINA_VELO_SLOPES) {
+        for (int k = tid; k < n_sbox; k += nthreads) {
+            float4 A = __ldg(gbox + 2 * k);
+            sz2[k] = search_box<MODEL>(A, __ldg(gbox + 2 * k + 1));
+            sbox[k] = A;
+        }
+        return;
+    }
+    const int n_super = (n_sbox + 3) >> 2;
+    for (int q = tid; q < n_super; q += nthreads) {
+        float4 U = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+        float w = INFINITY;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = 4 * q + j;
+            if (k < n_sbox) {
+                float4 A = __ldg(gbox + 2 * k);
+                const float z2 = search_box<MODEL>(A, __ldg(gbox + 2 * k + 1));
+                sz2[k] = z2;
+                sbox[k] = A;
+                U = make_float4(fminf(U.x, A.x), fmaxf(U.y, A.y), fminf(U.z, A.z), fmaxf(U.w, A.w));
+                w = fminf(w, z2);
+            }
+        }
+        ssb[q] = U;
+        ssz2[q] = w;
+    }
 }
 
 // One point's constants for the skipping test of one pass.  Slope model:
@@ -347,16 +453,18 @@ __device__ __forceinline__ bool box_culled(const float4 A, const float w, const 
 
 // Pass over the hits that can contribute for the P points of the warp.
 // Without boxes it is for_each_hit.  With boxes, each chunk of KEPT_CHUNK
-// blocks is tested at once (lane l tests blocks l, l + 32, l + 64, l + 96 of
-// the chunk: four independent tests), the ballots give the blocks some
-// point needs, in increasing order, as offsets in the warp's list, and the
-// warp walks the list, lane l taking hit 32 b + l of each block: the same
-// per-lane order as the full pass minus blocks whose terms are all exactly
-// zero - so every sum is bitwise the full pass's sum.  Returns the hits
-// visited (for the work counters).
-template <int MODEL, bool FOUR, typename T, typename F, typename F2>
+// blocks is tested (lane l tests blocks l, l + 32, l + 64, l + 96 of the
+// chunk in turn, or, for a chunk of staged slope-model boxes, superblock l
+// first and then the blocks of the kept superblocks), the ballots give the
+// blocks some point needs, in increasing order, as offsets in the warp's
+// list, and the warp walks the list, lane l taking hit 32 b + l of each
+// block: the same per-lane order as the full pass minus blocks whose terms
+// are all exactly zero - so every sum is bitwise the full pass's sum.
+// Returns the hits visited (for the work counters).
+template <int MODEL, typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                         int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
+                                        const float4 *__restrict__ ssb, const float *__restrict__ ssz2,
                                         const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
                                         T &&needed, F &&f, F2 &&f2) {
     if (!gbox) {
@@ -366,59 +474,86 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
     int visited = 0;
     const int nblk = (H + 31) >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    int *slot = list + KEPT_CHUNK;  // the warp's 32 superblock slots
     for (int c0 = 0; c0 < nblk; c0 += KEPT_CHUNK) {
-        bool keep[KEPT_CHUNK / 32];
-#pragma unroll
-        for (int w = 0; w < KEPT_CHUNK / 32; ++w) {
-            const int b = c0 + 32 * w + lane;
-            keep[w] = false;
-            if (b < nblk) {
-                float4 A;
-                float z2;
-                if (b < n_sbox) {
-                    A = sbox[b];
-                    z2 = sz2[b];
-                } else {
-                    A = __ldg(gbox + 2 * b);
-                    z2 = search_box<MODEL>(A, __ldg(gbox + 2 * b + 1));
-                }
-                keep[w] = needed(A, z2);
-            }
-        }
         int cnt = 0;
-#pragma unroll
-        for (int w = 0; w < KEPT_CHUNK / 32; ++w) {
-            const unsigned m = __ballot_sync(0xffffffffu, keep[w]);
-            if (keep[w]) list[cnt + __popc(m & lt)] = (c0 + 32 * w + lane) * 32;
-            cnt += __popc(m);
+        if (MODEL == RETINA_VELO_SLOPES && c0 + KEPT_CHUNK <= n_sbox) {
+            // two levels: lane l tests superblock c0 / 4 + l (blocks 4 of them),
+            // then the blocks of the superblocks some point needs, in
+            // increasing order (superblock rank, block within it)
+            const int q = (c0 >> 2) + lane;
+            const bool keep_q = needed(ssb[q], ssz2[q]);
+            const unsigned mq = __ballot_sync(0xffffffffu, keep_q);
+            if (mq == 0u) continue;
+            if (keep_q) slot[__popc(mq & lt)] = q;
+            __syncwarp();
+            const int n_sub = 4 * __popc(mq);
+            for (int k0 = 0; k0 < n_sub; k0 += 32) {
+                const int k = k0 + lane;
+                bool keep = false;
+                int b = 0;
+                if (k < n_sub) {
+                    b = 4 * slot[k >> 2] + (k & 3);
+                    keep = needed(sbox[b], sz2[b]);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) list[cnt + __popc(m & lt)] = b * 32;
+                cnt += __popc(m);
+            }
+        } else {
+#pragma unroll 1
+            for (int w = 0; w < KEPT_CHUNK / 32; ++w) {
+                const int b = c0 + 32 * w + lane;
+                bool keep = false;
+                if (b < nblk) {
+                    float4 A;
+                    float z2;
+                    if (b < n_sbox) {
+                        A = sbox[b];
+                        z2 = sz2[b];
+                    } else {
+                        A = __ldg(gbox + 2 * b);
+                        z2 = search_box<MODEL>(A, __ldg(gbox + 2 * b + 1));
+                    }
+                    keep = needed(A, z2);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) list[cnt + __popc(m & lt)] = b * 32;
+                cnt += __popc(m);
+            }
         }
         __syncwarp();
         if (cnt == 0) continue;
         // hits visited: 32 per kept block, the event's last block holding H - 32 (nblk - 1)
         const int last = list[cnt - 1];
         visited += 32 * cnt - (last == 32 * (nblk - 1) ? 32 * nblk - H : 0);
-        // blocks held whole in shared memory form a prefix of the list
+        // One loop body for every kept block (the kernel is large enough that
+        // its instruction footprint, not its instruction count, sets the
+        // pace: a second copy of the pair arithmetic doubled the instruction
+        // fetch stalls).  Blocks held whole in shared memory form a prefix of
+        // the list and are read from there, the rest from global memory
+        // through the same generic pointer (a staged hit is the same value in
+        // both places); the event's last block, when partial, is left to the
+        // one-block remainder, whose lanes past the event add nothing.  Per
+        // lane the hits are added in list order, and f2(a, b) adds exactly
+        // what f(a); f(b) adds, so every sum is the full pass's.
         const int n_fast = last + 32 <= n_staged ? cnt : (cnt > 1 && list[cnt - 2] + 32 <= n_staged ? cnt - 1 : 0);
+        const int n_pairs_end = cnt - ((last == 32 * (nblk - 1) && (H & 31)) ? 1 : 0);
         int i = 0;
-        if (FOUR) {
-            for (; i + 4 <= n_fast; i += 4) {
-                const int4 q = *reinterpret_cast<const int4 *>(list + i);
-                const float4 ha = sh[q.x + lane], hb = sh[q.y + lane];
-                const float4 hc = sh[q.z + lane], hd = sh[q.w + lane];
+#pragma unroll 1
+        for (int seg = 0; seg < 2; ++seg) {
+            const float4 *src = seg == 0 ? sh : gh;
+            const int end = seg == 0 ? (n_fast < n_pairs_end ? n_fast : n_pairs_end) : n_pairs_end;
+#pragma unroll 1
+            for (; i + 2 <= end; i += 2) {
+                const float4 ha = src[list[i] + lane], hb = src[list[i + 1] + lane];
                 f2(ha, hb);
-                f2(hc, hd);
             }
         }
-        for (; i + 2 <= n_fast; i += 2) {
-            const int2 q = *reinterpret_cast<const int2 *>(list + i);
-            f2(sh[q.x + lane], sh[q.y + lane]);
-        }
+#pragma unroll 1
         for (; i < cnt; ++i) {
             const int k = list[i] + lane;
-            if (k < n_staged)
-                f(sh[k]);
-            else if (k < H)
-                f(__ldg(gh + k));
+            if (k < H) f(gh[k]);
         }
         __syncwarp();  // the list is rewritten by the next chunk
     }
@@ -437,6 +572,7 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
 template <int MODEL, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                            int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
+                                           const float4 *__restrict__ ssb, const float *__restrict__ ssz2,
                                            const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
                                            const float *__restrict__ seeds, const LsParams &prm,
                                            float *__restrict__ theta_out, float *__restrict__ R_out,
@@ -455,8 +591,8 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
             RghAcc<MODEL> acc;
             acc.zero();
             const CullPt cp = cull_pt<MODEL>(th0, th1, kk, cull);
-            const int vis = hit_pass<MODEL, true>(
-                sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+            const int vis = hit_pass<MODEL>(
+                sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                 [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, cp); },
                 [&](const float4 h) { acc.add(h, th0, th1, kk); },
                 [&](const float4 a, const float4 b) { acc.add2(a, b, th0, th1, kk); });
@@ -489,11 +625,11 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                 const CullPt ct = cull_pt_union<MODEL>(tr0, tr1, kk, cull, kk2, prm.cull[j + 1]);
                 RghAcc<MODEL> acc;
                 acc.zero();
-                vis = hit_pass<MODEL, true>(
-                    sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                vis = hit_pass<MODEL>(
+                    sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                     [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
                     [&](const float4 h) {
-                        Rt += pair_r<MODEL>(h, tr0, tr1, kk);
+                        Rt = __fadd_rn(Rt, pair_r<MODEL>(h, tr0, tr1, kk));
                         acc.add(h, tr0, tr1, kk2);
                     },
                     [&](const float4 a, const float4 b) {
@@ -504,10 +640,10 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                 w_rgh += (uint32_t)vis;
             } else {
                 const CullPt ct = cull_pt<MODEL>(tr0, tr1, kk, cull);
-                vis = hit_pass<MODEL, false>(
-                    sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
+                vis = hit_pass<MODEL>(
+                    sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                     [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
-                    [&](const float4 h) { Rt += pair_r<MODEL>(h, tr0, tr1, kk); },
+                    [&](const float4 h) { Rt = __fadd_rn(Rt, pair_r<MODEL>(h, tr0, tr1, kk)); },
                     [&](const float4 a, const float4 b) { pair_r2<MODEL>(a, b, tr0, tr1, kk, Rt); });
             }
             w_r += (uint32_t)vis;
@@ -558,14 +694,15 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
 template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
                                              int n_staged, int H, int lane, const float4 *__restrict__ sbox,
-                                             const float *__restrict__ sz2, const float4 *__restrict__ gbox,
+                                             const float *__restrict__ sz2, const float4 *__restrict__ ssb,
+                                             const float *__restrict__ ssz2, const float4 *__restrict__ gbox,
                                              int n_sbox, int *__restrict__ list,
                                              const float *__restrict__ seeds,
                                              int n_live, const LsParams &prm, float *__restrict__ theta_out,
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
                                              uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work) {
     if constexpr (P == 1) {
-        search_one<MODEL, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list, seeds, prm, theta_out, R_out,
+        search_one<MODEL, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, seeds, prm, theta_out, R_out,
                           status, n_evals, work);
         return;
     }
@@ -595,24 +732,39 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             acc[p].zero();
             cp[p] = cull_pt<MODEL>(th0[p], th1[p], kk, cull);
         }
-        const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
-                                 [&](const float4 A, const float z2) {
-                                     bool need = false;
+        auto needed = [&](const float4 A, const float z2) {
+            bool need = false;
 #pragma unroll
-                                     for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, z2, cp[p]);
-                                     return need;
-                                 },
-                                 [&](const float4 h) {
-#pragma unroll
-                                     for (int p = 0; p < P; ++p) acc[p].add(h, th0[p], th1[p], kk);
-                                 },
-                                 [&](const float4 a, const float4 b) {
-#pragma unroll
-                                     for (int p = 0; p < P; ++p) acc[p].add2(a, b, th0[p], th1[p], kk);
-                                 });
+            for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, z2, cp[p]);
+            return need;
+        };
         float S[P][NS];
+        int vis;
+        if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) {
+            // both points' sums in packed FP32x2 (bitwise the scalar sums)
+            RghAcc2 a2;
+            a2.set(th0[0], th1[0], th0[1], th1[1], kk);
+            a2.zero();
+            vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
+                                         [&](const float4 h) { a2.add(h); },
+                                         [&](const float4 a, const float4 b) {
+                                             a2.add(a);
+                                             a2.add(b);
+                                         });
+            a2.sums(S[0], S[1]);
+        } else {
+            vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
+                                          [&](const float4 h) {
 #pragma unroll
-        for (int p = 0; p < P; ++p) acc[p].sums(S[p]);
+                                              for (int p = 0; p < P; ++p) acc[p].add(h, th0[p], th1[p], kk);
+                                          },
+                                          [&](const float4 a, const float4 b) {
+#pragma unroll
+                                              for (int p = 0; p < P; ++p) acc[p].add2(a, b, th0[p], th1[p], kk);
+                                          });
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[p].sums(S[p]);
+        }
         w_rgh += (uint32_t)vis * (uint32_t)n_live;
         float R[P], g0[P], g1[P], pp0[P], pp1[P], slope[P], t[P];
         bool pending[P];
@@ -649,24 +801,40 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 Rt[p] = 0.f;
                 ct[p] = cull_pt<MODEL>(tr0[p], tr1[p], kk, cull);
             }
-            const int vis = hit_pass<MODEL, P == 1>(sh, gh, n_staged, H, lane, sbox, sz2, gbox, n_sbox, list,
-                                     [&](const float4 A, const float z2) {
-                                         bool need = false;
+            auto needed_r = [&](const float4 A, const float z2) {
+                bool need = false;
 #pragma unroll
-                                         for (int p = 0; p < P; ++p)
-                                             need |= pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
-                                         return need;
-                                     },
-                                     [&](const float4 h) {
+                for (int p = 0; p < P; ++p) need |= pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
+                return need;
+            };
+            int vis;
+            if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) {
+                // both trial points in packed FP32x2; a point whose line search
+                // is over accumulates too, and its sum is not used
+                const unsigned long long nt0 = pack2(-tr0[0], -tr0[1]), nt1 = pack2(-tr1[0], -tr1[1]);
+                const unsigned long long nkk = pack2(-kk, -kk);
+                unsigned long long Rt2 = 0ull;
+                vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed_r,
+                                             [&](const float4 h) { pair_r_x2(h, nt0, nt1, nkk, Rt2); },
+                                             [&](const float4 a, const float4 b) {
+                                                 pair_r_x2(a, nt0, nt1, nkk, Rt2);
+                                                 pair_r_x2(b, nt0, nt1, nkk, Rt2);
+                                             });
+                unpack2(Rt2, Rt[0], Rt[1]);
+            } else {
+                vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed_r,
+                                              [&](const float4 h) {
 #pragma unroll
-                                         for (int p = 0; p < P; ++p)
-                                             if (pending[p]) Rt[p] += pair_r<MODEL>(h, tr0[p], tr1[p], kk);
-                                     },
-                                     [&](const float4 a, const float4 b) {
+                                                  for (int p = 0; p < P; ++p)
+                                                      if (pending[p])
+                                                          Rt[p] = __fadd_rn(Rt[p], pair_r<MODEL>(h, tr0[p], tr1[p], kk));
+                                              },
+                                              [&](const float4 a, const float4 b) {
 #pragma unroll
-                                         for (int p = 0; p < P; ++p)
-                                             if (pending[p]) pair_r2<MODEL>(a, b, tr0[p], tr1[p], kk, Rt[p]);
-                                     });
+                                                  for (int p = 0; p < P; ++p)
+                                                      if (pending[p]) pair_r2<MODEL>(a, b, tr0[p], tr1[p], kk, Rt[p]);
+                                              });
+            }
             int n_pend = 0;
 #pragma unroll
             for (int p = 0; p < P; ++p) n_pend += pending[p] ? 1 : 0;

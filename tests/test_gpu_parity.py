@@ -350,6 +350,7 @@ def test_local_search_alternative_updates_match_oracle(rt, update, wl_name):
 
     # the oracle ends 165 (velo) / 15 (toy) robust, well-conditioned seeds at converged maxima
     check_conditioned(th_g, R_g, st_g, res[3:], run, wl.grid_step, _converged_2d(ev, wl),
+                      lambda th: oracle.response(ev.hits, wl.model, [th], sig[-1])[0],
                       min_firm_conv=120 if wl_name == "velo" else 10)
 
 

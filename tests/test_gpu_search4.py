@@ -54,6 +54,27 @@ def _converged_at(ev):
     return at
 
 
+def _response_with_bound(ev):
+    """R(theta; sigma_q) in FP64 and the error float32 adds to it at theta:
+    each residual is one rounding of x - t_x w (about x0 + r, so at most
+    2^-24 (|x0| + |r|)) followed by an exact subtraction, and a residual error
+    dr moves a term by at most e 2 |r| dr / sigma^2 (plus R's own 1e-5)."""
+    h = ev.hits.astype(np.float64)
+    sig = SIGMA[-1]
+
+    def at(th):
+        w = h[:, 2] - ZREF
+        r0 = h[:, 0] - th[0] - th[2] * w
+        r1 = h[:, 1] - th[1] - th[3] * w
+        e = np.exp(-(r0 * r0 + r1 * r1) / sig ** 2)
+        u = 2.0 ** -24
+        dr0 = u * (abs(th[0]) + np.abs(r0))
+        dr1 = u * (abs(th[1]) + np.abs(r1))
+        bound = float(np.sum(e * 2.0 * (np.abs(r0) * dr0 + np.abs(r1) * dr1) / sig ** 2))
+        return oracle.response4(ev.hits, th, sig, zref=ZREF), bound
+    return at
+
+
 def test_search4_matches_oracle_on_a_smeared_vertex_event(rt):
     # point-wise parity on every robust seed whose path the oracle's perturbed
     # replicas show to be well conditioned; ill-conditioned paths must end in
@@ -68,7 +89,8 @@ def test_search4_matches_oracle_on_a_smeared_vertex_event(rt):
     def run(pt):
         return oracle.local_search4(ev.hits, seeds, SIGMA, SCALE, zref=ZREF, perturb=pt)
 
-    check_conditioned(th_g, R_g, st_g, run(None), run, SCALE, _converged_at(ev), min_firm_conv=CONV_MIN)
+    check_conditioned(th_g, R_g, st_g, run(None), run, SCALE, _converged_at(ev), _response_with_bound(ev),
+                      min_firm_conv=CONV_MIN)
 
 
 def test_search4_edge_cases(rt):
