@@ -454,46 +454,68 @@ def alpha_sweep(rt, stream, flush, reps: int = 3):
             "runs": out, "l2": "flushed before each replay"}
 
 
-def search4_measure(rt, stream, flush, ev, wl, n_seeds: int = 8192, reps: int = 20):
-    """The four-parameter search (x0, y0, t_x, t_y at z_ref = the layers' mean
-    z) on the step's event, whose vertex is smeared (the two-parameter model
-    cannot fit its tracks): n_seeds seeds with uniform slopes and zero offsets,
-    the paper's three bandwidths; kernel time (median over reps launches, L2
-    flushed before each) and the share of MC tracks with a converged seed
-    (status <= 1, R >= R0) within 1e-3 in slope and 0.1 mm in offset."""
+SEARCH4_LAYER_PAIRS = ((17, 25), (18, 24), (19, 23))  # indices of the 26 layers: the downstream end
+
+
+def search4_measure(rt, stream, flush, reps: int = 10):
+    """The four-parameter model (x0, y0, t_x, t_y at z_ref = the layers' mean z)
+    on smeared-vertex events, where the two-slope model cannot fit the
+    tracks: starting points from hit pairs on three downstream layer pairs
+    (lines passing within 0.3 mm of the beam axis at |z| <= 250 mm), the
+    four-parameter truncated-Newton search (q = 3, the paper's bandwidths),
+    cluster / select in four dimensions; one CUDA graph per batch.  The step's
+    event alone and the 1024-event batch (tracks ~ Poisson(150)), both as
+    generated (vertex smeared per track by (0.05, 0.05, 50) mm); MC efficiency
+    within 0.1 mm in the offsets and 1e-3 in the slopes."""
     import torch
+    from paper_1709_08610_gb300.pipeline import Search4Batch
     zref = float(np.mean(VELO_PLANES_Z))
-    t = ev.truth[:, :2]
-    v = ev.truth[:, 2:5]
-    truth4 = np.stack([v[:, 0] + t[:, 0] * (zref - v[:, 2]), v[:, 1] + t[:, 1] * (zref - v[:, 2]), t[:, 0], t[:, 1]], 1)
-    sl = uniform_seeds(wl, n_seeds, RUN_SEED, 4)
-    seeds = np.concatenate([np.zeros((n_seeds, 2), np.float32), sl], 1)[None]
-    hits = torch.from_numpy(ev.hits).cuda()
-    offs = torch.tensor([0, ev.n_hits], dtype=torch.int64, device="cuda")
-    sd = torch.from_numpy(np.ascontiguousarray(seeds)).cuda()
-    opts = rt.LsOpts4(sigma=tuple(wl.sigma_schedule), zref=zref)
-    out = rt.local_search4(hits, offs, sd, opts, stream=stream)
-    ts = []
-    for _ in range(reps):
-        flush.zero_()
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        rt.local_search4(hits, offs, sd, opts, out=out, stream=stream)
-        c.record(stream)
-        c.synchronize()
-        ts.append(a.elapsed_time(c))
-    th, R, st = (x.cpu().numpy()[0] for x in out)
-    ok = (st <= 1) & (R >= wl.R0)
+    z = np.asarray(VELO_PLANES_Z)
+    pairs = [(z[a], z[b]) for a, b in SEARCH4_LAYER_PAIRS]
+    opts = rt.LsOpts4(sigma=tuple(WORKLOADS["velo"].sigma_schedule), zref=zref)
     tol = np.array([0.1, 0.1, 1e-3, 1e-3])
-    found = 0
-    if ok.any():
-        d = np.max(np.abs(th[ok][:, None, :].astype(np.float64) - truth4[None]) / tol, axis=2)
-        found = int((d.min(axis=0) <= 1.0).sum())
-    ms = statistics.median(ts)
-    return {"workload": "the step's event (smeared vertex), %d seeds: uniform slopes, zero offsets at z_ref = %g mm"
-                        % (n_seeds, zref),
-            "ms": ms, "seeds_per_s": n_seeds / (ms * 1e-3), "mc_efficiency": found / len(truth4),
-            "converged_above_R0": int(ok.sum()), "l2": "flushed before each launch"}
+    out = {}
+    for name, wl_name, E, seed in (("velo_event", "velo", 1, RUN_SEED), ("velo_batch", "velo_batch", 1024,
+                                                                        BATCH_RUN_SEED + 3)):
+        wl = WORKLOADS[wl_name]
+        evs = [make_event(wl, seed, e) for e in range(E)]
+        b = batch_of(evs)
+        obj = Search4Batch(E, b.hits.shape[0], rt.Grid.of(wl), opts, wl.R0, pairs, 0.5, 0.3, (-250.0, 250.0))
+        obj.load(b.hits, b.offsets)
+        obj.capture()
+        obj.replay()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            obj.replay()
+            c.record(stream)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        found = obj.results()
+        n_seeds = obj.seeds[1].cpu().numpy()
+        hit = tot = fakes = 0
+        for f, ev in zip(found, evs):
+            t, v = ev.truth[:, :2], ev.truth[:, 2:5]
+            T = np.stack([v[:, 0] + t[:, 0] * (zref - v[:, 2]), v[:, 1] + t[:, 1] * (zref - v[:, 2]), t[:, 0],
+                          t[:, 1]], 1)
+            tot += len(T)
+            if len(f):
+                d = np.max(np.abs(f[:, None, :] - T[None]) / tol, axis=2)
+                hit += int((d.min(axis=0) <= 1).sum())
+                fakes += int((d.min(axis=1) > 1).sum())
+        ms = statistics.median(ts)
+        out[name] = {"events": E, "events_per_s": E / (ms * 1e-3), "ms": ms, "mc_efficiency": hit / tot,
+                     "fakes_per_event": fakes / E, "seeds_per_event": float(n_seeds.mean()),
+                     "tracks_per_event": float(np.mean([len(f) for f in found]))}
+        del obj
+        torch.cuda.empty_cache()
+    return {"workload": "smeared-vertex VELO-like events (vertex ~ N(0, (0.05, 0.05, 50)) mm per track): the step's "
+                        "event, and 1024 events with Poisson(150) tracks; hit-pair seeds on layers %s, "
+                        "four-parameter search, four-dimensional cluster/select; one CUDA graph per batch"
+                        % (list(SEARCH4_LAYER_PAIRS),),
+            "runs": out, "l2": "flushed before each replay"}
 
 
 SVELO_MULTIPLICITIES = (50, 100, 150, 200, 250, 300, 350)
@@ -1347,8 +1369,7 @@ def main():
         restore()
         extras["toy2d"] = toy_step(rt, with_cpu=with_cpu)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        wl2 = WORKLOADS["velo"]
-        extras["search4"] = search4_measure(rt, stream, flush, make_event(wl2, RUN_SEED, rank), wl2)
+        extras["search4"] = search4_measure(rt, stream, flush)
         if not args.no_batched:
             # the library's launch rules for batches: one grid hit slice at this many
             # tiles, the search filling the GPU

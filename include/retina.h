@@ -420,6 +420,10 @@ int retina_refine_maxima(const float *hits, int64_t n_hits, const int64_t *event
  * from global memory.
  *
  *   seeds     : float32 [n_events][n_seeds][4] starting points.
+ *   seed_count: nullable int32 [n_events]: event e searches its first
+ *               min(max(seed_count[e], 0), n_seeds) seeds (the n_seeds of
+ *               retina_pair_seeds4 can be passed as is); the outputs of the
+ *               others are left untouched.
  *   opts      : host pointer (below).
  *   theta_out : float32 [n_events][n_seeds][4];  R_out: float32
  *               [n_events][n_seeds] at sigma_q;  status: uint8
@@ -438,8 +442,43 @@ typedef struct {
     float zref;           /* reference plane of the offsets (finite)         */
 } retina_ls4_opts;
 int retina_local_search4(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
-                         const float *seeds, int32_t n_seeds, const retina_ls4_opts *opts, float *theta_out,
-                         float *R_out, uint8_t *status, void *stream);
+                         const float *seeds, int32_t n_seeds, const int32_t *seed_count, const retina_ls4_opts *opts,
+                         float *theta_out, float *R_out, uint8_t *status, void *stream);
+
+/*
+ * retina_pair_seeds4 - starting points for retina_local_search4 from pairs of hits.
+ *
+ * Paper: none (the paper has no four-parameter search; Algorithm 1 draws its
+ * starting points from a prior P_theta it leaves open).  Tracks come from
+ * the beam line, so two hits of one track on two layers span a line passing
+ * close to the z axis inside the luminous region, while two hits of
+ * different tracks rarely do.  For each layer pair p in order
+ * (z_a = layer_z[2 p], z_b = layer_z[2 p + 1]), every hit i of the event with
+ * |z_i - z_a| <= dz_tol and every hit j with |z_j - z_b| <= dz_tol, in
+ * increasing index order (i outer):
+ *   t = (x_j - x_i, y_j - y_i) / (z_j - z_i),  |t|^2 = t_x^2 + t_y^2,
+ *   kept when |t|^2 > 0, (x_i t_y - y_i t_x)^2 <= d_max^2 |t|^2 (the line's
+ *   distance to the z axis is at most d_max) and
+ *   zc_lo <= z_i - (x_i t_x + y_i t_y) / |t|^2 <= zc_hi (where it comes
+ *   closest);
+ *   seed = (x_i + t_x (zref - z_i), y_i + t_y (zref - z_i), t_x, t_y).
+ * Every operation is one float32 rounding in the order written (no
+ * contraction), so the kept pairs are a function of the float32 inputs.
+ *
+ *   hits, n_hits, event_offsets, n_events : as retina_local_search4.
+ *   layer_z    : host float32 [n_pairs][2], 1 <= n_pairs <= RETINA_MAX_LAYER_PAIRS.
+ *   seeds      : float32 [n_events][K][4], the first K kept pairs in order.
+ *   n_seeds    : int32 [n_events]: pairs kept (may exceed K), or -1 when a
+ *                layer held more than RETINA_PAIR_LAYER_CAP of the event's
+ *                hits (then only the first that many of it were paired).
+ * Returns RETINA_EINVAL for bad sizes, non-finite or negative cuts or null
+ * pointers (nothing launched); n_events == 0 is a no-op.
+ */
+#define RETINA_MAX_LAYER_PAIRS 8
+#define RETINA_PAIR_LAYER_CAP 4096
+int retina_pair_seeds4(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                       const float *layer_z, int32_t n_pairs, float dz_tol, float d_max, float zc_lo, float zc_hi,
+                       float zref, float *seeds, int32_t *n_seeds, int32_t K, void *stream);
 
 /*
  * retina_batched_search - Algorithm 1 over a ragged batch, one persistent launch.
@@ -513,6 +552,32 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
                           int32_t n_events, int32_t n_points, const retina_grid *box, float R0,
                           float merge_cells, float *tracks, float *track_R, int32_t *track_src,
                           int32_t *n_tracks, int32_t K, void *stream);
+
+/*
+ * retina_extract_tracks4 - cluster / select for four-parameter points.
+ *
+ * Paper: Algorithm 1, its last two lines, for theta = (x0, y0, t_x, t_y) of
+ * retina_local_search4.  Candidates are points with status 0 or 1 (status
+ * may be NULL), all four parameters finite, slopes (t_x, t_y) inside
+ * slope_box and R >= R0; they are visited by decreasing R (equal R: lower
+ * point index first) and a candidate is kept when, for every point kept
+ * before it, max_a |theta_a - theta_kept_a| / unit_a >= merge_units.  The
+ * comparison is exact when merge_units * unit_a are powers of two.
+ *
+ *   theta   : float32 [n_events][n_points][4];  R: float32 [n_events][n_points].
+ *   n_valid : nullable int32 [n_events]; only the first
+ *             min(n_valid[e], n_points) points of event e are considered.
+ *   unit    : host float32 [4] > 0 (e.g. the search's scale).
+ *   tracks  : float32 [n_events][K][4];  track_R: float32 [n_events][K];
+ *   track_src: nullable int32 [n_events][K];  n_tracks: int32 [n_events]
+ *             (may exceed K; the first K in visiting order are written).
+ *   n_points must be <= RETINA_MAX_EXTRACT_POINTS4 (else RETINA_ENOSPACE).
+ */
+#define RETINA_MAX_EXTRACT_POINTS4 4096
+int retina_extract_tracks4(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                           int32_t n_events, int32_t n_points, const retina_grid *slope_box, const float *unit, float R0,
+                           float merge_units, float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks,
+                           int32_t K, void *stream);
 
 /*
  * Learned seed proposer

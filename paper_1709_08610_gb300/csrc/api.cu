@@ -315,8 +315,8 @@ int retina_refine_maxima(const float *hits, int64_t n_hits, const int64_t *event
 }
 
 int retina_local_search4(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
-                         const float *seeds, int32_t n_seeds, const retina_ls4_opts *opts, float *theta_out,
-                         float *R_out, uint8_t *status, void *stream) {
+                         const float *seeds, int32_t n_seeds, const int32_t *seed_count, const retina_ls4_opts *opts,
+                         float *theta_out, float *R_out, uint8_t *status, void *stream) {
     if (n_events < 0 || n_seeds < 0 || n_hits < 0 || !opts) return RETINA_EINVAL;
     if (opts->q < 1 || opts->q > RETINA_MAX_Q) return RETINA_EINVAL;
     for (int j = 0; j < opts->q; ++j)
@@ -330,7 +330,25 @@ int retina_local_search4(const float *hits, int64_t n_hits, const int64_t *event
     if (!event_offsets || !seeds || !theta_out || !R_out || !status) return RETINA_EINVAL;
     if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
     return cuda_status(launch_local_search4((const float4 *)hits, n_hits, event_offsets, n_events, seeds, n_seeds,
-                                            opts, theta_out, R_out, status, g_opt_smem_hits, (cudaStream_t)stream));
+                                            seed_count, opts, theta_out, R_out, status, g_opt_smem_hits,
+                                            (cudaStream_t)stream));
+}
+
+int retina_pair_seeds4(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,
+                       const float *layer_z, int32_t n_pairs, float dz_tol, float d_max, float zc_lo, float zc_hi,
+                       float zref, float *seeds, int32_t *n_seeds, int32_t K, void *stream) {
+    if (n_events < 0 || n_hits < 0 || K < 1 || n_pairs < 1 || n_pairs > RETINA_MAX_LAYER_PAIRS) return RETINA_EINVAL;
+    if (!(isfinite(dz_tol) && dz_tol >= 0.f) || !(isfinite(d_max) && d_max >= 0.f) || !isfinite(zc_lo) ||
+        !isfinite(zc_hi) || !isfinite(zref) || !layer_z)
+        return RETINA_EINVAL;
+    for (int p = 0; p < 2 * n_pairs; ++p)
+        if (!isfinite(layer_z[p])) return RETINA_EINVAL;
+    if ((int64_t)K * 4 > (int64_t)INT32_MAX) return RETINA_EINVAL;
+    if (n_events == 0) return RETINA_OK;
+    if (!event_offsets || !seeds || !n_seeds) return RETINA_EINVAL;
+    if (n_hits > 0 && (!hits || !aligned16(hits))) return RETINA_EINVAL;
+    return cuda_status(launch_pair_seeds4((const float4 *)hits, n_hits, event_offsets, n_events, layer_z, n_pairs,
+                                          dz_tol, d_max, zc_lo, zc_hi, zref, seeds, n_seeds, K, (cudaStream_t)stream));
 }
 
 int retina_batched_search_workspace_size(int32_t n_events, size_t *bytes) {
@@ -384,6 +402,31 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
     if (!tracks || !track_R) return RETINA_EINVAL;
     return cuda_status(launch_extract_tracks(theta, R, status, n_valid, n_events, n_points, box, R0, merge_cells,
                                              tracks, track_R, track_src, n_tracks, K, (cudaStream_t)stream));
+}
+
+int retina_extract_tracks4(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                           int32_t n_events, int32_t n_points, const retina_grid *slope_box, const float *unit, float R0,
+                           float merge_units, float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks,
+                           int32_t K, void *stream) {
+    if (n_events < 0 || n_points < 0 || K < 1 || !slope_box || !unit || isnan(R0)) return RETINA_EINVAL;
+    if (!(isfinite(merge_units) && merge_units > 0.f)) return RETINA_EINVAL;
+    for (int a = 0; a < 4; ++a)
+        if (!(isfinite(unit[a]) && unit[a] > 0.f) || !isfinite(merge_units * unit[a])) return RETINA_EINVAL;
+    for (int a = 0; a < 2; ++a) {
+        if (!isfinite(slope_box->lo[a]) || !(isfinite(slope_box->step[a]) && slope_box->step[a] > 0.f) ||
+            slope_box->n[a] <= 0)
+            return RETINA_EINVAL;
+        // buckets of the slope coordinates are indexed in 21 bits
+        if ((double)slope_box->n[a] * slope_box->step[a] / ((double)merge_units * unit[2 + a]) > 1048576.0)
+            return RETINA_EINVAL;
+    }
+    if (n_events == 0) return RETINA_OK;
+    if (n_events > 65535) return RETINA_EINVAL;
+    if (n_points > RETINA_MAX_EXTRACT_POINTS4) return RETINA_ENOSPACE;
+    if (!theta || !R || !tracks || !track_R || !n_tracks) return RETINA_EINVAL;
+    return cuda_status(launch_extract_tracks4(theta, R, status, n_valid, n_events, n_points, slope_box, unit, R0,
+                                              merge_units, tracks, track_R, track_src, n_tracks, K,
+                                              (cudaStream_t)stream));
 }
 
 int retina_slope_histogram(const float *hits, int64_t n_hits, const int64_t *event_offsets, int32_t n_events,

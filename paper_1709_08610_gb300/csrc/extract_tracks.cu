@@ -101,14 +101,26 @@ __device__ __forceinline__ int lower_bound_u64(const uint64_t *keys, int n, uint
     return lo;
 }
 
+// Points have D coordinates (2: the two-parameter models, 4: (x0, y0, t_x,
+// t_y)); the box and the buckets are on the last two (the grid's axes).
 struct ExtractParams {
     float lo0, lo1, hi0, hi1;
-    float c0, c1;    // merge distance per axis: merge_cells * step
-    float w0, w1;    // bucket width per axis (slightly above c)
+    float c[4];      // merge distance per coordinate: merge_cells * step (or unit)
+    float w0, w1;    // bucket width of the last two coordinates (slightly above c)
     float R0;
     int n_points, K, cap;
 };
 
+// Conflict of two points: closer than the merge distance in every coordinate.
+template <int D>
+__device__ __forceinline__ bool conflict(const float *a, const float *b, const ExtractParams &prm) {
+    bool c = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) c = c && abs_diff_lt(a[d], b[d], prm.c[d]);
+    return c;
+}
+
+template <int D>
 __global__ void __launch_bounds__(EX_THREADS)
 extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__ R, const uint8_t *__restrict__ status,
                       const int32_t *__restrict__ n_valid, ExtractParams prm, float *__restrict__ tracks,
@@ -116,9 +128,8 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     extern __shared__ __align__(16) unsigned char smem[];
     const int cap = prm.cap;
     uint64_t *keys = reinterpret_cast<uint64_t *>(smem);
-    float *th0 = reinterpret_cast<float *>(keys + cap);
-    float *th1 = th0 + cap;
-    int32_t *src = reinterpret_cast<int32_t *>(th1 + cap);
+    float *th = reinterpret_cast<float *>(keys + cap);  // [D][cap]
+    int32_t *src = reinterpret_cast<int32_t *>(th + D * cap);
     volatile uint8_t *state = reinterpret_cast<uint8_t *>(src + cap);
     __shared__ int nc_s;
     __shared__ int warp_tot[EX_THREADS / 32];
@@ -138,25 +149,30 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     constexpr int FU = 8;
     for (int i0 = 0; i0 < n; i0 += FU * EX_THREADS) {
         float r[FU], a0[FU], a1[FU];
+        bool fin[FU];
         uint8_t sv[FU];
 #pragma unroll
         for (int u = 0; u < FU; ++u) {
             const int i = i0 + u * EX_THREADS + tid;
             r[u] = a0[u] = a1[u] = 0.f;
+            fin[u] = true;
             sv[u] = 0;
             if (i < n) {
                 const int64_t o = base + i;
                 r[u] = R[o];
-                a0[u] = theta[2 * o];
-                a1[u] = theta[2 * o + 1];
+                a0[u] = theta[D * o + D - 2];
+                a1[u] = theta[D * o + D - 1];
+#pragma unroll
+                for (int d = 0; d < D - 2; ++d) fin[u] = fin[u] && isfinite(theta[D * o + d]);
                 if (status) sv[u] = status[o];
             }
         }
 #pragma unroll
         for (int u = 0; u < FU; ++u) {
             const int i = i0 + u * EX_THREADS + tid;
-            const bool ok = i < n && isfinite(r[u]) && isfinite(a0[u]) && isfinite(a1[u]) && (r[u] >= prm.R0) &&
-                            sv[u] <= 1 && a0[u] >= prm.lo0 && a0[u] < prm.hi0 && a1[u] >= prm.lo1 && a1[u] < prm.hi1;
+            const bool ok = i < n && fin[u] && isfinite(r[u]) && isfinite(a0[u]) && isfinite(a1[u]) &&
+                            (r[u] >= prm.R0) && sv[u] <= 1 && a0[u] >= prm.lo0 && a0[u] < prm.hi0 &&
+                            a1[u] >= prm.lo1 && a1[u] < prm.hi1;
             if (ok) {
                 const int pos = atomicAdd(&nc_s, 1);
                 keys[pos] = ((uint64_t)(~float_order_key(r[u])) << 32) | (uint32_t)i;
@@ -175,7 +191,7 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
         for (int q = 0; q < 2; ++q) v[q] = 2 * lane + q < nc ? keys[2 * lane + q] : ~0ull;
         bitonic_sort_regs<uint64_t, 2, 32>(v, keys);
         // rank r = 2 lane + q holds v[q]; lane l keeps ranks l and l + 32 for the tests
-        float a0[2], a1[2];
+        float a[2][D];
         int si[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -183,20 +199,22 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
             const uint64_t k0 = __shfl_sync(0xffffffffu, v[0], r >> 1), k1 = __shfl_sync(0xffffffffu, v[1], r >> 1);
             const uint64_t kr = (r & 1) ? k1 : k0;
             si[h] = (int)(uint32_t)kr;
-            a0[h] = a1[h] = 0.f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) a[h][d] = 0.f;
             if (r < nc) {
                 const int64_t o = base + si[h];
-                a0[h] = theta[2 * o];
-                a1[h] = theta[2 * o + 1];
+#pragma unroll
+                for (int d = 0; d < D; ++d) a[h][d] = theta[D * o + d];
             }
         }
         unsigned kept0 = 0u, kept1 = 0u;  // bit l: rank l (kept0) or l + 32 (kept1) kept
         for (int r = 0; r < nc; ++r) {
             const int h = r >> 5, l = r & 31;
-            const float b0 = __shfl_sync(0xffffffffu, h ? a0[1] : a0[0], l);
-            const float b1 = __shfl_sync(0xffffffffu, h ? a1[1] : a1[0], l);
-            const bool c0 = ((kept0 >> lane) & 1u) && abs_diff_lt(a0[0], b0, prm.c0) && abs_diff_lt(a1[0], b1, prm.c1);
-            const bool c1 = ((kept1 >> lane) & 1u) && abs_diff_lt(a0[1], b0, prm.c0) && abs_diff_lt(a1[1], b1, prm.c1);
+            float b[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) b[d] = __shfl_sync(0xffffffffu, h ? a[1][d] : a[0][d], l);
+            const bool c0 = ((kept0 >> lane) & 1u) && conflict<D>(a[0], b, prm);
+            const bool c1 = ((kept1 >> lane) & 1u) && conflict<D>(a[1], b, prm);
             if (!__any_sync(0xffffffffu, c0 || c1)) {
                 if (h) kept1 |= 1u << l;
                 else kept0 |= 1u << l;
@@ -205,17 +223,15 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
         // kept ranks in rank order
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int r = lane + 32 * h;
             if (!(((h ? kept1 : kept0) >> lane) & 1u)) continue;
             const int pos = (h ? __popc(kept0) : 0) + __popc((h ? kept1 : kept0) & ((1u << lane) - 1u));
             if (pos < prm.K) {
                 const int64_t o = (int64_t)e * prm.K + pos;
-                tracks[2 * o] = a0[h];
-                tracks[2 * o + 1] = a1[h];
+#pragma unroll
+                for (int d = 0; d < D; ++d) tracks[D * o + d] = a[h][d];
                 track_R[o] = R[base + si[h]];
                 if (track_src) track_src[o] = si[h];
             }
-            (void)r;
         }
         if (lane == 0) n_tracks[e] = __popc(kept0) + __popc(kept1);
         return;
@@ -229,18 +245,19 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     for (int r = tid; r < nc; r += EX_THREADS) {
         const int i = (int)(uint32_t)keys[r];
         const int64_t o = base + i;
-        th0[r] = theta[2 * o];
-        th1[r] = theta[2 * o + 1];
+#pragma unroll
+        for (int d = 0; d < D; ++d) th[d * cap + r] = theta[D * o + d];
         src[r] = i;
         state[r] = 0;
     }
     __syncthreads();
+    const float *thb0 = th + (D - 2) * cap, *thb1 = th + (D - 1) * cap;  // the bucketed coordinates
     // 3. buckets
     const uint64_t bmax = (1ull << BUCKET_BITS) - 1;
     for (int r = tid; r < C; r += EX_THREADS) {
         if (r < nc) {
-            uint64_t b0 = (uint64_t)fminf(fmaxf(floorf((th0[r] - prm.lo0) / prm.w0), 0.f), (float)bmax);
-            uint64_t b1 = (uint64_t)fminf(fmaxf(floorf((th1[r] - prm.lo1) / prm.w1), 0.f), (float)bmax);
+            uint64_t b0 = (uint64_t)fminf(fmaxf(floorf((thb0[r] - prm.lo0) / prm.w0), 0.f), (float)bmax);
+            uint64_t b1 = (uint64_t)fminf(fmaxf(floorf((thb1[r] - prm.lo1) / prm.w1), 0.f), (float)bmax);
             keys[r] = (b1 << (BUCKET_BITS + RANK_BITS)) | (b0 << RANK_BITS) | (uint64_t)r;
         } else {
             keys[r] = ~0ull;
@@ -253,9 +270,11 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
         bool undecided = false;
         for (int r = tid; r < nc; r += EX_THREADS) {
             if (state[r] != 0) continue;
-            const float a0 = th0[r], a1 = th1[r];
-            const int64_t b0 = (int64_t)fminf(fmaxf(floorf((a0 - prm.lo0) / prm.w0), 0.f), (float)bmax);
-            const int64_t b1 = (int64_t)fminf(fmaxf(floorf((a1 - prm.lo1) / prm.w1), 0.f), (float)bmax);
+            float ar[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) ar[d] = th[d * cap + r];
+            const int64_t b0 = (int64_t)fminf(fmaxf(floorf((ar[D - 2] - prm.lo0) / prm.w0), 0.f), (float)bmax);
+            const int64_t b1 = (int64_t)fminf(fmaxf(floorf((ar[D - 1] - prm.lo1) / prm.w1), 0.f), (float)bmax);
             bool rejected = false, blocked = false;
             for (int dy = -1; dy <= 1 && !rejected; ++dy) {
                 const int64_t row = b1 + dy;
@@ -272,7 +291,10 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
                 for (int q = q0; q < q1; ++q) {
                     const int rj = (int)(keys[q] & ((1ull << RANK_BITS) - 1));
                     if (rj >= r) continue;
-                    if (!(abs_diff_lt(a0, th0[rj], prm.c0) && abs_diff_lt(a1, th1[rj], prm.c1))) continue;
+                    float bj[D];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) bj[d] = th[d * cap + rj];
+                    if (!conflict<D>(ar, bj, prm)) continue;
                     const uint8_t sj = state[rj];
                     if (sj == 1) {
                         rejected = true;
@@ -309,8 +331,8 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
             const int pos = run + before + __popc(bal & ((1u << lane) - 1u));
             if (pos < prm.K) {
                 const int64_t o = (int64_t)e * prm.K + pos;
-                tracks[2 * o] = th0[r];
-                tracks[2 * o + 1] = th1[r];
+#pragma unroll
+                for (int d = 0; d < D; ++d) tracks[D * o + d] = th[d * cap + r];
                 track_R[o] = R[base + src[r]];
                 if (track_src) track_src[o] = src[r];
             }
@@ -322,41 +344,59 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
     if (tid == 0) n_tracks[e] = run;
 }
 
-size_t extract_smem_bytes(int n_points) {
+size_t extract_smem_bytes(int n_points, int dims) {
     int C = 1;
     while (C < n_points) C <<= 1;
-    return (size_t)C * (sizeof(uint64_t) + 2 * sizeof(float) + sizeof(int32_t) + 1) + 16;
+    return (size_t)C * (sizeof(uint64_t) + (size_t)dims * sizeof(float) + sizeof(int32_t) + 1) + 16;
 }
 
-cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
-                                  int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
-                                  float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
-                                  cudaStream_t st) {
-    {
-        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(extract_tracks_kernel),
-                                               extract_smem_bytes(n_points));
-        if (aerr != cudaSuccess) return aerr;
-    }
-    ExtractParams prm;
+// merge[d]: the merge distance of coordinate d; box on the last two.
+template <int D>
+static cudaError_t launch_extract_d(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                                    int n_events, int n_points, const retina_grid *box, float R0, const float *merge,
+                                    float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
+                                    cudaStream_t st) {
+    const size_t smem = extract_smem_bytes(n_points, D);
+    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(extract_tracks_kernel<D>), smem);
+    if (aerr != cudaSuccess) return aerr;
+    ExtractParams prm{};
     prm.lo0 = box->lo[0];
     prm.lo1 = box->lo[1];
     prm.hi0 = box->lo[0] + (float)box->n[0] * box->step[0];
     prm.hi1 = box->lo[1] + (float)box->n[1] * box->step[1];
-    prm.c0 = merge_cells * box->step[0];
-    prm.c1 = merge_cells * box->step[1];
-    prm.w0 = prm.c0 * 1.015625f;
-    prm.w1 = prm.c1 * 1.015625f;
+    for (int d = 0; d < D; ++d) prm.c[d] = merge[d];
+    prm.w0 = prm.c[D - 2] * 1.015625f;
+    prm.w1 = prm.c[D - 1] * 1.015625f;
     prm.R0 = R0;
     prm.n_points = n_points;
     prm.K = K;
     int C = 1;
     while (C < n_points) C <<= 1;
     prm.cap = C;
-    PrioLaunch L(dim3(n_events), dim3(EX_THREADS), extract_smem_bytes(n_points), st, true);
-    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel, theta, R, status, n_valid, prm, tracks,
-                                                track_R, track_src, n_tracks);
+    PrioLaunch L(dim3(n_events), dim3(EX_THREADS), smem, st, true);
+    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel<D>, theta, R, status, n_valid, prm,
+                                                tracks, track_R, track_src, n_tracks);
     count_launches(1);
     return lerr != cudaSuccess ? lerr : cudaGetLastError();
+}
+
+cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                                  int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
+                                  float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
+                                  cudaStream_t st) {
+    const float merge[2] = {merge_cells * box->step[0], merge_cells * box->step[1]};
+    return launch_extract_d<2>(theta, R, status, n_valid, n_events, n_points, box, R0, merge, tracks, track_R,
+                               track_src, n_tracks, K, st);
+}
+
+cudaError_t launch_extract_tracks4(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                                   int n_events, int n_points, const retina_grid *slope_box, const float unit[4],
+                                   float R0, float merge_units, float *tracks, float *track_R, int32_t *track_src,
+                                   int32_t *n_tracks, int K, cudaStream_t st) {
+    const float merge[4] = {merge_units * unit[0], merge_units * unit[1], merge_units * unit[2],
+                            merge_units * unit[3]};
+    return launch_extract_d<4>(theta, R, status, n_valid, n_events, n_points, slope_box, R0, merge, tracks, track_R,
+                               track_src, n_tracks, K, st);
 }
 
 }  // namespace retina

@@ -50,9 +50,12 @@ cudaError_t launch_refine_maxima(const float4 *hits, int64_t n_hits, const int64
                                  int ctas, cudaStream_t st);
 size_t batched_ws_bytes(int n_events);
 cudaError_t launch_local_search4(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events,
-                                 const float *seeds, int n_seeds, const retina_ls4_opts *o, float *theta_out,
-                                 float *R_out, uint8_t *status, int smem_hits, cudaStream_t st);
+                                 const float *seeds, int n_seeds, const int32_t *seed_count, const retina_ls4_opts *o,
+                                 float *theta_out, float *R_out, uint8_t *status, int smem_hits, cudaStream_t st);
 int64_t prepared_box_count(int64_t n_hits, int n_events);
+cudaError_t launch_pair_seeds4(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events,
+                               const float *layer_z, int n_pairs, float dz_tol, float d_max, float zc_lo, float zc_hi,
+                               float zref, float *seeds, int32_t *n_seeds, int K, cudaStream_t st);
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                                 float4 *sorted, float4 *boxes, cudaStream_t st);
 int maxima_blocks(const retina_grid *g);
@@ -67,7 +70,12 @@ int option_value(int option);
 cudaError_t launch_conv2_head_tc(const uint16_t *h1, int n_events, const float *params, uint16_t *h2, float *logits,
                                  int32_t *err, cudaStream_t st);
 void count_launches(int n);
-size_t extract_smem_bytes(int n_points);
+size_t extract_smem_bytes(int n_points, int dims);
+cudaError_t launch_extract_tracks4(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                                   int n_events,
+                                   int n_points, const retina_grid *slope_box, const float unit[4], float R0,
+                                   float merge_units, float *tracks, float *track_R, int32_t *track_src,
+                                   int32_t *n_tracks, int K, cudaStream_t st);
 
 // A launch configuration that carries the stream's priority as a launch
 // attribute, so that a CUDA graph captured from the stream keeps it on the

@@ -129,10 +129,19 @@ __device__ __forceinline__ void newton_cg4(const float g_in[4], const float H[4]
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 local_search4_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int n_seeds,
-                     const float *__restrict__ seeds, Ls4Params prm, int smem_hits, float *__restrict__ theta_out,
-                     float *__restrict__ R_out, uint8_t *__restrict__ status) {
+                     const int32_t *__restrict__ seed_count, const float *__restrict__ seeds, Ls4Params prm,
+                     int smem_hits, float *__restrict__ theta_out, float *__restrict__ R_out,
+                     uint8_t *__restrict__ status) {
     extern __shared__ float4 sh[];
     const int e = blockIdx.y;
+    // seeds [count, n_seeds) of the event are not searched; a CTA with none
+    // of its seeds below the count leaves before staging (uniformly)
+    int count = n_seeds;
+    if (seed_count) {
+        const int c = seed_count[e];
+        count = c < 0 ? 0 : (c < n_seeds ? c : n_seeds);
+    }
+    if (blockIdx.x * WARPS >= count) return;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
     const int H = (int)(he - hb);
@@ -142,7 +151,7 @@ local_search4_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int6
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (s >= n_seeds) return;  // after the only barrier
+    if (s >= count) return;  // after the only barrier
     const int64_t o = (int64_t)e * n_seeds + s;
     float th[4];
 #pragma unroll
@@ -238,8 +247,8 @@ local_search4_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int6
 }
 
 cudaError_t launch_local_search4(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events,
-                                 const float *seeds, int n_seeds, const retina_ls4_opts *o, float *theta_out,
-                                 float *R_out, uint8_t *status, int smem_hits, cudaStream_t st) {
+                                 const float *seeds, int n_seeds, const int32_t *seed_count, const retina_ls4_opts *o,
+                                 float *theta_out, float *R_out, uint8_t *status, int smem_hits, cudaStream_t st) {
     Ls4Params prm;
     prm.q = o->q;
     for (int j = 0; j < RETINA_MAX_Q; ++j) {
@@ -262,8 +271,8 @@ cudaError_t launch_local_search4(const float4 *hits, int64_t n_hits, const int64
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(local_search4_kernel<WARPS>), smem);
     if (aerr != cudaSuccess) return aerr;
     dim3 grid((n_seeds + WARPS - 1) / WARPS, n_events);
-    local_search4_kernel<WARPS><<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, n_seeds, seeds, prm, smem_hits,
-                                                              theta_out, R_out, status);
+    local_search4_kernel<WARPS><<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, n_seeds, seed_count, seeds, prm,
+                                                              smem_hits, theta_out, R_out, status);
     count_launches(1);
     return cudaGetLastError();
 }

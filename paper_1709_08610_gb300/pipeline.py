@@ -180,6 +180,54 @@ class GridScanBatch:
     results = BatchTracker.results
 
 
+class Search4Batch:
+    """Tracks with the four-parameter model (x0, y0, t_x, t_y) at z_ref over a
+    batch: starting points from hit pairs on given layer pairs
+    (retina_pair_seeds4), the four-parameter search from each
+    (retina_local_search4 with the per-event seed counts), cluster / select in
+    four dimensions (retina_extract_tracks4).  No host synchronisation
+    between the launches, so ``capture`` records the step as one CUDA graph."""
+
+    def __init__(self, n_events: int, hit_capacity: int, slope_box: "rt.Grid", opts: "rt.LsOpts4", R0: float,
+                 layer_pairs, dz_tol: float, d_max: float, zc_range, max_seeds: int = 2048,
+                 merge_units: float = 2.0, max_tracks: int = 1024, device="cuda"):
+        E, H = int(n_events), int(hit_capacity)
+        self.E, self.H, self.K, self.S = E, H, int(max_tracks), int(max_seeds)
+        self.box, self.opts, self.R0, self.merge = slope_box, opts, float(R0), float(merge_units)
+        self.pairs, self.cuts = list(layer_pairs), dict(dz_tol=dz_tol, d_max=d_max, zc_range=tuple(zc_range),
+                                                         zref=opts.zref)
+        dev = torch.device(device)
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.hits = torch.zeros((H, 4), **f32)
+        self.offsets = torch.zeros(E + 1, dtype=torch.int64, device=dev)
+        self.seeds = (torch.empty((E, self.S, 4), **f32), torch.empty((E,), dtype=torch.int32, device=dev))
+        self.search_out = (torch.empty((E, self.S, 4), **f32), torch.empty((E, self.S), **f32),
+                           torch.empty((E, self.S), dtype=torch.uint8, device=dev))
+        self.tracks = dict(tracks=torch.empty((E, self.K, 4), **f32), track_R=torch.empty((E, self.K), **f32),
+                           track_src=torch.empty((E, self.K), dtype=torch.int32, device=dev),
+                           n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    load = BatchTracker.load
+
+    def step(self, stream=None):
+        rt.pair_seeds4(self.hits, self.offsets, self.pairs, K=self.S, out=self.seeds, stream=stream, **self.cuts)
+        rt.local_search4(self.hits, self.offsets, self.seeds[0], self.opts, out=self.search_out, stream=stream,
+                         seed_count=self.seeds[1])
+        th, R, st = self.search_out
+        rt.extract_tracks4(th, R, st, self.box, self.opts.scale, self.R0, self.merge, self.K, n_valid=self.seeds[1],
+                           out=self.tracks, stream=stream)
+
+    capture = BatchTracker.capture
+    replay = BatchTracker.replay
+
+    def results(self):
+        """Per event: float64 [n_tracks, 4] track parameters (host)."""
+        n = self.tracks["n_tracks"].cpu().numpy()
+        tr = self.tracks["tracks"].cpu().numpy()
+        return [tr[e, :min(int(n[e]), self.K)].astype(np.float64) for e in range(self.E)]
+
+
 def match_efficiency(found, truth, eps: float = 1e-3):
     """Fraction of truth tracks with a found track within eps (max norm) and
     the number of found tracks matching none (fakes)."""

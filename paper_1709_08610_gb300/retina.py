@@ -148,6 +148,8 @@ def _load():
     L.retina_pipeline_create.argtypes = [P, P]
     L.retina_pipeline_run.argtypes = [P, P, I64, P, I32, P, P, P, P, P, P, P, P]
     L.retina_pipeline_destroy.argtypes = [P]
+    L.retina_pair_seeds4.argtypes = [P, I64, P, I32, P, I32, F, F, F, F, F, P, P, I32, P]
+    L.retina_extract_tracks4.argtypes = [P, P, P, P, I32, I32, P, P, F, F, P, P, P, P, I32, P]
     L.retina_tracker_create.argtypes = [P, P, P]
     L.retina_tracker_buffers.argtypes = [P, P, P, P, P, P, P]
     L.retina_tracker_step.argtypes = [P, I32, P]
@@ -166,7 +168,7 @@ def _load():
     L.retina_response.argtypes = [P, I64, P, I32, I32, P, I32, F, I32, P, P]
     L.retina_local_search.argtypes = [P, I64, P, P, I32, I32, P, I32, P, P, P, P, P, P, P]
     L.retina_refine_maxima_workspace_size.argtypes = [I32, P]
-    L.retina_local_search4.argtypes = [P, I64, P, I32, P, I32, P, P, P, P, P]
+    L.retina_local_search4.argtypes = [P, I64, P, I32, P, I32, P, P, P, P, P, P]
     L.retina_refine_maxima.argtypes = [P, I64, P, P, I32, I32, P, P, I32, P, P, P, P, P, P, SZ, P]
     L.retina_extract_tracks.argtypes = [P, P, P, P, I32, I32, P, F, F, P, P, P, P, I32, P]
     L.retina_grid_response_workspace_size.argtypes = [I32, I32, P, I32, P]
@@ -197,7 +199,7 @@ def _load():
                  "retina_local_search", "retina_extract_tracks", "retina_slope_histogram",
                  "retina_seednet_forward", "retina_seednet_train_workspace_size", "retina_seednet_train_step",
                  "retina_seednet_adam", "retina_topk_seeds", "retina_device_error",
-                 "retina_sort_seeds"):
+                 "retina_sort_seeds", "retina_pair_seeds4", "retina_extract_tracks4"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -438,9 +440,11 @@ def refine_maxima(hits: torch.Tensor, offsets: torch.Tensor, model: int, theta_c
 
 
 def local_search4(hits: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor, opts: LsOpts4, out=None,
-                  stream=None) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+                  stream=None, seed_count: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, torch.Tensor,
+                                                                                   torch.Tensor]:
     """Algorithm 1 for four-parameter tracks: seeds [E, n, 4] ->
-    (theta [E, n, 4], R [E, n], status [E, n] uint8)."""
+    (theta [E, n, 4], R [E, n], status [E, n] uint8); with seed_count [E]
+    int32 only each event's first seed_count[e] seeds are searched."""
     _dev(hits, torch.float32, "hits", 4)
     _dev(offsets, torch.int64, "offsets")
     _dev(seeds, torch.float32, "seeds", 4)
@@ -455,7 +459,48 @@ def local_search4(hits: torch.Tensor, offsets: torch.Tensor, seeds: torch.Tensor
                torch.empty((E, n), dtype=torch.uint8, device=dev))
     o = opts.c()
     _check("retina_local_search4", lib.retina_local_search4(
-        _p(hits), hits.shape[0], _p(offsets), E, _p(seeds), n, ctypes.byref(o), _p(out[0]), _p(out[1]), _p(out[2]),
+        _p(hits), hits.shape[0], _p(offsets), E, _p(seeds), n, _p(seed_count), ctypes.byref(o), _p(out[0]),
+        _p(out[1]), _p(out[2]), _stream(stream)))
+    return out
+
+
+def pair_seeds4(hits: torch.Tensor, offsets: torch.Tensor, layer_pairs, dz_tol: float, d_max: float, zc_range,
+                zref: float, K: int, out=None, stream=None):
+    """Starting points of the four-parameter search from hit pairs on the
+    layer pairs [(z_a, z_b), ...] (retina_pair_seeds4); returns (seeds
+    [E, K, 4], n_seeds [E] int32: pairs kept, may exceed K; -1 when a layer
+    overflowed)."""
+    _dev(hits, torch.float32, "hits", 4)
+    _dev(offsets, torch.int64, "offsets")
+    E = offsets.numel() - 1
+    lz = np.ascontiguousarray(np.asarray(layer_pairs, dtype=np.float32).reshape(-1, 2))
+    if out is None:
+        out = (torch.empty((E, K, 4), dtype=torch.float32, device=hits.device),
+               torch.empty((E,), dtype=torch.int32, device=hits.device))
+    _check("retina_pair_seeds4", lib.retina_pair_seeds4(
+        _p(hits), hits.shape[0], _p(offsets), E, lz.ctypes.data_as(ctypes.c_void_p), lz.shape[0], float(dz_tol),
+        float(d_max), float(zc_range[0]), float(zc_range[1]), float(zref), _p(out[0]), _p(out[1]), int(K),
+        _stream(stream)))
+    return out
+
+
+def extract_tracks4(theta: torch.Tensor, R: torch.Tensor, status: Optional[torch.Tensor], slope_box: Grid, unit,
+                    R0: float, merge_units: float, K: int, n_valid: Optional[torch.Tensor] = None, out=None,
+                    stream=None) -> dict:
+    """Cluster / select of four-parameter points [E, n, 4] (retina_extract_tracks4)."""
+    _dev(theta, torch.float32, "theta", 4)
+    E, n = theta.shape[0], theta.shape[1]
+    dev = theta.device
+    if out is None:
+        out = dict(tracks=torch.empty((E, K, 4), dtype=torch.float32, device=dev),
+                   track_R=torch.empty((E, K), dtype=torch.float32, device=dev),
+                   track_src=torch.empty((E, K), dtype=torch.int32, device=dev),
+                   n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
+    u = np.ascontiguousarray(np.asarray(unit, dtype=np.float32).reshape(4))
+    g = slope_box.c()
+    _check("retina_extract_tracks4", lib.retina_extract_tracks4(
+        _p(theta), _p(R), _p(status), _p(n_valid), E, n, ctypes.byref(g), u.ctypes.data_as(ctypes.c_void_p), float(R0),
+        float(merge_units), _p(out["tracks"]), _p(out["track_R"]), _p(out["track_src"]), _p(out["n_tracks"]), int(K),
         _stream(stream)))
     return out
 

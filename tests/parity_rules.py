@@ -84,7 +84,7 @@ def compare_track_sets(pos_o, R_o, cand_o, pos_g, R_g, cand_g, tie, kept_o, kept
     """Found-track sets of the CUDA path and the oracle, equal up to near-ties.
 
     Items are the starting points of the extraction (search seeds, or grid
-    cells), indexed alike on both sides: end points pos_* [n, 2] (NaN where a
+    cells), indexed alike on both sides: end points pos_* [n, D] (NaN where a
     side has none), responses R_* [n], candidate masks cand_* [n] (what each
     side's cluster/select step considered), ``tie`` [n] the items whose own
     outcome is a near-tie (an oracle decision within tolerance of its
@@ -104,8 +104,9 @@ def compare_track_sets(pos_o, R_o, cand_o, pos_g, R_g, cand_g, tie, kept_o, kept
     must be the same on both sides within the tolerance.  Returns
     (components, tied components, oracle tracks compared)."""
     n = len(R_o)
+    dim = pos_o.shape[1]
     step = np.asarray(step, dtype=np.float64)
-    tol = np.broadcast_to(np.asarray(tol, dtype=np.float64), (n, 2))
+    tol = np.broadcast_to(np.asarray(tol, dtype=np.float64), (n, dim))
     tolR = lambda r: R_REL * np.abs(r) + R_ABS
     items = np.flatnonzero(cand_o | cand_g)
     if len(items) == 0:
@@ -161,10 +162,10 @@ def compare_track_sets(pos_o, R_o, cand_o, pos_g, R_g, cand_g, tie, kept_o, kept
     # kept items outside every candidate set cannot happen
     assert all(int(i) in where for i in kept_o) and all(int(i) in where for i in kept_g)
     # each side's kept positions in untied components have a partner on the other side
-    A = pos_o[np.asarray(ko, dtype=np.int64)].reshape(-1, 2)
-    B = pos_g[np.asarray(kg, dtype=np.int64)].reshape(-1, 2)
-    ta = tol[np.asarray(ko, dtype=np.int64)].reshape(-1, 2)
-    tb = tol[np.asarray(kg, dtype=np.int64)].reshape(-1, 2)
+    A = pos_o[np.asarray(ko, dtype=np.int64)].reshape(-1, dim)
+    B = pos_g[np.asarray(kg, dtype=np.int64)].reshape(-1, dim)
+    ta = tol[np.asarray(ko, dtype=np.int64)].reshape(-1, dim)
+    tb = tol[np.asarray(kg, dtype=np.int64)].reshape(-1, dim)
     assert len(A) == len(B), ("kept counts differ in untied components", len(A), len(B))
     if len(A):
         dA = np.abs(A[:, None] - B[None])

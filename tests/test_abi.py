@@ -208,17 +208,41 @@ def test_local_search4_rejects(mut):
         o.zref = float("inf")
     elif mut == "events":
         E = 65536
-    assert L.retina_local_search4(BOGUS, 10, BOGUS, E, BOGUS, 16, ctypes.byref(o), BOGUS, BOGUS, BOGUS,
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, E, BOGUS, 16, None, ctypes.byref(o), BOGUS, BOGUS, BOGUS,
                                   None) == EINVAL
 
 
 def test_local_search4_null_outputs_and_empty():
     o = rt.LsOpts4().c()
-    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, BOGUS, 16, ctypes.byref(o), None, BOGUS, BOGUS,
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, BOGUS, 16, None, ctypes.byref(o), None, BOGUS, BOGUS,
                                   None) == EINVAL
-    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, BOGUS, 16, None, BOGUS, BOGUS, BOGUS, None) == EINVAL
-    assert L.retina_local_search4(None, 0, None, 0, None, 16, ctypes.byref(o), None, None, None, None) == 0
-    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, None, 0, ctypes.byref(o), None, None, None, None) == 0
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, BOGUS, 16, None, None, BOGUS, BOGUS, BOGUS, None) == EINVAL
+    assert L.retina_local_search4(None, 0, None, 0, None, 16, None, ctypes.byref(o), None, None, None, None) == 0
+    assert L.retina_local_search4(BOGUS, 10, BOGUS, 1, None, 0, None, ctypes.byref(o), None, None, None, None) == 0
+
+
+def test_pair_seeds4_and_extract4_reject_bad_arguments():
+    lz = (ctypes.c_float * 2)(500.0, 700.0)
+    ok = dict(dz=0.5, dmax=0.3, zlo=-250.0, zhi=250.0, zref=225.0)
+
+    def ps(n_pairs=1, K=16, E=1, layer=lz, **kw):
+        a = dict(ok, **kw)
+        return L.retina_pair_seeds4(BOGUS, 10, BOGUS, E, layer, n_pairs, a["dz"], a["dmax"], a["zlo"], a["zhi"],
+                                    a["zref"], BOGUS, BOGUS, K, None)
+    assert ps(n_pairs=0) == EINVAL and ps(n_pairs=9) == EINVAL and ps(K=0) == EINVAL and ps(E=-1) == EINVAL
+    assert ps(dmax=-1.0) == EINVAL and ps(dz=float("nan")) == EINVAL and ps(zhi=float("inf")) == EINVAL
+    assert ps(layer=None) == EINVAL and ps(layer=(ctypes.c_float * 2)(float("nan"), 1.0)) == EINVAL
+    assert L.retina_pair_seeds4(BOGUS, 10, None, 1, lz, 1, 0.5, 0.3, -1.0, 1.0, 0.0, BOGUS, BOGUS, 16, None) == EINVAL
+    assert L.retina_pair_seeds4(None, 0, None, 0, lz, 1, 0.5, 0.3, -1.0, 1.0, 0.0, None, None, 16, None) == 0
+    g = rt.Grid((-0.5, -0.5), (2 ** -10, 2 ** -10), (1024, 1024)).c()
+    u = (ctypes.c_float * 4)(0.25, 0.25, 2 ** -10, 2 ** -10)
+    bad_u = (ctypes.c_float * 4)(0.25, 0.0, 2 ** -10, 2 ** -10)
+
+    def ex(n_points=100, K=8, units=u, merge=2.0, grid=g):
+        return L.retina_extract_tracks4(BOGUS, BOGUS, None, None, 1, n_points, ctypes.byref(grid) if grid else None,
+                                        units, 5.0, merge, BOGUS, BOGUS, None, BOGUS, K, None)
+    assert ex(units=bad_u) == EINVAL and ex(merge=0.0) == EINVAL and ex(K=0) == EINVAL and ex(grid=None) == EINVAL
+    assert ex(n_points=4097) == ENOSPACE
 
 
 def test_extract_tracks_rejects():

@@ -113,3 +113,169 @@ def test_search4_edge_cases(rt):
     torch.cuda.synchronize()
     assert np.all(np.isfinite(R.cpu().numpy()))
 
+
+
+# --------------------------------------------------------------------------
+# hit-pair starting points, four-parameter cluster / select, the whole method
+# --------------------------------------------------------------------------
+
+from parity_rules import R_ABS, R_REL, compare_track_sets  # noqa: E402
+from synth import VELO_PLANES_Z, batch_of  # noqa: E402
+
+Z = np.asarray(VELO_PLANES_Z)
+PAIRS = [(Z[17], Z[25]), (Z[18], Z[24]), (Z[19], Z[23])]
+PAIR_CUTS = dict(dz_tol=0.5, d_max=0.3, zc_range=(-250.0, 250.0), zref=ZREF)
+SIGMA3 = (0.3, 0.175, 0.05)
+
+
+def _truth4(ev):
+    t, v = ev.truth[:, :2], ev.truth[:, 2:5]
+    return np.stack([v[:, 0] + t[:, 0] * (ZREF - v[:, 2]), v[:, 1] + t[:, 1] * (ZREF - v[:, 2]), t[:, 0], t[:, 1]],
+                    1)
+
+
+def test_pair_seeds_are_the_oracle_seeds_bit_for_bit(rt):
+    evs = [make_event(WORKLOADS["velo"], 31, e) for e in range(4)]
+    evs += [make_event(WORKLOADS["velo_stress"], 31, e) for e in range(2)]
+    b = batch_of(evs)
+    K = 8192
+    seeds, n = rt.pair_seeds4(torch.from_numpy(b.hits).cuda(), torch.from_numpy(b.offsets).cuda(), PAIRS,
+                              K=K, **PAIR_CUTS)
+    seeds, n = seeds.cpu().numpy(), n.cpu().numpy()
+    for e, ev in enumerate(evs):
+        s_o, c_o = oracle.pair_seeds4(ev.hits, PAIRS, PAIR_CUTS["dz_tol"], PAIR_CUTS["d_max"], PAIR_CUTS["zc_range"],
+                                      ZREF)
+        assert n[e] == c_o > 100
+        assert np.array_equal(seeds[e, :min(c_o, K)], s_o[:K])
+    # truncation at K keeps the first K in order; the count is not clamped
+    s2, n2 = rt.pair_seeds4(torch.from_numpy(b.hits).cuda(), torch.from_numpy(b.offsets).cuda(), PAIRS, K=16,
+                            **PAIR_CUTS)
+    assert np.array_equal(n2.cpu().numpy(), n) and np.array_equal(s2.cpu().numpy(), seeds[:, :16])
+
+
+def test_extract4_is_the_oracle_selection_on_identical_points(rt):
+    # the oracle's own search end points (as float32) through both selections
+    evs = [make_event(WORKLOADS["velo"], 31, e) for e in range(3)]
+    wl = WORKLOADS["velo"]
+    th_all, R_all, st_all = [], [], []
+    n_max = 0
+    for ev in evs:
+        s, _ = oracle.pair_seeds4(ev.hits, PAIRS, PAIR_CUTS["dz_tol"], PAIR_CUTS["d_max"], PAIR_CUTS["zc_range"],
+                                  ZREF)
+        th, R, st, _ = oracle.local_search4(ev.hits, s, SIGMA3, SCALE, zref=ZREF)
+        th_all.append(th.astype(np.float32))
+        R_all.append(R.astype(np.float32))
+        st_all.append(st)
+        n_max = max(n_max, len(s))
+    E = len(evs)
+    TH = np.full((E, n_max, 4), np.nan, np.float32)
+    RR = np.zeros((E, n_max), np.float32)
+    ST = np.full((E, n_max), 3, np.uint8)
+    for e in range(E):
+        m = len(R_all[e])
+        TH[e, :m], RR[e, :m], ST[e, :m] = th_all[e], R_all[e], st_all[e]
+    R0 = float(np.float32(wl.R0))
+    out = rt.extract_tracks4(torch.from_numpy(TH).cuda(), torch.from_numpy(RR).cuda(), torch.from_numpy(ST).cuda(),
+                             rt.Grid.of(wl), SCALE, R0, 2.0, 1024)
+    for e in range(E):
+        keep = oracle.extract_tracks4(TH[e], RR[e], ST[e], wl.grid_lo, wl.grid_step, wl.grid_n, SCALE, R0, 2.0)
+        n = int(out["n_tracks"][e])
+        assert n == len(keep) > 100
+        assert out["track_src"][e, :n].cpu().numpy().tolist() == keep.tolist()
+        assert np.array_equal(out["tracks"][e, :n].cpu().numpy(), TH[e][keep])
+
+
+def test_extract4_exact_on_random_clusters_with_ties(rt):
+    # dense clusters on a lattice (exact merge-distance cases), equal R, all statuses
+    rng = np.random.default_rng(12)
+    E, P = 4, 1500
+    u = np.asarray(SCALE)
+    centres = np.concatenate([rng.uniform(-20, 20, (E, 50, 2)), rng.uniform(-0.2, 0.2, (E, 50, 2))], 2)
+    th = centres[np.arange(E)[:, None], rng.integers(0, 50, (E, P))] + rng.normal(0, 1.5, (E, P, 4)) * u
+    th = (np.round(th / (u / 8)) * (u / 8)).astype(np.float32)
+    R = rng.integers(0, 20, (E, P)).astype(np.float32)
+    st = rng.integers(0, 4, (E, P)).astype(np.uint8)
+    R[1, :1450] = 0.0  # few candidates: the one-warp path
+    box = rt.Grid((-0.5, -0.5), (2.0 ** -10, 2.0 ** -10), (1024, 1024))
+    for K in (2000, 7):
+        out = rt.extract_tracks4(torch.from_numpy(th).cuda(), torch.from_numpy(R).cuda(), torch.from_numpy(st).cuda(),
+                                 box, SCALE, 4.0, 2.0, K)
+        for e in range(E):
+            keep = oracle.extract_tracks4(th[e], R[e], st[e], box.lo, box.step, box.n, SCALE, 4.0, 2.0)
+            n = int(out["n_tracks"][e])
+            assert n == len(keep)
+            k = min(K, n)
+            assert out["track_src"][e, :k].cpu().numpy().tolist() == keep[:k].tolist()
+
+
+def test_four_parameter_method_finds_the_smeared_vertex_tracks(rt):
+    # hit-pair seeds -> four-parameter search -> cluster / select, on smeared-vertex
+    # VELO-like events: found-track sets equal to the oracle's up to near-ties, and
+    # MC efficiency (|dx0|, |dy0| <= 0.1 mm, |dt| <= 1e-3) above 97 % (the slope
+    # model finds none of these tracks)
+    wl = WORKLOADS["velo"]
+    evs = [make_event(wl, 31, e) for e in range(4)]
+    b = batch_of(evs)
+    hits, offs = torch.from_numpy(b.hits).cuda(), torch.from_numpy(b.offsets).cuda()
+    K = 2048
+    seeds, n_s_d = rt.pair_seeds4(hits, offs, PAIRS, K=K, **PAIR_CUTS)
+    th_g, R_g, st_g = rt.local_search4(hits, offs, seeds, rt.LsOpts4(sigma=SIGMA3, scale=SCALE, zref=ZREF),
+                                       seed_count=n_s_d)
+    R0 = float(np.float32(wl.R0))
+    tr = rt.extract_tracks4(th_g, R_g, st_g, rt.Grid.of(wl), SCALE, R0, 2.0, 1024, n_valid=n_s_d)
+    n_s = n_s_d.cpu().numpy()
+    assert 0 < n_s.max() <= K
+    found = total = 0
+    for e, ev in enumerate(evs):
+        m = int(n_s[e])
+        s_o, _ = oracle.pair_seeds4(ev.hits, PAIRS, PAIR_CUTS["dz_tol"], PAIR_CUTS["d_max"], PAIR_CUTS["zc_range"],
+                                    ZREF)
+
+        def run(pt):
+            return oracle.local_search4(ev.hits, s_o, SIGMA3, SCALE, zref=ZREF, perturb=pt)
+
+        th_o, R_o, st_o, m_o = base = run(None)
+        keep_o = oracle.extract_tracks4(th_o, R_o, st_o, wl.grid_lo, wl.grid_step, wl.grid_n, SCALE, R0, 2.0)
+        tg = th_g[e, :m].cpu().numpy().astype(np.float64)
+        Rg = R_g[e, :m].cpu().numpy().astype(np.float64)
+        sg = st_g[e, :m].cpu().numpy()
+        nt = int(tr["n_tracks"][e])
+        src = tr["track_src"][e, :nt].cpu().numpy()
+
+        def cand(th, R, st):
+            ok = (st <= 1) & np.isfinite(R) & np.all(np.isfinite(th), axis=1) & (R >= R0)
+            lo, hi = np.asarray(wl.grid_lo), np.asarray(wl.grid_lo) + np.asarray(wl.grid_n) * np.asarray(wl.grid_step)
+            return ok & np.all((th[:, 2:] >= lo) & (th[:, 2:] < hi), axis=1)
+
+        tol = np.tile(0.05 * np.asarray(SCALE), (m, 1))
+        conv_at = _converged_at_sigma(ev, SIGMA3[-1])
+        for i in np.flatnonzero(cand(th_o, R_o, st_o)):
+            c = conv_at(th_o[i])
+            if c is not None:
+                g, H, gabs = c
+                tol[i] = np.maximum(1e-3 * np.asarray(SCALE), np.abs(np.linalg.inv(H)) @ (1e-4 * gabs))
+        stable, _, _ = oracle.path_conditioning(run, base, tol, keys=oracle.PERTURB_KEYS[:8])
+        near0 = np.abs(R_o - R0) <= R_REL * np.abs(R_o) + R_ABS
+        compare_track_sets(th_o, R_o, cand(th_o, R_o, st_o) | (near0 & (st_o <= 1)), tg, Rg, cand(tg, Rg, sg),
+                           (m_o < 1.0) | ~stable, keep_o, src, tol, SCALE, 2.0, R0=R0)
+        T = _truth4(ev)
+        d = np.max(np.abs(tr["tracks"][e, :nt].cpu().numpy()[:, None, :].astype(np.float64) - T[None])
+                   / np.array([0.1, 0.1, 1e-3, 1e-3]), axis=2)
+        found += int((d.min(axis=0) <= 1).sum())
+        total += len(T)
+    assert found / total >= 0.97, found / total
+
+
+def _converged_at_sigma(ev, sigma):
+    def at(th):
+        o = oracle.rgh4(ev.hits, th, sigma, zref=ZREF)
+        H, g = o["hess"], o["grad"]
+        if not np.all(np.linalg.eigvalsh(H) < 0):
+            return None
+        try:
+            if np.max(np.abs(np.linalg.solve(H, g)) / np.asarray(SCALE)) > 0.05:
+                return None
+        except np.linalg.LinAlgError:
+            return None
+        return g, H, o["grad_abs"]
+    return at

@@ -160,3 +160,116 @@ def test_centred_reference_plane_decouples_and_converges():
         errs.append(np.max(np.abs(th[0] - [x0, y0, tx, ty]) / scale))
     assert all(b <= 0.7 * a for a, b in zip(errs[:6], errs[1:7]))
     assert errs[8] < 1e-4
+
+
+# --------------------------------------------------------------------------
+# starting points from hit pairs, and four-parameter cluster / select
+# --------------------------------------------------------------------------
+
+def _axis_event():
+    """Five noiseless tracks from points on the z axis, with well separated
+    azimuths, seen on two layers, plus three noise hits on them."""
+    za, zb = 500.0, 700.0
+    vz = np.array([-40.0, 0.0, 25.0, 60.0, -80.0])
+    phi = np.array([0.3, 1.5, 2.7, 3.9, 5.1])
+    tan = np.array([0.05, 0.08, 0.11, 0.03, 0.14])
+    t = np.stack([tan * np.cos(phi), tan * np.sin(phi)], 1)
+    hits = []
+    for z in (za, zb):
+        for k in range(5):
+            hits.append([t[k, 0] * (z - vz[k]), t[k, 1] * (z - vz[k]), z, 0.0])
+    hits += [[30.0, -20.0, za, 0.0], [-45.0, 10.0, zb, 0.0], [5.0, 55.0, zb, 0.0]]
+    return np.asarray(hits, np.float32), t, vz, (za, zb)
+
+
+def _axis_distance_by_sampling(hi, hj):
+    """Closest transverse distance of the line through two hits to the z axis
+    and its z, by sampling the line densely (independent of a closed form)."""
+    s = np.linspace(-20.0, 20.0, 400001)
+    p = hi[None, :3] + s[:, None] * (hj[:3] - hi[:3])[None, :]
+    d = np.hypot(p[:, 0], p[:, 1])
+    k = int(np.argmin(d))
+    return d[k], p[k, 2]
+
+
+def test_pair_seeds_keep_exactly_the_lines_through_the_axis():
+    hits, t, vz, (za, zb) = _axis_event()
+    zref = 225.0
+    seeds, cnt = oracle.pair_seeds4(hits, [(za, zb)], 0.5, 0.3, (-250.0, 250.0), zref)
+    # brute force over all pairs in order: kept iff the sampled line passes within
+    # d_max of the axis at -250 <= z <= 250 (no pair lies near either cut)
+    expect = []
+    for i in np.flatnonzero(hits[:, 2] == za):
+        for j in np.flatnonzero(hits[:, 2] == zb):
+            d, zc = _axis_distance_by_sampling(hits[i].astype(np.float64), hits[j].astype(np.float64))
+            assert abs(d - 0.3) > 0.05 and abs(abs(zc) - 250.0) > 5.0
+            if d <= 0.3 and -250.0 <= zc <= 250.0:
+                expect.append((i, j))
+    assert cnt == len(expect) == 5
+    # each kept line is a track: (x0, y0) = t (zref - vz) at zref, slopes t
+    truth = np.concatenate([t * (zref - vz)[:, None], t], 1)
+    for (i, j), s in zip(expect, seeds):
+        k = i  # the k-th track's hit on the first layer is hit k
+        np.testing.assert_allclose(s, truth[k], rtol=1e-5, atol=1e-4)
+
+
+def test_pair_seeds_cuts_and_order():
+    hits, t, vz, (za, zb) = _axis_event()
+    # no z window: nothing; a layer pair listed twice: the same seeds twice, in order
+    s0, c0 = oracle.pair_seeds4(hits, [(za, zb)], 0.5, 0.3, (-1.0, 1.0), 225.0)
+    assert c0 == 1  # only the track from vz = 0 comes closest inside |z| <= 1
+    s1, c1 = oracle.pair_seeds4(hits, [(za, zb), (za, zb)], 0.5, 0.3, (-250.0, 250.0), 225.0)
+    s2, c2 = oracle.pair_seeds4(hits, [(za, zb)], 0.5, 0.3, (-250.0, 250.0), 225.0)
+    assert c1 == 2 * c2 and np.array_equal(s1[:c2], s2) and np.array_equal(s1[c2:], s2)
+    # a wider distance cut keeps a superset; the layer tolerance selects the layers
+    _, c3 = oracle.pair_seeds4(hits, [(za, zb)], 0.5, 50.0, (-1e4, 1e4), 225.0)
+    assert c3 > c2
+    _, c4 = oracle.pair_seeds4(hits, [(za + 10.0, zb)], 0.5, 0.3, (-250.0, 250.0), 225.0)
+    assert c4 == 0
+    # capacity: the count is not clamped
+    s5, c5 = oracle.pair_seeds4(hits, [(za, zb)], 0.5, 0.3, (-250.0, 250.0), 225.0, cap=2)
+    assert c5 == 5 and len(s5) == 2 and np.array_equal(s5, s2[:2])
+
+
+UNITS4 = (0.25, 0.25, 2.0 ** -10, 2.0 ** -10)
+
+
+def test_extract4_reduces_to_the_slope_extraction_when_offsets_agree():
+    # equal offsets: a conflict is decided by the slopes alone, as in the
+    # (pinned) two-parameter extraction on a grid of the same steps
+    rng = np.random.default_rng(3)
+    n = 600
+    sl = rng.uniform(-0.05, 0.05, (n, 2))
+    sl = np.round(sl / 2 ** -12) * 2 ** -12
+    R = rng.integers(5, 40, n).astype(np.float64)
+    st = rng.integers(0, 3, n).astype(np.uint8)
+    th4 = np.concatenate([np.full((n, 2), 7.5), sl], 1)
+    lo, step, nn = (-0.5, -0.5), (2.0 ** -10, 2.0 ** -10), (1024, 1024)
+    k4 = oracle.extract_tracks4(th4, R, st, lo, step, nn, UNITS4, 10.0, 2.0)
+    k2 = oracle.extract_tracks(sl, R, st, lo, step, nn, 10.0, 2.0)
+    assert len(k4) > 20 and k4.tolist() == k2.tolist()
+
+
+def test_extract4_invariants_and_offsets_separate_tracks():
+    rng = np.random.default_rng(4)
+    n = 800
+    centres = np.concatenate([rng.uniform(-20, 20, (40, 2)), rng.uniform(-0.1, 0.1, (40, 2))], 1)
+    th = centres[rng.integers(0, 40, n)] + rng.normal(0, 1, (n, 4)) * np.array([0.3, 0.3, 1e-3, 1e-3])
+    R = rng.uniform(0, 30, n)
+    lo, step, nn = (-0.5, -0.5), (2.0 ** -10, 2.0 ** -10), (1024, 1024)
+    keep = oracle.extract_tracks4(th, R, None, lo, step, nn, UNITS4, 5.0, 2.0)
+    u = np.asarray(UNITS4)
+    cand = np.flatnonzero(R >= 5.0)
+    kept = th[keep]
+    # no two kept points conflict; every rejected candidate conflicts with a kept one of >= R
+    d = np.max(np.abs(kept[:, None] - kept[None]) / u, axis=2)
+    np.fill_diagonal(d, np.inf)
+    assert np.all(d >= 2.0)
+    for i in set(cand.tolist()) - set(keep.tolist()):
+        dd = np.max(np.abs(kept - th[i]) / u, axis=1)
+        assert np.any((dd < 2.0) & (R[keep] >= R[i]))
+    # two points with the same slopes but offsets 1 mm apart are two tracks
+    two = np.array([[0.0, 0.0, 0.01, 0.02], [1.0, 0.0, 0.01, 0.02]])
+    assert len(oracle.extract_tracks4(two, [9.0, 8.0], None, lo, step, nn, UNITS4, 5.0, 2.0)) == 2
+    assert len(oracle.extract_tracks4(two * [1, 1, 1, 1] + [[0, 0, 0, 0], [-0.6, 0, 0, 0]], [9.0, 8.0], None, lo,
+                                      step, nn, UNITS4, 5.0, 2.0)) == 1
