@@ -31,6 +31,7 @@ struct BatchArgs {
     const int64_t *seed_off;
     const int32_t *order;
     int smem_hits;
+    int box_cap;  // block boxes staged per event (a multiple of 4)
     int64_t max_rounds;
     float *theta_out;
     float *R_out;
@@ -73,10 +74,10 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
     pdl_release();  // the track extraction may be scheduled once every CTA has started
     const int tid = threadIdx.x, lane = tid & 31;
     float4 *sbox = staged_box_bounds(sh, a.smem_hits);
-    float *sz2 = staged_box_z2(sh, a.smem_hits);
-    float4 *ssb = staged_super_bounds(sh, a.smem_hits);
-    float *ssz2 = staged_super_z2(sh, a.smem_hits);
-    int *list = kept_list(sh, a.smem_hits, tid >> 5);
+    float *sz2 = staged_box_z2(sh, a.smem_hits, a.box_cap);
+    float4 *ssb = staged_super_bounds(sh, a.smem_hits, a.box_cap);
+    float *ssz2 = staged_super_z2(sh, a.smem_hits, a.box_cap);
+    int *list = kept_list(sh, a.smem_hits, a.box_cap, tid >> 5);
     int staged = -1;
     int n_staged = 0, n_sbox = 0;
     for (int64_t round = 0; round < a.max_rounds; ++round) {
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
         if (e != staged) {
             n_staged = H < a.smem_hits ? H : a.smem_hits;
             for (int k = tid; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
-            const int nblk = (H + 31) >> 5, cap = box_capacity(a.smem_hits);
+            const int nblk = (H + 31) >> 5, cap = a.box_cap;
             n_sbox = gbox ? (nblk < cap ? nblk : cap) : 0;
             stage_boxes<MODEL>(gbox, n_sbox, sbox, sz2, ssb, ssz2, tid, blockDim.x);
             staged = e;
@@ -143,9 +144,21 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
 size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(int32_t) + 255) / 256 * 256; }
 
 template <int MODEL, int P, int WARPS, int UPD>
-static cudaError_t launch_batched_t(const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
+static cudaError_t launch_batched_t(BatchArgs a, const LsParams &prm, int ctas, cudaStream_t st) {
     auto kern = batched_search_kernel<MODEL, P, WARPS, UPD>;
-    const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS);
+    // boxes take the shared memory the hits and the warps' lists leave (at
+    // least the staged hits' blocks, at most 4096 blocks = 131072 hits)
+    a.box_cap = default_box_cap(a.smem_hits);
+    if (a.boxes) {
+        const size_t avail = (size_t)max_dynamic_smem() - 1024;  // static shared memory and a margin
+        const size_t fixed = (size_t)a.smem_hits * 16 + search_list_bytes(WARPS);
+        if (avail > fixed) {
+            int cap = (int)((avail - fixed) / 25) & ~3;  // 20 B per block box + 5 B of its superblock's
+            cap = cap > 4096 ? 4096 : cap;
+            if (cap > a.box_cap) a.box_cap = cap;
+        }
+    }
+    const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS, a.box_cap);
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (aerr != cudaSuccess) return aerr;
     int per_sm = 0;
@@ -206,7 +219,7 @@ cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int6
                                   const retina_ls_opts *o, const retina_grid *box, float *theta_out, float *R_out,
                                   uint8_t *status, uint8_t *n_evals, int32_t *counters, int seeds_per_warp, int warps,
                                   int smem_hits, int ctas, cudaStream_t st) {
-    BatchArgs a{hits, n_hits, hit_off, boxes, n_events, seeds, n_seeds, seed_off, order, smem_hits, 0,
+    BatchArgs a{hits, n_hits, hit_off, boxes, n_events, seeds, n_seeds, seed_off, order, smem_hits, 0, 0,
                 theta_out, R_out, status, n_evals, counters, nullptr, nullptr, 0};
     return launch_batched(a, model, o, box, seeds_per_warp, warps, ctas, st);
 }
@@ -217,7 +230,7 @@ cudaError_t launch_refine_maxima(const float4 *hits, int64_t n_hits, const int64
                                  uint8_t *status, int32_t *counters, int seeds_per_warp, int warps, int smem_hits,
                                  int ctas, cudaStream_t st) {
     BatchArgs a{hits, n_hits, hit_off, boxes, n_events, theta_c, (int64_t)n_events * K, nullptr, nullptr, smem_hits,
-                0, theta_out, R_out, status, nullptr, counters, nullptr, n_max, (int64_t)K};
+                0, 0, theta_out, R_out, status, nullptr, counters, nullptr, n_max, (int64_t)K};
     return launch_batched(a, model, o, box, seeds_per_warp, warps, ctas, st);
 }
 

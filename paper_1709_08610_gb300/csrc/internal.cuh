@@ -62,6 +62,7 @@ int maxima_blocks(const retina_grid *g);
 cudaError_t launch_sort_seeds(const float *seeds, int64_t n_seeds, const int64_t *off, int n_events,
                               const retina_grid *box, float *out, int32_t *perm, cudaStream_t st);
 int sm_count();
+int max_dynamic_smem();
 cudaError_t ensure_dynamic_smem(const void *func, size_t bytes);
 unsigned long long *work_counters();
 int32_t *device_error_flag();

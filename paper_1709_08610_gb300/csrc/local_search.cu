@@ -23,11 +23,12 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     const int n_staged = H < smem_hits ? H : smem_hits;
     for (int k = threadIdx.x; k < n_staged; k += blockDim.x) sh[k] = __ldg(gh + k);
     float4 *sbox = staged_box_bounds(sh, smem_hits);
-    float *sz2 = staged_box_z2(sh, smem_hits);
-    float4 *ssb = staged_super_bounds(sh, smem_hits);
-    float *ssz2 = staged_super_z2(sh, smem_hits);
+    const int box_cap = default_box_cap(smem_hits);
+    float *sz2 = staged_box_z2(sh, smem_hits, box_cap);
+    float4 *ssb = staged_super_bounds(sh, smem_hits, box_cap);
+    float *ssz2 = staged_super_z2(sh, smem_hits, box_cap);
     const float4 *gbox = boxes ? boxes + 2 * (hb / 32 + e) : nullptr;
-    const int n_sbox = gbox ? (((H + 31) >> 5) < box_capacity(smem_hits) ? ((H + 31) >> 5) : box_capacity(smem_hits)) : 0;
+    const int n_sbox = gbox ? (((H + 31) >> 5) < box_cap ? ((H + 31) >> 5) : box_cap) : 0;
     stage_boxes<MODEL>(gbox, n_sbox, sbox, sz2, ssb, ssz2, threadIdx.x, blockDim.x);
     __syncthreads();
 
@@ -36,7 +37,7 @@ local_search_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
     if (s_first >= n_seeds) return;
     const int n_live = n_seeds - s_first < P ? n_seeds - s_first : P;
     const int64_t o = (int64_t)e * n_seeds + s_first;
-    search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, kept_list(sh, smem_hits, warp), seeds + 2 * o,
+    search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, kept_list(sh, smem_hits, box_cap, warp), seeds + 2 * o,
                            n_live, prm, theta_out + 2 * o, R_out + o,
                            status + o, n_evals ? n_evals + o : nullptr, work);
 }
@@ -107,7 +108,7 @@ static cudaError_t launch_ls_t(const float4 *hits, int64_t n_hits, const int64_t
                                int n_events, int n_seeds, const float *seeds, const LsParams &prm, int smem_hits,
                                float *theta_out, float *R_out, uint8_t *status, uint8_t *n_evals, cudaStream_t st) {
     auto kern = local_search_kernel<MODEL, P, WARPS, UPD>;
-    const size_t smem = search_smem_bytes(smem_hits, boxes != nullptr, WARPS);
+    const size_t smem = search_smem_bytes(smem_hits, boxes != nullptr, WARPS, default_box_cap(smem_hits));
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (aerr != cudaSuccess) return aerr;
     const int per_block = WARPS * P;

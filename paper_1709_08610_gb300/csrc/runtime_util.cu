@@ -27,6 +27,27 @@ int sm_count() {
     return n;
 }
 
+// The current device's opt-in limit of dynamic shared memory per block,
+// looked up once per device.
+int max_dynamic_smem() {
+    constexpr int kMax = 64;
+    static std::mutex mu;
+    static int v_of[kMax] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    int *slot = (dev >= 0 && dev < kMax) ? &v_of[dev] : nullptr;
+    if (slot && *slot > 0) return *slot;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) cudaGetLastError();
+    if (v <= 0) v = 48 * 1024;
+    if (slot) *slot = v;
+    return v;
+}
+
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (the
 // launch's own need, so that static + dynamic stays within the device's
 // opt-in limit; the default limit counts static memory too, so it is raised

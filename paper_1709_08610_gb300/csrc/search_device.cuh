@@ -299,35 +299,36 @@ struct LsParams {
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box);
 
 // Shared-memory layout of the search kernels: smem_hits hits, then (with
-// boxes) the boxes of the first box_capacity(smem_hits) blocks in search_box
-// form as two arrays (the slope bounds, float4, then the |z|min^2 terms,
-// padded to a multiple of 4 floats; lanes reading consecutive blocks touch
-// consecutive words), the same two arrays for superblocks (the union of 4
+// boxes) the boxes of the first box_cap blocks (a multiple of 4) in
+// search_box form as two arrays (the slope bounds, float4, then the
+// |z|min^2 terms; lanes reading consecutive blocks touch consecutive words),
+// the same two arrays for their box_cap / 4 superblocks (the union of 4
 // consecutive blocks' boxes), then per warp one list of KEPT_CHUNK
-// kept-block offsets and 32 superblock slots.
+// kept-block offsets and 32 superblock slots.  default_box_cap covers the
+// staged hits' blocks; the batched kernel gives the boxes whatever shared
+// memory the hits and lists leave (box tests of unstaged blocks cost more
+// issue slots than loads of unstaged hits).
 constexpr int KEPT_CHUNK = 128;  // blocks tested per chunk of a pass (4 per lane, or 1 superblock per lane)
-__host__ __device__ __forceinline__ int box_capacity(int smem_hits) { return (smem_hits + 31) / 32 + 1; }
-__host__ __device__ __forceinline__ int box_capacity4(int smem_hits) { return (box_capacity(smem_hits) + 3) & ~3; }
-__host__ __device__ __forceinline__ int super_capacity4(int smem_hits) { return ((box_capacity4(smem_hits) >> 2) + 3) & ~3; }
-__host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes, int warps) {
+__host__ __device__ __forceinline__ int default_box_cap(int smem_hits) { return ((smem_hits + 31) / 32 + 1 + 3) & ~3; }
+__host__ __device__ __forceinline__ size_t search_list_bytes(int warps) {
+    return (size_t)warps * (KEPT_CHUNK + 32) * sizeof(int);
+}
+__host__ __device__ __forceinline__ size_t search_smem_bytes(int smem_hits, bool with_boxes, int warps, int box_cap) {
     return (size_t)smem_hits * 16 +
-           (with_boxes ? (size_t)box_capacity(smem_hits) * 16 + (size_t)box_capacity4(smem_hits) * 4 +
-                             (size_t)super_capacity4(smem_hits) * 20 + (size_t)warps * (KEPT_CHUNK + 32) * sizeof(int)
-                       : 0);
+           (with_boxes ? (size_t)box_cap * 20 + (size_t)(box_cap / 4) * 20 + search_list_bytes(warps) : 0);
 }
 __device__ __forceinline__ float4 *staged_box_bounds(float4 *sh, int smem_hits) { return sh + smem_hits; }
-__device__ __forceinline__ float *staged_box_z2(float4 *sh, int smem_hits) {
-    return reinterpret_cast<float *>(sh + smem_hits + box_capacity(smem_hits));
+__device__ __forceinline__ float *staged_box_z2(float4 *sh, int smem_hits, int box_cap) {
+    return reinterpret_cast<float *>(sh + smem_hits + box_cap);
 }
-__device__ __forceinline__ float4 *staged_super_bounds(float4 *sh, int smem_hits) {
-    return reinterpret_cast<float4 *>(staged_box_z2(sh, smem_hits) + box_capacity4(smem_hits));
+__device__ __forceinline__ float4 *staged_super_bounds(float4 *sh, int smem_hits, int box_cap) {
+    return reinterpret_cast<float4 *>(staged_box_z2(sh, smem_hits, box_cap) + box_cap);
 }
-__device__ __forceinline__ float *staged_super_z2(float4 *sh, int smem_hits) {
-    return reinterpret_cast<float *>(staged_super_bounds(sh, smem_hits) + super_capacity4(smem_hits));
+__device__ __forceinline__ float *staged_super_z2(float4 *sh, int smem_hits, int box_cap) {
+    return reinterpret_cast<float *>(staged_super_bounds(sh, smem_hits, box_cap) + box_cap / 4);
 }
-__device__ __forceinline__ int *kept_list(float4 *sh, int smem_hits, int warp) {
-    return reinterpret_cast<int *>(staged_super_z2(sh, smem_hits) + super_capacity4(smem_hits)) +
-           warp * (KEPT_CHUNK + 32);
+__device__ __forceinline__ int *kept_list(float4 *sh, int smem_hits, int box_cap, int warp) {
+    return reinterpret_cast<int *>(staged_super_z2(sh, smem_hits, box_cap) + box_cap / 4) + warp * (KEPT_CHUNK + 32);
 }
 
 // Lane-strided pass over an event's hits: the staged prefix from shared
@@ -461,7 +462,7 @@ __device__ __forceinline__ bool box_culled(const float4 A, const float w, const 
 // block: the same per-lane order as the full pass minus blocks whose terms
 // are all exactly zero - so every sum is bitwise the full pass's sum.
 // Returns the hits visited (for the work counters).
-template <int MODEL, typename T, typename F, typename F2>
+template <int MODEL, int UNROLL = 2, typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                         int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
                                         const float4 *__restrict__ ssb, const float *__restrict__ ssz2,
@@ -545,9 +546,20 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
             const float4 *src = seg == 0 ? sh : gh;
             const int end = seg == 0 ? (n_fast < n_pairs_end ? n_fast : n_pairs_end) : n_pairs_end;
 #pragma unroll 1
-            for (; i + 2 <= end; i += 2) {
+            for (; i + UNROLL <= end; i += UNROLL) {
+                // UNROLL = 4 (one point per warp, latency-bound): four blocks in flight
                 const float4 ha = src[list[i] + lane], hb = src[list[i + 1] + lane];
-                f2(ha, hb);
+                if (UNROLL == 4) {
+                    const float4 hc = src[list[i + 2] + lane], hd = src[list[i + 3] + lane];
+                    f2(ha, hb);
+                    f2(hc, hd);
+                } else {
+                    f2(ha, hb);
+                }
+            }
+            if (UNROLL == 4 && i + 2 <= end) {
+                f2(src[list[i] + lane], src[list[i + 1] + lane]);
+                i += 2;
             }
         }
 #pragma unroll 1
@@ -591,7 +603,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
             RghAcc<MODEL> acc;
             acc.zero();
             const CullPt cp = cull_pt<MODEL>(th0, th1, kk, cull);
-            const int vis = hit_pass<MODEL>(
+            const int vis = hit_pass<MODEL, 4>(
                 sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                 [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, cp); },
                 [&](const float4 h) { acc.add(h, th0, th1, kk); },
@@ -625,7 +637,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                 const CullPt ct = cull_pt_union<MODEL>(tr0, tr1, kk, cull, kk2, prm.cull[j + 1]);
                 RghAcc<MODEL> acc;
                 acc.zero();
-                vis = hit_pass<MODEL>(
+                vis = hit_pass<MODEL, 4>(
                     sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                     [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
                     [&](const float4 h) {
@@ -640,7 +652,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                 w_rgh += (uint32_t)vis;
             } else {
                 const CullPt ct = cull_pt<MODEL>(tr0, tr1, kk, cull);
-                vis = hit_pass<MODEL>(
+                vis = hit_pass<MODEL, 4>(
                     sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                     [&](const float4 A, const float z2) { return !box_culled<MODEL>(A, z2, ct); },
                     [&](const float4 h) { Rt = __fadd_rn(Rt, pair_r<MODEL>(h, tr0, tr1, kk)); },
