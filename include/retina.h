@@ -546,12 +546,31 @@ int retina_sort_seeds(const float *seeds, int64_t n_seeds, const int64_t *seed_o
  *   track_src: nullable int32 [n_events][K], index of the kept point.
  *   n_tracks: int32 [n_events]; number kept (may exceed K; the first K in
  *             visiting order are written).
- *   n_points must be <= RETINA_MAX_EXTRACT_POINTS (else RETINA_ENOSPACE).
+ *   n_points must be <= RETINA_MAX_EXTRACT_POINTS (else RETINA_ENOSPACE;
+ *   retina_extract_tracks_ws takes more).
  */
 int retina_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
                           int32_t n_events, int32_t n_points, const retina_grid *box, float R0,
                           float merge_cells, float *tracks, float *track_R, int32_t *track_src,
                           int32_t *n_tracks, int32_t K, void *stream);
+
+/*
+ * retina_extract_tracks_ws - retina_extract_tracks for any number of points.
+ *
+ * The same rule and outputs as retina_extract_tracks, for n_points up to
+ * RETINA_MAX_EXTRACT_POINTS_WS: up to RETINA_MAX_EXTRACT_POINTS points per
+ * event the candidates are kept in shared memory as there (ws is not used),
+ * beyond that in the caller's workspace, whose size
+ * retina_extract_tracks_workspace_size gives (per event one array of keys,
+ * coordinates, sources and states for the next power of two >= n_points).
+ * Returns RETINA_ENOSPACE (nothing launched) when ws_bytes is too small.
+ */
+#define RETINA_MAX_EXTRACT_POINTS_WS (1 << 22)
+int retina_extract_tracks_workspace_size(int32_t n_events, int32_t n_points, size_t *bytes);
+int retina_extract_tracks_ws(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                             int32_t n_events, int32_t n_points, const retina_grid *box, float R0, float merge_cells,
+                             float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int32_t K,
+                             void *ws, size_t ws_bytes, void *stream);
 
 /*
  * retina_extract_tracks4 - cluster / select for four-parameter points.

@@ -404,6 +404,30 @@ int retina_extract_tracks(const float *theta, const float *R, const uint8_t *sta
                                              tracks, track_R, track_src, n_tracks, K, (cudaStream_t)stream));
 }
 
+int retina_extract_tracks_workspace_size(int32_t n_events, int32_t n_points, size_t *bytes) {
+    if (!bytes || n_events < 0 || n_points < 0 || n_points > RETINA_MAX_EXTRACT_POINTS_WS) return RETINA_EINVAL;
+    *bytes = n_points > RETINA_MAX_EXTRACT_POINTS ? (size_t)n_events * extract_ws_stride(n_points, 2) : 0;
+    return RETINA_OK;
+}
+
+int retina_extract_tracks_ws(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
+                             int32_t n_events, int32_t n_points, const retina_grid *box, float R0, float merge_cells,
+                             float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int32_t K,
+                             void *ws, size_t ws_bytes, void *stream) {
+    if (n_points <= RETINA_MAX_EXTRACT_POINTS)
+        return retina_extract_tracks(theta, R, status, n_valid, n_events, n_points, box, R0, merge_cells, tracks,
+                                     track_R, track_src, n_tracks, K, stream);
+    if (n_events < 0 || !valid_grid(box) || isnan(R0) || !finite_pos(merge_cells) || K < 1) return RETINA_EINVAL;
+    for (int a = 0; a < 2; ++a)
+        if ((double)box->n[a] / (double)merge_cells > 32768.0) return RETINA_EINVAL;
+    if (n_points > RETINA_MAX_EXTRACT_POINTS_WS || n_events > 65535) return RETINA_EINVAL;
+    if (n_events == 0) return RETINA_OK;
+    if (ws_bytes < (size_t)n_events * extract_ws_stride(n_points, 2)) return RETINA_ENOSPACE;
+    if (!ws || ((uintptr_t)ws & 255u) || !n_tracks || !theta || !R || !tracks || !track_R) return RETINA_EINVAL;
+    return cuda_status(launch_extract_tracks(theta, R, status, n_valid, n_events, n_points, box, R0, merge_cells,
+                                             tracks, track_R, track_src, n_tracks, K, (cudaStream_t)stream, ws));
+}
+
 int retina_extract_tracks4(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
                            int32_t n_events, int32_t n_points, const retina_grid *slope_box, const float *unit, float R0,
                            float merge_units, float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks,

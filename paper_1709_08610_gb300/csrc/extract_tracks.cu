@@ -120,14 +120,20 @@ __device__ __forceinline__ bool conflict(const float *a, const float *b, const E
     return c;
 }
 
-template <int D>
+// GWS: the candidate arrays (keys, coordinates, sources, states) of event e
+// live in the caller's workspace at e * ws_stride instead of shared memory
+// (events with more points than shared memory holds); the algorithm and its
+// result are the same.
+template <int D, bool GWS>
 __global__ void __launch_bounds__(EX_THREADS)
 extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__ R, const uint8_t *__restrict__ status,
                       const int32_t *__restrict__ n_valid, ExtractParams prm, float *__restrict__ tracks,
-                      float *__restrict__ track_R, int32_t *__restrict__ track_src, int32_t *__restrict__ n_tracks) {
+                      float *__restrict__ track_R, int32_t *__restrict__ track_src, int32_t *__restrict__ n_tracks,
+                      unsigned char *__restrict__ ws, int64_t ws_stride) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int cap = prm.cap;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *store = GWS ? ws + (int64_t)blockIdx.x * ws_stride : smem;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(store);
     float *th = reinterpret_cast<float *>(keys + cap);  // [D][cap]
     int32_t *src = reinterpret_cast<int32_t *>(th + D * cap);
     volatile uint8_t *state = reinterpret_cast<uint8_t *>(src + cap);
@@ -345,20 +351,26 @@ extract_tracks_kernel(const float *__restrict__ theta, const float *__restrict__
 }
 
 size_t extract_smem_bytes(int n_points, int dims) {
-    int C = 1;
+    int64_t C = 1;
     while (C < n_points) C <<= 1;
     return (size_t)C * (sizeof(uint64_t) + (size_t)dims * sizeof(float) + sizeof(int32_t) + 1) + 16;
 }
+
+// Workspace of the global-memory form: per event the same arrays, 256-aligned.
+size_t extract_ws_stride(int n_points, int dims) { return (extract_smem_bytes(n_points, dims) + 255) / 256 * 256; }
 
 // merge[d]: the merge distance of coordinate d; box on the last two.
 template <int D>
 static cudaError_t launch_extract_d(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
                                     int n_events, int n_points, const retina_grid *box, float R0, const float *merge,
                                     float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
-                                    cudaStream_t st) {
-    const size_t smem = extract_smem_bytes(n_points, D);
-    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(extract_tracks_kernel<D>), smem);
-    if (aerr != cudaSuccess) return aerr;
+                                    cudaStream_t st, void *ws = nullptr) {
+    const bool gws = ws != nullptr;
+    const size_t smem = gws ? 0 : extract_smem_bytes(n_points, D);
+    if (!gws) {
+        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(extract_tracks_kernel<D, false>), smem);
+        if (aerr != cudaSuccess) return aerr;
+    }
     ExtractParams prm{};
     prm.lo0 = box->lo[0];
     prm.lo1 = box->lo[1];
@@ -374,8 +386,13 @@ static cudaError_t launch_extract_d(const float *theta, const float *R, const ui
     while (C < n_points) C <<= 1;
     prm.cap = C;
     PrioLaunch L(dim3(n_events), dim3(EX_THREADS), smem, st, true);
-    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel<D>, theta, R, status, n_valid, prm,
-                                                tracks, track_R, track_src, n_tracks);
+    unsigned char *wsb = static_cast<unsigned char *>(ws);
+    const int64_t stride = gws ? (int64_t)extract_ws_stride(n_points, D) : 0;
+    const cudaError_t lerr =
+        gws ? cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel<D, true>, theta, R, status, n_valid, prm, tracks,
+                                 track_R, track_src, n_tracks, wsb, stride)
+            : cudaLaunchKernelEx(&L.cfg, extract_tracks_kernel<D, false>, theta, R, status, n_valid, prm, tracks,
+                                 track_R, track_src, n_tracks, wsb, stride);
     count_launches(1);
     return lerr != cudaSuccess ? lerr : cudaGetLastError();
 }
@@ -383,10 +400,11 @@ static cudaError_t launch_extract_d(const float *theta, const float *R, const ui
 cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
                                   int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
                                   float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, void *ws) {
     const float merge[2] = {merge_cells * box->step[0], merge_cells * box->step[1]};
+    // shared memory holds up to RETINA_MAX_EXTRACT_POINTS points; beyond that the workspace
     return launch_extract_d<2>(theta, R, status, n_valid, n_events, n_points, box, R0, merge, tracks, track_R,
-                               track_src, n_tracks, K, st);
+                               track_src, n_tracks, K, st, n_points > RETINA_MAX_EXTRACT_POINTS ? ws : nullptr);
 }
 
 cudaError_t launch_extract_tracks4(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,

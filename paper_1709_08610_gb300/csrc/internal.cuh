@@ -32,10 +32,13 @@ cudaError_t launch_local_search(const float4 *hits, int64_t n_hits, const int64_
 cudaError_t launch_response(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                             const float *theta, int n_points, float sigma, int want_derivs, float *out,
                             cudaStream_t st);
+// ws: the workspace of events with more than RETINA_MAX_EXTRACT_POINTS points
+// (extract_ws_stride bytes per event; ignored below that).
 cudaError_t launch_extract_tracks(const float *theta, const float *R, const uint8_t *status, const int32_t *n_valid,
                                   int n_events, int n_points, const retina_grid *box, float R0, float merge_cells,
                                   float *tracks, float *track_R, int32_t *track_src, int32_t *n_tracks, int K,
-                                  cudaStream_t st);
+                                  cudaStream_t st, void *ws = nullptr);
+size_t extract_ws_stride(int n_points, int dims);
 
 cudaError_t launch_batched_search(const float4 *hits, int64_t n_hits, const int64_t *hit_off, const float4 *boxes,
                                   int n_events, int model,

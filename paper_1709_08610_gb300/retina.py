@@ -149,6 +149,8 @@ def _load():
     L.retina_pipeline_run.argtypes = [P, P, I64, P, I32, P, P, P, P, P, P, P, P]
     L.retina_pipeline_destroy.argtypes = [P]
     L.retina_pair_seeds4.argtypes = [P, I64, P, I32, P, I32, F, F, F, F, F, P, P, I32, P]
+    L.retina_extract_tracks_workspace_size.argtypes = [I32, I32, P]
+    L.retina_extract_tracks_ws.argtypes = [P, P, P, P, I32, I32, P, F, F, P, P, P, P, I32, P, SZ, P]
     L.retina_extract_tracks4.argtypes = [P, P, P, P, I32, I32, P, P, F, F, P, P, P, P, I32, P]
     L.retina_tracker_create.argtypes = [P, P, P]
     L.retina_tracker_buffers.argtypes = [P, P, P, P, P, P, P]
@@ -199,7 +201,8 @@ def _load():
                  "retina_local_search", "retina_extract_tracks", "retina_slope_histogram",
                  "retina_seednet_forward", "retina_seednet_train_workspace_size", "retina_seednet_train_step",
                  "retina_seednet_adam", "retina_topk_seeds", "retina_device_error",
-                 "retina_sort_seeds", "retina_pair_seeds4", "retina_extract_tracks4"):
+                 "retina_sort_seeds", "retina_pair_seeds4", "retina_extract_tracks4",
+                 "retina_extract_tracks_workspace_size", "retina_extract_tracks_ws"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -589,10 +592,20 @@ def sort_seeds(seeds: torch.Tensor, seed_offsets: torch.Tensor, box: Grid, out: 
     return (out, perm) if (want_perm or perm is not None) else out
 
 
+def extract_tracks_workspace_size(n_events: int, n_points: int) -> int:
+    b = ctypes.c_size_t()
+    _check("retina_extract_tracks_workspace_size", lib.retina_extract_tracks_workspace_size(n_events, n_points,
+                                                                                           ctypes.byref(b)))
+    return b.value
+
+
 def extract_tracks(theta: torch.Tensor, R: torch.Tensor, status: Optional[torch.Tensor], box: Grid, R0: float,
                    merge_cells: float, K: int, n_valid: Optional[torch.Tensor] = None, out=None,
-                   stream=None) -> dict:
-    """Cluster + select best above R0 (Algorithm 1): kept points in visiting order."""
+                   stream=None, ws: Optional[torch.Tensor] = None) -> dict:
+    """Cluster + select best above R0 (Algorithm 1): kept points in visiting
+    order.  Beyond RETINA_MAX_EXTRACT_POINTS points per event the candidates
+    go to a workspace (retina_extract_tracks_ws; allocated here unless ws is
+    given)."""
     _dev(theta, torch.float32, "theta", 2)
     _dev(R, torch.float32, "R")
     if status is not None:
@@ -608,9 +621,13 @@ def extract_tracks(theta: torch.Tensor, R: torch.Tensor, status: Optional[torch.
                    track_src=torch.empty((E, K), dtype=torch.int32, device=dev),
                    n_tracks=torch.empty((E,), dtype=torch.int32, device=dev))
     g = box.c()
-    _check("retina_extract_tracks", lib.retina_extract_tracks(
+    need = extract_tracks_workspace_size(E, n)
+    if need > 0 and (ws is None or ws.numel() < need):
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    _check("retina_extract_tracks_ws", lib.retina_extract_tracks_ws(
         _p(theta), _p(R), _p(status), _p(n_valid), E, n, ctypes.byref(g), float(R0), float(merge_cells),
-        _p(out["tracks"]), _p(out["track_R"]), _p(out["track_src"]), _p(out["n_tracks"]), K, _stream(stream)))
+        _p(out["tracks"]), _p(out["track_R"]), _p(out["track_src"]), _p(out["n_tracks"]), K,
+        _p(ws) if need > 0 else None, ws.numel() if (need > 0 and ws is not None) else 0, _stream(stream)))
     return out
 
 

@@ -386,3 +386,18 @@ def test_tracker_configuration_is_validated_before_allocating():
     assert L.retina_tracker_step(None, 1, None) == EINVAL
     assert L.retina_tracker_run_host(None, None, 0, None, 1, None, None, None, None, None) == EINVAL
     assert L.retina_tracker_destroy(None) == EINVAL
+
+
+def test_extract_tracks_ws_sizes_and_validation():
+    b = ctypes.c_size_t()
+    assert L.retina_extract_tracks_workspace_size(4, 8192, ctypes.byref(b)) == 0 and b.value == 0
+    assert L.retina_extract_tracks_workspace_size(4, 8193, ctypes.byref(b)) == 0 and b.value >= 4 * 16384 * 17
+    assert L.retina_extract_tracks_workspace_size(4, (1 << 22) + 1, ctypes.byref(b)) == EINVAL
+    g = _grid()
+    args = (BOGUS, BOGUS, None, None, 2, 20000, ctypes.byref(g), 5.0, 2.0, BOGUS, BOGUS, None, BOGUS, 8)
+    need = ctypes.c_size_t()
+    L.retina_extract_tracks_workspace_size(2, 20000, ctypes.byref(need))
+    assert L.retina_extract_tracks_ws(*args, WS, need.value - 1, None) == ENOSPACE
+    assert L.retina_extract_tracks_ws(*args, ctypes.c_void_p(0x2010), need.value, None) == EINVAL  # misaligned
+    assert L.retina_extract_tracks_ws(*args, None, need.value, None) == EINVAL
+    assert L.retina_extract_tracks(*args, None) == ENOSPACE  # the shared-memory form stops at 8192

@@ -589,3 +589,75 @@ def test_grid_scan_full_size_track_sets(rt, wl_name):
         R_o = oracle.grid_response(ev.hits, wl.model, wl.grid_lo, wl.grid_step, wl.grid_n, wl.sigma_grid)
         compared += _grid_sets(rt, wl, [ev], out["R"].cpu().numpy(), out, tr, [R_o])
     assert compared >= (50 if wl_name == "toy2d" else 150), compared
+
+
+# ---------------------------------------------------------------------------
+# beyond the shared-memory sizes: more points than 8192 per event, events
+# with more hits than a CTA stages
+# ---------------------------------------------------------------------------
+
+def test_extract_tracks_exact_beyond_8192_points(rt):
+    rng = np.random.default_rng(21)
+    lo, step, n = (-1.0, -1.0), (2 ** -7, 2 ** -7), (256, 256)
+    E, P = 3, 20000
+    centres = rng.uniform(-1.0, 1.0, (E, 300, 2))
+    th = centres[np.arange(E)[:, None], rng.integers(0, 300, (E, P))] + rng.normal(0, 2 * step[0], (E, P, 2))
+    th = (np.round(th / (step[0] / 8)) * (step[0] / 8)).astype(np.float32)
+    R = rng.integers(0, 60, (E, P)).astype(np.float32)
+    st = rng.integers(0, 3, (E, P)).astype(np.uint8)
+    nv = np.array([P, 15000, 9000], np.int32)
+    for K in (4000, 50):
+        out = rt.extract_tracks(dev(th), dev(R), dev(st), rt.Grid(lo, step, n), 5.0, 2.0, K, n_valid=dev(nv))
+        n_tr = out["n_tracks"].cpu().numpy()
+        src = out["track_src"].cpu().numpy()
+        for e in range(E):
+            m = nv[e]
+            keep = oracle.extract_tracks(th[e, :m], R[e, :m], st[e, :m], lo, step, n, 5.0, 2.0)
+            assert n_tr[e] == len(keep) > 100
+            k = min(K, len(keep))
+            assert src[e, :k].tolist() == keep[:k].tolist()
+
+
+def test_search_and_extract_on_an_event_beyond_25k_hits_with_12288_points(rt):
+    # a high-multiplicity event with 1200 tracks (~33k hits: more than a CTA
+    # stages) and 12288 starting points around its tracks (more than the
+    # shared-memory extraction holds) through the batched search and the
+    # workspace extraction: found-track set equal to the oracle's up to near-ties
+    from paper_1709_08610_gb300.pipeline import BatchTracker
+    wl = WORKLOADS["velo_stress"]
+    ev = make_event(wl, 23, 0, vertex_sigma=(0, 0, 0), n_tracks=1200)
+    assert ev.n_hits > 25000
+    rng = np.random.default_rng(8)
+    S = 12288
+    seeds = (ev.truth[:, :2][rng.integers(0, len(ev.truth), S)] + rng.normal(0, 3, (S, 2)) * wl.grid_step[0])
+    seeds = seeds.astype(np.float32)
+    box = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    tr = BatchTracker(1, ev.n_hits, S, box, opts, wl.R0, max_tracks=4096, sort_seeds=True, seeds_per_warp=2,
+                      warps=32, smem_hits=12288)
+    tr.load(ev.hits, np.array([0, ev.n_hits], np.int64), seeds[None])
+    tr.step()
+    torch.cuda.synchronize()
+    th_g, R_g, st_g = (x.cpu().numpy() for x in tr.search_out)
+    th_g, R_g = th_g.astype(float), R_g.astype(float)
+    ss = tr.seeds_sorted.cpu().numpy()
+    nt = int(tr.tracks["n_tracks"][0])
+    assert 0 < nt <= 4096
+    src = tr.tracks["track_src"][0, :nt].cpu().numpy()
+    R0 = float(np.float32(wl.R0))
+    boxa = (wl.grid_lo, wl.grid_step, wl.grid_n)
+
+    def run(pt):
+        return oracle.local_search(ev.hits, 1, ss, wl.sigma_schedule, *boxa, perturb=pt)
+
+    th_o, R_o, st_o, m_o = base = run(None)
+    keep_o = oracle.extract_tracks(th_o, R_o, st_o, *boxa, R0, wl.merge_cells)
+    cand_o = candidates(th_o, R_o, st_o, *boxa, R0)
+    cand_g = candidates(th_g, R_g, st_g, *boxa, R0)
+    assert cand_g.sum() > 8192  # the extraction's candidates exceed shared memory
+    tol = search_tolerance(_converged_2d(ev, wl), th_o, cand_o | cand_g, wl.grid_step)
+    stable, _, _ = oracle.path_conditioning(run, base, tol, keys=oracle.PERTURB_KEYS[:4])
+    near0 = np.abs(R_o - R0) <= R_REL * np.abs(R_o) + R_ABS
+    _, _, compared = compare_track_sets(th_o, R_o, cand_o | (near0 & (st_o <= 1)), th_g, R_g, cand_g,
+                                        (m_o < 1.0) | ~stable, keep_o, src, tol, wl.grid_step, wl.merge_cells, R0=R0)
+    assert compared >= 500, compared
