@@ -32,6 +32,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from typing import Optional
 
 import numpy as np
 
@@ -47,6 +48,9 @@ METRIC = ("events/s (learned-seed batched local search at >= 95% of the oracle's
           "ordering, proposer, top-2048 seeds, truncated-Newton search, extraction; 1024 high-multiplicity events "
           "per step)")
 L2_FLUSH_BYTES = 256 << 20
+# algorithmic FP32 lane operations (an FMA counts once) per (seed, hit) pair of
+# the search: a gradient/Hessian pass 15, an R-only (line-search) pass 5
+LANE_OPS_RGH, LANE_OPS_R = 15.0, 5.0
 
 
 def parse():
@@ -273,7 +277,7 @@ BATCH_RUN_SEED = 5000
 
 
 def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: int = 512, reps: int = 5,
-                    comparisons: bool = False):
+                    comparisons: bool = False, fma_rate: Optional[float] = None):
     """1024 ragged VELO-like events with the vertex at the origin through three
     methods, each replayed as one CUDA graph per batch: the plain grid scan
     (with and without the refinement of its maxima), Algorithm 1 from 4096
@@ -282,8 +286,10 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
     events around graph replays (L2 flushed before each), MC-truth efficiency
     (|dtheta|_max <= 1e-3), fakes per event, the resolution of the matched
     tracks (|dtheta| per axis in grid cells) and the share of the plain
-    4096-seed search's tracks each method recovers.  With ``comparisons``:
-    the same searches with the steepest-ascent and modified-Newton updates."""
+    4096-seed search's tracks each method recovers; for the searches, the
+    search launch's own time and its rate against ``fma_rate`` (FP32 lane
+    operations/s).  With ``comparisons``: the same searches with the
+    steepest-ascent and modified-Newton updates."""
     import torch
     from paper_1709_08610_gb300.pipeline import (BatchTracker, GridScanBatch, match_efficiency, match_residuals,
                                                  recovered_fraction)
@@ -372,16 +378,28 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
             if bf16 and rt.get_option(rt.OPT_GRID_TC):
                 methods[name]["grid_frac_of_3xtf32_peak"] = tflops / (bf16 * (1.1 / 2.25) / 3)
         if isinstance(obj, BatchTracker):
-            # search work of one (eager) step, counted on the device; over the whole
-            # batch time this is a lower bound on the search kernel's own rate
+            # search work of one (eager) step, counted on the device, and the search
+            # launch's own time (CUDA events around it, L2 flushed before the step,
+            # median of three eager steps)
             rt.work_counters(enable=True, reset=True)
             obj.step()
             torch.cuda.synchronize()
             w = rt.work_counters(enable=False)
+            marks = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            k_ms = []
+            for _ in range(3):
+                flush.zero_()
+                obj.step(stream, marks=marks)
+                marks[1].synchronize()
+                k_ms.append(marks[0].elapsed_time(marks[1]))
+            k_ms = float(np.median(k_ms))
+            lane_ops = LANE_OPS_RGH * w[rt.WORK_RGH] + LANE_OPS_R * w[rt.WORK_R]
             pairs = w[rt.WORK_RGH] + w[rt.WORK_R]
             methods[name]["search_pairs_per_batch"] = int(pairs)
-            methods[name]["search_fp32_lane_ops_per_s_lower_bound"] = \
-                (16.0 * w[rt.WORK_RGH] + 6.0 * w[rt.WORK_R]) / (ms * 1e-3)
+            methods[name]["search_kernel_ms"] = k_ms
+            methods[name]["search_tlane_ops_per_s"] = lane_ops / (k_ms * 1e-3) / 1e12
+            if fma_rate:
+                methods[name]["search_frac_of_fp32_lane_rate"] = lane_ops / (k_ms * 1e-3) / fma_rate
         del obj
         torch.cuda.empty_cache()
     for name in methods:
@@ -827,9 +845,9 @@ def single_event_step(rt, tune, args, dev, rank, peaks, vertex_sigma=None, with_
     search_ms = float(np.mean(stage[:, 3]))
     # grid contraction: one FP32 FMA (2 flops) per evaluated (cell, hit) pair
     grid_tflops = 2.0 * grid_pairs / (grid_ms * 1e-3) / 1e12
-    # search: 16 FP32 ops + 1 ex2 per (seed, hit) pair of a gradient/Hessian
-    # pass, 6 FP32 ops + 1 ex2 per pair of an R pass (from the kernel source)
-    search_fp32_ops = 16.0 * rgh_pairs + 6.0 * r_pairs
+    # search: LANE_OPS_RGH FP32 operations + 1 ex2 per (seed, hit) pair of a
+    # gradient/Hessian pass, LANE_OPS_R + 1 ex2 per pair of an R pass
+    search_fp32_ops = LANE_OPS_RGH * rgh_pairs + LANE_OPS_R * r_pairs
     search_ex2 = rgh_pairs + r_pairs
     search_fp32_rate = search_fp32_ops / (search_ms * 1e-3)
     search_ex2_rate = search_ex2 / (search_ms * 1e-3)
@@ -1183,7 +1201,7 @@ def headline(rt, args, dev, rank, world, peaks, local_rank):
     rgh, rr = int(w[rt.WORK_RGH]), int(w[rt.WORK_R])
     search_ms = float(st_ms[:, 3].mean())
     fma_rate = max(peaks.get("ffma", 0.0), peaks.get("ffma2", 0.0))
-    lane_ops = 15.0 * rgh + 5.0 * rr  # FP32 operations per pair (an FMA counts once): RGH 15, R alone 5
+    lane_ops = LANE_OPS_RGH * rgh + LANE_OPS_R * rr
     achieved = lane_ops / (search_ms * 1e-3)
     ex2_rate = (rgh + rr) / (search_ms * 1e-3)
     roofline = {"kernel": "batched_search_kernel", "bound": "alu", "unit": "Tlane-op/s",
@@ -1375,10 +1393,12 @@ def main():
             # tiles, the search filling the GPU
             rt.set_option(rt.OPT_GRID_SPLITS, 0)
             rt.set_option(rt.OPT_BATCH_CTAS, 0)
-            extras["batched"] = batched_methods(rt, stream, flush, comparisons=True)
+            fma_rate = max(peaks.get("ffma", 0.0), peaks.get("ffma2", 0.0)) or None
+            extras["batched"] = batched_methods(rt, stream, flush, comparisons=True, fma_rate=fma_rate)
             extras["alpha_sweep"] = alpha_sweep(rt, stream, flush)
             extras["svelo_sweep"] = svelo_sweep(rt, stream, flush)
-            extras["batched_stress"] = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3)
+            extras["batched_stress"] = batched_methods(rt, stream, flush, "velo_stress", learned_k=2048, reps=3,
+                                                       fma_rate=fma_rate)
             restore()
 
     if rank == 0:

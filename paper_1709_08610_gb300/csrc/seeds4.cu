@@ -45,7 +45,8 @@ __device__ __forceinline__ int cta_rank(bool flag, int *warp_tot, int &total) {
 
 // List the indices (relative to the event) of the event's hits with
 // |z - z_layer| <= tol, in increasing order; returns how many (at most cap
-// are stored, the count is not clamped).
+// are stored, the count is not clamped).  All threads call it; the list is
+// complete for every thread when it returns.
 __device__ int list_layer(const float4 *__restrict__ gh, int H, float z_layer, float tol, int *idx, int cap,
                           int *warp_tot) {
     int n = 0;
@@ -57,6 +58,7 @@ __device__ int list_layer(const float4 *__restrict__ gh, int H, float z_layer, f
         if (in && n + pos < cap) idx[n + pos] = k;
         n += total;
     }
+    __syncthreads();  // the last window's entries are read by other threads next
     return n;
 }
 

@@ -68,8 +68,10 @@ class BatchTracker:
         if seeds is not None:
             self.seeds.copy_(torch.from_numpy(np.ascontiguousarray(seeds, dtype=np.float32)).reshape(self.seeds.shape))
 
-    def step(self, stream=None):
-        """Launch the whole step on the current (or given) stream."""
+    def step(self, stream=None, marks=None):
+        """Launch the whole step on the current (or given) stream.  ``marks``: two
+        CUDA events, recorded on that stream just before and just after the
+        search launch (eager steps only)."""
         rt.prepare_hits(self.hits, self.offsets, self.model, out=(self.sorted, self.boxes), stream=stream)
         if self.proposer is not None:
             self.proposer.propose(self.hits, self.offsets, self.n, seeds=self.seeds, stream=stream)
@@ -82,9 +84,14 @@ class BatchTracker:
         old = [(o, rt.get_option(o)) for o, _ in shape]
         for o, v in shape:
             rt.set_option(o, v)
+        st = stream if stream is not None else torch.cuda.current_stream()
         try:
+            if marks:
+                marks[0].record(st)
             rt.batched_search(self.sorted, self.offsets, self.model, seeds, self.seed_offsets, self.opts, self.box,
                               out=self.search_out, ws=self.ws, boxes=self.boxes, stream=stream)
+            if marks:
+                marks[1].record(st)
         finally:
             for o, v in old:
                 rt.set_option(o, v)
