@@ -628,9 +628,17 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         bool pending = true;
         Rfin = R;  // R at the point if no step is accepted
         const bool fuse = j + 1 < prm.q;
-        for (int hv = 0; hv <= prm.max_halvings && pending; ++hv) {
+        // the first trial (t = 1) alone; once it is rejected, the trials t and
+        // t / 2 share one pass (a block is skipped only when both points skip
+        // it, so each R is bitwise its own pass's) and are tested in order:
+        // the accepted point, its R and the trial count are the sequential
+        // backtracking's, in about half the dependent passes
+        for (int hv = 0; hv <= prm.max_halvings && pending;) {
             const float tr0 = __fmaf_rn(t, pp0, th0), tr1 = __fmaf_rn(t, pp1, th1);
-            float Rt = 0.f;
+            const bool two = hv > 0 && hv + 1 <= prm.max_halvings;
+            const float tb = t * 0.5f;
+            const float tb0 = __fmaf_rn(tb, pp0, th0), tb1 = __fmaf_rn(tb, pp1, th1);
+            float Rt = 0.f, Rb = 0.f;
             int vis;
             if (hv == 0 && fuse) {
                 const float kk2 = prm.kk[j + 1];
@@ -650,6 +658,37 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                     });
                 acc.sums(S);
                 w_rgh += (uint32_t)vis;
+            } else if (two) {
+                const CullPt ca = cull_pt<MODEL>(tr0, tr1, kk, cull), cb = cull_pt<MODEL>(tb0, tb1, kk, cull);
+                auto need2 = [&](const float4 A, const float z2) {
+                    return !box_culled<MODEL>(A, z2, ca) || !box_culled<MODEL>(A, z2, cb);
+                };
+                if constexpr (MODEL == RETINA_VELO_SLOPES) {
+                    // both trial points in packed FP32x2 (bitwise pair_r per lane)
+                    const unsigned long long nt0 = pack2(-tr0, -tb0), nt1 = pack2(-tr1, -tb1);
+                    const unsigned long long nkk = pack2(-kk, -kk);
+                    unsigned long long Rt2 = 0ull;
+                    vis = hit_pass<MODEL, 4>(
+                        sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, need2,
+                        [&](const float4 h) { pair_r_x2(h, nt0, nt1, nkk, Rt2); },
+                        [&](const float4 a, const float4 b) {
+                            pair_r_x2(a, nt0, nt1, nkk, Rt2);
+                            pair_r_x2(b, nt0, nt1, nkk, Rt2);
+                        });
+                    unpack2(Rt2, Rt, Rb);
+                } else {
+                    vis = hit_pass<MODEL, 4>(
+                        sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, need2,
+                        [&](const float4 h) {
+                            Rt = __fadd_rn(Rt, pair_r<MODEL>(h, tr0, tr1, kk));
+                            Rb = __fadd_rn(Rb, pair_r<MODEL>(h, tb0, tb1, kk));
+                        },
+                        [&](const float4 a, const float4 b) {
+                            pair_r2<MODEL>(a, b, tr0, tr1, kk, Rt);
+                            pair_r2<MODEL>(a, b, tb0, tb1, kk, Rb);
+                        });
+                }
+                w_r += (uint32_t)vis;  // the second point's pairs
             } else {
                 const CullPt ct = cull_pt<MODEL>(tr0, tr1, kk, cull);
                 vis = hit_pass<MODEL, 4>(
@@ -671,8 +710,21 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                     for (int i = 0; i < NS; ++i) S[i] = warp_sum(S[i]);
                     have = true;  // the next update's sums at the accepted point
                 }
+            } else if (two) {
+                ++evals;
+                const float rb = warp_sum(Rb);
+                if (rb >= R + prm.c1 * tb * slope) {
+                    th0 = tb0;
+                    th1 = tb1;
+                    Rfin = rb;
+                    pending = false;
+                } else {
+                    t = tb * 0.5f;
+                }
+                hv += 2;
             } else {
                 t *= 0.5f;
+                ++hv;
             }
         }
         if (pending) failed = true;
