@@ -73,6 +73,9 @@ def parse():
                          "warps per CTA, staged hits, CTA cap, grid hit slices")
     ap.add_argument("--graph", action="store_true", help="replay the step as one CUDA graph instead of enqueueing "
                                                          "its kernels one by one")
+    ap.add_argument("--profile-single", action="store_true",
+                    help="profiling runs: only the single-event step (vertex at the origin), --steps steps, no "
+                         "end-to-end leg; prints its summary instead of the bench line")
     return ap.parse_args()
 
 
@@ -604,7 +607,8 @@ def svelo_sweep(rt, stream, flush, reps: int = 3):
 # our arm
 # ---------------------------------------------------------------------------
 
-def single_event_step(rt, tune, args, dev, rank, peaks, vertex_sigma=None, with_cpu=False, steps=400):
+def single_event_step(rt, tune, args, dev, rank, peaks, vertex_sigma=None, with_cpu=False, steps=400,
+                      with_e2e=True):
     """The single-event step (one VELO-like event: the 1024 x 1024 grid scan,
     the 8192-seed truncated-Newton search and the extraction of both, the two
     branches on concurrent streams after the shared hit ordering), timed over
@@ -895,7 +899,7 @@ def single_event_step(rt, tune, args, dev, rank, peaks, vertex_sigma=None, with_
     # launch of the step, the two branches on two streams) - or replays the step
     # graph with --graph - and copies both track lists out to pinned host memory
     e2e = None
-    if True:
+    if with_e2e:
         hits_h = torch.from_numpy(ev.hits).pin_memory()
         seeds_h = torch.from_numpy(seeds_np).view(-1, 2).pin_memory()
         n_e2e = 200
@@ -1372,6 +1376,12 @@ def main():
     def restore():
         for o, v in defaults.items():
             rt.set_option(o, v)
+
+    if args.profile_single:
+        r = single_event_step(rt, tune, args, dev, rank, peaks, vertex_sigma=(0, 0, 0), steps=args.steps,
+                              with_e2e=False)
+        print(json.dumps({k: r[k] for k in ("workload", "events_per_s", "stages_ms", "tracks_found")}))
+        return
 
     head = headline(rt, args, dev, rank, world, peaks, local_rank)
 
