@@ -452,6 +452,37 @@ __device__ __forceinline__ bool box_culled(const float4 A, const float w, const 
     }
 }
 
+// The active points of a warp as one test (slope model): the smallest box
+// [t0lo, t0hi] x [t1lo, t1hi] holding them.  Its distance to a block's box
+// is at most each point's own (every rounding is monotone), so a block this
+// test skips is skipped by each point's box_culled: the kept set is a
+// superset of the union of the points' own, and the extra blocks add exact
+// zeros to each sum.  One test instead of one per point; the points of a
+// warp are spatial neighbours (sorted seeds), so few blocks are added.
+struct CullSpan {
+    float t0lo, t0hi, t1lo, t1hi, c;
+};
+template <int P>
+__device__ __forceinline__ CullSpan cull_span(const float (&t0)[P], const float (&t1)[P], const bool (&act)[P],
+                                              float cull) {
+    CullSpan s{INFINITY, -INFINITY, INFINITY, -INFINITY, cull};
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (!act[p]) continue;
+        if (!(isfinite(t0[p]) && isfinite(t1[p]))) s.c = INFINITY;  // never skip around a non-finite point
+        s.t0lo = fminf(s.t0lo, t0[p]);
+        s.t0hi = fmaxf(s.t0hi, t0[p]);
+        s.t1lo = fminf(s.t1lo, t1[p]);
+        s.t1hi = fmaxf(s.t1hi, t1[p]);
+    }
+    return s;
+}
+__device__ __forceinline__ bool span_culled(const float4 A, const float w, const CullSpan &s) {
+    const float du = fmaxf(fmaxf(A.x - s.t0hi, s.t0lo - A.y), 0.f);
+    const float dv = fmaxf(fmaxf(A.z - s.t1hi, s.t1lo - A.w), 0.f);
+    return __fmaf_rn(du, du, dv * dv) * w > s.c;
+}
+
 // Pass over the hits that can contribute for the P points of the warp.
 // Without boxes it is for_each_hit.  With boxes, each chunk of KEPT_CHUNK
 // blocks is tested (lane l tests blocks l, l + 32, l + 64, l + 96 of the
@@ -796,7 +827,9 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             acc[p].zero();
             cp[p] = cull_pt<MODEL>(th0[p], th1[p], kk, cull);
         }
+        const CullSpan span = cull_span<P>(th0, th1, live, cull);
         auto needed = [&](const float4 A, const float z2) {
+            if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span);
             bool need = false;
 #pragma unroll
             for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, z2, cp[p]);
@@ -865,7 +898,9 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 Rt[p] = 0.f;
                 ct[p] = cull_pt<MODEL>(tr0[p], tr1[p], kk, cull);
             }
+            const CullSpan span_r = cull_span<P>(tr0, tr1, pending, cull);
             auto needed_r = [&](const float4 A, const float z2) {
+                if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span_r);
                 bool need = false;
 #pragma unroll
                 for (int p = 0; p < P; ++p) need |= pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
