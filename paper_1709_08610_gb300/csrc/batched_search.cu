@@ -168,8 +168,11 @@ static cudaError_t launch_batched_t(BatchArgs a, const LsParams &prm, int ctas, 
     // persistent: as many CTAs as fit at once, or fewer when the caller leaves room for concurrent kernels
     const int fill = per_sm * sm_count();
     const int grid = (ctas > 0 && ctas < fill) ? ctas : fill;
+    // latency-bound (at most two seed groups per resident warp): pair the trials
+    LsParams p2 = prm;
+    p2.pair_trials = (a.n_seeds + P - 1) / P <= 2LL * grid * WARPS ? 1 : 0;
     PrioLaunch L(dim3(grid), dim3(WARPS * 32), smem, st);
-    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, kern, a, prm);
+    const cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, kern, a, p2);
     count_launches(1);
     return lerr != cudaSuccess ? lerr : cudaGetLastError();
 }

@@ -100,6 +100,7 @@ LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box) {
     prm.max_halvings = o->max_halvings;
     prm.cap = o->step_cap_cells;
     prm.box = GridDev{box->lo[0], box->lo[1], box->step[0], box->step[1], box->n[0], box->n[1]};
+    prm.pair_trials = 0;
     return prm;
 }
 
@@ -113,7 +114,10 @@ static cudaError_t launch_ls_t(const float4 *hits, int64_t n_hits, const int64_t
     if (aerr != cudaSuccess) return aerr;
     const int per_block = WARPS * P;
     dim3 grid((n_seeds + per_block - 1) / per_block, n_events);
-    kern<<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, boxes, n_seeds, seeds, prm, smem_hits, theta_out, R_out,
+    // latency-bound (at most two warps per warp slot of the GPU): pair the trials
+    LsParams p2 = prm;
+    p2.pair_trials = (int64_t)grid.x * grid.y * WARPS <= 2LL * sm_count() * 64 ? 1 : 0;
+    kern<<<grid, WARPS * 32, smem, st>>>(hits, n_hits, off, boxes, n_seeds, seeds, p2, smem_hits, theta_out, R_out,
                                          status, n_evals, work_counters());
     count_launches(1);
     return cudaGetLastError();

@@ -294,6 +294,11 @@ struct LsParams {
     int max_halvings;
     float cap;
     GridDev box;
+    // one-seed search: test the backtracking trials t and t/2 in one pass
+    // once t = 1 is rejected (the same results in fewer dependent passes,
+    // at the cost of the second point's terms when t is accepted); set by
+    // the launchers when the launch is latency-bound (few seeds per warp)
+    int pair_trials;
 };
 
 LsParams make_ls_params(const retina_ls_opts *o, const retina_grid *box);
@@ -659,14 +664,14 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         bool pending = true;
         Rfin = R;  // R at the point if no step is accepted
         const bool fuse = j + 1 < prm.q;
-        // the first trial (t = 1) alone; once it is rejected, the trials t and
-        // t / 2 share one pass (a block is skipped only when both points skip
+        // the first trial (t = 1) alone; once it is rejected, with
+        // prm.pair_trials, the trials t and t / 2 share one pass (a block is skipped only when both points skip
         // it, so each R is bitwise its own pass's) and are tested in order:
         // the accepted point, its R and the trial count are the sequential
         // backtracking's, in about half the dependent passes
         for (int hv = 0; hv <= prm.max_halvings && pending;) {
             const float tr0 = __fmaf_rn(t, pp0, th0), tr1 = __fmaf_rn(t, pp1, th1);
-            const bool two = hv > 0 && hv + 1 <= prm.max_halvings;
+            const bool two = prm.pair_trials && hv > 0 && hv + 1 <= prm.max_halvings;
             const float tb = t * 0.5f;
             const float tb0 = __fmaf_rn(tb, pp0, th0), tb1 = __fmaf_rn(tb, pp1, th1);
             float Rt = 0.f, Rb = 0.f;

@@ -71,11 +71,14 @@ def test_batched_matches_per_launch_search_bitwise(rt, update):
 
 
 @pytest.mark.parametrize("with_boxes", [False, True])
-@pytest.mark.parametrize("spw,warps", [(1, 8), (2, 16), (4, 32), (1, 32)])
-def test_batched_results_independent_of_order_and_shape(rt, spw, warps, with_boxes):
+@pytest.mark.parametrize("spw,warps,ctas", [(1, 8, 0), (2, 16, 0), (4, 32, 0), (1, 32, 0), (1, 8, 1)])
+def test_batched_results_independent_of_order_and_shape(rt, spw, warps, ctas, with_boxes):
     # one, two or four seeds per warp (shared block tests and hit loads, the
     # union of the seeds' kept blocks): the accepted trials, every sum and the
-    # trial counts must agree bit for bit, with exact block skipping on or off
+    # trial counts must agree bit for bit, with exact block skipping on or off;
+    # one seed per warp tests the backtracking trials in pairs when the launch
+    # has at most two seeds per warp (ctas 0: the whole GPU) and one at a time
+    # otherwise (one 8-warp CTA for the ~1000 seeds)
     wl, evs, b, seeds, so = _ragged(1)
     opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
     box = rt.Grid.of(wl)
@@ -84,12 +87,14 @@ def test_batched_results_independent_of_order_and_shape(rt, spw, warps, with_box
     boxes = bx if with_boxes else None
     S = len(seeds)
     ev_ref = torch.empty(S, dtype=torch.uint8, device="cuda")
-    old = (rt.get_option(rt.OPT_BATCH_SEEDS_PER_WARP), rt.get_option(rt.OPT_BATCH_WARPS))
+    old = (rt.get_option(rt.OPT_BATCH_SEEDS_PER_WARP), rt.get_option(rt.OPT_BATCH_WARPS),
+           rt.get_option(rt.OPT_BATCH_CTAS))
     try:
         rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, 2)
         ref = rt.batched_search(hits, offs, 1, _dev(seeds), _dev(so), opts, box, n_evals=ev_ref)
         rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, spw)
         rt.set_option(rt.OPT_BATCH_WARPS, warps)
+        rt.set_option(rt.OPT_BATCH_CTAS, ctas)
         order = _dev(np.array([3, 0, 4, 1, 2], np.int32))
         ev_got = torch.empty(S, dtype=torch.uint8, device="cuda")
         got = rt.batched_search(hits, offs, 1, _dev(seeds), _dev(so), opts, box, order=order, n_evals=ev_got,
@@ -97,6 +102,7 @@ def test_batched_results_independent_of_order_and_shape(rt, spw, warps, with_box
     finally:
         rt.set_option(rt.OPT_BATCH_SEEDS_PER_WARP, old[0])
         rt.set_option(rt.OPT_BATCH_WARPS, old[1])
+        rt.set_option(rt.OPT_BATCH_CTAS, old[2])
     for x, y in zip(ref, got):
         np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
     np.testing.assert_array_equal(ev_ref.cpu().numpy(), ev_got.cpu().numpy())
