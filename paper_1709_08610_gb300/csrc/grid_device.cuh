@@ -44,9 +44,10 @@ __device__ __forceinline__ bool block_zero_sep(const float4 A, const float4 B, c
     return du * du * z2k > GRID_CULL_EXPONENT || dv * dv * z2k > GRID_CULL_EXPONENT;
 }
 
-__global__ void grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
-                               const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0,
-                               float *__restrict__ out, int64_t split_stride, int64_t event_stride,
-                               unsigned long long *__restrict__ work, int32_t *__restrict__ err);
+// The tensor-core contraction (grid_tc.cu) on tiles of 128 x bn cells (bn =
+// 128 or 256), launched with programmatic serialization on stream st.
+cudaError_t launch_grid_tc(int bn, dim3 grid, cudaStream_t st, const float4 *hits, int64_t n_hits, const int64_t *off,
+                           const float4 *boxes, GridDev g, float kk, int splits, int tiles0, float *out,
+                           int64_t split_stride, int64_t event_stride, int32_t *err);
 
 }  // namespace retina

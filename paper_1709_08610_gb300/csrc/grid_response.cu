@@ -336,8 +336,17 @@ GridPlan plan_grid(int n_events, int model, const retina_grid *g, int flags, int
     const int tile = p.separable ? SEP_BM : DIR_TILE;
     p.tiles0 = (g->n[0] + tile - 1) / tile;
     p.tiles1 = (g->n[1] + tile - 1) / tile;
+    // tensor cores: 128 x 256 tiles (two CTAs per SM, a quarter less
+    // shared-memory traffic per multiply-add) when the 128 x 128 tiles would
+    // fill the GPU eight times over, else 128 x 128 (three CTAs per SM, more
+    // CTAs for few events)
+    p.tc_bn = 128;
+    if (p.tc && (int64_t)p.tiles0 * p.tiles1 * (n_events > 0 ? n_events : 1) >= 8LL * sm_count()) {
+        p.tc_bn = 256;
+        p.tiles1 = (g->n[1] + 255) / 256;
+    }
     const int64_t ctas = (int64_t)p.tiles0 * p.tiles1 * (n_events > 0 ? n_events : 1);
-    const int per_sm = p.tc ? 3 : (p.separable ? 2 : 4);
+    const int per_sm = p.tc ? (p.tc_bn == 256 ? 2 : 3) : (p.separable ? 2 : 4);
     const int64_t target = 4LL * sm_count() * per_sm;
     int64_t s = (target + ctas - 1) / ctas;
     if (s < 1) s = 1;
@@ -365,11 +374,8 @@ cudaError_t launch_grid_response(const GridPlan &p, const float4 *hits, int64_t 
     if (p.tc) {
         int32_t *flag = device_error_flag();
         if (!flag) return cudaErrorInvalidSymbol;
-        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(grid_tc_kernel), grid_tc_smem_bytes());
-        if (aerr != cudaSuccess) return aerr;
-        PrioLaunch L(grid, dim3(256), grid_tc_smem_bytes(), st, true);
-        cudaError_t lerr = cudaLaunchKernelEx(&L.cfg, grid_tc_kernel, hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0,
-                                              dst, split_stride, cells, work_counters(), flag);
+        cudaError_t lerr = launch_grid_tc(p.tc_bn, grid, st, hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst,
+                                          split_stride, cells, flag);
         if (lerr != cudaSuccess) return lerr;
     } else if (p.separable) {
         grid_sep_kernel<<<grid, SEP_THREADS, 0, st>>>(hits, n_hits, off, boxes, gd, kk, p.splits, p.tiles0, dst, split_stride, cells,

@@ -5,10 +5,14 @@
 //   R[j][i] = sum_k A[i][k] B[j][k],  A[i][k] = ex2(-(x_k - t_x,i z_k)^2 kk),
 //                                      B[j][k] = ex2(-(y_k - t_y,j z_k)^2 kk)
 // (the same exponentials, formed the same way, as grid_sep_kernel).  A CTA owns
-// a 128 x 128 tile of cells; for every 32-hit block that can contribute to the
-// tile (exact block skipping, as grid_sep_kernel) it builds the two 128 x 32
-// FP32 panels and accumulates A B^T into a 128 x 128 FP32 accumulator in
-// tensor memory with TF32 MMAs (M = N = 128, K = 8).  TF32 keeps 10 mantissa
+// a 128 x 256 tile of cells (128 theta_0 cells, 256 theta_1 cells); for every
+// 32-hit block that can contribute to the tile (exact block skipping, as
+// grid_sep_kernel) it builds the 128 x 32 and 256 x 32 FP32 panels and
+// accumulates A B^T into a 128 x 256 FP32 accumulator in tensor memory with
+// TF32 MMAs (M = 128, N = 256, K = 8).  The wide tile halves the A panels
+// built per cell and cuts the shared-memory traffic per multiply-add (panel
+// stores and the MMAs' operand reads, which share the shared-memory
+// bandwidth with the panel builds) by a quarter against a 128 x 128 tile.  TF32 keeps 10 mantissa
 // bits, so each panel is split into hi = (value with its 13 low mantissa bits
 // cleared) and lo = value - hi (exact), and three products hi.hi + hi.lo +
 // lo.hi are accumulated: every product is then within ~2^-19 of the FP32
@@ -21,19 +25,27 @@ namespace retina {
 
 namespace {
 
-constexpr int GT_BM = 128, GT_BN = 128, GT_BK = 32, GT_THREADS = 256;
-constexpr int GT_NCOLS = 128;                    // TMEM columns: the tile's 128 theta_1 cells
-constexpr int PANEL_BYTES = GT_BM * GT_BK * 4;   // 16 KB
-constexpr int OFF_AHI = 0, OFF_ALO = PANEL_BYTES, OFF_BHI = 2 * PANEL_BYTES, OFF_BLO = 3 * PANEL_BYTES;
-constexpr int OFF_HITS = 4 * PANEL_BYTES;        // the current block's 32 hits (float4)
-constexpr int OFF_MASK = OFF_HITS + GT_BK * 16;  // keep masks of the current window (8 x u32)
-constexpr int OFF_BAR = OFF_MASK + 32;           // mbarrier (8 B) + TMEM address (4 B)
-constexpr int GT_SMEM = OFF_BAR + 16;
+constexpr int GT_BM = 128, GT_BK = 32, GT_THREADS = 256;
+constexpr int PANEL_A = GT_BM * GT_BK * 4;       // 16 KB
+
+// shared-memory layout for tiles of BN (128 or 256) theta_1 cells: the A and
+// B panels (hi, lo), the current block's 32 hits (float4), the keep masks of
+// the current window (8 x u32), the mbarrier (8 B) and the TMEM address
+template <int BN>
+struct GtLayout {
+    static constexpr int PANEL_B = BN * GT_BK * 4;
+    static constexpr int OFF_AHI = 0, OFF_ALO = PANEL_A, OFF_BHI = 2 * PANEL_A, OFF_BLO = 2 * PANEL_A + PANEL_B;
+    static constexpr int OFF_HITS = 2 * PANEL_A + 2 * PANEL_B;
+    static constexpr int OFF_MASK = OFF_HITS + GT_BK * 16;
+    static constexpr int OFF_BAR = OFF_MASK + 32;
+    static constexpr int SMEM = OFF_BAR + 16;
+    // kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (format 2 at bits 7-9
+    // and 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((128u >> 4) << 24);
+};
 constexpr uint32_t GT_WAIT_LIMIT = 1u << 24;
 
-// kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (format 2 at bits 7-9 and
-// 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t GT_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -43,7 +55,7 @@ __device__ __forceinline__ uint64_t gt_desc(uint32_t addr, uint32_t lbo, uint32_
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// byte offset of element (row m, hit k) of a 128 x 32 FP32 K-major panel:
+// byte offset of element (row m, hit k) of a 128 (or 256) x 32 FP32 K-major panel:
 // core matrix (m / 8, k / 4) at (m / 8) * 1024 + (k / 4) * 128
 __device__ __forceinline__ int panel_off(int m, int k) { return (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4; }
 
@@ -70,12 +82,12 @@ __device__ __forceinline__ bool gt_wait(uint32_t addr, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void gt_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void gt_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(GT_IDESC), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void gt_ld32(uint32_t taddr, float (&v)[32]) {
@@ -98,11 +110,17 @@ __device__ __forceinline__ void gt_ld32(uint32_t taddr, float (&v)[32]) {
 
 // Grid over (tiles, hit slices, events) and partial layout as grid_sep_kernel;
 // the slices interleave 32-hit blocks instead of cutting contiguous ranges.
+// BN: the tile's theta_1 cells (128: three CTAs per SM; 256: two).
+template <int BN>
 __global__ void __launch_bounds__(GT_THREADS, 1)
 grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
                const float4 *__restrict__ boxes, GridDev g, float kk, int splits, int tiles0, float *__restrict__ out,
                int64_t split_stride, int64_t event_stride, unsigned long long *__restrict__ work,
                int32_t *__restrict__ err) {
+    using L = GtLayout<BN>;
+    constexpr int GT_BN = BN, GT_NCOLS = BN, NB = BN / 64;  // B rows per thread
+    constexpr int OFF_AHI = L::OFF_AHI, OFF_ALO = L::OFF_ALO, OFF_BHI = L::OFF_BHI, OFF_BLO = L::OFF_BLO;
+    constexpr int OFF_HITS = L::OFF_HITS, OFF_MASK = L::OFF_MASK, OFF_BAR = L::OFF_BAR;
     extern __shared__ __align__(1024) unsigned char gsm[];
     pdl_release();  // the slice reduction may be scheduled once every CTA has started
     pdl_wait();     // may be launched while the hit ordering finishes
@@ -128,13 +146,20 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    // panel role: lane l of warp w owns cells m = 8 (2w + a) + l / 4 (a = 0, 1)
-    // and hits k = 4 j + l % 4 (j = 0..7), so the 32 lanes of every store
-    // hit 32 different banks of the core-matrix layout
+    // panel role: lane l of warp w owns A rows (theta_0 cells) m = 8 (2w + a)
+    // + l / 4 (a = 0, 1), B rows (theta_1 cells) m + 128 c (c < BN / 128),
+    // and hits k = 4 j + l % 4 (j = 0..7), so the 32 lanes of every store hit
+    // 32 different banks of the core-matrix layout
     const int lm = lane >> 2, lk = lane & 3;
     const int m0 = 16 * warp + lm, m1 = m0 + 8;
     const float t0a = cell_centre(g.lo0, g.step0, ti0 + m0), t0b = cell_centre(g.lo0, g.step0, ti0 + m1);
-    const float t1a = cell_centre(g.lo1, g.step1, tj0 + m0), t1b = cell_centre(g.lo1, g.step1, tj0 + m1);
+    int mb[NB];
+    float t1[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        mb[c] = m0 + 8 * (c & 1) + 128 * (c >> 1);
+        t1[c] = cell_centre(g.lo1, g.step1, tj0 + mb[c]);
+    }
 
     // slice s takes the event's 32-hit blocks s, s + splits, s + 2 splits, ...:
     // the blocks a tile keeps cluster in the hits' spatial order, and
@@ -190,16 +215,20 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                 for (int j = 0; j < GT_BK / 4; ++j) {
                     const int kc = 4 * j + lk;
                     const int64_t k = kb + kc;
-                    float va0 = 0.f, va1 = 0.f, vb0 = 0.f, vb1 = 0.f;
+                    float va0 = 0.f, va1 = 0.f, vb[NB];
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) vb[c] = 0.f;
                     if (k < he) {
                         const float4 h = sh[kc];
                         // x - t_x z, y - t_y z with one rounding each, as grid_sep_kernel
                         const float u0 = __fmaf_rn(-t0a, h.z, h.x), u1 = __fmaf_rn(-t0b, h.z, h.x);
-                        const float v0 = __fmaf_rn(-t1a, h.z, h.y), v1 = __fmaf_rn(-t1b, h.z, h.y);
                         va0 = ex2_mufu(-(u0 * u0) * kk);
                         va1 = ex2_mufu(-(u1 * u1) * kk);
-                        vb0 = ex2_mufu(-(v0 * v0) * kk);
-                        vb1 = ex2_mufu(-(v1 * v1) * kk);
+#pragma unroll
+                        for (int c = 0; c < NB; ++c) {
+                            const float v = __fmaf_rn(-t1[c], h.z, h.y);
+                            vb[c] = ex2_mufu(-(v * v) * kk);
+                        }
                     }
                     float hi, lo;
                     const int o0 = panel_off(m0, kc), o1 = panel_off(m1, kc);
@@ -209,12 +238,13 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                     split_tf32(va1, hi, lo);
                     *reinterpret_cast<float *>(gsm + OFF_AHI + o1) = hi;
                     *reinterpret_cast<float *>(gsm + OFF_ALO + o1) = lo;
-                    split_tf32(vb0, hi, lo);
-                    *reinterpret_cast<float *>(gsm + OFF_BHI + o0) = hi;
-                    *reinterpret_cast<float *>(gsm + OFF_BLO + o0) = lo;
-                    split_tf32(vb1, hi, lo);
-                    *reinterpret_cast<float *>(gsm + OFF_BHI + o1) = hi;
-                    *reinterpret_cast<float *>(gsm + OFF_BLO + o1) = lo;
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) {
+                        const int ob = panel_off(mb[c], kc);
+                        split_tf32(vb[c], hi, lo);
+                        *reinterpret_cast<float *>(gsm + OFF_BHI + ob) = hi;
+                        *reinterpret_cast<float *>(gsm + OFF_BLO + ob) = lo;
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
@@ -227,9 +257,9 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
                         const uint64_t al = gt_desc(base + OFF_ALO + ks * 256, 128, 1024);
                         const uint64_t bh = gt_desc(base + OFF_BHI + ks * 256, 128, 1024);
                         const uint64_t bl = gt_desc(base + OFF_BLO + ks * 256, 128, 1024);
-                        gt_mma(tmem, ah, bh, (any || ks > 0) ? 1u : 0u);
-                        gt_mma(tmem, ah, bl, 1u);
-                        gt_mma(tmem, al, bh, 1u);
+                        gt_mma(tmem, ah, bh, L::IDESC, (any || ks > 0) ? 1u : 0u);
+                        gt_mma(tmem, ah, bl, L::IDESC, 1u);
+                        gt_mma(tmem, al, bh, L::IDESC, 1u);
                     }
                     asm volatile(
                         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_addr)
@@ -268,15 +298,15 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
             atomicAdd(work + RETINA_WORK_GRID, (unsigned long long)(done_hits * cw * ch));
         }
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (theta_0 cells) and
-        // columns 64 (w / 4) .. + 63 (theta_1 cells)
+        // columns 128 (w / 4) .. + 127 (theta_1 cells)
         const int q = warp & 3, half = warp >> 2;
         const int i = ti0 + 32 * q + lane;
         float *dst = out + (int64_t)s * split_stride + (int64_t)e * event_stride;
-#pragma unroll
-        for (int part = 0; part < 2; ++part) {
+#pragma unroll 1
+        for (int part = 0; part < GT_BN / 64; ++part) {
             float v[32];
             if (any) {
-                gt_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * half + 32 * part), v);
+                gt_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(GT_BN / 2 * half + 32 * part), v);
             } else {
 #pragma unroll
                 for (int c = 0; c < 32; ++c) v[c] = 0.f;
@@ -284,7 +314,7 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
             if (i < g.n0) {
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
-                    const int j = tj0 + 64 * half + 32 * part + c;
+                    const int j = tj0 + GT_BN / 2 * half + 32 * part + c;
                     if (j < g.n1) dst[(int64_t)j * g.n0 + i] = v[c];
                 }
             }
@@ -298,6 +328,25 @@ grid_tc_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *_
     }
 }
 
-size_t grid_tc_smem_bytes() { return GT_SMEM; }
+template <int BN>
+static cudaError_t launch_grid_tc_t(dim3 grid, cudaStream_t st, const float4 *hits, int64_t n_hits, const int64_t *off,
+                                   const float4 *boxes, GridDev g, float kk, int splits, int tiles0, float *out,
+                                   int64_t split_stride, int64_t event_stride, int32_t *err) {
+    const size_t smem = GtLayout<BN>::SMEM;
+    cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(grid_tc_kernel<BN>), smem);
+    if (aerr != cudaSuccess) return aerr;
+    PrioLaunch L(grid, dim3(GT_THREADS), smem, st, true);
+    return cudaLaunchKernelEx(&L.cfg, grid_tc_kernel<BN>, hits, n_hits, off, boxes, g, kk, splits, tiles0, out,
+                              split_stride, event_stride, work_counters(), err);
+}
+
+cudaError_t launch_grid_tc(int bn, dim3 grid, cudaStream_t st, const float4 *hits, int64_t n_hits, const int64_t *off,
+                           const float4 *boxes, GridDev g, float kk, int splits, int tiles0, float *out,
+                           int64_t split_stride, int64_t event_stride, int32_t *err) {
+    return bn == 256 ? launch_grid_tc_t<256>(grid, st, hits, n_hits, off, boxes, g, kk, splits, tiles0, out,
+                                             split_stride, event_stride, err)
+                     : launch_grid_tc_t<128>(grid, st, hits, n_hits, off, boxes, g, kk, splits, tiles0, out,
+                                             split_stride, event_stride, err);
+}
 
 }  // namespace retina

@@ -7,7 +7,8 @@ namespace retina {
 
 struct GridPlan {
     int separable;
-    int tc;  // separable contraction on the tensor cores
+    int tc;     // separable contraction on the tensor cores
+    int tc_bn;  // its tiles' theta_1 cells: 256 when the tiles fill the GPU, else 128
     int splits;
     int tiles0, tiles1;
 };
@@ -69,7 +70,6 @@ int max_dynamic_smem();
 cudaError_t ensure_dynamic_smem(const void *func, size_t bytes);
 unsigned long long *work_counters();
 int32_t *device_error_flag();
-size_t grid_tc_smem_bytes();
 int option_value(int option);
 cudaError_t launch_conv2_head_tc(const uint16_t *h1, int n_events, const float *params, uint16_t *h2, float *logits,
                                  int32_t *err, cudaStream_t st);

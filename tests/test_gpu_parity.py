@@ -142,6 +142,34 @@ def test_grid_response_full_size_sampled(rt, flags):
     assert R_g.min() >= 0 and R_g.max() <= ev.n_hits
 
 
+def test_grid_response_wide_tiles_on_a_batch(rt):
+    # a batch large enough for the 128 x 256 tensor-core tiles (the launch
+    # rule takes them from 8 x 152 tiles of 128 x 128 on), on a 1024 x 600
+    # window: the last tile column is ragged (88 cells); 3 of the 32 events
+    # against the oracle on sampled cells and the cells around the peaks
+    wl = WORKLOADS["velo_batch"]
+    evs = [make_event(wl, 3, e, vertex_sigma=(0, 0, 0)) for e in range(32)]
+    b = batch_of(evs)
+    n = (1024, 600)
+    lo = (wl.grid_lo[0], wl.grid_lo[1] + 200 * wl.grid_step[1])
+    grid = rt.Grid(lo, wl.grid_step, n)
+    R = torch.empty((len(evs), n[1], n[0]), dtype=torch.float32, device="cuda")
+    ws = torch.empty(max(rt.grid_response_workspace_size(len(evs), 1, grid), 1), dtype=torch.uint8, device="cuda")
+    offs = dev(b.offsets)
+    srt, bx = rt.prepare_hits(dev(b.hits), offs, 1)  # the bench's path: ordered hits, exact block skipping
+    rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, R_out=R, ws=ws, boxes=bx)
+    R_g = R.cpu().numpy().astype(float)
+    c0, c1 = oracle.cell_centres(lo, wl.grid_step, n)
+    rng = np.random.default_rng(2)
+    for e in (0, 17, 31):
+        idx = np.concatenate([rng.integers(0, n[0] * n[1], 1500), np.argsort(R_g[e].reshape(-1))[-300:],
+                              np.arange(n[0] * (n[1] - 1), n[0] * n[1])[::7]])  # the ragged last rows
+        i0, i1 = idx % n[0], idx // n[0]
+        R_o = oracle.response(evs[e].hits, 1, np.stack([c0[i0], c1[i1]], 1), wl.sigma_grid)
+        got = R_g[e].reshape(-1)[idx]
+        assert np.all(np.abs(got - R_o) <= R_REL * R_o + R_ABS), (e, np.max(np.abs(got - R_o)))
+
+
 # ---------------------------------------------------------------------------
 # grid maxima: exact on identical float32 inputs, tie-aware end to end
 # ---------------------------------------------------------------------------
