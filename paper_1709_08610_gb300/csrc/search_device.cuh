@@ -671,7 +671,11 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         // backtracking's, in about half the dependent passes
         for (int hv = 0; hv <= prm.max_halvings && pending;) {
             const float tr0 = __fmaf_rn(t, pp0, th0), tr1 = __fmaf_rn(t, pp1, th1);
-            const bool two = prm.pair_trials && hv > 0 && hv + 1 <= prm.max_halvings;
+            // (compiled into the truncated Newton search only: the comparison
+            // updates run throughput-bound batches, where the extra pass body
+            // would only crowd the instruction cache)
+            constexpr bool PAIRS = UPD == RETINA_UPDATE_TRUNCATED_NEWTON;
+            const bool two = PAIRS && prm.pair_trials && hv > 0 && hv + 1 <= prm.max_halvings;
             const float tb = t * 0.5f;
             const float tb0 = __fmaf_rn(tb, pp0, th0), tb1 = __fmaf_rn(tb, pp1, th1);
             float Rt = 0.f, Rb = 0.f;
@@ -694,7 +698,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
                     });
                 acc.sums(S);
                 w_rgh += (uint32_t)vis;
-            } else if (two) {
+            } else if (PAIRS && two) {
                 const CullPt ca = cull_pt<MODEL>(tr0, tr1, kk, cull), cb = cull_pt<MODEL>(tb0, tb1, kk, cull);
                 auto need2 = [&](const float4 A, const float z2) {
                     return !box_culled<MODEL>(A, z2, ca) || !box_culled<MODEL>(A, z2, cb);
