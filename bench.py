@@ -275,6 +275,15 @@ def oracle_threads() -> int:
 # batched methods: grid scan vs uniform multistart vs learned seeds
 # ---------------------------------------------------------------------------
 
+def batch_shape(hits_per_event: float) -> dict:
+    """Launch shape of the throughput-bound batched search: spatially ordered
+    seeds, 32-warp CTAs staging up to 12288 hits, and four seeds per warp (two
+    packed FP32x2 pairs sharing the box tests, block lists and hit loads) on
+    high-multiplicity events, two on smaller ones, where a pass has fewer hits
+    to share those costs over (measured fastest on each workload)."""
+    return dict(sort_seeds=True, seeds_per_warp=4 if hits_per_event > 8192 else 2, warps=32, smem_hits=12288)
+
+
 BATCH_EVENTS = 1024
 BATCH_RUN_SEED = 5000
 
@@ -323,10 +332,7 @@ def batched_methods(rt, stream, flush, workload: str = "velo_batch", learned_k: 
         return statistics.median(ts)
 
     n0, n1 = wl.grid_n
-    # throughput-bound batches: spatially ordered seeds, two per warp, 32-warp
-    # CTAs staging up to 12288 hits (measured fastest on both batch workloads:
-    # ~16 % over one unordered seed per warp, more on high-multiplicity events)
-    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    shape = batch_shape(H / E)
     seeds4096 = np.stack([uniform_seeds(wl, 4096, BATCH_RUN_SEED, e) for e in range(E)])
     runs = [("grid_scan_%dx%d" % (n0, n1), lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
             ("grid_scan_%dx%d_refined" % (n0, n1),
@@ -438,7 +444,7 @@ def alpha_sweep(rt, stream, flush, reps: int = 3):
     H = b.hits.shape[0]
     box = rt.Grid.of(wl)
     opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
-    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    shape = batch_shape(H / E)
     prop = SeedProposer.from_checkpoint(DEFAULT_WEIGHTS) if os.path.exists(DEFAULT_WEIGHTS) else None
     edges = sorted(set(ALPHA_MULTIPLICITIES)) + [ALPHA_MULTIPLICITIES[-1] + 1]
     n0, n1 = wl.grid_n
@@ -564,7 +570,7 @@ def svelo_sweep(rt, stream, flush, reps: int = 3):
     H = b.hits.shape[0]
     box = rt.Grid.of(wl)
     opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
-    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    shape = batch_shape(H / E)
     edges = list(SVELO_MULTIPLICITIES) + [SVELO_MULTIPLICITIES[-1] + 1]
     n_grid = (2 * 0.705 / 1e-3) ** 2
     runs = [("grid_scan_2048x2048", lambda: GridScanBatch(E, H, box, wl.sigma_grid, wl.R0), None),
@@ -1149,8 +1155,7 @@ def headline(rt, args, dev, rank, world, peaks, local_rank):
     params = read_checkpoint(DEFAULT_WEIGHTS)[1]["params"]
     box = rt.Grid.of(wl)
     opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
-    # throughput-bound batch: two spatially ordered seeds per warp, 32-warp CTAs, 12288 staged hits
-    shape = dict(sort_seeds=True, seeds_per_warp=2, warps=32, smem_hits=12288)
+    shape = batch_shape(H / E)
     tr = rt.Tracker(box, opts, wl.R0, wl.merge_cells, E, H, S, max_tracks=K, params=params, **shape)
     tr.load(b.hits, b.offsets)
     marks = [torch.cuda.Event(enable_timing=True) for _ in range(6)]

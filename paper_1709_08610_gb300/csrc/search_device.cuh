@@ -838,7 +838,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
         }
         const CullSpan span = cull_span<P>(th0, th1, live, cull);
         auto needed = [&](const float4 A, const float z2) {
-            if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span);
+            if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span);
             bool need = false;
 #pragma unroll
             for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, z2, cp[p]);
@@ -846,18 +846,30 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
         };
         float S[P][NS];
         int vis;
-        if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) {
-            // both points' sums in packed FP32x2 (bitwise the scalar sums)
-            RghAcc2 a2;
-            a2.set(th0[0], th1[0], th0[1], th1[1], kk);
-            a2.zero();
+        if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) {
+            // the points' sums in packed FP32x2, two points per register pair
+            // (bitwise the scalar sums)
+            constexpr int NP = P / 2;
+            RghAcc2 a2[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                a2[q].set(th0[2 * q], th1[2 * q], th0[2 * q + 1], th1[2 * q + 1], kk);
+                a2[q].zero();
+            }
             vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
-                                         [&](const float4 h) { a2.add(h); },
-                                         [&](const float4 a, const float4 b) {
-                                             a2.add(a);
-                                             a2.add(b);
-                                         });
-            a2.sums(S[0], S[1]);
+                                  [&](const float4 h) {
+#pragma unroll
+                                      for (int q = 0; q < NP; ++q) a2[q].add(h);
+                                  },
+                                  [&](const float4 a, const float4 b) {
+#pragma unroll
+                                      for (int q = 0; q < NP; ++q) {
+                                          a2[q].add(a);
+                                          a2[q].add(b);
+                                      }
+                                  });
+#pragma unroll
+            for (int q = 0; q < NP; ++q) a2[q].sums(S[2 * q], S[2 * q + 1]);
         } else {
             vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
                                           [&](const float4 h) {
@@ -909,26 +921,40 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             }
             const CullSpan span_r = cull_span<P>(tr0, tr1, pending, cull);
             auto needed_r = [&](const float4 A, const float z2) {
-                if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span_r);
+                if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span_r);
                 bool need = false;
 #pragma unroll
                 for (int p = 0; p < P; ++p) need |= pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
                 return need;
             };
             int vis;
-            if constexpr (P == 2 && MODEL == RETINA_VELO_SLOPES) {
-                // both trial points in packed FP32x2; a point whose line search
-                // is over accumulates too, and its sum is not used
-                const unsigned long long nt0 = pack2(-tr0[0], -tr0[1]), nt1 = pack2(-tr1[0], -tr1[1]);
+            if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) {
+                // the trial points in packed FP32x2, two per register pair; a
+                // point whose line search is over accumulates too, and its sum
+                // is not used
+                constexpr int NP = P / 2;
+                unsigned long long nt0[NP], nt1[NP], Rt2[NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    nt0[q] = pack2(-tr0[2 * q], -tr0[2 * q + 1]);
+                    nt1[q] = pack2(-tr1[2 * q], -tr1[2 * q + 1]);
+                    Rt2[q] = 0ull;
+                }
                 const unsigned long long nkk = pack2(-kk, -kk);
-                unsigned long long Rt2 = 0ull;
                 vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed_r,
-                                             [&](const float4 h) { pair_r_x2(h, nt0, nt1, nkk, Rt2); },
-                                             [&](const float4 a, const float4 b) {
-                                                 pair_r_x2(a, nt0, nt1, nkk, Rt2);
-                                                 pair_r_x2(b, nt0, nt1, nkk, Rt2);
-                                             });
-                unpack2(Rt2, Rt[0], Rt[1]);
+                                      [&](const float4 h) {
+#pragma unroll
+                                          for (int q = 0; q < NP; ++q) pair_r_x2(h, nt0[q], nt1[q], nkk, Rt2[q]);
+                                      },
+                                      [&](const float4 a, const float4 b) {
+#pragma unroll
+                                          for (int q = 0; q < NP; ++q) {
+                                              pair_r_x2(a, nt0[q], nt1[q], nkk, Rt2[q]);
+                                              pair_r_x2(b, nt0[q], nt1[q], nkk, Rt2[q]);
+                                          }
+                                      });
+#pragma unroll
+                for (int q = 0; q < NP; ++q) unpack2(Rt2[q], Rt[2 * q], Rt[2 * q + 1]);
             } else {
                 vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed_r,
                                               [&](const float4 h) {

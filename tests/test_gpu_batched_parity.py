@@ -4,7 +4,7 @@ events, against the FP64 oracle event by event:
 
 * 1024-event VELO-like batch (tracks ~ Poisson(150), smeared vertex): 4
   events, 4096 uniform seeds each through BatchTracker in the throughput
-  shape (spatially sorted seeds, two per warp, 32-warp CTAs) - found-track
+  shape (spatially sorted seeds, four per warp, 32-warp CTAs) - found-track
   sets equal up to near-ties; the whole 1024^2 grid of each event through
   GridScanBatch - maxima and tracks equal up to near-ties;
 * high-multiplicity batch (Poisson(600) tracks, ~16.8k hits: more hits than
@@ -39,7 +39,7 @@ def _batched_search_sets(rt, wl, evs, n_seeds):
     box = rt.Grid.of(wl)
     opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
     tr = BatchTracker(E, b.hits.shape[0], n_seeds, box, opts, wl.R0, max_tracks=4096, sort_seeds=True,
-                      seeds_per_warp=2, warps=32, smem_hits=12288)
+                      seeds_per_warp=4, warps=32, smem_hits=12288)
     seeds = np.stack([uniform_seeds(wl, n_seeds, RUN_SEED, e) for e in range(E)])
     tr.load(b.hits, b.offsets, seeds)
     tr.step()
