@@ -3,10 +3,11 @@
 // Eq. 1 is zero in float32.
 //
 // Per event (one CTA, chunks of up to SORT_CAP hits): each hit gets a 32-bit
-// key - a 17-bit spatial code above its 13-bit index in the chunk, so keys are
-// distinct and the order is deterministic - and the chunk is sorted by key.
-// Slope model: the code is a band of |z| (octaves from 16 mm) over a 14-bit
-// Morton code of the hit's slopes (u, v) = (x/z, y/z) quantised on [-1, 1],
+// key - a spatial code of up to 19 bits above its 13-bit index in the chunk,
+// so keys are distinct and the order is deterministic - and the chunk is
+// sorted by key.  Slope model: the code is a band of |z| (octaves from 16 mm)
+// over a 16-bit Morton code of the hit's slopes (u, v) = (x/z, y/z)
+// quantised on [-1, 1] (slopes beyond are clamped to the edges),
 // and the box of a block is (umin, umax, vmin, vmax, |z|min, |z|max): since
 // s^2 = z^2 |(u, v) - theta|^2, it bounds s^2 from below by
 // |z|min^2 dist(theta, box)^2.  2D toy: the code is a band of x over the
@@ -27,32 +28,33 @@ constexpr int PREP_THREADS = 1024;
 constexpr int IDX_BITS = 13;
 constexpr int SORT_CAP = 1 << IDX_BITS;  // 8192 hits per chunk
 
-// Spread the 7 low bits of v to the even bit positions 0, 2, ..., 12.
-__device__ __forceinline__ uint32_t spread7(uint32_t v) {
-    v &= 0x7fu;
+// Spread the 8 low bits of v to the even bit positions 0, 2, ..., 14.
+__device__ __forceinline__ uint32_t spread8(uint32_t v) {
+    v &= 0xffu;
     v = (v | (v << 4)) & 0x0f0fu;
     v = (v | (v << 2)) & 0x3333u;
     v = (v | (v << 1)) & 0x5555u;
     return v;
 }
 
-__device__ __forceinline__ uint32_t quant7(float v, float lo, float inv_range) {
+// v quantised on [lo, lo + 1 / inv_range] to the integers 0 .. levels
+__device__ __forceinline__ uint32_t quant(float v, float lo, float inv_range, float levels) {
     float t = (v - lo) * inv_range;
     t = isfinite(t) ? fminf(fmaxf(t, 0.f), 1.f) : (t > 0.f ? 1.f : 0.f);
-    return (uint32_t)(t * 127.f);
+    return (uint32_t)(t * levels);
 }
 
-// 17-bit spatial code of a hit (only orders the hits; any value is valid)
+// spatial code of a hit, below 2^19 (only orders the hits; any value is valid)
 __device__ __forceinline__ uint32_t hit_code(const float4 h, int model) {
     if (model == RETINA_VELO_SLOPES) {
         const float az = fabsf(h.z);
         uint32_t band = 0;  // |z| octaves: [0,16), [16,32), ..., [512, inf)
         for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
         const float rz = __frcp_rn(h.z);
-        const uint32_t m = spread7(quant7(h.x * rz, -1.f, 0.5f)) | (spread7(quant7(h.y * rz, -1.f, 0.5f)) << 1);
-        return (band << 14) | m;
+        const uint32_t m = spread8(quant(h.x * rz, -1.f, 0.5f, 255.f)) | (spread8(quant(h.y * rz, -1.f, 0.5f, 255.f)) << 1);
+        return (band << 16) | m;
     }
-    return ((float_order_key(h.x) >> 25) << 7) | quant7(h.y, -8.f, 1.f / 16.f);
+    return ((float_order_key(h.x) >> 25) << 7) | quant(h.y, -8.f, 1.f / 16.f, 127.f);
 }
 
 // Keys of chunk positions t R + r (padding ~0 sorts last), sorted, then the
