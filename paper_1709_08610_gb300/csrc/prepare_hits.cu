@@ -283,7 +283,10 @@ int64_t prepared_box_count(int64_t n_hits, int n_events) { return n_hits / 32 + 
 
 cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_t *off, int n_events, int model,
                                 float4 *sorted, float4 *boxes, cudaStream_t st) {
-    if ((int64_t)n_events * CL <= (int64_t)INT32_MAX) {
+    // few events (latency): a cluster of CL SMs per event; batches that fill
+    // the GPU many times over (throughput): one CTA per event, no cluster
+    // exchanges
+    if ((int64_t)n_events * CL <= 4LL * sm_count()) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(n_events * CL));
         cfg.blockDim = dim3(CL_THREADS);

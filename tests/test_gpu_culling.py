@@ -69,6 +69,27 @@ def test_prepared_hits_are_a_permutation_with_bounding_boxes(rt, model):
             assert np.median(side) <= 0.3, np.median(side)
 
 
+def test_batch_ordering_is_bitwise_the_per_event_ordering(rt):
+    # a batch that fills the GPU many times over is ordered one CTA per event,
+    # a single event by a cluster of CTAs: the same keys and total order, so
+    # the same sorted hits and boxes, bit for bit (events with two sort chunks
+    # and an empty one included)
+    wl = WORKLOADS["velo_batch"]
+    evs = [make_event(wl, 5, e, vertex_sigma=(0, 0, 0)) for e in range(120)]
+    evs[7] = make_event(WORKLOADS["velo"], 5, 7, n_tracks=700, vertex_sigma=(0, 0, 0))
+    evs[11] = make_event(WORKLOADS["velo"], 5, 11, n_tracks=0, noise_frac=0.0)
+    b = batch_of(evs)
+    assert len(evs) * 8 > 4 * torch.cuda.get_device_properties(0).multi_processor_count
+    srt, boxes = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), 1)
+    srt, boxes = srt.cpu().numpy(), boxes.cpu().numpy()
+    for e in (0, 7, 11, 63, 119):
+        h0, h1 = b.offsets[e], b.offsets[e + 1]
+        s1, b1 = rt.prepare_hits(_dev(b.hits[h0:h1]), _dev(np.array([0, h1 - h0], np.int64)), 1)
+        np.testing.assert_array_equal(srt[h0:h1], s1.cpu().numpy())
+        nb = (h1 - h0 + 31) // 32
+        np.testing.assert_array_equal(boxes[h0 // 32 + e:h0 // 32 + e + nb], b1.cpu().numpy()[:nb])
+
+
 @pytest.mark.parametrize("flags", [1, 2, 3])
 def test_grid_response_with_boxes_is_bitwise_the_full_sum(rt, flags):
     wl, evs, b = _batch(1)
