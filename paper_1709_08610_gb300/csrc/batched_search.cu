@@ -66,6 +66,14 @@ __device__ __forceinline__ int64_t n_groups_of(const BatchArgs &a, int e) {
     return (s1 - s0 + P - 1) / P;
 }
 
+template <int MODEL, int P>
+__host__ __device__ constexpr bool batch_smem_state() { return P == 4 && MODEL == RETINA_VELO_SLOPES; }
+
+template <int MODEL, int P>
+constexpr size_t batch_state_bytes(int warps) {
+    return batch_smem_state<MODEL, P>() ? (size_t)warps * ((sizeof(GroupState<P>) + 15) / 16 * 16) : 0;
+}
+
 // at most 64 registers per thread: 2048 / (32 WARPS) CTAs of WARPS warps fit the register file
 template <int MODEL, int P, int WARPS, int UPD>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(BatchArgs a, LsParams prm) {
@@ -78,6 +86,14 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
     float4 *ssb = staged_super_bounds(sh, a.smem_hits, a.box_cap);
     float *ssz2 = staged_super_z2(sh, a.smem_hits, a.box_cap);
     int *list = kept_list(sh, a.smem_hits, a.box_cap, tid >> 5);
+    // four seeds per warp keep their warp-uniform state in shared memory, one
+    // copy per warp after the lists (see batch_state_bytes)
+    constexpr bool SS = batch_smem_state<MODEL, P>();
+    GroupState<P> *gstate = nullptr;
+    if constexpr (SS)
+        gstate = reinterpret_cast<GroupState<P> *>(reinterpret_cast<unsigned char *>(sh) +
+                                                   search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS,
+                                                                     a.box_cap)) + (tid >> 5);
     int staged = -1;
     int n_staged = 0, n_sbox = 0;
     for (int64_t round = 0; round < a.max_rounds; ++round) {
@@ -132,9 +148,9 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             if (g >= groups) break;
             const int64_t s = s0 + (int64_t)g * P;
             const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
-            search_group<MODEL, P, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, a.seeds + 2 * s, n_live, prm,
-                                   a.theta_out + 2 * s,
-                                   a.R_out + s, a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work);
+            search_group<MODEL, P, UPD, SS>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
+                                            a.seeds + 2 * s, n_live, prm, a.theta_out + 2 * s, a.R_out + s,
+                                            a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work, gstate);
         }
         __syncthreads();  // all warps done with the staged hits before the next round
         if (round + 1 == a.max_rounds && tid == 0) atomicExch(&a.counters[1], 1);
@@ -151,14 +167,15 @@ static cudaError_t launch_batched_t(BatchArgs a, const LsParams &prm, int ctas, 
     a.box_cap = default_box_cap(a.smem_hits);
     if (a.boxes) {
         const size_t avail = (size_t)max_dynamic_smem() - 1024;  // static shared memory and a margin
-        const size_t fixed = (size_t)a.smem_hits * 16 + search_list_bytes(WARPS);
+        const size_t fixed = (size_t)a.smem_hits * 16 + search_list_bytes(WARPS) + batch_state_bytes<MODEL, P>(WARPS);
         if (avail > fixed) {
             int cap = (int)((avail - fixed) / 25) & ~3;  // 20 B per block box + 5 B of its superblock's
             cap = cap > 4096 ? 4096 : cap;
             if (cap > a.box_cap) a.box_cap = cap;
         }
     }
-    const size_t smem = search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS, a.box_cap);
+    const size_t smem =
+        search_smem_bytes(a.smem_hits, a.boxes != nullptr, WARPS, a.box_cap) + batch_state_bytes<MODEL, P>(WARPS);
     cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (aerr != cudaSuccess) return aerr;
     int per_sm = 0;

@@ -795,7 +795,15 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
 // at bandwidth sigma_j), then R(theta_q; sigma_q), status and the number of
 // R-only passes.  seeds / outputs point at the group's first seed; only the
 // first n_live (<= P) seeds exist.  Warp-uniform control flow throughout.
-template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
+// The per-point state of search_group kept across passes.
+template <int P>
+struct GroupState {
+    float th0[P], th1[P], Rfin[P], R[P], pp0[P], pp1[P], slope[P], t[P];
+    int evals[P];
+    bool live[P], failed[P], pending[P];
+};
+
+template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON, bool SS = false>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
                                              int n_staged, int H, int lane, const float4 *__restrict__ sbox,
                                              const float *__restrict__ sz2, const float4 *__restrict__ ssb,
@@ -804,7 +812,8 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                              const float *__restrict__ seeds,
                                              int n_live, const LsParams &prm, float *__restrict__ theta_out,
                                              float *__restrict__ R_out, uint8_t *__restrict__ status,
-                                             uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work) {
+                                             uint8_t *__restrict__ n_evals, unsigned long long *__restrict__ work,
+                                             GroupState<P> *state = nullptr) {
     if constexpr (P == 1) {
         search_one<MODEL, UPD>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, seeds, prm, theta_out, R_out,
                           status, n_evals, work);
@@ -812,18 +821,19 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     }
     uint32_t w_rgh = 0, w_r = 0;  // (point, hit) pairs visited (fewer than 2^32 per group)
     constexpr int NS = Model<MODEL>::NS;
-    float th0[P], th1[P], Rfin[P];
-    int evals[P];
-    bool live[P], failed[P];
+    // the points' state between passes: warp-uniform, in registers, or (SS)
+    // once per warp in shared memory, where 32 lanes' copies would spill
+    GroupState<P> gs_local;
+    GroupState<P> &gs = SS ? *state : gs_local;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        live[p] = p < n_live;
-        const int o = (live[p] ? p : 0) * 2;
-        th0[p] = seeds[o];
-        th1[p] = seeds[o + 1];
-        failed[p] = false;
-        evals[p] = 0;
-        Rfin[p] = 0.f;
+        gs.live[p] = p < n_live;
+        const int o = (gs.live[p] ? p : 0) * 2;
+        gs.th0[p] = seeds[o];
+        gs.th1[p] = seeds[o + 1];
+        gs.failed[p] = false;
+        gs.evals[p] = 0;
+        gs.Rfin[p] = 0.f;
     }
 
     for (int j = 0; j < prm.q; ++j) {
@@ -834,14 +844,14 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             acc[p].zero();
-            cp[p] = cull_pt<MODEL>(th0[p], th1[p], kk, cull);
+            cp[p] = cull_pt<MODEL>(gs.th0[p], gs.th1[p], kk, cull);
         }
-        const CullSpan span = cull_span<P>(th0, th1, live, cull);
+        const CullSpan span = cull_span<P>(gs.th0, gs.th1, gs.live, cull);
         auto needed = [&](const float4 A, const float z2) {
             if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span);
             bool need = false;
 #pragma unroll
-            for (int p = 0; p < P; ++p) need |= live[p] && !box_culled<MODEL>(A, z2, cp[p]);
+            for (int p = 0; p < P; ++p) need |= gs.live[p] && !box_culled<MODEL>(A, z2, cp[p]);
             return need;
         };
         float S[P][NS];
@@ -853,7 +863,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             RghAcc2 a2[NP];
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                a2[q].set(th0[2 * q], th1[2 * q], th0[2 * q + 1], th1[2 * q + 1], kk);
+                a2[q].set(gs.th0[2 * q], gs.th1[2 * q], gs.th0[2 * q + 1], gs.th1[2 * q + 1], kk);
                 a2[q].zero();
             }
             vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
@@ -874,57 +884,56 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
                                           [&](const float4 h) {
 #pragma unroll
-                                              for (int p = 0; p < P; ++p) acc[p].add(h, th0[p], th1[p], kk);
+                                              for (int p = 0; p < P; ++p) acc[p].add(h, gs.th0[p], gs.th1[p], kk);
                                           },
                                           [&](const float4 a, const float4 b) {
 #pragma unroll
-                                              for (int p = 0; p < P; ++p) acc[p].add2(a, b, th0[p], th1[p], kk);
+                                              for (int p = 0; p < P; ++p) acc[p].add2(a, b, gs.th0[p], gs.th1[p], kk);
                                           });
 #pragma unroll
             for (int p = 0; p < P; ++p) acc[p].sums(S[p]);
         }
         w_rgh += (uint32_t)vis * (uint32_t)n_live;
-        float R[P], g0[P], g1[P], pp0[P], pp1[P], slope[P], t[P];
-        bool pending[P];
+        float g0[P], g1[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
 #pragma unroll
             for (int i = 0; i < NS; ++i) S[p][i] = warp_sum(S[p][i]);
             float H00, H01, H11;
-            sums_to_rgh<MODEL>(S[p], k, R[p], g0[p], g1[p], H00, H01, H11);
-            update_direction<UPD>(g0[p], g1[p], H00, H01, H11, pp0[p], pp1[p]);
-            const float cells = fmaxf(fabsf(pp0[p]) / prm.box.step0, fabsf(pp1[p]) / prm.box.step1);
+            sums_to_rgh<MODEL>(S[p], k, gs.R[p], g0[p], g1[p], H00, H01, H11);
+            update_direction<UPD>(g0[p], g1[p], H00, H01, H11, gs.pp0[p], gs.pp1[p]);
+            const float cells = fmaxf(fabsf(gs.pp0[p]) / prm.box.step0, fabsf(gs.pp1[p]) / prm.box.step1);
             if (cells > prm.cap) {
                 const float sc = prm.cap / cells;
-                pp0[p] *= sc;
-                pp1[p] *= sc;
+                gs.pp0[p] *= sc;
+                gs.pp1[p] *= sc;
             }
-            slope[p] = g0[p] * pp0[p] + g1[p] * pp1[p];
-            t[p] = 1.f;
-            pending[p] = live[p];
-            Rfin[p] = R[p];  // R at the point if no step is accepted
+            gs.slope[p] = g0[p] * gs.pp0[p] + g1[p] * gs.pp1[p];
+            gs.t[p] = 1.f;
+            gs.pending[p] = gs.live[p];
+            gs.Rfin[p] = gs.R[p];  // R at the point if no step is accepted
         }
         // backtracking line search, all pending seeds of the warp together
         for (int hv = 0; hv <= prm.max_halvings; ++hv) {
             bool any = false;
 #pragma unroll
-            for (int p = 0; p < P; ++p) any |= pending[p];
+            for (int p = 0; p < P; ++p) any |= gs.pending[p];
             if (!any) break;
             float tr0[P], tr1[P], Rt[P];
             CullPt ct[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                tr0[p] = __fmaf_rn(t[p], pp0[p], th0[p]);
-                tr1[p] = __fmaf_rn(t[p], pp1[p], th1[p]);
+                tr0[p] = __fmaf_rn(gs.t[p], gs.pp0[p], gs.th0[p]);
+                tr1[p] = __fmaf_rn(gs.t[p], gs.pp1[p], gs.th1[p]);
                 Rt[p] = 0.f;
                 ct[p] = cull_pt<MODEL>(tr0[p], tr1[p], kk, cull);
             }
-            const CullSpan span_r = cull_span<P>(tr0, tr1, pending, cull);
+            const CullSpan span_r = cull_span<P>(tr0, tr1, gs.pending, cull);
             auto needed_r = [&](const float4 A, const float z2) {
                 if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span_r);
                 bool need = false;
 #pragma unroll
-                for (int p = 0; p < P; ++p) need |= pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
+                for (int p = 0; p < P; ++p) need |= gs.pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
                 return need;
             };
             int vis;
@@ -960,37 +969,37 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                               [&](const float4 h) {
 #pragma unroll
                                                   for (int p = 0; p < P; ++p)
-                                                      if (pending[p])
+                                                      if (gs.pending[p])
                                                           Rt[p] = __fadd_rn(Rt[p], pair_r<MODEL>(h, tr0[p], tr1[p], kk));
                                               },
                                               [&](const float4 a, const float4 b) {
 #pragma unroll
                                                   for (int p = 0; p < P; ++p)
-                                                      if (pending[p]) pair_r2<MODEL>(a, b, tr0[p], tr1[p], kk, Rt[p]);
+                                                      if (gs.pending[p]) pair_r2<MODEL>(a, b, tr0[p], tr1[p], kk, Rt[p]);
                                               });
             }
             int n_pend = 0;
 #pragma unroll
-            for (int p = 0; p < P; ++p) n_pend += pending[p] ? 1 : 0;
+            for (int p = 0; p < P; ++p) n_pend += gs.pending[p] ? 1 : 0;
             w_r += (uint32_t)vis * (uint32_t)n_pend;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (!pending[p]) continue;
-                ++evals[p];
+                if (!gs.pending[p]) continue;
+                ++gs.evals[p];
                 const float rt = warp_sum(Rt[p]);
-                if (rt >= R[p] + prm.c1 * t[p] * slope[p]) {
-                    th0[p] = tr0[p];
-                    th1[p] = tr1[p];
-                    Rfin[p] = rt;  // R at the accepted point, this update's bandwidth
-                    pending[p] = false;
+                if (rt >= gs.R[p] + prm.c1 * gs.t[p] * gs.slope[p]) {
+                    gs.th0[p] = tr0[p];
+                    gs.th1[p] = tr1[p];
+                    gs.Rfin[p] = rt;  // R at the accepted point, this update's bandwidth
+                    gs.pending[p] = false;
                 } else {
-                    t[p] *= 0.5f;
+                    gs.t[p] *= 0.5f;
                 }
             }
         }
 #pragma unroll
         for (int p = 0; p < P; ++p)
-            if (pending[p]) failed[p] = true;
+            if (gs.pending[p]) gs.failed[p] = true;
     }
 
     // After the last update Rfin holds R(theta_q; sigma_q): the accepted
@@ -1004,19 +1013,19 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     const float hi1 = prm.box.lo1 + (float)prm.box.n1 * prm.box.step1;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        if (!live[p] || lane != 0) continue;
+        if (!gs.live[p] || lane != 0) continue;
         uint8_t st;
-        if (!(isfinite(th0[p]) && isfinite(th1[p]) && isfinite(Rfin[p])))
+        if (!(isfinite(gs.th0[p]) && isfinite(gs.th1[p]) && isfinite(gs.Rfin[p])))
             st = 3;
-        else if (!(th0[p] >= prm.box.lo0 && th0[p] < hi0 && th1[p] >= prm.box.lo1 && th1[p] < hi1))
+        else if (!(gs.th0[p] >= prm.box.lo0 && gs.th0[p] < hi0 && gs.th1[p] >= prm.box.lo1 && gs.th1[p] < hi1))
             st = 2;
         else
-            st = failed[p] ? 1 : 0;
-        theta_out[2 * p] = th0[p];
-        theta_out[2 * p + 1] = th1[p];
-        R_out[p] = Rfin[p];
+            st = gs.failed[p] ? 1 : 0;
+        theta_out[2 * p] = gs.th0[p];
+        theta_out[2 * p + 1] = gs.th1[p];
+        R_out[p] = gs.Rfin[p];
         status[p] = st;
-        if (n_evals) n_evals[p] = (uint8_t)(evals[p] < 255 ? evals[p] : 255);
+        if (n_evals) n_evals[p] = (uint8_t)(gs.evals[p] < 255 ? gs.evals[p] : 255);
     }
 }
 
