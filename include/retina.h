@@ -198,10 +198,16 @@ int retina_alu_probe(int32_t kind, int32_t iters, float *sink, double *ops, void
  * sorts the hits into a spatial order and writes them to sorted_out
  * (float32 [n_hits][4], same event offsets); block b of event e (sorted hits
  * 32 b .. 32 b + 31) gets an 8-float box in boxes_out row
- * floor(event_offsets[e] / 32) + e + b.  Slope model: hits ordered by |z|
- * octave, then Morton order of their slopes (x/z, y/z); box = (min, max of
- * x/z, min, max of y/z, min, max of |z|, 0, 0).  2D toy: ordered by x band,
- * then y; box = (xmin, xmax, ymin, ymax, 0, 0, 0, 0).  boxes_out: float32
+ * floor(event_offsets[e] / 32) + e + b.  Order: per super-chunk of 32768
+ * consecutive hits of an event, the hits are grouped by band (stably), each
+ * band's run is cut into chunks of 8192, and each chunk is sorted by (code,
+ * position in the chunk); a super-chunk of at most 8192 hits is one chunk.
+ * Slope model: band = octave of |z| ([0,16), [16,32), ..., [512, inf) mm;
+ * NaN in the last), code = band above the Hilbert index (order 8) of the
+ * slopes (x/z, y/z) quantised to 256 levels on [-1, 1] (clamped); box = (min,
+ * max of x/z, min, max of y/z, min, max of |z|, 0, 0).  2D toy: one band,
+ * code = x band above the quantised y; box = (xmin, xmax, ymin, ymax, 0, 0,
+ * 0, 0).  boxes_out: float32
  * [retina_prepare_hits_box_count(n_hits, n_events)][8].  A box with a
  * non-finite value (e.g. a hit at z = 0) is infinite: never skipped.  The
  * order of hits within an event does not change R beyond float32 summation
@@ -516,10 +522,11 @@ int retina_batched_search(const float *hits, int64_t n_hits, const int64_t *even
  * free; consecutive points close in theta need mostly the same hit blocks,
  * which lets retina_batched_search with RETINA_OPT_BATCH_SEEDS_PER_WARP > 1
  * share block tests and hit loads.  Per event (rows seed_offsets[e] ..
- * seed_offsets[e+1]-1, in chunks of 8192): sorted by a Morton code of the
- * position in `box` quantised to 9 bits per axis (outside points clamp to the
- * edge, non-finite ones go last), then by original position.  Results of a
- * search on the sorted points belong to the sorted order; perm maps back.
+ * seed_offsets[e+1]-1, in chunks of 8192): sorted by the Hilbert index
+ * (order 9) of the position in `box` quantised to 9 bits per axis (outside
+ * points clamp to the edge, non-finite ones go after every finite one), then
+ * by original position.  Results of a search on the sorted points belong to
+ * the sorted order; perm maps back.
  *
  *   seeds, sorted_out : float32 [n_seeds][2], 8-byte aligned, not the same array.
  *   perm_out  : nullable int32 [n_seeds]: original row of each sorted row.
@@ -707,7 +714,7 @@ int retina_seednet_adam(float *params, float *adam_m, float *adam_v, const float
  * their centre.  Two tracks often share a 64 x 64 cell while the local search
  * converges only from a few 1e-3 in slope, hence the split.
  *
- *   logits      : float32 [n_events][64][64].
+ *   logits      : float32 [n_events][64][64], 16-byte aligned (EINVAL otherwise).
  *   K           : 1 .. 4096.
  *   zmin, min_sub_hits (>= 1) : as above; lo, hi as for the histogram.
  *   hits, n_hits, event_offsets : nullable hits (slope-model rows); offsets

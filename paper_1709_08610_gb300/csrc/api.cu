@@ -509,7 +509,7 @@ int retina_topk_seeds(const float *logits, int32_t n_events, int32_t K, float lo
     if (!isfinite(lo) || !isfinite(hi) || !(lo < hi) || !isfinite(256.f / (hi - lo))) return RETINA_EINVAL;
     if (!(zmin >= 0.f) || min_sub_hits < 1 || n_hits < 0) return RETINA_EINVAL;
     if (n_events == 0) return RETINA_OK;
-    if (!logits || !seeds) return RETINA_EINVAL;
+    if (!logits || !seeds || !aligned16(logits)) return RETINA_EINVAL;
     if (hits && (!event_offsets || !aligned16(hits))) return RETINA_EINVAL;
     return cuda_status(launch_propose_seeds(logits, n_events, K, lo, hi, zmin, min_sub_hits, (const float4 *)hits,
                                             hits ? n_hits : 0, event_offsets, seeds, cell_idx,

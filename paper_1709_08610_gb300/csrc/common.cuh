@@ -76,6 +76,38 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Index of cell (x, y), 0 <= x, y < 2^ORDER, along the Hilbert curve of that
+// order.  Classic iterative form: from the top level down, the quadrant of
+// (x, y) gives two bits of the index (quadrants visited in the order (0,0),
+// (0,1), (1,1), (1,0)), and (x, y) is carried into that quadrant's own frame -
+// the first quadrant transposed, the last one reflected through the
+// anti-diagonal - so that the curve of the level below enters and leaves where
+// the level above needs it.  Consecutive indices are edge-adjacent cells (a
+// Morton order jumps at every quadrant edge), so runs of consecutive points
+// stay compact.
+template <int ORDER>
+__device__ __forceinline__ uint32_t hilbert_index(uint32_t x, uint32_t y) {
+    uint32_t d = 0;
+#pragma unroll
+    for (int lev = ORDER - 1; lev >= 0; --lev) {
+        const uint32_t s = 1u << lev;
+        const uint32_t rx = (x >> lev) & 1u, ry = (y >> lev) & 1u;
+        d += s * s * ((3u * rx) ^ ry);
+        x &= s - 1;
+        y &= s - 1;
+        if (ry == 0) {
+            if (rx == 1) {
+                x = s - 1 - x;
+                y = s - 1 - y;
+            }
+            const uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
+}
+
 // Order-preserving map of a float to uint32 (larger float -> larger key).
 __device__ __forceinline__ uint32_t float_order_key(float f) {
     uint32_t u = __float_as_uint(f);

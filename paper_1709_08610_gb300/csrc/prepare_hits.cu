@@ -2,17 +2,27 @@
 // so that the response kernels can skip, exactly, blocks whose every term of
 // Eq. 1 is zero in float32.
 //
-// Per event (one CTA, chunks of up to SORT_CAP hits): each hit gets a 32-bit
-// key - a spatial code of up to 19 bits above its 13-bit index in the chunk,
-// so keys are distinct and the order is deterministic - and the chunk is
-// sorted by key.  Slope model: the code is a band of |z| (octaves from 16 mm)
-// over a 16-bit Morton code of the hit's slopes (u, v) = (x/z, y/z)
-// quantised on [-1, 1] (slopes beyond are clamped to the edges),
-// and the box of a block is (umin, umax, vmin, vmax, |z|min, |z|max): since
-// s^2 = z^2 |(u, v) - theta|^2, it bounds s^2 from below by
-// |z|min^2 dist(theta, box)^2.  2D toy: the code is a band of x over the
-// quantised y, and the box is (xmin, xmax, ymin, ymax, 0, 0).  The code only
-// orders the hits; the boxes use the exact float32 values.
+// Each hit gets a band and a spatial code.  Slope model: the band is an
+// octave of |z| (from 16 mm; 7 bands) and the code, below the band, is the
+// index of the hit's slopes (u, v) = (x/z, y/z), quantised to 256 levels on
+// [-1, 1] (clamped at the edges), along the Hilbert curve of order 8, whose
+// consecutive cells always touch (a Morton order jumps at every quadrant
+// edge, and a block of 32 hits spanning a jump gets a large box).  2D toy:
+// one band; the code is a band of x over the quantised y.  Per event (one
+// CTA, or one thread-block cluster for few events), in super-chunks of up to
+// SUPER consecutive hits: the hits are grouped by band (stably), each band's
+// run is cut into chunks of up to SORT_CAP hits, and each chunk is sorted by
+// the 32-bit key (code, position in the chunk) - keys are distinct and the
+// order deterministic.  A super-chunk of at most SORT_CAP hits is one chunk
+// (the band is the code's top bits, so one sort already groups it).  Sorting
+// a band whole, rather than cutting the event into chunks that each span all
+// bands, keeps each region of a band in one run of blocks: on 16.5k-hit
+// events it halves the blocks a point cannot skip.
+//
+// The box of a block is (umin, umax, vmin, vmax, |z|min, |z|max) for the
+// slope model: since s^2 = z^2 |(u, v) - theta|^2, it bounds s^2 from below
+// by |z|min^2 dist(theta, box)^2; 2D toy: (xmin, xmax, ymin, ymax, 0, 0).
+// The code only orders the hits; the boxes use the exact float32 values.
 // The sorted hits are written to the output in place of the event's hits
 // (same CSR offsets); block b of event e (sorted hits 32b .. 32b+31) gets a
 // box at index box_base(e) + b with box_base(e) = floor(offsets[e] / 32) + e,
@@ -26,16 +36,15 @@ namespace retina {
 
 constexpr int PREP_THREADS = 1024;
 constexpr int IDX_BITS = 13;
-constexpr int SORT_CAP = 1 << IDX_BITS;  // 8192 hits per chunk
+constexpr int SORT_CAP = 1 << IDX_BITS;  // 8192 hits per sorted chunk
+constexpr int SUPER = 32768;             // hits grouped by band at a time (16-bit positions)
+constexpr int N_BANDS = 8;               // band values 0 .. 6 (slope model), 0 (toy)
 
-// Spread the 8 low bits of v to the even bit positions 0, 2, ..., 14.
-__device__ __forceinline__ uint32_t spread8(uint32_t v) {
-    v &= 0xffu;
-    v = (v | (v << 4)) & 0x0f0fu;
-    v = (v | (v << 2)) & 0x3333u;
-    v = (v | (v << 1)) & 0x5555u;
-    return v;
-}
+// Shared scratch of the band grouping: positions g[SUPER] (uint16), then ints
+// band starts [N_BANDS + 1], running counts [N_BANDS], tile totals [N_BANDS],
+// per-warp counts [32][N_BANDS].
+constexpr int GROUP_INTS = (N_BANDS + 1) + N_BANDS + N_BANDS + 32 * N_BANDS;
+constexpr size_t GROUP_BYTES = (size_t)SUPER * sizeof(uint16_t) + GROUP_INTS * sizeof(int);
 
 // v quantised on [lo, lo + 1 / inv_range] to the integers 0 .. levels
 __device__ __forceinline__ uint32_t quant(float v, float lo, float inv_range, float levels) {
@@ -44,37 +53,128 @@ __device__ __forceinline__ uint32_t quant(float v, float lo, float inv_range, fl
     return (uint32_t)(t * levels);
 }
 
-// spatial code of a hit, below 2^19 (only orders the hits; any value is valid)
+// band of a hit: slope model |z| octaves [0,16), [16,32), ..., [512, inf)
+// (NaN in the last); 2D toy: 0
+__device__ __forceinline__ uint32_t hit_band(const float4 h, int model) {
+    if (model != RETINA_VELO_SLOPES) return 0;
+    const float az = fabsf(h.z);
+    uint32_t band = 0;
+    for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
+    return band;
+}
+
+// spatial code of a hit, below 2^19, its band in the top bits (only orders
+// the hits; any value is valid)
 __device__ __forceinline__ uint32_t hit_code(const float4 h, int model) {
     if (model == RETINA_VELO_SLOPES) {
-        const float az = fabsf(h.z);
-        uint32_t band = 0;  // |z| octaves: [0,16), [16,32), ..., [512, inf)
-        for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
         const float rz = __frcp_rn(h.z);
-        const uint32_t m = spread8(quant(h.x * rz, -1.f, 0.5f, 255.f)) | (spread8(quant(h.y * rz, -1.f, 0.5f, 255.f)) << 1);
-        return (band << 16) | m;
+        return (hit_band(h, model) << 16) |
+               hilbert_index<8>(quant(h.x * rz, -1.f, 0.5f, 255.f), quant(h.y * rz, -1.f, 0.5f, 255.f));
     }
     return ((float_order_key(h.x) >> 25) << 7) | quant(h.y, -8.f, 1.f / 16.f, 127.f);
 }
 
-// Keys of chunk positions t R + r (padding ~0 sorts last), sorted, then the
-// hits gathered in key order.
+// Stable grouping of the positions 0 .. n-1 (n <= SUPER) of the hits at base
+// by band: on return g[bs[q] .. bs[q+1]) lists, in increasing order, the
+// positions whose hit has band q.  All threads of the CTA call it (at least
+// N_BANDS warps, at most 32); it ends with a barrier.
+__device__ __forceinline__ void group_by_band(const float4 *__restrict__ hits, int64_t base, int n, int model, uint16_t *g,
+                              int *si) {
+    int *bs = si, *run = bs + N_BANDS + 1, *tot = run + N_BANDS, *wc = tot + N_BANDS;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    if (tid < N_BANDS) run[tid] = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < n; t0 += blockDim.x) {  // band counts
+        const int i = t0 + tid;
+        const int b = i < n ? (int)hit_band(__ldg(hits + base + i), model) : N_BANDS;
+#pragma unroll
+        for (int q = 0; q < N_BANDS; ++q) {
+            const unsigned m = __ballot_sync(0xffffffffu, b == q);
+            if (lane == 0 && m) atomicAdd(&run[q], __popc(m));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int q = 0; q < N_BANDS; ++q) {
+            bs[q] = acc;
+            acc += run[q];
+            run[q] = 0;
+        }
+        bs[N_BANDS] = acc;
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < n; t0 += blockDim.x) {  // stable scatter, one tile of blockDim positions at a time
+        const int i = t0 + tid;
+        const int b = i < n ? (int)hit_band(__ldg(hits + base + i), model) : N_BANDS;
+        int r = 0;
+#pragma unroll
+        for (int q = 0; q < N_BANDS; ++q) {
+            const unsigned m = __ballot_sync(0xffffffffu, b == q);
+            if (b == q) r = __popc(m & lt);
+            if (lane == 0) wc[w * N_BANDS + q] = __popc(m);
+        }
+        __syncthreads();
+        if (w < N_BANDS) {  // warp q: exclusive scan of band q's per-warp counts, in place
+            const int c = lane < nw ? wc[lane * N_BANDS + w] : 0;
+            int acc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, acc, o);
+                if (lane >= o) acc += u;
+            }
+            if (lane < nw) wc[lane * N_BANDS + w] = acc - c;
+            if (lane == 31) tot[w] = acc;
+        }
+        __syncthreads();
+        if (b < N_BANDS) g[bs[b] + run[b] + wc[w * N_BANDS + b] + r] = (uint16_t)i;
+        __syncthreads();
+        if (tid < N_BANDS) run[tid] += tot[tid];
+    }
+    __syncthreads();
+}
+
+// One chunk: positions p0 .. p0 + n - 1 of the super-chunk at base (hit
+// base + g[p] of the grouping, or base + p without one).  Keys of chunk
+// positions t R + r (padding ~0 sorts last), sorted, then the hits gathered
+// in key order to sorted[base + p0 ..].
 template <int R>
-__device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base, int n, int model,
+__device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base,
+                                                const uint16_t *__restrict__ g, int p0, int n, int model,
                                                 float4 *__restrict__ sorted, uint32_t *x) {
     uint32_t v[R];
     const int t = threadIdx.x;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t * R + r;
-        v[r] = i < n ? ((hit_code(__ldg(hits + base + i), model) << IDX_BITS) | (uint32_t)i) : 0xffffffffu;
+        v[r] = 0xffffffffu;
+        if (i < n) {
+            const int src = g ? (int)g[p0 + i] : p0 + i;
+            v[r] = (hit_code(__ldg(hits + base + src), model) << IDX_BITS) | (uint32_t)i;
+        }
     }
     bitonic_sort_regs<uint32_t, R, PREP_THREADS>(v, x);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t * R + r;
-        if (i < n) sorted[base + i] = __ldg(hits + base + (int)(v[r] & (SORT_CAP - 1)));
+        if (i < n) {
+            const int j = p0 + (int)(v[r] & (SORT_CAP - 1));
+            sorted[base + p0 + i] = __ldg(hits + base + (g ? (int)g[j] : j));
+        }
     }
+}
+
+__device__ __forceinline__ void sort_chunk(const float4 *__restrict__ hits, int64_t base, const uint16_t *g, int p0,
+                                           int n, int model, float4 *__restrict__ sorted, uint32_t *x) {
+    if (n <= PREP_THREADS)
+        sort_and_gather<1>(hits, base, g, p0, n, model, sorted, x);
+    else if (n <= 2 * PREP_THREADS)
+        sort_and_gather<2>(hits, base, g, p0, n, model, sorted, x);
+    else if (n <= 4 * PREP_THREADS)
+        sort_and_gather<4>(hits, base, g, p0, n, model, sorted, x);
+    else
+        sort_and_gather<8>(hits, base, g, p0, n, model, sorted, x);
 }
 
 // Boxes of the blocks of 32 sorted hits starting at chunk positions lo .. hi
@@ -128,25 +228,31 @@ __device__ __forceinline__ void chunk_boxes(const float4 *__restrict__ sorted, i
 __global__ void __launch_bounds__(PREP_THREADS)
 prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int model,
                     float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
-    extern __shared__ uint32_t keys[];
+    extern __shared__ __align__(16) uint32_t keys[];  // [SORT_CAP], then the grouping scratch
+    uint16_t *g = reinterpret_cast<uint16_t *>(keys + SORT_CAP);
+    int *si = reinterpret_cast<int *>(g + SUPER);
     const int e = blockIdx.x;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
     const int64_t H = he - hb;
     const int64_t box_base = (off[e] < 0 ? 0 : (off[e] > n_hits ? n_hits : off[e])) / 32 + e;
-    for (int64_t c0 = 0; c0 < H; c0 += SORT_CAP) {
-        const int n = (int)((H - c0) < SORT_CAP ? (H - c0) : SORT_CAP);
-        const int64_t base = hb + c0;
-        if (n <= PREP_THREADS)
-            sort_and_gather<1>(hits, base, n, model, sorted, keys);
-        else if (n <= 2 * PREP_THREADS)
-            sort_and_gather<2>(hits, base, n, model, sorted, keys);
-        else if (n <= 4 * PREP_THREADS)
-            sort_and_gather<4>(hits, base, n, model, sorted, keys);
-        else
-            sort_and_gather<8>(hits, base, n, model, sorted, keys);
-        __syncthreads();
-        chunk_boxes(sorted, hb + c0, n, 0, n, model, box_base + c0 / 32, boxes);
+    for (int64_t s0 = 0; s0 < H; s0 += SUPER) {
+        const int ns = (int)((H - s0) < SUPER ? (H - s0) : SUPER);
+        const int64_t base = hb + s0;
+        if (ns <= SORT_CAP) {
+            sort_chunk(hits, base, nullptr, 0, ns, model, sorted, keys);
+        } else {
+            group_by_band(hits, base, ns, model, g, si);
+            for (int q = 0; q < N_BANDS; ++q) {
+                const int q0 = si[q], q1 = si[q + 1];
+                for (int p0 = q0; p0 < q1; p0 += SORT_CAP) {
+                    sort_chunk(hits, base, g, p0, (q1 - p0) < SORT_CAP ? (q1 - p0) : SORT_CAP, model, sorted, keys);
+                    __syncthreads();
+                }
+            }
+        }
+        __syncthreads();  // the super-chunk's gathered hits, read back for its boxes
+        chunk_boxes(sorted, base, ns, 0, ns, model, box_base + s0 / 32, boxes);
         __syncthreads();
     }
 }
@@ -230,7 +336,8 @@ __device__ __forceinline__ void bitonic_cluster(uint32_t (&v)[R], uint32_t *x, i
 }
 
 template <int R>
-__device__ __forceinline__ void cluster_sort_gather(const float4 *__restrict__ hits, int64_t base, int n, int model,
+__device__ __forceinline__ void cluster_sort_gather(const float4 *__restrict__ hits, int64_t base,
+                                                    const uint16_t *__restrict__ g, int p0, int n, int model,
                                                     float4 *__restrict__ sorted, uint32_t *x, int rank) {
     constexpr int P = CL_THREADS * R;
     uint32_t v[R];
@@ -238,44 +345,88 @@ __device__ __forceinline__ void cluster_sort_gather(const float4 *__restrict__ h
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = rank * P + t * R + r;
-        v[r] = i < n ? ((hit_code(__ldg(hits + base + i), model) << IDX_BITS) | (uint32_t)i) : 0xffffffffu;
+        v[r] = 0xffffffffu;
+        if (i < n) {
+            const int src = g ? (int)g[p0 + i] : p0 + i;
+            v[r] = (hit_code(__ldg(hits + base + src), model) << IDX_BITS) | (uint32_t)i;
+        }
     }
     bitonic_cluster<R>(v, x, rank);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = rank * P + t * R + r;
-        if (i < n) sorted[base + i] = __ldg(hits + base + (int)(v[r] & (SORT_CAP - 1)));
+        if (i < n) {
+            const int j = p0 + (int)(v[r] & (SORT_CAP - 1));
+            sorted[base + p0 + i] = __ldg(hits + base + (g ? (int)g[j] : j));
+        }
     }
 }
 
-__global__ void __launch_bounds__(CL_THREADS)
+// Sorts one chunk over the cluster; returns the chunk positions per CTA.
+__device__ __forceinline__ int cluster_sort_chunk(const float4 *__restrict__ hits, int64_t base, const uint16_t *g,
+                                                  int p0, int n, int model, float4 *__restrict__ sorted, uint32_t *x,
+                                                  int rank) {
+    if (n <= CL * CL_THREADS) {
+        cluster_sort_gather<1>(hits, base, g, p0, n, model, sorted, x, rank);
+        return CL_THREADS;
+    }
+    if (n <= 2 * CL * CL_THREADS) {
+        cluster_sort_gather<2>(hits, base, g, p0, n, model, sorted, x, rank);
+        return 2 * CL_THREADS;
+    }
+    cluster_sort_gather<4>(hits, base, g, p0, n, model, sorted, x, rank);
+    return 4 * CL_THREADS;
+}
+
+__global__ void __launch_bounds__(CL_THREADS, 1)
 prepare_hits_cluster_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
                             int model, float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
     __shared__ uint32_t x[SORT_CAP / CL];
+    extern __shared__ __align__(16) uint16_t g[];  // [SUPER], then the grouping's ints
+    int *si = reinterpret_cast<int *>(g + SUPER);
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
     pdl_release();  // the grid kernel may be scheduled once every CTA has started
     const int e = blockIdx.x / CL, rank = blockIdx.x % CL;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
     const int64_t H = he - hb;
     const int64_t box_base = (off[e] < 0 ? 0 : (off[e] > n_hits ? n_hits : off[e])) / 32 + e;
-    for (int64_t c0 = 0; c0 < H; c0 += SORT_CAP) {
-        const int n = (int)((H - c0) < SORT_CAP ? (H - c0) : SORT_CAP);
-        const int64_t base = hb + c0;
-        int P;  // chunk positions per CTA: CL_THREADS x (keys per thread)
-        if (n <= CL * CL_THREADS) {
-            cluster_sort_gather<1>(hits, base, n, model, sorted, x, rank);
-            P = CL_THREADS;
-        } else if (n <= 2 * CL * CL_THREADS) {
-            cluster_sort_gather<2>(hits, base, n, model, sorted, x, rank);
-            P = 2 * CL_THREADS;
+    for (int64_t s0 = 0; s0 < H; s0 += SUPER) {
+        const int ns = (int)((H - s0) < SUPER ? (H - s0) : SUPER);
+        const int64_t base = hb + s0;
+        // every CTA groups a super-chunk of more than SORT_CAP hits itself (the
+        // same result); one of at most SORT_CAP hits is one chunk
+        const bool grouped = ns > SORT_CAP;
+        if (grouped) {
+            group_by_band(hits, base, ns, model, g, si);
         } else {
-            cluster_sort_gather<4>(hits, base, n, model, sorted, x, rank);
-            P = 4 * CL_THREADS;
+            if (threadIdx.x <= N_BANDS) si[threadIdx.x] = threadIdx.x == 0 ? 0 : ns;
+            __syncthreads();
         }
-        __syncthreads();  // this CTA's gathered hits, read back for its boxes
-        const int lo = rank * P, hi = (rank + 1) * P < n ? (rank + 1) * P : n;
-        if (lo < n) chunk_boxes(sorted, base, n, lo, hi, model, box_base + c0 / 32, boxes);
-        cooperative_groups::this_cluster().sync();  // x is reused by the next chunk's exchanges
+        int P = 0;
+        for (int q = 0; q < N_BANDS; ++q) {
+            const int q0 = si[q], q1 = si[q + 1];
+            for (int p0 = q0; p0 < q1; p0 += SORT_CAP) {
+                P = cluster_sort_chunk(hits, base, grouped ? g : nullptr, p0,
+                                       (q1 - p0) < SORT_CAP ? (q1 - p0) : SORT_CAP, model, sorted, x, rank);
+                if (grouped) cl.sync();  // x is reused by the next chunk's exchanges
+            }
+        }
+        int lo, hi;
+        if (grouped) {
+            __threadfence();
+            cl.sync();  // a block's hits may come from several CTAs' gathers
+            const int per = (((ns + 31) / 32) + CL - 1) / CL * 32;  // positions per CTA, whole blocks
+            lo = rank * per;
+            hi = (rank + 1) * per < ns ? (rank + 1) * per : ns;
+        } else {
+            __syncthreads();  // this CTA's gathered hits, read back for its boxes
+            lo = rank * P;
+            hi = (rank + 1) * P < ns ? (rank + 1) * P : ns;
+        }
+        if (lo < ns) chunk_boxes(sorted, base, ns, lo, hi, model, box_base + s0 / 32, boxes);
+        cl.sync();  // x and the grouping scratch are reused by the next super-chunk
     }
 }
 
@@ -287,10 +438,12 @@ cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_
     // the GPU many times over (throughput): one CTA per event, no cluster
     // exchanges
     if ((int64_t)n_events * CL <= 4LL * sm_count()) {
+        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_cluster_kernel), GROUP_BYTES);
+        if (aerr != cudaSuccess) return aerr;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(n_events * CL));
         cfg.blockDim = dim3(CL_THREADS);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = GROUP_BYTES;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -302,7 +455,7 @@ cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_
         count_launches(1);
         return cudaLaunchKernelEx(&cfg, prepare_hits_cluster_kernel, hits, n_hits, off, model, sorted, boxes);
     }
-    const size_t smem = (size_t)SORT_CAP * sizeof(uint32_t);
+    const size_t smem = (size_t)SORT_CAP * sizeof(uint32_t) + GROUP_BYTES;
     {
         cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_kernel), smem);
         if (aerr != cudaSuccess) return aerr;

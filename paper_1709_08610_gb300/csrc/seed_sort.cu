@@ -4,10 +4,13 @@
 // free.  Neighbouring points need mostly the same hit blocks, so a warp that
 // searches several consecutive points (RETINA_OPT_BATCH_SEEDS_PER_WARP > 1)
 // shares block tests and hit loads when the points are spatially ordered.
-// Key of a point: a Morton code of its position in the box quantised to 9
-// bits per axis (points outside the box clamp to the edge, non-finite ones
-// sort last), over its 13-bit index in the chunk (chunks of 8192 points per
-// event), so keys are distinct and the order is deterministic.
+// Key of a point: the Hilbert index (order 9) of its position in the box
+// quantised to 9 bits per axis (points outside the box clamp to the edge;
+// non-finite ones get 2^18, after every finite point), over its 13-bit index
+// in the chunk (chunks of 8192 points per event), so keys are distinct and
+// the order is deterministic.  Consecutive Hilbert cells touch, so groups of
+// consecutive points have small spans (a Morton order jumps at quadrant
+// edges).
 #include "internal.cuh"
 
 namespace retina {
@@ -15,15 +18,6 @@ namespace retina {
 constexpr int SS_THREADS = 1024;
 constexpr int SS_IDX_BITS = 13;
 constexpr int SS_CAP = 1 << SS_IDX_BITS;
-
-__device__ __forceinline__ uint32_t spread9(uint32_t v) {
-    v &= 0x1ffu;
-    v = (v | (v << 8)) & 0x00ff00ffu;
-    v = (v | (v << 4)) & 0x0f0f0f0fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
-}
 
 __device__ __forceinline__ uint32_t quant9(float t, float lo, float inv_ext) {
     const float q = (t - lo) * inv_ext;
@@ -45,8 +39,8 @@ __device__ __forceinline__ void sort_seed_chunk(const float2 *__restrict__ seeds
         if (i < n) {
             const float2 s = seeds[base + i];
             const uint32_t m = (isfinite(s.x) && isfinite(s.y))
-                                   ? (spread9(quant9(s.x, lo0, inv0)) | (spread9(quant9(s.y, lo1, inv1)) << 1))
-                                   : 0x3ffffu;  // 18 bits: after every finite point
+                                   ? hilbert_index<9>(quant9(s.x, lo0, inv0), quant9(s.y, lo1, inv1))
+                                   : (1u << 18);  // after every finite point
             key = (m << SS_IDX_BITS) | (uint32_t)i;
         }
         v[r] = key;

@@ -399,29 +399,30 @@ propose_seeds_kernel(const float *__restrict__ logits, int K, float lo, float w,
     int16_t *rank = reinterpret_cast<int16_t *>(scan + 64);                      // [4096]
     const int e = blockIdx.x, tid = threadIdx.x;
     const float s4 = scale * (float)SUB;
-    for (int i = tid; i < SN_PX; i += PROP_THREADS) {
-        const float z = logits[(int64_t)e * SN_PX + i] + 0.f;              // -0 -> +0: equal logits tie
-        const uint32_t k = isnan(z) ? 0u : float_order_key(z);            // NaN ranks below every number
-        keys[i] = ((uint64_t)(~k) << 32) | (uint32_t)i;                    // larger z first, then lower index
-    }
-    for (int i = tid; i < R_MAX * SUB * SUB; i += PROP_THREADS) sub[i] = 0;
-    __syncthreads();
-    for (int k = 2; k <= SN_PX; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < SN_PX; i += PROP_THREADS) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = keys[i], b = keys[ixj];
-                    if ((a > b) == ((i & k) == 0)) {
-                        keys[i] = b;
-                        keys[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    // rank the cells: thread t holds cells 4t .. 4t+3, sorted in registers
+    // (bitonic; shuffles and shared memory for the wider strides)
+    constexpr int KPT = SN_PX / PROP_THREADS;
+    static_assert(KPT == 4, "four cells per thread");
+    uint64_t kv[KPT];
+    {
+        const float4 z4 = reinterpret_cast<const float4 *>(logits + (int64_t)e * SN_PX)[tid];
+        const float zz[KPT] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+        for (int r = 0; r < KPT; ++r) {
+            const int i = tid * KPT + r;
+            const float z = zz[r] + 0.f;                                 // -0 -> +0: equal logits tie
+            const uint32_t k = isnan(z) ? 0u : float_order_key(z);      // NaN ranks below every number
+            kv[r] = ((uint64_t)(~k) << 32) | (uint32_t)i;                // larger z first, then lower index
         }
     }
-    for (int q = tid; q < SN_PX; q += PROP_THREADS) rank[(int)(uint32_t)keys[q]] = (int16_t)q;
+    for (int i = tid; i < R_MAX * SUB * SUB; i += PROP_THREADS) sub[i] = 0;
+    bitonic_sort_regs<uint64_t, KPT, PROP_THREADS>(kv, keys);
+    __syncthreads();  // the sort's last shared-memory reads are done before keys is overwritten
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) {
+        keys[tid * KPT + r] = kv[r];
+        rank[(int)(uint32_t)kv[r]] = (int16_t)(tid * KPT + r);
+    }
     __syncthreads();
     int64_t hb = 0, he = 0;
     if (hits) event_range(off, n_hits, e, hb, he);

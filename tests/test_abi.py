@@ -309,6 +309,7 @@ def test_seednet_entries_reject_before_launch():
     assert T(BOGUS, 1, 16, -0.5, 0.5, -1.0, 3, None, 0, None, BOGUS, None, None) == EINVAL
     assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 3, None, 0, None, None, None, None) == EINVAL
     assert T(BOGUS, 1, 16, -0.5, 0.5, 50.0, 3, BOGUS, 10, None, BOGUS, None, None) == EINVAL
+    assert T(ctypes.c_void_p(0x1004), 1, 16, -0.5, 0.5, 50.0, 3, None, 0, None, BOGUS, None, None) == EINVAL  # logits
     assert T(None, 0, 16, -0.5, 0.5, 50.0, 3, None, 0, None, None, None, None) == OK
 
 

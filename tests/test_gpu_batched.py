@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+from hit_order import hilbert
 from synth import WORKLOADS, make_event, batch_of, uniform_seeds
 
 pytestmark = pytest.mark.gpu
@@ -166,19 +167,13 @@ def test_batched_search_replays_in_a_cuda_graph(rt):
             np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
 
 
-def _morton9(S, box):
-    """Host restatement of the documented seed key (9-bit Morton code in the box)."""
+def _hilbert9(S, box):
+    """Host restatement of the documented seed key (order-9 Hilbert index in the box)."""
     lo = np.asarray(box.lo, np.float32)
     inv = (1.0 / (np.asarray(box.n, np.float64) * np.asarray(box.step, np.float64))).astype(np.float32)
     q = (S.astype(np.float32) - lo) * inv
     qi = np.where(q > 0, np.where(q < 1, np.floor(q * np.float32(512)).astype(np.int64) & 511, 511), 0)
-
-    def spread(v):
-        out = np.zeros_like(v)
-        for i in range(9):
-            out |= ((v >> i) & 1) << (2 * i)
-        return out
-    return spread(qi[:, 0]) | (spread(qi[:, 1]) << 1)
+    return hilbert(qi[:, 0], qi[:, 1], 9)
 
 
 def test_sorted_seeds_are_a_spatial_permutation_and_search_results_follow_them(rt):
@@ -194,7 +189,7 @@ def test_sorted_seeds_are_a_spatial_permutation_and_search_results_follow_them(r
         assert sorted(p.tolist()) == list(range(s0, s1))
         np.testing.assert_array_equal(srt[s0:s1], seeds[p])
         fin = np.isfinite(seeds[p]).all(1)
-        key = np.where(fin, _morton9(seeds[p], box), 1 << 18) * (1 << 13) + (p - s0)
+        key = np.where(fin, _hilbert9(seeds[p], box), 1 << 18) * (1 << 13) + (p - s0)
         assert np.all(np.diff(key) > 0)
     # the search is per seed: on sorted points with two seeds per warp, every
     # result is bitwise the unsorted one-seed-per-warp result of the same point
@@ -227,5 +222,5 @@ def test_sorted_seeds_in_chunks_of_8192(rt):
             c1 = min(c0 + 8192, so[e + 1])
             p = perm[c0:c1]
             assert sorted(p.tolist()) == list(range(c0, c1))
-            key = _morton9(S[p], box) * (1 << 13) + (p - c0)
+            key = _hilbert9(S[p], box) * (1 << 13) + (p - c0)
             assert np.all(np.diff(key) > 0)

@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import oracle
+from hit_order import documented_order
 from synth import WORKLOADS, make_event, batch_of, uniform_seeds
 
 pytestmark = pytest.mark.gpu
@@ -158,3 +159,44 @@ def test_non_finite_hit_blocks_are_never_skipped(rt):
     R_full = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=1)
     R_cull = rt.grid_response(srt, offs, 1, grid, wl.sigma_grid, flags=1, boxes=boxes)
     assert torch.isnan(R_full).all() and torch.isnan(R_cull).all()
+
+
+def _order_events():
+    wl = WORKLOADS["velo"]
+    rng = np.random.default_rng(17)
+    one_band = np.zeros((20000, 4), np.float32)  # a band of more than 8192 hits: two chunks
+    one_band[:, 2] = rng.uniform(256, 511, 20000)
+    one_band[:, :2] = rng.uniform(-0.4, 0.4, (20000, 2)) * one_band[:, 2:3]
+    odd = make_event(wl, 9, 3, n_tracks=300, vertex_sigma=(0, 0, 0)).hits.copy()
+    odd[5, 2] = 0.0  # slope of a hit at z = 0: infinite, clamped
+    odd[9, 0] = np.nan
+    odd[11, 2] = np.nan
+    odd[13, 1] = np.inf
+    return [make_event(wl, 9, 0, vertex_sigma=(0, 0, 0)).hits,  # one chunk
+            make_event(wl, 9, 1, n_tracks=700, vertex_sigma=(0, 0, 0)).hits,  # grouped by band
+            make_event(wl, 9, 2, n_tracks=1500, vertex_sigma=(0, 0, 0)).hits,  # two super-chunks
+            one_band, odd, np.zeros((0, 4), np.float32)]
+
+
+@pytest.mark.parametrize("many", [False, True])
+def test_prepared_order_is_the_documented_key(rt, many):
+    # few events take the cluster kernel, many the one-CTA-per-event kernel:
+    # both give exactly the documented order
+    hs = _order_events()
+    assert len(hs[2]) > 32768 and len(hs[1]) > 8192
+    if many:
+        hs = hs + [make_event(WORKLOADS["velo_batch"], 9, e, vertex_sigma=(0, 0, 0)).hits for e in range(90)]
+    off = np.concatenate([[0], np.cumsum([len(h) for h in hs])]).astype(np.int64)
+    srt, _ = rt.prepare_hits(_dev(np.concatenate(hs)), _dev(off), 1)
+    srt = srt.cpu().numpy()
+    for e, h in enumerate(hs):
+        np.testing.assert_array_equal(srt[off[e]:off[e + 1]], h[documented_order(h, 1)], err_msg="event %d" % e)
+
+
+def test_prepared_order_toy_is_the_documented_key(rt):
+    wl, evs, b = _batch(0)
+    srt, _ = rt.prepare_hits(_dev(b.hits), _dev(b.offsets), 0)
+    srt = srt.cpu().numpy()
+    for e, ev in enumerate(evs):
+        h0, h1 = b.offsets[e], b.offsets[e + 1]
+        np.testing.assert_array_equal(srt[h0:h1], b.hits[h0:h1][documented_order(b.hits[h0:h1], 0)])
