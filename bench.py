@@ -1254,7 +1254,9 @@ def headline(rt, args, dev, rank, world, peaks, local_rank):
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
            "note": "retina_tracker_run_host per step: the batch's hits and offsets copied in from page-locked host "
                    "memory, the step's graph replayed, every event's track list (tracks, R, count) copied out to "
-                   "page-locked host memory, in stream order, timed with CUDA events; steps back to back"}
+                   "page-locked host memory, timed with CUDA events; steps back to back, each step's hit copy (on "
+                   "the tracker's copy stream) overlapping the previous step's search once that step's hit ordering "
+                   "is done"}
 
     # ---- the oracle on a sample of the same events (rank 0, one GPU)
     cpu = None

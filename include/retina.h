@@ -846,12 +846,18 @@ int retina_pipeline_destroy(retina_pipeline *p);
  *   recorded again at the next step.
  * retina_tracker_run_host: one step from host memory - copies n_hits hits,
  *   n_events + 1 offsets and (caller seeds only) n_events * S seeds in,
- *   steps, copies n_events rows of tracks, track_R and n_tracks out, all
- *   enqueued on `stream` in that order; the call returns before the copies
- *   finish: synchronise the stream before reading the host outputs.  Host
- *   buffers should be page-locked for the copies to be asynchronous.  The
- *   offsets are checked on the host (non-decreasing, within [0, n_hits]):
- *   RETINA_EINVAL, nothing enqueued.
+ *   steps, copies n_events rows of tracks, track_R and n_tracks out; the call
+ *   returns before the copies finish: synchronise the stream before reading
+ *   the host outputs.  Everything but the hit copy is enqueued on `stream` in
+ *   that order.  The hit copy runs on the tracker's own copy stream as soon
+ *   as the previous step's hit ordering has finished (the only launch that
+ *   reads the unsorted hits), so consecutive calls overlap one step's copy
+ *   with the previous step's search; the step waits for it.  So the host hit
+ *   buffer must hold this step's hits when the call is made (it is not
+ *   ordered after work already enqueued on `stream`), and must not change
+ *   until `stream` has passed the step.  Host buffers should be page-locked
+ *   for the copies to be asynchronous.  The offsets are checked on the host
+ *   (non-decreasing, within [0, n_hits]): RETINA_EINVAL, nothing enqueued.
  */
 typedef struct {
     retina_grid box;

@@ -166,18 +166,39 @@ __device__ __forceinline__ void pair_r_x2(const float4 h, unsigned long long nt0
 template <int MODEL>
 __device__ __forceinline__ void sums_to_rgh(const float *S, float k, float &R, float &g0, float &g1, float &H00,
                                             float &H01, float &H11) {
-    const float k2 = 2.f * k, k4 = 4.f * k * k;
+    // every operation rounded explicitly, so that each search shape (one
+    // point per warp, groups, lane-parallel epilogues) computes the same bits
+    const float k2 = __fmul_rn(2.f, k), k4 = __fmul_rn(__fmul_rn(4.f, k), k);
     R = S[0];
-    g0 = k2 * S[1];
-    g1 = k2 * S[2];
+    g0 = __fmul_rn(k2, S[1]);
+    g1 = __fmul_rn(k2, S[2]);
     if (MODEL == RETINA_VELO_SLOPES) {
-        H00 = k4 * S[3] - k2 * S[6];
-        H01 = k4 * S[4];
-        H11 = k4 * S[5] - k2 * S[6];
+        H00 = __fsub_rn(__fmul_rn(k4, S[3]), __fmul_rn(k2, S[6]));
+        H01 = __fmul_rn(k4, S[4]);
+        H11 = __fsub_rn(__fmul_rn(k4, S[5]), __fmul_rn(k2, S[6]));
     } else {
-        H00 = k4 * S[3] - k2 * S[6];
-        H01 = k4 * S[4] - k2 * S[7];
-        H11 = k4 * S[5] - k2 * S[0];
+        H00 = __fsub_rn(__fmul_rn(k4, S[3]), __fmul_rn(k2, S[6]));
+        H01 = __fsub_rn(__fmul_rn(k4, S[4]), __fmul_rn(k2, S[7]));
+        H11 = __fsub_rn(__fmul_rn(k4, S[5]), __fmul_rn(k2, S[0]));
+    }
+}
+
+// Directional derivative g . p and the Armijo bound R + c1 t (g . p) of the
+// backtracking line search (Algorithm 1), rounded explicitly.
+__device__ __forceinline__ float dir_slope(float g0, float g1, float p0, float p1) {
+    return __fmaf_rn(g0, p0, __fmul_rn(g1, p1));
+}
+__device__ __forceinline__ float armijo_bound(float R, float c1, float t, float slope) {
+    return __fmaf_rn(__fmul_rn(c1, t), slope, R);
+}
+
+// Step cap: scale (p0, p1) so that it moves at most cap grid cells on either axis.
+__device__ __forceinline__ void cap_step(float &p0, float &p1, float step0, float step1, float cap) {
+    const float cells = fmaxf(__fdiv_rn(fabsf(p0), step0), __fdiv_rn(fabsf(p1), step1));
+    if (cells > cap) {
+        const float sc = __fdiv_rn(cap, cells);
+        p0 = __fmul_rn(p0, sc);
+        p1 = __fmul_rn(p1, sc);
     }
 }
 
@@ -539,7 +560,7 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
             }
         } else {
 #pragma unroll 1
-            for (int w = 0; w < KEPT_CHUNK / 32; ++w) {
+            for (int w = 0; w < KEPT_CHUNK / 32 && c0 + 32 * w < nblk; ++w) {  // the event's last chunk may be short
                 const int b = c0 + 32 * w + lane;
                 bool keep = false;
                 if (b < nblk) {
@@ -653,13 +674,8 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
         float R, g0, g1, H00, H01, H11, pp0, pp1;
         sums_to_rgh<MODEL>(S, k, R, g0, g1, H00, H01, H11);
         update_direction<UPD>(g0, g1, H00, H01, H11, pp0, pp1);
-        const float cells = fmaxf(fabsf(pp0) / prm.box.step0, fabsf(pp1) / prm.box.step1);
-        if (cells > prm.cap) {
-            const float sc = prm.cap / cells;
-            pp0 *= sc;
-            pp1 *= sc;
-        }
-        const float slope = g0 * pp0 + g1 * pp1;
+        cap_step(pp0, pp1, prm.box.step0, prm.box.step1, prm.cap);
+        const float slope = dir_slope(g0, g1, pp0, pp1);
         float t = 1.f;
         bool pending = true;
         Rfin = R;  // R at the point if no step is accepted
@@ -740,7 +756,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
             w_r += (uint32_t)vis;
             ++evals;
             const float rt = warp_sum(Rt);
-            if (rt >= R + prm.c1 * t * slope) {
+            if (rt >= armijo_bound(R, prm.c1, t, slope)) {
                 th0 = tr0;
                 th1 = tr1;
                 Rfin = rt;  // R at the accepted point, this update's bandwidth
@@ -753,7 +769,7 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
             } else if (two) {
                 ++evals;
                 const float rb = warp_sum(Rb);
-                if (rb >= R + prm.c1 * tb * slope) {
+                if (rb >= armijo_bound(R, prm.c1, tb, slope)) {
                     th0 = tb0;
                     th1 = tb1;
                     Rfin = rb;
@@ -790,6 +806,50 @@ __device__ __forceinline__ void search_one(const float4 *__restrict__ sh, const 
     if (n_evals) n_evals[0] = (uint8_t)(evals < 255 ? evals : 255);
 }
 
+// Warp totals of the seven RGH sums of four points (packed pairs A: points 0
+// and 1, B: points 2 and 3, per lane), reduced and scattered at once: lane l
+// ends with the total of sum l & 7 of point l >> 3 (0.0 for l & 7 = 7).  Each
+// level halves what a lane holds - it keeps the half its lane bit selects and
+// adds the partner's copy of that half - in warp_sum's order (xor 16, 8, 4, 2,
+// 1), and every partial it adds is the one warp_sum adds at that level, so
+// each total is bitwise warp_sum's: 28 shuffles for the 28 totals instead of
+// 140.
+__device__ __forceinline__ float scatter_sums4(const unsigned long long (&A)[7], const unsigned long long (&B)[7],
+                                               int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const unsigned long long got = __shfl_xor_sync(0xffffffffu, b4 ? A[i] : B[i], 16);
+        float lo, hi;
+        unpack2(add2_rn(b4 ? B[i] : A[i], got), lo, hi);
+        v[i] = __fadd_rn(b3 ? hi : lo, __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8));
+    }
+    v[7] = 0.f;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        w[i] = __fadd_rn(b2 ? v[4 + i] : v[i], __shfl_xor_sync(0xffffffffu, b2 ? v[i] : v[4 + i], 4));
+    float x[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        x[i] = __fadd_rn(b1 ? w[2 + i] : w[i], __shfl_xor_sync(0xffffffffu, b1 ? w[i] : w[2 + i], 2));
+    return __fadd_rn(b0 ? x[1] : x[0], __shfl_xor_sync(0xffffffffu, b0 ? x[0] : x[1], 1));
+}
+
+// Warp totals of one sum of four points (packed pairs A: points 0, 1, B:
+// points 2, 3): every lane of group l >> 3 ends with point l >> 3's total,
+// bitwise warp_sum's (the same levels as scatter_sums4, then xor 4, 2, 1).
+__device__ __forceinline__ float group_sums4(unsigned long long A, unsigned long long B, int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8;
+    float lo, hi;
+    unpack2(add2_rn(b4 ? B : A, __shfl_xor_sync(0xffffffffu, b4 ? A : B, 16)), lo, hi);
+    float v = __fadd_rn(b3 ? hi : lo, __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8));
+#pragma unroll
+    for (int m = 4; m >= 1; m >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
+    return v;
+}
+
 // Algorithm 1 for the P seeds of one warp: q truncated-Newton updates
 // (gradient/Hessian pass, Newton-CG direction, step cap, Armijo backtracking
 // at bandwidth sigma_j), then R(theta_q; sigma_q), status and the number of
@@ -823,6 +883,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
     constexpr int NS = Model<MODEL>::NS;
     // the points' state between passes: warp-uniform, in registers, or (SS)
     // once per warp in shared memory, where 32 lanes' copies would spill
+    static_assert(!SS || (P == 4 && MODEL == RETINA_VELO_SLOPES), "shared state: four slope-model points");
     GroupState<P> gs_local;
     GroupState<P> &gs = SS ? *state : gs_local;
 #pragma unroll
@@ -855,6 +916,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             return need;
         };
         float S[P][NS];
+        float tot_ss = 0.f;  // four points: this lane's scattered total
         int vis;
         if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) {
             // the points' sums in packed FP32x2, two points per register pair
@@ -878,8 +940,12 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                           a2[q].add(b);
                                       }
                                   });
+            if constexpr (SS) {
+                tot_ss = scatter_sums4(a2[0].S, a2[1].S, lane);
+            } else {
 #pragma unroll
-            for (int q = 0; q < NP; ++q) a2[q].sums(S[2 * q], S[2 * q + 1]);
+                for (int q = 0; q < NP; ++q) a2[q].sums(S[2 * q], S[2 * q + 1]);
+            }
         } else {
             vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
                                           [&](const float4 h) {
@@ -894,24 +960,44 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             for (int p = 0; p < P; ++p) acc[p].sums(S[p]);
         }
         w_rgh += (uint32_t)vis * (uint32_t)n_live;
-        float g0[P], g1[P];
+        if constexpr (SS) {
+            // four points (state in shared memory): the 28 totals scattered
+            // over the warp, then lanes 8p .. 8p + 7 take point p's update
+            // together - one copy of the update code for all four points
+            const float tot = tot_ss;
+            const int p = lane >> 3;
+            float Sp[NS];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) S[p][i] = warp_sum(S[p][i]);
-            float H00, H01, H11;
-            sums_to_rgh<MODEL>(S[p], k, gs.R[p], g0[p], g1[p], H00, H01, H11);
-            update_direction<UPD>(g0[p], g1[p], H00, H01, H11, gs.pp0[p], gs.pp1[p]);
-            const float cells = fmaxf(fabsf(gs.pp0[p]) / prm.box.step0, fabsf(gs.pp1[p]) / prm.box.step1);
-            if (cells > prm.cap) {
-                const float sc = prm.cap / cells;
-                gs.pp0[p] *= sc;
-                gs.pp1[p] *= sc;
+            for (int i = 0; i < NS; ++i) Sp[i] = __shfl_sync(0xffffffffu, tot, (lane & 24) | i);
+            float R, g0, g1, H00, H01, H11, pp0, pp1;
+            sums_to_rgh<MODEL>(Sp, k, R, g0, g1, H00, H01, H11);
+            update_direction<UPD>(g0, g1, H00, H01, H11, pp0, pp1);
+            cap_step(pp0, pp1, prm.box.step0, prm.box.step1, prm.cap);
+            const float slope = dir_slope(g0, g1, pp0, pp1);
+            if ((lane & 7) == 0) {
+                gs.R[p] = R;
+                gs.pp0[p] = pp0;
+                gs.pp1[p] = pp1;
+                gs.slope[p] = slope;
+                gs.t[p] = 1.f;
+                gs.pending[p] = gs.live[p];
+                gs.Rfin[p] = R;  // R at the point if no step is accepted
             }
-            gs.slope[p] = g0[p] * gs.pp0[p] + g1[p] * gs.pp1[p];
-            gs.t[p] = 1.f;
-            gs.pending[p] = gs.live[p];
-            gs.Rfin[p] = gs.R[p];  // R at the point if no step is accepted
+            __syncwarp();
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) S[p][i] = warp_sum(S[p][i]);
+                float g0, g1, H00, H01, H11;
+                sums_to_rgh<MODEL>(S[p], k, gs.R[p], g0, g1, H00, H01, H11);
+                update_direction<UPD>(g0, g1, H00, H01, H11, gs.pp0[p], gs.pp1[p]);
+                cap_step(gs.pp0[p], gs.pp1[p], prm.box.step0, prm.box.step1, prm.cap);
+                gs.slope[p] = dir_slope(g0, g1, gs.pp0[p], gs.pp1[p]);
+                gs.t[p] = 1.f;
+                gs.pending[p] = gs.live[p];
+                gs.Rfin[p] = gs.R[p];  // R at the point if no step is accepted
+            }
         }
         // backtracking line search, all pending seeds of the warp together
         for (int hv = 0; hv <= prm.max_halvings; ++hv) {
@@ -936,6 +1022,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 for (int p = 0; p < P; ++p) need |= gs.pending[p] && !box_culled<MODEL>(A, z2, ct[p]);
                 return need;
             };
+            float rt_ss = 0.f;  // four points: the total of this lane's point
             int vis;
             if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) {
                 // the trial points in packed FP32x2, two per register pair; a
@@ -962,8 +1049,12 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                               pair_r_x2(b, nt0[q], nt1[q], nkk, Rt2[q]);
                                           }
                                       });
+                if constexpr (SS) {
+                    rt_ss = group_sums4(Rt2[0], Rt2[1], lane);
+                } else {
 #pragma unroll
-                for (int q = 0; q < NP; ++q) unpack2(Rt2[q], Rt[2 * q], Rt[2 * q + 1]);
+                    for (int q = 0; q < NP; ++q) unpack2(Rt2[q], Rt[2 * q], Rt[2 * q + 1]);
+                }
             } else {
                 vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed_r,
                                               [&](const float4 h) {
@@ -982,18 +1073,40 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
 #pragma unroll
             for (int p = 0; p < P; ++p) n_pend += gs.pending[p] ? 1 : 0;
             w_r += (uint32_t)vis * (uint32_t)n_pend;
+            if constexpr (SS) {
+                // lanes 8p .. 8p + 7 test point p's trial; lane 8p writes
+                const int p = lane >> 3;
+                const bool pend = gs.pending[p];
+                const float t = gs.t[p];
+                const bool acc = pend && rt_ss >= armijo_bound(gs.R[p], prm.c1, t, gs.slope[p]);
+                const float a0 = __fmaf_rn(t, gs.pp0[p], gs.th0[p]), a1 = __fmaf_rn(t, gs.pp1[p], gs.th1[p]);
+                __syncwarp();  // every lane has read the state it needs
+                if (pend && (lane & 7) == 0) {
+                    ++gs.evals[p];
+                    if (acc) {
+                        gs.th0[p] = a0;  // the trial point (bitwise tr0, tr1)
+                        gs.th1[p] = a1;
+                        gs.Rfin[p] = rt_ss;  // R at the accepted point, this update's bandwidth
+                        gs.pending[p] = false;
+                    } else {
+                        gs.t[p] = __fmul_rn(t, 0.5f);
+                    }
+                }
+                __syncwarp();
+            } else {
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (!gs.pending[p]) continue;
-                ++gs.evals[p];
-                const float rt = warp_sum(Rt[p]);
-                if (rt >= gs.R[p] + prm.c1 * gs.t[p] * gs.slope[p]) {
-                    gs.th0[p] = tr0[p];
-                    gs.th1[p] = tr1[p];
-                    gs.Rfin[p] = rt;  // R at the accepted point, this update's bandwidth
-                    gs.pending[p] = false;
-                } else {
-                    gs.t[p] *= 0.5f;
+                for (int p = 0; p < P; ++p) {
+                    if (!gs.pending[p]) continue;
+                    ++gs.evals[p];
+                    const float rt = warp_sum(Rt[p]);
+                    if (rt >= armijo_bound(gs.R[p], prm.c1, gs.t[p], gs.slope[p])) {
+                        gs.th0[p] = tr0[p];
+                        gs.th1[p] = tr1[p];
+                        gs.Rfin[p] = rt;  // R at the accepted point, this update's bandwidth
+                        gs.pending[p] = false;
+                    } else {
+                        gs.t[p] *= 0.5f;
+                    }
                 }
             }
         }

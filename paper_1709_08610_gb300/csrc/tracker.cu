@@ -31,6 +31,11 @@ struct retina_tracker {
     bool learned = false;
     int device = 0;
     cudaStream_t cap = nullptr;  // capture stream (graphs cannot be recorded on a legacy stream)
+    // run_host's hit copy: on its own stream, after the previous step's hit
+    // ordering (the one launch that reads the unsorted hits) - not after the
+    // whole previous step - so it overlaps that step's search
+    cudaStream_t copy = nullptr;
+    cudaEvent_t hits_free = nullptr, hits_in = nullptr;
     cudaGraphExec_t exec = nullptr;
     GraphKey key;
     cudaEvent_t marks[RETINA_TRACKER_MARKS] = {};  // stage marks (retina_tracker_set_marks)
@@ -118,12 +123,18 @@ cudaError_t enqueue_step(retina_tracker &t, const GraphKey &k, cudaStream_t st, 
     const float lo = -0.5f, hi = 0.5f, zmin = 50.f;  // the proposer's histogram (as trained)
     cudaError_t err = mark(t, 0, st, capturing);
     if (err == cudaSuccess) err = launch_prepare_hits(t.hits, H, t.offsets, E, RETINA_VELO_SLOPES, t.sorted, t.boxes, st);
+    // every later launch reads the ordered copy: the input buffer is free
+    // (the proposer's histogram and sub-cell sums are integer counts and
+    // fixed-point sums, the same in any hit order)
+    if (err == cudaSuccess)
+        err = capturing ? cudaEventRecordWithFlags(t.hits_free, st, cudaEventRecordExternal)
+                        : cudaEventRecord(t.hits_free, st);
     if (err == cudaSuccess) err = mark(t, 1, st, capturing);
     if (err == cudaSuccess && t.learned) {
-        err = launch_slope_hist(t.hits, H, t.offsets, E, lo, hi, zmin, t.feat, nullptr, st);
+        err = launch_slope_hist(t.sorted, H, t.offsets, E, lo, hi, zmin, t.feat, nullptr, st);
         if (err == cudaSuccess) err = launch_seednet_forward(t.feat, E, t.params, t.logits, t.h1, nullptr, st);
         if (err == cudaSuccess)
-            err = launch_propose_seeds(t.logits, E, (int)S, lo, hi, zmin, 3, t.hits, H, t.offsets, t.seeds, nullptr,
+            err = launch_propose_seeds(t.logits, E, (int)S, lo, hi, zmin, 3, t.sorted, H, t.offsets, t.seeds, nullptr,
                                        st);
     }
     if (err == cudaSuccess) err = mark(t, 2, st, capturing);
@@ -188,6 +199,9 @@ int retina_tracker_destroy(retina_tracker *t) {
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (t->cap) cudaStreamDestroy(t->cap);
+    if (t->copy) cudaStreamDestroy(t->copy);
+    if (t->hits_free) cudaEventDestroy(t->hits_free);
+    if (t->hits_in) cudaEventDestroy(t->hits_in);
     delete t;
     return RETINA_OK;
 }
@@ -204,6 +218,9 @@ int retina_tracker_create(const retina_tracker_config *config, const float *seed
     const int64_t px = E * RETINA_SEEDNET_BINS * RETINA_SEEDNET_BINS;
     cudaError_t e = cudaGetDevice(&t->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->hits_free, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->hits_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = alloc(t->hits, (size_t)H * sizeof(float4));
     if (e == cudaSuccess) e = alloc(t->offsets, (size_t)(E + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = alloc(t->seeds, (size_t)(E * S) * 2 * sizeof(float));
@@ -291,8 +308,13 @@ int retina_tracker_run_host(retina_tracker *t, const float *hits, int64_t n_hits
     const cudaStream_t st = (cudaStream_t)stream;
     const retina_tracker_config &c = t->cfg;
     const size_t S = (size_t)c.seeds_per_event, K = (size_t)c.max_tracks;
-    cudaError_t err = cudaSuccess;
-    if (n_hits > 0) err = cudaMemcpyAsync(t->hits, hits, (size_t)n_hits * sizeof(float4), cudaMemcpyHostToDevice, st);
+    // the hits on the copy stream, once the previous step's hit ordering is
+    // done (a wait on a never-recorded event passes); the step waits for them
+    cudaError_t err = cudaStreamWaitEvent(t->copy, t->hits_free, 0);
+    if (err == cudaSuccess && n_hits > 0)
+        err = cudaMemcpyAsync(t->hits, hits, (size_t)n_hits * sizeof(float4), cudaMemcpyHostToDevice, t->copy);
+    if (err == cudaSuccess) err = cudaEventRecord(t->hits_in, t->copy);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, t->hits_in, 0);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(t->offsets, event_offsets, (size_t)(n_events + 1) * sizeof(int64_t),
                               cudaMemcpyHostToDevice, st);

@@ -111,3 +111,35 @@ def test_tracker_from_host_buffers_equals_device_step(rt):
     with pytest.raises(rt.RetinaError):
         tr.run_host(hits_h, bad, out, stream=s)
     tr.close()
+
+
+def test_back_to_back_host_runs_overlap_safely(rt):
+    # consecutive run_host calls without a synchronisation in between: each
+    # step's hit copy overlaps the previous step's search (it waits only for
+    # that step's hit ordering), and every step still returns exactly its own
+    # batch's tracks
+    from paper_1709_08610_gb300.seednet import DEFAULT_WEIGHTS, read_checkpoint
+    wl = WORKLOADS["velo_stress"]
+    E, S, K = 6, 2048, 2048
+    batches = [_batch(wl, E, 79)[1], _batch(wl, E, 80)[1]]
+    H = max(bb.hits.shape[0] for bb in batches)
+    box = rt.Grid.of(wl)
+    opts = rt.LsOpts(sigma=tuple(wl.sigma_schedule))
+    params = read_checkpoint(DEFAULT_WEIGHTS)[1]["params"]
+    tr = rt.Tracker(box, opts, wl.R0, 2.0, E, H, S, max_tracks=K, params=params)
+    refs = []
+    for bb in batches:
+        tr.step(tr.load(bb.hits, bb.offsets))
+        torch.cuda.synchronize()
+        refs.append((tr.tracks.cpu().clone(), tr.track_R.cpu().clone(), tr.n_tracks.cpu().clone()))
+    ins = [(torch.from_numpy(bb.hits).pin_memory(), torch.from_numpy(bb.offsets).pin_memory()) for bb in batches]
+    outs = [dict(tracks=torch.full((E, K, 2), -5.0).pin_memory(), track_R=torch.full((E, K), -5.0).pin_memory(),
+                 n_tracks=torch.full((E,), -5, dtype=torch.int32).pin_memory()) for _ in range(4)]
+    s = torch.cuda.Stream()
+    for i in range(4):
+        tr.run_host(ins[i % 2][0], ins[i % 2][1], outs[i], stream=s)
+    s.synchronize()
+    for i in range(4):
+        r = refs[i % 2]
+        _same(r[0], r[1], r[2], outs[i]["tracks"], outs[i]["track_R"], outs[i]["n_tracks"], K)
+    tr.close()
