@@ -198,16 +198,13 @@ int retina_alu_probe(int32_t kind, int32_t iters, float *sink, double *ops, void
  * sorts the hits into a spatial order and writes them to sorted_out
  * (float32 [n_hits][4], same event offsets); block b of event e (sorted hits
  * 32 b .. 32 b + 31) gets an 8-float box in boxes_out row
- * floor(event_offsets[e] / 32) + e + b.  Order: per super-chunk of 32768
- * consecutive hits of an event, the hits are grouped by band (stably), each
- * band's run is cut into chunks of 8192, and each chunk is sorted by (code,
- * position in the chunk); a super-chunk of at most 8192 hits is one chunk.
- * Slope model: band = octave of |z| ([0,16), [16,32), ..., [512, inf) mm;
- * NaN in the last), code = band above the Hilbert index (order 8) of the
- * slopes (x/z, y/z) quantised to 256 levels on [-1, 1] (clamped); box = (min,
- * max of x/z, min, max of y/z, min, max of |z|, 0, 0).  2D toy: one band,
- * code = x band above the quantised y; box = (xmin, xmax, ymin, ymax, 0, 0,
- * 0, 0).  boxes_out: float32
+ * floor(event_offsets[e] / 32) + e + b.  Order: each super-chunk of 32768
+ * consecutive hits of an event is sorted by (code, index).  Slope model: code
+ * = band of |z| (octaves [0,16), [16,32), ..., [512, inf) mm; NaN in the
+ * last) above the Hilbert index (order 8) of the slopes (x/z, y/z) quantised
+ * to 256 levels on [-1, 1] (clamped); box = (min, max of x/z, min, max of
+ * y/z, min, max of |z|, 0, 0).  2D toy: code = x band above the quantised y;
+ * box = (xmin, xmax, ymin, ymax, 0, 0, 0, 0).  boxes_out: float32
  * [retina_prepare_hits_box_count(n_hits, n_events)][8].  A box with a
  * non-finite value (e.g. a hit at z = 0) is infinite: never skipped.  The
  * order of hits within an event does not change R beyond float32 summation

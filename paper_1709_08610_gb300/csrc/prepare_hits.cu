@@ -2,22 +2,21 @@
 // so that the response kernels can skip, exactly, blocks whose every term of
 // Eq. 1 is zero in float32.
 //
-// Each hit gets a band and a spatial code.  Slope model: the band is an
-// octave of |z| (from 16 mm; 7 bands) and the code, below the band, is the
-// index of the hit's slopes (u, v) = (x/z, y/z), quantised to 256 levels on
-// [-1, 1] (clamped at the edges), along the Hilbert curve of order 8, whose
-// consecutive cells always touch (a Morton order jumps at every quadrant
-// edge, and a block of 32 hits spanning a jump gets a large box).  2D toy:
-// one band; the code is a band of x over the quantised y.  Per event (one
-// CTA, or one thread-block cluster for few events), in super-chunks of up to
-// SUPER consecutive hits: the hits are grouped by band (stably), each band's
-// run is cut into chunks of up to SORT_CAP hits, and each chunk is sorted by
-// the 32-bit key (code, position in the chunk) - keys are distinct and the
-// order deterministic.  A super-chunk of at most SORT_CAP hits is one chunk
-// (the band is the code's top bits, so one sort already groups it).  Sorting
-// a band whole, rather than cutting the event into chunks that each span all
-// bands, keeps each region of a band in one run of blocks: on 16.5k-hit
-// events it halves the blocks a point cannot skip.
+// Each hit gets a spatial code.  Slope model: a band of |z| (octaves from 16
+// mm; 7 bands) over the index of the hit's slopes (u, v) = (x/z, y/z),
+// quantised to 256 levels on [-1, 1] (clamped at the edges), along the
+// Hilbert curve of order 8, whose consecutive cells always touch (a Morton
+// order jumps at every quadrant edge, and a block of 32 hits spanning a jump
+// gets a large box).  2D toy: a band of x over the quantised y.  Per event
+// (one CTA, or one thread-block cluster for few events), each super-chunk of
+// up to SUPER consecutive hits is sorted by (code, index): chunks of up to
+// SORT_CAP hits are sorted by the 32-bit key (code, position in the chunk),
+// then merged by rank - an element's output position is its rank in its own
+// chunk plus, in every other chunk, the number of codes below its own (or
+// not above it, for the chunks before its own, so that equal codes keep
+// index order).  Sorting the event whole, rather than chunk by chunk, keeps
+// each region of a band in one run of blocks: on 16.5k-hit events it halves
+// the blocks a point cannot skip.
 //
 // The box of a block is (umin, umax, vmin, vmax, |z|min, |z|max) for the
 // slope model: since s^2 = z^2 |(u, v) - theta|^2, it bounds s^2 from below
@@ -37,144 +36,107 @@ namespace retina {
 constexpr int PREP_THREADS = 1024;
 constexpr int IDX_BITS = 13;
 constexpr int SORT_CAP = 1 << IDX_BITS;  // 8192 hits per sorted chunk
-constexpr int SUPER = 32768;             // hits grouped by band at a time (16-bit positions)
-constexpr int N_BANDS = 8;               // band values 0 .. 6 (slope model), 0 (toy)
+constexpr int SUPER_CHUNKS = 4;
+constexpr int SUPER = SUPER_CHUNKS * SORT_CAP;  // 32768 hits sorted together
 
-// Shared scratch of the band grouping: positions g[SUPER] (uint16), then ints
-// band starts [N_BANDS + 1], running counts [N_BANDS], tile totals [N_BANDS],
-// per-warp counts [32][N_BANDS].
-constexpr int GROUP_INTS = (N_BANDS + 1) + N_BANDS + N_BANDS + 32 * N_BANDS;
-constexpr size_t GROUP_BYTES = (size_t)SUPER * sizeof(uint16_t) + GROUP_INTS * sizeof(int);
-
-// v quantised on [lo, lo + 1 / inv_range] to the integers 0 .. levels
+// v quantised on [lo, lo + 1 / inv_range] to the integers 0 .. levels, every
+// operation rounded on its own (no multiply-add contraction with the
+// caller's product), so that the documented order can be restated exactly
 __device__ __forceinline__ uint32_t quant(float v, float lo, float inv_range, float levels) {
-    float t = (v - lo) * inv_range;
+    float t = __fmul_rn(__fsub_rn(v, lo), inv_range);
     t = isfinite(t) ? fminf(fmaxf(t, 0.f), 1.f) : (t > 0.f ? 1.f : 0.f);
-    return (uint32_t)(t * levels);
+    return (uint32_t)__fmul_rn(t, levels);
 }
 
-// band of a hit: slope model |z| octaves [0,16), [16,32), ..., [512, inf)
-// (NaN in the last); 2D toy: 0
-__device__ __forceinline__ uint32_t hit_band(const float4 h, int model) {
-    if (model != RETINA_VELO_SLOPES) return 0;
-    const float az = fabsf(h.z);
-    uint32_t band = 0;
-    for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
-    return band;
-}
-
-// spatial code of a hit, below 2^19, its band in the top bits (only orders
-// the hits; any value is valid)
+// spatial code of a hit, below 2^19 (only orders the hits; any value is valid)
 __device__ __forceinline__ uint32_t hit_code(const float4 h, int model) {
     if (model == RETINA_VELO_SLOPES) {
+        const float az = fabsf(h.z);
+        uint32_t band = 0;  // |z| octaves: [0,16), [16,32), ..., [512, inf) (NaN in the last)
+        for (float lim = 16.f; band < 6 && !(az < lim); lim *= 2.f) ++band;
         const float rz = __frcp_rn(h.z);
-        return (hit_band(h, model) << 16) |
-               hilbert_index<8>(quant(h.x * rz, -1.f, 0.5f, 255.f), quant(h.y * rz, -1.f, 0.5f, 255.f));
+        return (band << 16) | hilbert_index<8>(quant(__fmul_rn(h.x, rz), -1.f, 0.5f, 255.f),
+                                               quant(__fmul_rn(h.y, rz), -1.f, 0.5f, 255.f));
     }
     return ((float_order_key(h.x) >> 25) << 7) | quant(h.y, -8.f, 1.f / 16.f, 127.f);
 }
 
-// Stable grouping of the positions 0 .. n-1 (n <= SUPER) of the hits at base
-// by band: on return g[bs[q] .. bs[q+1]) lists, in increasing order, the
-// positions whose hit has band q.  All threads of the CTA call it (at least
-// N_BANDS warps, at most 32); it ends with a barrier.
-__device__ __forceinline__ void group_by_band(const float4 *__restrict__ hits, int64_t base, int n, int model, uint16_t *g,
-                              int *si) {
-    int *bs = si, *run = bs + N_BANDS + 1, *tot = run + N_BANDS, *wc = tot + N_BANDS;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    if (tid < N_BANDS) run[tid] = 0;
-    __syncthreads();
-    for (int t0 = 0; t0 < n; t0 += blockDim.x) {  // band counts
-        const int i = t0 + tid;
-        const int b = i < n ? (int)hit_band(__ldg(hits + base + i), model) : N_BANDS;
-#pragma unroll
-        for (int q = 0; q < N_BANDS; ++q) {
-            const unsigned m = __ballot_sync(0xffffffffu, b == q);
-            if (lane == 0 && m) atomicAdd(&run[q], __popc(m));
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int q = 0; q < N_BANDS; ++q) {
-            bs[q] = acc;
-            acc += run[q];
-            run[q] = 0;
-        }
-        bs[N_BANDS] = acc;
-    }
-    __syncthreads();
-    for (int t0 = 0; t0 < n; t0 += blockDim.x) {  // stable scatter, one tile of blockDim positions at a time
-        const int i = t0 + tid;
-        const int b = i < n ? (int)hit_band(__ldg(hits + base + i), model) : N_BANDS;
-        int r = 0;
-#pragma unroll
-        for (int q = 0; q < N_BANDS; ++q) {
-            const unsigned m = __ballot_sync(0xffffffffu, b == q);
-            if (b == q) r = __popc(m & lt);
-            if (lane == 0) wc[w * N_BANDS + q] = __popc(m);
-        }
-        __syncthreads();
-        if (w < N_BANDS) {  // warp q: exclusive scan of band q's per-warp counts, in place
-            const int c = lane < nw ? wc[lane * N_BANDS + w] : 0;
-            int acc = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, acc, o);
-                if (lane >= o) acc += u;
-            }
-            if (lane < nw) wc[lane * N_BANDS + w] = acc - c;
-            if (lane == 31) tot[w] = acc;
-        }
-        __syncthreads();
-        if (b < N_BANDS) g[bs[b] + run[b] + wc[w * N_BANDS + b] + r] = (uint16_t)i;
-        __syncthreads();
-        if (tid < N_BANDS) run[tid] += tot[tid];
-    }
-    __syncthreads();
+// key of chunk position i (n valid; padding ~0 sorts last)
+__device__ __forceinline__ uint32_t chunk_key(const float4 *__restrict__ hits, int64_t base, int i, int n, int model) {
+    return i < n ? ((hit_code(__ldg(hits + base + i), model) << IDX_BITS) | (uint32_t)i) : 0xffffffffu;
 }
 
-// One chunk: positions p0 .. p0 + n - 1 of the super-chunk at base (hit
-// base + g[p] of the grouping, or base + p without one).  Keys of chunk
-// positions t R + r (padding ~0 sorts last), sorted, then the hits gathered
-// in key order to sorted[base + p0 ..].
+// Keys of chunk positions t R + r, sorted, then the hits gathered in key
+// order to sorted[base ..] (a super-chunk that is one chunk).
 template <int R>
-__device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base,
-                                                const uint16_t *__restrict__ g, int p0, int n, int model,
+__device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base, int n, int model,
                                                 float4 *__restrict__ sorted, uint32_t *x) {
     uint32_t v[R];
     const int t = threadIdx.x;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = t * R + r;
-        v[r] = 0xffffffffu;
-        if (i < n) {
-            const int src = g ? (int)g[p0 + i] : p0 + i;
-            v[r] = (hit_code(__ldg(hits + base + src), model) << IDX_BITS) | (uint32_t)i;
-        }
-    }
+    for (int r = 0; r < R; ++r) v[r] = chunk_key(hits, base, t * R + r, n, model);
     bitonic_sort_regs<uint32_t, R, PREP_THREADS>(v, x);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t * R + r;
-        if (i < n) {
-            const int j = p0 + (int)(v[r] & (SORT_CAP - 1));
-            sorted[base + p0 + i] = __ldg(hits + base + (g ? (int)g[j] : j));
-        }
+        if (i < n) sorted[base + i] = __ldg(hits + base + (int)(v[r] & (SORT_CAP - 1)));
     }
 }
 
-__device__ __forceinline__ void sort_chunk(const float4 *__restrict__ hits, int64_t base, const uint16_t *g, int p0,
-                                           int n, int model, float4 *__restrict__ sorted, uint32_t *x) {
-    if (n <= PREP_THREADS)
-        sort_and_gather<1>(hits, base, g, p0, n, model, sorted, x);
-    else if (n <= 2 * PREP_THREADS)
-        sort_and_gather<2>(hits, base, g, p0, n, model, sorted, x);
-    else if (n <= 4 * PREP_THREADS)
-        sort_and_gather<4>(hits, base, g, p0, n, model, sorted, x);
-    else
-        sort_and_gather<8>(hits, base, g, p0, n, model, sorted, x);
+// The same sort, the sorted keys left in K[0 .. 1024 R) (K is also the
+// sort's exchange buffer).
+template <int R>
+__device__ __forceinline__ void sort_keys(const float4 *__restrict__ hits, int64_t base, int n, int model,
+                                          uint32_t *K) {
+    uint32_t v[R];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = chunk_key(hits, base, t * R + r, n, model);
+    bitonic_sort_regs<uint32_t, R, PREP_THREADS>(v, K);
+    __syncthreads();  // every exchange read is done before K holds the result
+#pragma unroll
+    for (int r = 0; r < R; ++r) K[t * R + r] = v[r];
+}
+
+template <bool GATHER>
+__device__ __forceinline__ void sort_chunk(const float4 *__restrict__ hits, int64_t base, int n, int model,
+                                           float4 *__restrict__ sorted, uint32_t *x) {
+    if (n <= PREP_THREADS) {
+        if (GATHER) sort_and_gather<1>(hits, base, n, model, sorted, x); else sort_keys<1>(hits, base, n, model, x);
+    } else if (n <= 2 * PREP_THREADS) {
+        if (GATHER) sort_and_gather<2>(hits, base, n, model, sorted, x); else sort_keys<2>(hits, base, n, model, x);
+    } else if (n <= 4 * PREP_THREADS) {
+        if (GATHER) sort_and_gather<4>(hits, base, n, model, sorted, x); else sort_keys<4>(hits, base, n, model, x);
+    } else {
+        if (GATHER) sort_and_gather<8>(hits, base, n, model, sorted, x); else sort_keys<8>(hits, base, n, model, x);
+    }
+}
+
+// Number of the first n entries of the ascending array at(.) below thr
+// (binary search; at(j) reads entry j).
+template <typename At>
+__device__ __forceinline__ int count_below(At &&at, int n, uint64_t thr) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint64_t)at(mid) < thr)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Keys below this bound in another chunk go before a key of code `code`:
+// codes below it, and equal codes too when that chunk comes first (equal
+// codes keep index order).
+__device__ __forceinline__ uint64_t rank_bound(uint32_t code, bool earlier_chunk) {
+    return (uint64_t)(code + (earlier_chunk ? 1u : 0u)) << IDX_BITS;
+}
+
+// size of chunk c of a super-chunk of ns hits
+__device__ __forceinline__ int chunk_size(int ns, int c) {
+    return ns - c * SORT_CAP < SORT_CAP ? ns - c * SORT_CAP : SORT_CAP;
 }
 
 // Boxes of the blocks of 32 sorted hits starting at chunk positions lo .. hi
@@ -228,9 +190,7 @@ __device__ __forceinline__ void chunk_boxes(const float4 *__restrict__ sorted, i
 __global__ void __launch_bounds__(PREP_THREADS)
 prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int model,
                     float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
-    extern __shared__ __align__(16) uint32_t keys[];  // [SORT_CAP], then the grouping scratch
-    uint16_t *g = reinterpret_cast<uint16_t *>(keys + SORT_CAP);
-    int *si = reinterpret_cast<int *>(g + SUPER);
+    extern __shared__ __align__(16) uint32_t K[];  // [SUPER]: each chunk's sorted keys
     const int e = blockIdx.x;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
@@ -240,14 +200,25 @@ prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
         const int ns = (int)((H - s0) < SUPER ? (H - s0) : SUPER);
         const int64_t base = hb + s0;
         if (ns <= SORT_CAP) {
-            sort_chunk(hits, base, nullptr, 0, ns, model, sorted, keys);
+            sort_chunk<true>(hits, base, ns, model, sorted, K);
         } else {
-            group_by_band(hits, base, ns, model, g, si);
-            for (int q = 0; q < N_BANDS; ++q) {
-                const int q0 = si[q], q1 = si[q + 1];
-                for (int p0 = q0; p0 < q1; p0 += SORT_CAP) {
-                    sort_chunk(hits, base, g, p0, (q1 - p0) < SORT_CAP ? (q1 - p0) : SORT_CAP, model, sorted, keys);
-                    __syncthreads();
+            const int nch = (ns + SORT_CAP - 1) / SORT_CAP;
+            for (int c = 0; c < nch; ++c)
+                sort_chunk<false>(hits, base + c * SORT_CAP, chunk_size(ns, c), model, sorted, K + c * SORT_CAP);
+            __syncthreads();
+            // merge by rank: chunk c's j-th key goes to j + (keys before it in the other chunks)
+            for (int c = 0; c < nch; ++c) {
+                const int n = chunk_size(ns, c);
+                for (int j = threadIdx.x; j < n; j += PREP_THREADS) {
+                    const uint32_t key = K[c * SORT_CAP + j];
+                    const uint32_t code = key >> IDX_BITS;
+                    int out = j;
+                    for (int c2 = 0; c2 < nch; ++c2) {
+                        if (c2 == c) continue;
+                        const uint32_t *K2 = K + c2 * SORT_CAP;
+                        out += count_below([&](int m) { return K2[m]; }, chunk_size(ns, c2), rank_bound(code, c2 < c));
+                    }
+                    sorted[base + out] = __ldg(hits + base + c * SORT_CAP + (int)(key & (SORT_CAP - 1)));
                 }
             }
         }
@@ -335,46 +306,42 @@ __device__ __forceinline__ void bitonic_cluster(uint32_t (&v)[R], uint32_t *x, i
     }
 }
 
-template <int R>
-__device__ __forceinline__ void cluster_sort_gather(const float4 *__restrict__ hits, int64_t base,
-                                                    const uint16_t *__restrict__ g, int p0, int n, int model,
-                                                    float4 *__restrict__ sorted, uint32_t *x, int rank) {
+// One chunk over the cluster: keys sorted, then either the hits gathered in
+// key order (GATHER: a super-chunk that is one chunk) or this CTA's slice of
+// the sorted keys kept in Ks[0 .. P).
+template <int R, bool GATHER>
+__device__ __forceinline__ void cluster_sort(const float4 *__restrict__ hits, int64_t base, int n, int model,
+                                             float4 *__restrict__ sorted, uint32_t *x, uint32_t *Ks, int rank) {
     constexpr int P = CL_THREADS * R;
     uint32_t v[R];
     const int t = threadIdx.x;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = rank * P + t * R + r;
-        v[r] = 0xffffffffu;
-        if (i < n) {
-            const int src = g ? (int)g[p0 + i] : p0 + i;
-            v[r] = (hit_code(__ldg(hits + base + src), model) << IDX_BITS) | (uint32_t)i;
-        }
-    }
+    for (int r = 0; r < R; ++r) v[r] = chunk_key(hits, base, rank * P + t * R + r, n, model);
     bitonic_cluster<R>(v, x, rank);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = rank * P + t * R + r;
-        if (i < n) {
-            const int j = p0 + (int)(v[r] & (SORT_CAP - 1));
-            sorted[base + p0 + i] = __ldg(hits + base + (g ? (int)g[j] : j));
+        if (GATHER) {
+            if (i < n) sorted[base + i] = __ldg(hits + base + (int)(v[r] & (SORT_CAP - 1)));
+        } else {
+            Ks[t * R + r] = v[r];
         }
     }
 }
 
 // Sorts one chunk over the cluster; returns the chunk positions per CTA.
-__device__ __forceinline__ int cluster_sort_chunk(const float4 *__restrict__ hits, int64_t base, const uint16_t *g,
-                                                  int p0, int n, int model, float4 *__restrict__ sorted, uint32_t *x,
-                                                  int rank) {
+template <bool GATHER>
+__device__ __forceinline__ int cluster_sort_chunk(const float4 *__restrict__ hits, int64_t base, int n, int model,
+                                                  float4 *__restrict__ sorted, uint32_t *x, uint32_t *Ks, int rank) {
     if (n <= CL * CL_THREADS) {
-        cluster_sort_gather<1>(hits, base, g, p0, n, model, sorted, x, rank);
+        cluster_sort<1, GATHER>(hits, base, n, model, sorted, x, Ks, rank);
         return CL_THREADS;
     }
     if (n <= 2 * CL * CL_THREADS) {
-        cluster_sort_gather<2>(hits, base, g, p0, n, model, sorted, x, rank);
+        cluster_sort<2, GATHER>(hits, base, n, model, sorted, x, Ks, rank);
         return 2 * CL_THREADS;
     }
-    cluster_sort_gather<4>(hits, base, g, p0, n, model, sorted, x, rank);
+    cluster_sort<4, GATHER>(hits, base, n, model, sorted, x, Ks, rank);
     return 4 * CL_THREADS;
 }
 
@@ -382,8 +349,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1)
 prepare_hits_cluster_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off,
                             int model, float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
     __shared__ uint32_t x[SORT_CAP / CL];
-    extern __shared__ __align__(16) uint16_t g[];  // [SUPER], then the grouping's ints
-    int *si = reinterpret_cast<int *>(g + SUPER);
+    __shared__ uint32_t Ks[SUPER_CHUNKS][SORT_CAP / CL];  // this CTA's slice of each chunk's sorted keys
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     pdl_release();  // the grid kernel may be scheduled once every CTA has started
@@ -395,38 +361,52 @@ prepare_hits_cluster_kernel(const float4 *__restrict__ hits, int64_t n_hits, con
     for (int64_t s0 = 0; s0 < H; s0 += SUPER) {
         const int ns = (int)((H - s0) < SUPER ? (H - s0) : SUPER);
         const int64_t base = hb + s0;
-        // every CTA groups a super-chunk of more than SORT_CAP hits itself (the
-        // same result); one of at most SORT_CAP hits is one chunk
-        const bool grouped = ns > SORT_CAP;
-        if (grouped) {
-            group_by_band(hits, base, ns, model, g, si);
-        } else {
-            if (threadIdx.x <= N_BANDS) si[threadIdx.x] = threadIdx.x == 0 ? 0 : ns;
-            __syncthreads();
-        }
-        int P = 0;
-        for (int q = 0; q < N_BANDS; ++q) {
-            const int q0 = si[q], q1 = si[q + 1];
-            for (int p0 = q0; p0 < q1; p0 += SORT_CAP) {
-                P = cluster_sort_chunk(hits, base, grouped ? g : nullptr, p0,
-                                       (q1 - p0) < SORT_CAP ? (q1 - p0) : SORT_CAP, model, sorted, x, rank);
-                if (grouped) cl.sync();  // x is reused by the next chunk's exchanges
-            }
-        }
         int lo, hi;
-        if (grouped) {
-            __threadfence();
-            cl.sync();  // a block's hits may come from several CTAs' gathers
-            const int per = (((ns + 31) / 32) + CL - 1) / CL * 32;  // positions per CTA, whole blocks
-            lo = rank * per;
-            hi = (rank + 1) * per < ns ? (rank + 1) * per : ns;
-        } else {
+        if (ns <= SORT_CAP) {
+            const int P = cluster_sort_chunk<true>(hits, base, ns, model, sorted, x, nullptr, rank);
             __syncthreads();  // this CTA's gathered hits, read back for its boxes
             lo = rank * P;
             hi = (rank + 1) * P < ns ? (rank + 1) * P : ns;
+        } else {
+            const int nch = (ns + SORT_CAP - 1) / SORT_CAP;
+            int Pc[SUPER_CHUNKS];
+#pragma unroll
+            for (int c = 0; c < SUPER_CHUNKS; ++c) {
+                if (c >= nch) break;
+                Pc[c] = cluster_sort_chunk<false>(hits, base + c * SORT_CAP, chunk_size(ns, c), model, sorted, x,
+                                                  Ks[c], rank);
+                cl.sync();  // x is reused by the next chunk's exchanges; every slice is stored
+            }
+            // merge by rank: each CTA places its own slices' keys, searching
+            // the other chunks through distributed shared memory
+#pragma unroll
+            for (int c = 0; c < SUPER_CHUNKS; ++c) {
+                if (c >= nch) break;
+                const int n = chunk_size(ns, c);
+                for (int m = threadIdx.x; m < Pc[c]; m += CL_THREADS) {
+                    const int j = rank * Pc[c] + m;
+                    if (j >= n) break;
+                    const uint32_t key = Ks[c][m];
+                    const uint32_t code = key >> IDX_BITS;
+                    int out = j;
+#pragma unroll
+                    for (int c2 = 0; c2 < SUPER_CHUNKS; ++c2) {
+                        if (c2 >= nch || c2 == c) continue;
+                        const int P2 = Pc[c2];
+                        out += count_below([&](int q) { return cl.map_shared_rank(&Ks[c2][0], q / P2)[q % P2]; },
+                                           chunk_size(ns, c2), rank_bound(code, c2 < c));
+                    }
+                    sorted[base + out] = __ldg(hits + base + c * SORT_CAP + (int)(key & (SORT_CAP - 1)));
+                }
+            }
+            __threadfence();
+            cl.sync();  // a block's hits come from several CTAs' writes
+            const int per = (((ns + 31) / 32) + CL - 1) / CL * 32;  // positions per CTA, whole blocks
+            lo = rank * per;
+            hi = (rank + 1) * per < ns ? (rank + 1) * per : ns;
         }
         if (lo < ns) chunk_boxes(sorted, base, ns, lo, hi, model, box_base + s0 / 32, boxes);
-        cl.sync();  // x and the grouping scratch are reused by the next super-chunk
+        cl.sync();  // x and Ks are reused (and read remotely) until every CTA is here
     }
 }
 
@@ -438,12 +418,10 @@ cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_
     // the GPU many times over (throughput): one CTA per event, no cluster
     // exchanges
     if ((int64_t)n_events * CL <= 4LL * sm_count()) {
-        cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_cluster_kernel), GROUP_BYTES);
-        if (aerr != cudaSuccess) return aerr;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(n_events * CL));
         cfg.blockDim = dim3(CL_THREADS);
-        cfg.dynamicSmemBytes = GROUP_BYTES;
+        cfg.dynamicSmemBytes = 0;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -455,7 +433,7 @@ cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_
         count_launches(1);
         return cudaLaunchKernelEx(&cfg, prepare_hits_cluster_kernel, hits, n_hits, off, model, sorted, boxes);
     }
-    const size_t smem = (size_t)SORT_CAP * sizeof(uint32_t) + GROUP_BYTES;
+    const size_t smem = (size_t)SUPER * sizeof(uint32_t);
     {
         cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_kernel), smem);
         if (aerr != cudaSuccess) return aerr;

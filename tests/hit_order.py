@@ -1,10 +1,8 @@
 """Host restatement of retina_prepare_hits' documented hit order (test
-infrastructure): per super-chunk of 32768 consecutive hits, the hits grouped by
-band (stably), each band's run cut into chunks of 8192, each chunk sorted by
-(spatial code, position in the chunk); a super-chunk of at most 8192 hits is
-one chunk.  Slope model: band = octave of |z| from 16 mm (7 bands, NaN in the
-last), code = band above the Hilbert index (order 8) of the slopes quantised
-on [-1, 1]; 2D toy: one band, code = a band of x above the quantised y.
+infrastructure): each super-chunk of 32768 consecutive hits of an event is
+sorted by (spatial code, index).  Slope model: code = octave band of |z| from
+16 mm (7 bands, NaN in the last) above the Hilbert index (order 8) of the
+slopes quantised on [-1, 1]; 2D toy: code = a band of x above the quantised y.
 """
 import numpy as np
 
@@ -54,13 +52,6 @@ def bands_codes(h, model):
 def documented_order(h, model):
     perm = []
     for s0 in range(0, len(h), 32768):
-        band, code = bands_codes(h[s0:s0 + 32768], model)
-        n = len(band)
-        runs = [np.arange(n)] if n <= 8192 else [np.flatnonzero(band == q) for q in range(8)]
-        for run in runs:
-            for c0 in range(0, len(run), 8192):
-                ch = run[c0:c0 + 8192]
-                perm.append(s0 + ch[np.lexsort((np.arange(len(ch)), code[ch]))])
+        _, code = bands_codes(h[s0:s0 + 32768], model)
+        perm.append(s0 + np.lexsort((np.arange(len(code)), code)))
     return np.concatenate(perm) if perm else np.zeros(0, np.int64)
-
-

@@ -164,7 +164,7 @@ def test_non_finite_hit_blocks_are_never_skipped(rt):
 def _order_events():
     wl = WORKLOADS["velo"]
     rng = np.random.default_rng(17)
-    one_band = np.zeros((20000, 4), np.float32)  # a band of more than 8192 hits: two chunks
+    one_band = np.zeros((20000, 4), np.float32)  # one band, three sorted chunks merged
     one_band[:, 2] = rng.uniform(256, 511, 20000)
     one_band[:, :2] = rng.uniform(-0.4, 0.4, (20000, 2)) * one_band[:, 2:3]
     odd = make_event(wl, 9, 3, n_tracks=300, vertex_sigma=(0, 0, 0)).hits.copy()
@@ -173,7 +173,7 @@ def _order_events():
     odd[11, 2] = np.nan
     odd[13, 1] = np.inf
     return [make_event(wl, 9, 0, vertex_sigma=(0, 0, 0)).hits,  # one chunk
-            make_event(wl, 9, 1, n_tracks=700, vertex_sigma=(0, 0, 0)).hits,  # grouped by band
+            make_event(wl, 9, 1, n_tracks=700, vertex_sigma=(0, 0, 0)).hits,  # two chunks merged
             make_event(wl, 9, 2, n_tracks=1500, vertex_sigma=(0, 0, 0)).hits,  # two super-chunks
             one_band, odd, np.zeros((0, 4), np.float32)]
 
