@@ -513,10 +513,10 @@ __device__ __forceinline__ bool span_culled(const float4 A, const float w, const
 // Without boxes it is for_each_hit.  With boxes, each chunk of KEPT_CHUNK
 // blocks is tested (lane l tests blocks l, l + 32, l + 64, l + 96 of the
 // chunk in turn, or, for a chunk of staged slope-model boxes, superblock l
-// first and then the blocks of the kept superblocks), the ballots give the
-// blocks some point needs, in increasing order, as offsets in the warp's
-// list, and the warp walks the list, lane l taking hit 32 b + l of each
-// block: the same per-lane order as the full pass minus blocks whose terms
+// first and then the blocks of the kept superblocks), the ballots append
+// the blocks some point needs, in increasing order, as offsets to the warp's
+// list (consecutive chunks while they fit), and the warp walks the list,
+// lane l taking hit 32 b + l of each block: the same per-lane order as the full pass minus blocks whose terms
 // are all exactly zero - so every sum is bitwise the full pass's sum.
 // Returns the hits visited (for the work counters).
 template <int MODEL, int UNROLL = 2, typename T, typename F, typename F2>
@@ -533,98 +533,125 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
     const int nblk = (H + 31) >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int *slot = list + KEPT_CHUNK;  // the warp's 32 superblock slots
-    for (int c0 = 0; c0 < nblk; c0 += KEPT_CHUNK) {
+    // Kept blocks of consecutive chunks collect in the list (increasing block
+    // order) as long as a chunk's candidates are sure to fit; then the list
+    // is walked once - usually a single walk per pass.
+    int c0 = 0;
+    for (;;) {
         int cnt = 0;
-        if (MODEL == RETINA_VELO_SLOPES && c0 + KEPT_CHUNK <= n_sbox) {
-            // two levels: lane l tests superblock c0 / 4 + l (blocks 4 of them),
-            // then the blocks of the superblocks some point needs, in
-            // increasing order (superblock rank, block within it)
-            const int q = (c0 >> 2) + lane;
-            const bool keep_q = needed(ssb[q], ssz2[q]);
-            const unsigned mq = __ballot_sync(0xffffffffu, keep_q);
-            if (mq == 0u) continue;
-            if (keep_q) slot[__popc(mq & lt)] = q;
-            __syncwarp();
-            const int n_sub = 4 * __popc(mq);
-            for (int k0 = 0; k0 < n_sub; k0 += 32) {
-                const int k = k0 + lane;
-                bool keep = false;
-                int b = 0;
-                if (k < n_sub) {
-                    b = 4 * slot[k >> 2] + (k & 3);
-                    keep = needed(sbox[b], sz2[b]);
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep) list[cnt + __popc(m & lt)] = b * 32;
-                cnt += __popc(m);
+        bool done = false;
+        for (;;) {
+            if (c0 >= nblk) {
+                done = true;
+                break;
             }
-        } else {
-#pragma unroll 1
-            for (int w = 0; w < KEPT_CHUNK / 32 && c0 + 32 * w < nblk; ++w) {  // the event's last chunk may be short
-                const int b = c0 + 32 * w + lane;
-                bool keep = false;
-                if (b < nblk) {
-                    float4 A;
-                    float z2;
-                    if (b < n_sbox) {
-                        A = sbox[b];
-                        z2 = sz2[b];
-                    } else {
-                        A = __ldg(gbox + 2 * b);
-                        z2 = search_box<MODEL>(A, __ldg(gbox + 2 * b + 1));
+            if (MODEL == RETINA_VELO_SLOPES && c0 + KEPT_CHUNK <= n_sbox) {
+                // two levels: lane l tests superblock c0 / 4 + l (blocks 4 of them),
+                // then the blocks of the superblocks some point needs, in
+                // increasing order (superblock rank, block within it)
+                const int q = (c0 >> 2) + lane;
+                const bool keep_q = needed(ssb[q], ssz2[q]);
+                const unsigned mq = __ballot_sync(0xffffffffu, keep_q);
+                const int n_sub = 4 * __popc(mq);
+                if (cnt + n_sub > KEPT_CHUNK) break;  // walk the list first, then test this chunk again
+                c0 += KEPT_CHUNK;
+                if (mq == 0u) continue;
+                if (keep_q) slot[__popc(mq & lt)] = q;
+                __syncwarp();
+                for (int k0 = 0; k0 < n_sub; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool keep = false;
+                    int b = 0;
+                    if (k < n_sub) {
+                        b = 4 * slot[k >> 2] + (k & 3);
+                        keep = needed(sbox[b], sz2[b]);
                     }
-                    keep = needed(A, z2);
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep) list[cnt + __popc(m & lt)] = b * 32;
+                    cnt += __popc(m);
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep) list[cnt + __popc(m & lt)] = b * 32;
-                cnt += __popc(m);
+                __syncwarp();  // the slots are rewritten by the next chunk
+            } else {
+                const int n_chunk = nblk - c0 < KEPT_CHUNK ? nblk - c0 : KEPT_CHUNK;
+                if (cnt + n_chunk > KEPT_CHUNK) break;  // walk the list first
+#pragma unroll 1
+                for (int w = 0; w < KEPT_CHUNK / 32 && 32 * w < n_chunk; ++w) {
+                    const int b = c0 + 32 * w + lane;
+                    bool keep = false;
+                    if (b < nblk) {
+                        float4 A;
+                        float z2;
+                        if (b < n_sbox) {
+                            A = sbox[b];
+                            z2 = sz2[b];
+                        } else {
+                            A = __ldg(gbox + 2 * b);
+                            z2 = search_box<MODEL>(A, __ldg(gbox + 2 * b + 1));
+                        }
+                        keep = needed(A, z2);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep) list[cnt + __popc(m & lt)] = b * 32;
+                    cnt += __popc(m);
+                }
+                c0 += KEPT_CHUNK;
             }
         }
         __syncwarp();
-        if (cnt == 0) continue;
-        // hits visited: 32 per kept block, the event's last block holding H - 32 (nblk - 1)
-        const int last = list[cnt - 1];
-        visited += 32 * cnt - (last == 32 * (nblk - 1) ? 32 * nblk - H : 0);
-        // One loop body for every kept block (the kernel is large enough that
-        // its instruction footprint, not its instruction count, sets the
-        // pace: a second copy of the pair arithmetic doubled the instruction
-        // fetch stalls).  Blocks held whole in shared memory form a prefix of
-        // the list and are read from there, the rest from global memory
-        // through the same generic pointer (a staged hit is the same value in
-        // both places); the event's last block, when partial, is left to the
-        // one-block remainder, whose lanes past the event add nothing.  Per
-        // lane the hits are added in list order, and f2(a, b) adds exactly
-        // what f(a); f(b) adds, so every sum is the full pass's.
-        const int n_fast = last + 32 <= n_staged ? cnt : (cnt > 1 && list[cnt - 2] + 32 <= n_staged ? cnt - 1 : 0);
-        const int n_pairs_end = cnt - ((last == 32 * (nblk - 1) && (H & 31)) ? 1 : 0);
-        int i = 0;
-#pragma unroll 1
-        for (int seg = 0; seg < 2; ++seg) {
-            const float4 *src = seg == 0 ? sh : gh;
-            const int end = seg == 0 ? (n_fast < n_pairs_end ? n_fast : n_pairs_end) : n_pairs_end;
-#pragma unroll 1
-            for (; i + UNROLL <= end; i += UNROLL) {
-                // UNROLL = 4 (one point per warp, latency-bound): four blocks in flight
-                const float4 ha = src[list[i] + lane], hb = src[list[i + 1] + lane];
-                if (UNROLL == 4) {
-                    const float4 hc = src[list[i + 2] + lane], hd = src[list[i + 3] + lane];
-                    f2(ha, hb);
-                    f2(hc, hd);
-                } else {
-                    f2(ha, hb);
+        if (cnt > 0) {
+            // hits visited: 32 per kept block, the event's last block holding H - 32 (nblk - 1)
+            const int last = list[cnt - 1];
+            visited += 32 * cnt - (last == 32 * (nblk - 1) ? 32 * nblk - H : 0);
+            // One loop body for every kept block (the kernel is large enough that
+            // its instruction footprint, not its instruction count, sets the
+            // pace: a second copy of the pair arithmetic doubled the instruction
+            // fetch stalls).  Blocks held whole in shared memory form a prefix of
+            // the list and are read from there, the rest from global memory
+            // through the same generic pointer (a staged hit is the same value in
+            // both places); the event's last block, when partial, is left to the
+            // one-block remainder, whose lanes past the event add nothing.  Per
+            // lane the hits are added in list order, and f2(a, b) adds exactly
+            // what f(a); f(b) adds, so every sum is the full pass's.
+            int n_fast = cnt;  // the staged prefix of the list
+            if (last + 32 > n_staged) {
+                n_fast = 0;
+                for (int k0 = 0; k0 < cnt; k0 += 32) {
+                    const int k = k0 + lane;
+                    n_fast += __popc(__ballot_sync(0xffffffffu, k < cnt && list[k] + 32 <= n_staged));
                 }
             }
-            if (UNROLL == 4 && i + 2 <= end) {
-                f2(src[list[i] + lane], src[list[i + 1] + lane]);
-                i += 2;
-            }
-        }
+            const int n_pairs_end = cnt - ((last == 32 * (nblk - 1) && (H & 31)) ? 1 : 0);
+            int i = 0;
 #pragma unroll 1
-        for (; i < cnt; ++i) {
-            const int k = list[i] + lane;
-            if (k < H) f(gh[k]);
+            for (int seg = 0; seg < 2; ++seg) {
+                const float4 *src = seg == 0 ? sh : gh;
+                const int end = seg == 0 ? (n_fast < n_pairs_end ? n_fast : n_pairs_end) : n_pairs_end;
+#pragma unroll 1
+                for (; i + UNROLL <= end; i += UNROLL) {
+                    // UNROLL = 4 (one point per warp, latency-bound): four blocks in flight
+                    const float4 ha = src[list[i] + lane], hb = src[list[i + 1] + lane];
+                    if (UNROLL == 4) {
+                        const float4 hc = src[list[i + 2] + lane], hd = src[list[i + 3] + lane];
+                        f2(ha, hb);
+                        f2(hc, hd);
+                    } else {
+                        f2(ha, hb);
+                    }
+                }
+                if (UNROLL == 4 && i + 2 <= end) {
+                    f2(src[list[i] + lane], src[list[i + 1] + lane]);
+                    i += 2;
+                }
+            }
+#pragma unroll 1
+            for (; i < cnt; ++i) {
+                const int k = list[i] + lane;
+                const float4 *src = list[i] + 32 <= n_staged ? sh : gh;  // a staged remainder from shared memory
+                if (k < H) f(src[k]);
+            }
+            __syncwarp();  // the list is rewritten by the next round
         }
-        __syncwarp();  // the list is rewritten by the next chunk
+        if (done) break;
     }
     return visited;
 }
