@@ -75,7 +75,7 @@ constexpr size_t batch_state_bytes(int warps) {
 }
 
 // at most 64 registers per thread: 2048 / (32 WARPS) CTAs of WARPS warps fit the register file
-template <int MODEL, int P, int WARPS, int UPD>
+template <int MODEL, int P, int WARPS, int UPD, bool RL>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(BatchArgs a, LsParams prm) {
     extern __shared__ float4 sh[];
     __shared__ int cur_e;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
             if (g >= groups) break;
             const int64_t s = s0 + (int64_t)g * P;
             const int n_live = (int)((s1 - s) < P ? (s1 - s) : P);
-            search_group<MODEL, P, UPD, SS>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
+            search_group<MODEL, P, UPD, SS, RL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
                                             a.seeds + 2 * s, n_live, prm, a.theta_out + 2 * s, a.R_out + s,
                                             a.status + s, a.n_evals ? a.n_evals + s : nullptr, a.work, gstate);
         }
@@ -159,9 +159,9 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) batched_search_kernel(
 
 size_t batched_ws_bytes(int n_events) { return ((size_t)(n_events + 2) * sizeof(int32_t) + 255) / 256 * 256; }
 
-template <int MODEL, int P, int WARPS, int UPD>
+template <int MODEL, int P, int WARPS, int UPD, bool RL = false>
 static cudaError_t launch_batched_t(BatchArgs a, const LsParams &prm, int ctas, cudaStream_t st) {
-    auto kern = batched_search_kernel<MODEL, P, WARPS, UPD>;
+    auto kern = batched_search_kernel<MODEL, P, WARPS, UPD, RL>;
     // boxes take the shared memory the hits and the warps' lists leave (at
     // least the staged hits' blocks, at most 4096 blocks = 131072 hits)
     a.box_cap = default_box_cap(a.smem_hits);
@@ -196,6 +196,16 @@ static cudaError_t launch_batched_t(BatchArgs a, const LsParams &prm, int ctas, 
 
 template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON>
 static cudaError_t launch_batched_w(int warps, const BatchArgs &a, const LsParams &prm, int ctas, cudaStream_t st) {
+    // four packed slope-model seeds on events of at most 128 blocks on
+    // average: the kernel whose updates keep one kept-block list for their
+    // trials (a separate instantiation, so the other shapes' code is untouched)
+    if constexpr (MODEL == RETINA_VELO_SLOPES && P == 4 && UPD == RETINA_UPDATE_TRUNCATED_NEWTON) {
+        if (a.boxes && a.n_hits <= (int64_t)a.n_events * 32 * KEPT_CHUNK) {
+            if (warps >= 32) return launch_batched_t<MODEL, P, 32, UPD, true>(a, prm, ctas, st);
+            if (warps >= 16) return launch_batched_t<MODEL, P, 16, UPD, true>(a, prm, ctas, st);
+            return launch_batched_t<MODEL, P, 8, UPD, true>(a, prm, ctas, st);
+        }
+    }
     if (warps >= 32) return launch_batched_t<MODEL, P, 32, UPD>(a, prm, ctas, st);
     if (warps >= 16) return launch_batched_t<MODEL, P, 16, UPD>(a, prm, ctas, st);
     return launch_batched_t<MODEL, P, 8, UPD>(a, prm, ctas, st);

@@ -518,13 +518,16 @@ __device__ __forceinline__ bool span_culled(const float4 A, const float w, const
 // list (consecutive chunks while they fit), and the warp walks the list,
 // lane l taking hit 32 b + l of each block: the same per-lane order as the full pass minus blocks whose terms
 // are all exactly zero - so every sum is bitwise the full pass's sum.
-// Returns the hits visited (for the work counters).
-template <int MODEL, int UNROLL = 2, typename T, typename F, typename F2>
+// With REUSE, reuse >= 0 walks list[0 .. reuse) as an earlier pass left it,
+// without tests (the caller knows it holds every block this pass needs), and
+// reuse == -2 reports through built the number of kept blocks when one walk
+// held them all (else -1).  Returns the hits visited (for the work counters).
+template <int MODEL, int UNROLL = 2, bool REUSE = false, typename T, typename F, typename F2>
 __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const float4 *__restrict__ gh, int n_staged,
                                         int H, int lane, const float4 *__restrict__ sbox, const float *__restrict__ sz2,
                                         const float4 *__restrict__ ssb, const float *__restrict__ ssz2,
                                         const float4 *__restrict__ gbox, int n_sbox, int *__restrict__ list,
-                                        T &&needed, F &&f, F2 &&f2) {
+                                        T &&needed, F &&f, F2 &&f2, int reuse = -1, int *built = nullptr) {
     if (!gbox) {
         for_each_hit(sh, gh, n_staged, H, lane, f, f2);
         return H;
@@ -536,11 +539,14 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
     // Kept blocks of consecutive chunks collect in the list (increasing block
     // order) as long as a chunk's candidates are sure to fit; then the list
     // is walked once - usually a single walk per pass.
-    int c0 = 0;
+    int c0 = 0, walks = 0, first = -1;
     for (;;) {
         int cnt = 0;
         bool done = false;
-        for (;;) {
+        if (REUSE && reuse >= 0) {  // the list an earlier pass built
+            cnt = reuse;
+            done = true;
+        } else for (;;) {
             if (c0 >= nblk) {
                 done = true;
                 break;
@@ -651,7 +657,13 @@ __device__ __forceinline__ int hit_pass(const float4 *__restrict__ sh, const flo
             }
             __syncwarp();  // the list is rewritten by the next round
         }
+        if constexpr (REUSE) {
+            if (walks++ == 0) first = cnt;
+        }
         if (done) break;
+    }
+    if constexpr (REUSE) {
+        if (built) *built = (reuse == -2 && walks == 1) ? first : -1;  // the whole kept set, if one walk held it
     }
     return visited;
 }
@@ -890,7 +902,7 @@ struct GroupState {
     bool live[P], failed[P], pending[P];
 };
 
-template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON, bool SS = false>
+template <int MODEL, int P, int UPD = RETINA_UPDATE_TRUNCATED_NEWTON, bool SS = false, bool RL = false>
 __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, const float4 *__restrict__ gh,
                                              int n_staged, int H, int lane, const float4 *__restrict__ sbox,
                                              const float *__restrict__ sz2, const float4 *__restrict__ ssb,
@@ -934,7 +946,26 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
             acc[p].zero();
             cp[p] = cull_pt<MODEL>(gs.th0[p], gs.th1[p], kk, cull);
         }
-        const CullSpan span = cull_span<P>(gs.th0, gs.th1, gs.live, cull);
+        CullSpan span = cull_span<P>(gs.th0, gs.th1, gs.live, cull);
+        // RL (packed slope-model groups on events of one 128-block chunk,
+        // where each box test is one block per lane, with no superblocks):
+        // this pass tests its blocks against the points' box grown by one
+        // capped step - every trial point of the update lies inside it
+        // (|p_a| <= cap step_a, t <= 1; the 0.1 % covers the roundings) - so
+        // that the list, when one walk holds it, serves all the update's
+        // trials without tests; the extra blocks add exact zeros.
+        int kept = -1;
+        bool reuse = false;
+        if constexpr (RL) {
+            static_assert(P % 2 == 0 && MODEL == RETINA_VELO_SLOPES, "packed slope-model groups");
+            reuse = ((H + 31) >> 5) <= KEPT_CHUNK;
+            const float g = reuse ? 1.001f * prm.cap : 0.f;
+            const float d0 = g * prm.box.step0, d1 = g * prm.box.step1;
+            span.t0lo -= d0;
+            span.t0hi += d0;
+            span.t1lo -= d1;
+            span.t1hi += d1;
+        }
         auto needed = [&](const float4 A, const float z2) {
             if constexpr (P % 2 == 0 && MODEL == RETINA_VELO_SLOPES) return !span_culled(A, z2, span);
             bool need = false;
@@ -955,7 +986,7 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                 a2[q].set(gs.th0[2 * q], gs.th1[2 * q], gs.th0[2 * q + 1], gs.th1[2 * q + 1], kk);
                 a2[q].zero();
             }
-            vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
+            vis = hit_pass<MODEL, 2, RL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed,
                                   [&](const float4 h) {
 #pragma unroll
                                       for (int q = 0; q < NP; ++q) a2[q].add(h);
@@ -966,7 +997,8 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                           a2[q].add(a);
                                           a2[q].add(b);
                                       }
-                                  });
+                                  },
+                                  reuse ? -2 : -1, &kept);
             if constexpr (SS) {
                 tot_ss = scatter_sums4(a2[0].S, a2[1].S, lane);
             } else {
@@ -1064,7 +1096,8 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                     Rt2[q] = 0ull;
                 }
                 const unsigned long long nkk = pack2(-kk, -kk);
-                vis = hit_pass<MODEL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list, needed_r,
+                vis = hit_pass<MODEL, 2, RL>(sh, gh, n_staged, H, lane, sbox, sz2, ssb, ssz2, gbox, n_sbox, list,
+                                      needed_r,
                                       [&](const float4 h) {
 #pragma unroll
                                           for (int q = 0; q < NP; ++q) pair_r_x2(h, nt0[q], nt1[q], nkk, Rt2[q]);
@@ -1075,7 +1108,8 @@ __device__ __forceinline__ void search_group(const float4 *__restrict__ sh, cons
                                               pair_r_x2(a, nt0[q], nt1[q], nkk, Rt2[q]);
                                               pair_r_x2(b, nt0[q], nt1[q], nkk, Rt2[q]);
                                           }
-                                      });
+                                      },
+                                      kept);
                 if constexpr (SS) {
                     rt_ss = group_sums4(Rt2[0], Rt2[1], lane);
                 } else {
