@@ -66,16 +66,80 @@ __device__ __forceinline__ uint32_t chunk_key(const float4 *__restrict__ hits, i
     return i < n ? ((hit_code(__ldg(hits + base + i), model) << IDX_BITS) | (uint32_t)i) : 0xffffffffu;
 }
 
+// Stable LSD radix sort of the 1024 R keys a CTA holds blocked (thread t
+// holds positions t R .. t R + R - 1) by their code bits (above the
+// IDX_BITS position bits), RADIX_BITS a pass.  A pass counts every thread's
+// keys per digit into digit-major, thread-minor counters, scans them in
+// that order, and moves each key to its digit's start plus the keys of
+// that digit in earlier threads and earlier in its own thread: equal
+// digits keep their order, so after the last pass the keys are in their
+// one sorted order (the positions make them distinct).  Linear in the keys,
+// where the bitonic network does log^2 stages of compare-exchanges.
+// x: 1024 R keys of exchange; ctr: RADIX x PREP_THREADS counters.
+constexpr int RADIX_BITS = 4, RADIX = 1 << RADIX_BITS;
+constexpr int CODE_BITS = 32 - IDX_BITS;  // codes are below 2^19 = 2^CODE_BITS
+template <int R>
+__device__ __forceinline__ void radix_sort_regs(uint32_t (&v)[R], uint32_t *x, uint32_t *ctr) {
+    __shared__ uint32_t wsum[PREP_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll 1
+    for (int s = IDX_BITS; s < IDX_BITS + CODE_BITS; s += RADIX_BITS) {
+        uint32_t off[R];
+        int dg[R];
+#pragma unroll
+        for (int d = 0; d < RADIX; ++d) ctr[d * PREP_THREADS + t] = 0;  // this thread's column
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            dg[r] = (int)((v[r] >> s) & (RADIX - 1));
+            off[r] = ctr[dg[r] * PREP_THREADS + t];
+            ctr[dg[r] * PREP_THREADS + t] = off[r] + 1;
+        }
+        __syncthreads();
+        // exclusive scan of the RADIX x PREP_THREADS counters in index order:
+        // thread t owns entries RADIX t .. RADIX t + RADIX - 1
+        uint32_t loc[RADIX], tot = 0;
+#pragma unroll
+        for (int j = 0; j < RADIX; ++j) {
+            loc[j] = ctr[RADIX * t + j];
+            tot += loc[j];
+        }
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        uint32_t run = inc - tot;
+        for (int i = 0; i < w; ++i) run += wsum[i];
+#pragma unroll
+        for (int j = 0; j < RADIX; ++j) {
+            ctr[RADIX * t + j] = run;
+            run += loc[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[ctr[dg[r] * PREP_THREADS + t] + off[r]] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[t * R + r];
+        // the next pass first rewrites only this thread's counter column and
+        // this thread's exchange reads are its own; its scatter comes after
+        // two more barriers
+    }
+}
+
 // Keys of chunk positions t R + r, sorted, then the hits gathered in key
 // order to sorted[base ..] (a super-chunk that is one chunk).
 template <int R>
 __device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits, int64_t base, int n, int model,
-                                                float4 *__restrict__ sorted, uint32_t *x) {
+                                                float4 *__restrict__ sorted, uint32_t *x, uint32_t *ctr) {
     uint32_t v[R];
     const int t = threadIdx.x;
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = chunk_key(hits, base, t * R + r, n, model);
-    bitonic_sort_regs<uint32_t, R, PREP_THREADS>(v, x);
+    radix_sort_regs<R>(v, x, ctr);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = t * R + r;
@@ -87,12 +151,12 @@ __device__ __forceinline__ void sort_and_gather(const float4 *__restrict__ hits,
 // sort's exchange buffer).
 template <int R>
 __device__ __forceinline__ void sort_keys(const float4 *__restrict__ hits, int64_t base, int n, int model,
-                                          uint32_t *K) {
+                                          uint32_t *K, uint32_t *ctr) {
     uint32_t v[R];
     const int t = threadIdx.x;
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = chunk_key(hits, base, t * R + r, n, model);
-    bitonic_sort_regs<uint32_t, R, PREP_THREADS>(v, K);
+    radix_sort_regs<R>(v, K, ctr);
     __syncthreads();  // every exchange read is done before K holds the result
 #pragma unroll
     for (int r = 0; r < R; ++r) K[t * R + r] = v[r];
@@ -100,15 +164,19 @@ __device__ __forceinline__ void sort_keys(const float4 *__restrict__ hits, int64
 
 template <bool GATHER>
 __device__ __forceinline__ void sort_chunk(const float4 *__restrict__ hits, int64_t base, int n, int model,
-                                           float4 *__restrict__ sorted, uint32_t *x) {
+                                           float4 *__restrict__ sorted, uint32_t *x, uint32_t *ctr) {
     if (n <= PREP_THREADS) {
-        if (GATHER) sort_and_gather<1>(hits, base, n, model, sorted, x); else sort_keys<1>(hits, base, n, model, x);
+        if (GATHER) sort_and_gather<1>(hits, base, n, model, sorted, x, ctr);
+        else sort_keys<1>(hits, base, n, model, x, ctr);
     } else if (n <= 2 * PREP_THREADS) {
-        if (GATHER) sort_and_gather<2>(hits, base, n, model, sorted, x); else sort_keys<2>(hits, base, n, model, x);
+        if (GATHER) sort_and_gather<2>(hits, base, n, model, sorted, x, ctr);
+        else sort_keys<2>(hits, base, n, model, x, ctr);
     } else if (n <= 4 * PREP_THREADS) {
-        if (GATHER) sort_and_gather<4>(hits, base, n, model, sorted, x); else sort_keys<4>(hits, base, n, model, x);
+        if (GATHER) sort_and_gather<4>(hits, base, n, model, sorted, x, ctr);
+        else sort_keys<4>(hits, base, n, model, x, ctr);
     } else {
-        if (GATHER) sort_and_gather<8>(hits, base, n, model, sorted, x); else sort_keys<8>(hits, base, n, model, x);
+        if (GATHER) sort_and_gather<8>(hits, base, n, model, sorted, x, ctr);
+        else sort_keys<8>(hits, base, n, model, x, ctr);
     }
 }
 
@@ -190,7 +258,8 @@ __device__ __forceinline__ void chunk_boxes(const float4 *__restrict__ sorted, i
 __global__ void __launch_bounds__(PREP_THREADS)
 prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64_t *__restrict__ off, int model,
                     float4 *__restrict__ sorted, float4 *__restrict__ boxes) {
-    extern __shared__ __align__(16) uint32_t K[];  // [SUPER]: each chunk's sorted keys
+    extern __shared__ __align__(16) uint32_t K[];  // [SUPER]: each chunk's sorted keys, then the radix counters
+    uint32_t *ctr = K + SUPER;
     const int e = blockIdx.x;
     int64_t hb, he;
     event_range(off, n_hits, e, hb, he);
@@ -200,11 +269,11 @@ prepare_hits_kernel(const float4 *__restrict__ hits, int64_t n_hits, const int64
         const int ns = (int)((H - s0) < SUPER ? (H - s0) : SUPER);
         const int64_t base = hb + s0;
         if (ns <= SORT_CAP) {
-            sort_chunk<true>(hits, base, ns, model, sorted, K);
+            sort_chunk<true>(hits, base, ns, model, sorted, K, ctr);
         } else {
             const int nch = (ns + SORT_CAP - 1) / SORT_CAP;
             for (int c = 0; c < nch; ++c)
-                sort_chunk<false>(hits, base + c * SORT_CAP, chunk_size(ns, c), model, sorted, K + c * SORT_CAP);
+                sort_chunk<false>(hits, base + c * SORT_CAP, chunk_size(ns, c), model, sorted, K + c * SORT_CAP, ctr);
             __syncthreads();
             // merge by rank: chunk c's j-th key goes to j + (keys before it in the other chunks)
             for (int c = 0; c < nch; ++c) {
@@ -433,7 +502,7 @@ cudaError_t launch_prepare_hits(const float4 *hits, int64_t n_hits, const int64_
         count_launches(1);
         return cudaLaunchKernelEx(&cfg, prepare_hits_cluster_kernel, hits, n_hits, off, model, sorted, boxes);
     }
-    const size_t smem = (size_t)SUPER * sizeof(uint32_t);
+    const size_t smem = (size_t)(SUPER + RADIX * PREP_THREADS) * sizeof(uint32_t);
     {
         cudaError_t aerr = ensure_dynamic_smem(reinterpret_cast<const void *>(prepare_hits_kernel), smem);
         if (aerr != cudaSuccess) return aerr;
